@@ -1,0 +1,21 @@
+"""CPU oracle for the one-sided Jacobi hyperbolic SVD.
+
+Test infrastructure only: the tests, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` import it.  The library path never does; the two
+share no code.  ``hsvd_oracle.c`` holds the arithmetic, ``oracle.py`` the
+ctypes marshalling and its build step.
+"""
+from .oracle import (  # noqa: F401
+    ORC_ARG,
+    ORC_NONFINITE,
+    ORC_NOT_CONVERGED,
+    ORC_OK,
+    ORC_RANK,
+    block_hsvd,
+    build,
+    hsvd,
+    inner_solve,
+    load,
+    modulus_pairs,
+    rotation,
+)

@@ -1,0 +1,638 @@
+/*
+ * hsvd_oracle.c -- plain, slow, single-threaded FP64 CPU oracle for the
+ * one-sided Jacobi hyperbolic SVD (Novakovic & Singer, "A GPU-based hyperbolic
+ * SVD algorithm").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the library path may link, import or
+ * call this file: only the tests, the smoke check and the CPU-baseline leg of
+ * the benchmark use it.  It shares no code, header, table or constant with
+ * the CUDA library; the two are written independently from the paper.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fPIC -shared (contraction off, so every
+ * fused multiply-add in here is one written as fma() on purpose).
+ *
+ * Storage is column-major FP64 throughout, zero-based indices (Sec. 4).
+ *
+ * What each function follows:
+ *   orc_rotation       -- rotation parameters from a 2x2 pivot block
+ *                         (Sec. 2, Eq. 2.2, the theta/t definitions, Eq. 2.6).
+ *   orc_modulus_pairs  -- the modified modulus pivot strategy as the stepper
+ *                         of Alg. 4.3 / Alg. 4.4 (Sec. 2 text on the strategy).
+ *   orc_hsvd           -- pointwise one-sided hyperbolic Jacobi (Eq. 2.1,
+ *                         Eq. 2.3 test, Eq. 2.4/2.5 updates in the unified
+ *                         form of Alg. 4.5, Sec. 2 stopping rule), with the
+ *                         row-cyclic order or the modulus order and optional
+ *                         diagonal sorting (Sec. 4, Sort_Diagonal).
+ *   orc_inner_solve    -- J-orthogonalisation of one 2b x 2b pivot block A_P by
+ *                         two-sided rotations (Sec. 5 block-oriented method,
+ *                         Sec. 6 full-block variant), pair order taken from the
+ *                         modulus strategy applied inside the block.
+ *   orc_block_hsvd     -- blocked one-sided method: modulus strategy over block
+ *                         columns, Gram block, inner solve, G/V update
+ *                         (Sec. 5 block-oriented description, Eq. 2.1).
+ *
+ * Readings of the paper where it is silent or garbled (also listed in the
+ * design notes of the repository):
+ *   R1  theta as printed in Sec. 2 has the sign of `hyp' flipped against the
+ *       update of Alg. 4.5; requiring a'_ij = 0 under that update gives
+ *       theta = 2 a_ij / (-a_ii - hyp a_jj).  Eq. 2.6 agrees with this form.
+ *   R2  t is the smaller root of the zeroing quadratic (|phi| <= pi/4),
+ *       written through zeta so nothing overflows:
+ *         trigonometric  zeta = (a_jj - a_ii) / (2 a_ij),
+ *                        t = sign(zeta) / (|zeta| + sqrt(zeta^2 + 1)),
+ *                        c = 1 / sqrt(1 + t^2)
+ *         hyperbolic     zeta = -(a_ii + a_jj) / (2 a_ij),
+ *                        t = sign(zeta) / (|zeta| + sqrt(zeta^2 - 1)),
+ *                        c = 1 / sqrt((1 - t)(1 + t)).
+ *       sign(0) is +1.  |zeta| <= 1 in the hyperbolic case means the pair is
+ *       numerically rank deficient: status ORC_RANK, nothing is rotated.
+ *   R3  Alg. 4.4 as printed steps out of range with zero-based indices; the
+ *       threshold that reproduces the strategy described in Sec. 2 (r steps,
+ *       r/2 disjoint pairs per step, pairs (i, i+r/2) twice, next quasi-sweep
+ *       starting with the assignment reversed) is  ip + jp > r - 2.
+ *   R4  Sorting (Sec. 4): the J = +1 part by d decreasing, the J = -1 part by
+ *       d increasing, equal keys keep their current relative order.
+ *   R5  A sweep counts every sweep run, including the final one in which no
+ *       pair rotates (Sec. 2 stopping rule).
+ *   R6  A pair with a_ij == 0 exactly is orthogonal and is never rotated (the
+ *       strict test of Eq. 2.3 would otherwise "rotate" a zero column by the
+ *       identity for ever).  A zero column (sigma_j = 0) is rank deficiency,
+ *       which the paper excludes (Sec. 1): status ORC_RANK.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_NOT_CONVERGED 1
+#define ORC_ARG (-1)
+#define ORC_RANK (-2)
+#define ORC_NONFINITE (-3)
+
+/* ------------------------------------------------------------------------ */
+/* Rotation parameters (Sec. 2, Eq. 2.2; readings R1, R2).                    */
+/* hyp = -1: trigonometric (equal signs in J), +1: hyperbolic.                */
+/* The rotation applied to a column pair is                                   */
+/*   g_i' = (g_i + hyp*t*g_j) * c,   g_j' = (t*g_i + g_j) * c   (Alg. 4.5).   */
+/* ------------------------------------------------------------------------ */
+int orc_rotation(double aii, double ajj, double aij, int hyp, double *t, double *c)
+{
+    double zeta, tt;
+    if (hyp < 0) {
+        zeta = (ajj - aii) / (2.0 * aij);
+        tt = 1.0 / (fabs(zeta) + sqrt(zeta * zeta + 1.0));
+        if (zeta < 0.0) tt = -tt;
+        *t = tt;
+        *c = 1.0 / sqrt(1.0 + tt * tt);
+        return ORC_OK;
+    }
+    zeta = -(aii + ajj) / (2.0 * aij);
+    if (!(fabs(zeta) > 1.0)) {
+        *t = 0.0;
+        *c = 1.0;
+        return ORC_RANK;
+    }
+    tt = 1.0 / (fabs(zeta) + sqrt(zeta * zeta - 1.0));
+    if (zeta < 0.0) tt = -tt;
+    *t = tt;
+    *c = 1.0 / sqrt((1.0 - tt) * (1.0 + tt));
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Modified modulus strategy (Sec. 2; Alg. 4.3 and Alg. 4.4 with R3).        */
+/* r even.  pairs[(s*(r/2) + k)*2 + {0,1}] = pivot pair of task k at step s,  */
+/* for s = 0 .. nsteps-1 (nsteps may exceed r: the stepper just continues).   */
+/* ------------------------------------------------------------------------ */
+void orc_modulus_pairs(int r, int nsteps, int *pairs)
+{
+    int half = r / 2;
+    int *ip = (int *)malloc(sizeof(int) * half), *jp = (int *)malloc(sizeof(int) * half);
+    int *ib = (int *)malloc(sizeof(int) * half), *jb = (int *)malloc(sizeof(int) * half);
+    for (int k = 0; k < half; ++k) { /* Alg. 4.3: antidiagonal start */
+        ip[k] = k;
+        ib[k] = k;
+        jp[k] = r - k - 1;
+        jb[k] = jp[k];
+    }
+    for (int s = 0; s < nsteps; ++s) {
+        for (int k = 0; k < half; ++k) {
+            pairs[(s * half + k) * 2 + 0] = ib[k];
+            pairs[(s * half + k) * 2 + 1] = jb[k];
+        }
+        for (int k = 0; k < half; ++k) { /* Alg. 4.4 with threshold r-2 */
+            if (ip[k] + jp[k] > r - 2) {
+                ip[k] = ip[k] + 1;
+                if (ip[k] == jp[k]) {
+                    ip[k] = ip[k] - half;
+                    jp[k] = ip[k];
+                }
+                ib[k] = ip[k];
+            } else {
+                jp[k] = jp[k] + 1;
+                jb[k] = jp[k];
+            }
+        }
+    }
+    free(ip); free(jp); free(ib); free(jb);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Small helpers (plain loops).                                               */
+/* ------------------------------------------------------------------------ */
+static double dot(int64_t m, const double *x, const double *y)
+{
+    double s = 0.0;
+    for (int64_t i = 0; i < m; ++i) s += x[i] * y[i];
+    return s;
+}
+
+/* Euclidean norm with the scale / sum-of-squares recurrence of the reference
+ * BLAS dnrm2, so no intermediate overflows or underflows. */
+static double nrm2(int64_t m, const double *x)
+{
+    double scale = 0.0, ssq = 1.0;
+    for (int64_t i = 0; i < m; ++i) {
+        if (x[i] != 0.0) {
+            double a = fabs(x[i]);
+            if (scale < a) {
+                ssq = 1.0 + ssq * (scale / a) * (scale / a);
+                scale = a;
+            } else {
+                ssq += (a / scale) * (a / scale);
+            }
+        }
+    }
+    return scale * sqrt(ssq);
+}
+
+/* Column update of Alg. 4.5 (Eq. 2.4 / 2.5): the parenthesised term with one
+ * fused multiply-add (Sec. 2), then the scaling by c. */
+static void rotate_cols(int64_t m, double *x, double *y, int hyp, double t, double c)
+{
+    double ht = hyp < 0 ? -t : t;
+    for (int64_t i = 0; i < m; ++i) {
+        double xi = x[i], yi = y[i];
+        x[i] = fma(ht, yi, xi) * c;
+        y[i] = fma(t, xi, yi) * c;
+    }
+}
+
+static int all_finite(int64_t m, int64_t n, const double *G, int64_t ld)
+{
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t i = 0; i < m; ++i)
+            if (!isfinite(G[i + j * ld])) return 0;
+    return 1;
+}
+
+/* Sorting permutation (Sec. 4, Sort_Diagonal; reading R4).  pos[] lists the
+ * columns in their current order; on return it lists them sorted, J+ part by
+ * d decreasing then J- part by d increasing, equal keys in current order.
+ * Written as a plain stable insertion sort. */
+static void sort_positions(int n, int *pos, const double *d, const int8_t *sgn)
+{
+    int *tmp = (int *)malloc(sizeof(int) * n);
+    int np = 0;
+    for (int k = 0; k < n; ++k)
+        if (sgn[pos[k]] > 0) tmp[np++] = pos[k];
+    int nm = np;
+    for (int k = 0; k < n; ++k)
+        if (sgn[pos[k]] < 0) tmp[nm++] = pos[k];
+    for (int k = 1; k < np; ++k) { /* decreasing d */
+        int v = tmp[k], x = k - 1;
+        while (x >= 0 && d[tmp[x]] < d[v]) { tmp[x + 1] = tmp[x]; --x; }
+        tmp[x + 1] = v;
+    }
+    for (int k = np + 1; k < n; ++k) { /* increasing d */
+        int v = tmp[k], x = k - 1;
+        while (x >= np && d[tmp[x]] > d[v]) { tmp[x + 1] = tmp[x]; --x; }
+        tmp[x + 1] = v;
+    }
+    memcpy(pos, tmp, sizeof(int) * n);
+    free(tmp);
+}
+
+/* Finalisation (Sec. 2): sigma_j = ||g_j||, u_j = g_j / sigma_j, V = W. */
+static void finalise(int64_t m, int64_t n, const double *Gw, const double *W,
+                     double *sigma, double *U, int64_t ldu, double *V, int64_t ldv)
+{
+    for (int64_t j = 0; j < n; ++j) {
+        double s = nrm2(m, Gw + j * m);
+        sigma[j] = s;
+        if (U)
+            for (int64_t i = 0; i < m; ++i) U[i + j * ldu] = Gw[i + j * m] / s;
+        if (V)
+            for (int64_t i = 0; i < n; ++i) V[i + j * ldv] = W[i + j * n];
+    }
+}
+
+/* One pivot pair of the pointwise method: Gram entries recomputed from the
+ * current columns, the relative orthogonality test (Eq. 2.3), and if it fails
+ * the rotation of the G and W columns (Alg. 4.5). */
+static int pointwise_pair(int64_t mw, int64_t nw, double *Gw, double *W, const int8_t *sgn,
+                          double tol, int pi, int pj, int64_t *nrot)
+{
+    double *gi = Gw + (int64_t)pi * mw, *gj = Gw + (int64_t)pj * mw;
+    double aii = dot(mw, gi, gi), ajj = dot(mw, gj, gj), aij = dot(mw, gi, gj);
+    if (aij == 0.0 || fabs(aij) < tol * sqrt(aii * ajj)) return ORC_OK; /* Eq. 2.3, R6 */
+    int hyp = (sgn[pi] == sgn[pj]) ? -1 : 1;
+    double t, c;
+    if (orc_rotation(aii, ajj, aij, hyp, &t, &c) != ORC_OK) return ORC_RANK;
+    rotate_cols(mw, gi, gj, hyp, t, c);
+    rotate_cols(nw, W + (int64_t)pi * nw, W + (int64_t)pj * nw, hyp, t, c);
+    ++*nrot;
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Pointwise one-sided hyperbolic Jacobi (Eq. 2.1 - 2.5, Alg. 4.5).           */
+/*   order 0: row-cyclic (i < j, i outer), the sequential comparison method   */
+/*            of Sec. 5;                                                      */
+/*   order 1: modified modulus strategy (Sec. 2), pairs of a step applied one */
+/*            after the other (they are disjoint, so this equals applying     */
+/*            them at once), positions mapped to columns through the current  */
+/*            permutation (Sec. 4: columns are never moved).                  */
+/* For order 1 the columns are first grouped J+ then J- (Alg. 4.2 assumes     */
+/* J = diag(I_p, -I_{n-p})), odd n gets one bordering column (Eq. 4.1).       */
+/* sort != 0 sorts the positions before the first sweep and after each sweep  */
+/* (Alg. 4.1).  Returns ORC_OK, ORC_NOT_CONVERGED, ORC_RANK, ORC_NONFINITE or */
+/* ORC_ARG; sigma, U (m x n, ldu) and V (n x n, ldv; either may be NULL) are   */
+/* written in input column order.                                             */
+/* ------------------------------------------------------------------------ */
+int orc_hsvd(int64_t m, int64_t n, const double *G, int64_t ldg, const int8_t *J,
+             double tol, int max_sweeps, int order, int sort,
+             double *sigma, double *U, int64_t ldu, double *V, int64_t ldv,
+             int *sweeps, int64_t *rotations)
+{
+    if (m < n || n < 1 || ldg < m || max_sweeps < 1 || !(tol > 0.0)) return ORC_ARG;
+    for (int64_t j = 0; j < n; ++j)
+        if (J[j] != 1 && J[j] != -1) return ORC_ARG;
+    if (!all_finite(m, n, G, ldg)) return ORC_NONFINITE;
+
+    /* working copy, bordered with one unit column in a fresh row if the
+     * modulus strategy needs an even order (Eq. 4.1) */
+    int64_t nw = (order == 1 && (n % 2)) ? n + 1 : n;
+    int64_t mw = m + (nw - n);
+    double *Gw = (double *)calloc((size_t)(mw * nw), sizeof(double));
+    double *W = (double *)calloc((size_t)(nw * nw), sizeof(double));
+    int8_t *sgn = (int8_t *)malloc((size_t)nw);
+    double *d = (double *)malloc(sizeof(double) * (size_t)nw);
+    int *pos = (int *)malloc(sizeof(int) * (size_t)nw);
+    for (int64_t j = 0; j < n; ++j) {
+        for (int64_t i = 0; i < m; ++i) Gw[i + j * mw] = G[i + j * ldg];
+        sgn[j] = J[j];
+    }
+    for (int64_t j = n; j < nw; ++j) {
+        Gw[(m + (j - n)) + j * mw] = 1.0;
+        sgn[j] = 1;
+    }
+    for (int64_t j = 0; j < nw; ++j) W[j + j * nw] = 1.0;
+
+    int *pairs = NULL;
+    if (order == 1) {
+        pairs = (int *)malloc(sizeof(int) * (size_t)(nw * nw));
+        orc_modulus_pairs((int)nw, (int)nw, pairs);
+        int k = 0; /* J+ first, J- after, each in input order */
+        for (int64_t j = 0; j < nw; ++j) if (sgn[j] > 0) pos[k++] = (int)j;
+        for (int64_t j = 0; j < nw; ++j) if (sgn[j] < 0) pos[k++] = (int)j;
+    } else {
+        for (int64_t j = 0; j < nw; ++j) pos[j] = (int)j;
+    }
+
+    int status = ORC_NOT_CONVERGED, sw = 0;
+    int64_t nrot_total = 0;
+    if (order == 1 && sort) {
+        for (int64_t j = 0; j < nw; ++j) d[j] = dot(mw, Gw + j * mw, Gw + j * mw);
+        sort_positions((int)nw, pos, d, sgn);
+    }
+    for (sw = 1; sw <= max_sweeps; ++sw) {
+        int64_t nrot = 0;
+        int st = ORC_OK;
+        if (order == 1) {
+            for (int64_t q = 0; q < nw * (nw / 2) && st == ORC_OK; ++q) {
+                int a = pairs[q * 2], b = pairs[q * 2 + 1];
+                st = pointwise_pair(mw, nw, Gw, W, sgn, tol, pos[a < b ? a : b], pos[a < b ? b : a], &nrot);
+            }
+        } else {
+            for (int64_t i = 0; i < nw - 1 && st == ORC_OK; ++i)
+                for (int64_t j = i + 1; j < nw && st == ORC_OK; ++j)
+                    st = pointwise_pair(mw, nw, Gw, W, sgn, tol, (int)i, (int)j, &nrot);
+        }
+        if (st != ORC_OK) {
+            status = st;
+            goto done;
+        }
+        nrot_total += nrot;
+        if (nrot == 0) {
+            status = ORC_OK;
+            break;
+        }
+        if (order == 1 && sort) {
+            for (int64_t j = 0; j < nw; ++j) d[j] = dot(mw, Gw + j * mw, Gw + j * mw);
+            sort_positions((int)nw, pos, d, sgn);
+        }
+    }
+    if (sw > max_sweeps) sw = max_sweeps;
+    if (!all_finite(mw, nw, Gw, mw)) status = ORC_NONFINITE;
+done:
+    if (status == ORC_OK || status == ORC_NOT_CONVERGED) {
+        /* drop the bordering row/column: the unit column never rotates */
+        double *Gc = (double *)malloc(sizeof(double) * (size_t)(m * n));
+        double *Wc = (double *)malloc(sizeof(double) * (size_t)(n * n));
+        for (int64_t j = 0; j < n; ++j) {
+            for (int64_t i = 0; i < m; ++i) Gc[i + j * m] = Gw[i + j * mw];
+            for (int64_t i = 0; i < n; ++i) Wc[i + j * n] = W[i + j * nw];
+        }
+        finalise(m, n, Gc, Wc, sigma, U, ldu, V, ldv);
+        for (int64_t j = 0; j < n; ++j)
+            if (!(sigma[j] > 0.0)) status = ORC_RANK;
+        free(Gc);
+        free(Wc);
+    }
+    if (sweeps) *sweeps = sw;
+    if (rotations) *rotations = nrot_total;
+    free(Gw); free(W); free(sgn); free(d); free(pos); free(pairs);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Inner solve: J-orthogonalisation of a pivot block A_P (nn x nn, nn even,   */
+/* symmetric, column-major, ld = nn) with signs sgn[nn] (Sec. 5 block method, */
+/* Sec. 6 full-block variant).  The rotations of one inner step are the       */
+/* disjoint pairs of one step of a pivot strategy; all of them are computed   */
+/* from the step's starting A, then applied at once:                          */
+/*   - pair (p,q), p < q: test Eq. 2.3 on (a_pp, a_qq, a_pq); if it fails,    */
+/*     (t, c) from orc_rotation, else t = 0, c = 1 (identity);                */
+/*   - for two different pairs k, l with p_k < p_l, the 2x2 block           */
+/*     B = A[{p_k,q_k},{p_l,q_l}] becomes R_k^T B R_l, computed as the row    */
+/*     update with R_k first and the column update with R_l second, each      */
+/*     entry in the form fma(hyp*t, other, own) * c (Alg. 4.5);              */
+/*     A is kept symmetric by writing each result to both (x,y) and (y,x);    */
+/*   - for a rotated pair, Eq. 2.6: a_pp += hyp*t*a_pq, a_qq += t*a_pq (one   */
+/*     fma each), a_pq = a_qp = 0;                                            */
+/*   - W <- W R: columns p, q of W as in Alg. 4.5.                           */
+/* Modes:                                                                     */
+/*   0 full-block: passes of the modulus strategy over nn indices (nn steps), */
+/*     until a pass rotates nothing or max_passes passes ran;                 */
+/*   1 cross pass: one pass over the pairs (k, h + ((k + s) mod h)),          */
+/*     s = 0 .. h-1, h = nn/2 -- only the off-diagonal block of A_P (Sec. 5,  */
+/*     block-oriented method, steps after the first);                         */
+/*   2 one pass of the modulus strategy over all nn indices (Sec. 5, first    */
+/*     step of the block-oriented method).                                    */
+/* W (nn x nn) receives the accumulated transformation, starting from I.      */
+/* ------------------------------------------------------------------------ */
+int orc_inner_solve(int nn, double *A, const int8_t *sgn, double tol, int mode,
+                    int max_passes, double *W, int64_t *nrot_out, int *passes_out)
+{
+    if (nn < 2 || (nn % 2) || max_passes < 1) return ORC_ARG;
+    int h = nn / 2;
+    int *pairs = (int *)malloc(sizeof(int) * (size_t)nn * (size_t)h * 2);
+    int *P = (int *)malloc(sizeof(int) * h), *Q = (int *)malloc(sizeof(int) * h);
+    double *T = (double *)malloc(sizeof(double) * h), *C = (double *)malloc(sizeof(double) * h);
+    int *H = (int *)malloc(sizeof(int) * h), *rot = (int *)malloc(sizeof(int) * h);
+    orc_modulus_pairs(nn, nn, pairs);
+    memset(W, 0, sizeof(double) * (size_t)nn * nn);
+    for (int i = 0; i < nn; ++i) W[i + i * nn] = 1.0;
+#define AE(x, y) A[(x) + (int64_t)(y) * nn]
+    int status = ORC_OK, npass = 0;
+    int64_t nrot_total = 0;
+    int npass_max = (mode == 0) ? max_passes : 1;
+    for (int pass = 0; pass < npass_max; ++pass) {
+        ++npass;
+        int64_t nrot_pass = 0;
+        int nsteps = (mode == 1) ? h : nn;
+        for (int s = 0; s < nsteps; ++s) {
+            for (int k = 0; k < h; ++k) {
+                int a, b;
+                if (mode == 1) {
+                    a = k;
+                    b = h + ((k + s) % h);
+                } else {
+                    a = pairs[(s * h + k) * 2];
+                    b = pairs[(s * h + k) * 2 + 1];
+                }
+                P[k] = a < b ? a : b;
+                Q[k] = a < b ? b : a;
+            }
+            for (int k = 0; k < h; ++k) {
+                int p = P[k], q = Q[k];
+                double app = AE(p, p), aqq = AE(q, q), apq = AE(p, q);
+                H[k] = (sgn[p] == sgn[q]) ? -1 : 1;
+                T[k] = 0.0;
+                C[k] = 1.0;
+                rot[k] = 0;
+                if (apq == 0.0 || fabs(apq) < tol * sqrt(app * aqq)) continue; /* Eq. 2.3, R6 */
+                if (orc_rotation(app, aqq, apq, H[k], &T[k], &C[k]) != ORC_OK) {
+                    status = ORC_RANK;
+                    goto out;
+                }
+                rot[k] = 1;
+                ++nrot_pass;
+            }
+            /* off-diagonal 2x2 blocks between different pairs; of two pairs
+             * the one with the smaller first index takes the row update */
+            for (int k = 0; k < h; ++k) {
+                for (int l = 0; l < h; ++l) {
+                    if (!(P[k] < P[l])) continue;
+                    int rk[2] = {P[k], Q[k]}, cl[2] = {P[l], Q[l]};
+                    double B[2][2], X[2][2];
+                    for (int x = 0; x < 2; ++x)
+                        for (int y = 0; y < 2; ++y) B[x][y] = AE(rk[x], cl[y]);
+                    double htk = H[k] < 0 ? -T[k] : T[k];
+                    double htl = H[l] < 0 ? -T[l] : T[l];
+                    for (int y = 0; y < 2; ++y) { /* rows: R_k^T B */
+                        X[0][y] = fma(htk, B[1][y], B[0][y]) * C[k];
+                        X[1][y] = fma(T[k], B[0][y], B[1][y]) * C[k];
+                    }
+                    for (int x = 0; x < 2; ++x) { /* columns: (R_k^T B) R_l */
+                        B[x][0] = fma(htl, X[x][1], X[x][0]) * C[l];
+                        B[x][1] = fma(T[l], X[x][0], X[x][1]) * C[l];
+                    }
+                    for (int x = 0; x < 2; ++x)
+                        for (int y = 0; y < 2; ++y) {
+                            AE(rk[x], cl[y]) = B[x][y];
+                            AE(cl[y], rk[x]) = B[x][y];
+                        }
+                }
+            }
+            /* diagonal blocks: Eq. 2.6 */
+            for (int k = 0; k < h; ++k) {
+                if (!rot[k]) continue;
+                int p = P[k], q = Q[k];
+                double apq = AE(p, q);
+                double ht = H[k] < 0 ? -T[k] : T[k];
+                AE(p, p) = fma(ht, apq, AE(p, p));
+                AE(q, q) = fma(T[k], apq, AE(q, q));
+                AE(p, q) = 0.0;
+                AE(q, p) = 0.0;
+            }
+            /* W <- W R */
+            for (int k = 0; k < h; ++k) {
+                if (!rot[k]) continue;
+                rotate_cols(nn, W + (int64_t)P[k] * nn, W + (int64_t)Q[k] * nn, H[k], T[k], C[k]);
+            }
+        }
+        nrot_total += nrot_pass;
+        if (nrot_pass == 0) break;
+    }
+out:
+#undef AE
+    if (nrot_out) *nrot_out = nrot_total;
+    if (passes_out) *passes_out = npass;
+    free(pairs); free(P); free(Q); free(T); free(C); free(H); free(rot);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Blocked one-sided hyperbolic Jacobi (Sec. 5 block-oriented method; the     */
+/* transformation of a pivot block applied to G_P and V_P from the right,     */
+/* Eq. 2.1).  Columns are bordered (Eq. 4.1) to a multiple of 2b with unit    */
+/* columns in fresh rows (sign +1), grouped J+ then J-, optionally sorted     */
+/* (reading R4) before the first sweep and after each sweep, and the columns  */
+/* are physically reordered to follow that order.  Each sweep runs nb steps   */
+/* of the modulus strategy over the nb = n'/b block columns; each pair        */
+/* (I, J) of a step forms A_P = [G_I G_J]^T [G_I G_J] (plain triple loop),    */
+/* calls orc_inner_solve (inner_mode 0: full-block with inner_max_passes;     */
+/* inner_mode 1: block-oriented -- whole block in the first step of a sweep,  */
+/* cross pass afterwards), and, if any inner rotation was applied, updates    */
+/* [G_I G_J] <- [G_I G_J] W_P and [V_I V_J] <- [V_I V_J] W_P (plain triple    */
+/* loops).  Stops after a sweep with no rotation.  Outputs in input order.    */
+/* ------------------------------------------------------------------------ */
+int orc_block_hsvd(int64_t m, int64_t n, const double *G, int64_t ldg, const int8_t *J,
+                   int b, double tol, int max_sweeps, int inner_mode, int inner_max_passes,
+                   int sort, double *sigma, double *U, int64_t ldu, double *V, int64_t ldv,
+                   int *sweeps, int64_t *rotations)
+{
+    if (m < n || n < 1 || ldg < m || b < 1 || max_sweeps < 1 || !(tol > 0.0)) return ORC_ARG;
+    for (int64_t j = 0; j < n; ++j)
+        if (J[j] != 1 && J[j] != -1) return ORC_ARG;
+    if (!all_finite(m, n, G, ldg)) return ORC_NONFINITE;
+    int64_t nw = ((n + 2 * b - 1) / (2 * b)) * (2 * b);
+    int64_t mw = m + (nw - n);
+    int nb = (int)(nw / b), nn = 2 * b;
+    double *Gw = (double *)calloc((size_t)(mw * nw), sizeof(double));
+    double *W = (double *)calloc((size_t)(nw * nw), sizeof(double));
+    double *Gt = (double *)malloc(sizeof(double) * (size_t)(mw * nw));
+    double *Wt = (double *)malloc(sizeof(double) * (size_t)(nw * nw));
+    int8_t *sgn = (int8_t *)malloc((size_t)nw), *sgt = (int8_t *)malloc((size_t)nw);
+    int *col = (int *)malloc(sizeof(int) * (size_t)nw), *colt = (int *)malloc(sizeof(int) * (size_t)nw);
+    int *pos = (int *)malloc(sizeof(int) * (size_t)nw);
+    double *d = (double *)malloc(sizeof(double) * (size_t)nw);
+    double *A = (double *)malloc(sizeof(double) * nn * nn), *Wp = (double *)malloc(sizeof(double) * nn * nn);
+    double *Pan = (double *)malloc(sizeof(double) * (size_t)(mw > nw ? mw : nw) * nn);
+    int8_t *ps = (int8_t *)malloc(nn);
+    int *pairs = (int *)malloc(sizeof(int) * (size_t)nb * nb);
+    orc_modulus_pairs(nb, nb, pairs);
+
+    /* bordered copy; col[k] = input column held at working position k */
+    for (int64_t j = 0; j < n; ++j) {
+        for (int64_t i = 0; i < m; ++i) Gt[i + j * mw] = G[i + j * ldg];
+        for (int64_t i = m; i < mw; ++i) Gt[i + j * mw] = 0.0;
+        sgt[j] = J[j];
+    }
+    for (int64_t j = n; j < nw; ++j) {
+        for (int64_t i = 0; i < mw; ++i) Gt[i + j * mw] = 0.0;
+        Gt[(m + (j - n)) + j * mw] = 1.0;
+        sgt[j] = 1;
+    }
+    {
+        int k = 0;
+        for (int64_t j = 0; j < nw; ++j) if (sgt[j] > 0) pos[k++] = (int)j;
+        for (int64_t j = 0; j < nw; ++j) if (sgt[j] < 0) pos[k++] = (int)j;
+    }
+    if (sort) {
+        for (int64_t j = 0; j < nw; ++j) d[j] = dot(mw, Gt + j * mw, Gt + j * mw);
+        sort_positions((int)nw, pos, d, sgt);
+    }
+    for (int64_t k = 0; k < nw; ++k) {
+        memcpy(Gw + k * mw, Gt + (int64_t)pos[k] * mw, sizeof(double) * (size_t)mw);
+        sgn[k] = sgt[pos[k]];
+        col[k] = pos[k];
+        W[(int64_t)pos[k] + k * nw] = 1.0; /* W holds V's columns for the working order */
+    }
+
+    int status = ORC_NOT_CONVERGED, sw;
+    int64_t nrot_total = 0;
+    for (sw = 1; sw <= max_sweeps; ++sw) {
+        int64_t nrot = 0;
+        for (int s = 0; s < nb; ++s) {
+            for (int k = 0; k < nb / 2; ++k) {
+                int a = pairs[(s * (nb / 2) + k) * 2], bb = pairs[(s * (nb / 2) + k) * 2 + 1];
+                int I = a < bb ? a : bb, Jb = a < bb ? bb : a;
+                int cidx[2] = {I * b, Jb * b};
+                /* A_P = G_P^T G_P (plain triple loop) */
+                for (int y = 0; y < nn; ++y) {
+                    const double *gy = Gw + (int64_t)(cidx[y / b] + y % b) * mw;
+                    ps[y] = sgn[cidx[y / b] + y % b];
+                    for (int x = 0; x < nn; ++x) {
+                        const double *gx = Gw + (int64_t)(cidx[x / b] + x % b) * mw;
+                        A[x + y * nn] = dot(mw, gx, gy);
+                    }
+                }
+                int mode = (inner_mode == 0) ? 0 : (s == 0 ? 2 : 1);
+                int64_t nr = 0;
+                int st = orc_inner_solve(nn, A, ps, tol, mode, inner_max_passes, Wp, &nr, NULL);
+                if (st != ORC_OK) { status = st; goto done; }
+                if (nr == 0) continue;
+                nrot += nr;
+                /* [G_I G_J] <- [G_I G_J] W_P and [V_I V_J] <- [V_I V_J] W_P */
+                for (int which = 0; which < 2; ++which) {
+                    double *M = which ? W : Gw;
+                    int64_t rows = which ? nw : mw;
+                    for (int y = 0; y < nn; ++y)
+                        for (int64_t i = 0; i < rows; ++i) {
+                            double acc = 0.0;
+                            for (int x = 0; x < nn; ++x)
+                                acc += M[i + (int64_t)(cidx[x / b] + x % b) * rows] * Wp[x + y * nn];
+                            Pan[i + (int64_t)y * rows] = acc;
+                        }
+                    for (int y = 0; y < nn; ++y)
+                        memcpy(M + (int64_t)(cidx[y / b] + y % b) * rows, Pan + (int64_t)y * rows,
+                               sizeof(double) * (size_t)rows);
+                }
+            }
+        }
+        nrot_total += nrot;
+        if (nrot == 0) { status = ORC_OK; break; }
+        if (sort) {
+            for (int64_t k = 0; k < nw; ++k) { d[k] = dot(mw, Gw + k * mw, Gw + k * mw); pos[k] = (int)k; }
+            sort_positions((int)nw, pos, d, sgn);
+            memcpy(Gt, Gw, sizeof(double) * (size_t)(mw * nw));
+            memcpy(Wt, W, sizeof(double) * (size_t)(nw * nw));
+            memcpy(sgt, sgn, (size_t)nw);
+            memcpy(colt, col, sizeof(int) * (size_t)nw);
+            for (int64_t k = 0; k < nw; ++k) {
+                memcpy(Gw + k * mw, Gt + (int64_t)pos[k] * mw, sizeof(double) * (size_t)mw);
+                memcpy(W + k * nw, Wt + (int64_t)pos[k] * nw, sizeof(double) * (size_t)nw);
+                sgn[k] = sgt[pos[k]];
+                col[k] = colt[pos[k]];
+            }
+        }
+    }
+    if (sw > max_sweeps) sw = max_sweeps;
+    if (!all_finite(mw, nw, Gw, mw)) status = ORC_NONFINITE;
+done:
+    if (status == ORC_OK || status == ORC_NOT_CONVERGED) {
+        /* back to input order; drop the bordering */
+        double *Gc = (double *)malloc(sizeof(double) * (size_t)(m * n));
+        double *Wc = (double *)malloc(sizeof(double) * (size_t)(n * n));
+        for (int64_t k = 0; k < nw; ++k) {
+            int j = col[k];
+            if (j >= n) continue;
+            for (int64_t i = 0; i < m; ++i) Gc[i + (int64_t)j * m] = Gw[i + k * mw];
+            for (int64_t i = 0; i < n; ++i) Wc[i + (int64_t)j * n] = W[i + k * nw];
+        }
+        finalise(m, n, Gc, Wc, sigma, U, ldu, V, ldv);
+        for (int64_t j = 0; j < n; ++j)
+            if (!(sigma[j] > 0.0)) status = ORC_RANK;
+        free(Gc);
+        free(Wc);
+    }
+    if (sweeps) *sweeps = sw;
+    if (rotations) *rotations = nrot_total;
+    free(Gw); free(W); free(Gt); free(Wt); free(sgn); free(sgt); free(col); free(colt);
+    free(pos); free(d); free(A); free(Wp); free(Pan); free(ps); free(pairs);
+    return status;
+}

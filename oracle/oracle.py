@@ -1,0 +1,157 @@
+"""ctypes face of ``hsvd_oracle.c`` (test infrastructure only).
+
+Every function here only moves numpy arrays in and out of the C oracle; the
+arithmetic lives in ``hsvd_oracle.c`` and is described there with the paper's
+section, equation or algorithm it follows.  The shared object is compiled with
+gcc on first use (or by :func:`build`) into ``oracle/_build``.
+"""
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+ORC_OK = 0
+ORC_NOT_CONVERGED = 1
+ORC_ARG = -1
+ORC_RANK = -2
+ORC_NONFINITE = -3
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hsvd_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_SO = os.path.join(_OUT_DIR, "liboracle_hsvd.so")
+_lock = threading.Lock()
+_lib = None
+
+_p = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_int = ctypes.c_int
+_dbl = ctypes.c_double
+
+
+def build(force=False, src=None, out=None):
+    """Compile the oracle with gcc (-O2, no floating-point contraction).
+
+    ``src``/``out`` compile another copy of the source (used by the tests
+    that plant mistakes in a copy of the oracle)."""
+    src = _SRC if src is None else src
+    out = _SO if out is None else out
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(src):
+        return out
+    tmp = out + ".tmp.%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-Wall", "-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
+def _bind(lib):
+    lib.orc_rotation.argtypes = [_dbl, _dbl, _dbl, _int, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl)]
+    lib.orc_rotation.restype = _int
+    lib.orc_modulus_pairs.argtypes = [_int, _int, _p]
+    lib.orc_modulus_pairs.restype = None
+    lib.orc_hsvd.argtypes = [_i64, _i64, _p, _i64, _p, _dbl, _int, _int, _int,
+                             _p, _p, _i64, _p, _i64, _p, _p]
+    lib.orc_hsvd.restype = _int
+    lib.orc_inner_solve.argtypes = [_int, _p, _p, _dbl, _int, _int, _p, _p, _p]
+    lib.orc_inner_solve.restype = _int
+    lib.orc_block_hsvd.argtypes = [_i64, _i64, _p, _i64, _p, _int, _dbl, _int, _int, _int,
+                                   _int, _p, _p, _i64, _p, _i64, _p, _p]
+    lib.orc_block_hsvd.restype = _int
+    return lib
+
+
+def load(path=None):
+    """The oracle's shared object; ``path`` loads another build of the same
+    source (the tests use this to run the pins against planted mistakes)."""
+    global _lib
+    if path is not None:
+        return _bind(ctypes.CDLL(path))
+    with _lock:
+        if _lib is None:
+            _lib = _bind(ctypes.CDLL(build()))
+    return _lib
+
+
+def _load():
+    return load()
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def _fcol(G):
+    return np.asfortranarray(np.asarray(G, dtype=np.float64))
+
+
+def _signs(J, n):
+    j = np.ascontiguousarray(np.asarray(J).astype(np.int8))
+    if j.shape != (n,):
+        raise ValueError("J must have one entry per column")
+    return j
+
+
+def rotation(aii, ajj, aij, hyp, lib=None):
+    """(t, c, status) of the rotation annihilating a_ij (Sec. 2, Eq. 2.2)."""
+    t, c = _dbl(), _dbl()
+    st = (lib or _load()).orc_rotation(float(aii), float(ajj), float(aij), int(hyp), ctypes.byref(t), ctypes.byref(c))
+    return t.value, c.value, st
+
+
+def modulus_pairs(r, nsteps=None, lib=None):
+    """Pivot pairs of the modified modulus strategy, shape (nsteps, r/2, 2)."""
+    nsteps = r if nsteps is None else nsteps
+    out = np.zeros((nsteps, r // 2, 2), dtype=np.int32)
+    (lib or _load()).orc_modulus_pairs(int(r), int(nsteps), _ptr(out))
+    return out
+
+
+def hsvd(G, J, tol, max_sweeps=30, order="cyclic", sort=False, want_u=True, want_v=True, lib=None):
+    """Pointwise one-sided hyperbolic Jacobi SVD on the CPU.
+
+    ``order`` is ``"cyclic"`` (row-cyclic) or ``"modulus"``.  Returns a dict
+    with sigma, U, V (input column order), sweeps, rotations and status.
+    """
+    G = _fcol(G)
+    m, n = G.shape
+    j = _signs(J, n)
+    sigma = np.zeros(n)
+    U = np.zeros((m, n), order="F") if want_u else None
+    V = np.zeros((n, n), order="F") if want_v else None
+    sweeps, rots = _int(), _i64()
+    st = (lib or _load()).orc_hsvd(m, n, _ptr(G), m, _ptr(j), float(tol), int(max_sweeps),
+                          1 if order == "modulus" else 0, 1 if sort else 0,
+                          _ptr(sigma), _ptr(U), m, _ptr(V), n, ctypes.byref(sweeps), ctypes.byref(rots))
+    return dict(sigma=sigma, U=U, V=V, sweeps=sweeps.value, rotations=rots.value, status=st)
+
+
+def inner_solve(A, sgn, tol, mode=0, max_passes=8, lib=None):
+    """J-orthogonalise one pivot block; returns (A_out, W, rotations, passes, status)."""
+    A = np.array(A, dtype=np.float64, order="F", copy=True)
+    nn = A.shape[0]
+    s = _signs(sgn, nn)
+    W = np.zeros((nn, nn), order="F")
+    nrot, passes = _i64(), _int()
+    st = (lib or _load()).orc_inner_solve(nn, _ptr(A), _ptr(s), float(tol), int(mode), int(max_passes),
+                                 _ptr(W), ctypes.byref(nrot), ctypes.byref(passes))
+    return A, W, nrot.value, passes.value, st
+
+
+def block_hsvd(G, J, b, tol, max_sweeps=30, inner_mode=0, inner_max_passes=8, sort=True,
+               want_u=True, want_v=True, lib=None):
+    """Blocked one-sided hyperbolic Jacobi SVD on the CPU (block width b)."""
+    G = _fcol(G)
+    m, n = G.shape
+    j = _signs(J, n)
+    sigma = np.zeros(n)
+    U = np.zeros((m, n), order="F") if want_u else None
+    V = np.zeros((n, n), order="F") if want_v else None
+    sweeps, rots = _int(), _i64()
+    st = (lib or _load()).orc_block_hsvd(m, n, _ptr(G), m, _ptr(j), int(b), float(tol), int(max_sweeps),
+                                int(inner_mode), int(inner_max_passes), 1 if sort else 0,
+                                _ptr(sigma), _ptr(U), m, _ptr(V), n, ctypes.byref(sweeps), ctypes.byref(rots))
+    return dict(sigma=sigma, U=U, V=V, sweeps=sweeps.value, rotations=rots.value, status=st)

@@ -1,0 +1,134 @@
+"""The pins are strong enough to catch plausible mistakes in the oracle.
+
+Each case plants one mistake (a dropped term, a flipped sign, a transposed
+operand, a wrong index or threshold) in a temporary copy of the oracle's C
+source, builds that copy with the same compiler flags, and runs a small
+battery of the independent checks of ``test_oracle_pins.py`` against it: at
+least one check must fail.  The unmodified source must pass the same battery.
+Everything here runs on the CPU."""
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from paper_1008_1371_gb300 import workloads as W
+
+U = 2.0 ** -53
+SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle", "hsvd_oracle.c")
+
+MUTANTS = {
+    "hyperbolic_theta_sign": ("zeta = -(aii + ajj) / (2.0 * aij);", "zeta = (aii + ajj) / (2.0 * aij);"),
+    "trig_zeta_swapped": ("zeta = (ajj - aii) / (2.0 * aij);", "zeta = (aii - ajj) / (2.0 * aij);"),
+    "hyperbolic_cosh_as_cos": ("*c = 1.0 / sqrt((1.0 - tt) * (1.0 + tt));", "*c = 1.0 / sqrt(1.0 + tt * tt);"),
+    "update_drops_hyp": ("    double ht = hyp < 0 ? -t : t;\n    for (int64_t i = 0; i < m; ++i) {",
+                         "    double ht = t;\n    for (int64_t i = 0; i < m; ++i) {"),
+    "update_operands_transposed": ("x[i] = fma(ht, yi, xi) * c;", "x[i] = fma(ht, xi, yi) * c;"),
+    "dot_drops_first_term": ("for (int64_t i = 0; i < m; ++i) s += x[i] * y[i];",
+                             "for (int64_t i = 1; i < m; ++i) s += x[i] * y[i];"),
+    "stepper_threshold": ("if (ip[k] + jp[k] > r - 2) {", "if (ip[k] + jp[k] > r - 3) {"),
+    "inner_diag_drops_hyp": ("AE(p, p) = fma(ht, apq, AE(p, p));", "AE(p, p) = fma(T[k], apq, AE(p, p));"),
+    "inner_row_update_transposed": ("X[0][y] = fma(htk, B[1][y], B[0][y]) * C[k];",
+                                    "X[0][y] = fma(htk, B[0][y], B[1][y]) * C[k];"),
+    "block_update_transposed_W": ("* Wp[x + y * nn];", "* Wp[y + x * nn];"),
+    "test_uses_product_not_sqrt": ("if (aij == 0.0 || fabs(aij) < tol * sqrt(aii * ajj)) return ORC_OK;",
+                                   "if (aij == 0.0 || fabs(aij) < tol * (aii * ajj)) return ORC_OK;"),
+}
+
+
+def _battery(orc, lib):
+    """Returns the list of failed checks (empty when all hold)."""
+    failed = []
+    rng = np.random.default_rng(5)
+    # closed-form root of the zeroing condition, exact rational arithmetic
+    for hyp in (-1, 1):
+        for _ in range(40):
+            x, y = rng.standard_normal(4), rng.standard_normal(4) * 3
+            aii, ajj, aij = float(x @ x), float(y @ y), float(x @ y)
+            t, c, st = orc.rotation(aii, ajj, aij, hyp, lib=lib)
+            F = Fraction
+            res = F(aij) * (1 + hyp * F(t) ** 2) + F(t) * (F(aii) + hyp * F(ajj))
+            sc = abs(F(aij)) * (1 + F(t) ** 2) + abs(F(t)) * (F(aii) + F(ajj))
+            ok = st == 0 and abs(res) <= 8 * U * sc and abs(c - 1 / np.sqrt(1 - hyp * t * t)) <= 1e-15 * c
+            if not ok:
+                failed.append("rotation")
+                break
+    # strategy properties (Sec. 2): disjoint pairs, each pair once except
+    # (i, i+4) twice, and the ninth step is the first with tasks reversed
+    P = orc.modulus_pairs(8, 9, lib=lib)
+    count = {}
+    for s in range(8):
+        if sorted(P[s].ravel().tolist()) != list(range(8)):
+            failed.append("strategy")
+            break
+        for a, b in P[s]:
+            count[(min(a, b), max(a, b))] = count.get((min(a, b), max(a, b)), 0) + 1
+    want = {(i, j): (2 if j - i == 4 else 1) for i in range(8) for j in range(i + 1, 8)}
+    if count != want or [sorted(p) for p in P[8]] != [sorted(p) for p in P[0]][::-1]:
+        failed.append("strategy-cover")
+    # pointwise: invariants and LAPACK eigenvalues of G J G^T
+    n = 32
+    G, J = W.gaussian(n, seed=7)
+    Jd = np.diag(J.astype(float))
+    for order in ("cyclic", "modulus"):
+        r = orc.hsvd(G, J, n * U, 30, order=order, sort=True, lib=lib)
+        if r["status"] != 0 or not np.all(np.isfinite(r["sigma"])):
+            failed.append("pointwise-status-" + order)
+            continue
+        lam = np.sort(r["sigma"] ** 2 * J)
+        ev = np.sort(np.linalg.eigvalsh((G * J[None, :]) @ G.T))
+        if np.max(np.abs(lam - ev)) > 8 * n * U * np.max(np.abs(ev)):
+            failed.append("pointwise-eig-" + order)
+        V, Uo = r["V"], r["U"]
+        if np.max(np.abs(V.T @ Jd @ V - Jd)) > 1e-12 * max(1, np.max(np.abs(V)) ** 2):
+            failed.append("pointwise-junitary-" + order)
+        if np.max(np.abs(G @ V - Uo * r["sigma"])) > 1e-12 * np.linalg.norm(G):
+            failed.append("pointwise-residual-" + order)
+    # scale invariance: sigma(alpha G) = alpha sigma(G), alpha a power of two
+    r1 = orc.hsvd(G, J, n * U, 30, order="modulus", sort=True, lib=lib)
+    r2 = orc.hsvd(G * 1024.0, J, n * U, 30, order="modulus", sort=True, lib=lib)
+    if r1["status"] != 0 or r2["status"] != 0 or \
+            np.max(np.abs(np.sort(r2["sigma"]) / 1024.0 - np.sort(r1["sigma"])) / np.sort(r1["sigma"])) > 1e-12:
+        failed.append("scale")
+    # the stopping test (Eq. 2.3) leaves the columns relatively orthogonal to tol
+    for r in (r1, r2):
+        if r["status"] == 0 and np.max(np.abs(r["U"].T @ r["U"] - np.eye(n))) > 2 * n * U + 8 * n * U:
+            failed.append("final-orthogonality")
+    # inner solve: congruence and eigenvalues of J A
+    nn = 16
+    Gp = rng.standard_normal((40, nn))
+    A = Gp.T @ Gp
+    sg = W.signs_block(nn, 6)
+    Ao, Wp, nrot, passes, st = orc.inner_solve(A, sg, nn * U, mode=0, max_passes=20, lib=lib)
+    Jn = np.diag(sg.astype(float))
+    if st != 0 or not np.allclose(Wp.T @ A @ Wp, Ao, rtol=0, atol=1e-11 * np.max(np.abs(A))) \
+            or not np.allclose(np.sort(sg * np.diag(Ao)), np.sort(np.linalg.eigvals(Jn @ A).real), rtol=1e-9) \
+            or np.max(np.abs(Wp.T @ Jn @ Wp - Jn)) > 1e-11 * max(1, np.max(np.abs(Wp)) ** 2):
+        failed.append("inner")
+    # blocked method against LAPACK
+    r = orc.block_hsvd(G, J, 4, n * U, 30, inner_mode=1, lib=lib)
+    lam = np.sort(r["sigma"] ** 2 * J)
+    ev = np.sort(np.linalg.eigvalsh((G * J[None, :]) @ G.T))
+    if r["status"] != 0 or np.max(np.abs(lam - ev)) > 8 * n * U * np.max(np.abs(ev)):
+        failed.append("blocked")
+    return failed
+
+
+def _variant(orc, tmp_path, name, old, new):
+    src = open(SRC).read()
+    assert src.count(old) >= 1, name
+    path = tmp_path / ("orc_%s.c" % name)
+    path.write_text(src.replace(old, new))
+    so = orc.build(force=True, src=str(path), out=str(tmp_path / ("liborc_%s.so" % name)))
+    return orc.load(so)
+
+
+def test_battery_passes_on_oracle(orc):
+    assert _battery(orc, orc.load()) == []
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_battery_catches_planted_mistake(orc, tmp_path, name):
+    old, new = MUTANTS[name]
+    lib = _variant(orc, tmp_path, name, old, new)
+    assert _battery(orc, lib), "planted mistake %s went unnoticed" % name
