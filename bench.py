@@ -1,0 +1,334 @@
+#!/usr/bin/env python
+"""Benchmark of the one-sided Jacobi hyperbolic SVD on GB300.
+
+One step = one complete HSVD (all sweeps until the Eq. 2.3 test passes for
+every pair, then the finalisation) of the plain blocked FP64 method on the
+1024 x 1024 graded factor G = B diag(10^(-6 i/n)), B i.i.d. N(0,1) (seed 2),
+J = diag(+1 x 512, -1 x 512), block width 32, tol = n 2^-53, inputs already
+in HBM.  The metric is effective TFLOP/s = S * 2 n^2 (4m + 2n) / time, S the
+sweeps of this plain run (the same flop count for every form), and the time
+per HSVD.
+
+``--impl reference`` times the CPU oracle (plain row-cyclic FP64 C code) on
+the host cores instead: each step is one sweep of the oracle on the same G.
+
+Multi-GPU: independent factors per rank (replicas, weak scaling), no
+collective on the data path; a barrier and max-over-ranks timing only.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 1024
+M = 1024
+BLOCK = 32
+DECADES = 6.0
+SEED = 2
+TOL = N * 2.0 ** -53
+MAX_SWEEPS = 30
+GOLDEN = os.path.join(ROOT, "tests", "golden", "graded1024_sigma.txt")
+WORKLOAD = "graded 1024x1024 G=B diag(10^(-6i/n)), J=diag(+1x512,-1x512), plain blocked FP64, b=32"
+
+
+def flops_per_sweep(m, n):
+    """Blocked-method work of one quasi-sweep: Gram 4mn^2, G update 4mn^2, V update 4n^3."""
+    return 2.0 * n * n * (4.0 * m + 2.0 * n)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-sweeps", type=int, default=2, help="oracle sweeps timed for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % gpu_index)
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sms, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sms) if sms else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+def accuracy_vs_golden(G, J, sigma):
+    """Largest relative sigma error against the stored oracle values, overall
+    and over the values whose noise floor u*kappa_j is below 1e-12."""
+    import hashlib
+
+    if not os.path.exists(GOLDEN):
+        return {"note": "no stored oracle values"}
+    with open(GOLDEN) as f:
+        head = [ln for ln in f.read().splitlines() if ln.startswith("#")]
+    want = next((ln.split("sha256(G)=")[1].strip() for ln in head if "sha256(G)=" in ln), None)
+    have = hashlib.sha256(np.ascontiguousarray(G, dtype="<f8").tobytes(order="F")).hexdigest()
+    if want != have:
+        return {"note": "stored oracle values belong to other bytes of G (libm rounding); not compared"}
+    ref = np.loadtxt(GOLDEN)
+    worst, worst_tight, n_loose = 0.0, 0.0, 0
+    for sg in (1, -1):
+        idx = np.where(J == sg)[0]
+        o = np.argsort(ref[idx, 0])
+        y, k = ref[idx, 0][o], ref[idx, 1][o]
+        e = np.abs(np.sort(sigma[idx]) - y) / y
+        worst = max(worst, float(e.max()))
+        tight = k <= 1e-12
+        n_loose += int((~tight).sum())
+        if tight.any():
+            worst_tight = max(worst_tight, float(e[tight].max()))
+    return {"sigma_max_rel_err": worst, "sigma_max_rel_err_where_floor_below_1e-12": worst_tight,
+            "values_with_floor_above_1e-12": n_loose}
+
+
+def cpu_baseline(G, J, sweeps):
+    """The oracle as it stands, single-threaded on a host core: `sweeps`
+    sweeps of the row-cyclic method on the same factor."""
+    import oracle
+
+    oracle.build()
+    t0 = time.perf_counter()
+    r = oracle.hsvd(G, J, TOL, sweeps, want_u=False, want_v=False)
+    dt = time.perf_counter() - t0
+    per_sweep = dt / max(r["sweeps"], 1)
+    return {"value": flops_per_sweep(M, N) / per_sweep / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+            "sample": "%d sweep(s) of the row-cyclic FP64 oracle on the same %dx%d factor, %.2f s per sweep; "
+                      "effective rate per sweep with the blocked flop count 2n^2(4m+2n)" % (r["sweeps"], M, N,
+                                                                                            per_sweep)}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1008_1371_gb300 import workloads
+
+    G, J = workloads.graded(N, decades=DECADES, seed=SEED)
+    import oracle
+
+    oracle.build()
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        r = oracle.hsvd(G, J, TOL, 1, want_u=False, want_v=False)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    per = sum(times) / len(times)
+    value = flops_per_sweep(M, N) / per / 1e12
+    line = {
+        "impl": "reference", "metric": "HSVD effective TFLOP/s (plain FP64, sigma rel-err <= 1e-12)",
+        "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "m": M, "n": N, "block_w": BLOCK,
+                                        "sample": "one sweep of the CPU oracle per step"},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+                         "sample": "one sweep of the row-cyclic FP64 oracle per step on the same factor"},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "oracle_status": r["status"],
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    from paper_1008_1371_gb300 import api, build_lib, workloads
+
+    if local == 0:
+        build_lib.build()
+    if world > 1:
+        dist.barrier()
+    G_np, J_np = workloads.graded(N, decades=DECADES, seed=SEED + rank)
+    G = torch.from_numpy(G_np).to(dev).t().contiguous().t()
+    J = torch.from_numpy(J_np).to(dev)
+    sigma = torch.empty(N, dtype=torch.float64, device=dev)
+    U = torch.empty((N, M), dtype=torch.float64, device=dev).t()
+    V = torch.empty((N, N), dtype=torch.float64, device=dev).t()
+    opts = api.make_opts(tol=TOL, max_sweeps=MAX_SWEEPS, method=api.HSVD_METHOD_BLOCKED, block_w=BLOCK,
+                         profile=True)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    stream = torch.cuda.current_stream(dev)
+
+    def solve():
+        return api.hsvd_solve_ex(G, J, opts, out=(sigma, U, V), stream=stream)
+
+    for _ in range(args.warmup):
+        solve()
+    torch.cuda.synchronize()
+    infos, step_ms = [], []
+    with ClockSampler(local) as clk:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = solve()
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            infos.append(info)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+    ms = sum(step_ms) / len(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    info = infos[-1]
+    assert info.status == api.HSVD_OK, api.hsvd_status_string(info.status)
+    sweeps = info.sweeps
+    eff_flops = sweeps * flops_per_sweep(M, N)
+    value = world * eff_flops / (ms * 1e-3) / 1e12
+
+    # dominant kernel class by CUDA-event time over the timed steps
+    tot = {k: sum(getattr(i, "ms_" + k) for i in infos) for k in ("gram", "solve", "update", "other")}
+    upd_pairs = sum(i.pair_updates for i in infos)
+    nb = N // BLOCK
+    visits = sum(i.sweeps for i in infos) * nb * (nb // 2)
+    alg = {
+        "update": upd_pairs * 2.0 * (M + N) * (2 * BLOCK) ** 2,
+        "gram": visits * 6.0 * M * BLOCK * BLOCK,
+    }
+    dom = max(("gram", "update", "solve"), key=lambda k: tot[k])
+    fp64_peak = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk x flop x max clock
+    if dom in alg:
+        achieved = alg[dom] / (tot[dom] * 1e-3) / 1e12
+    else:
+        achieved = None
+    roofline = {"kernel": {"gram": "k_gram<32>", "update": "k_update<64>", "solve": "k_solve<64>"}[dom],
+                "bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": (achieved / fp64_peak) if achieved else None, "traffic": None,
+                "peak_source": "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (derived)",
+                "ms_by_kernel": {k: v / len(infos) for k, v in tot.items()},
+                "alg_tflops_by_kernel": {k: alg[k] / (tot[k] * 1e-3) / 1e12 for k in alg if tot[k] > 0}}
+
+    # accuracy against the stored oracle values (written by tests/golden/make_golden.py
+    # on a machine whose G has the same bytes as this one's)
+    accuracy = accuracy_vs_golden(G_np, J_np, sigma.cpu().numpy()) if rank == 0 else None
+
+    # end to end through the C ABI with pinned host arrays, copies inside the timed region
+    Gh = torch.from_numpy(G_np).t().contiguous().t().pin_memory()
+    Jh = torch.from_numpy(J_np).pin_memory()
+    sh = torch.empty(N, dtype=torch.float64).pin_memory()
+    Uh = torch.empty((N, M), dtype=torch.float64).pin_memory().t()
+    Vh = torch.empty((N, N), dtype=torch.float64).pin_memory().t()
+    opts_e2e = api.make_opts(tol=TOL, max_sweeps=MAX_SWEEPS, method=api.HSVD_METHOD_BLOCKED, block_w=BLOCK)
+    api.hsvd_solve_ex(Gh, Jh, opts_e2e, out=(sh, Uh, Vh))
+    e2e_t = []
+    for _ in range(max(3, args.steps // 2)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        api.hsvd_solve_ex(Gh, Jh, opts_e2e, out=(sh, Uh, Vh))
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = sum(e2e_t) / len(e2e_t)
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * eff_flops / e2e_s / 1e12, "unit": "TFLOP/s", "ms_per_step": e2e_s * 1e3,
+           "h2d_bytes_per_step": M * N * 8 + N, "d2h_bytes_per_step": N * 8 + M * N * 8 + N * N * 8}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(G_np, J_np, args.cpu_sweeps)
+
+    if rank == 0:
+        line = {
+            "metric": "HSVD effective TFLOP/s (plain FP64, sigma rel-err <= 1e-12)", "value": value,
+            "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "m": M, "n": N, "block_w": BLOCK, "tol": TOL, "sweeps": sweeps,
+                       "inner": "block-oriented", "sort": False, "l2": "flushed (256 MB write) between steps",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "accuracy": accuracy,
+            "gpu_launches": int(sum(i.kernel_launches for i in infos)),
+            "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk.summary(),
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,177 @@
+/*
+ * hsvd.h -- C ABI of the GB300 (sm_103a) one-sided Jacobi hyperbolic SVD.
+ *
+ * Problem (Sec. 1, Eq. 1.1): for a real m x n factor G, m >= n, of full column
+ * rank and a signature J = diag(+-1), compute
+ *
+ *     G V = U Sigma,   U^T U = I,   V^T J V = J,   Sigma = diag(sigma) > 0,
+ *
+ * so that M = G J G^T = U (Sigma^2 J) U^T (Sec. 1): lambda_j = sigma_j^2 J_jj.
+ * V is the accumulated product of the J-unitary rotations applied to G's
+ * columns (Eq. 2.1, the paper's V^{-T}); the paper's right hyperbolic singular
+ * vectors are J V J (Sec. 2).
+ *
+ * Conventions shared by every entry point:
+ *  - Matrices are column-major FP64 with a leading dimension >= rows.
+ *  - Outputs are in INPUT column order: sigma[j], U(:,j), V(:,j) belong to the
+ *    column that started as G(:,j), and keep its sign J[j] (the paper also
+ *    returns results in the original column order, Sec. 4).  Sort them if you
+ *    need lambda in order.
+ *  - Memory: for hsvd_solve / hsvd_solve_ex / hsvd_solve_batched every array
+ *    argument is either a device pointer (cudaMalloc / PyTorch CUDA memory of
+ *    the current device) or a host pointer (pageable or pinned); all arrays of
+ *    one call must be of the same kind.  With host arrays the library copies
+ *    the inputs in and the results out on `stream` and returns after the copy
+ *    back.  The caller owns every array; the library allocates only its own
+ *    workspace (stream-ordered, released before return) and never keeps a
+ *    pointer after return.  G is read-only.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  With
+ *    device arrays the call still synchronises `stream` once per sweep to read
+ *    the convergence flag, and before returning.
+ *  - Return value: one of the HSVD_* status codes below.  No exception or
+ *    abort crosses the ABI.  Outputs are written for HSVD_OK and
+ *    HSVD_NOT_CONVERGED only.
+ */
+#ifndef HSVD_H
+#define HSVD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define HSVD_OK 0
+#define HSVD_NOT_CONVERGED 1   /* max_sweeps reached; outputs hold the last iterate   */
+#define HSVD_ERR_ARG (-1)      /* bad size, leading dimension, signature or option      */
+#define HSVD_ERR_RANK (-2)     /* a hyperbolic pair with |zeta| <= 1, or a zero column:
+                                  G (or G J G^T) is numerically rank deficient, Sec. 1 */
+#define HSVD_ERR_NONFINITE (-3) /* NaN or Inf in G or produced during the sweep         */
+#define HSVD_ERR_CUDA (-4)     /* a CUDA runtime call failed                            */
+#define HSVD_ERR_NOMEM (-5)    /* workspace allocation failed                           */
+
+/* Methods. */
+#define HSVD_METHOD_AUTO 0      /* pointwise when the factor fits one SM, else blocked */
+#define HSVD_METHOD_POINTWISE 1 /* column-pair rotations (Alg. 4.5), one CTA per factor */
+#define HSVD_METHOD_BLOCKED 2   /* block-column pairs (Sec. 5 block-oriented method)    */
+
+/* Inner pivot-block solve of the blocked method. */
+#define HSVD_INNER_ORIENTED 0 /* Sec. 5: whole block in the first step of a sweep,
+                                 then one pass over the off-diagonal block only */
+#define HSVD_INNER_FULL 1     /* Sec. 6: diagonalise the pivot block (passes until
+                                 no inner rotation, at most inner_max_passes) */
+
+#define HSVD_SORT_AUTO (-1)
+
+typedef struct hsvd_opts {
+    double tol;           /* relative orthogonality threshold of Eq. 2.3;
+                             <= 0 selects n * 2^-53                                   */
+    int max_sweeps;       /* <= 0 selects 30                                           */
+    int method;           /* HSVD_METHOD_*                                             */
+    int block_w;          /* block width b of the blocked method: 16, 32 or 64; 0=auto */
+    int inner_mode;       /* HSVD_INNER_*                                              */
+    int inner_max_passes; /* cap for HSVD_INNER_FULL; <= 0 selects 8                   */
+    int sort;             /* 1: diagonal sorting before the first sweep and after each
+                             sweep (Sec. 4): J+ part by ||g||^2 decreasing, J- part
+                             increasing; 0: no sorting; HSVD_SORT_AUTO: sorting for the
+                             pointwise method only                                     */
+    int profile;          /* nonzero: time every kernel with CUDA events (hsvd_info)   */
+    int reserved[7];      /* must be zero                                              */
+} hsvd_opts;
+
+typedef struct hsvd_info {
+    int sweeps;           /* sweeps run, including the final one without rotations     */
+    int method;           /* method actually used                                      */
+    int block_w;          /* block width actually used (1 for pointwise)               */
+    int status;           /* same as the return value                                  */
+    int64_t rotations;    /* rotations applied (inner rotations for the blocked method) */
+    int64_t pair_updates; /* blocked method: pivot pairs whose panels were updated     */
+    int64_t kernel_launches; /* kernels of this library launched by the call           */
+    double ms_gram;       /* with opts.profile: summed CUDA-event time of the Gram      */
+    double ms_solve;      /*   kernels, the inner-solve kernels, the update kernels,    */
+    double ms_update;     /*   and of everything else (bordering, reordering,           */
+    double ms_other;      /*   finalisation; the pointwise kernel counts as "solve")   */
+} hsvd_info;
+
+/* Fills *opts with the defaults (tol = n 2^-53 at call time, 30 sweeps, auto
+ * method and block width, block-oriented inner solve, HSVD_SORT_AUTO). */
+void hsvd_default_opts(hsvd_opts *opts);
+
+/*
+ * hsvd_solve -- the HSVD of one factor (Sec. 1, Eq. 1.1) by the one-sided
+ * hyperbolic Jacobi method (Sec. 2): sweeps of the modified modulus strategy
+ * (Sec. 2) until a sweep in which every pair passes the relative
+ * orthogonality test |a_ij| < tol sqrt(a_ii a_jj) (Eq. 2.3, Sec. 2 stopping
+ * rule).
+ *   G      m x n, leading dimension ldg >= m, m >= n >= 1          (input)
+ *   J      n signs, each +1 or -1 (int8)                              (input)
+ *   tol    <= 0 selects n * 2^-53; max_sweeps <= 0 selects 30
+ *   sigma  n                                                          (output)
+ *   U      m x n, ldu >= m, may be NULL                               (output)
+ *   V      n x n, ldv >= n, may be NULL                               (output)
+ *   sweeps may be NULL; receives the number of sweeps run
+ */
+int hsvd_solve(const double *G, int64_t m, int64_t n, int64_t ldg, const int8_t *J,
+               double tol, int max_sweeps, double *sigma, double *U, int64_t ldu,
+               double *V, int64_t ldv, int *sweeps, void *stream);
+
+/* hsvd_solve with explicit options (opts may be NULL for the defaults) and an
+ * optional info record. */
+int hsvd_solve_ex(const double *G, int64_t m, int64_t n, int64_t ldg, const int8_t *J,
+                  double *sigma, double *U, int64_t ldu, double *V, int64_t ldv,
+                  const hsvd_opts *opts, hsvd_info *info, void *stream);
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *hsvd_status_string(int status);
+
+/*
+ * Pivot strategy (Sec. 2, Alg. 4.3 / 4.4): the modified modulus strategy on r
+ * indices, r even, 2 <= r <= 65536.  Writes nsteps * (r/2) pairs (i, j), i < j,
+ * as pairs[2*(s*(r/2)+k) + {0,1}]: step s (0-based, taken modulo r) holds the
+ * pairs with i + j = (r - 1 + s) mod r (mod r), plus (c/2, c/2 + r/2) when that
+ * residue c is even.  Host memory.  Returns HSVD_ERR_ARG on bad r.
+ */
+int hsvd_modulus_pairs(int r, int nsteps, int *pairs);
+
+/*
+ * Kernel-level entry points of the blocked method, exposed so each kernel can
+ * be checked on its own.  All pointers are device pointers; the call is
+ * stream-ordered (no synchronisation); the caller owns all memory.
+ *
+ * hsvd_pivot_gram: A_P = [G_I G_J]^T [G_I G_J] for npairs block-column pairs
+ * (Sec. 2 pivot block A_P, blocked as in Sec. 5).  G has `rows` rows (a
+ * multiple of 64), leading dimension ldg; col0[2k], col0[2k+1] are the first
+ * columns of blocks I and J of pair k (device int array).  A receives npairs
+ * (2b x 2b) column-major blocks, A + k*(2b)^2.  b in {16, 32, 64}.
+ */
+int hsvd_pivot_gram(const double *G, int64_t rows, int64_t ldg, int b, int npairs,
+                    const int *col0, double *A, void *stream);
+
+/*
+ * hsvd_pivot_solve: J-orthogonalise npairs pivot blocks A (each 2b x 2b,
+ * overwritten by W^T A W) with signs sgn (npairs x 2b int8, device) by
+ * two-sided rotations (Sec. 5 block method; Sec. 6 full-block), writing the
+ * transformation W (npairs x (2b)^2) and rotated[k] = number of rotations.
+ * mode: 0 passes over all index pairs until none rotates (at most max_passes),
+ * 1 one pass over the off-diagonal block only, 2 one pass over all pairs.
+ * Returns HSVD_ERR_RANK through *status_dev (device int, may be NULL) when a
+ * hyperbolic pair has |zeta| <= 1.
+ */
+int hsvd_pivot_solve(int b, int npairs, double *A, const int8_t *sgn, double tol, int mode,
+                     int max_passes, double *W, int *rotated, int *status_dev, void *stream);
+
+/*
+ * hsvd_pivot_update: [X_I X_J] <- [X_I X_J] W_k in place for every pair k with
+ * rotated[k] != 0 (Eq. 2.1 applied to a block-column pair).  X has `rows` rows
+ * (a multiple of 32), leading dimension ldx.
+ */
+int hsvd_pivot_update(double *X, int64_t rows, int64_t ldx, int b, int npairs, const int *col0,
+                      const double *W, const int *rotated, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HSVD_H */

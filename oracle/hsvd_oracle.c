@@ -54,6 +54,12 @@
  *       d increasing, equal keys keep their current relative order.
  *   R5  A sweep counts every sweep run, including the final one in which no
  *       pair rotates (Sec. 2 stopping rule).
+ *   R7  Inside a pivot block the diagonal is carried by Eq. 2.6 (as Sec. 4
+ *       carries d for the pointwise method) rather than recomputed.
+ *   R8  The paper leaves the order of the two one-sided halves of R^T A R on
+ *       a pivot block open; here they alternate from inner step to inner step
+ *       (column half first on even steps, row half first on odd steps), which
+ *       lets a distributed implementation transpose once per step.
  *   R6  A pair with a_ij == 0 exactly is orthogonal and is never rotated (the
  *       strict test of Eq. 2.3 would otherwise "rotate" a zero column by the
  *       identity for ever).  A zero column (sigma_j = 0) is rank deficiency,
@@ -359,19 +365,25 @@ done:
 
 /* ------------------------------------------------------------------------ */
 /* Inner solve: J-orthogonalisation of a pivot block A_P (nn x nn, nn even,   */
-/* symmetric, column-major, ld = nn) with signs sgn[nn] (Sec. 5 block method, */
-/* Sec. 6 full-block variant).  The rotations of one inner step are the       */
-/* disjoint pairs of one step of a pivot strategy; all of them are computed   */
-/* from the step's starting A, then applied at once:                          */
-/*   - pair (p,q), p < q: test Eq. 2.3 on (a_pp, a_qq, a_pq); if it fails,    */
-/*     (t, c) from orc_rotation, else t = 0, c = 1 (identity);                */
-/*   - for two different pairs k, l with p_k < p_l, the 2x2 block           */
-/*     B = A[{p_k,q_k},{p_l,q_l}] becomes R_k^T B R_l, computed as the row    */
-/*     update with R_k first and the column update with R_l second, each      */
-/*     entry in the form fma(hyp*t, other, own) * c (Alg. 4.5);              */
-/*     A is kept symmetric by writing each result to both (x,y) and (y,x);    */
-/*   - for a rotated pair, Eq. 2.6: a_pp += hyp*t*a_pq, a_qq += t*a_pq (one   */
-/*     fma each), a_pq = a_qp = 0;                                            */
+/* symmetric on entry, column-major, ld = nn) with signs sgn[nn] (Sec. 5      */
+/* block method, Sec. 6 full-block variant).  One inner step takes the        */
+/* disjoint pairs of one step of a pivot strategy and applies all their       */
+/* rotations R at once, A <- R^T A R (Eq. 2.1 / 2.2 on the pivot block):      */
+/*   - the diagonal of A is kept in d[] (reading R7);                         */
+/*   - pair (p,q), p < q: test Eq. 2.3 on (d_p, d_q, a_pq) with a_pq the      */
+/*     entry in row p, column q; if it fails, (t, c) from orc_rotation,       */
+/*     else the pair is left alone (identity);                                */
+/*   - the two one-sided halves of R^T A R are applied as two passes of the   */
+/*     column update of Alg. 4.5, x_p <- fma(hyp t, x_q, x_p) c,             */
+/*     x_q <- fma(t, x_p, x_q) c, over every row of a stored matrix S, with   */
+/*     S transposed between the passes: S = A at the first step, so the first */
+/*     step computes A R, transposes, then mixes the rows of (A R)^T, giving  */
+/*     S = (R^T A R)^T; the next step therefore starts from S = A^T and ends  */
+/*     with S = A, and so on -- the order of the two halves alternates from   */
+/*     step to step (reading R8);                                             */
+/*   - for a rotated pair, Eq. 2.6: d_p += hyp t a_pq, d_q += t a_pq (one fma */
+/*     each, with the a_pq of the step's start); the entries (p,p), (q,q) of  */
+/*     S take d_p, d_q and (p,q), (q,p) become 0;                             */
 /*   - W <- W R: columns p, q of W as in Alg. 4.5.                           */
 /* Modes:                                                                     */
 /*   0 full-block: passes of the modulus strategy over nn indices (nn steps), */
@@ -381,8 +393,24 @@ done:
 /*     block-oriented method, steps after the first);                         */
 /*   2 one pass of the modulus strategy over all nn indices (Sec. 5, first    */
 /*     step of the block-oriented method).                                    */
-/* W (nn x nn) receives the accumulated transformation, starting from I.      */
+/* On return A holds the final R^T A R (A itself, not its transpose) and W    */
+/* (nn x nn) the accumulated transformation, starting from I.                 */
 /* ------------------------------------------------------------------------ */
+static void mix_rows(int nn, double *S, int h, const int *P, const int *Q, const double *T,
+                     const double *C, const int *H, const int *rot)
+{
+    /* every row x of the row-major nn x nn matrix S: columns p, q of pair k */
+    for (int x = 0; x < nn; ++x)
+        for (int k = 0; k < h; ++k) {
+            if (!rot[k]) continue;
+            double *row = S + (int64_t)x * nn;
+            double a = row[P[k]], b = row[Q[k]];
+            double ht = H[k] < 0 ? -T[k] : T[k];
+            row[P[k]] = fma(ht, b, a) * C[k];
+            row[Q[k]] = fma(T[k], a, b) * C[k];
+        }
+}
+
 int orc_inner_solve(int nn, double *A, const int8_t *sgn, double tol, int mode,
                     int max_passes, double *W, int64_t *nrot_out, int *passes_out)
 {
@@ -392,10 +420,18 @@ int orc_inner_solve(int nn, double *A, const int8_t *sgn, double tol, int mode,
     int *P = (int *)malloc(sizeof(int) * h), *Q = (int *)malloc(sizeof(int) * h);
     double *T = (double *)malloc(sizeof(double) * h), *C = (double *)malloc(sizeof(double) * h);
     int *H = (int *)malloc(sizeof(int) * h), *rot = (int *)malloc(sizeof(int) * h);
+    double *S = (double *)malloc(sizeof(double) * (size_t)nn * nn);
+    double *St = (double *)malloc(sizeof(double) * (size_t)nn * nn);
+    double *d = (double *)malloc(sizeof(double) * nn);
+    double *apq = (double *)malloc(sizeof(double) * h);
     orc_modulus_pairs(nn, nn, pairs);
     memset(W, 0, sizeof(double) * (size_t)nn * nn);
     for (int i = 0; i < nn; ++i) W[i + i * nn] = 1.0;
-#define AE(x, y) A[(x) + (int64_t)(y) * nn]
+    /* S row-major: S[x*nn + y] = A(x, y); A column-major A[x + y*nn] */
+    for (int x = 0; x < nn; ++x)
+        for (int y = 0; y < nn; ++y) S[(int64_t)x * nn + y] = A[x + (int64_t)y * nn];
+    for (int x = 0; x < nn; ++x) d[x] = A[x + (int64_t)x * nn];
+    int transposed = 0; /* 0: S = A, 1: S = A^T */
     int status = ORC_OK, npass = 0;
     int64_t nrot_total = 0;
     int npass_max = (mode == 0) ? max_passes : 1;
@@ -418,55 +454,38 @@ int orc_inner_solve(int nn, double *A, const int8_t *sgn, double tol, int mode,
             }
             for (int k = 0; k < h; ++k) {
                 int p = P[k], q = Q[k];
-                double app = AE(p, p), aqq = AE(q, q), apq = AE(p, q);
+                double a_pq = transposed ? S[(int64_t)q * nn + p] : S[(int64_t)p * nn + q];
+                apq[k] = a_pq;
                 H[k] = (sgn[p] == sgn[q]) ? -1 : 1;
                 T[k] = 0.0;
                 C[k] = 1.0;
                 rot[k] = 0;
-                if (apq == 0.0 || fabs(apq) < tol * sqrt(app * aqq)) continue; /* Eq. 2.3, R6 */
-                if (orc_rotation(app, aqq, apq, H[k], &T[k], &C[k]) != ORC_OK) {
+                if (a_pq == 0.0 || fabs(a_pq) < tol * sqrt(d[p] * d[q])) continue; /* Eq. 2.3, R6 */
+                if (orc_rotation(d[p], d[q], a_pq, H[k], &T[k], &C[k]) != ORC_OK) {
                     status = ORC_RANK;
                     goto out;
                 }
                 rot[k] = 1;
                 ++nrot_pass;
             }
-            /* off-diagonal 2x2 blocks between different pairs; of two pairs
-             * the one with the smaller first index takes the row update */
-            for (int k = 0; k < h; ++k) {
-                for (int l = 0; l < h; ++l) {
-                    if (!(P[k] < P[l])) continue;
-                    int rk[2] = {P[k], Q[k]}, cl[2] = {P[l], Q[l]};
-                    double B[2][2], X[2][2];
-                    for (int x = 0; x < 2; ++x)
-                        for (int y = 0; y < 2; ++y) B[x][y] = AE(rk[x], cl[y]);
-                    double htk = H[k] < 0 ? -T[k] : T[k];
-                    double htl = H[l] < 0 ? -T[l] : T[l];
-                    for (int y = 0; y < 2; ++y) { /* rows: R_k^T B */
-                        X[0][y] = fma(htk, B[1][y], B[0][y]) * C[k];
-                        X[1][y] = fma(T[k], B[0][y], B[1][y]) * C[k];
-                    }
-                    for (int x = 0; x < 2; ++x) { /* columns: (R_k^T B) R_l */
-                        B[x][0] = fma(htl, X[x][1], X[x][0]) * C[l];
-                        B[x][1] = fma(T[l], X[x][0], X[x][1]) * C[l];
-                    }
-                    for (int x = 0; x < 2; ++x)
-                        for (int y = 0; y < 2; ++y) {
-                            AE(rk[x], cl[y]) = B[x][y];
-                            AE(cl[y], rk[x]) = B[x][y];
-                        }
-                }
-            }
-            /* diagonal blocks: Eq. 2.6 */
+            /* first half on the rows of S, transpose, second half */
+            mix_rows(nn, S, h, P, Q, T, C, H, rot);
+            for (int x = 0; x < nn; ++x)
+                for (int y = 0; y < nn; ++y) St[(int64_t)y * nn + x] = S[(int64_t)x * nn + y];
+            memcpy(S, St, sizeof(double) * (size_t)nn * nn);
+            transposed ^= 1;
+            mix_rows(nn, S, h, P, Q, T, C, H, rot);
+            /* Eq. 2.6 on the diagonal, zeros at (p,q) and (q,p) */
             for (int k = 0; k < h; ++k) {
                 if (!rot[k]) continue;
                 int p = P[k], q = Q[k];
-                double apq = AE(p, q);
                 double ht = H[k] < 0 ? -T[k] : T[k];
-                AE(p, p) = fma(ht, apq, AE(p, p));
-                AE(q, q) = fma(T[k], apq, AE(q, q));
-                AE(p, q) = 0.0;
-                AE(q, p) = 0.0;
+                d[p] = fma(ht, apq[k], d[p]);
+                d[q] = fma(T[k], apq[k], d[q]);
+                S[(int64_t)p * nn + p] = d[p];
+                S[(int64_t)q * nn + q] = d[q];
+                S[(int64_t)p * nn + q] = 0.0;
+                S[(int64_t)q * nn + p] = 0.0;
             }
             /* W <- W R */
             for (int k = 0; k < h; ++k) {
@@ -478,10 +497,14 @@ int orc_inner_solve(int nn, double *A, const int8_t *sgn, double tol, int mode,
         if (nrot_pass == 0) break;
     }
 out:
-#undef AE
+    /* A <- the current R^T A R (S or its transpose) */
+    for (int x = 0; x < nn; ++x)
+        for (int y = 0; y < nn; ++y)
+            A[x + (int64_t)y * nn] = transposed ? S[(int64_t)y * nn + x] : S[(int64_t)x * nn + y];
     if (nrot_out) *nrot_out = nrot_total;
     if (passes_out) *passes_out = npass;
     free(pairs); free(P); free(Q); free(T); free(C); free(H); free(rot);
+    free(S); free(St); free(d); free(apq);
     return status;
 }
 

@@ -1,0 +1,256 @@
+"""Thin Python binding of the C ABI in ``include/hsvd.h`` (ctypes).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of ``libhsvd.so``.  PyTorch provides device memory and streams.  The
+library is loaded on first use; if it has not been built (``build_lib.build()``
+or ``__graft_entry__.build()``) the call raises -- there is no fallback.
+
+Matrices are column-major: an m x n matrix is a tensor of shape (m, n) with
+strides (1, ld).  Inputs in another layout are copied into that layout.
+"""
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+from typing import Optional
+
+import torch
+
+HSVD_OK = 0
+HSVD_NOT_CONVERGED = 1
+HSVD_ERR_ARG = -1
+HSVD_ERR_RANK = -2
+HSVD_ERR_NONFINITE = -3
+HSVD_ERR_CUDA = -4
+HSVD_ERR_NOMEM = -5
+
+HSVD_METHOD_AUTO = 0
+HSVD_METHOD_POINTWISE = 1
+HSVD_METHOD_BLOCKED = 2
+HSVD_INNER_ORIENTED = 0
+HSVD_INNER_FULL = 1
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhsvd.so")
+_lock = threading.Lock()
+_lib = None
+
+_p = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_int = ctypes.c_int
+_dbl = ctypes.c_double
+
+
+class HsvdOpts(ctypes.Structure):
+    _fields_ = [("tol", _dbl), ("max_sweeps", _int), ("method", _int), ("block_w", _int),
+                ("inner_mode", _int), ("inner_max_passes", _int), ("sort", _int), ("profile", _int),
+                ("reserved", _int * 7)]
+
+
+class HsvdInfo(ctypes.Structure):
+    _fields_ = [("sweeps", _int), ("method", _int), ("block_w", _int), ("status", _int),
+                ("rotations", _i64), ("pair_updates", _i64), ("kernel_launches", _i64),
+                ("ms_gram", _dbl), ("ms_solve", _dbl), ("ms_update", _dbl), ("ms_other", _dbl)]
+
+
+class HsvdError(RuntimeError):
+    def __init__(self, status):
+        super().__init__("hsvd failed: %s (%d)" % (hsvd_status_string(status), status))
+        self.status = status
+
+
+def lib():
+    """The loaded ``libhsvd.so`` (raises if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError("libhsvd.so is not built (%s); run paper_1008_1371_gb300.build_lib.build()"
+                                   % LIB_PATH)
+            L = ctypes.CDLL(LIB_PATH)
+            L.hsvd_default_opts.argtypes = [ctypes.POINTER(HsvdOpts)]
+            L.hsvd_default_opts.restype = None
+            L.hsvd_status_string.argtypes = [_int]
+            L.hsvd_status_string.restype = ctypes.c_char_p
+            L.hsvd_solve.argtypes = [_p, _i64, _i64, _i64, _p, _dbl, _int, _p, _p, _i64, _p, _i64, _p, _p]
+            L.hsvd_solve.restype = _int
+            L.hsvd_solve_ex.argtypes = [_p, _i64, _i64, _i64, _p, _p, _p, _i64, _p, _i64,
+                                        ctypes.POINTER(HsvdOpts), ctypes.POINTER(HsvdInfo), _p]
+            L.hsvd_solve_ex.restype = _int
+            L.hsvd_modulus_pairs.argtypes = [_int, _int, _p]
+            L.hsvd_modulus_pairs.restype = _int
+            L.hsvd_pivot_gram.argtypes = [_p, _i64, _i64, _int, _int, _p, _p, _p]
+            L.hsvd_pivot_gram.restype = _int
+            L.hsvd_pivot_solve.argtypes = [_int, _int, _p, _p, _dbl, _int, _int, _p, _p, _p, _p]
+            L.hsvd_pivot_solve.restype = _int
+            L.hsvd_pivot_update.argtypes = [_p, _i64, _i64, _int, _int, _p, _p, _p, _p]
+            L.hsvd_pivot_update.restype = _int
+            _lib = L
+    return _lib
+
+
+def hsvd_status_string(status):
+    return lib().hsvd_status_string(int(status)).decode()
+
+
+def _colmajor(X, dtype):
+    """(m, n) tensor with strides (1, ld >= m), converting if needed."""
+    if X.dtype != dtype:
+        X = X.to(dtype)
+    m, n = X.shape
+    if X.stride(0) == 1 and (n == 1 or X.stride(1) >= max(m, 1)):
+        return X
+    return X.t().contiguous().t()
+
+
+def _empty_colmajor(m, n, like):
+    return torch.empty((n, m), dtype=torch.float64, device=like.device,
+                       pin_memory=(like.device.type == "cpu" and like.is_pinned())).t()
+
+
+def _stream_ptr(stream, device):
+    if device.type != "cuda":
+        return None
+    s = stream if stream is not None else torch.cuda.current_stream(device)
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+@dataclass
+class HsvdResult:
+    sigma: torch.Tensor
+    U: Optional[torch.Tensor]
+    V: Optional[torch.Tensor]
+    sweeps: int
+    status: int
+    method: int = 0
+    block_w: int = 0
+    rotations: int = 0
+    pair_updates: int = 0
+    kernel_launches: int = 0
+    ms_gram: float = 0.0
+    ms_solve: float = 0.0
+    ms_update: float = 0.0
+    ms_other: float = 0.0
+
+
+HSVD_SORT_AUTO = -1
+
+
+def make_opts(tol=0.0, max_sweeps=30, method=HSVD_METHOD_AUTO, block_w=0, inner_mode=HSVD_INNER_ORIENTED,
+              inner_max_passes=8, sort=None, profile=False):
+    """Options record; ``sort=None`` lets the library choose (sorting for the
+    pointwise method only)."""
+    o = HsvdOpts()
+    lib().hsvd_default_opts(ctypes.byref(o))
+    o.tol = float(tol)
+    o.max_sweeps = int(max_sweeps)
+    o.method = int(method)
+    o.block_w = int(block_w)
+    o.inner_mode = int(inner_mode)
+    o.inner_max_passes = int(inner_max_passes)
+    o.sort = HSVD_SORT_AUTO if sort is None else (1 if sort else 0)
+    o.profile = 1 if profile else 0
+    return o
+
+
+def hsvd_solve_ex(G, J, opts=None, compute_u=True, compute_v=True, stream=None, check=True, out=None):
+    """HSVD of one factor: G V = U diag(sigma), U^T U = I, V^T J V = J.
+
+    ``G`` (m x n float64) and ``J`` (n signs) are both CUDA tensors or both
+    CPU tensors (pinned memory makes the copies asynchronous).  ``opts`` is an
+    :class:`HsvdOpts` (see :func:`make_opts`).  ``out`` may hold preallocated
+    (sigma, U, V) tensors in column-major layout.  Returns an
+    :class:`HsvdResult`; raises :class:`HsvdError` on a negative status when
+    ``check``.
+    """
+    L = lib()
+    Gc = _colmajor(G, torch.float64)
+    m, n = Gc.shape
+    Jc = J.to(torch.int8).contiguous()
+    if Jc.device != Gc.device:
+        raise ValueError("G and J must be on the same device")
+    if out is not None:
+        sigma, U, V = out
+    else:
+        sigma = torch.empty(n, dtype=torch.float64, device=Gc.device,
+                            pin_memory=(Gc.device.type == "cpu" and Gc.is_pinned()))
+        U = _empty_colmajor(m, n, Gc) if compute_u else None
+        V = _empty_colmajor(n, n, Gc) if compute_v else None
+    o = opts if opts is not None else make_opts()
+    info = HsvdInfo()
+    st = L.hsvd_solve_ex(Gc.data_ptr(), m, n, Gc.stride(1) if n > 1 else m, Jc.data_ptr(), sigma.data_ptr(),
+                         U.data_ptr() if U is not None else None, U.stride(1) if U is not None else m,
+                         V.data_ptr() if V is not None else None, V.stride(1) if V is not None else n,
+                         ctypes.byref(o), ctypes.byref(info), _stream_ptr(stream, Gc.device))
+    if check and st < 0:
+        raise HsvdError(st)
+    return HsvdResult(sigma, U, V, info.sweeps, st, info.method, info.block_w, info.rotations, info.pair_updates,
+                      info.kernel_launches, info.ms_gram, info.ms_solve, info.ms_update, info.ms_other)
+
+
+def hsvd_solve(G, J, tol=0.0, max_sweeps=30, compute_u=True, compute_v=True, stream=None, check=True):
+    """``hsvd_solve`` of the C ABI: default options with the given tol and sweep cap."""
+    return hsvd_solve_ex(G, J, make_opts(tol=tol, max_sweeps=max_sweeps), compute_u, compute_v, stream, check)
+
+
+def hsvd_modulus_pairs(r, nsteps=None):
+    """The library's modified modulus table: int32 array (nsteps, r/2, 2)."""
+    import numpy as np
+
+    nsteps = r if nsteps is None else nsteps
+    out = np.zeros((nsteps, r // 2, 2), dtype=np.int32)
+    st = lib().hsvd_modulus_pairs(int(r), int(nsteps), out.ctypes.data_as(ctypes.c_void_p))
+    if st != HSVD_OK:
+        raise HsvdError(st)
+    return out
+
+
+def hsvd_pivot_gram(G, b, col0, stream=None):
+    """A_P blocks (npairs, 2b, 2b) of the block pairs whose first columns are
+    col0 (int32 CUDA tensor of shape (npairs, 2)); G column-major on the GPU,
+    rows a multiple of 64."""
+    L = lib()
+    Gc = _colmajor(G, torch.float64)
+    rows = Gc.shape[0]
+    npairs = col0.shape[0]
+    c0 = col0.to(torch.int32).contiguous()
+    A = torch.empty((npairs, 2 * b, 2 * b), dtype=torch.float64, device=Gc.device)
+    st = L.hsvd_pivot_gram(Gc.data_ptr(), rows, Gc.stride(1), int(b), npairs, c0.data_ptr(), A.data_ptr(),
+                           _stream_ptr(stream, Gc.device))
+    if st != HSVD_OK:
+        raise HsvdError(st)
+    # blocks are column-major: element (x, y) at x + y*2b -> tensor [k, y, x]
+    return A.transpose(1, 2)
+
+
+def hsvd_pivot_solve(A, sgn, tol, mode=1, max_passes=8, stream=None):
+    """J-orthogonalise pivot blocks A (npairs, 2b, 2b); returns
+    (A_out, W, rotations, status)."""
+    L = lib()
+    npairs, nn, _ = A.shape
+    Ab = A.transpose(1, 2).contiguous().clone()  # column-major blocks
+    W = torch.empty_like(Ab)
+    s = sgn.to(torch.int8).contiguous()
+    rot = torch.zeros(npairs, dtype=torch.int32, device=A.device)
+    status = torch.zeros(1, dtype=torch.int32, device=A.device)
+    st = L.hsvd_pivot_solve(nn // 2, npairs, Ab.data_ptr(), s.data_ptr(), float(tol), int(mode), int(max_passes),
+                            W.data_ptr(), rot.data_ptr(), status.data_ptr(), _stream_ptr(stream, A.device))
+    if st != HSVD_OK:
+        raise HsvdError(st)
+    return Ab.transpose(1, 2), W.transpose(1, 2), rot, status
+
+
+def hsvd_pivot_update(X, b, col0, W, rotated, stream=None):
+    """In place: X[:, I|J] <- X[:, I|J] W_k for pairs with rotated[k] != 0."""
+    L = lib()
+    if not (X.stride(0) == 1):
+        raise ValueError("X must be column-major")
+    rows = X.shape[0]
+    c0 = col0.to(torch.int32).contiguous()
+    Wb = W.transpose(1, 2).contiguous()
+    r = rotated.to(torch.int32).contiguous()
+    st = L.hsvd_pivot_update(X.data_ptr(), rows, X.stride(1), int(b), c0.shape[0], c0.data_ptr(), Wb.data_ptr(),
+                             r.data_ptr(), _stream_ptr(stream, X.device))
+    if st != HSVD_OK:
+        raise HsvdError(st)
+    return X

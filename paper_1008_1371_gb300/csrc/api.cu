@@ -1,0 +1,508 @@
+// api.cu -- the C ABI (include/hsvd.h): argument checks, host/device staging,
+// workspace, and the sweep driver of the blocked method (Alg. 4.1 on the host:
+// one CUDA graph per sweep, one synchronisation per sweep to read the
+// convergence counter).
+#include <cuda_runtime.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "hsvd_internal.cuh"
+
+using namespace hsvd;
+
+namespace {
+
+// Modified modulus pairs on r indices (Sec. 2), closed form: step s holds the
+// pairs (a, b), a < b, with a + b = (r - 1 + s) mod r (mod r), plus
+// (c/2, c/2 + r/2) for even residue c; slots ordered by a.
+void fill_modulus(int r, int nsteps, int *pairs) {
+    const int h = r / 2;
+    for (int s = 0; s < nsteps; ++s)
+        for (int k = 0; k < h; ++k) {
+            int a, b;
+            modulus_pair(r, s, k, a, b);
+            pairs[2 * (s * h + k)] = a;
+            pairs[2 * (s * h + k) + 1] = b;
+        }
+}
+
+// Cross pass over the off-diagonal block of a 2h x 2h pivot block: step s
+// pairs (k, h + (k + s) mod h).
+void fill_cross(int h, int *pairs) {
+    for (int s = 0; s < h; ++s)
+        for (int k = 0; k < h; ++k) {
+            pairs[2 * (s * h + k)] = k;
+            pairs[2 * (s * h + k) + 1] = h + (k + s) % h;
+        }
+}
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+struct Ws {
+    std::vector<void *> ptrs;
+    cudaStream_t st;
+    explicit Ws(cudaStream_t s) : st(s) {}
+    template <class T>
+    T *get(size_t count) {
+        void *p = nullptr;
+        if (cudaMallocAsync(&p, count * sizeof(T) + 16, st) != cudaSuccess) return nullptr;
+        ptrs.push_back(p);
+        return static_cast<T *>(p);
+    }
+    ~Ws() {
+        for (void *p : ptrs) cudaFreeAsync(p, st);
+    }
+};
+
+int64_t round_up(int64_t x, int64_t k) { return (x + k - 1) / k * k; }
+
+int choose_block(int64_t n) {
+    if (n >= 2048) return 32;
+    if (n >= 512) return 32;
+    return 16;
+}
+
+struct SweepStats {
+    int sweeps = 0;
+    long long rotations = 0, pair_updates = 0, launches = 0;
+    double ms_gram = 0, ms_solve = 0, ms_update = 0, ms_other = 0;
+};
+
+// CUDA events recorded as graph nodes around every kernel of a sweep when
+// profiling: ev[4 s + 0..3] bracket Gram / solve / update of step s, the last
+// two bracket the reordering.
+struct SweepEvents {
+    std::vector<cudaEvent_t> ev;
+    ~SweepEvents() {
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+    bool create(size_t count) {
+        ev.assign(count, nullptr);
+        for (auto &e : ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return false;
+        return true;
+    }
+    cudaError_t record(size_t i, cudaStream_t st) {
+        return ev.empty() ? cudaSuccess : cudaEventRecordWithFlags(ev[i], st, cudaEventRecordExternal);
+    }
+    float between(size_t a, size_t b) const {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[a], ev[b]);
+        return ms;
+    }
+};
+
+struct GraphGuard {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int *h_cnt = nullptr;
+    ~GraphGuard() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (h_cnt) cudaFreeHost(h_cnt);
+    }
+};
+
+#define CKR(expr)                                   \
+    do {                                            \
+        if ((expr) != cudaSuccess) return HSVD_ERR_CUDA; \
+    } while (0)
+
+// Blocked method on device arrays (Sec. 5; host loop of Alg. 4.1).
+int solve_blocked_core(const double *G, int64_t m, int64_t n, int64_t ldg, const int8_t *J, double *sigma,
+                       double *U, int64_t ldu, double *V, int64_t ldv, const hsvd_opts &o, double tol, int b,
+                       SweepStats &stats, cudaStream_t st) {
+    const int nn = 2 * b;
+    const int64_t n_pad = round_up(n, nn);
+    const int64_t m_pad = round_up(m + (n_pad - n), 64);
+    const int64_t ldw = round_up(n_pad, 64);
+    const int nb = (int)(n_pad / b);
+    const int npairs = nb / 2;
+    const int nsplit = gram_nsplit(m_pad, npairs);
+    GraphGuard gg;
+    Ws ws(st);
+    double *Gw = ws.get<double>(m_pad * n_pad), *Gt = ws.get<double>(m_pad * n_pad);
+    double *Ww = ws.get<double>(ldw * n_pad), *Wt = ws.get<double>(ldw * n_pad);
+    int *perm = ws.get<int>(n_pad), *perm_t = ws.get<int>(n_pad), *newpos = ws.get<int>(n_pad);
+    int8_t *sgn = ws.get<int8_t>(n_pad), *sgn_t = ws.get<int8_t>(n_pad);
+    double *d = ws.get<double>(n_pad);
+    double *part = ws.get<double>((size_t)npairs * 3 * nsplit * b * b);
+    double *Wp = ws.get<double>((size_t)npairs * nn * nn);
+    int *rotated = ws.get<int>(npairs);
+    // counters: [0] status (int), [2..3] rotations (u64), [4..5] updated pairs (u64)
+    int *cnt = ws.get<int>(8);
+    int *d_tab_outer = ws.get<int>((size_t)nb * npairs * 2);
+    int *d_tab_full = ws.get<int>((size_t)nn * b * 2);
+    int *d_tab_cross = ws.get<int>((size_t)b * b * 2);
+    if (!Gw || !Gt || !Ww || !Wt || !perm || !perm_t || !newpos || !sgn || !sgn_t || !d || !part || !Wp ||
+        !rotated || !cnt || !d_tab_outer || !d_tab_full || !d_tab_cross)
+        return HSVD_ERR_NOMEM;
+    unsigned long long *rot_ctr = reinterpret_cast<unsigned long long *>(cnt + 2);
+    unsigned long long *upd_ctr = reinterpret_cast<unsigned long long *>(cnt + 4);
+    {
+        // pair tables: outer over nb block columns as first-column indices
+        std::vector<int> outer((size_t)nb * npairs * 2), full((size_t)nn * b * 2), cross((size_t)b * b * 2);
+        fill_modulus(nb, nb, outer.data());
+        for (auto &v : outer) v *= b;
+        fill_modulus(nn, nn, full.data());
+        fill_cross(b, cross.data());
+        CKR(cudaMemcpyAsync(d_tab_outer, outer.data(), outer.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+        CKR(cudaMemcpyAsync(d_tab_full, full.data(), full.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+        CKR(cudaMemcpyAsync(d_tab_cross, cross.data(), cross.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+        CKR(cudaStreamSynchronize(st));  // the host vectors go out of scope
+    }
+    CKR(cudaMallocHost(&gg.h_cnt, 8 * sizeof(int)));
+    int *h_cnt = gg.h_cnt;
+    CKR(cudaMemsetAsync(cnt, 0, 8 * sizeof(int), st));
+    CKR(launch_load_pad(G, ldg, m, n, J, Gw, m_pad, n_pad, Ww, ldw, perm, sgn, cnt, st));
+    CKR(launch_reorder(Gw, Gt, m_pad, Ww, Wt, ldw, n_pad, perm, perm_t, sgn, sgn_t, d, newpos, o.sort, st));
+    CKR(cudaMemcpyAsync(h_cnt, cnt, 8 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CKR(cudaStreamSynchronize(st));
+    if (h_cnt[0] != 0) return h_cnt[0];
+
+    const int reorder_kernels = o.sort ? 3 : 2;
+    stats.launches += 1 + reorder_kernels;
+    SweepEvents evs;
+    if (o.profile && !evs.create((size_t)nb * 4 + 2)) return HSVD_ERR_CUDA;
+    const size_t evr = (size_t)nb * 4;
+
+    // one sweep as a graph: nb steps of (Gram, inner solve, update), then reorder
+    CKR(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+    {
+        cudaError_t e = cudaMemsetAsync(cnt + 2, 0, 4 * sizeof(int), st);
+        for (int s = 0; s < nb && e == cudaSuccess; ++s) {
+            const int *col0 = d_tab_outer + (size_t)s * npairs * 2;
+            const int mode = (o.inner_mode == HSVD_INNER_FULL) ? 0 : (s == 0 ? 2 : 1);
+            e = evs.record(4 * s, st);
+            if (e == cudaSuccess) e = launch_gram(Gw, m_pad, m_pad, b, npairs, col0, nsplit, part, st);
+            if (e == cudaSuccess) e = evs.record(4 * s + 1, st);
+            if (e == cudaSuccess)
+                e = launch_solve(b, npairs, part, nsplit, nullptr, sgn, col0, nullptr, tol, mode,
+                                 o.inner_max_passes, d_tab_full, d_tab_cross, Wp, rotated, rot_ctr, cnt, st);
+            if (e == cudaSuccess) e = evs.record(4 * s + 2, st);
+            if (e == cudaSuccess)
+                e = launch_update(Gw, m_pad, m_pad, Ww, ldw, ldw, b, npairs, col0, Wp, rotated, upd_ctr, st);
+            if (e == cudaSuccess) e = evs.record(4 * s + 3, st);
+        }
+        if (e == cudaSuccess) e = evs.record(evr, st);
+        if (e == cudaSuccess)
+            e = launch_reorder(Gw, Gt, m_pad, Ww, Wt, ldw, n_pad, perm, perm_t, sgn, sgn_t, d, newpos, o.sort, st);
+        if (e == cudaSuccess) e = evs.record(evr + 1, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h_cnt, cnt, 8 * sizeof(int), cudaMemcpyDeviceToHost, st);
+        const cudaError_t e2 = cudaStreamEndCapture(st, &gg.graph);
+        if (e != cudaSuccess || e2 != cudaSuccess) return HSVD_ERR_CUDA;
+    }
+    CKR(cudaGraphInstantiate(&gg.exec, gg.graph, 0));
+    int status = HSVD_NOT_CONVERGED, sweep;
+    for (sweep = 1; sweep <= o.max_sweeps; ++sweep) {
+        CKR(cudaGraphLaunch(gg.exec, st));
+        CKR(cudaStreamSynchronize(st));
+        unsigned long long rots, upds;
+        memcpy(&rots, h_cnt + 2, sizeof rots);
+        memcpy(&upds, h_cnt + 4, sizeof upds);
+        stats.rotations += (long long)rots;
+        stats.pair_updates += (long long)upds;
+        stats.sweeps = sweep;
+        stats.launches += 3LL * nb + reorder_kernels;
+        if (o.profile) {
+            for (int s = 0; s < nb; ++s) {
+                stats.ms_gram += evs.between(4 * s, 4 * s + 1);
+                stats.ms_solve += evs.between(4 * s + 1, 4 * s + 2);
+                stats.ms_update += evs.between(4 * s + 2, 4 * s + 3);
+            }
+            stats.ms_other += evs.between(evr, evr + 1);
+        }
+        if (h_cnt[0] != 0) { status = h_cnt[0]; break; }
+        if (rots == 0) { status = HSVD_OK; break; }
+    }
+    if (status == HSVD_OK || status == HSVD_NOT_CONVERGED) {
+        CKR(cudaMemsetAsync(cnt, 0, sizeof(int), st));
+        CKR(launch_finalize(Gw, m_pad, Ww, ldw, perm, n_pad, m, n, sigma, U, ldu, V, ldv, cnt, st));
+        stats.launches += 1;
+        CKR(cudaMemcpyAsync(h_cnt, cnt, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CKR(cudaStreamSynchronize(st));
+        if (h_cnt[0] != 0) status = h_cnt[0];
+    }
+    return status;
+}
+
+int solve_blocked(const double *G, int64_t m, int64_t n, int64_t ldg, const int8_t *J, double *sigma, double *U,
+                  int64_t ldu, double *V, int64_t ldv, const hsvd_opts &o, double tol, int b, hsvd_info *info,
+                  cudaStream_t st) {
+    SweepStats stats;
+    const int rc = solve_blocked_core(G, m, n, ldg, J, sigma, U, ldu, V, ldv, o, tol, b, stats, st);
+    if (info) {
+        info->sweeps = stats.sweeps;
+        info->method = HSVD_METHOD_BLOCKED;
+        info->block_w = b;
+        info->rotations = stats.rotations;
+        info->pair_updates = stats.pair_updates;
+        info->kernel_launches = stats.launches;
+        info->ms_gram = stats.ms_gram;
+        info->ms_solve = stats.ms_solve;
+        info->ms_update = stats.ms_update;
+        info->ms_other = stats.ms_other;
+    }
+    return rc;
+}
+
+int solve_pointwise(const double *G, int64_t m, int64_t n, int64_t ldg, const int8_t *J, double *sigma, double *U,
+                    int64_t ldu, double *V, int64_t ldv, const hsvd_opts &o, double tol, hsvd_info *info,
+                    cudaStream_t st) {
+    const int64_t n_pad = n + (n & 1);
+    Ws ws(st);
+    double *W = ws.get<double>(n_pad * n_pad);
+    int *out = ws.get<int>(4);
+    long long *rot = ws.get<long long>(1);
+    int h_out[4] = {0, 0, 0, 0};
+    long long h_rot = 0;
+    if (!W || !out || !rot) return HSVD_ERR_NOMEM;
+    SweepEvents evs;
+    if (o.profile && !evs.create(2)) return HSVD_ERR_CUDA;
+    CKR(evs.record(0, st));
+    CKR(launch_pointwise(G, ldg, (int)m, (int)n, J, tol, o.max_sweeps, o.sort, W, sigma, U, ldu, V, ldv, out, rot,
+                         st));
+    CKR(evs.record(1, st));
+    CKR(cudaMemcpyAsync(h_out, out, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CKR(cudaMemcpyAsync(&h_rot, rot, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    CKR(cudaStreamSynchronize(st));
+    if (info) {
+        info->sweeps = h_out[1];
+        info->method = HSVD_METHOD_POINTWISE;
+        info->block_w = 1;
+        info->rotations = h_rot;
+        info->pair_updates = 0;
+        info->kernel_launches = 1;
+        if (o.profile) info->ms_solve = evs.between(0, 1);
+    }
+    return h_out[0];
+}
+
+int validate(const double *G, int64_t m, int64_t n, int64_t ldg, const int8_t *J, const double *sigma, int64_t ldu,
+             const double *U, int64_t ldv, const double *V) {
+    if (!G || !J || !sigma) return HSVD_ERR_ARG;
+    if (n < 1 || m < n || ldg < m) return HSVD_ERR_ARG;
+    if (n > (int64_t)1 << 24 || m > (int64_t)1 << 31) return HSVD_ERR_ARG;
+    if (U && ldu < m) return HSVD_ERR_ARG;
+    if (V && ldv < n) return HSVD_ERR_ARG;
+    return HSVD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void hsvd_default_opts(hsvd_opts *o) {
+    if (!o) return;
+    memset(o, 0, sizeof *o);
+    o->tol = 0.0;
+    o->max_sweeps = 30;
+    o->method = HSVD_METHOD_AUTO;
+    o->block_w = 0;
+    o->inner_mode = HSVD_INNER_ORIENTED;
+    o->inner_max_passes = 8;
+    o->sort = HSVD_SORT_AUTO;
+}
+
+const char *hsvd_status_string(int s) {
+    switch (s) {
+        case HSVD_OK: return "HSVD_OK";
+        case HSVD_NOT_CONVERGED: return "HSVD_NOT_CONVERGED";
+        case HSVD_ERR_ARG: return "HSVD_ERR_ARG";
+        case HSVD_ERR_RANK: return "HSVD_ERR_RANK";
+        case HSVD_ERR_NONFINITE: return "HSVD_ERR_NONFINITE";
+        case HSVD_ERR_CUDA: return "HSVD_ERR_CUDA";
+        case HSVD_ERR_NOMEM: return "HSVD_ERR_NOMEM";
+        default: return "HSVD_UNKNOWN_STATUS";
+    }
+}
+
+int hsvd_modulus_pairs(int r, int nsteps, int *pairs) {
+    if (r < 2 || (r & 1) || r > 65536 || nsteps < 0 || (!pairs && nsteps > 0)) return HSVD_ERR_ARG;
+    fill_modulus(r, nsteps, pairs);
+    return HSVD_OK;
+}
+
+int hsvd_solve_ex(const double *G, int64_t m, int64_t n, int64_t ldg, const int8_t *J, double *sigma, double *U,
+                  int64_t ldu, double *V, int64_t ldv, const hsvd_opts *opts_in, hsvd_info *info, void *stream) {
+    hsvd_opts o;
+    if (opts_in) o = *opts_in;
+    else hsvd_default_opts(&o);
+    if (info) memset(info, 0, sizeof *info);
+    int rc = validate(G, m, n, ldg, J, sigma, ldu, U, ldv, V);
+    if (rc == HSVD_OK) {
+        for (int i = 0; i < 7; ++i)
+            if (o.reserved[i]) rc = HSVD_ERR_ARG;
+        if (o.max_sweeps <= 0) o.max_sweeps = 30;
+        if (o.inner_max_passes <= 0) o.inner_max_passes = 8;
+        if (o.method < HSVD_METHOD_AUTO || o.method > HSVD_METHOD_BLOCKED) rc = HSVD_ERR_ARG;
+        if (o.block_w != 0 && o.block_w != 16 && o.block_w != 32 && o.block_w != 64) rc = HSVD_ERR_ARG;
+        if (o.inner_mode != HSVD_INNER_ORIENTED && o.inner_mode != HSVD_INNER_FULL) rc = HSVD_ERR_ARG;
+        if (o.sort != 0 && o.sort != 1 && o.sort != HSVD_SORT_AUTO) rc = HSVD_ERR_ARG;
+        if (!(o.tol == o.tol)) rc = HSVD_ERR_ARG;
+    }
+    if (rc != HSVD_OK) {
+        if (info) info->status = rc;
+        return rc;
+    }
+    const double tol = (o.tol > 0.0) ? o.tol : (double)n * 0x1p-53;
+    cudaStream_t user = static_cast<cudaStream_t>(stream);
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    const bool dev = is_device_ptr(G);
+    // all arrays of one call are of one kind
+    const void *arrs[5] = {J, sigma, U, V, nullptr};
+    for (int i = 0; i < 4; ++i)
+        if (arrs[i] && is_device_ptr(arrs[i]) != dev) {
+            if (info) info->status = HSVD_ERR_ARG;
+            return HSVD_ERR_ARG;
+        }
+    int method = o.method;
+    if (method == HSVD_METHOD_AUTO) method = pointwise_fits(m, n) ? HSVD_METHOD_POINTWISE : HSVD_METHOD_BLOCKED;
+    // diagonal sorting pays for the pointwise method (Sec. 5, Table 5.3) but
+    // costs sweeps in the blocked one (measured on the graded 1024 factor)
+    if (o.sort == HSVD_SORT_AUTO) o.sort = (method == HSVD_METHOD_POINTWISE) ? 1 : 0;
+    if (method == HSVD_METHOD_POINTWISE && !pointwise_fits(m, n)) {
+        if (info) info->status = HSVD_ERR_ARG;
+        return HSVD_ERR_ARG;
+    }
+    const int b = o.block_w ? o.block_w : choose_block(n);
+    double *dG = nullptr, *dS = nullptr, *dU = nullptr, *dV = nullptr;
+    int8_t *dJ = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+        if (info) info->status = HSVD_ERR_CUDA;
+        return HSVD_ERR_CUDA;
+    }
+    // order after the work already queued on the caller's stream
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(ev, user) != cudaSuccess || cudaStreamWaitEvent(st, ev, 0) != cudaSuccess) {
+        rc = HSVD_ERR_CUDA;
+        goto done;
+    }
+    if (!dev) {
+        // host arrays: stage through device memory on the internal stream
+        if (cudaMallocAsync((void **)&dG, sizeof(double) * m * n, st) != cudaSuccess ||
+            cudaMallocAsync((void **)&dJ, n, st) != cudaSuccess ||
+            cudaMallocAsync((void **)&dS, sizeof(double) * n, st) != cudaSuccess ||
+            (U && cudaMallocAsync((void **)&dU, sizeof(double) * m * n, st) != cudaSuccess) ||
+            (V && cudaMallocAsync((void **)&dV, sizeof(double) * n * n, st) != cudaSuccess)) {
+            rc = HSVD_ERR_NOMEM;
+            goto done;
+        }
+        if (cudaMemcpy2DAsync(dG, sizeof(double) * m, G, sizeof(double) * ldg, sizeof(double) * m, n,
+                              cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(dJ, J, n, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+            rc = HSVD_ERR_CUDA;
+            goto done;
+        }
+    }
+    {
+        const double *g = dev ? G : dG;
+        const int8_t *j = dev ? J : dJ;
+        double *s = dev ? sigma : dS;
+        double *u = dev ? U : dU;
+        double *v = dev ? V : dV;
+        const int64_t lg = dev ? ldg : m, lu = dev ? ldu : m, lv = dev ? ldv : n;
+        if (method == HSVD_METHOD_POINTWISE)
+            rc = solve_pointwise(g, m, n, lg, j, s, u, lu, v, lv, o, tol, info, st);
+        else
+            rc = solve_blocked(g, m, n, lg, j, s, u, lu, v, lv, o, tol, b, info, st);
+    }
+    if (!dev && (rc == HSVD_OK || rc == HSVD_NOT_CONVERGED)) {
+        if (cudaMemcpyAsync(sigma, dS, sizeof(double) * n, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            (U && cudaMemcpy2DAsync(U, sizeof(double) * ldu, dU, sizeof(double) * m, sizeof(double) * m, n,
+                                    cudaMemcpyDeviceToHost, st) != cudaSuccess) ||
+            (V && cudaMemcpy2DAsync(V, sizeof(double) * ldv, dV, sizeof(double) * n, sizeof(double) * n, n,
+                                    cudaMemcpyDeviceToHost, st) != cudaSuccess))
+            rc = HSVD_ERR_CUDA;
+    }
+done:
+    if (dG) cudaFreeAsync(dG, st);
+    if (dJ) cudaFreeAsync(dJ, st);
+    if (dS) cudaFreeAsync(dS, st);
+    if (dU) cudaFreeAsync(dU, st);
+    if (dV) cudaFreeAsync(dV, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess && rc >= 0) rc = HSVD_ERR_CUDA;
+    if (ev) cudaEventDestroy(ev);
+    cudaStreamDestroy(st);
+    if (info) info->status = rc;
+    return rc;
+}
+
+int hsvd_solve(const double *G, int64_t m, int64_t n, int64_t ldg, const int8_t *J, double tol, int max_sweeps,
+               double *sigma, double *U, int64_t ldu, double *V, int64_t ldv, int *sweeps, void *stream) {
+    hsvd_opts o;
+    hsvd_default_opts(&o);
+    o.tol = tol;
+    o.max_sweeps = max_sweeps;
+    hsvd_info info;
+    const int rc = hsvd_solve_ex(G, m, n, ldg, J, sigma, U, ldu, V, ldv, &o, &info, stream);
+    if (sweeps) *sweeps = info.sweeps;
+    return rc;
+}
+
+int hsvd_pivot_gram(const double *G, int64_t rows, int64_t ldg, int b, int npairs, const int *col0, double *A,
+                    void *stream) {
+    if (!G || !col0 || !A || npairs < 1 || rows < 1 || (rows % 64) || ldg < rows) return HSVD_ERR_ARG;
+    if (b != 16 && b != 32 && b != 64) return HSVD_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int nsplit = gram_nsplit(rows, npairs);
+    double *part = nullptr;
+    if (cudaMallocAsync((void **)&part, sizeof(double) * npairs * 3 * nsplit * b * b, st) != cudaSuccess)
+        return HSVD_ERR_NOMEM;
+    int rc = HSVD_OK;
+    if (launch_gram(G, rows, ldg, b, npairs, col0, nsplit, part, st) != cudaSuccess ||
+        launch_assemble(b, npairs, part, nsplit, A, st) != cudaSuccess)
+        rc = HSVD_ERR_CUDA;
+    cudaFreeAsync(part, st);
+    return rc;
+}
+
+int hsvd_pivot_solve(int b, int npairs, double *A, const int8_t *sgn, double tol, int mode, int max_passes, double *W,
+                     int *rotated, int *status_dev, void *stream) {
+    if (!A || !sgn || !W || !rotated || npairs < 1 || !(tol > 0.0)) return HSVD_ERR_ARG;
+    if (b != 16 && b != 32 && b != 64) return HSVD_ERR_ARG;
+    if (mode < 0 || mode > 2 || (mode == 0 && max_passes < 1)) return HSVD_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int nn = 2 * b;
+    std::vector<int> full((size_t)nn * b * 2), cross((size_t)b * b * 2);
+    fill_modulus(nn, nn, full.data());
+    fill_cross(b, cross.data());
+    int *dt = nullptr;
+    if (cudaMallocAsync((void **)&dt, sizeof(int) * (full.size() + cross.size()), st) != cudaSuccess)
+        return HSVD_ERR_NOMEM;
+    int rc = HSVD_OK;
+    if (cudaMemcpyAsync(dt, full.data(), full.size() * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(dt + full.size(), cross.data(), cross.size() * sizeof(int), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        launch_solve(b, npairs, nullptr, 0, A, nullptr, nullptr, sgn, tol, mode, mode == 0 ? max_passes : 1, dt,
+                     dt + full.size(), W, rotated, nullptr, status_dev, st) != cudaSuccess)
+        rc = HSVD_ERR_CUDA;
+    // the host tables must outlive the asynchronous copies
+    if (cudaStreamSynchronize(st) != cudaSuccess) rc = HSVD_ERR_CUDA;
+    cudaFreeAsync(dt, st);
+    return rc;
+}
+
+int hsvd_pivot_update(double *X, int64_t rows, int64_t ldx, int b, int npairs, const int *col0, const double *W,
+                      const int *rotated, void *stream) {
+    if (!X || !col0 || !W || !rotated || npairs < 1 || rows < 1 || (rows % 32) || ldx < rows) return HSVD_ERR_ARG;
+    if (b != 16 && b != 32 && b != 64) return HSVD_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return launch_update(X, rows, ldx, nullptr, 0, 0, b, npairs, col0, W, rotated, nullptr, st) == cudaSuccess
+               ? HSVD_OK
+               : HSVD_ERR_CUDA;
+}
+
+}  // extern "C"

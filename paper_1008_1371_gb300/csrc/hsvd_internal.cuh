@@ -1,0 +1,153 @@
+// hsvd_internal.cuh -- device helpers and cross-file declarations of the GB300
+// hyperbolic SVD library.  Everything here is internal; the public C ABI is
+// include/hsvd.h.
+//
+// The whole library is compiled with -fmad=false: every fused multiply-add is
+// written out as fma(), so the rounding of each formula is the one stated in
+// its comment (the parenthesised terms of Eq. 2.4 / 2.5 use one FMA, Sec. 2).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/hsvd.h"
+
+namespace hsvd {
+
+constexpr int kWarp = 32;
+
+// Relative orthogonality test (Eq. 2.3): a pair is left alone when
+// |a_ij| < tol sqrt(a_ii a_jj), and also when a_ij == 0 exactly (exactly
+// orthogonal columns, e.g. a zero or bordering column, are never rotated).
+__device__ __forceinline__ bool pair_passes(double aii, double ajj, double aij, double tol) {
+    return aij == 0.0 || fabs(aij) < tol * sqrt(aii * ajj);
+}
+
+// Rotation annihilating a_ij (Sec. 2, Eq. 2.2).  hyp = -1 trigonometric
+// (equal signs in J), +1 hyperbolic.  The update it defines is
+//   g_i' = (g_i + hyp t g_j) c,   g_j' = (t g_i + g_j) c        (Alg. 4.5).
+// Requiring a_ij' = 0 gives a_ij (1 + hyp t^2) + t (a_ii + hyp a_jj) = 0; t is
+// its smaller root, written through zeta so that nothing overflows:
+//   trig: zeta = (a_jj - a_ii)/(2 a_ij), t = sign(zeta)/(|zeta| + sqrt(zeta^2+1)),
+//         c = 1/sqrt(1 + t^2)
+//   hyp:  zeta = -(a_ii + a_jj)/(2 a_ij), t = sign(zeta)/(|zeta| + sqrt(zeta^2-1)),
+//         c = 1/sqrt((1 - t)(1 + t))
+// sign(0) = +1.  Returns false (t = 0, c = 1) when a hyperbolic pair has
+// |zeta| <= 1: no J-unitary rotation exists, the pair is rank deficient.
+__device__ __forceinline__ bool rotation_params(double aii, double ajj, double aij, int hyp,
+                                                double &t, double &c) {
+    if (hyp < 0) {
+        const double zeta = (ajj - aii) / (2.0 * aij);
+        double tt = 1.0 / (fabs(zeta) + sqrt(zeta * zeta + 1.0));
+        if (zeta < 0.0) tt = -tt;
+        t = tt;
+        c = 1.0 / sqrt(1.0 + tt * tt);
+        return true;
+    }
+    const double zeta = -(aii + ajj) / (2.0 * aij);
+    if (!(fabs(zeta) > 1.0)) {
+        t = 0.0;
+        c = 1.0;
+        return false;
+    }
+    double tt = 1.0 / (fabs(zeta) + sqrt(zeta * zeta - 1.0));
+    if (zeta < 0.0) tt = -tt;
+    t = tt;
+    c = 1.0 / sqrt((1.0 - tt) * (1.0 + tt));
+    return true;
+}
+
+// k-th pivot pair (a < b) of step `s` of the modified modulus strategy on r
+// indices (Sec. 2): the pairs with a + b = c (mod r), c = (r - 1 + s) mod r,
+// plus (c/2, c/2 + r/2) for even c.  Slots are ordered by their smaller index.
+__host__ __device__ __forceinline__ void modulus_pair(int r, int s, int k, int &a, int &b) {
+    const int c = (r - 1 + (s % r)) % r;
+    if (c & 1) {
+        const int low = (c + 1) / 2;  // pairs (k, c - k), k < low
+        if (k < low) { a = k; b = c - k; }
+        else { a = c + 1 + (k - low); b = c + r - a; }
+    } else {
+        const int low = c / 2;
+        if (k < low) { a = k; b = c - k; }
+        else if (k == low) { a = c / 2; b = c / 2 + r / 2; }
+        else { a = c + 1 + (k - low - 1); b = c + r - a; }
+    }
+    if (a > b) { const int x = a; a = b; b = x; }
+}
+
+// Scaled Euclidean norm pieces: x * 2^-e with 2^e >= max|x| is exact, so the
+// scaled sum of squares equals the plain one without over- or underflow.
+__device__ __forceinline__ double pow2_scale_for(double maxabs, int &e) {
+    if (maxabs == 0.0 || !isfinite(maxabs)) { e = 0; return 1.0; }
+    frexp(maxabs, &e);
+    return ldexp(1.0, -e);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// A_P element e = x + y NN of pair `pair` from the three partial blocks
+// (I,I) | (I,J) / (J,I) = (I,J)^T | (J,J), each summed over the row splits in
+// split order.  A_P comes out exactly symmetric.
+template <int NN>
+__device__ __forceinline__ double assemble_entry(const double *__restrict__ part, int nsplit, int pair, int e) {
+    constexpr int B = NN / 2;
+    const int x = e % NN, y = e / NN;
+    int blk, bx = x % B, by = y % B;
+    if (x < B && y < B) blk = 0;
+    else if (x >= B && y >= B) blk = 2;
+    else {
+        blk = 1;
+        if (x >= B) { const int z = bx; bx = by; by = z; }
+    }
+    const double *pp = part + ((size_t)pair * 3 + blk) * nsplit * B * B + bx + (size_t)by * B;
+    double v = 0.0;
+    for (int s = 0; s < nsplit; ++s) v += pp[(size_t)s * B * B];
+    return v;
+}
+
+// ---- launchers implemented in the .cu files --------------------------------
+
+// pointwise.cu: one CTA solves one factor held in shared memory.
+size_t pointwise_smem_bytes(int64_t m_pad, int64_t n_pad);
+bool pointwise_fits(int64_t m, int64_t n);
+cudaError_t launch_pointwise(const double *G, int64_t ldg, int m, int n, const int8_t *J,
+                             double tol, int max_sweeps, int sort, double *Wws,
+                             double *sigma, double *U, int64_t ldu, double *V, int64_t ldv,
+                             int *dev_out, long long *dev_rot, cudaStream_t st);
+
+// blocked.cu: the three kernels of one step of the blocked method.
+int gram_nsplit(int64_t rows, int npairs);
+cudaError_t launch_gram(const double *G, int64_t rows, int64_t ldg, int b, int npairs,
+                        const int *col0, int nsplit, double *part, cudaStream_t st);
+cudaError_t launch_solve(int b, int npairs, const double *part, int nsplit, double *A,
+                         const int8_t *sgn_cols, const int *col0, const int8_t *sgn_direct,
+                         double tol, int mode, int max_passes, const int *tab_full,
+                         const int *tab_cross, double *Wp, int *rotated,
+                         unsigned long long *rot_count, int *status, cudaStream_t st);
+cudaError_t launch_assemble(int b, int npairs, const double *part, int nsplit, double *A, cudaStream_t st);
+cudaError_t launch_update(double *X, int64_t rows, int64_t ldx, double *Y, int64_t rowsY,
+                          int64_t ldy, int b, int npairs, const int *col0, const double *Wp,
+                          const int *rotated, unsigned long long *upd_count, cudaStream_t st);
+
+// prep.cu: bordering, reordering, finalisation.
+cudaError_t launch_load_pad(const double *G, int64_t ldg, int64_t m, int64_t n, const int8_t *J,
+                            double *Gw, int64_t m_pad, int64_t n_pad, double *Ww, int64_t ldw,
+                            int *perm, int8_t *sgn, int *status, cudaStream_t st);
+cudaError_t launch_reorder(double *Gw, double *Gt, int64_t m_pad, double *Ww, double *Wt,
+                           int64_t ldw, int64_t n_pad, int *perm, int *perm_t, int8_t *sgn,
+                           int8_t *sgn_t, double *d, int *newpos, int sort, cudaStream_t st);
+cudaError_t launch_finalize(const double *Gw, int64_t m_pad, const double *Ww, int64_t ldw,
+                            const int *perm, int64_t n_pad, int64_t m, int64_t n, double *sigma,
+                            double *U, int64_t ldu, double *V, int64_t ldv, int *status,
+                            cudaStream_t st);
+
+}  // namespace hsvd

@@ -1,0 +1,77 @@
+"""The C ABI library builds, loads without a GPU and exports every symbol the
+header declares; host-only entry points (status strings, the pivot-strategy
+table, argument checks) work on the CPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "hsvd.h")
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_1008_1371_gb300 import api, build_lib
+
+    build_lib.build()
+    return api
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hsvd_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_symbols_exported(api):
+    L = api.lib()
+    names = _declared_functions()
+    assert "hsvd_solve" in names and "hsvd_solve_ex" in names
+    for name in names:
+        assert hasattr(L, name), name  # ctypes resolves the symbol or raises
+
+
+def test_status_strings(api):
+    for code, name in ((0, "HSVD_OK"), (1, "HSVD_NOT_CONVERGED"), (-1, "HSVD_ERR_ARG"), (-2, "HSVD_ERR_RANK"),
+                       (-3, "HSVD_ERR_NONFINITE"), (-4, "HSVD_ERR_CUDA"), (-5, "HSVD_ERR_NOMEM")):
+        assert api.hsvd_status_string(code) == name
+    assert api.hsvd_status_string(12345) == "HSVD_UNKNOWN_STATUS"
+
+
+@pytest.mark.parametrize("r", [2, 4, 8, 16, 32, 64, 128, 256])
+def test_library_strategy_matches_oracle_stepper(api, orc, r):
+    """The library's closed-form modulus table and the oracle's Alg. 4.4
+    stepper (written independently) give the same pair sets in every step,
+    across two quasi-sweeps."""
+    lib_t = api.hsvd_modulus_pairs(r, 2 * r)
+    orc_t = orc.modulus_pairs(r, 2 * r)
+    for s in range(2 * r):
+        a = {tuple(sorted(p)) for p in lib_t[s].tolist()}
+        b = {tuple(sorted(p)) for p in orc_t[s].tolist()}
+        assert a == b, s
+        # library slots are ordered by their smaller index, a < b inside a pair
+        firsts = [p[0] for p in lib_t[s].tolist()]
+        assert firsts == sorted(firsts) and all(p[0] < p[1] for p in lib_t[s].tolist())
+
+
+def test_argument_errors_without_gpu(api):
+    L = api.lib()
+    G = np.zeros((4, 4))
+    J = np.ones(4, dtype=np.int8)
+    s = np.zeros(4)
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    # m < n, ldg < m, n < 1, bad pair-table argument
+    assert L.hsvd_solve(p(G), 3, 4, 4, p(J), 0.0, 30, p(s), None, 3, None, 4, None, None) == api.HSVD_ERR_ARG
+    assert L.hsvd_solve(p(G), 4, 4, 3, p(J), 0.0, 30, p(s), None, 4, None, 4, None, None) == api.HSVD_ERR_ARG
+    assert L.hsvd_solve(p(G), 4, 0, 4, p(J), 0.0, 30, p(s), None, 4, None, 4, None, None) == api.HSVD_ERR_ARG
+    assert L.hsvd_solve(None, 4, 4, 4, p(J), 0.0, 30, p(s), None, 4, None, 4, None, None) == api.HSVD_ERR_ARG
+    out = np.zeros(8, dtype=np.int32)
+    assert L.hsvd_modulus_pairs(3, 1, p(out)) == api.HSVD_ERR_ARG
+    o = api.make_opts(block_w=24)
+    info = api.HsvdInfo()
+    assert L.hsvd_solve_ex(p(G), 4, 4, 4, p(J), p(s), None, 4, None, 4, ctypes.byref(o), ctypes.byref(info),
+                           None) == api.HSVD_ERR_ARG
+    assert info.status == api.HSVD_ERR_ARG

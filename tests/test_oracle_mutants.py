@@ -27,9 +27,10 @@ MUTANTS = {
     "dot_drops_first_term": ("for (int64_t i = 0; i < m; ++i) s += x[i] * y[i];",
                              "for (int64_t i = 1; i < m; ++i) s += x[i] * y[i];"),
     "stepper_threshold": ("if (ip[k] + jp[k] > r - 2) {", "if (ip[k] + jp[k] > r - 3) {"),
-    "inner_diag_drops_hyp": ("AE(p, p) = fma(ht, apq, AE(p, p));", "AE(p, p) = fma(T[k], apq, AE(p, p));"),
-    "inner_row_update_transposed": ("X[0][y] = fma(htk, B[1][y], B[0][y]) * C[k];",
-                                    "X[0][y] = fma(htk, B[0][y], B[1][y]) * C[k];"),
+    "inner_diag_drops_hyp": ("d[p] = fma(ht, apq[k], d[p]);", "d[p] = fma(T[k], apq[k], d[p]);"),
+    "inner_update_transposed": ("row[P[k]] = fma(ht, b, a) * C[k];", "row[P[k]] = fma(ht, a, b) * C[k];"),
+    "inner_second_half_dropped": ("            transposed ^= 1;\n            mix_rows(nn, S, h, P, Q, T, C, H, rot);",
+                                  "            transposed ^= 1;\n"),
     "block_update_transposed_W": ("* Wp[x + y * nn];", "* Wp[y + x * nn];"),
     "test_uses_product_not_sqrt": ("if (aij == 0.0 || fabs(aij) < tol * sqrt(aii * ajj)) return ORC_OK;",
                                    "if (aij == 0.0 || fabs(aij) < tol * (aii * ajj)) return ORC_OK;"),
