@@ -26,6 +26,17 @@ def _rng(seed):
     return np.random.Generator(np.random.PCG64(seed))
 
 
+def _pow10(exponents):
+    """10**x rounded to float64 through 40-digit decimal arithmetic, so the
+    bytes do not depend on the platform's libm (its pow() may differ in the
+    last bit between machines)."""
+    import decimal
+
+    ctx = decimal.Context(prec=40)
+    ten = decimal.Decimal(10)
+    return np.array([float(ctx.power(ten, decimal.Decimal(repr(float(x))))) for x in exponents])
+
+
 def _haar(rng, n):
     """Haar-distributed orthogonal matrix: QR of a Gaussian matrix with the
     signs of R's diagonal moved into Q."""
@@ -64,7 +75,7 @@ def graded(n, decades=6.0, m=None, p=None, seed=2):
     m = n if m is None else m
     p = n // 2 if p is None else p
     B = rng.standard_normal((m, n))
-    scale = 10.0 ** (-decades * np.arange(n) / n)
+    scale = _pow10(-decades * np.arange(n) / n)
     G = np.asfortranarray(B * scale[None, :])
     return G, signs_block(n, p)
 
@@ -75,7 +86,7 @@ def haar(n, lo=1e-6, hi=1.0, p=None, seed=3):
     p = n // 2 if p is None else p
     Q1 = _haar(rng, n)
     Q2 = _haar(rng, n)
-    sigma = 10.0 ** rng.uniform(np.log10(lo), np.log10(hi), size=n)
+    sigma = _pow10(rng.uniform(np.log10(lo), np.log10(hi), size=n))
     G = np.asfortranarray((Q1 * sigma[None, :]) @ Q2)
     return G, signs_random(rng, n, p)
 

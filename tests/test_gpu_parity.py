@@ -157,13 +157,15 @@ def test_pointwise_statuses(api):
 
 
 # ---------------------------------------------------------------- blocked
-@pytest.mark.parametrize("b,inner", [(16, 0), (32, 0), (16, 1), (64, 0), (32, 1)])
-def test_blocked_graded_256(api, b, inner):
+@pytest.mark.parametrize("b,inner,sort", [(16, 0, False), (32, 0, False), (16, 1, False), (64, 0, False),
+                                          (32, 1, False), (32, 0, True)])
+def test_blocked_graded_256(api, b, inner, sort):
     n = 256
     G, J = W.graded(n, decades=6, seed=2)
     tol = n * U64
     ref = oracle.hsvd(G, J, tol, 40)
-    r = _gpu(api, G, J, tol=tol, max_sweeps=40, method=api.HSVD_METHOD_BLOCKED, block_w=b, inner_mode=inner)
+    r = _gpu(api, G, J, tol=tol, max_sweeps=40, method=api.HSVD_METHOD_BLOCKED, block_w=b, inner_mode=inner,
+             sort=sort)
     assert r["status"] == api.HSVD_OK
     assert _sigma_err(J, r["sigma"], ref["sigma"]) <= 1e-12
     orth, junit, resid = _invariants(G, J, r)
@@ -172,7 +174,7 @@ def test_blocked_graded_256(api, b, inner):
     # the oracle's blocked method with the same block width, inner mode and sorting
     # (the oracle numbers its inner modes 0 = full-block, 1 = block-oriented)
     ob = oracle.block_hsvd(G, J, b, tol, 40, inner_mode=1 if inner == api.HSVD_INNER_ORIENTED else 0,
-                           inner_max_passes=8, sort=True)
+                           inner_max_passes=8, sort=sort)
     assert ob["status"] == 0 and abs(ob["sweeps"] - r["sweeps"]) <= 1
     assert _sigma_err(J, r["sigma"], ob["sigma"]) <= 1e-12
 
