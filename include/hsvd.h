@@ -170,6 +170,32 @@ int hsvd_pivot_solve(int b, int npairs, double *A, const int8_t *sgn, double tol
 int hsvd_pivot_update(double *X, int64_t rows, int64_t ldx, int b, int npairs, const int *col0,
                       const double *W, const int *rotated, void *stream);
 
+/*
+ * hsvd_solve_pointwise_noalloc -- the pointwise solver (HSVD_METHOD_POINTWISE)
+ * without any allocation, for callers that cannot allocate device memory: code
+ * running while another allocator owns the device, real-time or certified
+ * code that forbids allocation after start-up, memory-capped contexts.  The
+ * paper has no counterpart; it is an interface choice of this library.
+ *
+ * Its scratch (the accumulated transformation and two status words) is a fixed
+ * device array inside the library, sized for n <= HSVD_NOALLOC_MAX_N, that every
+ * GPU which loads the library holds until the process exits (about 200 KB).
+ * The caller passes inputs and outputs as DEVICE pointers with the meanings of
+ * hsvd_solve; sort != 0 selects diagonal sorting (Sec. 4).  The call launches
+ * on `stream`, then waits for it to read the status; it calls no cudaMalloc,
+ * cudaFree or other allocating routine.  Sizes beyond the limit, or a factor
+ * whose G does not fit one SM's shared memory (m x n FP64 up to about 200 KB),
+ * return HSVD_ERR_ARG.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current: make that first call
+ * before any stream capture.  Every call on a device shares the one array, so
+ * calls that overlap on the GPU (other streams, other host threads) race: issue
+ * them one after the other.  Nothing has to be cleared between calls.
+ */
+#define HSVD_NOALLOC_MAX_N 160
+int hsvd_solve_pointwise_noalloc(const double *G, int64_t m, int64_t n, int64_t ldg, const int8_t *J,
+                                 double tol, int max_sweeps, int sort, double *sigma, double *U,
+                                 int64_t ldu, double *V, int64_t ldv, int *sweeps, void *stream);
+
 #ifdef __cplusplus
 }
 #endif
