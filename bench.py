@@ -2,12 +2,13 @@
 """Benchmark of the one-sided Jacobi hyperbolic SVD on GB300.
 
 One step = one complete HSVD (all sweeps until the Eq. 2.3 test passes for
-every pair, then the finalisation) of the plain blocked FP64 method on the
-1024 x 1024 graded factor G = B diag(10^(-6 i/n)), B i.i.d. N(0,1) (seed 2),
-J = diag(+1 x 512, -1 x 512), block width 32, tol = n 2^-53, inputs already
-in HBM.  The metric is effective TFLOP/s = S * 2 n^2 (4m + 2n) / time, S the
-sweeps of this plain run (the same flop count for every form), and the time
-per HSVD.
+every pair, then the finalisation), inputs already in HBM.  Default: the
+plain blocked FP64 method on the 1024 x 1024 graded factor
+G = B diag(10^(-6 i/n)), B i.i.d. N(0,1) (seed 2), J = diag(+1 x 512, -1 x 512),
+block width 32, tol = n 2^-53.  ``--workload haar4096 --form bf16x8`` measures
+the split-precision form on the 4096 Haar factor.  The metric is effective
+TFLOP/s = S * 2 n^2 (4m + 2n) / time, S the sweeps of the run (the same flop
+count for every form), and the time per HSVD.
 
 ``--impl reference`` times the CPU oracle (plain row-cyclic FP64 C code) on
 the host cores instead: each step is one sweep of the oracle on the same G.
@@ -28,15 +29,25 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-N = 1024
-M = 1024
-BLOCK = 32
-DECADES = 6.0
-SEED = 2
-TOL = N * 2.0 ** -53
-MAX_SWEEPS = 30
+MAX_SWEEPS = 40
 GOLDEN = os.path.join(ROOT, "tests", "golden", "graded1024_sigma.txt")
-WORKLOAD = "graded 1024x1024 G=B diag(10^(-6i/n)), J=diag(+1x512,-1x512), plain blocked FP64, b=32"
+
+# name -> (n, generator description, default block width); the default is the
+# measured configuration (graded 1024, plain FP64, b = 32)
+WORKLOADS = {
+    "graded1024": (1024, "graded 1024x1024 G=B diag(10^(-6i/n)), J=diag(+1x512,-1x512)", 32),
+    "haar4096": (4096, "4096x4096 G=Q1 diag(sigma) Q2, Haar Q, sigma log-uniform [1e-6,1], 2048 random +1 in J", 64),
+    "haar1024": (1024, "1024x1024 G=Q1 diag(sigma) Q2, Haar Q, sigma log-uniform [1e-6,1], 512 random +1 in J", 64),
+}
+
+
+def make_input(name, seed_offset=0):
+    from paper_1008_1371_gb300 import workloads
+
+    n = WORKLOADS[name][0]
+    if name.startswith("graded"):
+        return workloads.graded(n, decades=6.0, seed=2 + seed_offset)
+    return workloads.haar(n, seed=3 + seed_offset)
 
 
 def flops_per_sweep(m, n):
@@ -52,6 +63,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-sweeps", type=int, default=2, help="oracle sweeps timed for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="graded1024", choices=sorted(WORKLOADS))
+    ap.add_argument("--form", default="fp64", choices=["fp64", "bf16x8"],
+                    help="Gram/update arithmetic: FP64 FMA or BF16 slices on the tensor cores")
+    ap.add_argument("--block", type=int, default=0, help="block width (0: the workload's)")
     return ap.parse_args()
 
 
@@ -145,46 +161,52 @@ def accuracy_vs_golden(G, J, sigma):
             "values_with_floor_above_1e-12": n_loose}
 
 
-def cpu_baseline(G, J, sweeps):
+def cpu_baseline(G, J, tol, sweeps):
     """The oracle as it stands, single-threaded on a host core: `sweeps`
     sweeps of the row-cyclic method on the same factor."""
     import oracle
 
     oracle.build()
+    m, n = G.shape
     t0 = time.perf_counter()
-    r = oracle.hsvd(G, J, TOL, sweeps, want_u=False, want_v=False)
+    r = oracle.hsvd(G, J, tol, sweeps, want_u=False, want_v=False)
     dt = time.perf_counter() - t0
     per_sweep = dt / max(r["sweeps"], 1)
-    return {"value": flops_per_sweep(M, N) / per_sweep / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+    return {"value": flops_per_sweep(m, n) / per_sweep / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
             "sample": "%d sweep(s) of the row-cyclic FP64 oracle on the same %dx%d factor, %.2f s per sweep; "
-                      "effective rate per sweep with the blocked flop count 2n^2(4m+2n)" % (r["sweeps"], M, N,
+                      "effective rate per sweep with the blocked flop count 2n^2(4m+2n)" % (r["sweeps"], m, n,
                                                                                             per_sweep)}
+
+
+def metric_name(form):
+    return ("HSVD effective TFLOP/s (%s, sigma rel-err <= 1e-12)"
+            % ("plain FP64" if form == "fp64" else "split-precision BF16x8 products"))
 
 
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
         return 0
-    from paper_1008_1371_gb300 import workloads
-
-    G, J = workloads.graded(N, decades=DECADES, seed=SEED)
     import oracle
 
     oracle.build()
+    G, J = make_input(args.workload)
+    m, n = G.shape
+    tol = n * 2.0 ** -53
     times = []
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        r = oracle.hsvd(G, J, TOL, 1, want_u=False, want_v=False)
+        r = oracle.hsvd(G, J, tol, 1, want_u=False, want_v=False)
         dt = time.perf_counter() - t0
         if i >= args.warmup:
             times.append(dt)
     per = sum(times) / len(times)
-    value = flops_per_sweep(M, N) / per / 1e12
+    value = flops_per_sweep(m, n) / per / 1e12
     line = {
-        "impl": "reference", "metric": "HSVD effective TFLOP/s (plain FP64, sigma rel-err <= 1e-12)",
+        "impl": "reference", "metric": metric_name(args.form),
         "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "m": M, "n": N, "block_w": BLOCK,
+        "data": "synthetic", "config": {"workload": WORKLOADS[args.workload][1], "m": m, "n": n,
                                         "sample": "one sweep of the CPU oracle per step"},
         "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
                          "sample": "one sweep of the row-cyclic FP64 oracle per step on the same factor"},
@@ -208,20 +230,27 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    from paper_1008_1371_gb300 import api, build_lib, workloads
+    from paper_1008_1371_gb300 import api, build_lib
 
     if local == 0:
         build_lib.build()
     if world > 1:
         dist.barrier()
-    G_np, J_np = workloads.graded(N, decades=DECADES, seed=SEED + rank)
+    n, wdesc, wblock = WORKLOADS[args.workload]
+    block = args.block or wblock
+    prec = api.HSVD_PRECISION_BF16X8 if args.form == "bf16x8" else api.HSVD_PRECISION_FP64
+    if prec == api.HSVD_PRECISION_BF16X8:
+        block = 64
+    G_np, J_np = make_input(args.workload, seed_offset=rank)
+    m = G_np.shape[0]
+    tol = n * 2.0 ** -53
     G = torch.from_numpy(G_np).to(dev).t().contiguous().t()
     J = torch.from_numpy(J_np).to(dev)
-    sigma = torch.empty(N, dtype=torch.float64, device=dev)
-    U = torch.empty((N, M), dtype=torch.float64, device=dev).t()
-    V = torch.empty((N, N), dtype=torch.float64, device=dev).t()
-    opts = api.make_opts(tol=TOL, max_sweeps=MAX_SWEEPS, method=api.HSVD_METHOD_BLOCKED, block_w=BLOCK,
-                         profile=True)
+    sigma = torch.empty(n, dtype=torch.float64, device=dev)
+    U = torch.empty((n, m), dtype=torch.float64, device=dev).t()
+    V = torch.empty((n, n), dtype=torch.float64, device=dev).t()
+    opts = api.make_opts(tol=tol, max_sweeps=MAX_SWEEPS, method=api.HSVD_METHOD_BLOCKED, block_w=block,
+                         profile=True, precision=prec)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
     stream = torch.cuda.current_stream(dev)
 
@@ -257,68 +286,83 @@ def main():
     info = infos[-1]
     assert info.status == api.HSVD_OK, api.hsvd_status_string(info.status)
     sweeps = info.sweeps
-    eff_flops = sweeps * flops_per_sweep(M, N)
+    eff_flops = sweeps * flops_per_sweep(m, n)
     value = world * eff_flops / (ms * 1e-3) / 1e12
 
     # dominant kernel class by CUDA-event time over the timed steps
     tot = {k: sum(getattr(i, "ms_" + k) for i in infos) for k in ("gram", "solve", "update", "other")}
     upd_pairs = sum(i.pair_updates for i in infos)
-    nb = N // BLOCK
+    nb = -(-n // (2 * block)) * 2
     visits = sum(i.sweeps for i in infos) * nb * (nb // 2)
     alg = {
-        "update": upd_pairs * 2.0 * (M + N) * (2 * BLOCK) ** 2,
-        "gram": visits * 6.0 * M * BLOCK * BLOCK,
+        "update": upd_pairs * 2.0 * (m + n) * (2 * block) ** 2,
+        "gram": visits * (6.0 if prec == api.HSVD_PRECISION_FP64 else 8.0) * m * block * block,
     }
     dom = max(("gram", "update", "solve"), key=lambda k: tot[k])
     fp64_peak = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk x flop x max clock
-    if dom in alg:
-        achieved = alg[dom] / (tot[dom] * 1e-3) / 1e12
+    achieved = alg[dom] / (tot[dom] * 1e-3) / 1e12 if dom in alg else None
+    kname = {"gram": "k_gram<%d>" % block, "update": "k_update<%d>" % (2 * block),
+             "solve": "k_solve_cluster<%d,8>" % (2 * block)}
+    if prec == api.HSVD_PRECISION_BF16X8:
+        kname = {"gram": "k_gram_x", "update": "k_update_x", "solve": "k_solve_cluster<128,8>"}
+    if prec == api.HSVD_PRECISION_FP64:
+        roofline = {"kernel": kname[dom], "bound": "alu", "achieved": achieved, "peak": fp64_peak,
+                    "unit": "TFLOP/s", "frac": (achieved / fp64_peak) if achieved else None, "traffic": None,
+                    "peak_source": "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (derived from units and clock)"}
     else:
-        achieved = None
-    roofline = {"kernel": {"gram": "k_gram<32>", "update": "k_update<64>", "solve": "k_solve<64>"}[dom],
-                "bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": (achieved / fp64_peak) if achieved else None, "traffic": None,
-                "peak_source": "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (derived)",
-                "ms_by_kernel": {k: v / len(infos) for k, v in tot.items()},
-                "alg_tflops_by_kernel": {k: alg[k] / (tot[k] * 1e-3) / 1e12 for k in alg if tot[k] > 0}}
+        # the tensor work of a split product: 36 BF16 slice products per FP64 product
+        bf16_peak = 1934.1
+        ach_t = 36.0 * achieved if achieved else None
+        roofline = {"kernel": kname[dom], "bound": "tensor", "achieved": ach_t, "peak": bf16_peak,
+                    "unit": "TFLOP/s", "frac": (ach_t / bf16_peak) if ach_t else None, "traffic": None,
+                    "peak_source": "bf16 dense, measured (MEASURED_PEAKS.json, burst)",
+                    "fp64_equivalent_tflops": achieved}
+    roofline["ms_by_kernel"] = {k: v / len(infos) for k, v in tot.items()}
+    roofline["alg_fp64_tflops_by_kernel"] = {k: alg[k] / (tot[k] * 1e-3) / 1e12 for k in alg if tot[k] > 0}
 
     # accuracy against the stored oracle values (written by tests/golden/make_golden.py
     # on a machine whose G has the same bytes as this one's)
-    accuracy = accuracy_vs_golden(G_np, J_np, sigma.cpu().numpy()) if rank == 0 else None
+    accuracy = None
+    if rank == 0 and args.workload == "graded1024":
+        accuracy = accuracy_vs_golden(G_np, J_np, sigma.cpu().numpy())
 
     # end to end through the C ABI with pinned host arrays, copies inside the timed region
-    Gh = torch.from_numpy(G_np).t().contiguous().t().pin_memory()
-    Jh = torch.from_numpy(J_np).pin_memory()
-    sh = torch.empty(N, dtype=torch.float64).pin_memory()
-    Uh = torch.empty((N, M), dtype=torch.float64).pin_memory().t()
-    Vh = torch.empty((N, N), dtype=torch.float64).pin_memory().t()
-    opts_e2e = api.make_opts(tol=TOL, max_sweeps=MAX_SWEEPS, method=api.HSVD_METHOD_BLOCKED, block_w=BLOCK)
-    api.hsvd_solve_ex(Gh, Jh, opts_e2e, out=(sh, Uh, Vh))
-    e2e_t = []
-    for _ in range(max(3, args.steps // 2)):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
+    e2e = None
+    if not args.no_e2e:
+        Gh = torch.from_numpy(G_np).t().contiguous().t().pin_memory()
+        Jh = torch.from_numpy(J_np).pin_memory()
+        sh = torch.empty(n, dtype=torch.float64).pin_memory()
+        Uh = torch.empty((n, m), dtype=torch.float64).pin_memory().t()
+        Vh = torch.empty((n, n), dtype=torch.float64).pin_memory().t()
+        opts_e2e = api.make_opts(tol=tol, max_sweeps=MAX_SWEEPS, method=api.HSVD_METHOD_BLOCKED, block_w=block,
+                                 precision=prec)
         api.hsvd_solve_ex(Gh, Jh, opts_e2e, out=(sh, Uh, Vh))
-        e2e_t.append(time.perf_counter() - t0)
-    e2e_s = sum(e2e_t) / len(e2e_t)
-    if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * eff_flops / e2e_s / 1e12, "unit": "TFLOP/s", "ms_per_step": e2e_s * 1e3,
-           "h2d_bytes_per_step": M * N * 8 + N, "d2h_bytes_per_step": N * 8 + M * N * 8 + N * N * 8}
+        e2e_t = []
+        for _ in range(max(3, args.steps // 2)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            api.hsvd_solve_ex(Gh, Jh, opts_e2e, out=(sh, Uh, Vh))
+            e2e_t.append(time.perf_counter() - t0)
+        e2e_s = sum(e2e_t) / len(e2e_t)
+        if world > 1:
+            t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": world * eff_flops / e2e_s / 1e12, "unit": "TFLOP/s", "ms_per_step": e2e_s * 1e3,
+               "h2d_bytes_per_step": m * n * 8 + n, "d2h_bytes_per_step": n * 8 + m * n * 8 + n * n * 8}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(G_np, J_np, args.cpu_sweeps)
+        cpu = cpu_baseline(G_np, J_np, tol, args.cpu_sweeps)
 
     if rank == 0:
         line = {
-            "metric": "HSVD effective TFLOP/s (plain FP64, sigma rel-err <= 1e-12)", "value": value,
+            "metric": metric_name(args.form), "value": value,
             "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "m": M, "n": N, "block_w": BLOCK, "tol": TOL, "sweeps": sweeps,
-                       "inner": "block-oriented", "sort": False, "l2": "flushed (256 MB write) between steps",
+            "config": {"workload": wdesc + ", blocked, b=%d, %s" % (block, args.form), "m": m, "n": n,
+                       "block_w": block, "form": args.form, "tol": tol, "sweeps": sweeps, "inner": "block-oriented",
+                       "sort": False, "l2": "flushed (256 MB write) between steps",
                        "parallelism": "replicas" if world > 1 else "single"},
             "accuracy": accuracy,
             "gpu_launches": int(sum(i.kernel_launches for i in infos)),

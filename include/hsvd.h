@@ -65,6 +65,15 @@ extern "C" {
 
 #define HSVD_SORT_AUTO (-1)
 
+/* Arithmetic of the blocked method's Gram and update products. */
+#define HSVD_PRECISION_FP64 0   /* FP64 FMA                                             */
+#define HSVD_PRECISION_BF16X8 1 /* split precision: each FP64 operand as 8 BF16 slices
+                                   (balanced 7-bit digits), the 36 leading slice
+                                   products on the tensor cores with exact FP32
+                                   accumulation, recombined exactly into FP64; rotation
+                                   angles, the test of Eq. 2.3 and the norms stay FP64.
+                                   Requires block_w = 64 (0 selects it).             */
+
 typedef struct hsvd_opts {
     double tol;           /* relative orthogonality threshold of Eq. 2.3;
                              <= 0 selects n * 2^-53                                   */
@@ -78,7 +87,8 @@ typedef struct hsvd_opts {
                              increasing; 0: no sorting; HSVD_SORT_AUTO: sorting for the
                              pointwise method only                                     */
     int profile;          /* nonzero: time every kernel with CUDA events (hsvd_info)   */
-    int reserved[7];      /* must be zero                                              */
+    int precision;        /* HSVD_PRECISION_FP64 or HSVD_PRECISION_BF16X8              */
+    int reserved[6];      /* must be zero                                              */
 } hsvd_opts;
 
 typedef struct hsvd_info {
@@ -169,6 +179,19 @@ int hsvd_pivot_solve(int b, int npairs, double *A, const int8_t *sgn, double tol
  */
 int hsvd_pivot_update(double *X, int64_t rows, int64_t ldx, int b, int npairs, const int *col0,
                       const double *W, const int *rotated, void *stream);
+
+/*
+ * Split-precision kernel-level entry points (HSVD_PRECISION_BF16X8, b = 64),
+ * the counterparts of hsvd_pivot_gram and hsvd_pivot_update: same operands,
+ * device pointers, stream-ordered, the caller owns the outputs.  They allocate
+ * their scratch (partials, slices) stream-ordered and free it before return.
+ * hsvd_pivot_update_x: dexp (npairs x 128 ints, device, may be NULL for none)
+ * are the balancing exponents d_k of X W = (X 2^-d)(2^d W).
+ */
+int hsvd_pivot_gram_x(const double *G, int64_t rows, int64_t ldg, int npairs, const int *col0, double *A,
+                      void *stream);
+int hsvd_pivot_update_x(double *X, int64_t rows, int64_t ldx, int npairs, const int *col0, const double *W,
+                        const int *rotated, const int *dexp, void *stream);
 
 /*
  * hsvd_solve_pointwise_noalloc -- the pointwise solver (HSVD_METHOD_POINTWISE)

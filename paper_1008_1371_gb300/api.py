@@ -29,6 +29,8 @@ HSVD_METHOD_POINTWISE = 1
 HSVD_METHOD_BLOCKED = 2
 HSVD_INNER_ORIENTED = 0
 HSVD_INNER_FULL = 1
+HSVD_PRECISION_FP64 = 0
+HSVD_PRECISION_BF16X8 = 1
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libhsvd.so")
@@ -44,7 +46,7 @@ _dbl = ctypes.c_double
 class HsvdOpts(ctypes.Structure):
     _fields_ = [("tol", _dbl), ("max_sweeps", _int), ("method", _int), ("block_w", _int),
                 ("inner_mode", _int), ("inner_max_passes", _int), ("sort", _int), ("profile", _int),
-                ("reserved", _int * 7)]
+                ("precision", _int), ("reserved", _int * 6)]
 
 
 class HsvdInfo(ctypes.Structure):
@@ -85,6 +87,10 @@ def lib():
             L.hsvd_pivot_solve.restype = _int
             L.hsvd_pivot_update.argtypes = [_p, _i64, _i64, _int, _int, _p, _p, _p, _p]
             L.hsvd_pivot_update.restype = _int
+            L.hsvd_pivot_gram_x.argtypes = [_p, _i64, _i64, _int, _p, _p, _p]
+            L.hsvd_pivot_gram_x.restype = _int
+            L.hsvd_pivot_update_x.argtypes = [_p, _i64, _i64, _int, _p, _p, _p, _p, _p]
+            L.hsvd_pivot_update_x.restype = _int
             _lib = L
     return _lib
 
@@ -137,7 +143,7 @@ HSVD_SORT_AUTO = -1
 
 
 def make_opts(tol=0.0, max_sweeps=30, method=HSVD_METHOD_AUTO, block_w=0, inner_mode=HSVD_INNER_ORIENTED,
-              inner_max_passes=8, sort=None, profile=False):
+              inner_max_passes=8, sort=None, profile=False, precision=HSVD_PRECISION_FP64):
     """Options record; ``sort=None`` lets the library choose (sorting for the
     pointwise method only)."""
     o = HsvdOpts()
@@ -150,6 +156,7 @@ def make_opts(tol=0.0, max_sweeps=30, method=HSVD_METHOD_AUTO, block_w=0, inner_
     o.inner_max_passes = int(inner_max_passes)
     o.sort = HSVD_SORT_AUTO if sort is None else (1 if sort else 0)
     o.profile = 1 if profile else 0
+    o.precision = int(precision)
     return o
 
 
@@ -251,6 +258,37 @@ def hsvd_pivot_update(X, b, col0, W, rotated, stream=None):
     r = rotated.to(torch.int32).contiguous()
     st = L.hsvd_pivot_update(X.data_ptr(), rows, X.stride(1), int(b), c0.shape[0], c0.data_ptr(), Wb.data_ptr(),
                              r.data_ptr(), _stream_ptr(stream, X.device))
+    if st != HSVD_OK:
+        raise HsvdError(st)
+    return X
+
+
+def hsvd_pivot_gram_x(G, col0, stream=None):
+    """Split-precision A_P blocks (npairs, 128, 128) of the block pairs (b = 64)."""
+    L = lib()
+    Gc = _colmajor(G, torch.float64)
+    rows = Gc.shape[0]
+    c0 = col0.to(torch.int32).contiguous()
+    npairs = c0.shape[0]
+    A = torch.empty((npairs, 128, 128), dtype=torch.float64, device=Gc.device)
+    st = L.hsvd_pivot_gram_x(Gc.data_ptr(), rows, Gc.stride(1), npairs, c0.data_ptr(), A.data_ptr(),
+                             _stream_ptr(stream, Gc.device))
+    if st != HSVD_OK:
+        raise HsvdError(st)
+    return A.transpose(1, 2)
+
+
+def hsvd_pivot_update_x(X, col0, W, rotated, dexp=None, stream=None):
+    """In place, split precision: X[:, I|J] <- X[:, I|J] W_k (b = 64)."""
+    L = lib()
+    if not (X.stride(0) == 1):
+        raise ValueError("X must be column-major")
+    c0 = col0.to(torch.int32).contiguous()
+    Wb = W.transpose(1, 2).contiguous()
+    r = rotated.to(torch.int32).contiguous()
+    d = dexp.to(torch.int32).contiguous() if dexp is not None else None
+    st = L.hsvd_pivot_update_x(X.data_ptr(), X.shape[0], X.stride(1), c0.shape[0], c0.data_ptr(), Wb.data_ptr(),
+                               r.data_ptr(), d.data_ptr() if d is not None else None, _stream_ptr(stream, X.device))
     if st != HSVD_OK:
         raise HsvdError(st)
     return X

@@ -148,6 +148,14 @@ int solve_blocked_core(const double *G, int64_t m, int64_t n, int64_t ldg, const
     if (!Gw || !Gt || !Ww || !Wt || !perm || !perm_t || !newpos || !sgn || !sgn_t || !d || !part || !Wp ||
         !rotated || !cnt || !d_tab_outer || !d_tab_full || !d_tab_cross)
         return HSVD_ERR_NOMEM;
+    // split-precision products: full 2b x 2b Gram partials, W' slices, exponents
+    const bool prec = o.precision == HSVD_PRECISION_BF16X8;
+    const int ksplit_x = prec ? precision_gram_ksplit(m_pad) : 0;
+    double *part_x = prec ? ws.get<double>((size_t)npairs * ksplit_x * nn * nn) : nullptr;
+    uint16_t *wsl = prec ? ws.get<uint16_t>(precision_wsl_elems(npairs)) : nullptr;
+    int *wexp = prec ? ws.get<int>((size_t)npairs * 2 * nn) : nullptr;
+    int *dexp = prec ? ws.get<int>((size_t)npairs * nn) : nullptr;
+    if (prec && (!part_x || !wsl || !wexp || !dexp)) return HSVD_ERR_NOMEM;
     unsigned long long *rot_ctr = reinterpret_cast<unsigned long long *>(cnt + 2);
     unsigned long long *upd_ctr = reinterpret_cast<unsigned long long *>(cnt + 4);
     {
@@ -185,14 +193,22 @@ int solve_blocked_core(const double *G, int64_t m, int64_t n, int64_t ldg, const
             const int *col0 = d_tab_outer + (size_t)s * npairs * 2;
             const int mode = (o.inner_mode == HSVD_INNER_FULL) ? 0 : (s == 0 ? 2 : 1);
             e = evs.record(4 * s, st);
-            if (e == cudaSuccess) e = launch_gram(Gw, m_pad, m_pad, b, npairs, col0, nsplit, part, st);
+            if (e == cudaSuccess)
+                e = prec ? launch_gram_x(Gw, m_pad, m_pad, npairs, col0, part_x, cnt, st)
+                         : launch_gram(Gw, m_pad, m_pad, b, npairs, col0, nsplit, part, st);
             if (e == cudaSuccess) e = evs.record(4 * s + 1, st);
             if (e == cudaSuccess)
-                e = launch_solve(b, npairs, part, nsplit, nullptr, sgn, col0, nullptr, tol, mode,
-                                 o.inner_max_passes, d_tab_full, d_tab_cross, Wp, rotated, rot_ctr, cnt, st);
+                e = prec ? launch_solve(b, npairs, part_x, ksplit_x, nullptr, sgn, col0, nullptr, tol, mode,
+                                        o.inner_max_passes, d_tab_full, d_tab_cross, Wp, rotated, rot_ctr, cnt, st,
+                                        1, dexp)
+                         : launch_solve(b, npairs, part, nsplit, nullptr, sgn, col0, nullptr, tol, mode,
+                                        o.inner_max_passes, d_tab_full, d_tab_cross, Wp, rotated, rot_ctr, cnt, st);
             if (e == cudaSuccess) e = evs.record(4 * s + 2, st);
+            if (e == cudaSuccess && prec) e = launch_wprep_x(npairs, Wp, dexp, rotated, wsl, wexp, upd_ctr, st);
             if (e == cudaSuccess)
-                e = launch_update(Gw, m_pad, m_pad, Ww, ldw, ldw, b, npairs, col0, Wp, rotated, upd_ctr, st);
+                e = prec ? launch_update_x(Gw, m_pad, m_pad, Ww, ldw, ldw, npairs, col0, wsl, wexp, dexp, rotated,
+                                           cnt, st)
+                         : launch_update(Gw, m_pad, m_pad, Ww, ldw, ldw, b, npairs, col0, Wp, rotated, upd_ctr, st);
             if (e == cudaSuccess) e = evs.record(4 * s + 3, st);
         }
         if (e == cudaSuccess) e = evs.record(evr, st);
@@ -214,7 +230,7 @@ int solve_blocked_core(const double *G, int64_t m, int64_t n, int64_t ldg, const
         stats.rotations += (long long)rots;
         stats.pair_updates += (long long)upds;
         stats.sweeps = sweep;
-        stats.launches += 3LL * nb + reorder_kernels;
+        stats.launches += (prec ? 4LL : 3LL) * nb + reorder_kernels;
         if (o.profile) {
             for (int s = 0; s < nb; ++s) {
                 stats.ms_gram += evs.between(4 * s, 4 * s + 1);
@@ -342,7 +358,7 @@ int hsvd_solve_ex(const double *G, int64_t m, int64_t n, int64_t ldg, const int8
     if (info) memset(info, 0, sizeof *info);
     int rc = validate(G, m, n, ldg, J, sigma, ldu, U, ldv, V);
     if (rc == HSVD_OK) {
-        for (int i = 0; i < 7; ++i)
+        for (int i = 0; i < 6; ++i)
             if (o.reserved[i]) rc = HSVD_ERR_ARG;
         if (o.max_sweeps <= 0) o.max_sweeps = 30;
         if (o.inner_max_passes <= 0) o.inner_max_passes = 8;
@@ -350,6 +366,10 @@ int hsvd_solve_ex(const double *G, int64_t m, int64_t n, int64_t ldg, const int8
         if (o.block_w != 0 && o.block_w != 16 && o.block_w != 32 && o.block_w != 64) rc = HSVD_ERR_ARG;
         if (o.inner_mode != HSVD_INNER_ORIENTED && o.inner_mode != HSVD_INNER_FULL) rc = HSVD_ERR_ARG;
         if (o.sort != 0 && o.sort != 1 && o.sort != HSVD_SORT_AUTO) rc = HSVD_ERR_ARG;
+        if (o.precision != HSVD_PRECISION_FP64 && o.precision != HSVD_PRECISION_BF16X8) rc = HSVD_ERR_ARG;
+        if (o.precision == HSVD_PRECISION_BF16X8 &&
+            (o.method == HSVD_METHOD_POINTWISE || (o.block_w != 0 && o.block_w != 64)))
+            rc = HSVD_ERR_ARG;
         if (!(o.tol == o.tol)) rc = HSVD_ERR_ARG;
     }
     if (rc != HSVD_OK) {
@@ -369,7 +389,9 @@ int hsvd_solve_ex(const double *G, int64_t m, int64_t n, int64_t ldg, const int8
             return HSVD_ERR_ARG;
         }
     int method = o.method;
-    if (method == HSVD_METHOD_AUTO) method = pointwise_fits(m, n) ? HSVD_METHOD_POINTWISE : HSVD_METHOD_BLOCKED;
+    if (method == HSVD_METHOD_AUTO)
+        method = (pointwise_fits(m, n) && o.precision == HSVD_PRECISION_FP64) ? HSVD_METHOD_POINTWISE
+                                                                              : HSVD_METHOD_BLOCKED;
     // diagonal sorting pays for the pointwise method (Sec. 5, Table 5.3) but
     // costs sweeps in the blocked one (measured on the graded 1024 factor)
     if (o.sort == HSVD_SORT_AUTO) o.sort = (method == HSVD_METHOD_POINTWISE) ? 1 : 0;
@@ -377,7 +399,7 @@ int hsvd_solve_ex(const double *G, int64_t m, int64_t n, int64_t ldg, const int8
         if (info) info->status = HSVD_ERR_ARG;
         return HSVD_ERR_ARG;
     }
-    const int b = o.block_w ? o.block_w : choose_block(n);
+    const int b = o.block_w ? o.block_w : (o.precision == HSVD_PRECISION_BF16X8 ? 64 : choose_block(n));
     double *dG = nullptr, *dS = nullptr, *dU = nullptr, *dV = nullptr;
     int8_t *dJ = nullptr;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
@@ -503,6 +525,65 @@ int hsvd_pivot_update(double *X, int64_t rows, int64_t ldx, int b, int npairs, c
     return launch_update(X, rows, ldx, nullptr, 0, 0, b, npairs, col0, W, rotated, nullptr, st) == cudaSuccess
                ? HSVD_OK
                : HSVD_ERR_CUDA;
+}
+
+int hsvd_pivot_gram_x(const double *G, int64_t rows, int64_t ldg, int npairs, const int *col0, double *A,
+                      void *stream) {
+    if (!G || !col0 || !A || npairs < 1 || rows < 1 || (rows % 64) || ldg < rows) return HSVD_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int ks = precision_gram_ksplit(rows);
+    double *part = nullptr;
+    int *status = nullptr;
+    if (cudaMallocAsync((void **)&part, sizeof(double) * (size_t)npairs * ks * 128 * 128, st) != cudaSuccess)
+        return HSVD_ERR_NOMEM;
+    if (cudaMallocAsync((void **)&status, sizeof(int), st) != cudaSuccess) {
+        cudaFreeAsync(part, st);
+        return HSVD_ERR_NOMEM;
+    }
+    int rc = HSVD_OK, h = 0;
+    if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess ||
+        launch_gram_x(G, rows, ldg, npairs, col0, part, status, st) != cudaSuccess ||
+        launch_assemble_x(npairs, part, ks, A, st) != cudaSuccess ||
+        cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        rc = HSVD_ERR_CUDA;
+    if (rc == HSVD_OK && h) rc = h;
+    cudaFreeAsync(part, st);
+    cudaFreeAsync(status, st);
+    return rc;
+}
+
+int hsvd_pivot_update_x(double *X, int64_t rows, int64_t ldx, int npairs, const int *col0, const double *W,
+                        const int *rotated, const int *dexp, void *stream) {
+    if (!X || !col0 || !W || !rotated || npairs < 1 || rows < 1 || ldx < rows) return HSVD_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint16_t *wsl = nullptr;
+    int *wexp = nullptr, *dz = nullptr, *status = nullptr;
+    int rc = HSVD_OK, h = 0;
+    if (cudaMallocAsync((void **)&wsl, sizeof(uint16_t) * precision_wsl_elems(npairs), st) != cudaSuccess ||
+        cudaMallocAsync((void **)&wexp, sizeof(int) * (size_t)npairs * 256, st) != cudaSuccess ||
+        cudaMallocAsync((void **)&dz, sizeof(int) * (size_t)npairs * 128, st) != cudaSuccess ||
+        cudaMallocAsync((void **)&status, sizeof(int), st) != cudaSuccess)
+        rc = HSVD_ERR_NOMEM;
+    if (rc == HSVD_OK) {
+        const int *dk = dexp;
+        if (!dk && cudaMemsetAsync(dz, 0, sizeof(int) * (size_t)npairs * 128, st) != cudaSuccess) rc = HSVD_ERR_CUDA;
+        if (!dk) dk = dz;
+        if (rc == HSVD_OK &&
+            (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess ||
+             launch_wprep_x(npairs, W, dk, rotated, wsl, wexp, nullptr, st) != cudaSuccess ||
+             launch_update_x(X, rows, ldx, nullptr, 0, 0, npairs, col0, wsl, wexp, dk, rotated, status, st) !=
+                 cudaSuccess ||
+             cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+             cudaStreamSynchronize(st) != cudaSuccess))
+            rc = HSVD_ERR_CUDA;
+        if (rc == HSVD_OK && h) rc = h;
+    }
+    if (wsl) cudaFreeAsync(wsl, st);
+    if (wexp) cudaFreeAsync(wexp, st);
+    if (dz) cudaFreeAsync(dz, st);
+    if (status) cudaFreeAsync(status, st);
+    return rc;
 }
 
 }  // extern "C"

@@ -132,11 +132,24 @@ cudaError_t launch_solve(int b, int npairs, const double *part, int nsplit, doub
                          const int8_t *sgn_cols, const int *col0, const int8_t *sgn_direct,
                          double tol, int mode, int max_passes, const int *tab_full,
                          const int *tab_cross, double *Wp, int *rotated,
-                         unsigned long long *rot_count, int *status, cudaStream_t st);
+                         unsigned long long *rot_count, int *status, cudaStream_t st,
+                         int full_part = 0, int *dexp = nullptr);
 cudaError_t launch_assemble(int b, int npairs, const double *part, int nsplit, double *A, cudaStream_t st);
 cudaError_t launch_update(double *X, int64_t rows, int64_t ldx, double *Y, int64_t rowsY,
                           int64_t ldy, int b, int npairs, const int *col0, const double *Wp,
                           const int *rotated, unsigned long long *upd_count, cudaStream_t st);
+
+// precision.cu: split-precision (BF16 slices on tcgen05) Gram and update, b = 64.
+size_t precision_wsl_elems(int npairs);
+int precision_gram_ksplit(int64_t rows);
+cudaError_t launch_gram_x(const double *G, int64_t rows, int64_t ldg, int npairs, const int *col0, double *part,
+                          int *status, cudaStream_t st);
+cudaError_t launch_assemble_x(int npairs, const double *part, int ksplit, double *A, cudaStream_t st);
+cudaError_t launch_wprep_x(int npairs, const double *Wp, const int *dexp, const int *rotated, uint16_t *wsl,
+                           int *wexp, unsigned long long *upd_count, cudaStream_t st);
+cudaError_t launch_update_x(double *X, int64_t rowsX, int64_t ldx, double *Y, int64_t rowsY, int64_t ldy,
+                            int npairs, const int *col0, const uint16_t *wsl, const int *wexp, const int *dexp,
+                            const int *rotated, int *status, cudaStream_t st);
 
 // prep.cu: bordering, reordering, finalisation.
 cudaError_t launch_load_pad(const double *G, int64_t ldg, int64_t m, int64_t n, const int8_t *J,

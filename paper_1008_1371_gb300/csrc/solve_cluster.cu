@@ -40,12 +40,12 @@ struct ClusterOf {
 
 template <int NN, int C>
 __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kClThreads)
-k_solve_cluster(const double *__restrict__ part, int nsplit, double *__restrict__ A_io,
+k_solve_cluster(const double *__restrict__ part, int nsplit, int full_part, double *__restrict__ A_io,
                 const int8_t *__restrict__ sgn_cols, const int *__restrict__ col0,
                 const int8_t *__restrict__ sgn_direct, double tol, int mode, int max_passes,
                 const int *__restrict__ tab_full, const int *__restrict__ tab_cross,
                 double *__restrict__ Wout, int *__restrict__ rotated,
-                unsigned long long *__restrict__ rot_count, int *__restrict__ status) {
+                unsigned long long *__restrict__ rot_count, int *__restrict__ status, int *__restrict__ dexp) {
     constexpr int H = NN / 2, R = NN / C, LD = NN + 1, B = NN / 2;
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
@@ -63,19 +63,31 @@ k_solve_cluster(const double *__restrict__ part, int nsplit, double *__restrict_
     __shared__ double T[2][H], Cc[2][H], Apq[2][H];
     __shared__ int s_flag;
 
-    // initial state: own rows of A_P, the whole diagonal, W = I
+    // initial state: own rows of A_P, the whole diagonal, W = I.  A_P comes from
+    // the three-block partials of the FP64 Gram, from full 2b x 2b partials of
+    // the split-precision Gram (upper triangle, so A_P is exactly symmetric),
+    // or from A_io.
+    auto entry = [&](int x, int y) -> double {
+        if (!part) return A_io[(size_t)pair * NN * NN + x + y * NN];
+        if (!full_part) return assemble_entry<NN>(part, nsplit, pair, x + y * NN);
+        const int lo = x < y ? x : y, hi = x < y ? y : x;
+        const double *pp = part + (size_t)pair * nsplit * NN * NN + lo + (size_t)hi * NN;
+        double v = 0.0;
+        for (int s = 0; s < nsplit; ++s) v += pp[(size_t)s * NN * NN];
+        return v;
+    };
     if (tid == 0) s_flag = 0;
     for (int x = tid; x < NN; x += kClThreads) {
         if (sgn_direct) sg[x] = sgn_direct[(size_t)pair * NN + x];
         else sg[x] = sgn_cols[col0[2 * pair + (x >= B)] + (x % B)];
-        const int e = x + x * NN;
-        D[x] = part ? assemble_entry<NN>(part, nsplit, pair, e) : A_io[(size_t)pair * NN * NN + e];
+        D[x] = entry(x, x);
+        // column-norm exponents for the balancing of the split-precision update
+        if (dexp && rank == 0) dexp[(size_t)pair * NN + x] = D[x] > 0.0 ? (ilogb(D[x]) >> 1) : 0;
     }
     for (int e = tid; e < R * NN; e += kClThreads) {
         const int x = e / NN, y = e % NN;
         const int gx = row0 + x;
-        const int ea = gx + y * NN;  // A(gx, y), column-major
-        Sa[x * LD + y] = part ? assemble_entry<NN>(part, nsplit, pair, ea) : A_io[(size_t)pair * NN * NN + ea];
+        Sa[x * LD + y] = entry(gx, y);
         Wl[x * NN + y] = (gx == y) ? 1.0 : 0.0;
     }
     double *S = Sa, *Rv = Sb;
@@ -207,18 +219,19 @@ k_solve_cluster(const double *__restrict__ part, int nsplit, double *__restrict_
 }
 
 template <int NN>
-cudaError_t solve_cluster_impl(int npairs, const double *part, int nsplit, double *A, const int8_t *sgn_cols,
-                               const int *col0, const int8_t *sgn_direct, double tol, int mode, int max_passes,
-                               const int *tab_full, const int *tab_cross, double *Wp, int *rotated,
-                               unsigned long long *rot_count, int *status, cudaStream_t st) {
+cudaError_t solve_cluster_impl(int npairs, const double *part, int nsplit, int full_part, double *A,
+                               const int8_t *sgn_cols, const int *col0, const int8_t *sgn_direct, double tol,
+                               int mode, int max_passes, const int *tab_full, const int *tab_cross, double *Wp,
+                               int *rotated, unsigned long long *rot_count, int *status, int *dexp,
+                               cudaStream_t st) {
     constexpr int C = ClusterOf<NN>::C, R = NN / C;
     const size_t smem = (size_t)(2 * R * (NN + 1) + R * NN) * sizeof(double);
     cudaError_t e = cudaFuncSetAttribute(k_solve_cluster<NN, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    k_solve_cluster<NN, C><<<npairs * C, kClThreads, smem, st>>>(part, nsplit, A, sgn_cols, col0, sgn_direct, tol,
-                                                                 mode, max_passes, tab_full, tab_cross, Wp, rotated,
-                                                                 rot_count, status);
+    k_solve_cluster<NN, C><<<npairs * C, kClThreads, smem, st>>>(part, nsplit, full_part, A, sgn_cols, col0,
+                                                                 sgn_direct, tol, mode, max_passes, tab_full,
+                                                                 tab_cross, Wp, rotated, rot_count, status, dexp);
     return cudaGetLastError();
 }
 
@@ -227,14 +240,17 @@ cudaError_t solve_cluster_impl(int npairs, const double *part, int nsplit, doubl
 cudaError_t launch_solve(int b, int npairs, const double *part, int nsplit, double *A, const int8_t *sgn_cols,
                          const int *col0, const int8_t *sgn_direct, double tol, int mode, int max_passes,
                          const int *tab_full, const int *tab_cross, double *Wp, int *rotated,
-                         unsigned long long *rot_count, int *status, cudaStream_t st) {
+                         unsigned long long *rot_count, int *status, cudaStream_t st, int full_part, int *dexp) {
     switch (b) {
-        case 16: return solve_cluster_impl<32>(npairs, part, nsplit, A, sgn_cols, col0, sgn_direct, tol, mode,
-                                               max_passes, tab_full, tab_cross, Wp, rotated, rot_count, status, st);
-        case 32: return solve_cluster_impl<64>(npairs, part, nsplit, A, sgn_cols, col0, sgn_direct, tol, mode,
-                                               max_passes, tab_full, tab_cross, Wp, rotated, rot_count, status, st);
-        case 64: return solve_cluster_impl<128>(npairs, part, nsplit, A, sgn_cols, col0, sgn_direct, tol, mode,
-                                                max_passes, tab_full, tab_cross, Wp, rotated, rot_count, status, st);
+        case 16: return solve_cluster_impl<32>(npairs, part, nsplit, full_part, A, sgn_cols, col0, sgn_direct, tol,
+                                               mode, max_passes, tab_full, tab_cross, Wp, rotated, rot_count,
+                                               status, dexp, st);
+        case 32: return solve_cluster_impl<64>(npairs, part, nsplit, full_part, A, sgn_cols, col0, sgn_direct, tol,
+                                               mode, max_passes, tab_full, tab_cross, Wp, rotated, rot_count,
+                                               status, dexp, st);
+        case 64: return solve_cluster_impl<128>(npairs, part, nsplit, full_part, A, sgn_cols, col0, sgn_direct,
+                                                tol, mode, max_passes, tab_full, tab_cross, Wp, rotated, rot_count,
+                                                status, dexp, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -1,0 +1,144 @@
+"""The split-precision form (BF16 slices on the tensor cores): the Gram and
+update kernels against FP64 products with derived error bounds, and whole
+solves against the CPU oracle at the same sigma tolerance as the FP64 path.
+
+Error model of a split product (see csrc/precision.cu): every operand is cut
+to 56 bits relative to the scale 2^E of its row (or column), the 36 leading
+slice products are summed exactly and rounded once.  Per output element the
+error is below K * 2^-53 * 2^(E_row + E_col) plus one rounding, which is the
+size of an FP64 product's own error bound."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1008_1371_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+U64 = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_1008_1371_gb300 import api, build_lib
+
+    build_lib.build()
+    oracle.build()
+    assert torch.cuda.is_available()
+    return api
+
+
+def _scale(v):
+    """2^E with |v| < 2^E (elementwise max over the given axis already taken)."""
+    return np.exp2(np.floor(np.log2(np.maximum(v, 1e-300))) + 1)
+
+
+@pytest.mark.parametrize("rows", [640, 1024])
+def test_kernel_gram_x(api, rows):
+    rng = np.random.default_rng(rows)
+    ncols = 6 * 64
+    G = rng.standard_normal((rows, ncols)) * 10.0 ** rng.uniform(-4, 4, ncols)[None, :]
+    G[:, 5] = 0.0  # a zero column
+    col0 = np.array([[0, 320], [128, 192], [256, 64]], dtype=np.int32)
+    dev = torch.device("cuda:0")
+    A = api.hsvd_pivot_gram_x(torch.from_numpy(np.asfortranarray(G)).to(dev),
+                              torch.from_numpy(col0).to(dev)).cpu().numpy()
+    for k, (i0, j0) in enumerate(col0):
+        P = np.concatenate([G[:, i0:i0 + 64], G[:, j0:j0 + 64]], axis=1)
+        ref = P.T @ P
+        s = _scale(np.abs(P).max(axis=0))
+        bound = 2 * rows * U64 * np.outer(s, s) + 2 * rows * U64 * (np.abs(P).T @ np.abs(P))
+        assert np.all(np.abs(A[k] - ref) <= bound), np.max(np.abs(A[k] - ref) / bound)
+        assert np.array_equal(A[k], A[k].T)
+        # relative orthogonality values, the quantity Eq. 2.3 tests
+        dd = np.sqrt(np.maximum(np.diag(ref), 1e-300))
+        rel = np.abs(A[k] - ref) / np.outer(dd, dd)
+        assert np.max(rel[np.outer(dd, dd) > 0]) <= 1e-13
+
+
+@pytest.mark.parametrize("balanced", [False, True])
+def test_kernel_update_x(api, balanced):
+    rng = np.random.default_rng(3 + balanced)
+    rows, ncols = 320, 4 * 64
+    grading = 10.0 ** rng.uniform(-6, 0, ncols)
+    X = rng.standard_normal((rows, ncols)) * grading[None, :]
+    col0 = np.array([[0, 128], [192, 64]], dtype=np.int32)
+    Wm = np.stack([np.eye(128) + 0.3 * rng.standard_normal((128, 128)) for _ in range(2)])
+    Wm[1, :, 7] *= 1e-9  # a column with tiny entries
+    rot = np.array([1, 2], dtype=np.int32)
+    dexp = np.zeros((2, 128), dtype=np.int32)
+    if balanced:
+        for k, (i0, j0) in enumerate(col0):
+            cols = np.r_[i0:i0 + 64, j0:j0 + 64]
+            dexp[k] = np.floor(np.log2(np.linalg.norm(X[:, cols], axis=0))).astype(np.int32)
+    dev = torch.device("cuda:0")
+    Xd = torch.from_numpy(np.asfortranarray(X)).to(dev).t().contiguous().t()
+    api.hsvd_pivot_update_x(Xd, torch.from_numpy(col0).to(dev), torch.from_numpy(Wm).to(dev),
+                            torch.from_numpy(rot).to(dev), torch.from_numpy(dexp).to(dev) if balanced else None)
+    out = Xd.cpu().numpy()
+    for k, (i0, j0) in enumerate(col0):
+        cols = np.r_[i0:i0 + 64, j0:j0 + 64]
+        ref = X[:, cols] @ Wm[k]
+        d = np.exp2(dexp[k].astype(float))
+        xs = _scale(np.abs(X[:, cols] / d[None, :]).max(axis=1))
+        ws = _scale(np.abs(Wm[k] * d[:, None]).max(axis=0))
+        bound = 2 * 128 * U64 * np.outer(xs, ws) + 2 * 128 * U64 * (np.abs(X[:, cols]) @ np.abs(Wm[k]))
+        assert np.all(np.abs(out[:, cols] - ref) <= bound), np.max(np.abs(out[:, cols] - ref) / bound)
+    if balanced:
+        # graded columns keep their relative accuracy
+        cols = np.r_[0:64, 128:192]
+        rel = np.abs(out[:, cols] - X[:, cols] @ Wm[0]) / np.abs(X[:, cols] @ Wm[0]).max(axis=0)[None, :]
+        assert np.max(rel) <= 1e-13
+
+
+def _sigma_err(J, a, b):
+    err = 0.0
+    for s in (1, -1):
+        if np.any(J == s):
+            x, y = np.sort(a[J == s]), np.sort(b[J == s])
+            err = max(err, float(np.max(np.abs(x - y) / y)))
+    return err
+
+
+def _run(api, G, J, **kw):
+    dev = torch.device("cuda:0")
+    r = api.hsvd_solve_ex(torch.from_numpy(np.asfortranarray(G)).to(dev), torch.from_numpy(J).to(dev),
+                          api.make_opts(**kw), check=False)
+    torch.cuda.synchronize()
+    return r
+
+
+@pytest.mark.parametrize("kind,n", [("graded", 256), ("haar", 384), ("gaussian", 200)])
+def test_precision_solve_matches_oracle(api, kind, n):
+    if kind == "graded":
+        G, J = W.graded(n, decades=6, seed=2)
+    elif kind == "haar":
+        G, J = W.haar(n, seed=3)
+    else:
+        G, J = W.gaussian(n, m=n + 37, p=70, seed=9)
+    tol = n * U64
+    ref = oracle.hsvd(G, J, tol, 40)
+    assert ref["status"] == 0
+    r = _run(api, G, J, tol=tol, max_sweeps=40, method=api.HSVD_METHOD_BLOCKED,
+             precision=api.HSVD_PRECISION_BF16X8)
+    assert r.status == api.HSVD_OK and r.block_w == 64
+    s = r.sigma.cpu().numpy()
+    kap = U64 * np.linalg.norm(np.abs(G) @ np.abs(ref["V"]), axis=0) / ref["sigma"]
+    worst = 0.0
+    for sg in (1, -1):
+        idx = np.where(J == sg)[0]
+        if not idx.size:
+            continue
+        o = np.argsort(ref["sigma"][idx])
+        y = ref["sigma"][idx][o]
+        worst = max(worst, float(np.max(np.abs(np.sort(s[idx]) - y) / y / np.maximum(1e-12, kap[idx][o]))))
+    assert worst <= 1.0, worst
+    U_, V = r.U.cpu().numpy(), r.V.cpu().numpy()
+    Jd = np.diag(J.astype(float))
+    assert np.max(np.abs(U_.T @ U_ - np.eye(n))) <= 1e-12 * n
+    assert np.max(np.abs(V.T @ Jd @ V - Jd)) / max(1.0, np.max(np.abs(V)) ** 2) <= 1e-12 * n
+    res = np.max(np.linalg.norm(G @ V - U_ * s[None, :], axis=0) / (np.linalg.norm(G) * np.linalg.norm(V, axis=0)))
+    assert res <= 1e-12 * n
+    # the FP64 run of the same blocked method converges in about as many sweeps
+    r64 = _run(api, G, J, tol=tol, max_sweeps=40, method=api.HSVD_METHOD_BLOCKED, block_w=64)
+    assert r64.status == 0 and abs(r64.sweeps - r.sweeps) <= 2
