@@ -30,6 +30,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 MAX_SWEEPS = 40
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
+# kernel, from one ncu capture of this workload; an entry is removed when the
+# kernel changes
+PROFILED_TRAFFIC = {
+    ("graded1024", "fp64", "k_solve_cluster<64,8>"): (4.777e6, "profiles/kernels_graded1024_fp64.md"),
+    ("graded1024", "fp64", "k_update<64>"): (17.318e6, "profiles/kernels_graded1024_fp64.md"),
+    ("graded1024", "fp64", "k_gram<32>"): (8.396e6, "profiles/kernels_graded1024_fp64.md"),
+}
 GOLDEN = os.path.join(ROOT, "tests", "golden", "graded1024_sigma.txt")
 
 # name -> (n, generator description, default block width); the default is the
@@ -38,7 +47,10 @@ WORKLOADS = {
     "graded1024": (1024, "graded 1024x1024 G=B diag(10^(-6i/n)), J=diag(+1x512,-1x512)", 32),
     "haar4096": (4096, "4096x4096 G=Q1 diag(sigma) Q2, Haar Q, sigma log-uniform [1e-6,1], 2048 random +1 in J", 64),
     "haar1024": (1024, "1024x1024 G=Q1 diag(sigma) Q2, Haar Q, sigma log-uniform [1e-6,1], 512 random +1 in J", 64),
+    "batch10k": (256, "10000 independent square N(0,1) factors, n uniform on [16,256], m=n, random p in [0,n] "
+                      "+1 signs at random positions (seed 4)", 1),
 }
+BATCH_COUNT = 10000
 
 
 def make_input(name, seed_offset=0):
@@ -178,9 +190,211 @@ def cpu_baseline(G, J, tol, sweeps):
                                                                                             per_sweep)}
 
 
+def pointwise_flops_per_sweep(m, n):
+    """Pointwise work of one sweep (n^2/2 pairs): three dot products and the
+    updates of two G columns and two W columns, (n^2/2)(12m + 6n)."""
+    return 0.5 * n * n * (12.0 * m + 6.0 * n)
+
+
+def run_batched(args):
+    """The batched form on the 10,000-factor workload, against a loop of
+    single solves (timed on a bounded sample and scaled by the flops)."""
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    from paper_1008_1371_gb300 import api, build_lib, workloads
+
+    if local == 0:
+        build_lib.build()
+    if world > 1:
+        dist.barrier()
+    facs = workloads.batch(BATCH_COUNT, seed=4 + rank)
+    ms_ = [G.shape[0] for G, _ in facs]
+    ns_ = [G.shape[1] for G, _ in facs]
+    # one device buffer per array kind, factors as column-major views into it
+    def packed(sizes, dtype, device, pin=False):
+        tot = sum(sizes)
+        buf = torch.empty(tot, dtype=dtype, device=device, pin_memory=pin)
+        out, o = [], 0
+        for z in sizes:
+            out.append(buf[o:o + z])
+            o += z
+        return buf, out
+    gbuf, gv = packed([m * n for m, n in zip(ms_, ns_)], torch.float64, dev)
+    jbuf, jv = packed(ns_, torch.int8, dev)
+    for (G, J), g, j in zip(facs, gv, jv):
+        g.copy_(torch.from_numpy(G.ravel(order="F")))
+        j.copy_(torch.from_numpy(J))
+    Gs = [g.view(n, m).t() for g, m, n in zip(gv, ms_, ns_)]
+    sbuf, sig = packed(ns_, torch.float64, dev)
+    ubuf, uv = packed([m * n for m, n in zip(ms_, ns_)], torch.float64, dev)
+    vbuf, vv = packed([n * n for n in ns_], torch.float64, dev)
+    Us = [u.view(n, m).t() for u, m, n in zip(uv, ms_, ns_)]
+    Vs = [v.view(n, n).t() for v, n in zip(vv, ns_)]
+    opts = api.make_batch_opts(max_sweeps=30)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def solve():
+        return api.hsvd_solve_batched(Gs, jv, opts, out=(sig, Us, Vs), stream=stream)
+
+    for _ in range(args.warmup):
+        r = solve()
+    torch.cuda.synchronize()
+    step_ms, infos = [], []
+    with ClockSampler(local) as clk:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = solve()
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            infos.append(r.info)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+    assert r.rc == api.HSVD_OK, r.rc
+    ms = sum(step_ms) / len(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    eff = sum(sw * pointwise_flops_per_sweep(m, n) for sw, m, n in zip(r.sweeps, ms_, ns_))
+    value = world * eff / (ms * 1e-3) / 1e12
+    kern_ms = sum(i.ms_kernel for i in infos) / len(infos)
+    fp64_peak = 152 * 2 * 2 * 2.070e9 / 1e12
+    achieved = eff / (kern_ms * 1e-3) / 1e12
+    roofline = {"kernel": "k_batched", "bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak, "traffic": None,
+                "peak_source": "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (derived from units and clock)",
+                "ms_kernel": kern_ms, "group_width_per_bucket": list(r.info.bucket_width),
+                "resident_G_W_shared__G_shared__neither": list(r.info.resident)}
+
+    # a loop of single solves (the library's default method per factor) on a
+    # bounded sample, scaled to the whole batch by the effective flops
+    loop = None
+    if rank == 0:
+        idx = list(range(0, BATCH_COUNT, BATCH_COUNT // 40))
+        t_loop, f_loop = 0.0, 0.0
+        for k in idx:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            one = api.hsvd_solve_ex(Gs[k], jv[k], api.make_opts(max_sweeps=30), out=(sig[k], Us[k], Vs[k]),
+                                    stream=stream)
+            torch.cuda.synchronize()
+            t_loop += time.perf_counter() - t0
+            f_loop += one.sweeps * pointwise_flops_per_sweep(ms_[k], ns_[k])
+        est_ms = t_loop * 1e3 * eff / f_loop
+        loop = {"ms_estimated": est_ms, "tflops": f_loop / t_loop / 1e12, "speedup_of_batched": est_ms / ms,
+                "sample": "%d of %d factors (every %dth), one hsvd_solve call each, %.2f s measured, scaled by "
+                          "effective flops" % (len(idx), BATCH_COUNT, BATCH_COUNT // 40, t_loop)}
+
+    e2e = None
+    if not args.no_e2e:
+        Gh = [torch.from_numpy(G) for G, _ in facs]
+        Gh = [g.pin_memory() for g in Gh]
+        Jh = [torch.from_numpy(J).pin_memory() for _, J in facs]
+        api.hsvd_solve_batched(Gh, Jh, opts)
+        ts = []
+        for _ in range(max(3, args.steps // 2)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rh = api.hsvd_solve_batched(Gh, Jh, opts)
+            ts.append(time.perf_counter() - t0)
+        e2e_s = sum(ts) / len(ts)
+        h2d = sum(m * n * 8 + n for m, n in zip(ms_, ns_))
+        d2h = sum(n * 8 + m * n * 8 + n * n * 8 for m, n in zip(ms_, ns_))
+        e2e = {"value": world * eff / e2e_s / 1e12, "unit": "TFLOP/s", "ms_per_step": e2e_s * 1e3,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "note": "host arrays (pinned), one copy per matrix and direction inside the call"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        idx = list(range(0, BATCH_COUNT, BATCH_COUNT // 20))
+        t0 = time.perf_counter()
+        f = 0.0
+        for k in idx:
+            G, J = facs[k]
+            rr = oracle.hsvd(G, J, G.shape[1] * 2.0 ** -53, 30, want_u=False, want_v=False)
+            f += rr["sweeps"] * pointwise_flops_per_sweep(*G.shape)
+        dt = time.perf_counter() - t0
+        cpu = {"value": f / dt / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+               "sample": "%d of %d factors (every %dth), complete row-cyclic FP64 oracle solves, %.1f s"
+                         % (len(idx), BATCH_COUNT, BATCH_COUNT // 20, dt)}
+
+    if rank == 0:
+        line = {
+            "metric": "HSVD effective TFLOP/s (batched form, sigma rel-err <= 1e-12)", "value": value,
+            "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS["batch10k"][1], "count": BATCH_COUNT, "form": "batched",
+                       "method": "pointwise per factor, diagonal sorting", "tol": "n 2^-53 per factor",
+                       "max_sweeps_run": int(r.info.max_sweeps_run),
+                       "l2": "flushed (256 MB write) between steps; inputs 2.6 GB > L2",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "gpu_launches": int(sum(i.kernel_launches for i in infos)),
+            "roofline": roofline, "loop_of_single_solves": loop, "e2e": e2e, "cpu_baseline": cpu,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def metric_name(form):
     return ("HSVD effective TFLOP/s (%s, sigma rel-err <= 1e-12)"
             % ("plain FP64" if form == "fp64" else "split-precision BF16x8 products"))
+
+
+def run_reference_batched(args, oracle):
+    """The oracle on the batch workload: each step solves a bounded sample of
+    the factors completely (every 500th), rate scaled in effective flops."""
+    from paper_1008_1371_gb300 import workloads
+
+    facs = workloads.batch(BATCH_COUNT, seed=4)
+    idx = list(range(0, BATCH_COUNT, 500))
+    times, flops = [], []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        f = 0.0
+        for k in idx:
+            G, J = facs[k]
+            r = oracle.hsvd(G, J, G.shape[1] * 2.0 ** -53, 30, want_u=False, want_v=False)
+            f += r["sweeps"] * pointwise_flops_per_sweep(*G.shape)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+            flops.append(f)
+    value = sum(flops) / sum(times) / 1e12
+    per = sum(times) / len(times)
+    sample = "%d of %d factors (every 500th) solved completely by the row-cyclic FP64 oracle per step" % (
+        len(idx), BATCH_COUNT)
+    line = {
+        "impl": "reference", "metric": "HSVD effective TFLOP/s (batched form, sigma rel-err <= 1e-12)",
+        "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOADS["batch10k"][1], "count": BATCH_COUNT,
+                                        "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
 
 
 def run_reference(args):
@@ -190,6 +404,8 @@ def run_reference(args):
     import oracle
 
     oracle.build()
+    if args.workload == "batch10k":
+        return run_reference_batched(args, oracle)
     G, J = make_input(args.workload)
     m, n = G.shape
     tol = n * 2.0 ** -53
@@ -221,6 +437,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch10k":
+        return run_batched(args)
     import torch
 
     rank, world, local = dist_env()
@@ -297,6 +515,9 @@ def main():
     alg = {
         "update": upd_pairs * 2.0 * (m + n) * (2 * block) ** 2,
         "gram": visits * (6.0 if prec == api.HSVD_PRECISION_FP64 else 8.0) * m * block * block,
+        # an inner rotation mixes two rows and two columns of A_P and two
+        # columns of W_P: 3 vector pairs of length 2b, 6 flops per index
+        "solve": sum(i.rotations for i in infos) * 18.0 * (2 * block),
     }
     dom = max(("gram", "update", "solve"), key=lambda k: tot[k])
     fp64_peak = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk x flop x max clock
@@ -305,10 +526,13 @@ def main():
              "solve": "k_solve_cluster<%d,8>" % (2 * block)}
     if prec == api.HSVD_PRECISION_BF16X8:
         kname = {"gram": "k_gram_x", "update": "k_update_x", "solve": "k_solve_cluster<128,8>"}
-    if prec == api.HSVD_PRECISION_FP64:
+    if dom == "solve" or prec == api.HSVD_PRECISION_FP64:
         roofline = {"kernel": kname[dom], "bound": "alu", "achieved": achieved, "peak": fp64_peak,
                     "unit": "TFLOP/s", "frac": (achieved / fp64_peak) if achieved else None, "traffic": None,
                     "peak_source": "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (derived from units and clock)"}
+        if dom == "solve":
+            roofline["note"] = ("the inner solve is a chain of dependent rotation steps (sqrt/div latency and "
+                                "cluster barriers per step): latency bound, far below the FP64 unit's rate")
     else:
         # the tensor work of a split product: 36 BF16 slice products per FP64 product
         bf16_peak = 1934.1
@@ -319,6 +543,10 @@ def main():
                     "fp64_equivalent_tflops": achieved}
     roofline["ms_by_kernel"] = {k: v / len(infos) for k, v in tot.items()}
     roofline["alg_fp64_tflops_by_kernel"] = {k: alg[k] / (tot[k] * 1e-3) / 1e12 for k in alg if tot[k] > 0}
+    traffic = PROFILED_TRAFFIC.get((args.workload, args.form, roofline["kernel"]))
+    if traffic:
+        roofline["traffic"] = traffic[0]
+        roofline["traffic_source"] = traffic[1]
 
     # accuracy against the stored oracle values (written by tests/golden/make_golden.py
     # on a machine whose G has the same bytes as this one's)

@@ -219,6 +219,69 @@ int hsvd_solve_pointwise_noalloc(const double *G, int64_t m, int64_t n, int64_t 
                                  double tol, int max_sweeps, int sort, double *sigma, double *U,
                                  int64_t ldu, double *V, int64_t ldv, int *sweeps, void *stream);
 
+/*
+ * Batched form: many independent factors of mixed sizes in one persistent
+ * launch (a captured CUDA graph), each solved by the pointwise method
+ * (Sec. 2, Alg. 4.5) with diagonal sorting (Sec. 4).  Factors are dispatched
+ * largest first from one work queue; a CTA of 1024 threads solves one large
+ * factor at a time and splits into groups of 512 or 256 threads for smaller
+ * ones.  The group width of each size bucket (n < 40, < 72, < 128, < 192, and
+ * larger) is picked by an autotuner that times the candidate widths on a
+ * sample of the call's factors (two sweeps each) the first time a device sees
+ * a set of buckets, and reuses that choice afterwards.
+ */
+typedef struct hsvd_batch_opts {
+    double tol;      /* <= 0: n_k 2^-53 for factor k                                */
+    int max_sweeps;  /* <= 0 selects 30                                             */
+    int sort;        /* nonzero (default): diagonal sorting (Sec. 4)                */
+    int group_width; /* 0 (default): autotuned per size bucket; 256, 512 or 1024:
+                        that width for every factor                                 */
+    int use_graph;   /* nonzero (default): the launch is captured as a CUDA graph  */
+    int reserved[4]; /* must be zero                                                */
+} hsvd_batch_opts;
+
+typedef struct hsvd_batch_info {
+    int grid;             /* CTAs of the persistent launch (one per SM)            */
+    int tuned;            /* 1: the autotuner ran in this call, 2: its cached
+                             choice was used, 0: group_width was given              */
+    int bucket_width[5];  /* group width used per size bucket                      */
+    int max_sweeps_run;   /* largest sweep count over the factors                  */
+    int64_t rotations;    /* rotations applied, all factors                        */
+    int64_t kernel_launches; /* kernels of this library launched by the solve (1) */
+    int64_t resident[3];  /* factors with G and W in shared memory, with G only,
+                             with neither                                           */
+    double ms_kernel;     /* CUDA-event time of the batched launch                 */
+    double ms_tune;       /* CUDA-event time of the autotuner's sample runs        */
+} hsvd_batch_info;
+
+/* Fills *opts with the defaults above. */
+void hsvd_default_batch_opts(hsvd_batch_opts *opts);
+
+/*
+ * hsvd_solve_batched -- `count` independent HSVDs (Sec. 1, Eq. 1.1).  The
+ * arrays G, m, n, ldg, J, sigma, U, V, sweeps and status are HOST arrays with
+ * `count` entries.  The matrices they point to are all device pointers or all
+ * host pointers (then staged through device copies, one copy per matrix).
+ * Factor k: G[k] is m[k] x n[k] with leading dimension ldg[k], m >= n >= 1,
+ * n <= 2048, m <= 4096; J[k] holds n[k] signs (int8, +-1); sigma[k] receives
+ * n[k] values; U[k] (m[k] x n[k], leading dimension m[k]) and V[k] (n[k] x
+ * n[k], leading dimension n[k]) may be NULL, and U or V itself may be NULL for
+ * none at all.  sweeps and status (may be NULL) receive each factor's sweep
+ * count and status code.  The call returns after the results are complete:
+ * HSVD_OK if every factor converged, otherwise the first error code met
+ * (or HSVD_NOT_CONVERGED); argument errors return HSVD_ERR_ARG before any work.
+ */
+int hsvd_solve_batched(int64_t count, const double *const *G, const int64_t *m, const int64_t *n,
+                       const int64_t *ldg, const int8_t *const *J, double tol, int max_sweeps,
+                       double *const *sigma, double *const *U, double *const *V, int *sweeps, int *status,
+                       void *stream);
+
+/* hsvd_solve_batched with options (NULL: defaults) and an optional report. */
+int hsvd_solve_batched_ex(int64_t count, const double *const *G, const int64_t *m, const int64_t *n,
+                          const int64_t *ldg, const int8_t *const *J, double *const *sigma, double *const *U,
+                          double *const *V, int *sweeps, int *status, const hsvd_batch_opts *opts,
+                          hsvd_batch_info *info, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -55,6 +55,17 @@ class HsvdInfo(ctypes.Structure):
                 ("ms_gram", _dbl), ("ms_solve", _dbl), ("ms_update", _dbl), ("ms_other", _dbl)]
 
 
+class HsvdBatchOpts(ctypes.Structure):
+    _fields_ = [("tol", _dbl), ("max_sweeps", _int), ("sort", _int), ("group_width", _int), ("use_graph", _int),
+                ("reserved", _int * 4)]
+
+
+class HsvdBatchInfo(ctypes.Structure):
+    _fields_ = [("grid", _int), ("tuned", _int), ("bucket_width", _int * 5), ("max_sweeps_run", _int),
+                ("rotations", _i64), ("kernel_launches", _i64), ("resident", _i64 * 3), ("ms_kernel", _dbl),
+                ("ms_tune", _dbl)]
+
+
 class HsvdError(RuntimeError):
     def __init__(self, status):
         super().__init__("hsvd failed: %s (%d)" % (hsvd_status_string(status), status))
@@ -91,6 +102,13 @@ def lib():
             L.hsvd_pivot_gram_x.restype = _int
             L.hsvd_pivot_update_x.argtypes = [_p, _i64, _i64, _int, _p, _p, _p, _p, _p]
             L.hsvd_pivot_update_x.restype = _int
+            L.hsvd_default_batch_opts.argtypes = [ctypes.POINTER(HsvdBatchOpts)]
+            L.hsvd_default_batch_opts.restype = None
+            L.hsvd_solve_batched.argtypes = [_i64, _p, _p, _p, _p, _p, _dbl, _int, _p, _p, _p, _p, _p, _p]
+            L.hsvd_solve_batched.restype = _int
+            L.hsvd_solve_batched_ex.argtypes = [_i64, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p,
+                                                ctypes.POINTER(HsvdBatchOpts), ctypes.POINTER(HsvdBatchInfo), _p]
+            L.hsvd_solve_batched_ex.restype = _int
             _lib = L
     return _lib
 
@@ -292,3 +310,72 @@ def hsvd_pivot_update_x(X, col0, W, rotated, dexp=None, stream=None):
     if st != HSVD_OK:
         raise HsvdError(st)
     return X
+
+
+@dataclass
+class HsvdBatchResult:
+    sigma: list
+    U: Optional[list]
+    V: Optional[list]
+    sweeps: list
+    status: list
+    rc: int
+    info: HsvdBatchInfo
+
+
+def make_batch_opts(tol=0.0, max_sweeps=30, sort=True, group_width=0, use_graph=True):
+    o = HsvdBatchOpts()
+    lib().hsvd_default_batch_opts(ctypes.byref(o))
+    o.tol = float(tol)
+    o.max_sweeps = int(max_sweeps)
+    o.sort = 1 if sort else 0
+    o.group_width = int(group_width)
+    o.use_graph = 1 if use_graph else 0
+    return o
+
+
+def _ptr_array(ptrs):
+    arr = (ctypes.c_void_p * max(len(ptrs), 1))()
+    for i, q in enumerate(ptrs):
+        arr[i] = q
+    return arr
+
+
+def hsvd_solve_batched(Gs, Js, opts=None, compute_u=True, compute_v=True, stream=None, check=True, out=None):
+    """``hsvd_solve_batched_ex``: independent HSVDs of the factors ``Gs`` (a
+    list of m_k x n_k float64 tensors, all CUDA or all CPU) with signatures
+    ``Js``, in one persistent launch.  ``out`` may hold preallocated
+    (sigmas, Us, Vs) lists (column-major, leading dimensions m_k and n_k).
+    Returns an :class:`HsvdBatchResult`; raises :class:`HsvdError` on a
+    negative status when ``check``."""
+    L = lib()
+    count = len(Gs)
+    Gc = [_colmajor(G, torch.float64) for G in Gs]
+    Jc = [J.to(torch.int8).contiguous() for J in Js]
+    if len(Jc) != count:
+        raise ValueError("one signature per factor")
+    dev = Gc[0].device if count else torch.device("cpu")
+    m = (ctypes.c_int64 * max(count, 1))(*[G.shape[0] for G in Gc])
+    n = (ctypes.c_int64 * max(count, 1))(*[G.shape[1] for G in Gc])
+    ld = (ctypes.c_int64 * max(count, 1))(*[(G.stride(1) if G.shape[1] > 1 else G.shape[0]) for G in Gc])
+    pin = dev.type == "cpu" and count > 0 and Gc[0].is_pinned()
+    if out is not None:
+        sig, Us, Vs = out
+    else:
+        sig = [torch.empty(G.shape[1], dtype=torch.float64, device=dev, pin_memory=pin) for G in Gc]
+        Us = [torch.empty((G.shape[1], G.shape[0]), dtype=torch.float64, device=dev, pin_memory=pin).t()
+              for G in Gc] if compute_u else None
+        Vs = [torch.empty((G.shape[1], G.shape[1]), dtype=torch.float64, device=dev, pin_memory=pin).t()
+              for G in Gc] if compute_v else None
+    sweeps = (ctypes.c_int * max(count, 1))()
+    status = (ctypes.c_int * max(count, 1))()
+    o = opts if opts is not None else make_batch_opts()
+    info = HsvdBatchInfo()
+    rc = L.hsvd_solve_batched_ex(count, _ptr_array([G.data_ptr() for G in Gc]), m, n, ld,
+                                 _ptr_array([J.data_ptr() for J in Jc]), _ptr_array([x.data_ptr() for x in sig]),
+                                 _ptr_array([x.data_ptr() for x in Us]) if Us is not None else None,
+                                 _ptr_array([x.data_ptr() for x in Vs]) if Vs is not None else None,
+                                 sweeps, status, ctypes.byref(o), ctypes.byref(info), _stream_ptr(stream, dev))
+    if check and rc < 0:
+        raise HsvdError(rc)
+    return HsvdBatchResult(sig, Us, Vs, list(sweeps)[:count], list(status)[:count], rc, info)

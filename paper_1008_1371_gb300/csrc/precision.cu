@@ -6,9 +6,8 @@
 // finalisation) stays in FP64.  Pivot blocks are 128 x 128 (block width 64).
 //
 // Splitting (tc.cuh): a row or column of an operand with |x| < 2^E is written
-// as 8 balanced base-128 digits, x 2^-E = sum_k q_k 2^(-6-7(k-1)) + r with
-// |q_k| <= 64 and |r| < 2^-55; slice k is the exact BF16 number
-// q_k 2^(-6-7(k-1)).  The 36 products of slices a, b with a + b <= 9 run on the
+// as 8 balanced base-128 digits, x 2^-E = sum_k q_k 2^(1-7k) + r with
+// |q_k| <= 64 and |r| < 2^-55; slice k is the exact BF16 number q_k 2^(1-7k).  The 36 products of slices a, b with a + b <= 9 run on the
 // tensor cores; those with a + b = d accumulate in TMEM accumulator d - 2,
 // where every partial sum is an integer below 2^24 in its unit (at most 512
 // rows per accumulation), so the FP32 accumulation is exact.  The eight
@@ -32,12 +31,13 @@ using namespace tc;
 
 constexpr int NNX = 128;             // pivot block order 2b
 constexpr int kThrX = 256;           // eight warps: two per TMEM lane quarter
-constexpr int kGramK = 512;          // rows of G per Gram CTA (exactness window)
-constexpr int kGramKT = 64;          // rows per shared-memory tile of the Gram
+constexpr int kGramK = 512;          // rows of G per Gram CTA pair (exactness window)
+constexpr int kGramKT = 32;          // rows per shared-memory tile of the Gram
 constexpr int kUpdKT = 32;           // k per shared-memory tile of the update
 constexpr int kUpdRows = 64;         // rows of G or V per update item (N)
 constexpr int kN = 64;               // MMA N
 constexpr uint32_t kTmemCols = 512;  // eight accumulators of 64 columns
+constexpr uint32_t kWaitIter = 1u << 26;
 
 __device__ __forceinline__ int warp_max_i(int v) {
 #pragma unroll
@@ -60,79 +60,115 @@ __device__ __forceinline__ void issue_products(uint32_t tmem, uint32_t a_base, u
         }
 }
 
-// this thread's lane (row of D) and 8 columns [c0, c0+8) of all eight accumulators
+// this thread's lane and 8 columns [c0, c0+8) of all eight accumulators: the
+// eight loads are issued back to back and waited for once
 __device__ __forceinline__ void read_accs(uint32_t tmem, int lane_base, int c0, float (&v)[8][8]) {
+    uint32_t r[8][8];
 #pragma unroll
-    for (int acc = 0; acc < 8; ++acc) tmem_ld8(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(acc * kN + c0), v[acc]);
+    for (int acc = 0; acc < 8; ++acc) tmem_ld8_raw(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(acc * kN + c0), r[acc]);
+    tmem_wait_ld();
+#pragma unroll
+    for (int acc = 0; acc < 8; ++acc) {
+        reg_dep8(r[acc]);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[acc][j] = __uint_as_float(r[acc][j]);
+    }
 }
 
 // ---------------------------------------------------------------- Gram
-// CTA (pair, split, half): columns [64 h, 64 h + 64) of the partial A_P over
-// rows [512 split, 512 split + 512) of the panel P = [G_I G_J] (m x 128).
-// A = P^T (128 x K, K-major); B = rows [64 h, 64 h + 64) of the same tile.
-__global__ void __launch_bounds__(kThrX, 1)
+// A cluster of two CTAs per (pair, split): CTA h forms columns [64 h, 64 h + 64)
+// of the partial A_P over rows [512 split, 512 split + 512) of the panel
+// P = [G_I G_J] (m x 128): A = P^T (128 x K, K-major), B = rows [64 h, 64 h + 64)
+// of the same tile.  Each CTA splits its own 64 columns of every 32-row tile
+// and writes the slices to both CTAs' shared memory, so the tile is split once;
+// tiles are double-buffered, the split of tile t overlapping the products of
+// tile t - 1.  One cluster barrier per tile.
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThrX, 1)
 k_gram_x(const double *__restrict__ G, int64_t rows, int64_t ldg, const int *__restrict__ col0, int ksplit,
          double *__restrict__ part, int *__restrict__ status) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    uint16_t *sl = reinterpret_cast<uint16_t *>(smem);  // kSlices x (128 x 64)
+    constexpr uint32_t kSliceBytes = NNX * kGramKT * 2;     // one slice of a tile (8 KB)
+    constexpr uint32_t kBufBytes = kSlices * kSliceBytes;   // one tile (64 KB)
     __shared__ int Ecol[NNX];
-    __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tbase;
     __shared__ int s_fail;
-    constexpr uint32_t kSliceBytes = NNX * kGramKT * 2;
-    const int half = blockIdx.x & 1;
+    const uint32_t half = cluster_rank(), peer = half ^ 1u;
     const int pair = (blockIdx.x >> 1) / ksplit, split = (blockIdx.x >> 1) % ksplit;
     const int64_t r0 = (int64_t)split * kGramK, r1 = min(rows, r0 + kGramK);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int cI = col0[2 * pair], cJ = col0[2 * pair + 1];
-    for (int c = warp; c < NNX; c += kThrX / 32) {
+    const uint32_t sbase = smem_addr(smem), sbase_peer = map_peer(sbase, peer);
+    cluster_sync();  // both CTAs are running before either touches the other's shared memory
+    // column exponents of this CTA's 64 columns over the CTA pair's rows, to both CTAs
+    for (int cc = warp; cc < NNX / 2; cc += kThrX / 32) {
+        const int c = NNX / 2 * (int)half + cc;
         const double *g = G + (int64_t)(c < NNX / 2 ? cI + c : cJ + c - NNX / 2) * ldg;
         int e = -2000;
         for (int64_t r = r0 + lane; r < r1; r += 32) e = max(e, exp_bound(g[r]));
         e = warp_max_i(e);
-        if (lane == 0) Ecol[c] = e < -1000 ? 0 : e;
+        if (lane == 0) {
+            e = e < -1000 ? 0 : e;
+            Ecol[c] = e;
+            st_cluster_s32(map_peer(smem_addr(&Ecol[c]), peer), e);
+        }
     }
     if (tid == 0) {
         s_fail = 0;
-        mbar_init(&mbar, 1);
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
     }
     if (warp == 0) tmem_alloc(&tbase, kTmemCols);
     fence_before();
-    __syncthreads();
+    cluster_sync();
     fence_after();
     const uint32_t tmem = tbase;
     const uint32_t idesc = idesc_bf16(NNX, kN);
     const uint32_t sbo = (kGramKT / 8) * 128;
-    const uint32_t b_off = core_offset(kN * half, 0, kGramKT);
+    const uint32_t b_off = core_offset(kN * (int)half, 0, kGramKT);
     int inited[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    uint32_t phase = 0;
-    for (int64_t t0 = r0; t0 < r1; t0 += kGramKT) {
-        for (int e = tid; e < kGramKT * NNX; e += kThrX) {
-            const int r = e % kGramKT, c = e / kGramKT;
-            const int64_t row = t0 + r;
-            const double x = row < r1 ? G[row + (int64_t)(c < NNX / 2 ? cI + c : cJ + c - NNX / 2) * ldg] : 0.0;
-            uint16_t s[kSlices];
-            split_slices(x, Ecol[c], s);
-            const uint32_t off = core_offset(c, r, kGramKT) >> 1;
+    const int ntiles = (int)((r1 - r0 + kGramKT - 1) / kGramKT);
+    // split mapping: a warp writes one 8 x 8 core matrix per step; lane -> column
+    // (lane >> 2) of the group, rows 2 (lane & 3) and 2 (lane & 3) + 1
+    const int cc = lane >> 2, kp = 2 * (lane & 3);
+    for (int t = 0; t < ntiles; ++t) {
+        const uint32_t buf = (uint32_t)(t & 1) * kBufBytes;
+        const int64_t t0 = r0 + (int64_t)t * kGramKT;
+        for (int core = warp; core < (NNX / 2 / 8) * (kGramKT / 8); core += kThrX / 32) {
+            const int cg = core / (kGramKT / 8), kg = core % (kGramKT / 8);
+            const int c = NNX / 2 * (int)half + cg * 8 + cc, k = kg * 8 + kp;
+            const double *g = G + (int64_t)(c < NNX / 2 ? cI + c : cJ + c - NNX / 2) * ldg;
+            const int64_t row = t0 + k;
+            const double x0 = row < r1 ? g[row] : 0.0, x1 = row + 1 < r1 ? g[row + 1] : 0.0;
+            const long long w0 = digit_word(x0, Ecol[c]), w1 = digit_word(x1, Ecol[c]);
+            const uint32_t off = buf + core_offset(c, k, kGramKT);
 #pragma unroll
-            for (int k = 0; k < kSlices; ++k) sl[k * (NNX * kGramKT) + off] = s[k];
+            for (int s = 0; s < kSlices; ++s) {
+                const uint32_t v = slice_pair(w0, w1, s + 1);
+                const uint32_t o = off + (uint32_t)s * kSliceBytes;
+                *reinterpret_cast<uint32_t *>(smem + o) = v;
+                st_cluster_u32(sbase_peer + o, v);
+            }
         }
+        fence_proxy_async_cluster();
         fence_proxy_async();
+        // the products of tile t - 1 are done in this CTA: its buffer is free
+        // for tile t + 1 in both CTAs once both have passed the barrier below
+        if (t >= 1 && !s_fail && !mbar_wait(&mbar[(t - 1) & 1], ((t - 1) >> 1) & 1, kWaitIter)) s_fail = 1;
         fence_before();
-        __syncthreads();
+        cluster_sync();
         fence_after();
-        if (tid == 0) {
-            const uint32_t base = smem_addr(sl);
+        if (tid == 0 && !s_fail) {
+            fence_proxy_async();
+            const uint32_t base = sbase + buf;
             for (int ks = 0; ks < kGramKT / 16; ++ks)
                 issue_products(tmem, base, kSliceBytes, base + b_off, kSliceBytes, ks * 256, sbo, idesc, inited);
-            commit(&mbar);
+            commit(&mbar[t & 1]);
         }
-        if (!mbar_wait(&mbar, phase)) atomicExch(&s_fail, 1);
-        phase ^= 1;
-        fence_after();
-        __syncthreads();
-        if (s_fail) break;
     }
+    if (ntiles > 0 && !s_fail && !mbar_wait(&mbar[(ntiles - 1) & 1], ((ntiles - 1) >> 1) & 1, kWaitIter)) s_fail = 1;
+    fence_after();
+    __syncthreads();
     if (!s_fail) {
         // lane c = row of A_P; warp group h2 takes TMEM columns [32 h2, 32 h2 + 32)
         const int q = warp & 3, c = 32 * q + lane, h2 = warp >> 2;
@@ -145,7 +181,7 @@ k_gram_x(const double *__restrict__ G, int64_t rows, int64_t ldg, const int *__r
                 float d[8];
 #pragma unroll
                 for (int a = 0; a < 8; ++a) d[a] = v[a][j];
-                const int col = kN * half + c0 + j;
+                const int col = kN * (int)half + c0 + j;
                 out[c + (size_t)col * NNX] = combine8(d, Ecol[c] + Ecol[col]);
             }
         }
@@ -153,7 +189,7 @@ k_gram_x(const double *__restrict__ G, int64_t rows, int64_t ldg, const int *__r
         atomicExch(status, HSVD_ERR_CUDA);
     }
     fence_before();
-    __syncthreads();
+    cluster_sync();  // no CTA leaves while its peer may still touch its shared memory
     fence_after();
     if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
@@ -190,17 +226,21 @@ k_wprep_x(const double *__restrict__ Wp, const int *__restrict__ dexp, const int
     __syncthreads();
     for (int e = tid; e < 2 * NNX; e += kThrX) wexp[(size_t)pair * 2 * NNX + e] = F[e / NNX][e % NNX];
     constexpr size_t kTile = (size_t)NNX * kUpdKT;  // elements per slice tile
-    for (int e = tid; e < 2 * NNX * NNX; e += kThrX) {
-        const int which = e / (NNX * NNX), rem = e % (NNX * NNX);
-        const int k = rem % NNX, j = rem / NNX;  // consecutive threads: consecutive k (coalesced reads)
-        const double w = W[k + (size_t)j * NNX];
-        uint16_t s[kSlices];
-        split_slices(w, which == 0 ? F[0][j] - dk[k] : F[1][j], s);
+    // a warp step covers one 8 (j) x 8 (k) core matrix: lane -> j (lane >> 2),
+    // k pair 2 (lane & 3)
+    const int jj = lane >> 2, kp = 2 * (lane & 3);
+    for (int core = warp; core < 2 * (NNX / 8) * (NNX / 8); core += kThrX / 32) {
+        const int which = core / ((NNX / 8) * (NNX / 8)), rem = core % ((NNX / 8) * (NNX / 8));
+        const int j = (rem / (NNX / 8)) * 8 + jj, k = (rem % (NNX / 8)) * 8 + kp;
+        const double w0 = W[k + (size_t)j * NNX], w1 = W[k + 1 + (size_t)j * NNX];
+        const long long d0 = digit_word(w0, which == 0 ? F[0][j] - dk[k] : F[1][j]);
+        const long long d1 = digit_word(w1, which == 0 ? F[0][j] - dk[k + 1] : F[1][j]);
         const int q = k / kUpdKT, kk = k % kUpdKT;
         uint16_t *dst = wsl + (((size_t)pair * 2 + which) * 4 + q) * kSlices * kTile;
         const uint32_t off = core_offset(j, kk, kUpdKT) >> 1;
 #pragma unroll
-        for (int s_ = 0; s_ < kSlices; ++s_) dst[s_ * kTile + off] = s[s_];
+        for (int s = 0; s < kSlices; ++s)
+            *reinterpret_cast<uint32_t *>(dst + s * kTile + off) = slice_pair(d0, d1, s + 1);
     }
 }
 
@@ -209,6 +249,16 @@ k_wprep_x(const double *__restrict__ Wp, const int *__restrict__ dexp, const int
 // transposed, Out^T = W'^T X'^T: A = W'^T (128 x 128 from k_wprep_x, bulk
 // copies per k quarter), B = X' (the chunk's 64 rows, K-major over the panel's
 // 128 columns), split per row after balancing.  D is 128 (columns j) x 64 (rows).
+// Software pipeline over the flat sequence of k-quarter tiles of all items of
+// the CTA: A and B tiles are double-buffered, the split of tile g + 1 (and the
+// row exponents of the next item) run while the products of tile g are on the
+// tensor cores; only the epilogue (TMEM -> FP64) waits for the products.
+struct UpdItem {
+    double *M;
+    int64_t ld, rows, r0;
+    int pair, which, cI, cJ;
+};
+
 __global__ void __launch_bounds__(kThrX, 1)
 k_update_x(double *__restrict__ X, int64_t rowsX, int64_t ldx, double *__restrict__ Y, int64_t rowsY, int64_t ldy,
            int npairs, const int *__restrict__ col0, const uint16_t *__restrict__ wsl,
@@ -217,10 +267,11 @@ k_update_x(double *__restrict__ X, int64_t rowsX, int64_t ldx, double *__restric
     extern __shared__ __align__(1024) unsigned char smem[];
     constexpr uint32_t kATile = NNX * kUpdKT * 2;       // one slice of W'^T (8 KB)
     constexpr uint32_t kBTile = kUpdRows * kUpdKT * 2;  // one slice of X' (4 KB)
-    uint16_t *As = reinterpret_cast<uint16_t *>(smem);  // kSlices A tiles
-    uint16_t *Bs = As + kSlices * NNX * kUpdKT;         // kSlices B tiles
-    __shared__ int Erow[kUpdRows], Fcol[NNX], dk[NNX];
-    __shared__ __align__(8) uint64_t mbar_a, mbar_m;
+    constexpr uint32_t kABuf = kSlices * kATile, kBBuf = kSlices * kBTile;
+    unsigned char *As = smem;                // two A buffers
+    unsigned char *Bs = smem + 2 * kABuf;    // two B buffers
+    __shared__ int Erow[2][kUpdRows], Fcol[2][NNX], dk[2][NNX];
+    __shared__ __align__(8) uint64_t mbar_a[2], mbar_m[2];
     __shared__ uint32_t tbase;
     __shared__ int s_fail;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -229,8 +280,10 @@ k_update_x(double *__restrict__ X, int64_t rowsX, int64_t ldx, double *__restric
     const int64_t items = (int64_t)npairs * chunks;
     if (tid == 0) {
         s_fail = 0;
-        mbar_init(&mbar_a, 1);
-        mbar_init(&mbar_m, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&mbar_a[b], 1);
+            mbar_init(&mbar_m[b], 1);
+        }
     }
     if (warp == 0) tmem_alloc(&tbase, kTmemCols);
     fence_before();
@@ -239,94 +292,162 @@ k_update_x(double *__restrict__ X, int64_t rowsX, int64_t ldx, double *__restric
     const uint32_t tmem = tbase;
     const uint32_t idesc = idesc_bf16(NNX, kN);
     const uint32_t sbo = (kUpdKT / 8) * 128;
-    uint32_t phase_a = 0, phase_m = 0;
-    for (int64_t item = blockIdx.x; item < items && !s_fail; item += gridDim.x) {
-        const int pair = (int)(item / chunks);
-        const int64_t chunk = item % chunks;
-        if (!rotated[pair]) continue;
-        const int which = chunk < chunksX ? 0 : 1;
-        double *M = which == 0 ? X : Y;
-        const int64_t ld = which == 0 ? ldx : ldy, rows = which == 0 ? rowsX : rowsY;
-        const int64_t r0 = (which == 0 ? chunk : chunk - chunksX) * kUpdRows;
-        const int cI = col0[2 * pair], cJ = col0[2 * pair + 1];
+
+    auto next_item = [&](int64_t from) -> int64_t {
+        for (int64_t it = from; it < items; it += gridDim.x)
+            if (rotated[it / chunks]) return it;
+        return -1;
+    };
+    auto describe = [&](int64_t it) {
+        UpdItem d;
+        d.pair = (int)(it / chunks);
+        const int64_t chunk = it % chunks;
+        d.which = chunk < chunksX ? 0 : 1;
+        d.M = d.which == 0 ? X : Y;
+        d.ld = d.which == 0 ? ldx : ldy;
+        d.rows = d.which == 0 ? rowsX : rowsY;
+        d.r0 = (d.which == 0 ? chunk : chunk - chunksX) * kUpdRows;
+        d.cI = col0[2 * d.pair];
+        d.cJ = col0[2 * d.pair + 1];
+        return d;
+    };
+    // exponents of the item into slot s (block-wide, with barriers)
+    auto setup = [&](const UpdItem &d, int s) {
         for (int k = tid; k < NNX; k += kThrX) {
-            dk[k] = which == 0 ? dexp[(size_t)pair * NNX + k] : 0;
-            Fcol[k] = wexp[((size_t)pair * 2 + which) * NNX + k];
+            dk[s][k] = d.which == 0 ? dexp[(size_t)d.pair * NNX + k] : 0;
+            Fcol[s][k] = wexp[((size_t)d.pair * 2 + d.which) * NNX + k];
         }
-        if (tid < kUpdRows) Erow[tid] = -2000;
+        if (tid < kUpdRows) Erow[s][tid] = -2000;
         __syncthreads();
-        {   // row exponents of X' = X D^-1 (four threads per row)
-            const int i = tid & (kUpdRows - 1), part4 = tid >> 6;
-            const int64_t row = r0 + i;
-            int e = -2000;
-            if (row < rows)
-                for (int k = part4 * 32; k < part4 * 32 + 32; ++k) {
-                    const int col = k < NNX / 2 ? cI + k : cJ + k - NNX / 2;
-                    e = max(e, exp_bound(M[row + (int64_t)col * ld]) - dk[k]);
-                }
-            atomicMax(&Erow[i], e);
-        }
-        __syncthreads();
-        int inited[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (int q = 0; q < NNX / kUpdKT; ++q) {
-            if (tid == 0) {
-                mbar_expect_tx(&mbar_a, kSlices * kATile);
-                bulk_g2s(As, wsl + (((size_t)pair * 2 + which) * 4 + q) * kSlices * NNX * kUpdKT, kSlices * kATile,
-                         &mbar_a);
+        const int i = tid & (kUpdRows - 1), part4 = tid >> 6;
+        const int64_t row = d.r0 + i;
+        int e = -2000;
+        if (row < d.rows)
+            for (int k = part4 * 32; k < part4 * 32 + 32; ++k) {
+                const int col = k < NNX / 2 ? d.cI + k : d.cJ + k - NNX / 2;
+                e = max(e, exp_bound(d.M[row + (int64_t)col * d.ld]) - dk[s][k]);
             }
-            for (int e = tid; e < kUpdRows * kUpdKT; e += kThrX) {
-                const int i = e % kUpdRows, kk = e / kUpdRows, k = q * kUpdKT + kk;
-                const int64_t row = r0 + i;
-                const int col = k < NNX / 2 ? cI + k : cJ + k - NNX / 2;
-                const double x = row < rows ? M[row + (int64_t)col * ld] : 0.0;
-                uint16_t s[kSlices];
-                split_slices(x, (Erow[i] < -1000 ? 0 : Erow[i]) + dk[k], s);
-                const uint32_t off = core_offset(i, kk, kUpdKT) >> 1;
+        atomicMax(&Erow[s][i], e);
+        __syncthreads();
+        if (tid < kUpdRows && Erow[s][tid] < -1000) Erow[s][tid] = 0;
+        __syncthreads();
+    };
+    // tile g (k quarter q of item d, exponents in slot s) into buffer b
+    const int rr = lane >> 2, kp = 2 * (lane & 3);
+    auto produce = [&](const UpdItem &d, int s, int q, int b, uint32_t use) {
+        if (tid == 0) {
+            mbar_expect_tx(&mbar_a[b], kABuf);
+            bulk_g2s(As + b * kABuf, wsl + (((size_t)d.pair * 2 + d.which) * 4 + q) * kSlices * NNX * kUpdKT, kABuf,
+                     &mbar_a[b]);
+        }
+        (void)use;
+        unsigned char *Bb = Bs + b * kBBuf;
+        for (int core = warp; core < (kUpdRows / 8) * (kUpdKT / 8); core += kThrX / 32) {
+            const int i = (core / (kUpdKT / 8)) * 8 + rr, kk = (core % (kUpdKT / 8)) * 8 + kp;
+            const int k = q * kUpdKT + kk;
+            const int64_t row = d.r0 + i;
+            const int c0 = k < NNX / 2 ? d.cI + k : d.cJ + k - NNX / 2;
+            const int c1 = k + 1 < NNX / 2 ? d.cI + k + 1 : d.cJ + k + 1 - NNX / 2;
+            const double x0 = row < d.rows ? d.M[row + (int64_t)c0 * d.ld] : 0.0;
+            const double x1 = row < d.rows ? d.M[row + (int64_t)c1 * d.ld] : 0.0;
+            const long long w0 = digit_word(x0, Erow[s][i] + dk[s][k]);
+            const long long w1 = digit_word(x1, Erow[s][i] + dk[s][k + 1]);
+            const uint32_t off = core_offset(i, kk, kUpdKT);
 #pragma unroll
-                for (int s_ = 0; s_ < kSlices; ++s_) Bs[s_ * (kUpdRows * kUpdKT) + off] = s[s_];
+            for (int sl = 0; sl < kSlices; ++sl)
+                *reinterpret_cast<uint32_t *>(Bb + sl * kBTile + off) = slice_pair(w0, w1, sl + 1);
+        }
+    };
+    auto wait_mma = [&](int64_t g) {  // the products of tile g are complete
+        if (g >= 0 && !s_fail && !mbar_wait(&mbar_m[g & 1], (uint32_t)((g >> 1) & 1), kWaitIter)) s_fail = 1;
+    };
+
+    int64_t it = next_item(blockIdx.x);
+    int slot = 0;
+    int64_t g = 0;  // tile counter
+    int64_t issued_a = -1, issued_m = -1;
+    if (it >= 0) {
+        UpdItem cur = describe(it);
+        setup(cur, slot);
+        produce(cur, slot, 0, 0, 0);
+        issued_a = 0;
+        while (true) {
+            int64_t nit = -1;
+            UpdItem nxt = cur;
+            int inited[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            for (int q = 0; q < NNX / kUpdKT; ++q, ++g) {
+                const int b = (int)(g & 1);
+                fence_proxy_async();
+                fence_before();
+                __syncthreads();
+                fence_after();
+                if (s_fail) break;
+                if (tid == 0) {
+                    if (!mbar_wait(&mbar_a[b], (uint32_t)((g >> 1) & 1), kWaitIter)) {
+                        s_fail = 1;
+                    } else {
+                        const uint32_t ab = smem_addr(As + b * kABuf), bb = smem_addr(Bs + b * kBBuf);
+                        for (int ks = 0; ks < kUpdKT / 16; ++ks)
+                            issue_products(tmem, ab, kATile, bb, kBTile, ks * 256, sbo, idesc, inited);
+                        commit(&mbar_m[b]);
+                        issued_m = g;
+                    }
+                }
+                // the next tile: the next k quarter, or the first of the next item
+                if (q + 1 < NNX / kUpdKT) {
+                    wait_mma(g - 1);
+                    produce(cur, slot, q + 1, b ^ 1, 0);
+                    if (tid == 0) issued_a = g + 1;
+                } else {
+                    nit = next_item(it + gridDim.x);
+                    if (nit >= 0) {
+                        nxt = describe(nit);
+                        setup(nxt, slot ^ 1);
+                        wait_mma(g - 1);
+                        produce(nxt, slot ^ 1, 0, b ^ 1, 0);
+                        if (tid == 0) issued_a = g + 1;
+                    }
+                }
             }
-            fence_proxy_async();
-            if (!mbar_wait(&mbar_a, phase_a)) atomicExch(&s_fail, 1);
-            phase_a ^= 1;
+            __syncthreads();
+            if (s_fail) break;
+            // epilogue of the item: lane j = output column, warp group h2 = rows [32 h2, 32 h2 + 32)
+            wait_mma(g - 1);
+            fence_after();
+            __syncthreads();
+            if (s_fail) break;
+            {
+                const int qd = warp & 3, j = 32 * qd + lane, h2 = warp >> 2;
+                const int jj = j < NNX / 2 ? cur.cI + j : cur.cJ + j - NNX / 2;
+                for (int c0 = 32 * h2; c0 < 32 * h2 + 32; c0 += 8) {
+                    float v[8][8];
+                    read_accs(tmem, 32 * qd, c0, v);
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) {
+                        const int i = c0 + t;
+                        const int64_t row = cur.r0 + i;
+                        if (row >= cur.rows) continue;
+                        float d[8];
+#pragma unroll
+                        for (int a = 0; a < 8; ++a) d[a] = v[a][t];
+                        cur.M[row + (int64_t)jj * cur.ld] = combine8(d, Erow[slot][i] + Fcol[slot][j]);
+                    }
+                }
+            }
             fence_before();
-            __syncthreads();
-            fence_after();
-            if (s_fail) break;
-            if (tid == 0) {
-                for (int ks = 0; ks < kUpdKT / 16; ++ks)
-                    issue_products(tmem, smem_addr(As), kATile, smem_addr(Bs), kBTile, ks * 256, sbo, idesc, inited);
-                commit(&mbar_m);
-            }
-            if (!mbar_wait(&mbar_m, phase_m)) atomicExch(&s_fail, 1);
-            phase_m ^= 1;
-            fence_after();
-            __syncthreads();
-            if (s_fail) break;
+            if (nit < 0) break;
+            it = nit;
+            cur = nxt;
+            slot ^= 1;
         }
-        if (s_fail) break;
-        {   // epilogue: lane j = output column, warp group h2 = rows [32 h2, 32 h2 + 32)
-            const int qd = warp & 3, j = 32 * qd + lane, h2 = warp >> 2;
-            const int jj = j < NNX / 2 ? cI + j : cJ + j - NNX / 2;
-            for (int c0 = 32 * h2; c0 < 32 * h2 + 32; c0 += 8) {
-                float v[8][8];
-                read_accs(tmem, 32 * qd, c0, v);
-#pragma unroll
-                for (int t = 0; t < 8; ++t) {
-                    const int i = c0 + t;
-                    const int64_t row = r0 + i;
-                    if (row >= rows) continue;
-                    float d[8];
-#pragma unroll
-                    for (int a = 0; a < 8; ++a) d[a] = v[a][t];
-                    M[row + (int64_t)jj * ld] = combine8(d, (Erow[i] < -1000 ? 0 : Erow[i]) + Fcol[j]);
-                }
-            }
-        }
-        fence_before();
-        __syncthreads();
-        fence_after();
     }
-    if (s_fail && tid == 0 && status) atomicExch(status, HSVD_ERR_CUDA);
+    __syncthreads();
+    if (s_fail && tid == 0) {
+        // let copies and products already issued finish (bounded) before TMEM is freed
+        if (issued_a >= 0) mbar_wait(&mbar_a[issued_a & 1], (uint32_t)((issued_a >> 1) & 1), kWaitIter);
+        if (issued_m >= 0) mbar_wait(&mbar_m[issued_m & 1], (uint32_t)((issued_m >> 1) & 1), kWaitIter);
+        if (status) atomicExch(status, HSVD_ERR_CUDA);
+    }
     fence_before();
     __syncthreads();
     fence_after();
@@ -354,7 +475,7 @@ int precision_gram_ksplit(int64_t rows) { return (int)((rows + kGramK - 1) / kGr
 cudaError_t launch_gram_x(const double *G, int64_t rows, int64_t ldg, int npairs, const int *col0, double *part,
                           int *status, cudaStream_t st) {
     const int ksplit = precision_gram_ksplit(rows);
-    const size_t smem = (size_t)kSlices * NNX * kGramKT * 2;
+    const size_t smem = (size_t)2 * kSlices * NNX * kGramKT * 2;  // two tiles
     cudaError_t e = cudaFuncSetAttribute(k_gram_x, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_gram_x<<<npairs * ksplit * 2, kThrX, smem, st>>>(G, rows, ldg, col0, ksplit, part, status);
@@ -375,10 +496,10 @@ cudaError_t launch_wprep_x(int npairs, const double *Wp, const int *dexp, const 
 cudaError_t launch_update_x(double *X, int64_t rowsX, int64_t ldx, double *Y, int64_t rowsY, int64_t ldy,
                             int npairs, const int *col0, const uint16_t *wsl, const int *wexp, const int *dexp,
                             const int *rotated, int *status, cudaStream_t st) {
-    // 96 KB of operands, requested as 120 KB so that two CTAs never share an
-    // SM: each holds all 512 TMEM columns for its whole life
-    const size_t smem = (size_t)120 * 1024;
-    static_assert((size_t)kSlices * (NNX + kUpdRows) * kUpdKT * 2 <= (size_t)120 * 1024, "update smem");
+    // two A tiles (2 x 64 KB) and two B tiles (2 x 32 KB): one CTA per SM, each
+    // holding all 512 TMEM columns for its whole life
+    const size_t smem = (size_t)2 * kSlices * (NNX + kUpdRows) * kUpdKT * 2;
+    static_assert((size_t)2 * kSlices * (NNX + kUpdRows) * kUpdKT * 2 <= (size_t)200 * 1024, "update smem");
     cudaError_t e = cudaFuncSetAttribute(k_update_x, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 152;

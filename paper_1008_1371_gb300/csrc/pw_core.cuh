@@ -1,0 +1,273 @@
+// pw_core.cuh -- the per-factor body of the pointwise one-sided hyperbolic
+// Jacobi method (Sec. 2, Alg. 4.5), shared by the single-factor kernel
+// (pointwise.cu) and the persistent batched kernel (batched.cu).
+//
+// A group of NT threads (a whole CTA, or an aligned part of one that
+// synchronises on its own named barrier `bar`) owns one factor for all sweeps.  G (column-major, rows
+// padded to a multiple of 32) and the accumulated transformation W (the paper's
+// V^{-T}, Eq. 2.1) sit wherever the caller put them: shared memory when they
+// fit, otherwise global memory (L2-resident at these sizes).  A step of the
+// modified modulus strategy (Sec. 2) has n'/2 disjoint pairs; warp w takes
+// pairs w, w + NT/32, ...  For each pair the warp recomputes a_ii, a_jj, a_ij
+// from the current columns (lane l owns rows l, l+32, ...; xor-butterfly
+// reduction, so every lane holds the same sums), applies the test of Eq. 2.3,
+// computes (t, c) redundantly in all lanes (uniform control flow, no divergence
+// between the two rotation kinds inside a warp) and updates its two columns of
+// G and of W with the FMA form of Alg. 4.5.  One group barrier separates
+// steps.  The convergence check is a shared counter (the bit-or reduction of
+// Eq. 4.2 collapses to "any rotation in this sweep"), so no host round trip is
+// needed between sweeps.
+//
+// Columns are never moved: positions map to columns through pos[] (Sec. 4).
+// Before the first sweep positions are grouped J+ then J- (Alg. 4.2 assumes
+// J = diag(I_p, -I_{n-p})); with sorting on they are then ordered by
+// d = ||g||^2, decreasing in the J+ part and increasing in the J- part, ties in
+// current order (Sec. 4, Sort_Diagonal), again after every sweep.  An odd n is
+// bordered with one unit column in a fresh row (Eq. 4.1).
+#pragma once
+
+#include "hsvd_internal.cuh"
+
+namespace hsvd {
+
+// the factor's working arrays: G (m_pad x n_pad), W (n_pad x n_pad), and the
+// per-column arrays d (doubles), pos, newpos, sg (ints), all n_pad long
+struct PwArrays {
+    double *G;
+    double *W;
+    double *d;
+    int *pos;
+    int *newpos;
+    int *sg;
+};
+
+// barrier of a group of NT threads (NT a multiple of 32; id 0 with NT equal
+// to the CTA size is __syncthreads)
+template <int NT>
+__device__ __forceinline__ void grp_sync(int bar) {
+    asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(NT) : "memory");
+}
+
+// shared scalars of a group
+struct PwScalars {
+    int rot, err, bad;
+    unsigned long long total;
+};
+
+template <int NT>
+__device__ void pw_reorder(const PwArrays &sh, int m_pad, int n_pad, int use_d, int bar) {
+    constexpr int kW = NT / kWarp;
+    const int tid = threadIdx.x & (NT - 1), lane = tid & 31, warp = tid >> 5;
+    if (use_d) {
+        for (int j = warp; j < n_pad; j += kW) {
+            const double *g = sh.G + (size_t)j * m_pad;
+            double s = 0.0;
+            for (int i = lane; i < m_pad; i += kWarp) s = fma(g[i], g[i], s);
+            s = warp_sum(s);
+            if (lane == 0) sh.d[j] = s;
+        }
+    }
+    grp_sync<NT>(bar);
+    int nplus = 0;
+    for (int a = 0; a < n_pad; ++a) nplus += sh.sg[sh.pos[a]] > 0;
+    for (int a = tid; a < n_pad; a += NT) {
+        const int col = sh.pos[a];
+        const int grp = sh.sg[col];
+        const double key = use_d ? sh.d[col] : 0.0;
+        int rank = 0;
+        for (int b = 0; b < n_pad; ++b) {
+            const int cb = sh.pos[b];
+            if (sh.sg[cb] != grp || b == a) continue;
+            const double kb = use_d ? sh.d[cb] : 0.0;
+            const bool before = (grp > 0) ? (kb > key) : (kb < key);
+            if (before || (kb == key && b < a)) ++rank;
+        }
+        sh.newpos[(grp > 0 ? 0 : nplus) + rank] = col;
+    }
+    grp_sync<NT>(bar);
+    for (int a = tid; a < n_pad; a += NT) sh.pos[a] = sh.newpos[a];
+    grp_sync<NT>(bar);
+}
+
+// Solves one factor; every thread of the group calls it.  Writes status, sweeps
+// and the rotation count through out_status / out_sweeps / out_rot (thread 0).
+template <int NT>
+__device__ void pw_solve(const double *__restrict__ G, int64_t ldg, int m, int n, const int8_t *__restrict__ J,
+                         int m_pad, int n_pad, double tol, int max_sweeps, int sort, const PwArrays &sh,
+                         PwScalars &sc, double *__restrict__ sigma, double *__restrict__ U, int64_t ldu,
+                         double *__restrict__ V, int64_t ldv, int *out_status, int *out_sweeps,
+                         long long *out_rot, int bar) {
+    constexpr int kW = NT / kWarp;
+    const int tid = threadIdx.x & (NT - 1), lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        sc.rot = 0;
+        sc.err = 0;
+        sc.bad = 0;
+        sc.total = 0;
+    }
+    grp_sync<NT>(bar);
+
+    // load and border (Eq. 4.1): pad columns are unit vectors in fresh rows
+    int bad = 0;
+    for (int j = warp; j < n_pad; j += kW) {
+        double *g = sh.G + (size_t)j * m_pad;
+        for (int i = lane; i < m_pad; i += kWarp) {
+            double v = 0.0;
+            if (j < n) {
+                if (i < m) v = G[i + (int64_t)j * ldg];
+            } else if (i == m + (j - n)) {
+                v = 1.0;
+            }
+            bad |= !isfinite(v);
+            g[i] = v;
+        }
+    }
+    for (int64_t e = tid; e < (int64_t)n_pad * n_pad; e += NT) {
+        const int64_t i = e % n_pad, j = e / n_pad;
+        sh.W[e] = (i == j) ? 1.0 : 0.0;
+    }
+    if (bad) atomicOr(&sc.bad, 1);
+    for (int j = tid; j < n_pad; j += NT) {
+        const int sj = (j < n) ? (int)J[j] : 1;
+        sh.sg[j] = sj > 0 ? 1 : -1;
+        if (sj != 1 && sj != -1) atomicOr(&sc.bad, 2);
+    }
+    grp_sync<NT>(bar);
+    if (sc.bad) {
+        const int b = sc.bad;
+        grp_sync<NT>(bar);
+        if (tid == 0) {
+            *out_status = (b & 2) ? HSVD_ERR_ARG : HSVD_ERR_NONFINITE;
+            *out_sweeps = 0;
+            *out_rot = 0;
+        }
+        return;
+    }
+    // initial positions: J+ columns in index order, then J- columns
+    for (int j = tid; j < n_pad; j += NT) {
+        int before = 0;
+        for (int i = 0; i < j; ++i) before += (sh.sg[i] > 0) == (sh.sg[j] > 0);
+        int nplus = 0;
+        if (sh.sg[j] < 0)
+            for (int i = 0; i < n_pad; ++i) nplus += sh.sg[i] > 0;
+        sh.pos[(sh.sg[j] > 0 ? 0 : nplus) + before] = j;
+    }
+    grp_sync<NT>(bar);
+    if (sort) pw_reorder<NT>(sh, m_pad, n_pad, 1, bar);
+
+    long long rot_total = 0;
+    int sweep = 0, status = HSVD_NOT_CONVERGED;
+    const int half = n_pad / 2;
+    for (sweep = 1; sweep <= max_sweeps; ++sweep) {
+        for (int s = 0; s < n_pad; ++s) {
+            for (int k = warp; k < half; k += kW) {
+                int a, b;
+                modulus_pair(n_pad, s, k, a, b);
+                const int p = sh.pos[a], q = sh.pos[b];
+                double *gp = sh.G + (size_t)p * m_pad, *gq = sh.G + (size_t)q * m_pad;
+                double app = 0.0, aqq = 0.0, apq = 0.0;
+                for (int i = lane; i < m_pad; i += kWarp) {
+                    const double x = gp[i], y = gq[i];
+                    app = fma(x, x, app);
+                    aqq = fma(y, y, aqq);
+                    apq = fma(x, y, apq);
+                }
+                app = warp_sum(app);
+                aqq = warp_sum(aqq);
+                apq = warp_sum(apq);
+                if (pair_passes(app, aqq, apq, tol)) continue;
+                const int hyp = (sh.sg[p] == sh.sg[q]) ? -1 : 1;
+                double t, c;
+                if (!rotation_params(app, aqq, apq, hyp, t, c)) {
+                    if (lane == 0) atomicExch(&sc.err, HSVD_ERR_RANK);
+                    continue;
+                }
+                const double ht = hyp < 0 ? -t : t;
+                for (int i = lane; i < m_pad; i += kWarp) {
+                    const double x = gp[i], y = gq[i];
+                    gp[i] = fma(ht, y, x) * c;
+                    gq[i] = fma(t, x, y) * c;
+                }
+                double *wp = sh.W + (size_t)p * n_pad, *wq = sh.W + (size_t)q * n_pad;
+                for (int i = lane; i < n_pad; i += kWarp) {
+                    const double x = wp[i], y = wq[i];
+                    wp[i] = fma(ht, y, x) * c;
+                    wq[i] = fma(t, x, y) * c;
+                }
+                if (lane == 0) {
+                    atomicAdd(&sc.rot, 1);
+                    ++rot_total;
+                }
+            }
+            grp_sync<NT>(bar);
+            if (sc.err) break;
+        }
+        if (sc.err) {
+            status = sc.err;
+            break;
+        }
+        const int nrot = sc.rot;
+        grp_sync<NT>(bar);
+        if (tid == 0) sc.rot = 0;
+        if (nrot == 0) {
+            status = HSVD_OK;
+            break;
+        }
+        if (sort) pw_reorder<NT>(sh, m_pad, n_pad, 1, bar);
+        else grp_sync<NT>(bar);
+    }
+    if (sweep > max_sweeps) sweep = max_sweeps;
+    grp_sync<NT>(bar);
+
+    // finalisation (Sec. 2): sigma_j = ||g_j||, u_j = g_j / sigma_j, V = W
+    if (status == HSVD_OK || status == HSVD_NOT_CONVERGED) {
+        for (int j = warp; j < n; j += kW) {
+            const double *g = sh.G + (size_t)j * m_pad;
+            double mx = 0.0;
+            for (int i = lane; i < m; i += kWarp) mx = fmax(mx, fabs(g[i]));
+            mx = warp_max(mx);
+            int e;
+            const double scl = pow2_scale_for(mx, e);
+            double ss = 0.0;
+            for (int i = lane; i < m; i += kWarp) {
+                const double v = g[i] * scl;
+                ss = fma(v, v, ss);
+            }
+            ss = warp_sum(ss);
+            const double sj = ldexp(sqrt(ss), e);
+            if (lane == 0) {
+                sigma[j] = sj;
+                if (!(sj > 0.0)) atomicExch(&sc.err, HSVD_ERR_RANK);
+                if (!isfinite(sj)) atomicExch(&sc.err, HSVD_ERR_NONFINITE);
+            }
+            if (U)
+                for (int i = lane; i < m; i += kWarp) U[i + (int64_t)j * ldu] = g[i] / sj;
+            if (V)
+                for (int i = lane; i < n; i += kWarp) V[i + (int64_t)j * ldv] = sh.W[i + (size_t)j * n_pad];
+        }
+        grp_sync<NT>(bar);
+        if (sc.err) status = sc.err;
+    }
+    if (lane == 0 && rot_total) atomicAdd(&sc.total, (unsigned long long)rot_total);
+    grp_sync<NT>(bar);
+    if (tid == 0) {
+        *out_status = status;
+        *out_sweeps = sweep;
+        *out_rot = (long long)sc.total;
+    }
+    grp_sync<NT>(bar);
+}
+
+// rows of G's working copy: m plus the bordering row of an odd n, rounded up to 32
+__host__ __device__ inline int pw_rows_pad(int64_t m, int64_t n) {
+    const int64_t n_pad = n + (n & 1);
+    const int64_t rows = m + (n_pad - n);
+    return (int)((rows + 31) / 32 * 32);
+}
+
+// shared bytes of the per-column arrays (d, pos, newpos, sg)
+__host__ __device__ inline size_t pw_aux_bytes(int64_t n_pad) {
+    return (size_t)n_pad * (sizeof(double) + 3 * sizeof(int));
+}
+
+}  // namespace hsvd

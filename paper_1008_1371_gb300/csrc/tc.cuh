@@ -122,14 +122,55 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
     for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// 8 TMEM columns without the wait: the caller issues tmem_wait_ld() and then
+// reg_dep8() on every destination before using it (the empty asm makes the
+// uses depend on the wait)
+__device__ __forceinline__ void tmem_ld8_raw(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void reg_dep8(uint32_t (&r)[8]) {
+    asm volatile("" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]));
+}
+
+// ---- thread-block clusters -------------------------------------------------------
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// address of the same shared-memory location in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t map_peer(uint32_t saddr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void st_cluster_u32(uint32_t caddr, uint32_t v) {
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(caddr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_cluster_s32(uint32_t caddr, int v) {
+    asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(caddr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_cluster() {
+    asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
+}
+
 // ---- split precision ---------------------------------------------------------
 // A finite double x with |x| < 2^E is cut into kSlices balanced base-128 digits:
-//   x 2^-E ~ V 2^-55,  V = trunc(x 2^(55-E)),  V = sum_k q_k 128^(8-k),
-//   q_k in [-64, 64],  so  x 2^-E = sum_k q_k 2^(-6-7(k-1)) + r,  |r| < 2^-55.
-// The digits come from x's integer mantissa (integer arithmetic only: the FP64
-// pipe of this GPU is narrow).  Slice k is the BF16 number q_k 2^(-6-7(k-1)),
-// exact (|q_k| <= 64 has at most 7 significant bits).
+//   x 2^-E ~ V 2^-55,  V = trunc(x 2^(55-E)),  |V| < 2^55,
+//   V = sum_k q_k 128^(8-k),  q_2..q_8 in [-64, 63],  q_1 in [-64, 64],
+//   so  x 2^-E = sum_k q_k 2^(1-7k) + r,  |r| < 2^-55.
+// The digits need no carry loop: W = V + B with B = 64 sum_{j<7} 128^j has
+// plain base-128 digits q_k + 64 in its low 49 bits and q_1 = floor(W / 2^49).
+// Integer arithmetic only (the FP64 pipe of this GPU is narrow).  Slice k is
+// the BF16 number q_k 2^(1-7k), exact (|q_k| <= 64).
 constexpr int kSlices = 8;
+constexpr long long kDigitBias = 64LL * 4432676798593LL;  // 64 (128^7 - 1) / 127
 
 // exponent E with |x| < 2^E for a finite nonzero x (E = ilogb(x) + 1); zero and
 // subnormals give a very small value
@@ -138,19 +179,8 @@ __device__ __forceinline__ int exp_bound(double x) {
     return ex == 0 ? -2000 : ex - 1022;
 }
 
-// BF16 bits of q 2^(-6-7(k-1)), |q| <= 64
-__device__ __forceinline__ uint16_t digit_bits(int q, int k) {
-    if (!q) return 0;
-    const uint32_t sign = q < 0 ? 0x8000u : 0u;
-    const uint32_t a = (uint32_t)(q < 0 ? -q : q);
-    const int msb = 31 - __clz((int)a);
-    const uint32_t biased = (uint32_t)(msb - 6 - 7 * (k - 1) + 127);
-    const uint32_t mant = (a << (7 - msb)) & 0x7Fu;
-    return (uint16_t)(sign | (biased << 7) | mant);
-}
-
-// slices of x 2^-E (the caller guarantees |x| < 2^E); out[k-1] = slice k
-__device__ __forceinline__ void split_slices(double x, int E, uint16_t (&out)[kSlices]) {
+// W = V + B for x 2^-E (the caller guarantees |x| < 2^E)
+__device__ __forceinline__ long long digit_word(double x, int E) {
     const uint64_t b = (uint64_t)__double_as_longlong(x);
     const int ex = (int)((b >> 52) & 0x7FF);
     long long V = 0;
@@ -162,29 +192,68 @@ __device__ __forceinline__ void split_slices(double x, int E, uint16_t (&out)[kS
         else if (sh > -64) F = M >> (-sh);
         V = (b >> 63) ? -(long long)F : (long long)F;
     }
-#pragma unroll
-    for (int k = kSlices; k >= 2; --k) {
-        int d = (int)(V & 127);
-        if (d >= 64) d -= 128;
-        V = (V - d) >> 7;
-        out[k - 1] = digit_bits(d, k);
-    }
-    out[0] = digit_bits((int)V, 1);
+    return V + kDigitBias;
+}
+
+// BF16 bits of slice k (1-based) of a digit word: q is formed exactly with the
+// 1.5 * 2^23 magic number, then scaled by 2^(1-7k)
+__device__ __forceinline__ uint32_t slice_bits(long long W, int k) {
+    const int q = k == 1 ? (int)(W >> 49) : (int)((W >> (7 * (kSlices - k))) & 127) - 64;
+    const float f = (__int_as_float(0x4B400000 + q) - 12582912.0f) * __int_as_float((128 - 7 * k) << 23);
+    return __float_as_uint(f) >> 16;
+}
+
+// two slices (k of elements lo and hi, adjacent along K) as one 32-bit word
+__device__ __forceinline__ uint32_t slice_pair(long long Wlo, long long Whi, int k) {
+    return slice_bits(Wlo, k) | (slice_bits(Whi, k) << 16);
 }
 
 // Products S_a S_b with a + b = d (d = 2..9) accumulate in accumulator d - 2:
-// integers in units 2^(-12-7(d-2)) of at most K (d-1) 2^12 <= 2^24 for
-// K <= 512, exact in FP32.  Recombination: H = sum_{d<=5} I_d 2^(7(5-d)) (units
-// 2^-33), L = sum_{d>=6} I_d 2^(7(9-d)) (units 2^-61), both exact in 64-bit
-// integers and in FP64; value = 2^-61 (H 2^28 + L) 2^escale with one rounding.
+// integers in units 2^(2-7d) of magnitude at most K (d-1) 2^12 <= 2^24 for
+// K <= 512, exact in FP32.  Recombination in integers: H = sum_{d<=5} I_d
+// 2^(7(5-d)) (units 2^-33), L = sum_{d>=6} I_d 2^(7(9-d)) (units 2^-61),
+// T = H 2^28 + L exactly (128 bits), value = T 2^(escale-61) rounded once to
+// nearest even.  No FP64 instruction on the normal-range path.
 __device__ __forceinline__ double combine8(const float (&d)[8], int escale) {
     long long I[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) I[k] = __float2ll_rn(ldexpf(d[k], 12 + 7 * k));
+    for (int k = 0; k < 8; ++k) I[k] = (long long)__float2int_rn(d[k] * __int_as_float((127 + 12 + 7 * k) << 23));
     const long long H = (I[0] << 21) + (I[1] << 14) + (I[2] << 7) + I[3];
     const long long L = (I[4] << 21) + (I[5] << 14) + (I[6] << 7) + I[7];
-    const double v = fma((double)H, 268435456.0, (double)L);
-    return ldexp(v, escale - 61);
+    // T = H 2^28 + L as hi:lo (two's complement, 128 bits)
+    const unsigned long long lo = ((unsigned long long)H << 28) + (unsigned long long)L;
+    const long long carry = (unsigned long long)lo < ((unsigned long long)H << 28) ? 1 : 0;
+    const long long hi = (H >> 36) + (L >> 63) + carry;
+    if (hi == 0 && lo == 0) return 0.0;
+    const bool neg = hi < 0;
+    unsigned long long ahi = (unsigned long long)hi, alo = lo;
+    if (neg) {  // |T|
+        alo = ~alo + 1ull;
+        ahi = ~ahi + (alo == 0 ? 1ull : 0ull);
+    }
+    // most significant bit position of |T| (< 75)
+    const int msb = ahi ? 127 - __clzll((long long)ahi) : 63 - __clzll((long long)alo);
+    unsigned long long mant;
+    int e2 = msb;
+    if (msb <= 52) {
+        mant = alo << (52 - msb);
+    } else {
+        const int sh = msb - 52;  // 1..22: |T| < 2^75
+        const unsigned long long keep = (alo >> sh) | (ahi << (64 - sh));
+        const unsigned long long rem = alo & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+        mant = keep + ((rem > half || (rem == half && (keep & 1ull))) ? 1ull : 0ull);
+        if (mant >> 53) {
+            mant >>= 1;
+            ++e2;
+        }
+    }
+    const int biased = e2 + escale - 61 + 1023;
+    if (biased <= 0 || biased >= 2047) {  // outside the normal range: FP64 arithmetic
+        const double v = ldexp((double)mant, e2 - 52);
+        return ldexp(neg ? -v : v, escale - 61);
+    }
+    return __longlong_as_double((long long)((neg ? (1ull << 63) : 0ull) | ((unsigned long long)biased << 52) |
+                                            (mant & 0xFFFFFFFFFFFFFull)));
 }
 
 }  // namespace tc

@@ -75,3 +75,29 @@ def test_argument_errors_without_gpu(api):
     assert L.hsvd_solve_ex(p(G), 4, 4, 4, p(J), p(s), None, 4, None, 4, ctypes.byref(o), ctypes.byref(info),
                            None) == api.HSVD_ERR_ARG
     assert info.status == api.HSVD_ERR_ARG
+
+
+def test_batched_argument_errors_without_gpu(api):
+    L = api.lib()
+    G = np.zeros((4, 4))
+    J = np.ones(4, dtype=np.int8)
+    s = np.zeros(4)
+    arr = lambda *a: (ctypes.c_void_p * len(a))(*[x.ctypes.data for x in a])  # noqa: E731
+    i64 = lambda *a: (ctypes.c_int64 * len(a))(*a)  # noqa: E731
+    o = api.make_batch_opts()
+    # negative count
+    assert L.hsvd_solve_batched_ex(-1, None, None, None, None, None, None, None, None, None, None,
+                                   ctypes.byref(o), None, None) == api.HSVD_ERR_ARG
+    # m < n, then ldg < m
+    assert L.hsvd_solve_batched_ex(1, arr(G), i64(3), i64(4), i64(4), arr(J), arr(s), None, None, None, None,
+                                   ctypes.byref(o), None, None) == api.HSVD_ERR_ARG
+    assert L.hsvd_solve_batched_ex(1, arr(G), i64(4), i64(4), i64(3), arr(J), arr(s), None, None, None, None,
+                                   ctypes.byref(o), None, None) == api.HSVD_ERR_ARG
+    # bad group width, reserved field set
+    o2 = api.make_batch_opts(group_width=384)
+    assert L.hsvd_solve_batched_ex(1, arr(G), i64(4), i64(4), i64(4), arr(J), arr(s), None, None, None, None,
+                                   ctypes.byref(o2), None, None) == api.HSVD_ERR_ARG
+    o3 = api.make_batch_opts()
+    o3.reserved[1] = 7
+    assert L.hsvd_solve_batched_ex(1, arr(G), i64(4), i64(4), i64(4), arr(J), arr(s), None, None, None, None,
+                                   ctypes.byref(o3), None, None) == api.HSVD_ERR_ARG
