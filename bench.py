@@ -47,6 +47,8 @@ WORKLOADS = {
     "graded1024": (1024, "graded 1024x1024 G=B diag(10^(-6i/n)), J=diag(+1x512,-1x512)", 32),
     "haar4096": (4096, "4096x4096 G=Q1 diag(sigma) Q2, Haar Q, sigma log-uniform [1e-6,1], 2048 random +1 in J", 64),
     "haar1024": (1024, "1024x1024 G=Q1 diag(sigma) Q2, Haar Q, sigma log-uniform [1e-6,1], 512 random +1 in J", 64),
+    "graded2048": (2048, "graded 2048x2048 G=B diag(10^(-6i/n)), J=diag(+1x1024,-1x1024)", 32),
+    "graded8192": (8192, "graded 8192x8192 G=B diag(10^(-8i/n)) (condition 1e8), J=diag(+1x4096,-1x4096)", 64),
     "batch10k": (256, "10000 independent square N(0,1) factors, n uniform on [16,256], m=n, random p in [0,n] "
                       "+1 signs at random positions (seed 4)", 1),
 }
@@ -57,6 +59,8 @@ def make_input(name, seed_offset=0):
     from paper_1008_1371_gb300 import workloads
 
     n = WORKLOADS[name][0]
+    if name == "graded8192":
+        return workloads.graded(n, decades=8.0, seed=5 + seed_offset)
     if name.startswith("graded"):
         return workloads.graded(n, decades=6.0, seed=2 + seed_offset)
     return workloads.haar(n, seed=3 + seed_offset)
@@ -77,8 +81,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="graded1024", choices=sorted(WORKLOADS))
-    ap.add_argument("--form", default="fp64", choices=["fp64", "bf16x8"],
-                    help="Gram/update arithmetic: FP64 FMA or BF16 slices on the tensor cores")
+    ap.add_argument("--form", default="fp64", choices=["fp64", "bf16x8", "learned", "learned-bf16x8"],
+                    help="Gram/update arithmetic (FP64 FMA or BF16 slices on the tensor cores), optionally "
+                         "with the learned skip network")
+    ap.add_argument("--tau", type=float, default=0.5, help="learned form: skip threshold on P(rotation)")
     ap.add_argument("--block", type=int, default=0, help="block width (0: the workload's)")
     return ap.parse_args()
 
@@ -358,8 +364,27 @@ def run_batched(args):
 
 
 def metric_name(form):
-    return ("HSVD effective TFLOP/s (%s, sigma rel-err <= 1e-12)"
-            % ("plain FP64" if form == "fp64" else "split-precision BF16x8 products"))
+    names = {"fp64": "plain FP64", "bf16x8": "split-precision BF16x8 products",
+             "learned": "learned skip network, FP64 products",
+             "learned-bf16x8": "learned skip network, BF16x8 products"}
+    return "HSVD effective TFLOP/s (%s, sigma rel-err <= 1e-12)" % names[form]
+
+
+def train_skip_model(block, prec, log):
+    """The learned form's network, trained on traces of the plain method on
+    graded factors of other seeds (1024 x 1024, decades 4, 6, 8), by the
+    library's own kernels; seeded, outside every timed region."""
+    from paper_1008_1371_gb300 import learn, workloads
+
+    t0 = time.perf_counter()
+    train_set = [workloads.graded(1024, decades=d, seed=s) for d, s in ((6.0, 100), (4.0, 101), (8.0, 102),
+                                                                         (6.0, 103))]
+    X, y = learn.collect(train_set, block_w=block, precision=prec)
+    params, losses = learn.train(X, y, steps=600, lr=3e-3, batch=4096, seed=0)
+    log.update({"train_rows": int(X.shape[0]), "train_positive_fraction": float(y.mean()),
+                "train_loss_first_last": [losses[0], losses[-1]], "train_s": time.perf_counter() - t0,
+                "train_set": "graded 1024x1024, decades 6/4/8/6, seeds 100-103, plain blocked traces"})
+    return params
 
 
 def run_reference_batched(args, oracle):
@@ -456,9 +481,12 @@ def main():
         dist.barrier()
     n, wdesc, wblock = WORKLOADS[args.workload]
     block = args.block or wblock
-    prec = api.HSVD_PRECISION_BF16X8 if args.form == "bf16x8" else api.HSVD_PRECISION_FP64
+    prec = api.HSVD_PRECISION_BF16X8 if args.form in ("bf16x8", "learned-bf16x8") else api.HSVD_PRECISION_FP64
     if prec == api.HSVD_PRECISION_BF16X8:
         block = 64
+    learned = args.form.startswith("learned")
+    learn_log = {}
+    skip_model = train_skip_model(block, prec, learn_log) if learned else None
     G_np, J_np = make_input(args.workload, seed_offset=rank)
     m = G_np.shape[0]
     tol = n * 2.0 ** -53
@@ -467,13 +495,32 @@ def main():
     sigma = torch.empty(n, dtype=torch.float64, device=dev)
     U = torch.empty((n, m), dtype=torch.float64, device=dev).t()
     V = torch.empty((n, n), dtype=torch.float64, device=dev).t()
-    opts = api.make_opts(tol=tol, max_sweeps=MAX_SWEEPS, method=api.HSVD_METHOD_BLOCKED, block_w=block,
-                         profile=True, precision=prec)
+    opts = api.make_opts(tol=tol, max_sweeps=MAX_SWEEPS * (2 if learned else 1), method=api.HSVD_METHOD_BLOCKED,
+                         block_w=block, profile=True, precision=prec, sort=False, skip_model=skip_model,
+                         skip_tau=args.tau)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
     stream = torch.cuda.current_stream(dev)
 
     def solve():
         return api.hsvd_solve_ex(G, J, opts, out=(sigma, U, V), stream=stream)
+
+    # the learned form is measured against the plain method on the same factor:
+    # one plain solve (after one warm-up), untimed in the step loop; its sweep
+    # count is the S of the effective flop count
+    plain = None
+    if learned:
+        popts = api.make_opts(tol=tol, max_sweeps=MAX_SWEEPS, method=api.HSVD_METHOD_BLOCKED, block_w=block,
+                              precision=prec, sort=False)
+        api.hsvd_solve_ex(G, J, popts, out=(sigma, U, V), stream=stream)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pr = api.hsvd_solve_ex(G, J, popts, out=(sigma, U, V), stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        plain = {"ms": e0.elapsed_time(e1), "sweeps": pr.sweeps, "pair_visits": pr.pair_visits,
+                 "sigma": sigma.clone()}
 
     for _ in range(args.warmup):
         solve()
@@ -504,8 +551,22 @@ def main():
     info = infos[-1]
     assert info.status == api.HSVD_OK, api.hsvd_status_string(info.status)
     sweeps = info.sweeps
-    eff_flops = sweeps * flops_per_sweep(m, n)
+    # S of the effective flop count: the plain run's sweeps (the learned form's
+    # own count includes its masked and judge sweeps)
+    s_eff = plain["sweeps"] if plain else sweeps
+    eff_flops = s_eff * flops_per_sweep(m, n)
+    vs_plain = None
+    if plain:
+        vs_plain = {"plain_ms": plain["ms"], "learned_ms": None, "plain_sweeps": plain["sweeps"],
+                    "learned_sweeps": sweeps, "masked_sweeps": info.masked_sweeps,
+                    "judge_sweeps": info.judge_sweeps, "plain_pair_visits": plain["pair_visits"],
+                    "learned_pair_visits": info.pair_visits,
+                    "max_rel_sigma_diff_vs_plain": float(((sigma - plain["sigma"]).abs() / plain["sigma"]).max()),
+                    "tau": args.tau, "training": learn_log}
     value = world * eff_flops / (ms * 1e-3) / 1e12
+    if vs_plain:
+        vs_plain["learned_ms"] = ms
+        vs_plain["speedup_vs_plain"] = plain["ms"] / ms
 
     # dominant kernel class by CUDA-event time over the timed steps
     tot = {k: sum(getattr(i, "ms_" + k) for i in infos) for k in ("gram", "solve", "update", "other")}
@@ -562,8 +623,9 @@ def main():
         sh = torch.empty(n, dtype=torch.float64).pin_memory()
         Uh = torch.empty((n, m), dtype=torch.float64).pin_memory().t()
         Vh = torch.empty((n, n), dtype=torch.float64).pin_memory().t()
-        opts_e2e = api.make_opts(tol=tol, max_sweeps=MAX_SWEEPS, method=api.HSVD_METHOD_BLOCKED, block_w=block,
-                                 precision=prec)
+        opts_e2e = api.make_opts(tol=tol, max_sweeps=MAX_SWEEPS * (2 if learned else 1),
+                                 method=api.HSVD_METHOD_BLOCKED, block_w=block, precision=prec, sort=False,
+                                 skip_model=skip_model, skip_tau=args.tau)
         api.hsvd_solve_ex(Gh, Jh, opts_e2e, out=(sh, Uh, Vh))
         e2e_t = []
         for _ in range(max(3, args.steps // 2)):
@@ -589,10 +651,11 @@ def main():
             "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": wdesc + ", blocked, b=%d, %s" % (block, args.form), "m": m, "n": n,
-                       "block_w": block, "form": args.form, "tol": tol, "sweeps": sweeps, "inner": "block-oriented",
+                       "block_w": block, "form": args.form, "tol": tol, "sweeps": sweeps, "sweeps_in_flop_count": s_eff,
+                       "inner": "block-oriented",
                        "sort": False, "l2": "flushed (256 MB write) between steps",
                        "parallelism": "replicas" if world > 1 else "single"},
-            "accuracy": accuracy,
+            "accuracy": accuracy, "learned_vs_plain": vs_plain,
             "gpu_launches": int(sum(i.kernel_launches for i in infos)),
             "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk.summary(),
         }

@@ -65,6 +65,14 @@ extern "C" {
 
 #define HSVD_SORT_AUTO (-1)
 
+/* Learned form: per-visit features and the MLP 8 -> 64 -> 64 -> 1 (ReLU, ReLU,
+ * logit).  Parameter vector (FP32 master values; weights are rounded to BF16
+ * where the network runs, accumulation is FP32): W1[64][8], b1[64],
+ * W2[64][64], b2[64], w3[64], b3. */
+#define HSVD_MLP_FEATURES 8
+#define HSVD_MLP_PARAMS 4801
+#define HSVD_TRACE_FIELDS 8
+
 /* Arithmetic of the blocked method's Gram and update products. */
 #define HSVD_PRECISION_FP64 0   /* FP64 FMA                                             */
 #define HSVD_PRECISION_BF16X8 1 /* split precision: each FP64 operand as 8 BF16 slices
@@ -88,6 +96,16 @@ typedef struct hsvd_opts {
                              pointwise method only                                     */
     int profile;          /* nonzero: time every kernel with CUDA events (hsvd_info)   */
     int precision;        /* HSVD_PRECISION_FP64 or HSVD_PRECISION_BF16X8              */
+    const float *skip_model; /* learned form (blocked method, sort = 0): HSVD_MLP_PARAMS
+                             floats, host or device; NULL = plain sweeps              */
+    double skip_tau;      /* learned form: a visit is skipped when the predicted
+                             probability that it rotates is below skip_tau; <= 0
+                             selects 0.5                                              */
+    float *trace_out;     /* blocked method, sort = 0: device array receiving training
+                             rows (HSVD_MLP_FEATURES features, then the label 1/0:
+                             the visit rotated) for every block-pair visit of every
+                             sweep after the first; NULL = none                       */
+    int64_t trace_cap;    /* rows available at trace_out                               */
     int reserved[6];      /* must be zero                                              */
 } hsvd_opts;
 
@@ -103,6 +121,11 @@ typedef struct hsvd_info {
     double ms_solve;      /*   kernels, the inner-solve kernels, the update kernels,    */
     double ms_update;     /*   and of everything else (bordering, reordering,           */
     double ms_other;      /*   finalisation; the pointwise kernel counts as "solve")   */
+    int64_t pair_visits;  /* blocked method: block-pair visits whose Gram was formed    */
+    int masked_sweeps;    /* learned form: sweeps run with a skip mask                  */
+    int judge_sweeps;     /* learned form: full sweeps run after a masked sweep without
+                             rotations                                                  */
+    int64_t trace_rows;   /* rows written to trace_out                                 */
 } hsvd_info;
 
 /* Fills *opts with the defaults (tol = n 2^-53 at call time, 30 sweeps, auto
@@ -281,6 +304,24 @@ int hsvd_solve_batched_ex(int64_t count, const double *const *G, const int64_t *
                           const int64_t *ldg, const int8_t *const *J, double *const *sigma, double *const *U,
                           double *const *V, int *sweeps, int *status, const hsvd_batch_opts *opts,
                           hsvd_batch_info *info, void *stream);
+
+/*
+ * Learned-form network kernels (device pointers, stream-ordered; the paper has
+ * no counterpart: the network and its features are this library's additions).
+ * hsvd_mlp_forward: logits[s] = net(X[s]) for n samples (X: n x 8 floats,
+ *   row-major).
+ * hsvd_mlp_grad: gradient of the mean binary cross-entropy with logits,
+ *   mean(softplus(z) - y z), with respect to the parameter vector (the BF16
+ *   rounding of the weights is treated as the identity); loss (device float,
+ *   may be NULL) receives the mean loss.  Deterministic: fixed summation order.
+ * hsvd_mlp_adam: one Adam step (Kingma and Ba) at step count t >= 1 on the
+ *   parameter vector with moment vectors m and v.
+ */
+int hsvd_mlp_forward(const float *params, const float *X, int64_t n, float *logits, void *stream);
+int hsvd_mlp_grad(const float *params, const float *X, const float *y, int64_t n, float *grad, float *loss,
+                  void *stream);
+int hsvd_mlp_adam(float *params, float *m, float *v, const float *grad, int t, float lr, float beta1, float beta2,
+                  float eps, void *stream);
 
 #ifdef __cplusplus
 }

@@ -43,16 +43,23 @@ _int = ctypes.c_int
 _dbl = ctypes.c_double
 
 
+HSVD_MLP_FEATURES = 8
+HSVD_MLP_PARAMS = 4801
+HSVD_TRACE_FIELDS = 8
+
+
 class HsvdOpts(ctypes.Structure):
     _fields_ = [("tol", _dbl), ("max_sweeps", _int), ("method", _int), ("block_w", _int),
                 ("inner_mode", _int), ("inner_max_passes", _int), ("sort", _int), ("profile", _int),
-                ("precision", _int), ("reserved", _int * 6)]
+                ("precision", _int), ("skip_model", _p), ("skip_tau", _dbl), ("trace_out", _p),
+                ("trace_cap", _i64), ("reserved", _int * 6)]
 
 
 class HsvdInfo(ctypes.Structure):
     _fields_ = [("sweeps", _int), ("method", _int), ("block_w", _int), ("status", _int),
                 ("rotations", _i64), ("pair_updates", _i64), ("kernel_launches", _i64),
-                ("ms_gram", _dbl), ("ms_solve", _dbl), ("ms_update", _dbl), ("ms_other", _dbl)]
+                ("ms_gram", _dbl), ("ms_solve", _dbl), ("ms_update", _dbl), ("ms_other", _dbl),
+                ("pair_visits", _i64), ("masked_sweeps", _int), ("judge_sweeps", _int), ("trace_rows", _i64)]
 
 
 class HsvdBatchOpts(ctypes.Structure):
@@ -102,6 +109,13 @@ def lib():
             L.hsvd_pivot_gram_x.restype = _int
             L.hsvd_pivot_update_x.argtypes = [_p, _i64, _i64, _int, _p, _p, _p, _p, _p]
             L.hsvd_pivot_update_x.restype = _int
+            L.hsvd_mlp_forward.argtypes = [_p, _p, _i64, _p, _p]
+            L.hsvd_mlp_forward.restype = _int
+            L.hsvd_mlp_grad.argtypes = [_p, _p, _p, _i64, _p, _p, _p]
+            L.hsvd_mlp_grad.restype = _int
+            L.hsvd_mlp_adam.argtypes = [_p, _p, _p, _p, _int, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                        ctypes.c_float, _p]
+            L.hsvd_mlp_adam.restype = _int
             L.hsvd_default_batch_opts.argtypes = [ctypes.POINTER(HsvdBatchOpts)]
             L.hsvd_default_batch_opts.restype = None
             L.hsvd_solve_batched.argtypes = [_i64, _p, _p, _p, _p, _p, _dbl, _int, _p, _p, _p, _p, _p, _p]
@@ -155,15 +169,23 @@ class HsvdResult:
     ms_solve: float = 0.0
     ms_update: float = 0.0
     ms_other: float = 0.0
+    pair_visits: int = 0
+    masked_sweeps: int = 0
+    judge_sweeps: int = 0
+    trace_rows: int = 0
 
 
 HSVD_SORT_AUTO = -1
 
 
 def make_opts(tol=0.0, max_sweeps=30, method=HSVD_METHOD_AUTO, block_w=0, inner_mode=HSVD_INNER_ORIENTED,
-              inner_max_passes=8, sort=None, profile=False, precision=HSVD_PRECISION_FP64):
+              inner_max_passes=8, sort=None, profile=False, precision=HSVD_PRECISION_FP64, skip_model=None,
+              skip_tau=0.0, trace_out=None):
     """Options record; ``sort=None`` lets the library choose (sorting for the
-    pointwise method only)."""
+    pointwise method only).  ``skip_model``: a float32 tensor of
+    HSVD_MLP_PARAMS values (the learned form); ``trace_out``: a CUDA float32
+    tensor of shape (rows, 9) receiving training rows.  The caller keeps both
+    tensors alive while the options are in use."""
     o = HsvdOpts()
     lib().hsvd_default_opts(ctypes.byref(o))
     o.tol = float(tol)
@@ -175,6 +197,17 @@ def make_opts(tol=0.0, max_sweeps=30, method=HSVD_METHOD_AUTO, block_w=0, inner_
     o.sort = HSVD_SORT_AUTO if sort is None else (1 if sort else 0)
     o.profile = 1 if profile else 0
     o.precision = int(precision)
+    if skip_model is not None:
+        if skip_model.dtype != torch.float32 or skip_model.numel() != HSVD_MLP_PARAMS or not skip_model.is_contiguous():
+            raise ValueError("skip_model: contiguous float32 tensor of %d values" % HSVD_MLP_PARAMS)
+        o.skip_model = skip_model.data_ptr()
+    o.skip_tau = float(skip_tau)
+    if trace_out is not None:
+        if trace_out.dtype != torch.float32 or trace_out.dim() != 2 or trace_out.shape[1] != HSVD_MLP_FEATURES + 1 \
+                or not trace_out.is_contiguous() or trace_out.device.type != "cuda":
+            raise ValueError("trace_out: contiguous CUDA float32 tensor of shape (rows, 9)")
+        o.trace_out = trace_out.data_ptr()
+        o.trace_cap = trace_out.shape[0]
     return o
 
 
@@ -210,7 +243,8 @@ def hsvd_solve_ex(G, J, opts=None, compute_u=True, compute_v=True, stream=None, 
     if check and st < 0:
         raise HsvdError(st)
     return HsvdResult(sigma, U, V, info.sweeps, st, info.method, info.block_w, info.rotations, info.pair_updates,
-                      info.kernel_launches, info.ms_gram, info.ms_solve, info.ms_update, info.ms_other)
+                      info.kernel_launches, info.ms_gram, info.ms_solve, info.ms_update, info.ms_other,
+                      info.pair_visits, info.masked_sweeps, info.judge_sweeps, info.trace_rows)
 
 
 def hsvd_solve(G, J, tol=0.0, max_sweeps=30, compute_u=True, compute_v=True, stream=None, check=True):
@@ -379,3 +413,47 @@ def hsvd_solve_batched(Gs, Js, opts=None, compute_u=True, compute_v=True, stream
     if check and rc < 0:
         raise HsvdError(rc)
     return HsvdBatchResult(sig, Us, Vs, list(sweeps)[:count], list(status)[:count], rc, info)
+
+
+def _f32_cuda(t, shape=None):
+    if t.dtype != torch.float32 or t.device.type != "cuda" or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA float32 tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError("expected shape %s, got %s" % (shape, tuple(t.shape)))
+    return t
+
+
+def hsvd_mlp_forward(params, X, stream=None):
+    """Logits of the learned-form network for the rows of X (n x 8)."""
+    _f32_cuda(params, (HSVD_MLP_PARAMS,))
+    _f32_cuda(X)
+    n = X.shape[0]
+    out = torch.empty(n, dtype=torch.float32, device=X.device)
+    rc = lib().hsvd_mlp_forward(params.data_ptr(), X.data_ptr(), n, out.data_ptr(), _stream_ptr(stream, X.device))
+    if rc != HSVD_OK:
+        raise HsvdError(rc)
+    return out
+
+
+def hsvd_mlp_grad(params, X, y, stream=None):
+    """(gradient, mean loss) of the mean binary cross-entropy with logits."""
+    _f32_cuda(params, (HSVD_MLP_PARAMS,))
+    _f32_cuda(X)
+    _f32_cuda(y, (X.shape[0],))
+    g = torch.empty(HSVD_MLP_PARAMS, dtype=torch.float32, device=X.device)
+    loss = torch.empty(1, dtype=torch.float32, device=X.device)
+    rc = lib().hsvd_mlp_grad(params.data_ptr(), X.data_ptr(), y.data_ptr(), X.shape[0], g.data_ptr(),
+                             loss.data_ptr(), _stream_ptr(stream, X.device))
+    if rc != HSVD_OK:
+        raise HsvdError(rc)
+    return g, loss
+
+
+def hsvd_mlp_adam(params, m, v, grad, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    """One Adam step on params (in place), moments m and v (in place)."""
+    for x in (params, m, v, grad):
+        _f32_cuda(x, (HSVD_MLP_PARAMS,))
+    rc = lib().hsvd_mlp_adam(params.data_ptr(), m.data_ptr(), v.data_ptr(), grad.data_ptr(), int(t), float(lr),
+                             float(beta1), float(beta2), float(eps), _stream_ptr(stream, params.device))
+    if rc != HSVD_OK:
+        raise HsvdError(rc)

@@ -6,6 +6,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
+#include <math.h>
 #include <vector>
 
 #include "hsvd_internal.cuh"
@@ -76,6 +78,8 @@ struct SweepStats {
     int sweeps = 0;
     long long rotations = 0, pair_updates = 0, launches = 0;
     double ms_gram = 0, ms_solve = 0, ms_update = 0, ms_other = 0;
+    long long pair_visits = 0, trace_rows = 0;
+    int masked_sweeps = 0, judge_sweeps = 0;
 };
 
 // CUDA events recorded as graph nodes around every kernel of a sweep when
@@ -107,10 +111,12 @@ struct GraphGuard {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int *h_cnt = nullptr;
+    int *h_tab = nullptr;
     ~GraphGuard() {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
         if (h_cnt) cudaFreeHost(h_cnt);
+        if (h_tab) cudaFreeHost(h_tab);
     }
 };
 
@@ -137,7 +143,12 @@ int solve_blocked_core(const double *G, int64_t m, int64_t n, int64_t ldg, const
     int *perm = ws.get<int>(n_pad), *perm_t = ws.get<int>(n_pad), *newpos = ws.get<int>(n_pad);
     int8_t *sgn = ws.get<int8_t>(n_pad), *sgn_t = ws.get<int8_t>(n_pad);
     double *d = ws.get<double>(n_pad);
-    double *part = ws.get<double>((size_t)npairs * 3 * nsplit * b * b);
+    // Gram partials: a step with np active pairs uses gram_nsplit(m_pad, np) row splits
+    int64_t part_items = 0;
+    for (int np = 1; np <= npairs; ++np)
+        part_items = std::max<int64_t>(part_items, (int64_t)np * gram_nsplit(m_pad, np));
+    double *part = ws.get<double>((size_t)part_items * 3 * b * b);
+    (void)nsplit;
     double *Wp = ws.get<double>((size_t)npairs * nn * nn);
     int *rotated = ws.get<int>(npairs);
     // counters: [0] status (int), [2..3] rotations (u64), [4..5] updated pairs (u64)
@@ -185,63 +196,189 @@ int solve_blocked_core(const double *G, int64_t m, int64_t n, int64_t ldg, const
     if (o.profile && !evs.create((size_t)nb * 4 + 2)) return HSVD_ERR_CUDA;
     const size_t evr = (size_t)nb * 4;
 
-    // one sweep as a graph: nb steps of (Gram, inner solve, update), then reorder
-    CKR(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
-    {
-        cudaError_t e = cudaMemsetAsync(cnt + 2, 0, 4 * sizeof(int), st);
+    // learned form and training export: one record per block-pair visit
+    const int nvis = nb * npairs;
+    const bool learned = o.skip_model != nullptr, export_rows = o.trace_out != nullptr;
+    float *trace = nullptr, *X = nullptr, *params = nullptr;
+    int8_t *skip = nullptr, *prev_skip = nullptr;
+    int *d_visit = nullptr, *d_tab_mask = nullptr, *d_visit_mask = nullptr;
+    int *h_tab = nullptr, *h_vis = nullptr;
+    int8_t *h_skip = nullptr;
+    if (learned || export_rows) {
+        trace = ws.get<float>((size_t)nvis * HSVD_TRACE_FIELDS);
+        X = ws.get<float>((size_t)nvis * HSVD_MLP_FEATURES);
+        d_visit = ws.get<int>(nvis);
+        prev_skip = ws.get<int8_t>(nvis);
+        if (!trace || !X || !d_visit || !prev_skip) return HSVD_ERR_NOMEM;
+        std::vector<int> ident((size_t)nvis);
+        for (int v = 0; v < nvis; ++v) ident[(size_t)v] = v;
+        CKR(cudaMemcpyAsync(d_visit, ident.data(), sizeof(int) * nvis, cudaMemcpyHostToDevice, st));
+        CKR(cudaMemsetAsync(trace, 0, sizeof(float) * nvis * HSVD_TRACE_FIELDS, st));
+        CKR(cudaMemsetAsync(prev_skip, 0, nvis, st));
+        CKR(cudaStreamSynchronize(st));
+    }
+    if (learned) {
+        params = ws.get<float>(HSVD_MLP_PARAMS);
+        skip = ws.get<int8_t>(nvis);
+        d_tab_mask = ws.get<int>((size_t)nvis * 2);
+        d_visit_mask = ws.get<int>(nvis);
+        if (!params || !skip || !d_tab_mask || !d_visit_mask) return HSVD_ERR_NOMEM;
+        CKR(cudaMemcpyAsync(params, o.skip_model, sizeof(float) * HSVD_MLP_PARAMS, cudaMemcpyDefault, st));
+        CKR(cudaMallocHost(&gg.h_tab, sizeof(int) * (size_t)nvis * 3 + nvis));
+        h_tab = gg.h_tab;
+        h_vis = h_tab + (size_t)nvis * 2;
+        h_skip = reinterpret_cast<int8_t *>(h_vis + nvis);
+    }
+    std::vector<int> outer_host;
+    if (learned) {
+        outer_host.resize((size_t)nb * npairs * 2);
+        CKR(cudaMemcpyAsync(outer_host.data(), d_tab_outer, sizeof(int) * outer_host.size(), cudaMemcpyDeviceToHost,
+                            st));
+        CKR(cudaStreamSynchronize(st));
+    }
+    const double tau = o.skip_tau > 0.0 ? o.skip_tau : 0.5;
+    const float logit_tau = (float)log(tau / (1.0 - tau));
+
+    // One sweep as a graph: for every step s with nact[s] > 0 pairs, whose first
+    // columns are tab + off[s] and visit indices vis + off[s]: Gram, inner
+    // solve, update; then the reordering and the read-back of the counters.
+    auto capture = [&](const int *tab, const int *vis, const std::vector<int> &nact, const std::vector<int> &off,
+                       cudaGraph_t *graph, long long *launches) -> cudaError_t {
+        cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
+        if (e != cudaSuccess) return e;
+        long long nl = 0;
+        e = cudaMemsetAsync(cnt + 2, 0, 4 * sizeof(int), st);
         for (int s = 0; s < nb && e == cudaSuccess; ++s) {
-            const int *col0 = d_tab_outer + (size_t)s * npairs * 2;
+            const int np = nact[(size_t)s];
+            if (np == 0) continue;
+            const int *col0 = tab + off[(size_t)s] * 2;
+            const int *vs = vis ? vis + off[(size_t)s] : nullptr;
+            const int ns = gram_nsplit(m_pad, np);
             const int mode = (o.inner_mode == HSVD_INNER_FULL) ? 0 : (s == 0 ? 2 : 1);
             e = evs.record(4 * s, st);
             if (e == cudaSuccess)
-                e = prec ? launch_gram_x(Gw, m_pad, m_pad, npairs, col0, part_x, cnt, st)
-                         : launch_gram(Gw, m_pad, m_pad, b, npairs, col0, nsplit, part, st);
+                e = prec ? launch_gram_x(Gw, m_pad, m_pad, np, col0, part_x, cnt, st)
+                         : launch_gram(Gw, m_pad, m_pad, b, np, col0, ns, part, st);
             if (e == cudaSuccess) e = evs.record(4 * s + 1, st);
             if (e == cudaSuccess)
-                e = prec ? launch_solve(b, npairs, part_x, ksplit_x, nullptr, sgn, col0, nullptr, tol, mode,
+                e = prec ? launch_solve(b, np, part_x, ksplit_x, nullptr, sgn, col0, nullptr, tol, mode,
                                         o.inner_max_passes, d_tab_full, d_tab_cross, Wp, rotated, rot_ctr, cnt, st,
-                                        1, dexp)
-                         : launch_solve(b, npairs, part, nsplit, nullptr, sgn, col0, nullptr, tol, mode,
-                                        o.inner_max_passes, d_tab_full, d_tab_cross, Wp, rotated, rot_ctr, cnt, st);
+                                        1, dexp, vs, vs ? trace : nullptr)
+                         : launch_solve(b, np, part, ns, nullptr, sgn, col0, nullptr, tol, mode,
+                                        o.inner_max_passes, d_tab_full, d_tab_cross, Wp, rotated, rot_ctr, cnt, st,
+                                        0, nullptr, vs, vs ? trace : nullptr);
             if (e == cudaSuccess) e = evs.record(4 * s + 2, st);
-            if (e == cudaSuccess && prec) e = launch_wprep_x(npairs, Wp, dexp, rotated, wsl, wexp, upd_ctr, st);
+            if (e == cudaSuccess && prec) e = launch_wprep_x(np, Wp, dexp, rotated, wsl, wexp, upd_ctr, st);
             if (e == cudaSuccess)
-                e = prec ? launch_update_x(Gw, m_pad, m_pad, Ww, ldw, ldw, npairs, col0, wsl, wexp, dexp, rotated,
-                                           cnt, st)
-                         : launch_update(Gw, m_pad, m_pad, Ww, ldw, ldw, b, npairs, col0, Wp, rotated, upd_ctr, st);
+                e = prec ? launch_update_x(Gw, m_pad, m_pad, Ww, ldw, ldw, np, col0, wsl, wexp, dexp, rotated, cnt,
+                                           st)
+                         : launch_update(Gw, m_pad, m_pad, Ww, ldw, ldw, b, np, col0, Wp, rotated, upd_ctr, st);
             if (e == cudaSuccess) e = evs.record(4 * s + 3, st);
+            nl += prec ? 4 : 3;
         }
         if (e == cudaSuccess) e = evs.record(evr, st);
         if (e == cudaSuccess)
             e = launch_reorder(Gw, Gt, m_pad, Ww, Wt, ldw, n_pad, perm, perm_t, sgn, sgn_t, d, newpos, o.sort, st);
         if (e == cudaSuccess) e = evs.record(evr + 1, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(h_cnt, cnt, 8 * sizeof(int), cudaMemcpyDeviceToHost, st);
-        const cudaError_t e2 = cudaStreamEndCapture(st, &gg.graph);
-        if (e != cudaSuccess || e2 != cudaSuccess) return HSVD_ERR_CUDA;
-    }
+        const cudaError_t e2 = cudaStreamEndCapture(st, graph);
+        *launches = nl + reorder_kernels;
+        return e != cudaSuccess ? e : e2;
+    };
+
+    std::vector<int> full_n((size_t)nb, npairs), full_off((size_t)nb);
+    for (int s = 0; s < nb; ++s) full_off[(size_t)s] = s * npairs;
+    long long full_launches = 0;
+    if (capture(d_tab_outer, d_visit, full_n, full_off, &gg.graph, &full_launches) != cudaSuccess)
+        return HSVD_ERR_CUDA;
     CKR(cudaGraphInstantiate(&gg.exec, gg.graph, 0));
+    // profiling spans every step, skipped ones included (they record nothing)
+    auto add_profile = [&](const std::vector<int> &nact) {
+        if (!o.profile) return;
+        for (int s = 0; s < nb; ++s) {
+            if (nact[(size_t)s] == 0) continue;
+            stats.ms_gram += evs.between(4 * s, 4 * s + 1);
+            stats.ms_solve += evs.between(4 * s + 1, 4 * s + 2);
+            stats.ms_update += evs.between(4 * s + 2, 4 * s + 3);
+        }
+        stats.ms_other += evs.between(evr, evr + 1);
+    };
+
     int status = HSVD_NOT_CONVERGED, sweep;
+    bool judge_next = false;  // the next sweep must be a full one
     for (sweep = 1; sweep <= o.max_sweeps; ++sweep) {
-        CKR(cudaGraphLaunch(gg.exec, st));
-        CKR(cudaStreamSynchronize(st));
+        const bool masked = learned && sweep >= 2 && !judge_next;
+        if ((masked || export_rows) && sweep >= 2) {
+            CKR(launch_features(trace, masked ? prev_skip : nullptr, d_tab_outer, nvis, b, nb, sweep, o.max_sweeps,
+                                tol, X, st));
+            stats.launches += 1;
+        }
         unsigned long long rots, upds;
+        if (masked) {
+            CKR(launch_mlp_infer(params, X, nvis, nullptr, skip, logit_tau, st));
+            CKR(cudaMemcpyAsync(h_skip, skip, nvis, cudaMemcpyDeviceToHost, st));
+            CKR(cudaMemcpyAsync(prev_skip, skip, nvis, cudaMemcpyDeviceToDevice, st));
+            CKR(cudaStreamSynchronize(st));
+            stats.launches += 1;
+            std::vector<int> nact((size_t)nb, 0), off((size_t)nb, 0);
+            int cur = 0;
+            for (int s = 0; s < nb; ++s) {
+                off[(size_t)s] = cur;
+                for (int k = 0; k < npairs; ++k) {
+                    const int v = s * npairs + k;
+                    if (h_skip[v]) continue;
+                    h_tab[2 * cur] = outer_host[2 * (size_t)v];
+                    h_tab[2 * cur + 1] = outer_host[2 * (size_t)v + 1];
+                    h_vis[cur] = v;
+                    ++cur;
+                }
+                nact[(size_t)s] = cur - off[(size_t)s];
+            }
+            stats.pair_visits += cur;
+            stats.masked_sweeps += 1;
+            CKR(cudaMemcpyAsync(d_tab_mask, h_tab, sizeof(int) * 2 * (size_t)std::max(cur, 1), cudaMemcpyHostToDevice,
+                                st));
+            CKR(cudaMemcpyAsync(d_visit_mask, h_vis, sizeof(int) * (size_t)std::max(cur, 1), cudaMemcpyHostToDevice,
+                                st));
+            GraphGuard mg;
+            long long ml = 0;
+            if (capture(d_tab_mask, d_visit_mask, nact, off, &mg.graph, &ml) != cudaSuccess) return HSVD_ERR_CUDA;
+            CKR(cudaGraphInstantiate(&mg.exec, mg.graph, 0));
+            CKR(cudaGraphLaunch(mg.exec, st));
+            CKR(cudaStreamSynchronize(st));
+            stats.launches += ml;
+            add_profile(nact);
+        } else {
+            if (learned && judge_next) stats.judge_sweeps += 1;
+            CKR(cudaGraphLaunch(gg.exec, st));
+            CKR(cudaStreamSynchronize(st));
+            stats.launches += full_launches;
+            stats.pair_visits += nvis;
+            add_profile(full_n);
+            if (learned) CKR(cudaMemsetAsync(prev_skip, 0, nvis, st));
+        }
         memcpy(&rots, h_cnt + 2, sizeof rots);
         memcpy(&upds, h_cnt + 4, sizeof upds);
         stats.rotations += (long long)rots;
         stats.pair_updates += (long long)upds;
         stats.sweeps = sweep;
-        stats.launches += (prec ? 4LL : 3LL) * nb + reorder_kernels;
-        if (o.profile) {
-            for (int s = 0; s < nb; ++s) {
-                stats.ms_gram += evs.between(4 * s, 4 * s + 1);
-                stats.ms_solve += evs.between(4 * s + 1, 4 * s + 2);
-                stats.ms_update += evs.between(4 * s + 2, 4 * s + 3);
-            }
-            stats.ms_other += evs.between(evr, evr + 1);
-        }
         if (h_cnt[0] != 0) { status = h_cnt[0]; break; }
-        if (rots == 0) { status = HSVD_OK; break; }
+        if (export_rows && sweep >= 2 && stats.trace_rows + nvis <= o.trace_cap) {
+            CKR(launch_export(X, trace, nvis, o.trace_out + (size_t)stats.trace_rows * (HSVD_MLP_FEATURES + 1), st));
+            stats.trace_rows += nvis;
+            stats.launches += 1;
+        }
+        if (rots == 0) {
+            if (masked) {
+                judge_next = true;  // a masked sweep never ends the iteration
+                continue;
+            }
+            status = HSVD_OK;
+            break;
+        }
+        judge_next = false;
     }
+    if (sweep > o.max_sweeps) sweep = o.max_sweeps;
     if (status == HSVD_OK || status == HSVD_NOT_CONVERGED) {
         CKR(cudaMemsetAsync(cnt, 0, sizeof(int), st));
         CKR(launch_finalize(Gw, m_pad, Ww, ldw, perm, n_pad, m, n, sigma, U, ldu, V, ldv, cnt, st));
@@ -269,6 +406,10 @@ int solve_blocked(const double *G, int64_t m, int64_t n, int64_t ldg, const int8
         info->ms_solve = stats.ms_solve;
         info->ms_update = stats.ms_update;
         info->ms_other = stats.ms_other;
+        info->pair_visits = stats.pair_visits;
+        info->masked_sweeps = stats.masked_sweeps;
+        info->judge_sweeps = stats.judge_sweeps;
+        info->trace_rows = stats.trace_rows;
     }
     return rc;
 }
@@ -395,6 +536,13 @@ int hsvd_solve_ex(const double *G, int64_t m, int64_t n, int64_t ldg, const int8
     // diagonal sorting pays for the pointwise method (Sec. 5, Table 5.3) but
     // costs sweeps in the blocked one (measured on the graded 1024 factor)
     if (o.sort == HSVD_SORT_AUTO) o.sort = (method == HSVD_METHOD_POINTWISE) ? 1 : 0;
+    // the learned form and the trace export follow block-pair visits across
+    // sweeps: blocked method without column reordering
+    if ((o.skip_model || o.trace_out) && (method != HSVD_METHOD_BLOCKED || o.sort != 0 ||
+                                          (o.trace_out && o.trace_cap < 1) || !(o.skip_tau < 1.0))) {
+        if (info) info->status = HSVD_ERR_ARG;
+        return HSVD_ERR_ARG;
+    }
     if (method == HSVD_METHOD_POINTWISE && !pointwise_fits(m, n)) {
         if (info) info->status = HSVD_ERR_ARG;
         return HSVD_ERR_ARG;

@@ -133,7 +133,15 @@ cudaError_t launch_solve(int b, int npairs, const double *part, int nsplit, doub
                          double tol, int mode, int max_passes, const int *tab_full,
                          const int *tab_cross, double *Wp, int *rotated,
                          unsigned long long *rot_count, int *status, cudaStream_t st,
-                         int full_part = 0, int *dexp = nullptr);
+                         int full_part = 0, int *dexp = nullptr, const int *visit = nullptr,
+                         float *trace = nullptr);
+
+// learned form (learned.cu)
+cudaError_t launch_features(const float *trace, const int8_t *prev_skip, const int *tab, int nvis, int b, int nb,
+                            int sweep, int max_sweeps, double tol, float *X, cudaStream_t st);
+cudaError_t launch_mlp_infer(const float *params, const float *X, int n, float *logits, int8_t *skip,
+                             float logit_tau, cudaStream_t st);
+cudaError_t launch_export(const float *X, const float *trace, int nvis, float *out, cudaStream_t st);
 cudaError_t launch_assemble(int b, int npairs, const double *part, int nsplit, double *A, cudaStream_t st);
 cudaError_t launch_update(double *X, int64_t rows, int64_t ldx, double *Y, int64_t rowsY,
                           int64_t ldy, int b, int npairs, const int *col0, const double *Wp,

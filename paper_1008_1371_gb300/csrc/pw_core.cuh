@@ -41,6 +41,60 @@ struct PwArrays {
     int *sg;
 };
 
+// a_pp, a_qq, a_pq of columns gp, gq (length len, a multiple of 32): lane l
+// sums rows l, l + 32, ... in order; four loads are issued ahead of their
+// FMAs so that columns in global memory stream (same arithmetic either way)
+__device__ __forceinline__ void pw_dots(const double *__restrict__ gp, const double *__restrict__ gq, int len,
+                                        int lane, double &app, double &aqq, double &apq) {
+    constexpr int U = 4;
+    int i = lane;
+    for (; i + (U - 1) * kWarp < len; i += U * kWarp) {
+        double x[U], y[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            x[u] = gp[i + u * kWarp];
+            y[u] = gq[i + u * kWarp];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            app = fma(x[u], x[u], app);
+            aqq = fma(y[u], y[u], aqq);
+            apq = fma(x[u], y[u], apq);
+        }
+    }
+    for (; i < len; i += kWarp) {
+        const double x = gp[i], y = gq[i];
+        app = fma(x, x, app);
+        aqq = fma(y, y, aqq);
+        apq = fma(x, y, apq);
+    }
+}
+
+// the column update of Alg. 4.5 on columns gp, gq (distinct), same loads-ahead scheme
+__device__ __forceinline__ void pw_rotate(double *__restrict__ gp, double *__restrict__ gq, int len, int lane,
+                                          double ht, double t, double c) {
+    constexpr int U = 4;
+    int i = lane;
+    for (; i + (U - 1) * kWarp < len; i += U * kWarp) {
+        double x[U], y[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            x[u] = gp[i + u * kWarp];
+            y[u] = gq[i + u * kWarp];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            gp[i + u * kWarp] = fma(ht, y[u], x[u]) * c;
+            gq[i + u * kWarp] = fma(t, x[u], y[u]) * c;
+        }
+    }
+    for (; i < len; i += kWarp) {
+        const double x = gp[i], y = gq[i];
+        gp[i] = fma(ht, y, x) * c;
+        gq[i] = fma(t, x, y) * c;
+    }
+}
+
 // barrier of a group of NT threads (NT a multiple of 32; id 0 with NT equal
 // to the CTA size is __syncthreads)
 template <int NT>
@@ -160,43 +214,52 @@ __device__ void pw_solve(const double *__restrict__ G, int64_t ldg, int m, int n
     const int half = n_pad / 2;
     for (sweep = 1; sweep <= max_sweeps; ++sweep) {
         for (int s = 0; s < n_pad; ++s) {
-            for (int k = warp; k < half; k += kW) {
-                int a, b;
-                modulus_pair(n_pad, s, k, a, b);
-                const int p = sh.pos[a], q = sh.pos[b];
-                double *gp = sh.G + (size_t)p * m_pad, *gq = sh.G + (size_t)q * m_pad;
-                double app = 0.0, aqq = 0.0, apq = 0.0;
-                for (int i = lane; i < m_pad; i += kWarp) {
-                    const double x = gp[i], y = gq[i];
-                    app = fma(x, x, app);
-                    aqq = fma(y, y, aqq);
-                    apq = fma(x, y, apq);
+            // A warp takes the pairs k = warp, warp + kW, ... in batches of up
+            // to 32: the dots of every pair of the batch (warp-wide, every lane
+            // ends with the sums), then lane j computes pair j's rotation, then
+            // the column updates.  Pairs of a step are disjoint, so this is the
+            // same arithmetic as one pair after the other.
+            for (int k0 = warp; k0 < half; k0 += 32 * kW) {
+                const int nbatch = min(32, (half - k0 + kW - 1) / kW);
+                double my_app = 0.0, my_aqq = 0.0, my_apq = 0.0;
+                int my_p = 0, my_q = 0;
+                for (int j = 0; j < nbatch; ++j) {
+                    int a, b;
+                    modulus_pair(n_pad, s, k0 + j * kW, a, b);
+                    const int p = sh.pos[a], q = sh.pos[b];
+                    double app = 0.0, aqq = 0.0, apq = 0.0;
+                    pw_dots(sh.G + (size_t)p * m_pad, sh.G + (size_t)q * m_pad, m_pad, lane, app, aqq, apq);
+                    app = warp_sum(app);
+                    aqq = warp_sum(aqq);
+                    apq = warp_sum(apq);
+                    if (lane == j) {
+                        my_app = app;
+                        my_aqq = aqq;
+                        my_apq = apq;
+                        my_p = p;
+                        my_q = q;
+                    }
                 }
-                app = warp_sum(app);
-                aqq = warp_sum(aqq);
-                apq = warp_sum(apq);
-                if (pair_passes(app, aqq, apq, tol)) continue;
-                const int hyp = (sh.sg[p] == sh.sg[q]) ? -1 : 1;
-                double t, c;
-                if (!rotation_params(app, aqq, apq, hyp, t, c)) {
-                    if (lane == 0) atomicExch(&sc.err, HSVD_ERR_RANK);
-                    continue;
+                double my_t = 0.0, my_c = 1.0;
+                int my_rot = 0, my_hyp = -1;
+                if (lane < nbatch && !pair_passes(my_app, my_aqq, my_apq, tol)) {
+                    my_hyp = (sh.sg[my_p] == sh.sg[my_q]) ? -1 : 1;
+                    if (rotation_params(my_app, my_aqq, my_apq, my_hyp, my_t, my_c)) my_rot = 1;
+                    else atomicExch(&sc.err, HSVD_ERR_RANK);
                 }
-                const double ht = hyp < 0 ? -t : t;
-                for (int i = lane; i < m_pad; i += kWarp) {
-                    const double x = gp[i], y = gq[i];
-                    gp[i] = fma(ht, y, x) * c;
-                    gq[i] = fma(t, x, y) * c;
+                const unsigned rmask = __ballot_sync(0xffffffffu, my_rot);
+                for (int j = 0; j < nbatch; ++j) {
+                    if (!((rmask >> j) & 1u)) continue;
+                    const double t = __shfl_sync(0xffffffffu, my_t, j), c = __shfl_sync(0xffffffffu, my_c, j);
+                    const int hyp = __shfl_sync(0xffffffffu, my_hyp, j);
+                    const int p = __shfl_sync(0xffffffffu, my_p, j), q = __shfl_sync(0xffffffffu, my_q, j);
+                    const double ht = hyp < 0 ? -t : t;
+                    pw_rotate(sh.G + (size_t)p * m_pad, sh.G + (size_t)q * m_pad, m_pad, lane, ht, t, c);
+                    pw_rotate(sh.W + (size_t)p * n_pad, sh.W + (size_t)q * n_pad, n_pad, lane, ht, t, c);
                 }
-                double *wp = sh.W + (size_t)p * n_pad, *wq = sh.W + (size_t)q * n_pad;
-                for (int i = lane; i < n_pad; i += kWarp) {
-                    const double x = wp[i], y = wq[i];
-                    wp[i] = fma(ht, y, x) * c;
-                    wq[i] = fma(t, x, y) * c;
-                }
-                if (lane == 0) {
-                    atomicAdd(&sc.rot, 1);
-                    ++rot_total;
+                if (lane == 0 && rmask) {
+                    atomicAdd(&sc.rot, __popc(rmask));
+                    rot_total += __popc(rmask);
                 }
             }
             grp_sync<NT>(bar);

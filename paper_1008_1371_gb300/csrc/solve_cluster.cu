@@ -10,9 +10,11 @@
 //
 // One inner step A <- R^T A R (reading of the paper: the two one-sided halves
 // alternate order from step to step):
-//   1. the owner of the stored row holding a_pq computes (t, c) for the pair
-//      (Sec. 2 rotation, test of Eq. 2.3) and writes them into every CTA of
+//   1. the owner of the stored row holding a_pq writes it into every CTA of
 //      the cluster through distributed shared memory;      cluster barrier
+//      every CTA computes (t, c) of every pair (Sec. 2 rotation, test of
+//      Eq. 2.3) from its replica of the diagonal;
+
 //   2. every CTA mixes columns p, q of its own rows of S and of W (the column
 //      update of Alg. 4.5), updates the replicated diagonal by Eq. 2.6, and
 //      scatters its rows of S transposed into the owners' receive buffers;
@@ -45,7 +47,8 @@ k_solve_cluster(const double *__restrict__ part, int nsplit, int full_part, doub
                 const int8_t *__restrict__ sgn_direct, double tol, int mode, int max_passes,
                 const int *__restrict__ tab_full, const int *__restrict__ tab_cross,
                 double *__restrict__ Wout, int *__restrict__ rotated,
-                unsigned long long *__restrict__ rot_count, int *__restrict__ status, int *__restrict__ dexp) {
+                unsigned long long *__restrict__ rot_count, int *__restrict__ status, int *__restrict__ dexp,
+                const int *__restrict__ visit, float *__restrict__ trace) {
     constexpr int H = NN / 2, R = NN / C, LD = NN + 1, B = NN / 2;
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
@@ -62,6 +65,7 @@ k_solve_cluster(const double *__restrict__ part, int nsplit, int full_part, doub
     __shared__ int P[2][H], Q[2][H], Hy[2][H], Rot[2][H];
     __shared__ double T[2][H], Cc[2][H], Apq[2][H];
     __shared__ int s_flag;
+    __shared__ double tr_max[C], tr_sum[C], tr_red[2][kClThreads / 32];
 
     // initial state: own rows of A_P, the whole diagonal, W = I.  A_P comes from
     // the three-block partials of the FP64 Gram, from full 2b x 2b partials of
@@ -93,6 +97,51 @@ k_solve_cluster(const double *__restrict__ part, int nsplit, int full_part, doub
     double *S = Sa, *Rv = Sb;
     int transposed = 0;  // 0: S holds rows of A, 1: rows of A^T
     cluster.sync();      // every CTA initialised before any remote write
+    // visit record for the learned form: the I x J block of A_P scaled by the
+    // diagonal (max and sum of squares of a_ij / sqrt(a_ii a_jj)), reduced into
+    // rank 0; the block means of the diagonal and the hyperbolic fraction
+    float rec_meanI = 0.f, rec_meanJ = 0.f, rec_hyp = 0.f;
+    if (trace) {
+        double lmax = 0.0, lsum = 0.0;
+        for (int e = tid; e < R * NN; e += kClThreads) {
+            const int x = e / NN, y = e % NN, gx = row0 + x;
+            if (gx < B && y >= B) {
+                const double dd = D[gx] * D[y];
+                const double sc = dd > 0.0 ? fabs(Sa[x * LD + y]) / sqrt(dd) : 0.0;
+                lmax = fmax(lmax, sc);
+                lsum = fma(sc, sc, lsum);
+            }
+        }
+        lmax = warp_max(lmax);
+        lsum = warp_sum(lsum);
+        if ((tid & 31) == 0) {
+            tr_red[0][tid >> 5] = lmax;
+            tr_red[1][tid >> 5] = lsum;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double mx = 0.0, sm2 = 0.0;
+            for (int w = 0; w < kClThreads / 32; ++w) {
+                mx = fmax(mx, tr_red[0][w]);
+                sm2 += tr_red[1][w];
+            }
+            *cluster.map_shared_rank(&tr_max[rank], 0) = mx;
+            *cluster.map_shared_rank(&tr_sum[rank], 0) = sm2;
+            if (rank == 0) {
+                double mi = 0.0, mj = 0.0;
+                int pi = 0, pj = 0;
+                for (int x = 0; x < B; ++x) {
+                    mi += D[x];
+                    mj += D[B + x];
+                    pi += sg[x] > 0;
+                    pj += sg[B + x] > 0;
+                }
+                rec_meanI = (float)(mi / B);
+                rec_meanJ = (float)(mj / B);
+                rec_hyp = (float)(pi * (B - pj) + (B - pi) * pj) / (float)(B * B);
+            }
+        }
+    }
 
     int total = 0, step = 0, err = 0;
     const int npass = (mode == 0) ? max_passes : 1;
@@ -107,31 +156,35 @@ k_solve_cluster(const double *__restrict__ part, int nsplit, int full_part, doub
                 Q[buf][tid] = tab[2 * tid + 1];
             }
             __syncthreads();
-            // 1. rotation parameters by the owner of a_pq, broadcast to the cluster
+            // 1. the owner of a_pq broadcasts it to the cluster; every CTA then
+            //    computes (t, c) for every pair itself (Sec. 2 rotation, test of
+            //    Eq. 2.3) from the replicated diagonal: the same operands and
+            //    operations everywhere, so the same bits
             if (tid < H) {
                 const int k = tid, p = P[buf][k], q = Q[buf][k];
                 const int orow = transposed ? q : p, ocol = transposed ? p : q;
                 if (orow / R == rank) {
                     const double apq = S[(orow - row0) * LD + ocol];
-                    const double app = D[p], aqq = D[q];
-                    const int hyp = (sg[p] == sg[q]) ? -1 : 1;
-                    double t = 0.0, c = 1.0;
-                    int rot = 0, bad = 0;
-                    if (!pair_passes(app, aqq, apq, tol)) {
-                        if (rotation_params(app, aqq, apq, hyp, t, c)) rot = 1;
-                        else bad = 1;
-                    }
-                    for (int r = 0; r < C; ++r) {
-                        *cluster.map_shared_rank(&T[buf][k], r) = t;
-                        *cluster.map_shared_rank(&Cc[buf][k], r) = c;
-                        *cluster.map_shared_rank(&Apq[buf][k], r) = apq;
-                        *cluster.map_shared_rank(&Hy[buf][k], r) = hyp;
-                        *cluster.map_shared_rank(&Rot[buf][k], r) = rot;
-                        if (bad) *cluster.map_shared_rank(&s_flag, r) = HSVD_ERR_RANK;
-                    }
+                    for (int r = 0; r < C; ++r) *cluster.map_shared_rank(&Apq[buf][k], r) = apq;
                 }
             }
             cluster.sync();
+            if (tid < H) {
+                const int k = tid, p = P[buf][k], q = Q[buf][k];
+                const double apq = Apq[buf][k], app = D[p], aqq = D[q];
+                const int hyp = (sg[p] == sg[q]) ? -1 : 1;
+                double t = 0.0, c = 1.0;
+                int rot = 0;
+                if (!pair_passes(app, aqq, apq, tol)) {
+                    if (rotation_params(app, aqq, apq, hyp, t, c)) rot = 1;
+                    else s_flag = HSVD_ERR_RANK;
+                }
+                T[buf][k] = t;
+                Cc[buf][k] = c;
+                Hy[buf][k] = hyp;
+                Rot[buf][k] = rot;
+            }
+            __syncthreads();
             if (s_flag) { err = 1; break; }
             // 2. first half on own rows of S, W rows, diagonal (Eq. 2.6), transpose-scatter
             for (int e = tid; e < R * H; e += kClThreads) {
@@ -187,10 +240,7 @@ k_solve_cluster(const double *__restrict__ part, int nsplit, int full_part, doub
                     S[(q - row0) * LD + p] = 0.0;
                 }
             }
-            int nr = 0;
-            for (int k = 0; k < H; ++k) nr += Rot[buf][k];
-            pass_rot += nr;
-            __syncthreads();
+            pass_rot += __syncthreads_count(tid < H && Rot[buf][tid]);
         }
         total += pass_rot;
         if (pass_rot == 0) break;
@@ -216,6 +266,20 @@ k_solve_cluster(const double *__restrict__ part, int nsplit, int full_part, doub
         if (s_flag && status) atomicExch(status, s_flag);
     }
     cluster.sync();  // no CTA leaves while others may still write into it
+    if (trace && rank == 0 && tid == 0) {
+        double mx = 0.0, sm2 = 0.0;
+        for (int r = 0; r < C; ++r) {
+            mx = fmax(mx, tr_max[r]);
+            sm2 += tr_sum[r];
+        }
+        float *rec = trace + (size_t)visit[pair] * HSVD_TRACE_FIELDS;
+        rec[0] = (float)mx;
+        rec[1] = (float)sqrt(sm2);
+        rec[2] = (float)total;
+        rec[3] = rec_meanI;
+        rec[4] = rec_meanJ;
+        rec[5] = rec_hyp;
+    }
 }
 
 template <int NN>
@@ -223,7 +287,7 @@ cudaError_t solve_cluster_impl(int npairs, const double *part, int nsplit, int f
                                const int8_t *sgn_cols, const int *col0, const int8_t *sgn_direct, double tol,
                                int mode, int max_passes, const int *tab_full, const int *tab_cross, double *Wp,
                                int *rotated, unsigned long long *rot_count, int *status, int *dexp,
-                               cudaStream_t st) {
+                               const int *visit, float *trace, cudaStream_t st) {
     constexpr int C = ClusterOf<NN>::C, R = NN / C;
     const size_t smem = (size_t)(2 * R * (NN + 1) + R * NN) * sizeof(double);
     cudaError_t e = cudaFuncSetAttribute(k_solve_cluster<NN, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -231,7 +295,8 @@ cudaError_t solve_cluster_impl(int npairs, const double *part, int nsplit, int f
     if (e != cudaSuccess) return e;
     k_solve_cluster<NN, C><<<npairs * C, kClThreads, smem, st>>>(part, nsplit, full_part, A, sgn_cols, col0,
                                                                  sgn_direct, tol, mode, max_passes, tab_full,
-                                                                 tab_cross, Wp, rotated, rot_count, status, dexp);
+                                                                 tab_cross, Wp, rotated, rot_count, status, dexp,
+                                                                 visit, trace);
     return cudaGetLastError();
 }
 
@@ -240,17 +305,18 @@ cudaError_t solve_cluster_impl(int npairs, const double *part, int nsplit, int f
 cudaError_t launch_solve(int b, int npairs, const double *part, int nsplit, double *A, const int8_t *sgn_cols,
                          const int *col0, const int8_t *sgn_direct, double tol, int mode, int max_passes,
                          const int *tab_full, const int *tab_cross, double *Wp, int *rotated,
-                         unsigned long long *rot_count, int *status, cudaStream_t st, int full_part, int *dexp) {
+                         unsigned long long *rot_count, int *status, cudaStream_t st, int full_part, int *dexp,
+                         const int *visit, float *trace) {
     switch (b) {
         case 16: return solve_cluster_impl<32>(npairs, part, nsplit, full_part, A, sgn_cols, col0, sgn_direct, tol,
                                                mode, max_passes, tab_full, tab_cross, Wp, rotated, rot_count,
-                                               status, dexp, st);
+                                               status, dexp, visit, trace, st);
         case 32: return solve_cluster_impl<64>(npairs, part, nsplit, full_part, A, sgn_cols, col0, sgn_direct, tol,
                                                mode, max_passes, tab_full, tab_cross, Wp, rotated, rot_count,
-                                               status, dexp, st);
+                                               status, dexp, visit, trace, st);
         case 64: return solve_cluster_impl<128>(npairs, part, nsplit, full_part, A, sgn_cols, col0, sgn_direct,
                                                 tol, mode, max_passes, tab_full, tab_cross, Wp, rotated, rot_count,
-                                                status, dexp, st);
+                                                status, dexp, visit, trace, st);
         default: return cudaErrorInvalidValue;
     }
 }
