@@ -89,6 +89,18 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(value, world, device=None):
+    """The largest of the ranks' values (the job's time is its slowest rank's)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -273,10 +285,7 @@ def run_batched(args):
             dist.barrier()
     assert r.rc == api.HSVD_OK, r.rc
     ms = sum(step_ms) / len(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     eff = sum(sw * pointwise_flops_per_sweep(m, n) for sw, m, n in zip(r.sweeps, ms_, ns_))
     value = world * eff / (ms * 1e-3) / 1e12
     kern_ms = sum(i.ms_kernel for i in infos) / len(infos)
@@ -319,7 +328,7 @@ def run_batched(args):
             t0 = time.perf_counter()
             rh = api.hsvd_solve_batched(Gh, Jh, opts)
             ts.append(time.perf_counter() - t0)
-        e2e_s = sum(ts) / len(ts)
+        e2e_s = max_over_ranks(sum(ts) / len(ts), world, dev)
         h2d = sum(m * n * 8 + n for m, n in zip(ms_, ns_))
         d2h = sum(n * 8 + m * n * 8 + n * n * 8 for m, n in zip(ms_, ns_))
         e2e = {"value": world * eff / e2e_s / 1e12, "unit": "TFLOP/s", "ms_per_step": e2e_s * 1e3,
@@ -544,10 +553,7 @@ def main():
         if world > 1:
             dist.barrier()
     ms = sum(step_ms) / len(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     info = infos[-1]
     assert info.status == api.HSVD_OK, api.hsvd_status_string(info.status)
     sweeps = info.sweeps
@@ -634,10 +640,7 @@ def main():
             api.hsvd_solve_ex(Gh, Jh, opts_e2e, out=(sh, Uh, Vh))
             e2e_t.append(time.perf_counter() - t0)
         e2e_s = sum(e2e_t) / len(e2e_t)
-        if world > 1:
-            t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(e2e_s, world, dev)
         e2e = {"value": world * eff_flops / e2e_s / 1e12, "unit": "TFLOP/s", "ms_per_step": e2e_s * 1e3,
                "h2d_bytes_per_step": m * n * 8 + n, "d2h_bytes_per_step": n * 8 + m * n * 8 + n * n * 8}
 

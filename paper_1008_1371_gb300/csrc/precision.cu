@@ -31,6 +31,8 @@ using namespace tc;
 
 constexpr int NNX = 128;             // pivot block order 2b
 constexpr int kThrX = 256;           // eight warps: two per TMEM lane quarter
+constexpr int kThrU = 512;           // update: sixteen warps, four per TMEM lane quarter
+constexpr int kThrG = 512;           // Gram: sixteen warps
 constexpr int kGramK = 512;          // rows of G per Gram CTA pair (exactness window)
 constexpr int kGramKT = 32;          // rows per shared-memory tile of the Gram
 constexpr int kUpdKT = 32;           // k per shared-memory tile of the update
@@ -83,7 +85,7 @@ __device__ __forceinline__ void read_accs(uint32_t tmem, int lane_base, int c0, 
 // and writes the slices to both CTAs' shared memory, so the tile is split once;
 // tiles are double-buffered, the split of tile t overlapping the products of
 // tile t - 1.  One cluster barrier per tile.
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThrX, 1)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThrG, 1)
 k_gram_x(const double *__restrict__ G, int64_t rows, int64_t ldg, const int *__restrict__ col0, int ksplit,
          double *__restrict__ part, int *__restrict__ status) {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -101,7 +103,7 @@ k_gram_x(const double *__restrict__ G, int64_t rows, int64_t ldg, const int *__r
     const uint32_t sbase = smem_addr(smem), sbase_peer = map_peer(sbase, peer);
     cluster_sync();  // both CTAs are running before either touches the other's shared memory
     // column exponents of this CTA's 64 columns over the CTA pair's rows, to both CTAs
-    for (int cc = warp; cc < NNX / 2; cc += kThrX / 32) {
+    for (int cc = warp; cc < NNX / 2; cc += kThrG / 32) {
         const int c = NNX / 2 * (int)half + cc;
         const double *g = G + (int64_t)(c < NNX / 2 ? cI + c : cJ + c - NNX / 2) * ldg;
         int e = -2000;
@@ -134,7 +136,7 @@ k_gram_x(const double *__restrict__ G, int64_t rows, int64_t ldg, const int *__r
     for (int t = 0; t < ntiles; ++t) {
         const uint32_t buf = (uint32_t)(t & 1) * kBufBytes;
         const int64_t t0 = r0 + (int64_t)t * kGramKT;
-        for (int core = warp; core < (NNX / 2 / 8) * (kGramKT / 8); core += kThrX / 32) {
+        for (int core = warp; core < (NNX / 2 / 8) * (kGramKT / 8); core += kThrG / 32) {
             const int cg = core / (kGramKT / 8), kg = core % (kGramKT / 8);
             const int c = NNX / 2 * (int)half + cg * 8 + cc, k = kg * 8 + kp;
             const double *g = G + (int64_t)(c < NNX / 2 ? cI + c : cJ + c - NNX / 2) * ldg;
@@ -170,10 +172,11 @@ k_gram_x(const double *__restrict__ G, int64_t rows, int64_t ldg, const int *__r
     fence_after();
     __syncthreads();
     if (!s_fail) {
-        // lane c = row of A_P; warp group h2 takes TMEM columns [32 h2, 32 h2 + 32)
+        // lane c = row of A_P; warp group h2 takes TMEM columns [16 h2, 16 h2 + 16)
         const int q = warp & 3, c = 32 * q + lane, h2 = warp >> 2;
+        constexpr int kCols = kN / (kThrG / 128);
         double *out = part + ((size_t)pair * ksplit + split) * NNX * NNX;
-        for (int c0 = 32 * h2; c0 < 32 * h2 + 32; c0 += 8) {
+        for (int c0 = kCols * h2; c0 < kCols * h2 + kCols; c0 += 8) {
             float v[8][8];
             read_accs(tmem, 32 * q, c0, v);
 #pragma unroll
@@ -195,48 +198,43 @@ k_gram_x(const double *__restrict__ G, int64_t rows, int64_t ldg, const int *__r
 }
 
 // ---------------------------------------------------------------- W' slices
-// One CTA per rotated pair: the A operand of the transposed update, W'^T
-// (128 x 128, K-major), for G rows (W' = D W_P) and for V rows (W' = W_P), in
-// four k quarters of 32, with per-column exponents F_j.
+// The A operand of the transposed update, W'^T (128 x 128, K-major), for G rows
+// (W' = D W_P) and for V rows (W' = W_P), in four k quarters of 32, with
+// per-column exponents F_j.  Eight CTAs per rotated pair: CTA (which, quarter)
+// forms one 128 x 32 tile of slices; every CTA derives the exponents F_j of its
+// `which` itself (the same operations, the same values).
 // wsl layout: [pair][which][quarter][slice][128 x 32 core-matrix tile]
 __global__ void __launch_bounds__(kThrX)
 k_wprep_x(const double *__restrict__ Wp, const int *__restrict__ dexp, const int *__restrict__ rotated,
           uint16_t *__restrict__ wsl, int *__restrict__ wexp, unsigned long long *__restrict__ upd_count) {
-    const int pair = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int pair = blockIdx.x >> 3, which = (blockIdx.x >> 2) & 1, q = blockIdx.x & 3;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (!rotated[pair]) return;
-    if (tid == 0 && upd_count) atomicAdd(upd_count, 1ull);
-    __shared__ int dk[NNX], F[2][NNX];
+    if (tid == 0 && upd_count && blockIdx.x % 8 == 0) atomicAdd(upd_count, 1ull);
+    __shared__ int dk[NNX], F[NNX];
     const double *W = Wp + (size_t)pair * NNX * NNX;  // W(k, j) at k + j * 128
-    for (int k = tid; k < NNX; k += kThrX) dk[k] = dexp[(size_t)pair * NNX + k];
+    for (int k = tid; k < NNX; k += kThrX) dk[k] = which == 0 ? dexp[(size_t)pair * NNX + k] : 0;
     __syncthreads();
     for (int j = warp; j < NNX; j += kThrX / 32) {
-        int e0 = -2000, e1 = -2000;
-        for (int k = lane; k < NNX; k += 32) {
-            const int e = exp_bound(W[k + (size_t)j * NNX]);
-            e0 = max(e0, e + dk[k]);
-            e1 = max(e1, e);
-        }
+        int e0 = -2000;
+        for (int k = lane; k < NNX; k += 32) e0 = max(e0, exp_bound(W[k + (size_t)j * NNX]) + dk[k]);
         e0 = warp_max_i(e0);
-        e1 = warp_max_i(e1);
-        if (lane == 0) {
-            F[0][j] = e0 < -1000 ? 0 : e0;
-            F[1][j] = e1 < -1000 ? 0 : e1;
-        }
+        if (lane == 0) F[j] = e0 < -1000 ? 0 : e0;
     }
     __syncthreads();
-    for (int e = tid; e < 2 * NNX; e += kThrX) wexp[(size_t)pair * 2 * NNX + e] = F[e / NNX][e % NNX];
+    if (q == 0)
+        for (int j = tid; j < NNX; j += kThrX) wexp[((size_t)pair * 2 + which) * NNX + j] = F[j];
     constexpr size_t kTile = (size_t)NNX * kUpdKT;  // elements per slice tile
+    uint16_t *dst = wsl + (((size_t)pair * 2 + which) * 4 + q) * kSlices * kTile;
     // a warp step covers one 8 (j) x 8 (k) core matrix: lane -> j (lane >> 2),
     // k pair 2 (lane & 3)
     const int jj = lane >> 2, kp = 2 * (lane & 3);
-    for (int core = warp; core < 2 * (NNX / 8) * (NNX / 8); core += kThrX / 32) {
-        const int which = core / ((NNX / 8) * (NNX / 8)), rem = core % ((NNX / 8) * (NNX / 8));
-        const int j = (rem / (NNX / 8)) * 8 + jj, k = (rem % (NNX / 8)) * 8 + kp;
+    for (int core = warp; core < (NNX / 8) * (kUpdKT / 8); core += kThrX / 32) {
+        const int j = (core / (kUpdKT / 8)) * 8 + jj, kk = (core % (kUpdKT / 8)) * 8 + kp;
+        const int k = q * kUpdKT + kk;
         const double w0 = W[k + (size_t)j * NNX], w1 = W[k + 1 + (size_t)j * NNX];
-        const long long d0 = digit_word(w0, which == 0 ? F[0][j] - dk[k] : F[1][j]);
-        const long long d1 = digit_word(w1, which == 0 ? F[0][j] - dk[k + 1] : F[1][j]);
-        const int q = k / kUpdKT, kk = k % kUpdKT;
-        uint16_t *dst = wsl + (((size_t)pair * 2 + which) * 4 + q) * kSlices * kTile;
+        const long long d0 = digit_word(w0, F[j] - dk[k]);
+        const long long d1 = digit_word(w1, F[j] - dk[k + 1]);
         const uint32_t off = core_offset(j, kk, kUpdKT) >> 1;
 #pragma unroll
         for (int s = 0; s < kSlices; ++s)
@@ -259,7 +257,7 @@ struct UpdItem {
     int pair, which, cI, cJ;
 };
 
-__global__ void __launch_bounds__(kThrX, 1)
+__global__ void __launch_bounds__(kThrU, 1)
 k_update_x(double *__restrict__ X, int64_t rowsX, int64_t ldx, double *__restrict__ Y, int64_t rowsY, int64_t ldy,
            int npairs, const int *__restrict__ col0, const uint16_t *__restrict__ wsl,
            const int *__restrict__ wexp, const int *__restrict__ dexp, const int *__restrict__ rotated,
@@ -313,17 +311,18 @@ k_update_x(double *__restrict__ X, int64_t rowsX, int64_t ldx, double *__restric
     };
     // exponents of the item into slot s (block-wide, with barriers)
     auto setup = [&](const UpdItem &d, int s) {
-        for (int k = tid; k < NNX; k += kThrX) {
+        for (int k = tid; k < NNX; k += kThrU) {
             dk[s][k] = d.which == 0 ? dexp[(size_t)d.pair * NNX + k] : 0;
             Fcol[s][k] = wexp[((size_t)d.pair * 2 + d.which) * NNX + k];
         }
         if (tid < kUpdRows) Erow[s][tid] = -2000;
         __syncthreads();
-        const int i = tid & (kUpdRows - 1), part4 = tid >> 6;
+        constexpr int kParts = kThrU / kUpdRows, kPer = NNX / kParts;
+        const int i = tid & (kUpdRows - 1), part = tid / kUpdRows;
         const int64_t row = d.r0 + i;
         int e = -2000;
         if (row < d.rows)
-            for (int k = part4 * 32; k < part4 * 32 + 32; ++k) {
+            for (int k = part * kPer; k < part * kPer + kPer; ++k) {
                 const int col = k < NNX / 2 ? d.cI + k : d.cJ + k - NNX / 2;
                 e = max(e, exp_bound(d.M[row + (int64_t)col * d.ld]) - dk[s][k]);
             }
@@ -342,7 +341,7 @@ k_update_x(double *__restrict__ X, int64_t rowsX, int64_t ldx, double *__restric
         }
         (void)use;
         unsigned char *Bb = Bs + b * kBBuf;
-        for (int core = warp; core < (kUpdRows / 8) * (kUpdKT / 8); core += kThrX / 32) {
+        for (int core = warp; core < (kUpdRows / 8) * (kUpdKT / 8); core += kThrU / 32) {
             const int i = (core / (kUpdKT / 8)) * 8 + rr, kk = (core % (kUpdKT / 8)) * 8 + kp;
             const int k = q * kUpdKT + kk;
             const int64_t row = d.r0 + i;
@@ -411,7 +410,7 @@ k_update_x(double *__restrict__ X, int64_t rowsX, int64_t ldx, double *__restric
             }
             __syncthreads();
             if (s_fail) break;
-            // epilogue of the item: lane j = output column, warp group h2 = rows [32 h2, 32 h2 + 32)
+            // epilogue of the item: lane j = output column, warp group h2 = rows [16 h2, 16 h2 + 16)
             wait_mma(g - 1);
             fence_after();
             __syncthreads();
@@ -419,7 +418,8 @@ k_update_x(double *__restrict__ X, int64_t rowsX, int64_t ldx, double *__restric
             {
                 const int qd = warp & 3, j = 32 * qd + lane, h2 = warp >> 2;
                 const int jj = j < NNX / 2 ? cur.cI + j : cur.cJ + j - NNX / 2;
-                for (int c0 = 32 * h2; c0 < 32 * h2 + 32; c0 += 8) {
+                constexpr int kCols = kN / (kThrU / 128);
+                for (int c0 = kCols * h2; c0 < kCols * h2 + kCols; c0 += 8) {
                     float v[8][8];
                     read_accs(tmem, 32 * qd, c0, v);
 #pragma unroll
@@ -478,7 +478,7 @@ cudaError_t launch_gram_x(const double *G, int64_t rows, int64_t ldg, int npairs
     const size_t smem = (size_t)2 * kSlices * NNX * kGramKT * 2;  // two tiles
     cudaError_t e = cudaFuncSetAttribute(k_gram_x, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_gram_x<<<npairs * ksplit * 2, kThrX, smem, st>>>(G, rows, ldg, col0, ksplit, part, status);
+    k_gram_x<<<npairs * ksplit * 2, kThrG, smem, st>>>(G, rows, ldg, col0, ksplit, part, status);
     return cudaGetLastError();
 }
 
@@ -489,7 +489,7 @@ cudaError_t launch_assemble_x(int npairs, const double *part, int ksplit, double
 
 cudaError_t launch_wprep_x(int npairs, const double *Wp, const int *dexp, const int *rotated, uint16_t *wsl,
                            int *wexp, unsigned long long *upd_count, cudaStream_t st) {
-    k_wprep_x<<<npairs, kThrX, 0, st>>>(Wp, dexp, rotated, wsl, wexp, upd_count);
+    k_wprep_x<<<npairs * 8, kThrX, 0, st>>>(Wp, dexp, rotated, wsl, wexp, upd_count);
     return cudaGetLastError();
 }
 
@@ -508,7 +508,7 @@ cudaError_t launch_update_x(double *X, int64_t rowsX, int64_t ldx, double *Y, in
     const int64_t chunks = (rowsX + kUpdRows - 1) / kUpdRows + (Y ? (rowsY + kUpdRows - 1) / kUpdRows : 0);
     const int64_t items = (int64_t)npairs * chunks;
     const unsigned grid = (unsigned)(items < sms ? items : sms);
-    k_update_x<<<grid, kThrX, smem, st>>>(X, rowsX, ldx, Y, rowsY, ldy, npairs, col0, wsl, wexp, dexp, rotated,
+    k_update_x<<<grid, kThrU, smem, st>>>(X, rowsX, ldx, Y, rowsY, ldy, npairs, col0, wsl, wexp, dexp, rotated,
                                           status);
     return cudaGetLastError();
 }

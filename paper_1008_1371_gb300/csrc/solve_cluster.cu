@@ -35,6 +35,9 @@ namespace {
 
 constexpr int kClThreads = 256;
 
+// barrier 1 among the last n threads of the CTA (warps 1..)
+__device__ __forceinline__ void grp_bar_mix(int n) { asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory"); }
+
 template <int NN>
 struct ClusterOf {
     static constexpr int C = NN == 32 ? 4 : 8;
@@ -282,6 +285,353 @@ k_solve_cluster(const double *__restrict__ part, int nsplit, int full_part, doub
     }
 }
 
+// The cross pass (block-oriented mode, Sec. 5: the pairs (k, h + (k + s) mod h)
+// of the off-diagonal block, h = b, s = 0..h-1) without transposes.  CTA r of
+// the cluster owns the pairs k in [r P, r P + P), P = h / C: their fixed rows
+// k and their current partner rows h + (k + s) mod h.  Both halves of
+// R^T A R touch only a pair's two rows (the row mix) and, inside every row,
+// the two columns of each pair (the column mix), so a step is local once the
+// CTA knows every pair's (t, c).  From step s to s + 1 pair k takes pair
+// k + 1's partner row: inside the CTA that is a ring of P + 1 row slots, and
+// across the cluster every CTA hands its first pair's partner row to the
+// previous CTA.  The next step's a_pq lies in the owner's fixed row, so the
+// owner computes that pair's (t, c) as soon as its rows are updated and writes
+// them into every CTA; one cluster barrier per step.  The element operations
+// and their order (column mix first on even steps, row mix first on odd
+// steps, Eq. 2.6 on the diagonal, zeros at the pair) are the oracle's, so the
+// result is bit-identical to it and to k_solve_cluster.
+template <int NN, int C>
+__global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kClThreads)
+k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double *__restrict__ A_io,
+              const int8_t *__restrict__ sgn_cols, const int *__restrict__ col0,
+              const int8_t *__restrict__ sgn_direct, double tol, double *__restrict__ Wout,
+              int *__restrict__ rotated, unsigned long long *__restrict__ rot_count, int *__restrict__ status,
+              int *__restrict__ dexp, const int *__restrict__ visit, float *__restrict__ trace) {
+    constexpr int h = NN / 2, P = h / C, RW = NN / C, B = NN / 2;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int pair = blockIdx.x / C;
+    const int tid = threadIdx.x;
+    const int k0 = rank * P;        // first pair owned
+    const int w0 = rank * RW;       // first row of W owned
+
+    extern __shared__ __align__(16) double sm[];
+    double *fix = sm;                 // [P][NN]    rows k0 .. k0 + P - 1
+    double *mov = fix + P * NN;       // [P + 1][NN] partner rows, ring
+    double *Wl = mov + (P + 1) * NN;  // [RW][NN]   rows w0 .. w0 + RW - 1 of W_P
+    __shared__ double D[NN];
+    __shared__ int sg[NN];
+    __shared__ double T[2][h], Cc[2][h], Apq[2][h];
+    __shared__ int Fl[2][h];          // bit 0: rotate, bit 1: rank deficient
+    __shared__ double tr_max[C], tr_sum[C], tr_red[2][kClThreads / 32];
+
+    auto entry = [&](int x, int y) -> double {
+        if (!part) return A_io[(size_t)pair * NN * NN + x + y * NN];
+        if (!full_part) return assemble_entry<NN>(part, nsplit, pair, x + y * NN);
+        const int lo = x < y ? x : y, hi = x < y ? y : x;
+        const double *pp = part + (size_t)pair * nsplit * NN * NN + lo + (size_t)hi * NN;
+        double v = 0.0;
+        for (int s = 0; s < nsplit; ++s) v += pp[(size_t)s * NN * NN];
+        return v;
+    };
+    for (int x = tid; x < NN; x += kClThreads) {
+        if (sgn_direct) sg[x] = sgn_direct[(size_t)pair * NN + x];
+        else sg[x] = sgn_cols[col0[2 * pair + (x >= B)] + (x % B)];
+        D[x] = entry(x, x);
+        if (dexp && rank == 0) dexp[(size_t)pair * NN + x] = D[x] > 0.0 ? (ilogb(D[x]) >> 1) : 0;
+    }
+    for (int e = tid; e < P * NN; e += kClThreads) {
+        const int kl = e / NN, y = e % NN;
+        fix[kl * NN + y] = entry(k0 + kl, y);
+        mov[kl * NN + y] = entry(h + k0 + kl, y);  // step 0: pair k with row h + k, ring slot kl
+    }
+    for (int e = tid; e < RW * NN; e += kClThreads) {
+        const int x = e / NN, y = e % NN;
+        Wl[x * NN + y] = (w0 + x == y) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    // visit record: the I x J block (rows k < h are the fixed rows) scaled by the diagonal
+    float rec_meanI = 0.f, rec_meanJ = 0.f, rec_hyp = 0.f;
+    double rec_max = 0.0, rec_sum = 0.0;
+    if (trace) {
+        double lmax = 0.0, lsum = 0.0;
+        for (int e = tid; e < P * h; e += kClThreads) {
+            const int kl = e / h, y = h + e % h, x = k0 + kl;
+            const double dd = D[x] * D[y];
+            const double sc = dd > 0.0 ? fabs(fix[kl * NN + y]) / sqrt(dd) : 0.0;
+            lmax = fmax(lmax, sc);
+            lsum = fma(sc, sc, lsum);
+        }
+        lmax = warp_max(lmax);
+        lsum = warp_sum(lsum);
+        if ((tid & 31) == 0) {
+            tr_red[0][tid >> 5] = lmax;
+            tr_red[1][tid >> 5] = lsum;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            for (int w = 0; w < kClThreads / 32; ++w) {
+                rec_max = fmax(rec_max, tr_red[0][w]);
+                rec_sum += tr_red[1][w];
+            }
+            if (rank == 0) {
+                double mi = 0.0, mj = 0.0;
+                int pi = 0, pj = 0;
+                for (int x = 0; x < B; ++x) {
+                    mi += D[x];
+                    mj += D[B + x];
+                    pi += sg[x] > 0;
+                    pj += sg[B + x] > 0;
+                }
+                rec_meanI = (float)(mi / B);
+                rec_meanJ = (float)(mj / B);
+                rec_hyp = (float)(pi * (B - pj) + (B - pi) * pj) / (float)(B * B);
+            }
+        }
+    }
+    cluster.sync();  // every CTA initialised before any remote write
+    if (trace && tid == 0) {
+        *cluster.map_shared_rank(&tr_max[rank], 0) = rec_max;
+        *cluster.map_shared_rank(&tr_sum[rank], 0) = rec_sum;
+    }
+    // (t, c) of the owned pairs for step s into every CTA (buffer s & 1)
+    auto params_out = [&](int s) {
+        if (tid < P) {
+            const int kl = tid, k = k0 + kl, p = k, q = h + (k + s) % h;
+            const double apq = fix[kl * NN + q];
+            const double app = D[p], aqq = D[q];
+            const int hyp = (sg[p] == sg[q]) ? -1 : 1;
+            double t = 0.0, c = 1.0;
+            int fl = 0;
+            if (!pair_passes(app, aqq, apq, tol)) {
+                if (rotation_params(app, aqq, apq, hyp, t, c)) fl = 1;
+                else fl = 2;
+            }
+            const int b = s & 1;
+            for (int r = 0; r < C; ++r) {
+                *cluster.map_shared_rank(&T[b][k], r) = t;
+                *cluster.map_shared_rank(&Cc[b][k], r) = c;
+                *cluster.map_shared_rank(&Apq[b][k], r) = apq;
+                *cluster.map_shared_rank(&Fl[b][k], r) = fl;
+            }
+        }
+    };
+    params_out(0);
+    cluster.sync();
+
+    // Warp 0 works one step ahead: at the top of step s lane kl < P reads the
+    // four entries of its rows (k, q_k) in the columns (j, q') of pair
+    // j = k + 1 and the diagonal values a_kk, a_q'q', forms the step-s values
+    // of a_kq' and of the two diagonal entries with the same operations as the
+    // bulk update below, and computes the (t, c) of pair (k, q') for step
+    // s + 1 while warps 1..7 update the rows (named barrier 1).
+    constexpr int kMixThreads = kClThreads - 32;
+    const int warp = tid >> 5, lane = tid & 31;
+    int total = 0, bad = 0, s_end = h - 1;
+    for (int s = 0; s < h; ++s) {
+        const int b = s & 1;
+        double nx_t = 0.0, nx_c = 1.0, nx_apq = 0.0;
+        int nx_fl = 0;
+        double e_kj = 0.0, e_kq = 0.0, e_qj = 0.0, e_qq = 0.0, d_k = 0.0, d_q = 0.0;
+        const bool ahead = warp == 0 && lane < P && s + 1 < h;
+        if (ahead) {
+            const int kl = lane, k = k0 + kl, j = (k + 1) % h, q2 = h + (j + s) % h;
+            const double *rk = fix + kl * NN, *rq = mov + ((kl + s) % (P + 1)) * NN;
+            e_kj = rk[j];
+            e_kq = rk[q2];
+            e_qj = rq[j];
+            e_qq = rq[q2];
+            d_k = D[k];
+            d_q = D[q2];
+        }
+        // every CTA sees every pair's flags: the same decision everywhere
+        const int f = tid < h ? Fl[b][tid] : 0;
+        bad = __syncthreads_or(f & 2);
+        if (bad) {
+            s_end = s;
+            break;
+        }
+        auto slot = [&](int kl) { return (kl + s) % (P + 1); };
+        if (warp == 0) {
+            if (ahead) {
+                const int kl = lane, k = k0 + kl, j = (k + 1) % h, q2 = h + (j + s) % h, qk = h + (k + s) % h;
+                const int fk = Fl[b][k] & 1, fj = Fl[b][j] & 1;
+                const double tk = T[b][k], ck = Cc[b][k], htk = (sg[k] == sg[qk]) ? -tk : tk;
+                const double tj = T[b][j], cj = Cc[b][j], htj = (sg[j] == sg[q2]) ? -tj : tj;
+                double v;
+                if ((s & 1) == 0) {  // column mix (pair j), then row mix (pair k)
+                    double r1 = e_kq, r2 = e_qq;
+                    if (fj) {
+                        r1 = fma(tj, e_kj, e_kq) * cj;
+                        r2 = fma(tj, e_qj, e_qq) * cj;
+                    }
+                    v = fk ? fma(htk, r2, r1) * ck : r1;
+                } else {  // row mix (pair k), then column mix (pair j)
+                    double u1 = e_kj, u2 = e_kq;
+                    if (fk) {
+                        u1 = fma(htk, e_qj, e_kj) * ck;
+                        u2 = fma(htk, e_qq, e_kq) * ck;
+                    }
+                    v = fj ? fma(tj, u1, u2) * cj : u2;
+                }
+                const double app = fk ? fma(htk, Apq[b][k], d_k) : d_k;
+                const double aqq = fj ? fma(tj, Apq[b][j], d_q) : d_q;
+                const int hyp = (sg[k] == sg[q2]) ? -1 : 1;
+                // the test and the rotation are independent: both are evaluated
+                const bool passes = pair_passes(app, aqq, v, tol);
+                double t, c;
+                const bool ok = rotation_params(app, aqq, v, hyp, t, c);
+                nx_apq = v;
+                if (!passes) {
+                    if (ok) {
+                        nx_t = t;
+                        nx_c = c;
+                        nx_fl = 1;
+                    } else {
+                        nx_fl = 2;
+                    }
+                }
+            }
+            if (tid == 0) {
+                int nrot = 0;
+                for (int k = 0; k < h; ++k) nrot += Fl[b][k] & 1;
+                total += nrot;
+            }
+        } else {
+            const int mt = tid - 32;
+            // the column mix on every owned row of A and of W: pair j's columns j and h + (j + s) mod h
+            auto col_mix = [&](bool with_w) {
+                constexpr int nA = 2 * P * h, nW = RW * h;
+                const int n_items = nA + (with_w ? nW : 0);
+                for (int e = mt; e < n_items; e += kMixThreads) {
+                    double *row;
+                    int j;
+                    if (e < nA) {
+                        const int r = e / h;
+                        j = e % h;
+                        row = r < P ? fix + r * NN : mov + slot(r - P) * NN;
+                    } else {
+                        const int x = (e - nA) / h;
+                        j = (e - nA) % h;
+                        row = Wl + x * NN;
+                    }
+                    if (!(Fl[b][j] & 1)) continue;
+                    const int p = j, q = h + (j + s) % h;
+                    const double t = T[b][j], c = Cc[b][j], ht = (sg[p] == sg[q]) ? -t : t;
+                    const double a = row[p], bb = row[q];
+                    row[p] = fma(ht, bb, a) * c;
+                    row[q] = fma(t, a, bb) * c;
+                }
+            };
+            // the row mix of every owned pair
+            auto row_mix = [&](bool with_w) {
+                const int n_items = P * NN + (with_w ? RW * h : 0);
+                for (int e = mt; e < n_items; e += kMixThreads) {
+                    if (e >= P * NN) {
+                        const int x = (e - P * NN) / h, j = (e - P * NN) % h;
+                        if (!(Fl[b][j] & 1)) continue;
+                        double *row = Wl + x * NN;
+                        const int p = j, q = h + (j + s) % h;
+                        const double t = T[b][j], c = Cc[b][j], ht = (sg[p] == sg[q]) ? -t : t;
+                        const double a = row[p], bb = row[q];
+                        row[p] = fma(ht, bb, a) * c;
+                        row[q] = fma(t, a, bb) * c;
+                        continue;
+                    }
+                    const int kl = e / NN, y = e % NN, k = k0 + kl;
+                    if (!(Fl[b][k] & 1)) continue;
+                    const int p = k, q = h + (k + s) % h;
+                    const double t = T[b][k], c = Cc[b][k], ht = (sg[p] == sg[q]) ? -t : t;
+                    double *rp = fix + kl * NN, *rq = mov + slot(kl) * NN;
+                    const double a = rp[y], bb = rq[y];
+                    rp[y] = fma(ht, bb, a) * c;
+                    rq[y] = fma(t, a, bb) * c;
+                }
+            };
+            if ((s & 1) == 0) {
+                col_mix(true);
+                grp_bar_mix(kMixThreads);
+                row_mix(false);
+            } else {
+                row_mix(true);
+                grp_bar_mix(kMixThreads);
+                col_mix(false);
+            }
+            grp_bar_mix(kMixThreads);
+            // Eq. 2.6 on the replicated diagonal, and the owned pairs' own entries
+            if (mt < h && (Fl[b][mt] & 1)) {
+                const int p = mt, q = h + (mt + s) % h;
+                const double t = T[b][mt], ht = (sg[p] == sg[q]) ? -t : t, apq = Apq[b][mt];
+                const double dp = fma(ht, apq, D[p]), dq = fma(t, apq, D[q]);
+                D[p] = dp;
+                D[q] = dq;
+                if (p >= k0 && p < k0 + P) {
+                    const int kl = p - k0;
+                    double *rp = fix + kl * NN, *rq = mov + slot(kl) * NN;
+                    rp[p] = dp;
+                    rp[q] = 0.0;
+                    rq[q] = dq;
+                    rq[p] = 0.0;
+                }
+            }
+        }
+        __syncthreads();
+        if (s + 1 < h) {
+            // hand the first pair's partner row to the previous CTA (its last
+            // pair's row at step s + 1, in the slot that is free during step s)
+            const int dst = (rank + C - 1) % C;
+            double *src = mov + slot(0) * NN;
+            double *rdst = cluster.map_shared_rank(mov, dst) + ((P + s) % (P + 1)) * NN;
+            for (int y = tid; y < NN; y += kClThreads) rdst[y] = src[y];
+            if (ahead) {
+                const int k = k0 + lane, nb = (s + 1) & 1;
+                for (int r = 0; r < C; ++r) {
+                    *cluster.map_shared_rank(&T[nb][k], r) = nx_t;
+                    *cluster.map_shared_rank(&Cc[nb][k], r) = nx_c;
+                    *cluster.map_shared_rank(&Apq[nb][k], r) = nx_apq;
+                    *cluster.map_shared_rank(&Fl[nb][k], r) = nx_fl;
+                }
+            }
+        }
+        cluster.sync();
+    }
+    // outputs: own rows of W (column-major W_P), and A_P when asked for
+    double *wo = Wout + (size_t)pair * NN * NN;
+    for (int e = tid; e < RW * NN; e += kClThreads) {
+        const int x = e / NN, y = e % NN;
+        wo[(w0 + x) + (size_t)y * NN] = Wl[x * NN + y];
+    }
+    if (!part) {
+        // rows where the pass ended: fixed rows k, partner rows h + (k + s_end) mod h
+        double *ao = A_io + (size_t)pair * NN * NN;
+        for (int e = tid; e < P * NN; e += kClThreads) {
+            const int kl = e / NN, y = e % NN, k = k0 + kl;
+            ao[k + (size_t)y * NN] = fix[kl * NN + y];
+            ao[(h + (k + s_end) % h) + (size_t)y * NN] = mov[((kl + s_end) % (P + 1)) * NN + y];
+        }
+    }
+    cluster.sync();
+    if (rank == 0 && tid == 0) {
+        rotated[pair] = total;
+        if (rot_count && total) atomicAdd(rot_count, (unsigned long long)total);
+        if (bad && status) atomicExch(status, HSVD_ERR_RANK);
+        if (trace) {
+            double mx = 0.0, sm2 = 0.0;
+            for (int r = 0; r < C; ++r) {
+                mx = fmax(mx, tr_max[r]);
+                sm2 += tr_sum[r];
+            }
+            float *rec = trace + (size_t)visit[pair] * HSVD_TRACE_FIELDS;
+            rec[0] = (float)mx;
+            rec[1] = (float)sqrt(sm2);
+            rec[2] = (float)total;
+            rec[3] = rec_meanI;
+            rec[4] = rec_meanJ;
+            rec[5] = rec_hyp;
+        }
+    }
+}
+
 template <int NN>
 cudaError_t solve_cluster_impl(int npairs, const double *part, int nsplit, int full_part, double *A,
                                const int8_t *sgn_cols, const int *col0, const int8_t *sgn_direct, double tol,
@@ -289,6 +639,17 @@ cudaError_t solve_cluster_impl(int npairs, const double *part, int nsplit, int f
                                int *rotated, unsigned long long *rot_count, int *status, int *dexp,
                                const int *visit, float *trace, cudaStream_t st) {
     constexpr int C = ClusterOf<NN>::C, R = NN / C;
+    if (mode == 1) {
+        constexpr int P = NN / 2 / C;
+        const size_t smem_x = (size_t)(P * NN + (P + 1) * NN + R * NN) * sizeof(double);
+        cudaError_t e = cudaFuncSetAttribute(k_solve_cross<NN, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem_x);
+        if (e != cudaSuccess) return e;
+        k_solve_cross<NN, C><<<npairs * C, kClThreads, smem_x, st>>>(part, nsplit, full_part, A, sgn_cols, col0,
+                                                                    sgn_direct, tol, Wp, rotated, rot_count,
+                                                                    status, dexp, visit, trace);
+        return cudaGetLastError();
+    }
     const size_t smem = (size_t)(2 * R * (NN + 1) + R * NN) * sizeof(double);
     cudaError_t e = cudaFuncSetAttribute(k_solve_cluster<NN, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
