@@ -85,6 +85,8 @@ def parse():
                     help="Gram/update arithmetic (FP64 FMA or BF16 slices on the tensor cores), optionally "
                          "with the learned skip network")
     ap.add_argument("--tau", type=float, default=0.5, help="learned form: skip threshold on P(rotation)")
+    ap.add_argument("--count", type=int, default=BATCH_COUNT, help="batch10k: number of factors")
+    ap.add_argument("--group-width", type=int, default=0, help="batch10k: 0 autotunes, else 256/512/1024")
     ap.add_argument("--block", type=int, default=0, help="block width (0: the workload's)")
     return ap.parse_args()
 
@@ -232,7 +234,8 @@ def run_batched(args):
         build_lib.build()
     if world > 1:
         dist.barrier()
-    facs = workloads.batch(BATCH_COUNT, seed=4 + rank)
+    count = args.count
+    facs = workloads.batch(count, seed=4 + rank)
     ms_ = [G.shape[0] for G, _ in facs]
     ns_ = [G.shape[1] for G, _ in facs]
     # one device buffer per array kind, factors as column-major views into it
@@ -255,7 +258,7 @@ def run_batched(args):
     vbuf, vv = packed([n * n for n in ns_], torch.float64, dev)
     Us = [u.view(n, m).t() for u, m, n in zip(uv, ms_, ns_)]
     Vs = [v.view(n, n).t() for v, n in zip(vv, ns_)]
-    opts = api.make_batch_opts(max_sweeps=30)
+    opts = api.make_batch_opts(max_sweeps=30, group_width=args.group_width)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -301,7 +304,7 @@ def run_batched(args):
     # bounded sample, scaled to the whole batch by the effective flops
     loop = None
     if rank == 0:
-        idx = list(range(0, BATCH_COUNT, BATCH_COUNT // 40))
+        idx = list(range(0, count, max(1, count // 40)))
         t_loop, f_loop = 0.0, 0.0
         for k in idx:
             torch.cuda.synchronize()
@@ -314,7 +317,7 @@ def run_batched(args):
         est_ms = t_loop * 1e3 * eff / f_loop
         loop = {"ms_estimated": est_ms, "tflops": f_loop / t_loop / 1e12, "speedup_of_batched": est_ms / ms,
                 "sample": "%d of %d factors (every %dth), one hsvd_solve call each, %.2f s measured, scaled by "
-                          "effective flops" % (len(idx), BATCH_COUNT, BATCH_COUNT // 40, t_loop)}
+                          "effective flops" % (len(idx), count, max(1, count // 40), t_loop)}
 
     e2e = None
     if not args.no_e2e:
@@ -340,7 +343,7 @@ def run_batched(args):
         import oracle
 
         oracle.build()
-        idx = list(range(0, BATCH_COUNT, BATCH_COUNT // 20))
+        idx = list(range(0, count, max(1, count // 20)))
         t0 = time.perf_counter()
         f = 0.0
         for k in idx:
@@ -350,14 +353,15 @@ def run_batched(args):
         dt = time.perf_counter() - t0
         cpu = {"value": f / dt / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
                "sample": "%d of %d factors (every %dth), complete row-cyclic FP64 oracle solves, %.1f s"
-                         % (len(idx), BATCH_COUNT, BATCH_COUNT // 20, dt)}
+                         % (len(idx), count, max(1, count // 20), dt)}
 
     if rank == 0:
         line = {
             "metric": "HSVD effective TFLOP/s (batched form, sigma rel-err <= 1e-12)", "value": value,
             "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOADS["batch10k"][1], "count": BATCH_COUNT, "form": "batched",
+            "config": {"workload": WORKLOADS["batch10k"][1].replace("10000", str(count)), "count": count,
+                       "form": "batched", "group_width": args.group_width or "autotuned",
                        "method": "pointwise per factor, diagonal sorting", "tol": "n 2^-53 per factor",
                        "max_sweeps_run": int(r.info.max_sweeps_run),
                        "l2": "flushed (256 MB write) between steps; inputs 2.6 GB > L2",
@@ -398,11 +402,12 @@ def train_skip_model(block, prec, log):
 
 def run_reference_batched(args, oracle):
     """The oracle on the batch workload: each step solves a bounded sample of
-    the factors completely (every 500th), rate scaled in effective flops."""
+    the factors completely , rate scaled in effective flops."""
     from paper_1008_1371_gb300 import workloads
 
-    facs = workloads.batch(BATCH_COUNT, seed=4)
-    idx = list(range(0, BATCH_COUNT, 500))
+    count = args.count
+    facs = workloads.batch(count, seed=4)
+    idx = list(range(0, count, max(1, count // 20)))
     times, flops = [], []
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
@@ -416,13 +421,13 @@ def run_reference_batched(args, oracle):
             flops.append(f)
     value = sum(flops) / sum(times) / 1e12
     per = sum(times) / len(times)
-    sample = "%d of %d factors (every 500th) solved completely by the row-cyclic FP64 oracle per step" % (
-        len(idx), BATCH_COUNT)
+    sample = "%d of %d factors (every %dth) solved completely by the row-cyclic FP64 oracle per step" % (
+        len(idx), count, max(1, count // 20))
     line = {
         "impl": "reference", "metric": "HSVD effective TFLOP/s (batched form, sigma rel-err <= 1e-12)",
         "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOADS["batch10k"][1], "count": BATCH_COUNT,
+        "data": "synthetic", "config": {"workload": WORKLOADS["batch10k"][1].replace("10000", str(count)), "count": count,
                                         "sample": sample},
         "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

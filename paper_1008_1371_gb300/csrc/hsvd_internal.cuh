@@ -57,6 +57,25 @@ __device__ __forceinline__ bool rotation_params(double aii, double ajj, double a
     return true;
 }
 
+// The test of Eq. 2.3 and the rotation of Sec. 2, evaluated side by side
+// (both depend only on the three entries, so their square roots and divides
+// overlap; the rotation is discarded when the pair passes).  Returns 0 (the
+// pair passes), 1 (rotate with t, c) or 2 (rank deficient); t = 0, c = 1
+// unless it returns 1.
+__device__ __forceinline__ int pair_decision(double aii, double ajj, double aij, int hyp, double tol,
+                                             double &t, double &c) {
+    const bool passes = pair_passes(aii, ajj, aij, tol);
+    double tt, cc;
+    const bool ok = rotation_params(aii, ajj, aij, hyp, tt, cc);
+    t = 0.0;
+    c = 1.0;
+    if (passes) return 0;
+    if (!ok) return 2;
+    t = tt;
+    c = cc;
+    return 1;
+}
+
 // k-th pivot pair (a < b) of step `s` of the modified modulus strategy on r
 // indices (Sec. 2): the pairs with a + b = c (mod r), c = (r - 1 + s) mod r,
 // plus (c/2, c/2 + r/2) for even c.  Slots are ordered by their smaller index.

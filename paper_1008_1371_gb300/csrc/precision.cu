@@ -107,7 +107,16 @@ k_gram_x(const double *__restrict__ G, int64_t rows, int64_t ldg, const int *__r
         const int c = NNX / 2 * (int)half + cc;
         const double *g = G + (int64_t)(c < NNX / 2 ? cI + c : cJ + c - NNX / 2) * ldg;
         int e = -2000;
-        for (int64_t r = r0 + lane; r < r1; r += 32) e = max(e, exp_bound(g[r]));
+        // eight loads in flight per lane
+        int64_t r = r0 + lane;
+        for (; r + 7 * 32 < r1; r += 8 * 32) {
+            double x[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) x[u] = g[r + u * 32];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) e = max(e, exp_bound(x[u]));
+        }
+        for (; r < r1; r += 32) e = max(e, exp_bound(g[r]));
         e = warp_max_i(e);
         if (lane == 0) {
             e = e < -1000 ? 0 : e;
@@ -321,11 +330,17 @@ k_update_x(double *__restrict__ X, int64_t rowsX, int64_t ldx, double *__restric
         const int i = tid & (kUpdRows - 1), part = tid / kUpdRows;
         const int64_t row = d.r0 + i;
         int e = -2000;
-        if (row < d.rows)
-            for (int k = part * kPer; k < part * kPer + kPer; ++k) {
+        if (row < d.rows) {
+            double x[kPer];
+#pragma unroll
+            for (int u = 0; u < kPer; ++u) {
+                const int k = part * kPer + u;
                 const int col = k < NNX / 2 ? d.cI + k : d.cJ + k - NNX / 2;
-                e = max(e, exp_bound(d.M[row + (int64_t)col * d.ld]) - dk[s][k]);
+                x[u] = d.M[row + (int64_t)col * d.ld];
             }
+#pragma unroll
+            for (int u = 0; u < kPer; ++u) e = max(e, exp_bound(x[u]) - dk[s][part * kPer + u]);
+        }
         atomicMax(&Erow[s][i], e);
         __syncthreads();
         if (tid < kUpdRows && Erow[s][tid] < -1000) Erow[s][tid] = 0;

@@ -241,11 +241,12 @@ __device__ void pw_solve(const double *__restrict__ G, int64_t ldg, int m, int n
                     }
                 }
                 double my_t = 0.0, my_c = 1.0;
-                int my_rot = 0, my_hyp = -1;
-                if (lane < nbatch && !pair_passes(my_app, my_aqq, my_apq, tol)) {
-                    my_hyp = (sh.sg[my_p] == sh.sg[my_q]) ? -1 : 1;
-                    if (rotation_params(my_app, my_aqq, my_apq, my_hyp, my_t, my_c)) my_rot = 1;
-                    else atomicExch(&sc.err, HSVD_ERR_RANK);
+                int my_rot = 0;
+                const int my_hyp = (sh.sg[my_p] == sh.sg[my_q]) ? -1 : 1;
+                if (lane < nbatch) {
+                    const int d = pair_decision(my_app, my_aqq, my_apq, my_hyp, tol, my_t, my_c);
+                    my_rot = d == 1;
+                    if (d == 2) atomicExch(&sc.err, HSVD_ERR_RANK);
                 }
                 const unsigned rmask = __ballot_sync(0xffffffffu, my_rot);
                 for (int j = 0; j < nbatch; ++j) {

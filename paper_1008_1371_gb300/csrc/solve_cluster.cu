@@ -34,9 +34,15 @@ namespace hsvd {
 namespace {
 
 constexpr int kClThreads = 256;
+constexpr int kCrossThreads = kClThreads + 32;  // cross pass: 8 mixing warps + the look-ahead warp
 
-// barrier 1 among the last n threads of the CTA (warps 1..)
-__device__ __forceinline__ void grp_bar_mix(int n) { asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory"); }
+// the mixing threads' barrier: barrier 1 among the last n threads of the CTA
+// (warps 1..) when warp 0 runs ahead, else the whole CTA
+template <bool LA>
+__device__ __forceinline__ void mix_sync(int n) {
+    if (LA) asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory");
+    else __syncthreads();
+}
 
 template <int NN>
 struct ClusterOf {
@@ -176,12 +182,10 @@ k_solve_cluster(const double *__restrict__ part, int nsplit, int full_part, doub
                 const int k = tid, p = P[buf][k], q = Q[buf][k];
                 const double apq = Apq[buf][k], app = D[p], aqq = D[q];
                 const int hyp = (sg[p] == sg[q]) ? -1 : 1;
-                double t = 0.0, c = 1.0;
-                int rot = 0;
-                if (!pair_passes(app, aqq, apq, tol)) {
-                    if (rotation_params(app, aqq, apq, hyp, t, c)) rot = 1;
-                    else s_flag = HSVD_ERR_RANK;
-                }
+                double t, c;
+                const int d = pair_decision(app, aqq, apq, hyp, tol, t, c);
+                const int rot = d == 1;
+                if (d == 2) s_flag = HSVD_ERR_RANK;
                 T[buf][k] = t;
                 Cc[buf][k] = c;
                 Hy[buf][k] = hyp;
@@ -300,14 +304,15 @@ k_solve_cluster(const double *__restrict__ part, int nsplit, int full_part, doub
 // and their order (column mix first on even steps, row mix first on odd
 // steps, Eq. 2.6 on the diagonal, zeros at the pair) are the oracle's, so the
 // result is bit-identical to it and to k_solve_cluster.
-template <int NN, int C>
-__global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kClThreads)
+template <int NN, int C, bool LA>
+__global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(LA ? kCrossThreads : kClThreads, 3)
 k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double *__restrict__ A_io,
               const int8_t *__restrict__ sgn_cols, const int *__restrict__ col0,
               const int8_t *__restrict__ sgn_direct, double tol, double *__restrict__ Wout,
               int *__restrict__ rotated, unsigned long long *__restrict__ rot_count, int *__restrict__ status,
               int *__restrict__ dexp, const int *__restrict__ visit, float *__restrict__ trace) {
     constexpr int h = NN / 2, P = h / C, RW = NN / C, B = NN / 2;
+    constexpr int kT = LA ? kCrossThreads : kClThreads;
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     const int pair = blockIdx.x / C;
@@ -323,7 +328,7 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
     __shared__ int sg[NN];
     __shared__ double T[2][h], Cc[2][h], Apq[2][h];
     __shared__ int Fl[2][h];          // bit 0: rotate, bit 1: rank deficient
-    __shared__ double tr_max[C], tr_sum[C], tr_red[2][kClThreads / 32];
+    __shared__ double tr_max[C], tr_sum[C], tr_red[2][kT / 32];
 
     auto entry = [&](int x, int y) -> double {
         if (!part) return A_io[(size_t)pair * NN * NN + x + y * NN];
@@ -334,18 +339,18 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
         for (int s = 0; s < nsplit; ++s) v += pp[(size_t)s * NN * NN];
         return v;
     };
-    for (int x = tid; x < NN; x += kClThreads) {
+    for (int x = tid; x < NN; x += kT) {
         if (sgn_direct) sg[x] = sgn_direct[(size_t)pair * NN + x];
         else sg[x] = sgn_cols[col0[2 * pair + (x >= B)] + (x % B)];
         D[x] = entry(x, x);
         if (dexp && rank == 0) dexp[(size_t)pair * NN + x] = D[x] > 0.0 ? (ilogb(D[x]) >> 1) : 0;
     }
-    for (int e = tid; e < P * NN; e += kClThreads) {
+    for (int e = tid; e < P * NN; e += kT) {
         const int kl = e / NN, y = e % NN;
         fix[kl * NN + y] = entry(k0 + kl, y);
         mov[kl * NN + y] = entry(h + k0 + kl, y);  // step 0: pair k with row h + k, ring slot kl
     }
-    for (int e = tid; e < RW * NN; e += kClThreads) {
+    for (int e = tid; e < RW * NN; e += kT) {
         const int x = e / NN, y = e % NN;
         Wl[x * NN + y] = (w0 + x == y) ? 1.0 : 0.0;
     }
@@ -355,7 +360,7 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
     double rec_max = 0.0, rec_sum = 0.0;
     if (trace) {
         double lmax = 0.0, lsum = 0.0;
-        for (int e = tid; e < P * h; e += kClThreads) {
+        for (int e = tid; e < P * h; e += kT) {
             const int kl = e / h, y = h + e % h, x = k0 + kl;
             const double dd = D[x] * D[y];
             const double sc = dd > 0.0 ? fabs(fix[kl * NN + y]) / sqrt(dd) : 0.0;
@@ -370,7 +375,7 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
         }
         __syncthreads();
         if (tid == 0) {
-            for (int w = 0; w < kClThreads / 32; ++w) {
+            for (int w = 0; w < kT / 32; ++w) {
                 rec_max = fmax(rec_max, tr_red[0][w]);
                 rec_sum += tr_red[1][w];
             }
@@ -401,12 +406,8 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
             const double apq = fix[kl * NN + q];
             const double app = D[p], aqq = D[q];
             const int hyp = (sg[p] == sg[q]) ? -1 : 1;
-            double t = 0.0, c = 1.0;
-            int fl = 0;
-            if (!pair_passes(app, aqq, apq, tol)) {
-                if (rotation_params(app, aqq, apq, hyp, t, c)) fl = 1;
-                else fl = 2;
-            }
+            double t, c;
+            const int fl = pair_decision(app, aqq, apq, hyp, tol, t, c);
             const int b = s & 1;
             for (int r = 0; r < C; ++r) {
                 *cluster.map_shared_rank(&T[b][k], r) = t;
@@ -425,7 +426,9 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
     // of a_kq' and of the two diagonal entries with the same operations as the
     // bulk update below, and computes the (t, c) of pair (k, q') for step
     // s + 1 while warps 1..7 update the rows (named barrier 1).
-    constexpr int kMixThreads = kClThreads - 32;
+    // Without the look-ahead (LA = false) every warp mixes and the owners
+    // compute the next parameters after the update.
+    constexpr int kMixThreads = LA ? kT - 32 : kT;
     const int warp = tid >> 5, lane = tid & 31;
     int total = 0, bad = 0, s_end = h - 1;
     for (int s = 0; s < h; ++s) {
@@ -433,7 +436,7 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
         double nx_t = 0.0, nx_c = 1.0, nx_apq = 0.0;
         int nx_fl = 0;
         double e_kj = 0.0, e_kq = 0.0, e_qj = 0.0, e_qq = 0.0, d_k = 0.0, d_q = 0.0;
-        const bool ahead = warp == 0 && lane < P && s + 1 < h;
+        const bool ahead = LA && warp == 0 && lane < P && s + 1 < h;
         if (ahead) {
             const int kl = lane, k = k0 + kl, j = (k + 1) % h, q2 = h + (j + s) % h;
             const double *rk = fix + kl * NN, *rq = mov + ((kl + s) % (P + 1)) * NN;
@@ -446,13 +449,15 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
         }
         // every CTA sees every pair's flags: the same decision everywhere
         const int f = tid < h ? Fl[b][tid] : 0;
+        const int nrot = __syncthreads_count(f & 1);
         bad = __syncthreads_or(f & 2);
         if (bad) {
             s_end = s;
             break;
         }
+        total += nrot;
         auto slot = [&](int kl) { return (kl + s) % (P + 1); };
-        if (warp == 0) {
+        if (LA && warp == 0) {
             if (ahead) {
                 const int kl = lane, k = k0 + kl, j = (k + 1) % h, q2 = h + (j + s) % h, qk = h + (k + s) % h;
                 const int fk = Fl[b][k] & 1, fj = Fl[b][j] & 1;
@@ -477,28 +482,11 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
                 const double app = fk ? fma(htk, Apq[b][k], d_k) : d_k;
                 const double aqq = fj ? fma(tj, Apq[b][j], d_q) : d_q;
                 const int hyp = (sg[k] == sg[q2]) ? -1 : 1;
-                // the test and the rotation are independent: both are evaluated
-                const bool passes = pair_passes(app, aqq, v, tol);
-                double t, c;
-                const bool ok = rotation_params(app, aqq, v, hyp, t, c);
+                nx_fl = pair_decision(app, aqq, v, hyp, tol, nx_t, nx_c);
                 nx_apq = v;
-                if (!passes) {
-                    if (ok) {
-                        nx_t = t;
-                        nx_c = c;
-                        nx_fl = 1;
-                    } else {
-                        nx_fl = 2;
-                    }
-                }
-            }
-            if (tid == 0) {
-                int nrot = 0;
-                for (int k = 0; k < h; ++k) nrot += Fl[b][k] & 1;
-                total += nrot;
             }
         } else {
-            const int mt = tid - 32;
+            const int mt = LA ? tid - 32 : tid;
             // the column mix on every owned row of A and of W: pair j's columns j and h + (j + s) mod h
             auto col_mix = [&](bool with_w) {
                 constexpr int nA = 2 * P * h, nW = RW * h;
@@ -550,14 +538,14 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
             };
             if ((s & 1) == 0) {
                 col_mix(true);
-                grp_bar_mix(kMixThreads);
+                mix_sync<LA>(kMixThreads);
                 row_mix(false);
             } else {
                 row_mix(true);
-                grp_bar_mix(kMixThreads);
+                mix_sync<LA>(kMixThreads);
                 col_mix(false);
             }
-            grp_bar_mix(kMixThreads);
+            mix_sync<LA>(kMixThreads);
             // Eq. 2.6 on the replicated diagonal, and the owned pairs' own entries
             if (mt < h && (Fl[b][mt] & 1)) {
                 const int p = mt, q = h + (mt + s) % h;
@@ -582,7 +570,8 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
             const int dst = (rank + C - 1) % C;
             double *src = mov + slot(0) * NN;
             double *rdst = cluster.map_shared_rank(mov, dst) + ((P + s) % (P + 1)) * NN;
-            for (int y = tid; y < NN; y += kClThreads) rdst[y] = src[y];
+            for (int y = tid; y < NN; y += kT) rdst[y] = src[y];
+            if (!LA) params_out(s + 1);
             if (ahead) {
                 const int k = k0 + lane, nb = (s + 1) & 1;
                 for (int r = 0; r < C; ++r) {
@@ -597,14 +586,14 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
     }
     // outputs: own rows of W (column-major W_P), and A_P when asked for
     double *wo = Wout + (size_t)pair * NN * NN;
-    for (int e = tid; e < RW * NN; e += kClThreads) {
+    for (int e = tid; e < RW * NN; e += kT) {
         const int x = e / NN, y = e % NN;
         wo[(w0 + x) + (size_t)y * NN] = Wl[x * NN + y];
     }
     if (!part) {
         // rows where the pass ended: fixed rows k, partner rows h + (k + s_end) mod h
         double *ao = A_io + (size_t)pair * NN * NN;
-        for (int e = tid; e < P * NN; e += kClThreads) {
+        for (int e = tid; e < P * NN; e += kT) {
             const int kl = e / NN, y = e % NN, k = k0 + kl;
             ao[k + (size_t)y * NN] = fix[kl * NN + y];
             ao[(h + (k + s_end) % h) + (size_t)y * NN] = mov[((kl + s_end) % (P + 1)) * NN + y];
@@ -642,12 +631,15 @@ cudaError_t solve_cluster_impl(int npairs, const double *part, int nsplit, int f
     if (mode == 1) {
         constexpr int P = NN / 2 / C;
         const size_t smem_x = (size_t)(P * NN + (P + 1) * NN + R * NN) * sizeof(double);
-        cudaError_t e = cudaFuncSetAttribute(k_solve_cross<NN, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        // the look-ahead warp pays at b = 64 (measured), not at b <= 32
+        constexpr bool LA = NN >= 128;
+        constexpr int threads = LA ? kCrossThreads : kClThreads;
+        cudaError_t e = cudaFuncSetAttribute(k_solve_cross<NN, C, LA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem_x);
         if (e != cudaSuccess) return e;
-        k_solve_cross<NN, C><<<npairs * C, kClThreads, smem_x, st>>>(part, nsplit, full_part, A, sgn_cols, col0,
-                                                                    sgn_direct, tol, Wp, rotated, rot_count,
-                                                                    status, dexp, visit, trace);
+        k_solve_cross<NN, C, LA><<<npairs * C, threads, smem_x, st>>>(part, nsplit, full_part, A, sgn_cols, col0,
+                                                                     sgn_direct, tol, Wp, rotated, rot_count,
+                                                                     status, dexp, visit, trace);
         return cudaGetLastError();
     }
     const size_t smem = (size_t)(2 * R * (NN + 1) + R * NN) * sizeof(double);

@@ -182,3 +182,30 @@ def test_trained_network_saves_gram_work(api):
     rel = (lm.sigma - plain.sigma).abs() / plain.sigma
     assert float(rel.max()) <= 1e-11
     assert lm.pair_visits < plain.pair_visits, (lm.pair_visits, plain.pair_visits, lm.sweeps, plain.sweeps)
+
+
+def test_full_size_graded8192_learned_vs_plain(api):
+    """The learned configuration at full size (graded 8192, condition 1e8,
+    b = 64, split-precision products to keep the test short): the masked run
+    ends with a full plain sweep, forms fewer Grams, and agrees with the plain
+    run; the invariants of Eq. 1.1 hold at this size."""
+    from paper_1008_1371_gb300 import learn
+
+    train_set = [W.graded(1024, decades=d, seed=s) for d, s in ((6.0, 100), (4.0, 101), (8.0, 102))]
+    X, y = learn.collect(train_set, block_w=64, precision=1)
+    params, _ = learn.train(X, y, steps=400, lr=3e-3, batch=4096, seed=0)
+    n = 8192
+    G, J = W.graded(n, decades=8.0, seed=5)
+    Gd = torch.from_numpy(np.asfortranarray(G)).to(DEV)
+    Jd = torch.from_numpy(J).to(DEV)
+    kw = dict(method=api.HSVD_METHOD_BLOCKED, block_w=64, sort=False, precision=1)
+    plain = api.hsvd_solve_ex(Gd, Jd, api.make_opts(max_sweeps=40, **kw))
+    lm = api.hsvd_solve_ex(Gd, Jd, api.make_opts(max_sweeps=80, skip_model=params, **kw))
+    assert plain.status == 0 and lm.status == 0 and lm.judge_sweeps >= 1
+    assert lm.pair_visits < plain.pair_visits
+    rel = float(((lm.sigma - plain.sigma).abs() / plain.sigma).max())
+    assert rel <= 1e-12, rel
+    I = torch.eye(n, dtype=torch.float64, device=DEV)
+    assert float((lm.U.T @ lm.U - I).abs().max()) <= 1e-12 * n
+    Jm = torch.diag(Jd.to(torch.float64))
+    assert float((lm.V.T @ Jm @ lm.V - Jm).abs().max()) / max(1.0, float(lm.V.abs().max()) ** 2) <= 1e-12 * n
