@@ -215,29 +215,65 @@ __device__ void pw_solve(const double *__restrict__ G, int64_t ldg, int m, int n
     for (sweep = 1; sweep <= max_sweeps; ++sweep) {
         for (int s = 0; s < n_pad; ++s) {
             // A warp takes the pairs k = warp, warp + kW, ... in batches of up
-            // to 32: the dots of every pair of the batch (warp-wide, every lane
-            // ends with the sums), then lane j computes pair j's rotation, then
-            // the column updates.  Pairs of a step are disjoint, so this is the
-            // same arithmetic as one pair after the other.
+            // to 32: the dots of every pair of the batch, then lane j computes
+            // pair j's rotation, then the column updates.  Pairs of a step are
+            // disjoint, so this is the same as one pair after the other.  The
+            // dots are reduced four pairs at a time: a butterfly that halves
+            // the values a lane carries at the first two levels (lanes with bit
+            // 4 clear keep pairs 0-1, bit 3 clear the first of those), then sums
+            // the eight lanes that hold the same pair; 18 shuffle-adds for four
+            // pairs instead of 15 per pair.
             for (int k0 = warp; k0 < half; k0 += 32 * kW) {
                 const int nbatch = min(32, (half - k0 + kW - 1) / kW);
                 double my_app = 0.0, my_aqq = 0.0, my_apq = 0.0;
                 int my_p = 0, my_q = 0;
-                for (int j = 0; j < nbatch; ++j) {
+                if (lane < nbatch) {
                     int a, b;
-                    modulus_pair(n_pad, s, k0 + j * kW, a, b);
-                    const int p = sh.pos[a], q = sh.pos[b];
-                    double app = 0.0, aqq = 0.0, apq = 0.0;
-                    pw_dots(sh.G + (size_t)p * m_pad, sh.G + (size_t)q * m_pad, m_pad, lane, app, aqq, apq);
-                    app = warp_sum(app);
-                    aqq = warp_sum(aqq);
-                    apq = warp_sum(apq);
-                    if (lane == j) {
-                        my_app = app;
-                        my_aqq = aqq;
-                        my_apq = apq;
-                        my_p = p;
-                        my_q = q;
+                    modulus_pair(n_pad, s, k0 + lane * kW, a, b);
+                    my_p = sh.pos[a];
+                    my_q = sh.pos[b];
+                }
+                for (int j0 = 0; j0 < nbatch; j0 += 4) {
+                    double v[12];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        double app = 0.0, aqq = 0.0, apq = 0.0;
+                        if (j0 + u < nbatch) {
+                            const int p = __shfl_sync(0xffffffffu, my_p, j0 + u);
+                            const int q = __shfl_sync(0xffffffffu, my_q, j0 + u);
+                            pw_dots(sh.G + (size_t)p * m_pad, sh.G + (size_t)q * m_pad, m_pad, lane, app, aqq, apq);
+                        }
+                        v[3 * u] = app;
+                        v[3 * u + 1] = aqq;
+                        v[3 * u + 2] = apq;
+                    }
+                    const bool h16 = lane & 16, h8 = lane & 8;
+                    double w[6], x[3];
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) {
+                        const double send = h16 ? v[i] : v[6 + i];
+                        w[i] = (h16 ? v[6 + i] : v[i]) + __shfl_xor_sync(0xffffffffu, send, 16);
+                    }
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        const double send = h8 ? w[i] : w[3 + i];
+                        x[i] = (h8 ? w[3 + i] : w[i]) + __shfl_xor_sync(0xffffffffu, send, 8);
+                    }
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        x[i] += __shfl_xor_sync(0xffffffffu, x[i], 4);
+                        x[i] += __shfl_xor_sync(0xffffffffu, x[i], 2);
+                        x[i] += __shfl_xor_sync(0xffffffffu, x[i], 1);
+                    }
+                    // lanes 8u .. 8u + 7 hold pair j0 + u; lane j0 + u takes it
+                    const int src = 8 * ((lane - j0) & 3);
+                    const double s0 = __shfl_sync(0xffffffffu, x[0], src);
+                    const double s1 = __shfl_sync(0xffffffffu, x[1], src);
+                    const double s2 = __shfl_sync(0xffffffffu, x[2], src);
+                    if (lane >= j0 && lane < j0 + 4) {
+                        my_app = s0;
+                        my_aqq = s1;
+                        my_apq = s2;
                     }
                 }
                 double my_t = 0.0, my_c = 1.0;
