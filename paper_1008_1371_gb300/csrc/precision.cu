@@ -48,18 +48,25 @@ __device__ __forceinline__ int warp_max_i(int v) {
 }
 
 // The 36 slice products of one K step (16 k): slice s of A at a_base + s *
-// a_stride bytes, of B at b_base + s * b_stride; koff selects the K step.
+// a_stride bytes, of B at b_base + s * b_stride; koff selects the K step.  The
+// descriptors of one K step differ only in the start-address field (address
+// >> 4 in the low 14 bits; every address here is below 2^18), so they are
+// formed once and advanced by one add per slice.
 __device__ __forceinline__ void issue_products(uint32_t tmem, uint32_t a_base, uint32_t a_stride, uint32_t b_base,
                                                uint32_t b_stride, uint32_t koff, uint32_t sbo, uint32_t idesc,
                                                int (&inited)[8]) {
-    for (int a = 1; a <= kSlices; ++a)
+    const uint64_t da0 = smem_desc(a_base + koff, 128, sbo), db0 = smem_desc(b_base + koff, 128, sbo);
+    const uint64_t as = a_stride >> 4, bs = b_stride >> 4;
+#pragma unroll
+    for (int a = 1; a <= kSlices; ++a) {
+        const uint64_t da = da0 + (uint64_t)(a - 1) * as;
+#pragma unroll
         for (int b = 1; a + b <= kSlices + 1; ++b) {
             const int acc = a + b - 2;
-            const uint64_t da = smem_desc(a_base + (a - 1) * a_stride + koff, 128, sbo);
-            const uint64_t db = smem_desc(b_base + (b - 1) * b_stride + koff, 128, sbo);
-            mma(tmem + (uint32_t)acc * kN, da, db, idesc, (uint32_t)inited[acc]);
+            mma(tmem + (uint32_t)acc * kN, da, db0 + (uint64_t)(b - 1) * bs, idesc, (uint32_t)inited[acc]);
             inited[acc] = 1;
         }
+    }
 }
 
 // this thread's lane and 8 columns [c0, c0+8) of all eight accumulators: the
@@ -165,7 +172,9 @@ k_gram_x(const double *__restrict__ G, int64_t rows, int64_t ldg, const int *__r
         fence_proxy_async();
         // the products of tile t - 1 are done in this CTA: its buffer is free
         // for tile t + 1 in both CTAs once both have passed the barrier below
-        if (t >= 1 && !s_fail && !mbar_wait(&mbar[(t - 1) & 1], ((t - 1) >> 1) & 1, kWaitIter)) s_fail = 1;
+        // one thread waits; the others block in the cluster barrier (no polling)
+        if (tid == 0 && t >= 1 && !s_fail && !mbar_wait(&mbar[(t - 1) & 1], ((t - 1) >> 1) & 1, kWaitIter))
+            s_fail = 1;
         fence_before();
         cluster_sync();
         fence_after();
@@ -177,9 +186,10 @@ k_gram_x(const double *__restrict__ G, int64_t rows, int64_t ldg, const int *__r
             commit(&mbar[t & 1]);
         }
     }
-    if (ntiles > 0 && !s_fail && !mbar_wait(&mbar[(ntiles - 1) & 1], ((ntiles - 1) >> 1) & 1, kWaitIter)) s_fail = 1;
-    fence_after();
+    if (tid == 0 && ntiles > 0 && !s_fail && !mbar_wait(&mbar[(ntiles - 1) & 1], ((ntiles - 1) >> 1) & 1, kWaitIter))
+        s_fail = 1;
     __syncthreads();
+    fence_after();
     if (!s_fail) {
         // lane c = row of A_P; warp group h2 takes TMEM columns [16 h2, 16 h2 + 16)
         const int q = warp & 3, c = 32 * q + lane, h2 = warp >> 2;
@@ -256,15 +266,27 @@ k_wprep_x(const double *__restrict__ Wp, const int *__restrict__ dexp, const int
 // transposed, Out^T = W'^T X'^T: A = W'^T (128 x 128 from k_wprep_x, bulk
 // copies per k quarter), B = X' (the chunk's 64 rows, K-major over the panel's
 // 128 columns), split per row after balancing.  D is 128 (columns j) x 64 (rows).
-// Software pipeline over the flat sequence of k-quarter tiles of all items of
-// the CTA: A and B tiles are double-buffered, the split of tile g + 1 (and the
-// row exponents of the next item) run while the products of tile g are on the
-// tensor cores; only the epilogue (TMEM -> FP64) waits for the products.
+// Warp-specialised pipeline over the flat sequence of k-quarter tiles of the
+// CTA's items, A and B tiles double-buffered:
+//   - warps 1..15 (producers) wait until the products that last read a
+//     buffer are done (mbarrier `empty`), start the bulk copy of the A tile
+//     and split the B tile, then arrive on `full` (two arrivals: the copy's
+//     expect-tx and the split);
+//   - warp 0, lane 0 waits on `full`, issues the 72 products of the tile and
+//     commits them to `empty`;
+//   - after the producers have filled the first tile of item i + 1, all 16
+//     warps form item i's epilogue (TMEM -> FP64), then warp 0 issues item
+//     i + 1's products: the eight accumulators take all of TMEM, so only the
+//     epilogue waits for the tensor cores.
+// Every wait is bounded; after a failure each role still passes the same
+// barriers (no deadlock) and the kernel reports HSVD_ERR_CUDA.
 struct UpdItem {
     double *M;
     int64_t ld, rows, r0;
     int pair, which, cI, cJ;
 };
+
+__device__ __forceinline__ void bar_named(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 
 __global__ void __launch_bounds__(kThrU, 1)
 k_update_x(double *__restrict__ X, int64_t rowsX, int64_t ldx, double *__restrict__ Y, int64_t rowsY, int64_t ldy,
@@ -275,10 +297,12 @@ k_update_x(double *__restrict__ X, int64_t rowsX, int64_t ldx, double *__restric
     constexpr uint32_t kATile = NNX * kUpdKT * 2;       // one slice of W'^T (8 KB)
     constexpr uint32_t kBTile = kUpdRows * kUpdKT * 2;  // one slice of X' (4 KB)
     constexpr uint32_t kABuf = kSlices * kATile, kBBuf = kSlices * kBTile;
+    constexpr int kProd = kThrU - 32;                   // producer threads (warps 1..)
+    constexpr int kTiles = NNX / kUpdKT;                // k quarters per item
     unsigned char *As = smem;                // two A buffers
     unsigned char *Bs = smem + 2 * kABuf;    // two B buffers
     __shared__ int Erow[2][kUpdRows], Fcol[2][NNX], dk[2][NNX];
-    __shared__ __align__(8) uint64_t mbar_a[2], mbar_m[2];
+    __shared__ __align__(8) uint64_t full[2], empty[2];
     __shared__ uint32_t tbase;
     __shared__ int s_fail;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -288,8 +312,8 @@ k_update_x(double *__restrict__ X, int64_t rowsX, int64_t ldx, double *__restric
     if (tid == 0) {
         s_fail = 0;
         for (int b = 0; b < 2; ++b) {
-            mbar_init(&mbar_a[b], 1);
-            mbar_init(&mbar_m[b], 1);
+            mbar_init(&full[b], 2);   // the copy's expect-tx arrival and the split's arrival
+            mbar_init(&empty[b], 1);  // the products' commit
         }
     }
     if (warp == 0) tmem_alloc(&tbase, kTmemCols);
@@ -318,149 +342,163 @@ k_update_x(double *__restrict__ X, int64_t rowsX, int64_t ldx, double *__restric
         d.cJ = col0[2 * d.pair + 1];
         return d;
     };
-    // exponents of the item into slot s (block-wide, with barriers)
-    auto setup = [&](const UpdItem &d, int s) {
-        for (int k = tid; k < NNX; k += kThrU) {
-            dk[s][k] = d.which == 0 ? dexp[(size_t)d.pair * NNX + k] : 0;
-            Fcol[s][k] = wexp[((size_t)d.pair * 2 + d.which) * NNX + k];
-        }
-        if (tid < kUpdRows) Erow[s][tid] = -2000;
-        __syncthreads();
-        constexpr int kParts = kThrU / kUpdRows, kPer = NNX / kParts;
-        const int i = tid & (kUpdRows - 1), part = tid / kUpdRows;
-        const int64_t row = d.r0 + i;
-        int e = -2000;
-        if (row < d.rows) {
-            double x[kPer];
-#pragma unroll
-            for (int u = 0; u < kPer; ++u) {
-                const int k = part * kPer + u;
-                const int col = k < NNX / 2 ? d.cI + k : d.cJ + k - NNX / 2;
-                x[u] = d.M[row + (int64_t)col * d.ld];
-            }
-#pragma unroll
-            for (int u = 0; u < kPer; ++u) e = max(e, exp_bound(x[u]) - dk[s][part * kPer + u]);
-        }
-        atomicMax(&Erow[s][i], e);
-        __syncthreads();
-        if (tid < kUpdRows && Erow[s][tid] < -1000) Erow[s][tid] = 0;
-        __syncthreads();
-    };
-    // tile g (k quarter q of item d, exponents in slot s) into buffer b
-    const int rr = lane >> 2, kp = 2 * (lane & 3);
-    auto produce = [&](const UpdItem &d, int s, int q, int b, uint32_t use) {
-        if (tid == 0) {
-            mbar_expect_tx(&mbar_a[b], kABuf);
-            bulk_g2s(As + b * kABuf, wsl + (((size_t)d.pair * 2 + d.which) * 4 + q) * kSlices * NNX * kUpdKT, kABuf,
-                     &mbar_a[b]);
-        }
-        (void)use;
-        unsigned char *Bb = Bs + b * kBBuf;
-        for (int core = warp; core < (kUpdRows / 8) * (kUpdKT / 8); core += kThrU / 32) {
-            const int i = (core / (kUpdKT / 8)) * 8 + rr, kk = (core % (kUpdKT / 8)) * 8 + kp;
-            const int k = q * kUpdKT + kk;
-            const int64_t row = d.r0 + i;
-            const int c0 = k < NNX / 2 ? d.cI + k : d.cJ + k - NNX / 2;
-            const int c1 = k + 1 < NNX / 2 ? d.cI + k + 1 : d.cJ + k + 1 - NNX / 2;
-            const double x0 = row < d.rows ? d.M[row + (int64_t)c0 * d.ld] : 0.0;
-            const double x1 = row < d.rows ? d.M[row + (int64_t)c1 * d.ld] : 0.0;
-            const long long w0 = digit_word(x0, Erow[s][i] + dk[s][k]);
-            const long long w1 = digit_word(x1, Erow[s][i] + dk[s][k + 1]);
-            const uint32_t off = core_offset(i, kk, kUpdKT);
-#pragma unroll
-            for (int sl = 0; sl < kSlices; ++sl)
-                *reinterpret_cast<uint32_t *>(Bb + sl * kBTile + off) = slice_pair(w0, w1, sl + 1);
-        }
-    };
-    auto wait_mma = [&](int64_t g) {  // the products of tile g are complete
-        if (g >= 0 && !s_fail && !mbar_wait(&mbar_m[g & 1], (uint32_t)((g >> 1) & 1), kWaitIter)) s_fail = 1;
+    // bounded wait by one thread; the caller follows it with a barrier
+    auto wait1 = [&](uint64_t *mb, int64_t use) {
+        if (!s_fail && !mbar_wait(mb, (uint32_t)((use >> 1) & 1), kWaitIter)) s_fail = 1;
     };
 
-    int64_t it = next_item(blockIdx.x);
-    int slot = 0;
-    int64_t g = 0;  // tile counter
-    int64_t issued_a = -1, issued_m = -1;
-    if (it >= 0) {
-        UpdItem cur = describe(it);
-        setup(cur, slot);
-        produce(cur, slot, 0, 0, 0);
-        issued_a = 0;
-        while (true) {
-            int64_t nit = -1;
-            UpdItem nxt = cur;
-            int inited[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            for (int q = 0; q < NNX / kUpdKT; ++q, ++g) {
+    // item i's epilogue, all 512 threads: lane j = output column, warp group
+    // h2 = rows [16 h2, 16 h2 + 16); glast = the item's last tile.  (Staging
+    // the tile through shared memory for coalesced stores measured slower.)
+    auto epilogue = [&](const UpdItem &d, int slot, int64_t glast) {
+        if (tid == 0) wait1(&empty[glast & 1], glast);
+        bar_named(2, kThrU);
+        fence_after();
+        if (!s_fail) {
+            const int qd = warp & 3, j = 32 * qd + lane, h2 = warp >> 2;
+            const int jj = j < NNX / 2 ? d.cI + j : d.cJ + j - NNX / 2;
+            constexpr int kCols = kN / (kThrU / 128);
+            for (int c0 = kCols * h2; c0 < kCols * h2 + kCols; c0 += 8) {
+                float v[8][8];
+                read_accs(tmem, 32 * qd, c0, v);
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const int i = c0 + t;
+                    const int64_t row = d.r0 + i;
+                    if (row >= d.rows) continue;
+                    float dd[8];
+#pragma unroll
+                    for (int a = 0; a < 8; ++a) dd[a] = v[a][t];
+                    d.M[row + (int64_t)jj * d.ld] = combine8(dd, Erow[slot][i] + Fcol[slot][j]);
+                }
+            }
+        }
+        fence_before();
+        bar_named(2, kThrU);
+        fence_after();
+    };
+
+    int64_t g_end = -1;  // last tile of the last item
+    if (warp > 0) {
+        // ------------------------------------------------ producers
+        const int ptid = tid - 32, pwarp = warp - 1;
+        const int rr = lane >> 2, kp = 2 * (lane & 3);
+        int64_t it = next_item(blockIdx.x);
+        int ii = 0;
+        UpdItem cur{}, prev{};
+        int64_t g = 0;
+        while (it >= 0) {
+            cur = describe(it);
+            const int slot = ii & 1;
+            // exponents of the item (producers only, barrier 1)
+            for (int k = ptid; k < NNX; k += kProd) {
+                dk[slot][k] = cur.which == 0 ? dexp[(size_t)cur.pair * NNX + k] : 0;
+                Fcol[slot][k] = wexp[((size_t)cur.pair * 2 + cur.which) * NNX + k];
+            }
+            if (ptid < kUpdRows) Erow[slot][ptid] = -2000;
+            bar_named(1, kProd);
+            {
+                constexpr int kParts = 8, kPer = NNX / kParts;
+                for (int e = ptid; e < kUpdRows * kParts; e += kProd) {
+                    const int i = e % kUpdRows, part = e / kUpdRows;
+                    const int64_t row = cur.r0 + i;
+                    int ex = -2000;
+                    if (row < cur.rows) {
+                        double x[kPer];
+#pragma unroll
+                        for (int u = 0; u < kPer; ++u) {
+                            const int k = part * kPer + u;
+                            const int col = k < NNX / 2 ? cur.cI + k : cur.cJ + k - NNX / 2;
+                            x[u] = cur.M[row + (int64_t)col * cur.ld];
+                        }
+#pragma unroll
+                        for (int u = 0; u < kPer; ++u) ex = max(ex, exp_bound(x[u]) - dk[slot][part * kPer + u]);
+                    }
+                    atomicMax(&Erow[slot][i], ex);
+                }
+            }
+            bar_named(1, kProd);
+            if (ptid < kUpdRows && Erow[slot][ptid] < -1000) Erow[slot][ptid] = 0;
+            bar_named(1, kProd);
+            for (int q = 0; q < kTiles; ++q, ++g) {
                 const int b = (int)(g & 1);
+                // the products that last read buffer b (tile g - 2) are done
+                if (ptid == 0) {
+                    if (g >= 2) wait1(&empty[b], g - 2);
+                    if (!s_fail) {
+                        mbar_expect_tx(&full[b], kABuf);
+                        bulk_g2s(As + b * kABuf,
+                                 wsl + (((size_t)cur.pair * 2 + cur.which) * 4 + q) * kSlices * NNX * kUpdKT, kABuf,
+                                 &full[b]);
+                    }
+                }
+                bar_named(1, kProd);
+                unsigned char *Bb = Bs + b * kBBuf;
+                for (int core = pwarp; core < (kUpdRows / 8) * (kUpdKT / 8); core += kProd / 32) {
+                    const int i = (core / (kUpdKT / 8)) * 8 + rr, kk = (core % (kUpdKT / 8)) * 8 + kp;
+                    const int k = q * kUpdKT + kk;
+                    const int64_t row = cur.r0 + i;
+                    const int c0 = k < NNX / 2 ? cur.cI + k : cur.cJ + k - NNX / 2;
+                    const int c1 = k + 1 < NNX / 2 ? cur.cI + k + 1 : cur.cJ + k + 1 - NNX / 2;
+                    const double x0 = row < cur.rows ? cur.M[row + (int64_t)c0 * cur.ld] : 0.0;
+                    const double x1 = row < cur.rows ? cur.M[row + (int64_t)c1 * cur.ld] : 0.0;
+                    const long long w0 = digit_word(x0, Erow[slot][i] + dk[slot][k]);
+                    const long long w1 = digit_word(x1, Erow[slot][i] + dk[slot][k + 1]);
+                    const uint32_t off = core_offset(i, kk, kUpdKT);
+#pragma unroll
+                    for (int sl = 0; sl < kSlices; ++sl)
+                        *reinterpret_cast<uint32_t *>(Bb + sl * kBTile + off) = slice_pair(w0, w1, sl + 1);
+                }
                 fence_proxy_async();
-                fence_before();
-                __syncthreads();
-                fence_after();
-                if (s_fail) break;
-                if (tid == 0) {
-                    if (!mbar_wait(&mbar_a[b], (uint32_t)((g >> 1) & 1), kWaitIter)) {
-                        s_fail = 1;
-                    } else {
+                bar_named(1, kProd);
+                if (ptid == 0 && !s_fail) mbar_arrive(&full[b]);
+                // item ii - 1's epilogue once item ii's first tile is on its way
+                if (q == 0 && ii > 0) epilogue(prev, (ii - 1) & 1, g - 1);
+            }
+            prev = cur;
+            ++ii;
+            it = next_item(it + gridDim.x);
+        }
+        if (ii > 0) epilogue(prev, (ii - 1) & 1, g - 1);
+        g_end = g - 1;
+    } else {
+        // ------------------------------------------------ warp 0: products
+        int64_t it = next_item(blockIdx.x);
+        int ii = 0;
+        UpdItem prev{};
+        int64_t g = 0;
+        while (it >= 0) {
+            const UpdItem cur = describe(it);
+            int inited[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            for (int q = 0; q < kTiles; ++q, ++g) {
+                if (q == 0 && ii > 0) epilogue(prev, (ii - 1) & 1, g - 1);
+                const int b = (int)(g & 1);
+                if (lane == 0) {
+                    wait1(&full[b], g);
+                    if (!s_fail) {
+                        fence_after();
                         const uint32_t ab = smem_addr(As + b * kABuf), bb = smem_addr(Bs + b * kBBuf);
                         for (int ks = 0; ks < kUpdKT / 16; ++ks)
                             issue_products(tmem, ab, kATile, bb, kBTile, ks * 256, sbo, idesc, inited);
-                        commit(&mbar_m[b]);
-                        issued_m = g;
+                        commit(&empty[b]);
                     }
                 }
-                // the next tile: the next k quarter, or the first of the next item
-                if (q + 1 < NNX / kUpdKT) {
-                    wait_mma(g - 1);
-                    produce(cur, slot, q + 1, b ^ 1, 0);
-                    if (tid == 0) issued_a = g + 1;
-                } else {
-                    nit = next_item(it + gridDim.x);
-                    if (nit >= 0) {
-                        nxt = describe(nit);
-                        setup(nxt, slot ^ 1);
-                        wait_mma(g - 1);
-                        produce(nxt, slot ^ 1, 0, b ^ 1, 0);
-                        if (tid == 0) issued_a = g + 1;
-                    }
-                }
+                __syncwarp();
             }
-            __syncthreads();
-            if (s_fail) break;
-            // epilogue of the item: lane j = output column, warp group h2 = rows [16 h2, 16 h2 + 16)
-            wait_mma(g - 1);
-            fence_after();
-            __syncthreads();
-            if (s_fail) break;
-            {
-                const int qd = warp & 3, j = 32 * qd + lane, h2 = warp >> 2;
-                const int jj = j < NNX / 2 ? cur.cI + j : cur.cJ + j - NNX / 2;
-                constexpr int kCols = kN / (kThrU / 128);
-                for (int c0 = kCols * h2; c0 < kCols * h2 + kCols; c0 += 8) {
-                    float v[8][8];
-                    read_accs(tmem, 32 * qd, c0, v);
-#pragma unroll
-                    for (int t = 0; t < 8; ++t) {
-                        const int i = c0 + t;
-                        const int64_t row = cur.r0 + i;
-                        if (row >= cur.rows) continue;
-                        float d[8];
-#pragma unroll
-                        for (int a = 0; a < 8; ++a) d[a] = v[a][t];
-                        cur.M[row + (int64_t)jj * cur.ld] = combine8(d, Erow[slot][i] + Fcol[slot][j]);
-                    }
-                }
-            }
-            fence_before();
-            if (nit < 0) break;
-            it = nit;
-            cur = nxt;
-            slot ^= 1;
+            prev = cur;
+            ++ii;
+            it = next_item(it + gridDim.x);
         }
+        if (ii > 0) epilogue(prev, (ii - 1) & 1, g - 1);
+        g_end = g - 1;
     }
     __syncthreads();
     if (s_fail && tid == 0) {
-        // let copies and products already issued finish (bounded) before TMEM is freed
-        if (issued_a >= 0) mbar_wait(&mbar_a[issued_a & 1], (uint32_t)((issued_a >> 1) & 1), kWaitIter);
-        if (issued_m >= 0) mbar_wait(&mbar_m[issued_m & 1], (uint32_t)((issued_m >> 1) & 1), kWaitIter);
+        // let the copies and products already issued finish (bounded) before TMEM is freed
+        for (int64_t gg = g_end > 1 ? g_end - 1 : 0; gg <= g_end; ++gg) {
+            mbar_wait(&full[gg & 1], (uint32_t)((gg >> 1) & 1), kWaitIter);
+            mbar_wait(&empty[gg & 1], (uint32_t)((gg >> 1) & 1), kWaitIter);
+        }
         if (status) atomicExch(status, HSVD_ERR_CUDA);
     }
     fence_before();

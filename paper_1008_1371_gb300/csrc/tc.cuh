@@ -11,6 +11,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <cuda_bf16.h>
 
 namespace hsvd {
 namespace tc {
@@ -79,6 +80,9 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *mbar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(bytes));
 }
 // Bounded wait for the phase with the given parity; false when it gave up.
+__device__ __forceinline__ void mbar_arrive(uint64_t *mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(mbar)) : "memory");
+}
 __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, uint32_t max_iter = (1u << 26)) {
     uint32_t ok = 0;
     for (uint32_t it = 0; it < max_iter; ++it) {
@@ -195,17 +199,30 @@ __device__ __forceinline__ long long digit_word(double x, int E) {
     return V + kDigitBias;
 }
 
-// BF16 bits of slice k (1-based) of a digit word: q is formed exactly with the
-// 1.5 * 2^23 magic number, then scaled by 2^(1-7k)
-__device__ __forceinline__ uint32_t slice_bits(long long W, int k) {
-    const int q = k == 1 ? (int)(W >> 49) : (int)((W >> (7 * (kSlices - k))) & 127) - 64;
-    const float f = (__int_as_float(0x4B400000 + q) - 12582912.0f) * __int_as_float((128 - 7 * k) << 23);
-    return __float_as_uint(f) >> 16;
-}
-
-// two slices (k of elements lo and hi, adjacent along K) as one 32-bit word
+// Two slices (k of elements lo and hi, adjacent along K) as one 32-bit word,
+// built two at a time in BF16x2: with u = q + 64 in [0, 128], the BF16 bit
+// pattern 0x4300 + u is the number 128 + u (the exponent of 128 makes the ULP
+// 1; u = 128 carries into the exponent and reads 256), and one packed FMA
+// (128 + u) 2^e - 192 2^e = q 2^e, e = 1 - 7k, is exact, so no rounding.
 __device__ __forceinline__ uint32_t slice_pair(long long Wlo, long long Whi, int k) {
-    return slice_bits(Wlo, k) | (slice_bits(Whi, k) << 16);
+    uint32_t ulo, uhi;
+    if (k == 1) {
+        ulo = (uint32_t)((int)(Wlo >> 49) + 64);
+        uhi = (uint32_t)((int)(Whi >> 49) + 64);
+    } else {
+        const int sh = 7 * (kSlices - k);
+        ulo = (uint32_t)(Wlo >> sh) & 127u;
+        uhi = (uint32_t)(Whi >> sh) & 127u;
+    }
+    const uint32_t packed = (ulo | (uhi << 16)) + 0x43004300u;
+    const uint32_t sc = (uint32_t)(128 - 7 * k) << 7;                   // BF16 2^(1-7k)
+    const uint32_t off = 0x8000u | ((uint32_t)(135 - 7 * k) << 7) | 0x40u;  // BF16 -1.5 2^(8-7k)
+    const __nv_bfloat162 r = __hfma2(*reinterpret_cast<const __nv_bfloat162 *>(&packed),
+                                     __halves2bfloat162(__ushort_as_bfloat16((unsigned short)sc),
+                                                        __ushort_as_bfloat16((unsigned short)sc)),
+                                     __halves2bfloat162(__ushort_as_bfloat16((unsigned short)off),
+                                                        __ushort_as_bfloat16((unsigned short)off)));
+    return *reinterpret_cast<const uint32_t *>(&r);
 }
 
 // Products S_a S_b with a + b = d (d = 2..9) accumulate in accumulator d - 2:
