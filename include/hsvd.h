@@ -206,7 +206,8 @@ int hsvd_pivot_update(double *X, int64_t rows, int64_t ldx, int b, int npairs, c
 /*
  * Split-precision kernel-level entry points (HSVD_PRECISION_BF16X8, b = 64),
  * the counterparts of hsvd_pivot_gram and hsvd_pivot_update: same operands,
- * device pointers, stream-ordered, the caller owns the outputs.  They allocate
+ * device pointers, stream-ordered, the caller owns the outputs; here `rows` may
+ * be any count >= 1.  They allocate
  * their scratch (partials, slices) stream-ordered and free it before return.
  * hsvd_pivot_update_x: dexp (npairs x 128 ints, device, may be NULL for none)
  * are the balancing exponents d_k of X W = (X 2^-d)(2^d W).

@@ -677,7 +677,7 @@ int hsvd_pivot_update(double *X, int64_t rows, int64_t ldx, int b, int npairs, c
 
 int hsvd_pivot_gram_x(const double *G, int64_t rows, int64_t ldg, int npairs, const int *col0, double *A,
                       void *stream) {
-    if (!G || !col0 || !A || npairs < 1 || rows < 1 || (rows % 64) || ldg < rows) return HSVD_ERR_ARG;
+    if (!G || !col0 || !A || npairs < 1 || rows < 1 || ldg < rows) return HSVD_ERR_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int ks = precision_gram_ksplit(rows);
     double *part = nullptr;

@@ -149,16 +149,33 @@ k_gram_x(const double *__restrict__ G, int64_t rows, int64_t ldg, const int *__r
     // split mapping: a warp writes one 8 x 8 core matrix per step; lane -> column
     // (lane >> 2) of the group, rows 2 (lane & 3) and 2 (lane & 3) + 1
     const int cc = lane >> 2, kp = 2 * (lane & 3);
-    for (int t = 0; t < ntiles; ++t) {
-        const uint32_t buf = (uint32_t)(t & 1) * kBufBytes;
+    constexpr int kCoresPerWarp = (NNX / 2 / 8) * (kGramKT / 8) / (kThrG / 32);
+    static_assert(kCoresPerWarp * (kThrG / 32) == (NNX / 2 / 8) * (kGramKT / 8), "Gram split mapping");
+    // the values of tile t this thread splits; the next tile's are loaded while
+    // the barrier and the products of the current one run
+    auto load_tile = [&](int t, double (&x)[kCoresPerWarp][2]) {
         const int64_t t0 = r0 + (int64_t)t * kGramKT;
-        for (int core = warp; core < (NNX / 2 / 8) * (kGramKT / 8); core += kThrG / 32) {
+#pragma unroll
+        for (int ci = 0; ci < kCoresPerWarp; ++ci) {
+            const int core = warp + ci * (kThrG / 32);
             const int cg = core / (kGramKT / 8), kg = core % (kGramKT / 8);
             const int c = NNX / 2 * (int)half + cg * 8 + cc, k = kg * 8 + kp;
             const double *g = G + (int64_t)(c < NNX / 2 ? cI + c : cJ + c - NNX / 2) * ldg;
             const int64_t row = t0 + k;
-            const double x0 = row < r1 ? g[row] : 0.0, x1 = row + 1 < r1 ? g[row + 1] : 0.0;
-            const long long w0 = digit_word(x0, Ecol[c]), w1 = digit_word(x1, Ecol[c]);
+            x[ci][0] = row < r1 ? g[row] : 0.0;
+            x[ci][1] = row + 1 < r1 ? g[row + 1] : 0.0;
+        }
+    };
+    double cur[kCoresPerWarp][2];
+    if (ntiles > 0) load_tile(0, cur);
+    for (int t = 0; t < ntiles; ++t) {
+        const uint32_t buf = (uint32_t)(t & 1) * kBufBytes;
+#pragma unroll
+        for (int ci = 0; ci < kCoresPerWarp; ++ci) {
+            const int core = warp + ci * (kThrG / 32);
+            const int cg = core / (kGramKT / 8), kg = core % (kGramKT / 8);
+            const int c = NNX / 2 * (int)half + cg * 8 + cc, k = kg * 8 + kp;
+            const long long w0 = digit_word(cur[ci][0], Ecol[c]), w1 = digit_word(cur[ci][1], Ecol[c]);
             const uint32_t off = buf + core_offset(c, k, kGramKT);
 #pragma unroll
             for (int s = 0; s < kSlices; ++s) {
@@ -168,6 +185,7 @@ k_gram_x(const double *__restrict__ G, int64_t rows, int64_t ldg, const int *__r
                 st_cluster_u32(sbase_peer + o, v);
             }
         }
+        if (t + 1 < ntiles) load_tile(t + 1, cur);
         fence_proxy_async_cluster();
         fence_proxy_async();
         // the products of tile t - 1 are done in this CTA: its buffer is free

@@ -33,7 +33,7 @@ def _scale(v):
     return np.exp2(np.floor(np.log2(np.maximum(v, 1e-300))) + 1)
 
 
-@pytest.mark.parametrize("rows", [640, 1024])
+@pytest.mark.parametrize("rows", [640, 1024, 600, 37])
 def test_kernel_gram_x(api, rows):
     rng = np.random.default_rng(rows)
     ncols = 6 * 64
@@ -56,10 +56,10 @@ def test_kernel_gram_x(api, rows):
         assert np.max(rel[np.outer(dd, dd) > 0]) <= 1e-13
 
 
-@pytest.mark.parametrize("balanced", [False, True])
-def test_kernel_update_x(api, balanced):
-    rng = np.random.default_rng(3 + balanced)
-    rows, ncols = 320, 4 * 64
+@pytest.mark.parametrize("balanced,rows", [(False, 320), (True, 320), (True, 300), (False, 1000)])
+def test_kernel_update_x(api, balanced, rows):
+    rng = np.random.default_rng(3 + balanced + rows)
+    ncols = 4 * 64
     grading = 10.0 ** rng.uniform(-6, 0, ncols)
     X = rng.standard_normal((rows, ncols)) * grading[None, :]
     col0 = np.array([[0, 128], [192, 64]], dtype=np.int32)
