@@ -18,4 +18,5 @@ from .oracle import (  # noqa: F401
     load,
     modulus_pairs,
     rotation,
+    set_threads,
 )

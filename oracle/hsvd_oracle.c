@@ -18,6 +18,7 @@
  *                         (Sec. 2, Eq. 2.2, the theta/t definitions, Eq. 2.6).
  *   orc_modulus_pairs  -- the modified modulus pivot strategy as the stepper
  *                         of Alg. 4.3 / Alg. 4.4 (Sec. 2 text on the strategy).
+ *   orc_set_threads    -- threads of the OpenMP modulus-parallel mode
  *   orc_hsvd           -- pointwise one-sided hyperbolic Jacobi (Eq. 2.1,
  *                         Eq. 2.3 test, Eq. 2.4/2.5 updates in the unified
  *                         form of Alg. 4.5, Sec. 2 stopping rule), with the
@@ -267,6 +268,24 @@ static int pointwise_pair(int64_t mw, int64_t nw, double *Gw, double *W, const i
 /* ORC_ARG; sigma, U (m x n, ldu) and V (n x n, ldv; either may be NULL) are   */
 /* written in input column order.                                             */
 /* ------------------------------------------------------------------------ */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads of the modulus-parallel mode (OpenMP builds; 0 = the runtime's
+ * default).  Returns the number of threads that will be used, 1 without
+ * OpenMP. */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 int orc_hsvd(int64_t m, int64_t n, const double *G, int64_t ldg, const int8_t *J,
              double tol, int max_sweeps, int order, int sort,
              double *sigma, double *U, int64_t ldu, double *V, int64_t ldv,
@@ -317,9 +336,23 @@ int orc_hsvd(int64_t m, int64_t n, const double *G, int64_t ldg, const int8_t *J
         int64_t nrot = 0;
         int st = ORC_OK;
         if (order == 1) {
-            for (int64_t q = 0; q < nw * (nw / 2) && st == ORC_OK; ++q) {
-                int a = pairs[q * 2], b = pairs[q * 2 + 1];
-                st = pointwise_pair(mw, nw, Gw, W, sgn, tol, pos[a < b ? a : b], pos[a < b ? b : a], &nrot);
+            /* the pairs of a step are disjoint, so the step's pairs may run in
+             * any order or at once: with OpenMP they are spread over the
+             * host's threads (same arithmetic per pair, the same result) */
+            const int64_t half = nw / 2;
+            for (int64_t s = 0; s < nw && st == ORC_OK; ++s) {
+                int64_t step_rot = 0;
+                int step_st = ORC_OK;
+#pragma omp parallel for schedule(static) reduction(+ : step_rot) reduction(min : step_st) if (nw >= 64)
+                for (int64_t k = 0; k < half; ++k) {
+                    const int a = pairs[(s * half + k) * 2], b = pairs[(s * half + k) * 2 + 1];
+                    int64_t r = 0;
+                    const int sk = pointwise_pair(mw, nw, Gw, W, sgn, tol, pos[a < b ? a : b], pos[a < b ? b : a], &r);
+                    step_rot += r;
+                    if (sk < step_st) step_st = sk;
+                }
+                nrot += step_rot;
+                st = step_st;
             }
         } else {
             for (int64_t i = 0; i < nw - 1 && st == ORC_OK; ++i)

@@ -43,7 +43,10 @@ def build(force=False, src=None, out=None):
         return out
     tmp = out + ".tmp.%d" % os.getpid()
     cmd = ["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-Wall", "-o", tmp, src, "-lm"]
-    subprocess.run(cmd, check=True)
+    # the modulus order runs its steps' pairs on OpenMP threads when the
+    # compiler has OpenMP; otherwise the same code is compiled serially
+    if subprocess.run(cmd[:1] + ["-fopenmp"] + cmd[1:], capture_output=True).returncode != 0:
+        subprocess.run(cmd, check=True)
     os.replace(tmp, out)
     return out
 
@@ -57,6 +60,8 @@ def _bind(lib):
                              _p, _p, _i64, _p, _i64, _p, _p]
     lib.orc_hsvd.restype = _int
     lib.orc_inner_solve.argtypes = [_int, _p, _p, _dbl, _int, _int, _p, _p, _p]
+    lib.orc_set_threads.argtypes = [_int]
+    lib.orc_set_threads.restype = _int
     lib.orc_inner_solve.restype = _int
     lib.orc_block_hsvd.argtypes = [_i64, _i64, _p, _i64, _p, _int, _dbl, _int, _int, _int,
                                    _int, _p, _p, _i64, _p, _i64, _p, _p]
@@ -108,6 +113,12 @@ def modulus_pairs(r, nsteps=None, lib=None):
     out = np.zeros((nsteps, r // 2, 2), dtype=np.int32)
     (lib or _load()).orc_modulus_pairs(int(r), int(nsteps), _ptr(out))
     return out
+
+
+def set_threads(n=0, lib=None):
+    """Threads of the modulus-parallel order (0: the OpenMP default); returns
+    the count in use (1 for a build without OpenMP)."""
+    return (lib or _load()).orc_set_threads(int(n))
 
 
 def hsvd(G, J, tol, max_sweeps=30, order="cyclic", sort=False, want_u=True, want_v=True, lib=None):

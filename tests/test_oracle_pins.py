@@ -344,3 +344,20 @@ def test_statuses(orc):
     Gz = G.copy()
     Gz[:, 7] = 0.0
     assert orc.hsvd(Gz, J, _tol(16), 30)["status"] == orc.ORC_RANK
+
+
+def test_modulus_parallel_mode_equals_serial():
+    """The OpenMP modulus-parallel mode spreads the disjoint pairs of a step
+    over threads: the result is the serial modulus order's, bit for bit."""
+    import oracle
+
+    oracle.build()
+    G, J = W.gaussian(96, m=110, p=40, seed=17)
+    tol = 96 * U
+    oracle.set_threads(1)
+    r1 = oracle.hsvd(G, J, tol, 30, order="modulus", sort=True)
+    oracle.set_threads(4)
+    r4 = oracle.hsvd(G, J, tol, 30, order="modulus", sort=True)
+    oracle.set_threads(0)
+    assert r1["status"] == 0 and r1["sweeps"] == r4["sweeps"]
+    assert np.array_equal(r1["sigma"], r4["sigma"]) and np.array_equal(r1["V"], r4["V"])
