@@ -101,3 +101,27 @@ def test_batched_argument_errors_without_gpu(api):
     o3.reserved[1] = 7
     assert L.hsvd_solve_batched_ex(1, arr(G), i64(4), i64(4), i64(4), arr(J), arr(s), None, None, None, None,
                                    ctypes.byref(o3), None, None) == api.HSVD_ERR_ARG
+
+
+def test_learned_option_errors_without_gpu(api):
+    """The learned form and the trace export follow block-pair visits across
+    sweeps: they need the blocked method without reordering; tau < 1."""
+    L = api.lib()
+    G = np.zeros((4, 4))
+    J = np.ones(4, dtype=np.int8)
+    s = np.zeros(4)
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    model = np.zeros(api.HSVD_MLP_PARAMS, dtype=np.float32)
+    info = api.HsvdInfo()
+    for kw in (dict(method=api.HSVD_METHOD_POINTWISE), dict(method=api.HSVD_METHOD_BLOCKED, sort=True),
+               dict(method=api.HSVD_METHOD_BLOCKED, sort=False, skip_tau=1.0)):
+        o = api.make_opts(**kw)
+        o.skip_model = model.ctypes.data
+        assert L.hsvd_solve_ex(p(G), 4, 4, 4, p(J), p(s), None, 4, None, 4, ctypes.byref(o), ctypes.byref(info),
+                               None) == api.HSVD_ERR_ARG, kw
+    # a trace array with no room
+    o = api.make_opts(method=api.HSVD_METHOD_BLOCKED, sort=False)
+    o.trace_out = model.ctypes.data
+    o.trace_cap = 0
+    assert L.hsvd_solve_ex(p(G), 4, 4, 4, p(J), p(s), None, 4, None, 4, ctypes.byref(o), ctypes.byref(info),
+                           None) == api.HSVD_ERR_ARG
