@@ -35,9 +35,12 @@ MAX_SWEEPS = 40
 # kernel, from one ncu capture of this workload; an entry is removed when the
 # kernel changes
 PROFILED_TRAFFIC = {
-    ("graded1024", "fp64", "k_solve_cluster<64,8>"): (4.777e6, "profiles/kernels_graded1024_fp64.md"),
-    ("graded1024", "fp64", "k_update<64>"): (17.318e6, "profiles/kernels_graded1024_fp64.md"),
+    ("graded1024", "fp64", "k_solve_cross<64,8>"): (4.794e6, "profiles/kernels_graded1024_fp64.md"),
+    ("graded1024", "fp64", "k_update<64>"): (17.317e6, "profiles/kernels_graded1024_fp64.md"),
     ("graded1024", "fp64", "k_gram<32>"): (8.396e6, "profiles/kernels_graded1024_fp64.md"),
+    ("haar4096", "bf16x8", "k_update_x"): (499.55e6, "profiles/kernels_haar4096_bf16x8.md"),
+    ("haar4096", "bf16x8", "k_gram_x"): (149.18e6, "profiles/kernels_haar4096_bf16x8.md"),
+    ("haar4096", "bf16x8", "k_solve_cross<128,8>"): (18.96e6, "profiles/kernels_haar4096_bf16x8.md"),
 }
 GOLDEN = os.path.join(ROOT, "tests", "golden", "graded1024_sigma.txt")
 
@@ -598,10 +601,11 @@ def main():
     dom = max(("gram", "update", "solve"), key=lambda k: tot[k])
     fp64_peak = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk x flop x max clock
     achieved = alg[dom] / (tot[dom] * 1e-3) / 1e12 if dom in alg else None
+    # the inner solve's main kernel: the cross pass (every step but the first of a sweep)
     kname = {"gram": "k_gram<%d>" % block, "update": "k_update<%d>" % (2 * block),
-             "solve": "k_solve_cluster<%d,8>" % (2 * block)}
+             "solve": "k_solve_cross<%d,%d>" % (2 * block, 4 if block == 16 else 8)}
     if prec == api.HSVD_PRECISION_BF16X8:
-        kname = {"gram": "k_gram_x", "update": "k_update_x", "solve": "k_solve_cluster<128,8>"}
+        kname = {"gram": "k_gram_x", "update": "k_update_x", "solve": "k_solve_cross<128,8>"}
     if dom == "solve" or prec == api.HSVD_PRECISION_FP64:
         roofline = {"kernel": kname[dom], "bound": "alu", "achieved": achieved, "peak": fp64_peak,
                     "unit": "TFLOP/s", "frac": (achieved / fp64_peak) if achieved else None, "traffic": None,
