@@ -88,6 +88,9 @@ def parse():
                     help="Gram/update arithmetic (FP64 FMA or BF16 slices on the tensor cores), optionally "
                          "with the learned skip network")
     ap.add_argument("--tau", type=float, default=0.5, help="learned form: skip threshold on P(rotation)")
+    ap.add_argument("--check", action="store_true",
+                    help="split precision: also solve with FP64 products (untimed) and report the sigma "
+                         "agreement and the invariants of Eq. 1.1")
     ap.add_argument("--count", type=int, default=BATCH_COUNT, help="batch10k: number of factors")
     ap.add_argument("--group-width", type=int, default=0, help="batch10k: 0 autotunes, else 256/512/1024")
     ap.add_argument("--block", type=int, default=0, help="block width (0: the workload's)")
@@ -194,6 +197,36 @@ def accuracy_vs_golden(G, J, sigma):
             worst_tight = max(worst_tight, float(e[tight].max()))
     return {"sigma_max_rel_err": worst, "sigma_max_rel_err_where_floor_below_1e-12": worst_tight,
             "values_with_floor_above_1e-12": n_loose}
+
+
+def check_against_fp64(api, G, J, sigma, U, V, tol, J_np):
+    """sigma of a split-precision run against a plain FP64 run on the same GPU
+    (per sign group, sorted), gated per value by max(1e-12, u kappa_j), and the
+    invariants of Eq. 1.1 of the split-precision result."""
+    import torch
+
+    n = G.shape[1]
+    r64 = api.hsvd_solve_ex(G, J, api.make_opts(tol=tol, max_sweeps=MAX_SWEEPS, method=api.HSVD_METHOD_BLOCKED,
+                                                block_w=64, sort=False))
+    kap = (2.0 ** -53 * torch.linalg.vector_norm(G.abs() @ r64.V.abs(), dim=0) / r64.sigma).cpu().numpy()
+    sx, s64 = sigma.cpu().numpy(), r64.sigma.cpu().numpy()
+    worst, worst_gate = 0.0, 0.0
+    for sg in (1, -1):
+        idx = np.where(J_np == sg)[0]
+        o = np.argsort(s64[idx])
+        e = np.abs(np.sort(sx[idx]) - s64[idx][o]) / s64[idx][o]
+        worst = max(worst, float(e.max()))
+        worst_gate = max(worst_gate, float((e / np.maximum(1e-12, kap[idx][o])).max()))
+    eye = torch.eye(n, dtype=torch.float64, device=G.device)
+    Jd = torch.diag(J.to(torch.float64))
+    e1 = float((U.T @ U - eye).abs().max())
+    e2 = float((V.T @ Jd @ V - Jd).abs().max()) / max(1.0, float(V.abs().max()) ** 2)
+    res = torch.linalg.vector_norm(G @ V - U * sigma[None, :], dim=0) / (
+        torch.linalg.matrix_norm(G) * torch.linalg.vector_norm(V, dim=0))
+    return {"vs_plain_fp64_max_rel_sigma_diff": worst, "vs_plain_fp64_worst_over_floor_gate": worst_gate,
+            "plain_fp64_sweeps": r64.sweeps, "max_abs_UtU_minus_I": e1, "max_VtJV_minus_J_scaled": e2,
+            "max_residual_GV_minus_U_sigma": float(res.max()),
+            "gate": "|d sigma|/sigma <= max(1e-12, u kappa_j) per value; invariants <= 1e-12 n"}
 
 
 def cpu_baseline(G, J, tol, sweeps):
@@ -324,6 +357,25 @@ def run_batched(args):
                 "sample": "%d of %d factors (every %dth), one hsvd_solve call each, %.2f s measured, scaled by "
                           "effective flops" % (len(idx), count, max(1, count // 40), t_loop)}
 
+    # sampled factors against the CPU oracle (per sign group, sorted)
+    accuracy = None
+    if rank == 0:
+        import oracle
+
+        oracle.build()
+        rng = np.random.default_rng(0)
+        worst = 0.0
+        for k in sorted(rng.choice(count, min(6, count), replace=False).tolist()):
+            G, J = facs[k]
+            ref = oracle.hsvd(G, J, G.shape[1] * 2.0 ** -53, 30, order="modulus", want_u=False, want_v=False)
+            s_k = sig[k].cpu().numpy()
+            for sg in (1, -1):
+                idx = np.where(J == sg)[0]
+                if idx.size:
+                    a, b = np.sort(s_k[idx]), np.sort(ref["sigma"][idx])
+                    worst = max(worst, float(np.max(np.abs(a - b) / b)))
+        accuracy = {"sampled_factors": min(6, count), "max_rel_sigma_err_vs_oracle": worst}
+
     e2e = None
     if not args.no_e2e:
         Gh = [torch.from_numpy(G) for G, _ in facs]
@@ -371,6 +423,7 @@ def run_batched(args):
                        "max_sweeps_run": int(r.info.max_sweeps_run),
                        "l2": "flushed (256 MB write) between steps; inputs 2.6 GB > L2",
                        "parallelism": "replicas" if world > 1 else "single"},
+            "ms_per_step_median": statistics.median(step_ms), "accuracy": accuracy,
             "gpu_launches": int(sum(i.kernel_launches for i in infos)),
             "roofline": roofline, "loop_of_single_solves": loop, "e2e": e2e, "cpu_baseline": cpu,
             "clocks": clk.summary(),
@@ -566,6 +619,7 @@ def main():
             dist.barrier()
     ms = sum(step_ms) / len(step_ms)
     ms = max_over_ranks(ms, world, dev)
+    ms_median = statistics.median(step_ms)
     info = infos[-1]
     assert info.status == api.HSVD_OK, api.hsvd_status_string(info.status)
     sweeps = info.sweeps
@@ -633,6 +687,8 @@ def main():
     accuracy = None
     if rank == 0 and args.workload == "graded1024":
         accuracy = accuracy_vs_golden(G_np, J_np, sigma.cpu().numpy())
+    if rank == 0 and args.check and prec == api.HSVD_PRECISION_BF16X8:
+        accuracy = check_against_fp64(api, G, J, sigma, U, V, tol, J_np)
 
     # end to end through the C ABI with pinned host arrays, copies inside the timed region
     e2e = None
@@ -666,6 +722,7 @@ def main():
             "metric": metric_name(args.form), "value": value,
             "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "ms_per_step_median": ms_median,
             "config": {"workload": wdesc + ", blocked, b=%d, %s" % (block, args.form), "m": m, "n": n,
                        "block_w": block, "form": args.form, "tol": tol, "sweeps": sweeps, "sweeps_in_flop_count": s_eff,
                        "inner": "block-oriented",

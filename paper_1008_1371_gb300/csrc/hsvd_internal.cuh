@@ -57,13 +57,28 @@ __device__ __forceinline__ bool rotation_params(double aii, double ajj, double a
     return true;
 }
 
-// The test of Eq. 2.3 and the rotation of Sec. 2, evaluated side by side
-// (both depend only on the three entries, so their square roots and divides
-// overlap; the rotation is discarded when the pair passes).  Returns 0 (the
-// pair passes), 1 (rotate with t, c) or 2 (rank deficient); t = 0, c = 1
-// unless it returns 1.
+// The test of Eq. 2.3, then the rotation of Sec. 2 for a pair that fails it.
+// Returns 0 (the pair passes), 1 (rotate with t, c) or 2 (rank deficient);
+// t = 0, c = 1 unless it returns 1.  Late in the iteration most pairs pass, so
+// the rotation's divides and square roots are skipped for them.
 __device__ __forceinline__ int pair_decision(double aii, double ajj, double aij, int hyp, double tol,
                                              double &t, double &c) {
+    t = 0.0;
+    c = 1.0;
+    if (pair_passes(aii, ajj, aij, tol)) return 0;
+    double tt, cc;
+    if (!rotation_params(aii, ajj, aij, hyp, tt, cc)) return 2;
+    t = tt;
+    c = cc;
+    return 1;
+}
+
+// The same decision with the test and the rotation evaluated side by side
+// (their square roots and divides overlap, the rotation is discarded when the
+// pair passes): for a thread whose chain is the critical path whatever the
+// outcome (the look-ahead warp of the cross pass).  Same results.
+__device__ __forceinline__ int pair_decision_eager(double aii, double ajj, double aij, int hyp, double tol,
+                                                   double &t, double &c) {
     const bool passes = pair_passes(aii, ajj, aij, tol);
     double tt, cc;
     const bool ok = rotation_params(aii, ajj, aij, hyp, tt, cc);

@@ -482,7 +482,7 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
                 const double app = fk ? fma(htk, Apq[b][k], d_k) : d_k;
                 const double aqq = fj ? fma(tj, Apq[b][j], d_q) : d_q;
                 const int hyp = (sg[k] == sg[q2]) ? -1 : 1;
-                nx_fl = pair_decision(app, aqq, v, hyp, tol, nx_t, nx_c);
+                nx_fl = pair_decision_eager(app, aqq, v, hyp, tol, nx_t, nx_c);
                 nx_apq = v;
             }
         } else {
