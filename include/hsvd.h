@@ -65,6 +65,19 @@ extern "C" {
 
 #define HSVD_SORT_AUTO (-1)
 
+/* Stopping (Sec. 2).  The iteration always stops after a sweep in which every
+ * pair passed the test of Eq. 2.3 (no rotation).  With opts.tstop != 0 it also
+ * stops after a sweep whose applied rotations all had |t| <= T (the
+ * convergence statistic of Eq. 4.2 reduced to (01)_2): quadratic convergence
+ * has set in and the confirming sweep is saved.  For the blocked method the
+ * tangents are those of the inner (pivot-block) rotations.  HSVD_TSTOP_PAPER
+ * is the paper's T_eps = sqrt(eps)/2 with eps = 2^-52; a negative tstop
+ * selects it. */
+#define HSVD_TSTOP_PAPER 7.450580596923828125e-9 /* 2^-27 */
+#define HSVD_STOP_NONE 0    /* not converged, or an error                      */
+#define HSVD_STOP_ORTHO 1   /* a sweep without rotations (every pair passed)   */
+#define HSVD_STOP_TANGENT 2 /* a sweep whose tangents were all <= T            */
+
 /* Learned form: per-visit features and the MLP 8 -> 64 -> 64 -> 1 (ReLU, ReLU,
  * logit).  Parameter vector (FP32 master values; weights are rounded to BF16
  * where the network runs, accumulation is FP32): W1[64][8], b1[64],
@@ -106,7 +119,9 @@ typedef struct hsvd_opts {
                              the visit rotated) for every block-pair visit of every
                              sweep after the first; NULL = none                       */
     int64_t trace_cap;    /* rows available at trace_out                               */
-    int reserved[6];      /* must be zero                                              */
+    double tstop;         /* tangent threshold T of the early stop: 0 (default) = off,
+                             < 0 = HSVD_TSTOP_PAPER, else T itself (0 < T <= 1)       */
+    int reserved[4];      /* must be zero                                              */
 } hsvd_opts;
 
 typedef struct hsvd_info {
@@ -126,6 +141,7 @@ typedef struct hsvd_info {
     int judge_sweeps;     /* learned form: full sweeps run after a masked sweep without
                              rotations                                                  */
     int64_t trace_rows;   /* rows written to trace_out                                 */
+    int stop_rule;        /* HSVD_STOP_*: which rule ended the iteration               */
 } hsvd_info;
 
 /* Fills *opts with the defaults (tol = n 2^-53 at call time, 30 sweeps, auto
@@ -261,7 +277,8 @@ typedef struct hsvd_batch_opts {
     int group_width; /* 0 (default): autotuned per size bucket; 256, 512 or 1024:
                         that width for every factor                                 */
     int use_graph;   /* nonzero (default): the launch is captured as a CUDA graph  */
-    int reserved[4]; /* must be zero                                                */
+    double tstop;    /* tangent threshold of the early stop, as hsvd_opts.tstop    */
+    int reserved[2]; /* must be zero                                                */
 } hsvd_batch_opts;
 
 typedef struct hsvd_batch_info {
@@ -276,6 +293,7 @@ typedef struct hsvd_batch_info {
                              with neither                                           */
     double ms_kernel;     /* CUDA-event time of the batched launch                 */
     double ms_tune;       /* CUDA-event time of the autotuner's sample runs        */
+    int64_t tangent_stops; /* factors whose iteration ended at the tangent threshold */
 } hsvd_batch_info;
 
 /* Fills *opts with the defaults above. */

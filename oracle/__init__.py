@@ -11,6 +11,10 @@ from .oracle import (  # noqa: F401
     ORC_NOT_CONVERGED,
     ORC_OK,
     ORC_RANK,
+    ORC_STOP_NONE,
+    ORC_STOP_ORTHO,
+    ORC_STOP_TANGENT,
+    T_EPS,
     block_hsvd,
     build,
     hsvd,

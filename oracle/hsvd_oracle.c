@@ -23,7 +23,9 @@
  *                         Eq. 2.3 test, Eq. 2.4/2.5 updates in the unified
  *                         form of Alg. 4.5, Sec. 2 stopping rule), with the
  *                         row-cyclic order or the modulus order and optional
- *                         diagonal sorting (Sec. 4, Sort_Diagonal).
+ *                         diagonal sorting (Sec. 4, Sort_Diagonal); optional
+ *                         early stop at the tangent threshold T_eps (Sec. 2)
+ *                         through the convergence statistic of Eq. 4.2.
  *   orc_inner_solve    -- J-orthogonalisation of one 2b x 2b pivot block A_P by
  *                         two-sided rotations (Sec. 5 block-oriented method,
  *                         Sec. 6 full-block variant), pair order taken from the
@@ -65,6 +67,15 @@
  *       strict test of Eq. 2.3 would otherwise "rotate" a zero column by the
  *       identity for ever).  A zero column (sigma_j = 0) is rank deficiency,
  *       which the paper excludes (Sec. 1): status ORC_RANK.
+ *   R14 The tangent threshold (Sec. 2, T_eps = sqrt(eps)/2) is optional and
+ *       off by default (tstop = 0): only a sweep without rotations ends the
+ *       iteration.  With tstop > 0 every applied rotation contributes the
+ *       code of Eq. 4.2 -- (11)_2 if |t| > tstop, (01)_2 otherwise -- to a
+ *       bitwise-or over the sweep (for the blocked method the tangents are
+ *       those of the inner rotations); (00)_2 (no rotation) stops as before,
+ *       (01)_2 also stops, after that sweep, and (11)_2 goes on.  Pairs that
+ *       pass Eq. 2.3 compute no tangent and contribute nothing.  The sweep
+ *       count includes the sweep that stopped.
  */
 #include <math.h>
 #include <stdint.h>
@@ -76,6 +87,17 @@
 #define ORC_ARG (-1)
 #define ORC_RANK (-2)
 #define ORC_NONFINITE (-3)
+
+/* how the iteration ended (R14) */
+#define ORC_STOP_NONE 0    /* not converged, or an error          */
+#define ORC_STOP_ORTHO 1   /* a sweep without rotations, Eq. 2.3  */
+#define ORC_STOP_TANGENT 2 /* every tangent of a sweep <= tstop   */
+
+/* Eq. 4.2: the convergence code of one applied rotation with tangent t */
+static int conv_code(double t, double tstop)
+{
+    return (tstop > 0.0 && fabs(t) <= tstop) ? 1 : 3;
+}
 
 /* ------------------------------------------------------------------------ */
 /* Rotation parameters (Sec. 2, Eq. 2.2; readings R1, R2).                    */
@@ -239,7 +261,7 @@ static void finalise(int64_t m, int64_t n, const double *Gw, const double *W,
  * current columns, the relative orthogonality test (Eq. 2.3), and if it fails
  * the rotation of the G and W columns (Alg. 4.5). */
 static int pointwise_pair(int64_t mw, int64_t nw, double *Gw, double *W, const int8_t *sgn,
-                          double tol, int pi, int pj, int64_t *nrot)
+                          double tol, int pi, int pj, int64_t *nrot, double tstop, int *cd)
 {
     double *gi = Gw + (int64_t)pi * mw, *gj = Gw + (int64_t)pj * mw;
     double aii = dot(mw, gi, gi), ajj = dot(mw, gj, gj), aij = dot(mw, gi, gj);
@@ -250,6 +272,7 @@ static int pointwise_pair(int64_t mw, int64_t nw, double *Gw, double *W, const i
     rotate_cols(mw, gi, gj, hyp, t, c);
     rotate_cols(nw, W + (int64_t)pi * nw, W + (int64_t)pj * nw, hyp, t, c);
     ++*nrot;
+    *cd |= conv_code(t, tstop);
     return ORC_OK;
 }
 
@@ -264,9 +287,10 @@ static int pointwise_pair(int64_t mw, int64_t nw, double *Gw, double *W, const i
 /* For order 1 the columns are first grouped J+ then J- (Alg. 4.2 assumes     */
 /* J = diag(I_p, -I_{n-p})), odd n gets one bordering column (Eq. 4.1).       */
 /* sort != 0 sorts the positions before the first sweep and after each sweep  */
-/* (Alg. 4.1).  Returns ORC_OK, ORC_NOT_CONVERGED, ORC_RANK, ORC_NONFINITE or */
-/* ORC_ARG; sigma, U (m x n, ldu) and V (n x n, ldv; either may be NULL) are   */
-/* written in input column order.                                             */
+/* (Alg. 4.1).  tstop > 0 adds the tangent-threshold stop (R14); *stop_rule  */
+/* (may be NULL) receives ORC_STOP_*.  Returns ORC_OK, ORC_NOT_CONVERGED,     */
+/* ORC_RANK, ORC_NONFINITE or ORC_ARG; sigma, U (m x n, ldu) and V (n x n,    */
+/* ldv; either may be NULL) are written in input column order.                */
 /* ------------------------------------------------------------------------ */
 #ifdef _OPENMP
 #include <omp.h>
@@ -289,9 +313,10 @@ int orc_set_threads(int n)
 int orc_hsvd(int64_t m, int64_t n, const double *G, int64_t ldg, const int8_t *J,
              double tol, int max_sweeps, int order, int sort,
              double *sigma, double *U, int64_t ldu, double *V, int64_t ldv,
-             int *sweeps, int64_t *rotations)
+             int *sweeps, int64_t *rotations, double tstop, int *stop_rule)
 {
-    if (m < n || n < 1 || ldg < m || max_sweeps < 1 || !(tol > 0.0)) return ORC_ARG;
+    if (stop_rule) *stop_rule = ORC_STOP_NONE;
+    if (m < n || n < 1 || ldg < m || max_sweeps < 1 || !(tol > 0.0) || !(tstop >= 0.0)) return ORC_ARG;
     for (int64_t j = 0; j < n; ++j)
         if (J[j] != 1 && J[j] != -1) return ORC_ARG;
     if (!all_finite(m, n, G, ldg)) return ORC_NONFINITE;
@@ -332,9 +357,10 @@ int orc_hsvd(int64_t m, int64_t n, const double *G, int64_t ldg, const int8_t *J
         for (int64_t j = 0; j < nw; ++j) d[j] = dot(mw, Gw + j * mw, Gw + j * mw);
         sort_positions((int)nw, pos, d, sgn);
     }
+    int rule = ORC_STOP_NONE;
     for (sw = 1; sw <= max_sweeps; ++sw) {
         int64_t nrot = 0;
-        int st = ORC_OK;
+        int st = ORC_OK, cd = 0;
         if (order == 1) {
             /* the pairs of a step are disjoint, so the step's pairs may run in
              * any order or at once: with OpenMP they are spread over the
@@ -342,30 +368,35 @@ int orc_hsvd(int64_t m, int64_t n, const double *G, int64_t ldg, const int8_t *J
             const int64_t half = nw / 2;
             for (int64_t s = 0; s < nw && st == ORC_OK; ++s) {
                 int64_t step_rot = 0;
-                int step_st = ORC_OK;
-#pragma omp parallel for schedule(static) reduction(+ : step_rot) reduction(min : step_st) if (nw >= 64)
+                int step_st = ORC_OK, step_cd = 0;
+#pragma omp parallel for schedule(static) reduction(+ : step_rot) reduction(min : step_st) reduction(| : step_cd) if (nw >= 64)
                 for (int64_t k = 0; k < half; ++k) {
                     const int a = pairs[(s * half + k) * 2], b = pairs[(s * half + k) * 2 + 1];
                     int64_t r = 0;
-                    const int sk = pointwise_pair(mw, nw, Gw, W, sgn, tol, pos[a < b ? a : b], pos[a < b ? b : a], &r);
+                    int c = 0;
+                    const int sk = pointwise_pair(mw, nw, Gw, W, sgn, tol, pos[a < b ? a : b], pos[a < b ? b : a], &r,
+                                                  tstop, &c);
                     step_rot += r;
+                    step_cd |= c;
                     if (sk < step_st) step_st = sk;
                 }
                 nrot += step_rot;
+                cd |= step_cd;
                 st = step_st;
             }
         } else {
             for (int64_t i = 0; i < nw - 1 && st == ORC_OK; ++i)
                 for (int64_t j = i + 1; j < nw && st == ORC_OK; ++j)
-                    st = pointwise_pair(mw, nw, Gw, W, sgn, tol, (int)i, (int)j, &nrot);
+                    st = pointwise_pair(mw, nw, Gw, W, sgn, tol, (int)i, (int)j, &nrot, tstop, &cd);
         }
         if (st != ORC_OK) {
             status = st;
             goto done;
         }
         nrot_total += nrot;
-        if (nrot == 0) {
+        if (cd == 0 || cd == 1) { /* (00)_2 or (01)_2 of Eq. 4.2 */
             status = ORC_OK;
+            rule = cd == 0 ? ORC_STOP_ORTHO : ORC_STOP_TANGENT;
             break;
         }
         if (order == 1 && sort) {
@@ -392,6 +423,7 @@ done:
     }
     if (sweeps) *sweeps = sw;
     if (rotations) *rotations = nrot_total;
+    if (stop_rule && status == ORC_OK) *stop_rule = rule;
     free(Gw); free(W); free(sgn); free(d); free(pos); free(pairs);
     return status;
 }
@@ -427,7 +459,8 @@ done:
 /*   2 one pass of the modulus strategy over all nn indices (Sec. 5, first    */
 /*     step of the block-oriented method).                                    */
 /* On return A holds the final R^T A R (A itself, not its transpose) and W    */
-/* (nn x nn) the accumulated transformation, starting from I.                 */
+/* (nn x nn) the accumulated transformation, starting from I; *tmax_out (may  */
+/* be NULL) the largest |t| of the rotations applied (0 if none).             */
 /* ------------------------------------------------------------------------ */
 static void mix_rows(int nn, double *S, int h, const int *P, const int *Q, const double *T,
                      const double *C, const int *H, const int *rot)
@@ -445,8 +478,9 @@ static void mix_rows(int nn, double *S, int h, const int *P, const int *Q, const
 }
 
 int orc_inner_solve(int nn, double *A, const int8_t *sgn, double tol, int mode,
-                    int max_passes, double *W, int64_t *nrot_out, int *passes_out)
+                    int max_passes, double *W, int64_t *nrot_out, int *passes_out, double *tmax_out)
 {
+    double tmax = 0.0; /* largest |t| of an applied rotation */
     if (nn < 2 || (nn % 2) || max_passes < 1) return ORC_ARG;
     int h = nn / 2;
     int *pairs = (int *)malloc(sizeof(int) * (size_t)nn * (size_t)h * 2);
@@ -500,6 +534,7 @@ int orc_inner_solve(int nn, double *A, const int8_t *sgn, double tol, int mode,
                 }
                 rot[k] = 1;
                 ++nrot_pass;
+                if (fabs(T[k]) > tmax) tmax = fabs(T[k]);
             }
             /* first half on the rows of S, transpose, second half */
             mix_rows(nn, S, h, P, Q, T, C, H, rot);
@@ -536,6 +571,7 @@ out:
             A[x + (int64_t)y * nn] = transposed ? S[(int64_t)y * nn + x] : S[(int64_t)x * nn + y];
     if (nrot_out) *nrot_out = nrot_total;
     if (passes_out) *passes_out = npass;
+    if (tmax_out) *tmax_out = tmax;
     free(pairs); free(P); free(Q); free(T); free(C); free(H); free(rot);
     free(S); free(St); free(d); free(apq);
     return status;
@@ -554,14 +590,16 @@ out:
 /* inner_mode 1: block-oriented -- whole block in the first step of a sweep,  */
 /* cross pass afterwards), and, if any inner rotation was applied, updates    */
 /* [G_I G_J] <- [G_I G_J] W_P and [V_I V_J] <- [V_I V_J] W_P (plain triple    */
-/* loops).  Stops after a sweep with no rotation.  Outputs in input order.    */
+/* loops).  Stops after a sweep with no rotation, or (tstop > 0, R14) after a  */
+/* sweep whose inner tangents are all <= tstop.  Outputs in input order.      */
 /* ------------------------------------------------------------------------ */
 int orc_block_hsvd(int64_t m, int64_t n, const double *G, int64_t ldg, const int8_t *J,
                    int b, double tol, int max_sweeps, int inner_mode, int inner_max_passes,
                    int sort, double *sigma, double *U, int64_t ldu, double *V, int64_t ldv,
-                   int *sweeps, int64_t *rotations)
+                   int *sweeps, int64_t *rotations, double tstop, int *stop_rule)
 {
-    if (m < n || n < 1 || ldg < m || b < 1 || max_sweeps < 1 || !(tol > 0.0)) return ORC_ARG;
+    if (stop_rule) *stop_rule = ORC_STOP_NONE;
+    if (m < n || n < 1 || ldg < m || b < 1 || max_sweeps < 1 || !(tol > 0.0) || !(tstop >= 0.0)) return ORC_ARG;
     for (int64_t j = 0; j < n; ++j)
         if (J[j] != 1 && J[j] != -1) return ORC_ARG;
     if (!all_finite(m, n, G, ldg)) return ORC_NONFINITE;
@@ -609,10 +647,11 @@ int orc_block_hsvd(int64_t m, int64_t n, const double *G, int64_t ldg, const int
         W[(int64_t)pos[k] + k * nw] = 1.0; /* W holds V's columns for the working order */
     }
 
-    int status = ORC_NOT_CONVERGED, sw;
+    int status = ORC_NOT_CONVERGED, sw, rule = ORC_STOP_NONE;
     int64_t nrot_total = 0;
     for (sw = 1; sw <= max_sweeps; ++sw) {
         int64_t nrot = 0;
+        int cd = 0; /* Eq. 4.2 over the sweep: the inner tangents */
         for (int s = 0; s < nb; ++s) {
             for (int k = 0; k < nb / 2; ++k) {
                 int a = pairs[(s * (nb / 2) + k) * 2], bb = pairs[(s * (nb / 2) + k) * 2 + 1];
@@ -629,10 +668,12 @@ int orc_block_hsvd(int64_t m, int64_t n, const double *G, int64_t ldg, const int
                 }
                 int mode = (inner_mode == 0) ? 0 : (s == 0 ? 2 : 1);
                 int64_t nr = 0;
-                int st = orc_inner_solve(nn, A, ps, tol, mode, inner_max_passes, Wp, &nr, NULL);
+                double tmax = 0.0;
+                int st = orc_inner_solve(nn, A, ps, tol, mode, inner_max_passes, Wp, &nr, NULL, &tmax);
                 if (st != ORC_OK) { status = st; goto done; }
                 if (nr == 0) continue;
                 nrot += nr;
+                cd |= conv_code(tmax, tstop); /* the block's largest tangent decides its code */
                 /* [G_I G_J] <- [G_I G_J] W_P and [V_I V_J] <- [V_I V_J] W_P */
                 for (int which = 0; which < 2; ++which) {
                     double *M = which ? W : Gw;
@@ -651,7 +692,11 @@ int orc_block_hsvd(int64_t m, int64_t n, const double *G, int64_t ldg, const int
             }
         }
         nrot_total += nrot;
-        if (nrot == 0) { status = ORC_OK; break; }
+        if (cd == 0 || cd == 1) { /* (00)_2 or (01)_2 of Eq. 4.2 */
+            status = ORC_OK;
+            rule = cd == 0 ? ORC_STOP_ORTHO : ORC_STOP_TANGENT;
+            break;
+        }
         if (sort) {
             for (int64_t k = 0; k < nw; ++k) { d[k] = dot(mw, Gw + k * mw, Gw + k * mw); pos[k] = (int)k; }
             sort_positions((int)nw, pos, d, sgn);
@@ -688,6 +733,7 @@ done:
     }
     if (sweeps) *sweeps = sw;
     if (rotations) *rotations = nrot_total;
+    if (stop_rule && status == ORC_OK) *stop_rule = rule;
     free(Gw); free(W); free(Gt); free(Wt); free(sgn); free(sgt); free(col); free(colt);
     free(pos); free(d); free(A); free(Wp); free(Pan); free(ps); free(pairs);
     return status;

@@ -18,6 +18,16 @@ ORC_ARG = -1
 ORC_RANK = -2
 ORC_NONFINITE = -3
 
+# how the iteration ended: not at all, a sweep without rotations (Eq. 2.3),
+# every tangent of a sweep at most the threshold (Sec. 2, Eq. 4.2)
+ORC_STOP_NONE = 0
+ORC_STOP_ORTHO = 1
+ORC_STOP_TANGENT = 2
+
+# the paper's threshold T_eps = sqrt(eps) / 2 with eps = 2^-52, the smallest
+# power of two with fl(1 + eps) > 1 (Sec. 2)
+T_EPS = 2.0 ** -27
+
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "hsvd_oracle.c")
 _OUT_DIR = os.path.join(_HERE, "_build")
@@ -57,14 +67,14 @@ def _bind(lib):
     lib.orc_modulus_pairs.argtypes = [_int, _int, _p]
     lib.orc_modulus_pairs.restype = None
     lib.orc_hsvd.argtypes = [_i64, _i64, _p, _i64, _p, _dbl, _int, _int, _int,
-                             _p, _p, _i64, _p, _i64, _p, _p]
+                             _p, _p, _i64, _p, _i64, _p, _p, _dbl, _p]
     lib.orc_hsvd.restype = _int
-    lib.orc_inner_solve.argtypes = [_int, _p, _p, _dbl, _int, _int, _p, _p, _p]
+    lib.orc_inner_solve.argtypes = [_int, _p, _p, _dbl, _int, _int, _p, _p, _p, _p]
     lib.orc_set_threads.argtypes = [_int]
     lib.orc_set_threads.restype = _int
     lib.orc_inner_solve.restype = _int
     lib.orc_block_hsvd.argtypes = [_i64, _i64, _p, _i64, _p, _int, _dbl, _int, _int, _int,
-                                   _int, _p, _p, _i64, _p, _i64, _p, _p]
+                                   _int, _p, _p, _i64, _p, _i64, _p, _p, _dbl, _p]
     lib.orc_block_hsvd.restype = _int
     return lib
 
@@ -121,11 +131,13 @@ def set_threads(n=0, lib=None):
     return (lib or _load()).orc_set_threads(int(n))
 
 
-def hsvd(G, J, tol, max_sweeps=30, order="cyclic", sort=False, want_u=True, want_v=True, lib=None):
+def hsvd(G, J, tol, max_sweeps=30, order="cyclic", sort=False, want_u=True, want_v=True, lib=None, tstop=0.0):
     """Pointwise one-sided hyperbolic Jacobi SVD on the CPU.
 
-    ``order`` is ``"cyclic"`` (row-cyclic) or ``"modulus"``.  Returns a dict
-    with sigma, U, V (input column order), sweeps, rotations and status.
+    ``order`` is ``"cyclic"`` (row-cyclic) or ``"modulus"``.  ``tstop`` > 0
+    also stops after a sweep whose tangents are all at most ``tstop`` (Sec. 2;
+    ``T_EPS`` is the paper's value).  Returns a dict with sigma, U, V (input
+    column order), sweeps, rotations, status and stop (ORC_STOP_*).
     """
     G = _fcol(G)
     m, n = G.shape
@@ -133,36 +145,42 @@ def hsvd(G, J, tol, max_sweeps=30, order="cyclic", sort=False, want_u=True, want
     sigma = np.zeros(n)
     U = np.zeros((m, n), order="F") if want_u else None
     V = np.zeros((n, n), order="F") if want_v else None
-    sweeps, rots = _int(), _i64()
+    sweeps, rots, stop = _int(), _i64(), _int()
     st = (lib or _load()).orc_hsvd(m, n, _ptr(G), m, _ptr(j), float(tol), int(max_sweeps),
                           1 if order == "modulus" else 0, 1 if sort else 0,
-                          _ptr(sigma), _ptr(U), m, _ptr(V), n, ctypes.byref(sweeps), ctypes.byref(rots))
-    return dict(sigma=sigma, U=U, V=V, sweeps=sweeps.value, rotations=rots.value, status=st)
+                          _ptr(sigma), _ptr(U), m, _ptr(V), n, ctypes.byref(sweeps), ctypes.byref(rots),
+                          float(tstop), ctypes.byref(stop))
+    return dict(sigma=sigma, U=U, V=V, sweeps=sweeps.value, rotations=rots.value, status=st, stop=stop.value)
 
 
-def inner_solve(A, sgn, tol, mode=0, max_passes=8, lib=None):
-    """J-orthogonalise one pivot block; returns (A_out, W, rotations, passes, status)."""
+def inner_solve(A, sgn, tol, mode=0, max_passes=8, lib=None, want_tmax=False):
+    """J-orthogonalise one pivot block; returns (A_out, W, rotations, passes,
+    status), and the largest applied |t| after them with ``want_tmax``."""
     A = np.array(A, dtype=np.float64, order="F", copy=True)
     nn = A.shape[0]
     s = _signs(sgn, nn)
     W = np.zeros((nn, nn), order="F")
-    nrot, passes = _i64(), _int()
+    nrot, passes, tmax = _i64(), _int(), _dbl()
     st = (lib or _load()).orc_inner_solve(nn, _ptr(A), _ptr(s), float(tol), int(mode), int(max_passes),
-                                 _ptr(W), ctypes.byref(nrot), ctypes.byref(passes))
+                                 _ptr(W), ctypes.byref(nrot), ctypes.byref(passes), ctypes.byref(tmax))
+    if want_tmax:
+        return A, W, nrot.value, passes.value, st, tmax.value
     return A, W, nrot.value, passes.value, st
 
 
 def block_hsvd(G, J, b, tol, max_sweeps=30, inner_mode=0, inner_max_passes=8, sort=True,
-               want_u=True, want_v=True, lib=None):
-    """Blocked one-sided hyperbolic Jacobi SVD on the CPU (block width b)."""
+               want_u=True, want_v=True, lib=None, tstop=0.0):
+    """Blocked one-sided hyperbolic Jacobi SVD on the CPU (block width b);
+    ``tstop`` as for :func:`hsvd`, over the inner rotations' tangents."""
     G = _fcol(G)
     m, n = G.shape
     j = _signs(J, n)
     sigma = np.zeros(n)
     U = np.zeros((m, n), order="F") if want_u else None
     V = np.zeros((n, n), order="F") if want_v else None
-    sweeps, rots = _int(), _i64()
+    sweeps, rots, stop = _int(), _i64(), _int()
     st = (lib or _load()).orc_block_hsvd(m, n, _ptr(G), m, _ptr(j), int(b), float(tol), int(max_sweeps),
                                 int(inner_mode), int(inner_max_passes), 1 if sort else 0,
-                                _ptr(sigma), _ptr(U), m, _ptr(V), n, ctypes.byref(sweeps), ctypes.byref(rots))
-    return dict(sigma=sigma, U=U, V=V, sweeps=sweeps.value, rotations=rots.value, status=st)
+                                _ptr(sigma), _ptr(U), m, _ptr(V), n, ctypes.byref(sweeps), ctypes.byref(rots),
+                                float(tstop), ctypes.byref(stop))
+    return dict(sigma=sigma, U=U, V=V, sweeps=sweeps.value, rotations=rots.value, status=st, stop=stop.value)

@@ -31,6 +31,10 @@ HSVD_INNER_ORIENTED = 0
 HSVD_INNER_FULL = 1
 HSVD_PRECISION_FP64 = 0
 HSVD_PRECISION_BF16X8 = 1
+HSVD_TSTOP_PAPER = 2.0 ** -27  # T_eps = sqrt(2^-52) / 2 (Sec. 2)
+HSVD_STOP_NONE = 0
+HSVD_STOP_ORTHO = 1
+HSVD_STOP_TANGENT = 2
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libhsvd.so")
@@ -52,25 +56,26 @@ class HsvdOpts(ctypes.Structure):
     _fields_ = [("tol", _dbl), ("max_sweeps", _int), ("method", _int), ("block_w", _int),
                 ("inner_mode", _int), ("inner_max_passes", _int), ("sort", _int), ("profile", _int),
                 ("precision", _int), ("skip_model", _p), ("skip_tau", _dbl), ("trace_out", _p),
-                ("trace_cap", _i64), ("reserved", _int * 6)]
+                ("trace_cap", _i64), ("tstop", _dbl), ("reserved", _int * 4)]
 
 
 class HsvdInfo(ctypes.Structure):
     _fields_ = [("sweeps", _int), ("method", _int), ("block_w", _int), ("status", _int),
                 ("rotations", _i64), ("pair_updates", _i64), ("kernel_launches", _i64),
                 ("ms_gram", _dbl), ("ms_solve", _dbl), ("ms_update", _dbl), ("ms_other", _dbl),
-                ("pair_visits", _i64), ("masked_sweeps", _int), ("judge_sweeps", _int), ("trace_rows", _i64)]
+                ("pair_visits", _i64), ("masked_sweeps", _int), ("judge_sweeps", _int), ("trace_rows", _i64),
+                ("stop_rule", _int)]
 
 
 class HsvdBatchOpts(ctypes.Structure):
     _fields_ = [("tol", _dbl), ("max_sweeps", _int), ("sort", _int), ("group_width", _int), ("use_graph", _int),
-                ("reserved", _int * 4)]
+                ("tstop", _dbl), ("reserved", _int * 2)]
 
 
 class HsvdBatchInfo(ctypes.Structure):
     _fields_ = [("grid", _int), ("tuned", _int), ("bucket_width", _int * 5), ("max_sweeps_run", _int),
                 ("rotations", _i64), ("kernel_launches", _i64), ("resident", _i64 * 3), ("ms_kernel", _dbl),
-                ("ms_tune", _dbl)]
+                ("ms_tune", _dbl), ("tangent_stops", _i64)]
 
 
 class HsvdError(RuntimeError):
@@ -173,6 +178,7 @@ class HsvdResult:
     masked_sweeps: int = 0
     judge_sweeps: int = 0
     trace_rows: int = 0
+    stop_rule: int = HSVD_STOP_NONE
 
 
 HSVD_SORT_AUTO = -1
@@ -180,9 +186,10 @@ HSVD_SORT_AUTO = -1
 
 def make_opts(tol=0.0, max_sweeps=30, method=HSVD_METHOD_AUTO, block_w=0, inner_mode=HSVD_INNER_ORIENTED,
               inner_max_passes=8, sort=None, profile=False, precision=HSVD_PRECISION_FP64, skip_model=None,
-              skip_tau=0.0, trace_out=None):
+              skip_tau=0.0, trace_out=None, tstop=0.0):
     """Options record; ``sort=None`` lets the library choose (sorting for the
-    pointwise method only).  ``skip_model``: a float32 tensor of
+    pointwise method only).  ``tstop``: tangent threshold of the early stop
+    (0 = off, negative = HSVD_TSTOP_PAPER).  ``skip_model``: a float32 tensor of
     HSVD_MLP_PARAMS values (the learned form); ``trace_out``: a CUDA float32
     tensor of shape (rows, 9) receiving training rows.  The caller keeps both
     tensors alive while the options are in use."""
@@ -208,6 +215,7 @@ def make_opts(tol=0.0, max_sweeps=30, method=HSVD_METHOD_AUTO, block_w=0, inner_
             raise ValueError("trace_out: contiguous CUDA float32 tensor of shape (rows, 9)")
         o.trace_out = trace_out.data_ptr()
         o.trace_cap = trace_out.shape[0]
+    o.tstop = float(tstop)
     return o
 
 
@@ -244,7 +252,7 @@ def hsvd_solve_ex(G, J, opts=None, compute_u=True, compute_v=True, stream=None, 
         raise HsvdError(st)
     return HsvdResult(sigma, U, V, info.sweeps, st, info.method, info.block_w, info.rotations, info.pair_updates,
                       info.kernel_launches, info.ms_gram, info.ms_solve, info.ms_update, info.ms_other,
-                      info.pair_visits, info.masked_sweeps, info.judge_sweeps, info.trace_rows)
+                      info.pair_visits, info.masked_sweeps, info.judge_sweeps, info.trace_rows, info.stop_rule)
 
 
 def hsvd_solve(G, J, tol=0.0, max_sweeps=30, compute_u=True, compute_v=True, stream=None, check=True):
@@ -357,7 +365,7 @@ class HsvdBatchResult:
     info: HsvdBatchInfo
 
 
-def make_batch_opts(tol=0.0, max_sweeps=30, sort=True, group_width=0, use_graph=True):
+def make_batch_opts(tol=0.0, max_sweeps=30, sort=True, group_width=0, use_graph=True, tstop=0.0):
     o = HsvdBatchOpts()
     lib().hsvd_default_batch_opts(ctypes.byref(o))
     o.tol = float(tol)
@@ -365,6 +373,7 @@ def make_batch_opts(tol=0.0, max_sweeps=30, sort=True, group_width=0, use_graph=
     o.sort = 1 if sort else 0
     o.group_width = int(group_width)
     o.use_graph = 1 if use_graph else 0
+    o.tstop = float(tstop)
     return o
 
 

@@ -80,6 +80,7 @@ struct SweepStats {
     double ms_gram = 0, ms_solve = 0, ms_update = 0, ms_other = 0;
     long long pair_visits = 0, trace_rows = 0;
     int masked_sweeps = 0, judge_sweeps = 0;
+    int stop_rule = HSVD_STOP_NONE;
 };
 
 // CUDA events recorded as graph nodes around every kernel of a sweep when
@@ -151,7 +152,8 @@ int solve_blocked_core(const double *G, int64_t m, int64_t n, int64_t ldg, const
     (void)nsplit;
     double *Wp = ws.get<double>((size_t)npairs * nn * nn);
     int *rotated = ws.get<int>(npairs);
-    // counters: [0] status (int), [2..3] rotations (u64), [4..5] updated pairs (u64)
+    // counters: [0] status (int), [2..3] rotations (u64), [4..5] updated pairs (u64),
+    // [6] a rotation of the sweep had |t| > tstop (the (11)_2 code of Eq. 4.2)
     int *cnt = ws.get<int>(8);
     int *d_tab_outer = ws.get<int>((size_t)nb * npairs * 2);
     int *d_tab_full = ws.get<int>((size_t)nn * b * 2);
@@ -169,6 +171,8 @@ int solve_blocked_core(const double *G, int64_t m, int64_t n, int64_t ldg, const
     if (prec && (!part_x || !wsl || !wexp || !dexp)) return HSVD_ERR_NOMEM;
     unsigned long long *rot_ctr = reinterpret_cast<unsigned long long *>(cnt + 2);
     unsigned long long *upd_ctr = reinterpret_cast<unsigned long long *>(cnt + 4);
+    const bool tangent_stop = o.tstop > 0.0;
+    int *tbig = tangent_stop ? cnt + 6 : nullptr;
     {
         // pair tables: outer over nb block columns as first-column indices
         std::vector<int> outer((size_t)nb * npairs * 2), full((size_t)nn * b * 2), cross((size_t)b * b * 2);
@@ -247,7 +251,7 @@ int solve_blocked_core(const double *G, int64_t m, int64_t n, int64_t ldg, const
         cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
         if (e != cudaSuccess) return e;
         long long nl = 0;
-        e = cudaMemsetAsync(cnt + 2, 0, 4 * sizeof(int), st);
+        e = cudaMemsetAsync(cnt + 2, 0, 5 * sizeof(int), st);
         for (int s = 0; s < nb && e == cudaSuccess; ++s) {
             const int np = nact[(size_t)s];
             if (np == 0) continue;
@@ -263,10 +267,10 @@ int solve_blocked_core(const double *G, int64_t m, int64_t n, int64_t ldg, const
             if (e == cudaSuccess)
                 e = prec ? launch_solve(b, np, part_x, ksplit_x, nullptr, sgn, col0, nullptr, tol, mode,
                                         o.inner_max_passes, d_tab_full, d_tab_cross, Wp, rotated, rot_ctr, cnt, st,
-                                        1, dexp, vs, vs ? trace : nullptr)
+                                        1, dexp, vs, vs ? trace : nullptr, o.tstop, tbig)
                          : launch_solve(b, np, part, ns, nullptr, sgn, col0, nullptr, tol, mode,
                                         o.inner_max_passes, d_tab_full, d_tab_cross, Wp, rotated, rot_ctr, cnt, st,
-                                        0, nullptr, vs, vs ? trace : nullptr);
+                                        0, nullptr, vs, vs ? trace : nullptr, o.tstop, tbig);
             if (e == cudaSuccess) e = evs.record(4 * s + 2, st);
             if (e == cudaSuccess && prec) e = launch_wprep_x(np, Wp, dexp, rotated, wsl, wexp, upd_ctr, st);
             if (e == cudaSuccess)
@@ -368,12 +372,16 @@ int solve_blocked_core(const double *G, int64_t m, int64_t n, int64_t ldg, const
             stats.trace_rows += nvis;
             stats.launches += 1;
         }
-        if (rots == 0) {
+        // Eq. 4.2 reduced over the sweep: (00)_2 no rotation, (01)_2 every
+        // tangent <= tstop, (11)_2 otherwise
+        const bool small_tangents = tangent_stop && h_cnt[6] == 0;
+        if (rots == 0 || small_tangents) {
             if (masked) {
                 judge_next = true;  // a masked sweep never ends the iteration
                 continue;
             }
             status = HSVD_OK;
+            stats.stop_rule = rots == 0 ? HSVD_STOP_ORTHO : HSVD_STOP_TANGENT;
             break;
         }
         judge_next = false;
@@ -410,6 +418,7 @@ int solve_blocked(const double *G, int64_t m, int64_t n, int64_t ldg, const int8
         info->masked_sweeps = stats.masked_sweeps;
         info->judge_sweeps = stats.judge_sweeps;
         info->trace_rows = stats.trace_rows;
+        info->stop_rule = rc == HSVD_OK ? stats.stop_rule : HSVD_STOP_NONE;
     }
     return rc;
 }
@@ -428,10 +437,10 @@ int solve_pointwise(const double *G, int64_t m, int64_t n, int64_t ldg, const in
     SweepEvents evs;
     if (o.profile && !evs.create(2)) return HSVD_ERR_CUDA;
     CKR(evs.record(0, st));
-    CKR(launch_pointwise(G, ldg, (int)m, (int)n, J, tol, o.max_sweeps, o.sort, W, sigma, U, ldu, V, ldv, out, rot,
-                         st));
+    CKR(launch_pointwise(G, ldg, (int)m, (int)n, J, tol, o.tstop, o.max_sweeps, o.sort, W, sigma, U, ldu, V, ldv, out,
+                         rot, st));
     CKR(evs.record(1, st));
-    CKR(cudaMemcpyAsync(h_out, out, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CKR(cudaMemcpyAsync(h_out, out, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
     CKR(cudaMemcpyAsync(&h_rot, rot, sizeof(long long), cudaMemcpyDeviceToHost, st));
     CKR(cudaStreamSynchronize(st));
     if (info) {
@@ -441,6 +450,7 @@ int solve_pointwise(const double *G, int64_t m, int64_t n, int64_t ldg, const in
         info->rotations = h_rot;
         info->pair_updates = 0;
         info->kernel_launches = 1;
+        info->stop_rule = h_out[2];
         if (o.profile) info->ms_solve = evs.between(0, 1);
     }
     return h_out[0];
@@ -499,8 +509,10 @@ int hsvd_solve_ex(const double *G, int64_t m, int64_t n, int64_t ldg, const int8
     if (info) memset(info, 0, sizeof *info);
     int rc = validate(G, m, n, ldg, J, sigma, ldu, U, ldv, V);
     if (rc == HSVD_OK) {
-        for (int i = 0; i < 6; ++i)
+        for (int i = 0; i < 4; ++i)
             if (o.reserved[i]) rc = HSVD_ERR_ARG;
+        if (o.tstop < 0.0) o.tstop = HSVD_TSTOP_PAPER;
+        if (!(o.tstop >= 0.0 && o.tstop <= 1.0)) rc = HSVD_ERR_ARG;
         if (o.max_sweeps <= 0) o.max_sweeps = 30;
         if (o.inner_max_passes <= 0) o.inner_max_passes = 8;
         if (o.method < HSVD_METHOD_AUTO || o.method > HSVD_METHOD_BLOCKED) rc = HSVD_ERR_ARG;

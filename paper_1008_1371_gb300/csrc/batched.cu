@@ -50,9 +50,10 @@ struct BArgs {
     int count;
     int *counter;
     int max_sweeps, sort;
+    double tstop;        // tangent threshold of the early stop, 0 = off
     double *ws;          // grid x ws_stride doubles
     int64_t ws_stride;   // doubles per CTA
-    int *res;            // 2 per factor: status, sweeps
+    int *res;            // 3 per factor: status, sweeps, stop rule
     long long *rot;      // per factor
     int *where;          // per factor: 0 G and W shared, 1 G shared, 2 global
 };
@@ -90,8 +91,9 @@ __device__ void solve_task(const BArgs &A, int k, int g, unsigned char *sm, size
     a.newpos = a.pos + n_pad;
     a.sg = a.newpos + n_pad;
     const int bar = bar_id(NT, g);
-    pw_solve<NT>(t.G, t.ldg, t.m, t.n, t.J, m_pad, n_pad, t.tol, A.max_sweeps, A.sort, a, sc[bar], t.sigma, t.U,
-                 t.ldu, t.V, t.ldv, &A.res[2 * t.idx], &A.res[2 * t.idx + 1], &A.rot[t.idx], bar);
+    int *res = A.res + 3 * (size_t)t.idx;
+    pw_solve<NT>(t.G, t.ldg, t.m, t.n, t.J, m_pad, n_pad, t.tol, A.tstop, A.max_sweeps, A.sort, a, sc[bar], t.sigma,
+                 t.U, t.ldu, t.V, t.ldv, &res[0], &res[1], &A.rot[t.idx], &res[2], bar);
     if ((threadIdx.x & (NT - 1)) == 0) A.where[t.idx] = where;
 }
 
@@ -163,8 +165,8 @@ struct Launch {
 
 // Runs the persistent kernel over `tasks` (already in queue order) as one
 // captured graph: counter reset + the launch.
-cudaError_t run_batch(const std::vector<BTask> &tasks, int max_sweeps, int sort, bool use_graph, int grid,
-                      int *res, long long *rot, int *where, cudaStream_t st, float *ms) {
+cudaError_t run_batch(const std::vector<BTask> &tasks, int max_sweeps, int sort, double tstop, bool use_graph,
+                      int grid, int *res, long long *rot, int *where, cudaStream_t st, float *ms) {
     const int count = (int)tasks.size();
     const int64_t stride = ws_stride_for(tasks);
     BTask *d_tasks = nullptr;
@@ -182,6 +184,7 @@ cudaError_t run_batch(const std::vector<BTask> &tasks, int max_sweeps, int sort,
     A.counter = d_counter;
     A.max_sweeps = max_sweeps;
     A.sort = sort;
+    A.tstop = tstop;
     A.ws = d_ws;
     A.ws_stride = stride;
     A.res = res;
@@ -288,7 +291,7 @@ cudaError_t tune_widths(const std::vector<BTask> &all, int grid, int *res, long 
             }
             order_tasks(sample);
             float ms = 0.f;
-            const cudaError_t e = run_batch(sample, 2, 1, false, grid, res, rot, where, st, &ms);
+            const cudaError_t e = run_batch(sample, 2, 1, 0.0, false, grid, res, rot, where, st, &ms);
             if (e != cudaSuccess) return e;
             if (ms_total) *ms_total += ms;
             const double score = work / std::max(ms, 1e-3f);
@@ -343,6 +346,8 @@ int hsvd_solve_batched_ex(int64_t count, const double *const *G, const int64_t *
         return HSVD_ERR_ARG;
     for (int r : o.reserved)
         if (r) return HSVD_ERR_ARG;
+    if (o.tstop < 0.0) o.tstop = HSVD_TSTOP_PAPER;
+    if (!(o.tstop >= 0.0 && o.tstop <= 1.0)) return HSVD_ERR_ARG;
     if (info) memset(info, 0, sizeof *info);
     if (count == 0) return HSVD_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -377,7 +382,7 @@ int hsvd_solve_batched_ex(int64_t count, const double *const *G, const int64_t *
     auto fail = [&](int code) {
         if (rc == HSVD_OK) rc = code;
     };
-    if (cudaMallocAsync((void **)&d_res, sizeof(int) * 2 * (size_t)count, st) != cudaSuccess ||
+    if (cudaMallocAsync((void **)&d_res, sizeof(int) * 3 * (size_t)count, st) != cudaSuccess ||
         cudaMallocAsync((void **)&d_where, sizeof(int) * (size_t)count, st) != cudaSuccess ||
         cudaMallocAsync((void **)&d_rot, sizeof(long long) * (size_t)count, st) != cudaSuccess)
         fail(HSVD_ERR_NOMEM);
@@ -438,13 +443,13 @@ int hsvd_solve_batched_ex(int64_t count, const double *const *G, const int64_t *
     order_tasks(tasks);
     float ms = 0.f;
     if (rc == HSVD_OK &&
-        run_batch(tasks, o.max_sweeps, o.sort ? 1 : 0, o.use_graph != 0, grid, d_res, d_rot, d_where, st, &ms) !=
-            cudaSuccess)
+        run_batch(tasks, o.max_sweeps, o.sort ? 1 : 0, o.tstop, o.use_graph != 0, grid, d_res, d_rot, d_where, st,
+                  &ms) != cudaSuccess)
         fail(HSVD_ERR_CUDA);
-    std::vector<int> h_res(2 * (size_t)count, 0), h_where((size_t)count, 0);
+    std::vector<int> h_res(3 * (size_t)count, 0), h_where((size_t)count, 0);
     std::vector<long long> h_rot((size_t)count, 0);
     if (rc == HSVD_OK &&
-        (cudaMemcpyAsync(h_res.data(), d_res, sizeof(int) * 2 * (size_t)count, cudaMemcpyDeviceToHost, st) !=
+        (cudaMemcpyAsync(h_res.data(), d_res, sizeof(int) * 3 * (size_t)count, cudaMemcpyDeviceToHost, st) !=
              cudaSuccess ||
          cudaMemcpyAsync(h_where.data(), d_where, sizeof(int) * (size_t)count, cudaMemcpyDeviceToHost, st) !=
              cudaSuccess ||
@@ -476,9 +481,9 @@ int hsvd_solve_batched_ex(int64_t count, const double *const *G, const int64_t *
     int worst = HSVD_OK;
     if (rc == HSVD_OK) {
         for (int64_t k = 0; k < count; ++k) {
-            const int s_k = h_res[2 * (size_t)k];
+            const int s_k = h_res[3 * (size_t)k];
             if (status) status[k] = s_k;
-            if (sweeps) sweeps[k] = h_res[2 * (size_t)k + 1];
+            if (sweeps) sweeps[k] = h_res[3 * (size_t)k + 1];
             if (s_k < 0 && worst >= 0) worst = s_k;
             else if (s_k == HSVD_NOT_CONVERGED && worst == HSVD_OK) worst = s_k;
         }
@@ -491,7 +496,8 @@ int hsvd_solve_batched_ex(int64_t count, const double *const *G, const int64_t *
             info->kernel_launches = 1;
             for (int64_t k = 0; k < count; ++k) {
                 info->rotations += h_rot[(size_t)k];
-                info->max_sweeps_run = std::max(info->max_sweeps_run, h_res[2 * (size_t)k + 1]);
+                info->max_sweeps_run = std::max(info->max_sweeps_run, h_res[3 * (size_t)k + 1]);
+                info->tangent_stops += h_res[3 * (size_t)k + 2] == HSVD_STOP_TANGENT;
                 info->resident[std::min(2, std::max(0, h_where[(size_t)k]))] += 1;
             }
         }

@@ -153,8 +153,9 @@ __device__ __forceinline__ double assemble_entry(const double *__restrict__ part
 // pointwise.cu: one CTA solves one factor held in shared memory.
 size_t pointwise_smem_bytes(int64_t m_pad, int64_t n_pad);
 bool pointwise_fits(int64_t m, int64_t n);
+// dev_out: status, sweeps, stop rule (HSVD_STOP_*); tstop = 0: strict stop only
 cudaError_t launch_pointwise(const double *G, int64_t ldg, int m, int n, const int8_t *J,
-                             double tol, int max_sweeps, int sort, double *Wws,
+                             double tol, double tstop, int max_sweeps, int sort, double *Wws,
                              double *sigma, double *U, int64_t ldu, double *V, int64_t ldv,
                              int *dev_out, long long *dev_rot, cudaStream_t st);
 
@@ -168,7 +169,7 @@ cudaError_t launch_solve(int b, int npairs, const double *part, int nsplit, doub
                          const int *tab_cross, double *Wp, int *rotated,
                          unsigned long long *rot_count, int *status, cudaStream_t st,
                          int full_part = 0, int *dexp = nullptr, const int *visit = nullptr,
-                         float *trace = nullptr);
+                         float *trace = nullptr, double tstop = 0.0, int *tbig = nullptr);
 
 // learned form (learned.cu)
 cudaError_t launch_features(const float *trace, const int8_t *prev_skip, const int *tab, int nvis, int b, int nb,

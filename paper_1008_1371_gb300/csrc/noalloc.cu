@@ -64,8 +64,8 @@ extern "C" int hsvd_solve_pointwise_noalloc(const double *G, int64_t m, int64_t 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // the kernel writes every scratch word it later reads (W = I first, the
     // status words last), so nothing has to be cleared between calls
-    if (launch_pointwise(G, ldg, (int)m, (int)n, J, tol, max_sweeps, sort ? 1 : 0, W, sigma, U, ldu, V, ldv, out,
-                         rot, st) != cudaSuccess)
+    if (launch_pointwise(G, ldg, (int)m, (int)n, J, tol, 0.0, max_sweeps, sort ? 1 : 0, W, sigma, U, ldu, V, ldv,
+                         out, rot, st) != cudaSuccess)
         return HSVD_ERR_CUDA;
     int h_out[2] = {0, 0};
     if (cudaMemcpyAsync(h_out, out, sizeof h_out, cudaMemcpyDeviceToHost, st) != cudaSuccess ||

@@ -11,7 +11,7 @@ constexpr int kThreads = 1024;
 
 __global__ void __launch_bounds__(kThreads, 1)
 k_pointwise(const double *__restrict__ G, int64_t ldg, int m, int n, const int8_t *__restrict__ J,
-            int m_pad, int n_pad, double tol, int max_sweeps, int sort, double *__restrict__ W,
+            int m_pad, int n_pad, double tol, double tstop, int max_sweeps, int sort, double *__restrict__ W,
             double *__restrict__ sigma, double *__restrict__ U, int64_t ldu, double *__restrict__ V,
             int64_t ldv, int *__restrict__ out, long long *__restrict__ rot_out) {
     extern __shared__ __align__(16) double smem[];
@@ -23,8 +23,8 @@ k_pointwise(const double *__restrict__ G, int64_t ldg, int m, int n, const int8_
     sh.pos = reinterpret_cast<int *>(sh.d + n_pad);
     sh.newpos = sh.pos + n_pad;
     sh.sg = sh.newpos + n_pad;
-    pw_solve<kThreads>(G, ldg, m, n, J, m_pad, n_pad, tol, max_sweeps, sort, sh, sc, sigma, U, ldu, V, ldv,
-                       &out[0], &out[1], rot_out, 0);
+    pw_solve<kThreads>(G, ldg, m, n, J, m_pad, n_pad, tol, tstop, max_sweeps, sort, sh, sc, sigma, U, ldu, V,
+                       ldv, &out[0], &out[1], rot_out, &out[2], 0);
 }
 
 }  // namespace
@@ -39,7 +39,7 @@ bool pointwise_fits(int64_t m, int64_t n) {
 }
 
 cudaError_t launch_pointwise(const double *G, int64_t ldg, int m, int n, const int8_t *J,
-                             double tol, int max_sweeps, int sort, double *Wws, double *sigma,
+                             double tol, double tstop, int max_sweeps, int sort, double *Wws, double *sigma,
                              double *U, int64_t ldu, double *V, int64_t ldv, int *dev_out,
                              long long *dev_rot, cudaStream_t st) {
     const int n_pad = n + (n & 1);
@@ -48,7 +48,7 @@ cudaError_t launch_pointwise(const double *G, int64_t ldg, int m, int n, const i
     cudaError_t e = cudaFuncSetAttribute(k_pointwise, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    k_pointwise<<<1, kThreads, smem, st>>>(G, ldg, m, n, J, m_pad, n_pad, tol, max_sweeps, sort, Wws,
+    k_pointwise<<<1, kThreads, smem, st>>>(G, ldg, m, n, J, m_pad, n_pad, tol, tstop, max_sweeps, sort, Wws,
                                            sigma, U, ldu, V, ldv, dev_out, dev_rot);
     return cudaGetLastError();
 }

@@ -14,9 +14,11 @@
 // computes (t, c) redundantly in all lanes (uniform control flow, no divergence
 // between the two rotation kinds inside a warp) and updates its two columns of
 // G and of W with the FMA form of Alg. 4.5.  One group barrier separates
-// steps.  The convergence check is a shared counter (the bit-or reduction of
-// Eq. 4.2 collapses to "any rotation in this sweep"), so no host round trip is
-// needed between sweeps.
+// steps.  The convergence check is the bit-or reduction of Eq. 4.2 held in two
+// shared words: the sweep's rotation count (code (00)_2 when it is zero) and,
+// with the tangent threshold T on, a flag set by any rotation with |t| > T
+// (code (11)_2); a sweep that rotated without setting it is code (01)_2 and
+// also ends the iteration.  No host round trip is needed between sweeps.
 //
 // Columns are never moved: positions map to columns through pos[] (Sec. 4).
 // Before the first sweep positions are grouped J+ then J- (Alg. 4.2 assumes
@@ -104,7 +106,7 @@ __device__ __forceinline__ void grp_sync(int bar) {
 
 // shared scalars of a group
 struct PwScalars {
-    int rot, err, bad;
+    int rot, err, bad, big;
     unsigned long long total;
 };
 
@@ -143,20 +145,23 @@ __device__ void pw_reorder(const PwArrays &sh, int m_pad, int n_pad, int use_d, 
     grp_sync<NT>(bar);
 }
 
-// Solves one factor; every thread of the group calls it.  Writes status, sweeps
-// and the rotation count through out_status / out_sweeps / out_rot (thread 0).
+// Solves one factor; every thread of the group calls it.  Writes status, sweeps,
+// the rotation count and the stop rule (HSVD_STOP_*) through out_status /
+// out_sweeps / out_rot / out_rule (thread 0; out_rule may be null).  tstop > 0
+// is the tangent threshold of the early stop (Sec. 2), 0 turns it off.
 template <int NT>
 __device__ void pw_solve(const double *__restrict__ G, int64_t ldg, int m, int n, const int8_t *__restrict__ J,
-                         int m_pad, int n_pad, double tol, int max_sweeps, int sort, const PwArrays &sh,
-                         PwScalars &sc, double *__restrict__ sigma, double *__restrict__ U, int64_t ldu,
-                         double *__restrict__ V, int64_t ldv, int *out_status, int *out_sweeps,
-                         long long *out_rot, int bar) {
+                         int m_pad, int n_pad, double tol, double tstop, int max_sweeps, int sort,
+                         const PwArrays &sh, PwScalars &sc, double *__restrict__ sigma, double *__restrict__ U,
+                         int64_t ldu, double *__restrict__ V, int64_t ldv, int *out_status, int *out_sweeps,
+                         long long *out_rot, int *out_rule, int bar) {
     constexpr int kW = NT / kWarp;
     const int tid = threadIdx.x & (NT - 1), lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
         sc.rot = 0;
         sc.err = 0;
         sc.bad = 0;
+        sc.big = 0;
         sc.total = 0;
     }
     grp_sync<NT>(bar);
@@ -194,6 +199,7 @@ __device__ void pw_solve(const double *__restrict__ G, int64_t ldg, int m, int n
             *out_status = (b & 2) ? HSVD_ERR_ARG : HSVD_ERR_NONFINITE;
             *out_sweeps = 0;
             *out_rot = 0;
+            if (out_rule) *out_rule = HSVD_STOP_NONE;
         }
         return;
     }
@@ -210,7 +216,7 @@ __device__ void pw_solve(const double *__restrict__ G, int64_t ldg, int m, int n
     if (sort) pw_reorder<NT>(sh, m_pad, n_pad, 1, bar);
 
     long long rot_total = 0;
-    int sweep = 0, status = HSVD_NOT_CONVERGED;
+    int sweep = 0, status = HSVD_NOT_CONVERGED, rule = HSVD_STOP_NONE;
     const int half = n_pad / 2;
     for (sweep = 1; sweep <= max_sweeps; ++sweep) {
         for (int s = 0; s < n_pad; ++s) {
@@ -285,6 +291,8 @@ __device__ void pw_solve(const double *__restrict__ G, int64_t ldg, int m, int n
                     if (d == 2) atomicExch(&sc.err, HSVD_ERR_RANK);
                 }
                 const unsigned rmask = __ballot_sync(0xffffffffu, my_rot);
+                if (tstop > 0.0 && __any_sync(0xffffffffu, my_rot && fabs(my_t) > tstop) && lane == 0)
+                    sc.big = 1;
                 for (int j = 0; j < nbatch; ++j) {
                     if (!((rmask >> j) & 1u)) continue;
                     const double t = __shfl_sync(0xffffffffu, my_t, j), c = __shfl_sync(0xffffffffu, my_c, j);
@@ -306,11 +314,15 @@ __device__ void pw_solve(const double *__restrict__ G, int64_t ldg, int m, int n
             status = sc.err;
             break;
         }
-        const int nrot = sc.rot;
+        const int nrot = sc.rot, big = sc.big;
         grp_sync<NT>(bar);
-        if (tid == 0) sc.rot = 0;
-        if (nrot == 0) {
+        if (tid == 0) {
+            sc.rot = 0;
+            sc.big = 0;
+        }
+        if (nrot == 0 || (tstop > 0.0 && !big)) {  // (00)_2 or (01)_2 of Eq. 4.2
             status = HSVD_OK;
+            rule = nrot == 0 ? HSVD_STOP_ORTHO : HSVD_STOP_TANGENT;
             break;
         }
         if (sort) pw_reorder<NT>(sh, m_pad, n_pad, 1, bar);
@@ -354,6 +366,7 @@ __device__ void pw_solve(const double *__restrict__ G, int64_t ldg, int m, int n
         *out_status = status;
         *out_sweeps = sweep;
         *out_rot = (long long)sc.total;
+        if (out_rule) *out_rule = status == HSVD_OK ? rule : HSVD_STOP_NONE;
     }
     grp_sync<NT>(bar);
 }

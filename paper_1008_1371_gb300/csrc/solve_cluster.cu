@@ -57,7 +57,7 @@ k_solve_cluster(const double *__restrict__ part, int nsplit, int full_part, doub
                 const int *__restrict__ tab_full, const int *__restrict__ tab_cross,
                 double *__restrict__ Wout, int *__restrict__ rotated,
                 unsigned long long *__restrict__ rot_count, int *__restrict__ status, int *__restrict__ dexp,
-                const int *__restrict__ visit, float *__restrict__ trace) {
+                const int *__restrict__ visit, float *__restrict__ trace, double tstop, int *__restrict__ tbig) {
     constexpr int H = NN / 2, R = NN / C, LD = NN + 1, B = NN / 2;
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
@@ -74,6 +74,7 @@ k_solve_cluster(const double *__restrict__ part, int nsplit, int full_part, doub
     __shared__ int P[2][H], Q[2][H], Hy[2][H], Rot[2][H];
     __shared__ double T[2][H], Cc[2][H], Apq[2][H];
     __shared__ int s_flag;
+    __shared__ int s_big;  // a rotation had |t| > tstop (Eq. 4.2 code (11)_2)
     __shared__ double tr_max[C], tr_sum[C], tr_red[2][kClThreads / 32];
 
     // initial state: own rows of A_P, the whole diagonal, W = I.  A_P comes from
@@ -89,7 +90,10 @@ k_solve_cluster(const double *__restrict__ part, int nsplit, int full_part, doub
         for (int s = 0; s < nsplit; ++s) v += pp[(size_t)s * NN * NN];
         return v;
     };
-    if (tid == 0) s_flag = 0;
+    if (tid == 0) {
+        s_flag = 0;
+        s_big = 0;
+    }
     for (int x = tid; x < NN; x += kClThreads) {
         if (sgn_direct) sg[x] = sgn_direct[(size_t)pair * NN + x];
         else sg[x] = sgn_cols[col0[2 * pair + (x >= B)] + (x % B)];
@@ -186,6 +190,7 @@ k_solve_cluster(const double *__restrict__ part, int nsplit, int full_part, doub
                 const int d = pair_decision(app, aqq, apq, hyp, tol, t, c);
                 const int rot = d == 1;
                 if (d == 2) s_flag = HSVD_ERR_RANK;
+                if (rot && fabs(t) > tstop) s_big = 1;
                 T[buf][k] = t;
                 Cc[buf][k] = c;
                 Hy[buf][k] = hyp;
@@ -271,6 +276,7 @@ k_solve_cluster(const double *__restrict__ part, int nsplit, int full_part, doub
         rotated[pair] = total;
         if (rot_count && total) atomicAdd(rot_count, (unsigned long long)total);
         if (s_flag && status) atomicExch(status, s_flag);
+        if (tbig && s_big) atomicOr(tbig, 1);
     }
     cluster.sync();  // no CTA leaves while others may still write into it
     if (trace && rank == 0 && tid == 0) {
@@ -310,7 +316,8 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
               const int8_t *__restrict__ sgn_cols, const int *__restrict__ col0,
               const int8_t *__restrict__ sgn_direct, double tol, double *__restrict__ Wout,
               int *__restrict__ rotated, unsigned long long *__restrict__ rot_count, int *__restrict__ status,
-              int *__restrict__ dexp, const int *__restrict__ visit, float *__restrict__ trace) {
+              int *__restrict__ dexp, const int *__restrict__ visit, float *__restrict__ trace, double tstop,
+              int *__restrict__ tbig) {
     constexpr int h = NN / 2, P = h / C, RW = NN / C, B = NN / 2;
     constexpr int kT = LA ? kCrossThreads : kClThreads;
     cg::cluster_group cluster = cg::this_cluster();
@@ -431,6 +438,7 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
     constexpr int kMixThreads = LA ? kT - 32 : kT;
     const int warp = tid >> 5, lane = tid & 31;
     int total = 0, bad = 0, s_end = h - 1;
+    int big = 0;  // a rotation of pair tid had |t| > tstop (Eq. 4.2 code (11)_2)
     for (int s = 0; s < h; ++s) {
         const int b = s & 1;
         double nx_t = 0.0, nx_c = 1.0, nx_apq = 0.0;
@@ -449,6 +457,7 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
         }
         // every CTA sees every pair's flags: the same decision everywhere
         const int f = tid < h ? Fl[b][tid] : 0;
+        if ((f & 1) && fabs(T[b][tid]) > tstop) big = 1;
         const int nrot = __syncthreads_count(f & 1);
         bad = __syncthreads_or(f & 2);
         if (bad) {
@@ -600,10 +609,12 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
         }
     }
     cluster.sync();
+    const int any_big = tbig ? __syncthreads_or(big) : 0;
     if (rank == 0 && tid == 0) {
         rotated[pair] = total;
         if (rot_count && total) atomicAdd(rot_count, (unsigned long long)total);
         if (bad && status) atomicExch(status, HSVD_ERR_RANK);
+        if (any_big) atomicOr(tbig, 1);
         if (trace) {
             double mx = 0.0, sm2 = 0.0;
             for (int r = 0; r < C; ++r) {
@@ -626,7 +637,7 @@ cudaError_t solve_cluster_impl(int npairs, const double *part, int nsplit, int f
                                const int8_t *sgn_cols, const int *col0, const int8_t *sgn_direct, double tol,
                                int mode, int max_passes, const int *tab_full, const int *tab_cross, double *Wp,
                                int *rotated, unsigned long long *rot_count, int *status, int *dexp,
-                               const int *visit, float *trace, cudaStream_t st) {
+                               const int *visit, float *trace, double tstop, int *tbig, cudaStream_t st) {
     constexpr int C = ClusterOf<NN>::C, R = NN / C;
     if (mode == 1) {
         constexpr int P = NN / 2 / C;
@@ -639,7 +650,7 @@ cudaError_t solve_cluster_impl(int npairs, const double *part, int nsplit, int f
         if (e != cudaSuccess) return e;
         k_solve_cross<NN, C, LA><<<npairs * C, threads, smem_x, st>>>(part, nsplit, full_part, A, sgn_cols, col0,
                                                                      sgn_direct, tol, Wp, rotated, rot_count,
-                                                                     status, dexp, visit, trace);
+                                                                     status, dexp, visit, trace, tstop, tbig);
         return cudaGetLastError();
     }
     const size_t smem = (size_t)(2 * R * (NN + 1) + R * NN) * sizeof(double);
@@ -649,7 +660,7 @@ cudaError_t solve_cluster_impl(int npairs, const double *part, int nsplit, int f
     k_solve_cluster<NN, C><<<npairs * C, kClThreads, smem, st>>>(part, nsplit, full_part, A, sgn_cols, col0,
                                                                  sgn_direct, tol, mode, max_passes, tab_full,
                                                                  tab_cross, Wp, rotated, rot_count, status, dexp,
-                                                                 visit, trace);
+                                                                 visit, trace, tstop, tbig);
     return cudaGetLastError();
 }
 
@@ -659,17 +670,17 @@ cudaError_t launch_solve(int b, int npairs, const double *part, int nsplit, doub
                          const int *col0, const int8_t *sgn_direct, double tol, int mode, int max_passes,
                          const int *tab_full, const int *tab_cross, double *Wp, int *rotated,
                          unsigned long long *rot_count, int *status, cudaStream_t st, int full_part, int *dexp,
-                         const int *visit, float *trace) {
+                         const int *visit, float *trace, double tstop, int *tbig) {
     switch (b) {
         case 16: return solve_cluster_impl<32>(npairs, part, nsplit, full_part, A, sgn_cols, col0, sgn_direct, tol,
                                                mode, max_passes, tab_full, tab_cross, Wp, rotated, rot_count,
-                                               status, dexp, visit, trace, st);
+                                               status, dexp, visit, trace, tstop, tbig, st);
         case 32: return solve_cluster_impl<64>(npairs, part, nsplit, full_part, A, sgn_cols, col0, sgn_direct, tol,
                                                mode, max_passes, tab_full, tab_cross, Wp, rotated, rot_count,
-                                               status, dexp, visit, trace, st);
+                                               status, dexp, visit, trace, tstop, tbig, st);
         case 64: return solve_cluster_impl<128>(npairs, part, nsplit, full_part, A, sgn_cols, col0, sgn_direct,
                                                 tol, mode, max_passes, tab_full, tab_cross, Wp, rotated, rot_count,
-                                                status, dexp, visit, trace, st);
+                                                status, dexp, visit, trace, tstop, tbig, st);
         default: return cudaErrorInvalidValue;
     }
 }

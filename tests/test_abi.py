@@ -125,3 +125,58 @@ def test_learned_option_errors_without_gpu(api):
     o.trace_cap = 0
     assert L.hsvd_solve_ex(p(G), 4, 4, 4, p(J), p(s), None, 4, None, 4, ctypes.byref(o), ctypes.byref(info),
                            None) == api.HSVD_ERR_ARG
+
+
+def test_tstop_argument_errors_without_gpu(api):
+    """The tangent threshold is 0 (off), negative (the paper's T_eps) or in
+    (0, 1]; anything else is an argument error, found before any GPU work."""
+    L = api.lib()
+    G = np.zeros((4, 4))
+    J = np.ones(4, dtype=np.int8)
+    s = np.zeros(4)
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    arr = lambda *a: (ctypes.c_void_p * len(a))(*[x.ctypes.data for x in a])  # noqa: E731
+    i64 = lambda *a: (ctypes.c_int64 * len(a))(*a)  # noqa: E731
+    info = api.HsvdInfo()
+    for bad in (float("nan"), 1.5, float("inf")):
+        o = api.make_opts(tstop=bad)
+        assert L.hsvd_solve_ex(p(G), 4, 4, 4, p(J), p(s), None, 4, None, 4, ctypes.byref(o), ctypes.byref(info),
+                               None) == api.HSVD_ERR_ARG, bad
+        assert info.stop_rule == api.HSVD_STOP_NONE
+        ob = api.make_batch_opts(tstop=bad)
+        assert L.hsvd_solve_batched_ex(1, arr(G), i64(4), i64(4), i64(4), arr(J), arr(s), None, None, None, None,
+                                       ctypes.byref(ob), None, None) == api.HSVD_ERR_ARG, bad
+    assert api.HSVD_TSTOP_PAPER == 2.0 ** -26 / 2  # sqrt(2^-52) / 2
+
+
+_LAYOUT_STRUCTS = {
+    "hsvd_opts": "HsvdOpts",
+    "hsvd_info": "HsvdInfo",
+    "hsvd_batch_opts": "HsvdBatchOpts",
+    "hsvd_batch_info": "HsvdBatchInfo",
+}
+
+
+def test_struct_layouts_match_header(api, tmp_path):
+    """The ctypes mirrors of the option and report structs have the size and
+    field offsets a C compiler gives the header's declarations."""
+    import subprocess
+
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "hsvd.h"', "int main(void) {"]
+    for cname, pyname in _LAYOUT_STRUCTS.items():
+        cls = getattr(api, pyname)
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        for fname, _ in cls._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, fname, cname, fname))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(line.split()[:2]): int(line.split()[2]) for line in out if line.strip()}
+    for cname, pyname in _LAYOUT_STRUCTS.items():
+        cls = getattr(api, pyname)
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)

@@ -1,0 +1,164 @@
+"""The tangent-threshold stop (Sec. 2, Eq. 4.2) on the GPU, through the C ABI,
+against the CPU oracle's implementation of the same rule.
+
+Checks per form (pointwise, blocked FP64 at b = 16, 32, 64, blocked split
+precision, batched, learned): sigma within 1e-12 of the oracle; the rule that
+ended the iteration; the sweep count against the oracle's (dot products are
+summed in another order, so one sweep of slack); T = 1 stops after the first
+sweep (every tangent is the smaller root, |t| <= 1); a vanishing threshold is
+the plain stop bit for bit; the early result is the plain one truncated at
+the same sweep; one large tangent among small ones keeps a sweep going.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1008_1371_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+U64 = 2.0 ** -53
+EPS = 2.0 ** -52
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_1008_1371_gb300 import api, build_lib
+
+    build_lib.build()
+    oracle.build()
+    assert torch.cuda.is_available()
+    return api
+
+
+FORMS = {
+    "pointwise": lambda api: dict(method=api.HSVD_METHOD_POINTWISE),
+    "blocked16": lambda api: dict(method=api.HSVD_METHOD_BLOCKED, block_w=16),
+    "blocked32": lambda api: dict(method=api.HSVD_METHOD_BLOCKED, block_w=32),
+    "blocked64": lambda api: dict(method=api.HSVD_METHOD_BLOCKED, block_w=64),
+    "bf16x8": lambda api: dict(method=api.HSVD_METHOD_BLOCKED, precision=api.HSVD_PRECISION_BF16X8),
+}
+
+
+def _gpu(api, G, J, **kw):
+    dev = torch.device("cuda:0")
+    r = api.hsvd_solve_ex(torch.from_numpy(np.asfortranarray(G)).to(dev), torch.from_numpy(J).to(dev),
+                          api.make_opts(**kw), check=False)
+    torch.cuda.synchronize()
+    return dict(sigma=r.sigma.cpu().numpy(), status=r.status, sweeps=r.sweeps, stop=r.stop_rule,
+                U=r.U.cpu().numpy(), V=r.V.cpu().numpy(), judge=r.judge_sweeps)
+
+
+def _err(J, a, b):
+    err = 0.0
+    for s in (1, -1):
+        if np.any(J == s):
+            x, y = np.sort(a[J == s]), np.sort(b[J == s])
+            err = max(err, float(np.max(np.abs(x - y) / y)))
+    return err
+
+
+def _oracle(G, J, tol, form, tstop):
+    if form == "pointwise":
+        return oracle.hsvd(G, J, tol, 40, order="modulus", sort=True, tstop=tstop, want_u=False, want_v=False)
+    b = 64 if form == "bf16x8" else int(form[7:])
+    return oracle.block_hsvd(G, J, b, tol, 40, inner_mode=1, sort=False, tstop=tstop, want_u=False, want_v=False)
+
+
+@pytest.mark.parametrize("form", sorted(FORMS))
+@pytest.mark.parametrize("case", ["paper", "graded"])
+def test_paper_threshold_matches_oracle(api, form, case):
+    """eps = 2^-52 in Eq. 2.3, T = T_eps: the threshold ends the iteration
+    before the plain stop, on the GPU as in the oracle, with the same values."""
+    n = 160 if form == "pointwise" else 256
+    if case == "paper":
+        G, J, _ = W.paper(n, p=n // 2, seed=20 + n)
+    else:
+        G, J = W.graded(n, decades=6.0, seed=21)
+    kw = FORMS[form](api)
+    strict = _gpu(api, G, J, tol=EPS, max_sweeps=40, **kw)
+    early = _gpu(api, G, J, tol=EPS, max_sweeps=40, tstop=-1.0, **kw)  # negative: the paper's T_eps
+    ref = _oracle(G, J, EPS, form, oracle.T_EPS)
+    ref_strict = _oracle(G, J, EPS, form, 0.0)
+    assert strict["status"] == early["status"] == api.HSVD_OK
+    assert strict["stop"] == api.HSVD_STOP_ORTHO
+    assert early["stop"] == api.HSVD_STOP_TANGENT and ref["stop"] == oracle.ORC_STOP_TANGENT
+    assert early["sweeps"] < strict["sweeps"]
+    assert abs(early["sweeps"] - ref["sweeps"]) <= 1, (early["sweeps"], ref["sweeps"])
+    assert _err(J, early["sigma"], ref_strict["sigma"]) <= 1e-12
+    assert _err(J, early["sigma"], strict["sigma"]) <= 1e-12
+
+
+@pytest.mark.parametrize("form", sorted(FORMS))
+def test_threshold_one_is_one_sweep(api, form):
+    G, J = W.gaussian(128, seed=31)
+    r = _gpu(api, G, J, max_sweeps=40, tstop=1.0, **FORMS[form](api))
+    assert r["status"] == api.HSVD_OK and r["sweeps"] == 1 and r["stop"] == api.HSVD_STOP_TANGENT
+
+
+@pytest.mark.parametrize("form", ["pointwise", "blocked32", "bf16x8"])
+def test_vanishing_threshold_and_truncation(api, form):
+    """T = 1e-300 reproduces the plain run bit for bit; the T_eps run equals
+    the plain run capped at the same sweep count, bit for bit."""
+    G, J = W.gaussian(192, seed=32)
+    kw = FORMS[form](api)
+    plain = _gpu(api, G, J, tol=EPS, max_sweeps=40, **kw)
+    tiny = _gpu(api, G, J, tol=EPS, max_sweeps=40, tstop=1e-300, **kw)
+    assert plain["sweeps"] == tiny["sweeps"] and tiny["stop"] == api.HSVD_STOP_ORTHO
+    assert np.array_equal(plain["sigma"], tiny["sigma"]) and np.array_equal(plain["V"], tiny["V"])
+    early = _gpu(api, G, J, tol=EPS, max_sweeps=40, tstop=api.HSVD_TSTOP_PAPER, **kw)
+    cut = _gpu(api, G, J, tol=EPS, max_sweeps=early["sweeps"], **kw)
+    assert early["stop"] == api.HSVD_STOP_TANGENT and cut["status"] == api.HSVD_NOT_CONVERGED
+    assert np.array_equal(early["sigma"], cut["sigma"]) and np.array_equal(early["U"], cut["U"])
+
+
+@pytest.mark.parametrize("form", ["pointwise", "blocked16"])
+def test_one_large_tangent_keeps_the_sweep_going(api, form):
+    """Columns orthogonal except pair A = (0, 1) (first tangent about 0.2)
+    and pair B = (32, 33) in another block (tangent about 1e-9, below T_eps,
+    still failing Eq. 2.3): the sweep that rotates both cannot end the
+    iteration, wherever B's rotation lands."""
+    G = np.diag(np.arange(1.0, 65.0))
+    G[0, 1] = 0.7
+    G[32, 33] = 2e-9
+    J = np.ones(64, dtype=np.int8)
+    r = _gpu(api, G, J, tol=EPS, max_sweeps=40, tstop=-1.0, **FORMS[form](api))
+    assert r["status"] == api.HSVD_OK and r["sweeps"] >= 2
+    ref = np.sort(np.linalg.svd(G, compute_uv=False))
+    assert np.max(np.abs(np.sort(r["sigma"]) - ref) / ref) <= 1e-13
+
+
+def test_batched_threshold(api):
+    """Batched form: per-factor early stops, the count reported, values
+    against the oracle."""
+    facs = W.batch(48, nmin=16, nmax=200, seed=41)
+    dev = torch.device("cuda:0")
+    Gs = [torch.from_numpy(np.asfortranarray(G)).to(dev) for G, _ in facs]
+    Js = [torch.from_numpy(J).to(dev) for _, J in facs]
+    strict = api.hsvd_solve_batched(Gs, Js, api.make_batch_opts(tol=EPS))
+    early = api.hsvd_solve_batched(Gs, Js, api.make_batch_opts(tol=EPS, tstop=-1.0))
+    assert strict.rc == early.rc == api.HSVD_OK
+    assert strict.info.tangent_stops == 0 and early.info.tangent_stops > len(facs) // 2
+    assert all(e <= s for e, s in zip(early.sweeps, strict.sweeps))
+    assert sum(early.sweeps) < sum(strict.sweeps)
+    for k, (G, J) in enumerate(facs):
+        ref = oracle.hsvd(G, J, EPS, 40, order="modulus", sort=True, tstop=oracle.T_EPS, want_u=False, want_v=False)
+        assert _err(J, early.sigma[k].cpu().numpy(), ref["sigma"]) <= 1e-12, k
+        assert abs(early.sweeps[k] - ref["sweeps"]) <= 1, k
+    one = api.hsvd_solve_batched(Gs, Js, api.make_batch_opts(tstop=1.0))
+    assert one.rc == api.HSVD_OK and set(one.sweeps) == {1} and one.info.tangent_stops == len(facs)
+
+
+def test_learned_form_with_threshold(api):
+    """A masked sweep never ends the iteration: with a skip network that
+    skips nothing and T_eps, the stop comes from a full (judge) sweep."""
+    G, J = W.graded(256, seed=43)
+    model = torch.zeros(api.HSVD_MLP_PARAMS, dtype=torch.float32, device="cuda")
+    model[-1] = 4.0
+    kw = dict(method=api.HSVD_METHOD_BLOCKED, block_w=16, sort=False, tol=EPS, max_sweeps=40)
+    plain = _gpu(api, G, J, tstop=-1.0, **kw)
+    r = _gpu(api, G, J, tstop=-1.0, skip_model=model, **kw)
+    assert plain["status"] == r["status"] == api.HSVD_OK
+    assert r["stop"] in (api.HSVD_STOP_TANGENT, api.HSVD_STOP_ORTHO) and r["judge"] >= 1
+    assert _err(J, r["sigma"], plain["sigma"]) <= 1e-12
+    assert r["sweeps"] <= plain["sweeps"] + 1

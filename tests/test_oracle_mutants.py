@@ -34,6 +34,14 @@ MUTANTS = {
     "block_update_transposed_W": ("* Wp[x + y * nn];", "* Wp[y + x * nn];"),
     "test_uses_product_not_sqrt": ("if (aij == 0.0 || fabs(aij) < tol * sqrt(aii * ajj)) return ORC_OK;",
                                    "if (aij == 0.0 || fabs(aij) < tol * (aii * ajj)) return ORC_OK;"),
+    # the tangent-threshold stop (Sec. 2, Eq. 4.2)
+    "conv_code_inverted": ("return (tstop > 0.0 && fabs(t) <= tstop) ? 1 : 3;",
+                           "return (tstop > 0.0 && fabs(t) > tstop) ? 1 : 3;"),
+    "conv_code_overwritten": ("*cd |= conv_code(t, tstop);", "*cd = conv_code(t, tstop);"),
+    "block_code_overwritten": ("cd |= conv_code(tmax, tstop);", "cd = conv_code(tmax, tstop);"),
+    "stop_on_large_tangents": ("if (cd == 0 || cd == 1) {", "if (cd == 0 || cd == 3) {"),
+    "inner_tmax_first_rotation": ("if (fabs(T[k]) > tmax) tmax = fabs(T[k]);",
+                                  "if (tmax == 0.0) tmax = fabs(T[k]);"),
 }
 
 
@@ -112,6 +120,62 @@ def _battery(orc, lib):
     ev = np.sort(np.linalg.eigvalsh((G * J[None, :]) @ G.T))
     if r["status"] != 0 or np.max(np.abs(lam - ev)) > 8 * n * U * np.max(np.abs(ev)):
         failed.append("blocked")
+    failed += _tstop_checks(orc, lib)
+    return failed
+
+
+def _tstop_checks(orc, lib):
+    """The tangent-threshold pins of ``test_oracle_tstop.py`` in brief."""
+    failed = []
+    eps = 2.0 ** -52
+    rng = np.random.default_rng(8)
+
+    def solve(kind, G, J, tol, tstop, max_sweeps=40):
+        if kind in ("cyclic", "modulus"):
+            return orc.hsvd(G, J, tol, max_sweeps, order=kind, sort=kind == "modulus", tstop=tstop, lib=lib)
+        return orc.block_hsvd(G, J, int(kind[5:]), tol, max_sweeps, inner_mode=1, sort=False, tstop=tstop, lib=lib)
+
+    # one pair: the threshold is compared with the closed-form tangent
+    for seed in range(4):
+        G = np.asfortranarray(rng.standard_normal((3, 2)))
+        J = np.array([1, 1 if seed % 2 else -1], dtype=np.int8)
+        a = G.T @ G
+        if J[0] == J[1]:
+            t1 = np.tan(0.5 * np.arctan2(2 * abs(a[0, 1]), abs(a[0, 0] - a[1, 1])))
+        else:
+            t1 = np.tanh(0.5 * np.arctanh(2 * abs(a[0, 1]) / (a[0, 0] + a[1, 1])))
+        for kind in ("cyclic", "modulus", "block1"):
+            up, down = solve(kind, G, J, 2 * U, t1 * (1 + 1e-6)), solve(kind, G, J, 2 * U, t1 * (1 - 1e-6))
+            if up["sweeps"] != 1 or up["stop"] != orc.ORC_STOP_TANGENT or down["sweeps"] < 2:
+                failed.append("tstop-2x2-" + kind)
+    # one large tangent early in a sweep keeps it going
+    for hyp_a in (False, True):
+        G = np.diag(np.arange(1.0, 17.0))
+        G[0, 1], G[8, 9] = 0.7, 2e-9
+        J = np.ones(16, dtype=np.int8)
+        J[1] = -1 if hyp_a else 1
+        for kind in ("cyclic", "modulus", "block4"):
+            if solve(kind, np.asfortranarray(G), J, eps, orc.T_EPS)["sweeps"] < 2:
+                failed.append("tstop-or-" + kind)
+    # two rotations in one inner step, the small one first: the block's code
+    # is its largest tangent's
+    G = np.diag(np.arange(1.0, 17.0))
+    G[0, 15], G[1, 14] = 2.5e-7, 5.0
+    if solve("block4", np.asfortranarray(G), np.ones(16, dtype=np.int8), eps, orc.T_EPS)["sweeps"] < 2:
+        failed.append("tstop-inner-max")
+    # constructed ground truth at the paper's eps: the rule fires first and
+    # the values hold to 1e-12; a vanishing threshold is the plain stop
+    G, J, sig = W.paper(96, p=40, seed=77)
+    for kind in ("cyclic", "modulus", "block8"):
+        strict, early = solve(kind, G, J, eps, 0.0), solve(kind, G, J, eps, orc.T_EPS)
+        tiny = solve(kind, G, J, eps, 1e-300)
+        if early["status"] != 0 or early["stop"] != orc.ORC_STOP_TANGENT or early["sweeps"] >= strict["sweeps"]:
+            failed.append("tstop-fires-" + kind)
+        elif max(np.max(np.abs(np.sort(early["sigma"][J == s]) - np.sort(sig[J == s])) / np.sort(sig[J == s]))
+                 for s in (1, -1)) > 1e-12:
+            failed.append("tstop-truth-" + kind)
+        if tiny["sweeps"] != strict["sweeps"] or not np.array_equal(tiny["sigma"], strict["sigma"]):
+            failed.append("tstop-vanishing-" + kind)
     return failed
 
 
