@@ -94,6 +94,11 @@ def parse():
     ap.add_argument("--count", type=int, default=BATCH_COUNT, help="batch10k: number of factors")
     ap.add_argument("--group-width", type=int, default=0, help="batch10k: 0 autotunes, else 256/512/1024")
     ap.add_argument("--block", type=int, default=0, help="block width (0: the workload's)")
+    ap.add_argument("--tstop", type=float, default=0.0,
+                    help="tangent-threshold early stop (Sec. 2): 0 off, negative = the paper's T_eps = 2^-27; "
+                         "the effective flop count then uses the plain run's sweeps")
+    ap.add_argument("--tol", type=float, default=0.0,
+                    help="eps of Eq. 2.3 (0: n 2^-53; the paper's own is 2^-52)")
     return ap.parse_args()
 
 
@@ -563,7 +568,7 @@ def main():
     skip_model = train_skip_model(block, prec, learn_log) if learned else None
     G_np, J_np = make_input(args.workload, seed_offset=rank)
     m = G_np.shape[0]
-    tol = n * 2.0 ** -53
+    tol = args.tol if args.tol > 0 else n * 2.0 ** -53
     G = torch.from_numpy(G_np).to(dev).t().contiguous().t()
     J = torch.from_numpy(J_np).to(dev)
     sigma = torch.empty(n, dtype=torch.float64, device=dev)
@@ -571,18 +576,18 @@ def main():
     V = torch.empty((n, n), dtype=torch.float64, device=dev).t()
     opts = api.make_opts(tol=tol, max_sweeps=MAX_SWEEPS * (2 if learned else 1), method=api.HSVD_METHOD_BLOCKED,
                          block_w=block, profile=True, precision=prec, sort=False, skip_model=skip_model,
-                         skip_tau=args.tau)
+                         skip_tau=args.tau, tstop=args.tstop)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
     stream = torch.cuda.current_stream(dev)
 
     def solve():
         return api.hsvd_solve_ex(G, J, opts, out=(sigma, U, V), stream=stream)
 
-    # the learned form is measured against the plain method on the same factor:
-    # one plain solve (after one warm-up), untimed in the step loop; its sweep
-    # count is the S of the effective flop count
+    # the learned form and the early stop are measured against the plain method
+    # on the same factor: one plain solve (after one warm-up), untimed in the
+    # step loop; its sweep count is the S of the effective flop count
     plain = None
-    if learned:
+    if learned or args.tstop != 0.0:
         popts = api.make_opts(tol=tol, max_sweeps=MAX_SWEEPS, method=api.HSVD_METHOD_BLOCKED, block_w=block,
                               precision=prec, sort=False)
         api.hsvd_solve_ex(G, J, popts, out=(sigma, U, V), stream=stream)
@@ -594,7 +599,7 @@ def main():
         e1.record(stream)
         e1.synchronize()
         plain = {"ms": e0.elapsed_time(e1), "sweeps": pr.sweeps, "pair_visits": pr.pair_visits,
-                 "sigma": sigma.clone()}
+                 "sigma": sigma.clone(), "status": pr.status}
 
     for _ in range(args.warmup):
         solve()
@@ -625,10 +630,16 @@ def main():
     sweeps = info.sweeps
     # S of the effective flop count: the plain run's sweeps (the learned form's
     # own count includes its masked and judge sweeps)
-    s_eff = plain["sweeps"] if plain else sweeps
+    s_eff = plain["sweeps"] if plain and plain["status"] == api.HSVD_OK else sweeps
     eff_flops = s_eff * flops_per_sweep(m, n)
-    vs_plain = None
-    if plain:
+    vs_plain, tstop_vs_plain = None, None
+    if plain and not learned:
+        tstop_vs_plain = {"plain_ms": plain["ms"], "tstop_ms": ms, "plain_sweeps": plain["sweeps"],
+                          "tstop_sweeps": sweeps, "plain_status": api.hsvd_status_string(plain["status"]),
+                          "stop_rule": {1: "orthogonality", 2: "tangent"}.get(info.stop_rule, "none"),
+                          "max_rel_sigma_diff_vs_plain":
+                              float(((sigma - plain["sigma"]).abs() / plain["sigma"]).max())}
+    if plain and learned:
         vs_plain = {"plain_ms": plain["ms"], "learned_ms": None, "plain_sweeps": plain["sweeps"],
                     "learned_sweeps": sweeps, "masked_sweeps": info.masked_sweeps,
                     "judge_sweeps": info.judge_sweeps, "plain_pair_visits": plain["pair_visits"],
@@ -700,7 +711,7 @@ def main():
         Vh = torch.empty((n, n), dtype=torch.float64).pin_memory().t()
         opts_e2e = api.make_opts(tol=tol, max_sweeps=MAX_SWEEPS * (2 if learned else 1),
                                  method=api.HSVD_METHOD_BLOCKED, block_w=block, precision=prec, sort=False,
-                                 skip_model=skip_model, skip_tau=args.tau)
+                                 skip_model=skip_model, skip_tau=args.tau, tstop=args.tstop)
         api.hsvd_solve_ex(Gh, Jh, opts_e2e, out=(sh, Uh, Vh))
         e2e_t = []
         for _ in range(max(3, args.steps // 2)):
@@ -724,11 +735,12 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "ms_per_step_median": ms_median,
             "config": {"workload": wdesc + ", blocked, b=%d, %s" % (block, args.form), "m": m, "n": n,
-                       "block_w": block, "form": args.form, "tol": tol, "sweeps": sweeps, "sweeps_in_flop_count": s_eff,
+                       "block_w": block, "form": args.form, "tol": tol, "tstop": args.tstop,
+                       "sweeps": sweeps, "sweeps_in_flop_count": s_eff,
                        "inner": "block-oriented",
                        "sort": False, "l2": "flushed (256 MB write) between steps",
                        "parallelism": "replicas" if world > 1 else "single"},
-            "accuracy": accuracy, "learned_vs_plain": vs_plain,
+            "accuracy": accuracy, "learned_vs_plain": vs_plain, "tstop_vs_plain": tstop_vs_plain,
             "gpu_launches": int(sum(i.kernel_launches for i in infos)),
             "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk.summary(),
         }
