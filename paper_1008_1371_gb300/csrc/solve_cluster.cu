@@ -49,6 +49,12 @@ struct ClusterOf {
     static constexpr int C = NN == 32 ? 4 : 8;
 };
 
+// CTAs per pivot block of the cross pass (the pass of every step but the first)
+template <int NN>
+struct CrossClusterOf {
+    static constexpr int C = NN == 32 ? 4 : 8;
+};
+
 template <int NN, int C>
 __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kClThreads)
 k_solve_cluster(const double *__restrict__ part, int nsplit, int full_part, double *__restrict__ A_io,
@@ -320,6 +326,8 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
               int *__restrict__ tbig) {
     constexpr int h = NN / 2, P = h / C, RW = NN / C, B = NN / 2;
     constexpr int kT = LA ? kCrossThreads : kClThreads;
+    static_assert(P * C == h && RW * C == NN, "the pairs and rows split evenly over the cluster");
+    static_assert(!LA || P <= 32, "the look-ahead warp has one lane per owned pair");
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     const int pair = blockIdx.x / C;
@@ -640,15 +648,15 @@ cudaError_t solve_cluster_impl(int npairs, const double *part, int nsplit, int f
                                const int *visit, float *trace, double tstop, int *tbig, cudaStream_t st) {
     constexpr int C = ClusterOf<NN>::C, R = NN / C;
     if (mode == 1) {
-        constexpr int P = NN / 2 / C;
-        const size_t smem_x = (size_t)(P * NN + (P + 1) * NN + R * NN) * sizeof(double);
+        constexpr int CX = CrossClusterOf<NN>::C, P = NN / 2 / CX, RX = NN / CX;
+        const size_t smem_x = (size_t)(P * NN + (P + 1) * NN + RX * NN) * sizeof(double);
         // the look-ahead warp pays at b = 64 (measured), not at b <= 32
         constexpr bool LA = NN >= 128;
         constexpr int threads = LA ? kCrossThreads : kClThreads;
-        cudaError_t e = cudaFuncSetAttribute(k_solve_cross<NN, C, LA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_solve_cross<NN, CX, LA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem_x);
         if (e != cudaSuccess) return e;
-        k_solve_cross<NN, C, LA><<<npairs * C, threads, smem_x, st>>>(part, nsplit, full_part, A, sgn_cols, col0,
+        k_solve_cross<NN, CX, LA><<<npairs * CX, threads, smem_x, st>>>(part, nsplit, full_part, A, sgn_cols, col0,
                                                                      sgn_direct, tol, Wp, rotated, rot_count,
                                                                      status, dexp, visit, trace, tstop, tbig);
         return cudaGetLastError();
