@@ -344,6 +344,8 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
     __shared__ double T[2][h], Cc[2][h], Apq[2][h];
     __shared__ int Fl[2][h];          // bit 0: rotate, bit 1: rank deficient
     __shared__ double tr_max[C], tr_sum[C], tr_red[2][kT / 32];
+    __shared__ int s_first[C];        // per CTA: first step with a pair failing Eq. 2.3 on A_P
+    __shared__ int s_own;
 
     auto entry = [&](int x, int y) -> double {
         if (!part) return A_io[(size_t)pair * NN * NN + x + y * NN];
@@ -360,14 +362,23 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
         D[x] = entry(x, x);
         if (dexp && rank == 0) dexp[(size_t)pair * NN + x] = D[x] > 0.0 ? (ilogb(D[x]) >> 1) : 0;
     }
+    if (tid == 0) s_own = h;
     for (int e = tid; e < P * NN; e += kT) {
         const int kl = e / NN, y = e % NN;
         fix[kl * NN + y] = entry(k0 + kl, y);
-        mov[kl * NN + y] = entry(h + k0 + kl, y);  // step 0: pair k with row h + k, ring slot kl
     }
     for (int e = tid; e < RW * NN; e += kT) {
         const int x = e / NN, y = e % NN;
         Wl[x * NN + y] = (w0 + x == y) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    // Steps before the first one holding a pair that fails Eq. 2.3 on A_P as
+    // it stands rotate nothing and change nothing: the pass starts there.
+    // Pair k meets partner h + j at step (j - k) mod h; every CTA tests its
+    // own rows' cross entries, and the cluster takes the minimum.
+    for (int e = tid; e < P * h; e += kT) {
+        const int kl = e / h, j = e % h, k = k0 + kl;
+        if (!pair_passes(D[k], D[h + j], fix[kl * NN + h + j], tol)) atomicMin(&s_own, (j - k + h) % h);
     }
     __syncthreads();
     // visit record: the I x J block (rows k < h are the fixed rows) scaled by the diagonal
@@ -414,6 +425,20 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
         *cluster.map_shared_rank(&tr_max[rank], 0) = rec_max;
         *cluster.map_shared_rank(&tr_sum[rank], 0) = rec_sum;
     }
+    if (tid < C) *cluster.map_shared_rank(&s_first[rank], tid) = s_own;
+    cluster.sync();
+    int s0 = h;
+    for (int r = 0; r < C; ++r) s0 = min(s0, s_first[r]);
+    // partner rows of the starting step (the last one when nothing fails):
+    // pair k with row h + (k + s) mod h in ring slot (kl + s) mod (P + 1)
+    {
+        const int sl = min(s0, h - 1);
+        for (int e = tid; e < P * NN; e += kT) {
+            const int kl = e / NN, y = e % NN;
+            mov[((kl + sl) % (P + 1)) * NN + y] = entry(h + (k0 + kl + sl) % h, y);
+        }
+    }
+    __syncthreads();
     // (t, c) of the owned pairs for step s into every CTA (buffer s & 1)
     auto params_out = [&](int s) {
         if (tid < P) {
@@ -432,7 +457,7 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
             }
         }
     };
-    params_out(0);
+    if (s0 < h) params_out(s0);
     cluster.sync();
 
     // Warp 0 works one step ahead: at the top of step s lane kl < P reads the
@@ -447,7 +472,7 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
     const int warp = tid >> 5, lane = tid & 31;
     int total = 0, bad = 0, s_end = h - 1;
     int big = 0;  // a rotation of pair tid had |t| > tstop (Eq. 4.2 code (11)_2)
-    for (int s = 0; s < h; ++s) {
+    for (int s = s0; s < h; ++s) {
         const int b = s & 1;
         double nx_t = 0.0, nx_c = 1.0, nx_apq = 0.0;
         int nx_fl = 0;

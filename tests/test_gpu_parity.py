@@ -283,6 +283,43 @@ def test_kernel_inner_solve_matches_oracle(api, b, mode):
 
 
 @pytest.mark.parametrize("b", [16, 32, 64])
+@pytest.mark.parametrize("first", ["none", "late", "last"])
+def test_kernel_cross_pass_late_first_rotation(api, b, first):
+    """Cross pass (mode 1) on pivot blocks whose off-diagonal block is zero
+    except at chosen pairs, so the first rotation comes at a chosen step (or
+    never): the steps before it change nothing, and the kernel, which starts
+    the pass at that step, still matches the oracle bit for bit."""
+    nn, h = 2 * b, b
+    rng = np.random.default_rng(500 + b)
+    picks = {"none": [], "late": [(5, h // 2 + 1), (h - 2, h // 2 + 3)], "last": [(1, h - 1)]}[first]
+    As, sg = [], []
+    for k in range(3):
+        A = np.zeros((nn, nn))
+        for lo in (0, h):
+            P = rng.standard_normal((2 * h, h)) * 10.0 ** rng.uniform(-2, 0, h)[None, :]
+            A[lo:lo + h, lo:lo + h] = P.T @ P
+        for i, s in picks:
+            q = h + (i + s) % h
+            A[i, q] = A[q, i] = 0.05 * np.sqrt(A[i, i] * A[q, q]) * (1 if k != 1 else -1)
+        As.append(A)
+        sg.append(W.signs_block(nn, [nn // 2, 5, nn][k]))
+    As, sg = np.stack(As), np.stack(sg)
+    dev = torch.device("cuda:0")
+    tol = nn * U64
+    Ao, Wg, rot, st = api.hsvd_pivot_solve(torch.from_numpy(As).to(dev), torch.from_numpy(sg).to(dev), tol, mode=1)
+    Ao, Wg, rot = Ao.cpu().numpy(), Wg.cpu().numpy(), rot.cpu().numpy()
+    assert int(st.cpu()[0]) == 0
+    for k in range(3):
+        Ar, Wr, nrot, passes, s = oracle.inner_solve(As[k], sg[k], tol, mode=1)
+        assert s == 0 and nrot == rot[k]
+        assert np.array_equal(Wg[k], Wr) and np.array_equal(Ao[k], Ar)
+        if first == "none":
+            assert rot[k] == 0 and np.array_equal(Wg[k], np.eye(nn)) and np.array_equal(Ao[k], As[k])
+        else:
+            assert rot[k] >= len(picks)
+
+
+@pytest.mark.parametrize("b", [16, 32, 64])
 def test_kernel_update(api, b):
     nn = 2 * b
     rng = np.random.default_rng(7 * b)
