@@ -65,6 +65,16 @@ extern "C" {
 
 #define HSVD_SORT_AUTO (-1)
 
+/* Schedule of a sweep of the blocked method.  Either way a sweep is one CUDA
+ * graph and the arithmetic is the same, so are the results. */
+#define HSVD_SCHEDULE_AUTO 0  /* pairs (the dependency graph) unless opts.profile    */
+#define HSVD_SCHEDULE_STEPS 1 /* the steps of the pivot strategy one after the other:
+                                 Gram of all pairs, inner solves, updates            */
+#define HSVD_SCHEDULE_PAIRS 2 /* every block-pair visit on its own: its Gram waits
+                                 only for the updates that last wrote its two block
+                                 columns, so one visit's latency-bound inner solve
+                                 overlaps other visits' Gram and update work        */
+
 /* Stopping (Sec. 2).  The iteration always stops after a sweep in which every
  * pair passed the test of Eq. 2.3 (no rotation).  With opts.tstop != 0 it also
  * stops after a sweep whose applied rotations all had |t| <= T (the
@@ -121,7 +131,9 @@ typedef struct hsvd_opts {
     int64_t trace_cap;    /* rows available at trace_out                               */
     double tstop;         /* tangent threshold T of the early stop: 0 (default) = off,
                              < 0 = HSVD_TSTOP_PAPER, else T itself (0 < T <= 1)       */
-    int reserved[4];      /* must be zero                                              */
+    int schedule;         /* HSVD_SCHEDULE_* (blocked method); with the pair schedule
+                             opts.profile reports only the sweep total, in ms_other  */
+    int reserved[3];      /* must be zero                                              */
 } hsvd_opts;
 
 typedef struct hsvd_info {

@@ -35,6 +35,9 @@ HSVD_TSTOP_PAPER = 2.0 ** -27  # T_eps = sqrt(2^-52) / 2 (Sec. 2)
 HSVD_STOP_NONE = 0
 HSVD_STOP_ORTHO = 1
 HSVD_STOP_TANGENT = 2
+HSVD_SCHEDULE_AUTO = 0
+HSVD_SCHEDULE_STEPS = 1
+HSVD_SCHEDULE_PAIRS = 2
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libhsvd.so")
@@ -56,7 +59,7 @@ class HsvdOpts(ctypes.Structure):
     _fields_ = [("tol", _dbl), ("max_sweeps", _int), ("method", _int), ("block_w", _int),
                 ("inner_mode", _int), ("inner_max_passes", _int), ("sort", _int), ("profile", _int),
                 ("precision", _int), ("skip_model", _p), ("skip_tau", _dbl), ("trace_out", _p),
-                ("trace_cap", _i64), ("tstop", _dbl), ("reserved", _int * 4)]
+                ("trace_cap", _i64), ("tstop", _dbl), ("schedule", _int), ("reserved", _int * 3)]
 
 
 class HsvdInfo(ctypes.Structure):
@@ -186,7 +189,7 @@ HSVD_SORT_AUTO = -1
 
 def make_opts(tol=0.0, max_sweeps=30, method=HSVD_METHOD_AUTO, block_w=0, inner_mode=HSVD_INNER_ORIENTED,
               inner_max_passes=8, sort=None, profile=False, precision=HSVD_PRECISION_FP64, skip_model=None,
-              skip_tau=0.0, trace_out=None, tstop=0.0):
+              skip_tau=0.0, trace_out=None, tstop=0.0, schedule=HSVD_SCHEDULE_AUTO):
     """Options record; ``sort=None`` lets the library choose (sorting for the
     pointwise method only).  ``tstop``: tangent threshold of the early stop
     (0 = off, negative = HSVD_TSTOP_PAPER).  ``skip_model``: a float32 tensor of
@@ -216,6 +219,7 @@ def make_opts(tol=0.0, max_sweeps=30, method=HSVD_METHOD_AUTO, block_w=0, inner_
         o.trace_out = trace_out.data_ptr()
         o.trace_cap = trace_out.shape[0]
     o.tstop = float(tstop)
+    o.schedule = int(schedule)
     return o
 
 

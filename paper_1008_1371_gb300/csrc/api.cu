@@ -98,8 +98,11 @@ struct SweepEvents {
             if (cudaEventCreate(&e) != cudaSuccess) return false;
         return true;
     }
-    cudaError_t record(size_t i, cudaStream_t st) {
+    cudaError_t record(size_t i, cudaStream_t st) {  // inside a stream capture
         return ev.empty() ? cudaSuccess : cudaEventRecordWithFlags(ev[i], st, cudaEventRecordExternal);
+    }
+    cudaError_t record_now(size_t i, cudaStream_t st) {  // outside a capture
+        return ev.empty() ? cudaSuccess : cudaEventRecord(ev[i], st);
     }
     float between(size_t a, size_t b) const {
         float ms = 0.f;
@@ -121,6 +124,35 @@ struct GraphGuard {
     }
 };
 
+// Streams and events with which a sweep of the pair schedule is captured:
+// one stream per visit slot, one event per block column (its last writer),
+// and the fork and join events of the capture.
+constexpr int kRing = 3;
+struct DagStreams {
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> col, join;
+    cudaEvent_t fork = nullptr;
+    bool create(int nstreams, int ncols) {
+        streams.assign((size_t)nstreams, nullptr);
+        join.assign((size_t)nstreams, nullptr);
+        col.assign((size_t)ncols, nullptr);
+        for (auto &x : streams)
+            if (cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking) != cudaSuccess) return false;
+        for (auto *v : {&join, &col})
+            for (auto &e : *v)
+                if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return false;
+        return cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess;
+    }
+    ~DagStreams() {
+        for (auto x : streams)
+            if (x) cudaStreamDestroy(x);
+        for (auto *v : {&join, &col})
+            for (auto e : *v)
+                if (e) cudaEventDestroy(e);
+        if (fork) cudaEventDestroy(fork);
+    }
+};
+
 #define CKR(expr)                                   \
     do {                                            \
         if ((expr) != cudaSuccess) return HSVD_ERR_CUDA; \
@@ -137,7 +169,13 @@ int solve_blocked_core(const double *G, int64_t m, int64_t n, int64_t ldg, const
     const int nb = (int)(n_pad / b);
     const int npairs = nb / 2;
     const int nsplit = gram_nsplit(m_pad, npairs);
+    // The pair schedule runs visits of up to kRing consecutive steps at once:
+    // every visit slot (Gram partials, W_P, flags) exists once per step of the
+    // ring.  The step schedule needs one per pair.
+    const bool pair_sched = o.schedule == HSVD_SCHEDULE_PAIRS || (o.schedule == HSVD_SCHEDULE_AUTO && !o.profile);
+    const int nslot = pair_sched ? kRing * npairs : npairs;
     GraphGuard gg;
+    DagStreams dag;
     Ws ws(st);
     double *Gw = ws.get<double>(m_pad * n_pad), *Gt = ws.get<double>(m_pad * n_pad);
     double *Ww = ws.get<double>(ldw * n_pad), *Wt = ws.get<double>(ldw * n_pad);
@@ -145,13 +183,13 @@ int solve_blocked_core(const double *G, int64_t m, int64_t n, int64_t ldg, const
     int8_t *sgn = ws.get<int8_t>(n_pad), *sgn_t = ws.get<int8_t>(n_pad);
     double *d = ws.get<double>(n_pad);
     // Gram partials: a step with np active pairs uses gram_nsplit(m_pad, np) row splits
-    int64_t part_items = 0;
+    // (the pair schedule launches one pair at a time with the full step's split)
+    int64_t part_items = (int64_t)nslot * nsplit;
     for (int np = 1; np <= npairs; ++np)
         part_items = std::max<int64_t>(part_items, (int64_t)np * gram_nsplit(m_pad, np));
     double *part = ws.get<double>((size_t)part_items * 3 * b * b);
-    (void)nsplit;
-    double *Wp = ws.get<double>((size_t)npairs * nn * nn);
-    int *rotated = ws.get<int>(npairs);
+    double *Wp = ws.get<double>((size_t)nslot * nn * nn);
+    int *rotated = ws.get<int>(nslot);
     // counters: [0] status (int), [2..3] rotations (u64), [4..5] updated pairs (u64),
     // [6] a rotation of the sweep had |t| > tstop (the (11)_2 code of Eq. 4.2)
     int *cnt = ws.get<int>(8);
@@ -164,20 +202,21 @@ int solve_blocked_core(const double *G, int64_t m, int64_t n, int64_t ldg, const
     // split-precision products: full 2b x 2b Gram partials, W' slices, exponents
     const bool prec = o.precision == HSVD_PRECISION_BF16X8;
     const int ksplit_x = prec ? precision_gram_ksplit(m_pad) : 0;
-    double *part_x = prec ? ws.get<double>((size_t)npairs * ksplit_x * nn * nn) : nullptr;
-    uint16_t *wsl = prec ? ws.get<uint16_t>(precision_wsl_elems(npairs)) : nullptr;
-    int *wexp = prec ? ws.get<int>((size_t)npairs * 2 * nn) : nullptr;
-    int *dexp = prec ? ws.get<int>((size_t)npairs * nn) : nullptr;
+    double *part_x = prec ? ws.get<double>((size_t)nslot * ksplit_x * nn * nn) : nullptr;
+    uint16_t *wsl = prec ? ws.get<uint16_t>(precision_wsl_elems(nslot)) : nullptr;
+    int *wexp = prec ? ws.get<int>((size_t)nslot * 2 * nn) : nullptr;
+    int *dexp = prec ? ws.get<int>((size_t)nslot * nn) : nullptr;
     if (prec && (!part_x || !wsl || !wexp || !dexp)) return HSVD_ERR_NOMEM;
     unsigned long long *rot_ctr = reinterpret_cast<unsigned long long *>(cnt + 2);
     unsigned long long *upd_ctr = reinterpret_cast<unsigned long long *>(cnt + 4);
     const bool tangent_stop = o.tstop > 0.0;
     int *tbig = tangent_stop ? cnt + 6 : nullptr;
+    // pair tables: outer over nb block columns as first-column indices
+    std::vector<int> outer((size_t)nb * npairs * 2);
+    fill_modulus(nb, nb, outer.data());
+    for (auto &v : outer) v *= b;
     {
-        // pair tables: outer over nb block columns as first-column indices
-        std::vector<int> outer((size_t)nb * npairs * 2), full((size_t)nn * b * 2), cross((size_t)b * b * 2);
-        fill_modulus(nb, nb, outer.data());
-        for (auto &v : outer) v *= b;
+        std::vector<int> full((size_t)nn * b * 2), cross((size_t)b * b * 2);
         fill_modulus(nn, nn, full.data());
         fill_cross(b, cross.data());
         CKR(cudaMemcpyAsync(d_tab_outer, outer.data(), outer.size() * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -197,7 +236,7 @@ int solve_blocked_core(const double *G, int64_t m, int64_t n, int64_t ldg, const
     const int reorder_kernels = o.sort ? 3 : 2;
     stats.launches += 1 + reorder_kernels;
     SweepEvents evs;
-    if (o.profile && !evs.create((size_t)nb * 4 + 2)) return HSVD_ERR_CUDA;
+    if (o.profile && !evs.create((size_t)nb * 4 + 4)) return HSVD_ERR_CUDA;
     const size_t evr = (size_t)nb * 4;
 
     // learned form and training export: one record per block-pair visit
@@ -233,13 +272,7 @@ int solve_blocked_core(const double *G, int64_t m, int64_t n, int64_t ldg, const
         h_vis = h_tab + (size_t)nvis * 2;
         h_skip = reinterpret_cast<int8_t *>(h_vis + nvis);
     }
-    std::vector<int> outer_host;
-    if (learned) {
-        outer_host.resize((size_t)nb * npairs * 2);
-        CKR(cudaMemcpyAsync(outer_host.data(), d_tab_outer, sizeof(int) * outer_host.size(), cudaMemcpyDeviceToHost,
-                            st));
-        CKR(cudaStreamSynchronize(st));
-    }
+    const std::vector<int> &outer_host = outer;
     const double tau = o.skip_tau > 0.0 ? o.skip_tau : 0.5;
     const float logit_tau = (float)log(tau / (1.0 - tau));
 
@@ -290,15 +323,98 @@ int solve_blocked_core(const double *G, int64_t m, int64_t n, int64_t ldg, const
         return e != cudaSuccess ? e : e2;
     };
 
+    // One sweep as a dependency graph of visits (the pair schedule): visit v =
+    // (I, J) of step s runs Gram, inner solve and update on the stream of its
+    // slot (s mod kRing, k), after the updates that last wrote block columns I
+    // and J.  Those are its only inputs; the slot's stream orders the reuse of
+    // the slot's buffers kRing steps later.
+    auto capture_pairs = [&](const int *tab, const int *vis, const std::vector<int> &nact,
+                             const std::vector<int> &off, const int *tab_host, cudaGraph_t *graph,
+                             long long *launches) -> cudaError_t {
+        cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
+        if (e != cudaSuccess) return e;
+        long long nl = 0;
+        e = cudaMemsetAsync(cnt + 2, 0, 5 * sizeof(int), st);
+        if (e == cudaSuccess) e = cudaEventRecord(dag.fork, st);
+        for (size_t i = 0; i < dag.streams.size() && e == cudaSuccess; ++i)
+            e = cudaStreamWaitEvent(dag.streams[i], dag.fork, 0);
+        std::vector<char> written((size_t)nb, 0);
+        for (int s = 0; s < nb && e == cudaSuccess; ++s) {
+            const int mode = (o.inner_mode == HSVD_INNER_FULL) ? 0 : (s == 0 ? 2 : 1);
+            for (int k = 0; k < nact[(size_t)s] && e == cudaSuccess; ++k) {
+                const int v = off[(size_t)s] + k;
+                const int cI = tab_host[2 * v] / b, cJ = tab_host[2 * v + 1] / b;
+                const int slot = (s % kRing) * npairs + k;
+                cudaStream_t ss = dag.streams[(size_t)slot];
+                if (written[(size_t)cI]) e = cudaStreamWaitEvent(ss, dag.col[(size_t)cI], 0);
+                if (e == cudaSuccess && written[(size_t)cJ]) e = cudaStreamWaitEvent(ss, dag.col[(size_t)cJ], 0);
+                const int *c0 = tab + 2 * v;
+                const int *vs = vis ? vis + v : nullptr;
+                double *wp = Wp + (size_t)slot * nn * nn;
+                int *rot = rotated + slot;
+                if (prec) {
+                    double *px = part_x + (size_t)slot * ksplit_x * nn * nn;
+                    int *dx = dexp + (size_t)slot * nn;
+                    uint16_t *wl = wsl + precision_wsl_elems(1) * slot;
+                    int *we = wexp + (size_t)slot * 2 * nn;
+                    if (e == cudaSuccess) e = launch_gram_x(Gw, m_pad, m_pad, 1, c0, px, cnt, ss);
+                    if (e == cudaSuccess)
+                        e = launch_solve(b, 1, px, ksplit_x, nullptr, sgn, c0, nullptr, tol, mode, o.inner_max_passes,
+                                         d_tab_full, d_tab_cross, wp, rot, rot_ctr, cnt, ss, 1, dx, vs,
+                                         vs ? trace : nullptr, o.tstop, tbig);
+                    if (e == cudaSuccess) e = launch_wprep_x(1, wp, dx, rot, wl, we, upd_ctr, ss);
+                    if (e == cudaSuccess)
+                        e = launch_update_x(Gw, m_pad, m_pad, Ww, ldw, ldw, 1, c0, wl, we, dx, rot, cnt, ss);
+                    nl += 4;
+                } else {
+                    double *pt = part + (size_t)slot * nsplit * 3 * b * b;
+                    if (e == cudaSuccess) e = launch_gram(Gw, m_pad, m_pad, b, 1, c0, nsplit, pt, ss);
+                    if (e == cudaSuccess)
+                        e = launch_solve(b, 1, pt, nsplit, nullptr, sgn, c0, nullptr, tol, mode, o.inner_max_passes,
+                                         d_tab_full, d_tab_cross, wp, rot, rot_ctr, cnt, ss, 0, nullptr, vs,
+                                         vs ? trace : nullptr, o.tstop, tbig);
+                    if (e == cudaSuccess)
+                        e = launch_update(Gw, m_pad, m_pad, Ww, ldw, ldw, b, 1, c0, wp, rot, upd_ctr, ss);
+                    nl += 3;
+                }
+                if (e == cudaSuccess) e = cudaEventRecord(dag.col[(size_t)cI], ss);
+                if (e == cudaSuccess) e = cudaEventRecord(dag.col[(size_t)cJ], ss);
+                written[(size_t)cI] = written[(size_t)cJ] = 1;
+            }
+        }
+        for (size_t i = 0; i < dag.streams.size() && e == cudaSuccess; ++i) {
+            e = cudaEventRecord(dag.join[i], dag.streams[i]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(st, dag.join[i], 0);
+        }
+        if (e == cudaSuccess) e = evs.record(evr, st);
+        if (e == cudaSuccess)
+            e = launch_reorder(Gw, Gt, m_pad, Ww, Wt, ldw, n_pad, perm, perm_t, sgn, sgn_t, d, newpos, o.sort, st);
+        if (e == cudaSuccess) e = evs.record(evr + 1, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h_cnt, cnt, 8 * sizeof(int), cudaMemcpyDeviceToHost, st);
+        const cudaError_t e2 = cudaStreamEndCapture(st, graph);
+        *launches = nl + reorder_kernels;
+        return e != cudaSuccess ? e : e2;
+    };
+
     std::vector<int> full_n((size_t)nb, npairs), full_off((size_t)nb);
     for (int s = 0; s < nb; ++s) full_off[(size_t)s] = s * npairs;
     long long full_launches = 0;
-    if (capture(d_tab_outer, d_visit, full_n, full_off, &gg.graph, &full_launches) != cudaSuccess)
+    if (pair_sched) {
+        if (!dag.create(nslot, nb)) return HSVD_ERR_CUDA;
+        if (capture_pairs(d_tab_outer, d_visit, full_n, full_off, outer.data(), &gg.graph, &full_launches) !=
+            cudaSuccess)
+            return HSVD_ERR_CUDA;
+    } else if (capture(d_tab_outer, d_visit, full_n, full_off, &gg.graph, &full_launches) != cudaSuccess) {
         return HSVD_ERR_CUDA;
+    }
     CKR(cudaGraphInstantiate(&gg.exec, gg.graph, 0));
     // profiling spans every step, skipped ones included (they record nothing)
-    auto add_profile = [&](const std::vector<int> &nact) {
+    auto add_profile = [&](const std::vector<int> &nact, bool steps) {
         if (!o.profile) return;
+        if (!steps) {  // visits overlap: only the sweep's total
+            stats.ms_other += evs.between(evr + 2, evr + 3);
+            return;
+        }
         for (int s = 0; s < nb; ++s) {
             if (nact[(size_t)s] == 0) continue;
             stats.ms_gram += evs.between(4 * s, 4 * s + 1);
@@ -351,14 +467,16 @@ int solve_blocked_core(const double *G, int64_t m, int64_t n, int64_t ldg, const
             CKR(cudaGraphLaunch(mg.exec, st));
             CKR(cudaStreamSynchronize(st));
             stats.launches += ml;
-            add_profile(nact);
+            add_profile(nact, true);
         } else {
             if (learned && judge_next) stats.judge_sweeps += 1;
+            CKR(evs.record_now(evr + 2, st));
             CKR(cudaGraphLaunch(gg.exec, st));
+            CKR(evs.record_now(evr + 3, st));
             CKR(cudaStreamSynchronize(st));
             stats.launches += full_launches;
             stats.pair_visits += nvis;
-            add_profile(full_n);
+            add_profile(full_n, !pair_sched);
             if (learned) CKR(cudaMemsetAsync(prev_skip, 0, nvis, st));
         }
         memcpy(&rots, h_cnt + 2, sizeof rots);
@@ -509,8 +627,9 @@ int hsvd_solve_ex(const double *G, int64_t m, int64_t n, int64_t ldg, const int8
     if (info) memset(info, 0, sizeof *info);
     int rc = validate(G, m, n, ldg, J, sigma, ldu, U, ldv, V);
     if (rc == HSVD_OK) {
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < 3; ++i)
             if (o.reserved[i]) rc = HSVD_ERR_ARG;
+        if (o.schedule < HSVD_SCHEDULE_AUTO || o.schedule > HSVD_SCHEDULE_PAIRS) rc = HSVD_ERR_ARG;
         if (o.tstop < 0.0) o.tstop = HSVD_TSTOP_PAPER;
         if (!(o.tstop >= 0.0 && o.tstop <= 1.0)) rc = HSVD_ERR_ARG;
         if (o.max_sweeps <= 0) o.max_sweeps = 30;
