@@ -128,6 +128,7 @@ struct GraphGuard {
 // one stream per visit slot, one event per block column (its last writer),
 // and the fork and join events of the capture.
 constexpr int kRing = 3;
+constexpr int64_t kMaxNodes = 1536;
 struct DagStreams {
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> col, join;
@@ -323,11 +324,17 @@ int solve_blocked_core(const double *G, int64_t m, int64_t n, int64_t ldg, const
         return e != cudaSuccess ? e : e2;
     };
 
-    // One sweep as a dependency graph of visits (the pair schedule): visit v =
-    // (I, J) of step s runs Gram, inner solve and update on the stream of its
-    // slot (s mod kRing, k), after the updates that last wrote block columns I
-    // and J.  Those are its only inputs; the slot's stream orders the reuse of
-    // the slot's buffers kRing steps later.
+    // One sweep as a dependency graph of visits (the pair schedule): a group of
+    // up to `grp` consecutive visits of step s runs Gram, inner solve and update
+    // on the stream of its first slot (s mod kRing, k), after the updates that
+    // last wrote its block columns.  Those are its only inputs; the slot's
+    // stream orders the reuse of the slot's buffers kRing steps later.  The
+    // group size keeps the graph near kMaxNodes kernel nodes per sweep: the
+    // GPU dispatches graph nodes at a bounded rate (about 2 us per node
+    // measured), which would otherwise bound the sweep.
+    const int kpv = prec ? 4 : 3;  // kernels per visit
+    const int grp = (int)std::min<int64_t>(npairs, std::max<int64_t>(1, ((int64_t)nb * npairs * kpv + kMaxNodes - 1) /
+                                                                          kMaxNodes));
     auto capture_pairs = [&](const int *tab, const int *vis, const std::vector<int> &nact,
                              const std::vector<int> &off, const int *tab_host, cudaGraph_t *graph,
                              long long *launches) -> cudaError_t {
@@ -341,13 +348,15 @@ int solve_blocked_core(const double *G, int64_t m, int64_t n, int64_t ldg, const
         std::vector<char> written((size_t)nb, 0);
         for (int s = 0; s < nb && e == cudaSuccess; ++s) {
             const int mode = (o.inner_mode == HSVD_INNER_FULL) ? 0 : (s == 0 ? 2 : 1);
-            for (int k = 0; k < nact[(size_t)s] && e == cudaSuccess; ++k) {
+            for (int k = 0; k < nact[(size_t)s] && e == cudaSuccess; k += grp) {
+                const int np = std::min(grp, nact[(size_t)s] - k);
                 const int v = off[(size_t)s] + k;
-                const int cI = tab_host[2 * v] / b, cJ = tab_host[2 * v + 1] / b;
                 const int slot = (s % kRing) * npairs + k;
                 cudaStream_t ss = dag.streams[(size_t)slot];
-                if (written[(size_t)cI]) e = cudaStreamWaitEvent(ss, dag.col[(size_t)cI], 0);
-                if (e == cudaSuccess && written[(size_t)cJ]) e = cudaStreamWaitEvent(ss, dag.col[(size_t)cJ], 0);
+                for (int i = 0; i < 2 * np && e == cudaSuccess; ++i) {
+                    const int c = tab_host[2 * v + i] / b;
+                    if (written[(size_t)c]) e = cudaStreamWaitEvent(ss, dag.col[(size_t)c], 0);
+                }
                 const int *c0 = tab + 2 * v;
                 const int *vs = vis ? vis + v : nullptr;
                 double *wp = Wp + (size_t)slot * nn * nn;
@@ -357,29 +366,31 @@ int solve_blocked_core(const double *G, int64_t m, int64_t n, int64_t ldg, const
                     int *dx = dexp + (size_t)slot * nn;
                     uint16_t *wl = wsl + precision_wsl_elems(1) * slot;
                     int *we = wexp + (size_t)slot * 2 * nn;
-                    if (e == cudaSuccess) e = launch_gram_x(Gw, m_pad, m_pad, 1, c0, px, cnt, ss);
+                    if (e == cudaSuccess) e = launch_gram_x(Gw, m_pad, m_pad, np, c0, px, cnt, ss);
                     if (e == cudaSuccess)
-                        e = launch_solve(b, 1, px, ksplit_x, nullptr, sgn, c0, nullptr, tol, mode, o.inner_max_passes,
-                                         d_tab_full, d_tab_cross, wp, rot, rot_ctr, cnt, ss, 1, dx, vs,
-                                         vs ? trace : nullptr, o.tstop, tbig);
-                    if (e == cudaSuccess) e = launch_wprep_x(1, wp, dx, rot, wl, we, upd_ctr, ss);
+                        e = launch_solve(b, np, px, ksplit_x, nullptr, sgn, c0, nullptr, tol, mode,
+                                         o.inner_max_passes, d_tab_full, d_tab_cross, wp, rot, rot_ctr, cnt, ss, 1, dx,
+                                         vs, vs ? trace : nullptr, o.tstop, tbig);
+                    if (e == cudaSuccess) e = launch_wprep_x(np, wp, dx, rot, wl, we, upd_ctr, ss);
                     if (e == cudaSuccess)
-                        e = launch_update_x(Gw, m_pad, m_pad, Ww, ldw, ldw, 1, c0, wl, we, dx, rot, cnt, ss);
+                        e = launch_update_x(Gw, m_pad, m_pad, Ww, ldw, ldw, np, c0, wl, we, dx, rot, cnt, ss);
                     nl += 4;
                 } else {
                     double *pt = part + (size_t)slot * nsplit * 3 * b * b;
-                    if (e == cudaSuccess) e = launch_gram(Gw, m_pad, m_pad, b, 1, c0, nsplit, pt, ss);
+                    if (e == cudaSuccess) e = launch_gram(Gw, m_pad, m_pad, b, np, c0, nsplit, pt, ss);
                     if (e == cudaSuccess)
-                        e = launch_solve(b, 1, pt, nsplit, nullptr, sgn, c0, nullptr, tol, mode, o.inner_max_passes,
-                                         d_tab_full, d_tab_cross, wp, rot, rot_ctr, cnt, ss, 0, nullptr, vs,
-                                         vs ? trace : nullptr, o.tstop, tbig);
+                        e = launch_solve(b, np, pt, nsplit, nullptr, sgn, c0, nullptr, tol, mode,
+                                         o.inner_max_passes, d_tab_full, d_tab_cross, wp, rot, rot_ctr, cnt, ss, 0,
+                                         nullptr, vs, vs ? trace : nullptr, o.tstop, tbig);
                     if (e == cudaSuccess)
-                        e = launch_update(Gw, m_pad, m_pad, Ww, ldw, ldw, b, 1, c0, wp, rot, upd_ctr, ss);
+                        e = launch_update(Gw, m_pad, m_pad, Ww, ldw, ldw, b, np, c0, wp, rot, upd_ctr, ss);
                     nl += 3;
                 }
-                if (e == cudaSuccess) e = cudaEventRecord(dag.col[(size_t)cI], ss);
-                if (e == cudaSuccess) e = cudaEventRecord(dag.col[(size_t)cJ], ss);
-                written[(size_t)cI] = written[(size_t)cJ] = 1;
+                for (int i = 0; i < 2 * np && e == cudaSuccess; ++i) {
+                    const int c = tab_host[2 * v + i] / b;
+                    e = cudaEventRecord(dag.col[(size_t)c], ss);
+                    written[(size_t)c] = 1;
+                }
             }
         }
         for (size_t i = 0; i < dag.streams.size() && e == cudaSuccess; ++i) {
