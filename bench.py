@@ -97,6 +97,8 @@ def parse():
     ap.add_argument("--tstop", type=float, default=0.0,
                     help="tangent-threshold early stop (Sec. 2): 0 off, negative = the paper's T_eps = 2^-27; "
                          "the effective flop count then uses the plain run's sweeps")
+    ap.add_argument("--schedule", default="auto", choices=["auto", "steps", "pairs"],
+                    help="sweep schedule of the blocked method (auto: the pair schedule)")
     ap.add_argument("--tol", type=float, default=0.0,
                     help="eps of Eq. 2.3 (0: n 2^-53; the paper's own is 2^-52)")
     return ap.parse_args()
@@ -574,9 +576,16 @@ def main():
     sigma = torch.empty(n, dtype=torch.float64, device=dev)
     U = torch.empty((n, m), dtype=torch.float64, device=dev).t()
     V = torch.empty((n, n), dtype=torch.float64, device=dev).t()
+    schedule = {"auto": api.HSVD_SCHEDULE_AUTO, "steps": api.HSVD_SCHEDULE_STEPS,
+                "pairs": api.HSVD_SCHEDULE_PAIRS}[args.schedule]
     opts = api.make_opts(tol=tol, max_sweeps=MAX_SWEEPS * (2 if learned else 1), method=api.HSVD_METHOD_BLOCKED,
-                         block_w=block, profile=True, precision=prec, sort=False, skip_model=skip_model,
-                         skip_tau=args.tau, tstop=args.tstop)
+                         block_w=block, precision=prec, sort=False, skip_model=skip_model,
+                         skip_tau=args.tau, tstop=args.tstop, schedule=schedule)
+    # kernel timing: the same solve with every kernel bracketed by CUDA events,
+    # under the step schedule (each kernel alone on the GPU, back to back)
+    opts_prof = api.make_opts(tol=tol, max_sweeps=MAX_SWEEPS * (2 if learned else 1), method=api.HSVD_METHOD_BLOCKED,
+                              block_w=block, profile=True, precision=prec, sort=False, skip_model=skip_model,
+                              skip_tau=args.tau, tstop=args.tstop, schedule=api.HSVD_SCHEDULE_STEPS)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
     stream = torch.cuda.current_stream(dev)
 
@@ -626,6 +635,13 @@ def main():
     ms = max_over_ranks(ms, world, dev)
     ms_median = statistics.median(step_ms)
     info = infos[-1]
+    # second timed region: per-kernel CUDA-event times (step schedule)
+    infos_k = []
+    for _ in range(max(3, args.steps // 2)):
+        flush.zero_()
+        infos_k.append(api.hsvd_solve_ex(G, J, opts_prof, out=(sigma, U, V), stream=stream))
+    torch.cuda.synchronize()
+    ms_steps = sum(i.ms_gram + i.ms_solve + i.ms_update + i.ms_other for i in infos_k) / len(infos_k)
     assert info.status == api.HSVD_OK, api.hsvd_status_string(info.status)
     sweeps = info.sweeps
     # S of the effective flop count: the plain run's sweeps (the learned form's
@@ -651,17 +667,17 @@ def main():
         vs_plain["learned_ms"] = ms
         vs_plain["speedup_vs_plain"] = plain["ms"] / ms
 
-    # dominant kernel class by CUDA-event time over the timed steps
-    tot = {k: sum(getattr(i, "ms_" + k) for i in infos) for k in ("gram", "solve", "update", "other")}
-    upd_pairs = sum(i.pair_updates for i in infos)
+    # dominant kernel class by CUDA-event time over the kernel-timing region
+    tot = {k: sum(getattr(i, "ms_" + k) for i in infos_k) for k in ("gram", "solve", "update", "other")}
+    upd_pairs = sum(i.pair_updates for i in infos_k)
     nb = -(-n // (2 * block)) * 2
-    visits = sum(i.sweeps for i in infos) * nb * (nb // 2)
+    visits = sum(i.sweeps for i in infos_k) * nb * (nb // 2)
     alg = {
         "update": upd_pairs * 2.0 * (m + n) * (2 * block) ** 2,
         "gram": visits * (6.0 if prec == api.HSVD_PRECISION_FP64 else 8.0) * m * block * block,
         # an inner rotation mixes two rows and two columns of A_P and two
         # columns of W_P: 3 vector pairs of length 2b, 6 flops per index
-        "solve": sum(i.rotations for i in infos) * 18.0 * (2 * block),
+        "solve": sum(i.rotations for i in infos_k) * 18.0 * (2 * block),
     }
     dom = max(("gram", "update", "solve"), key=lambda k: tot[k])
     fp64_peak = 152 * 2 * 2 * 2.070e9 / 1e12  # SMs x DFMA/clk x flop x max clock
@@ -686,7 +702,10 @@ def main():
                     "unit": "TFLOP/s", "frac": (ach_t / bf16_peak) if ach_t else None, "traffic": None,
                     "peak_source": "bf16 dense, measured (MEASURED_PEAKS.json, burst)",
                     "fp64_equivalent_tflops": achieved}
-    roofline["ms_by_kernel"] = {k: v / len(infos) for k, v in tot.items()}
+    roofline["ms_by_kernel"] = {k: v / len(infos_k) for k, v in tot.items()}
+    roofline["timing"] = ("kernels bracketed by CUDA events in a second timed region of %d solves under the step "
+                          "schedule (each kernel alone on the GPU); the step schedule's own time per solve there: "
+                          "%.2f ms" % (len(infos_k), ms_steps))
     roofline["alg_fp64_tflops_by_kernel"] = {k: alg[k] / (tot[k] * 1e-3) / 1e12 for k in alg if tot[k] > 0}
     traffic = PROFILED_TRAFFIC.get((args.workload, args.form, roofline["kernel"]))
     if traffic:
@@ -711,7 +730,7 @@ def main():
         Vh = torch.empty((n, n), dtype=torch.float64).pin_memory().t()
         opts_e2e = api.make_opts(tol=tol, max_sweeps=MAX_SWEEPS * (2 if learned else 1),
                                  method=api.HSVD_METHOD_BLOCKED, block_w=block, precision=prec, sort=False,
-                                 skip_model=skip_model, skip_tau=args.tau, tstop=args.tstop)
+                                 skip_model=skip_model, skip_tau=args.tau, tstop=args.tstop, schedule=schedule)
         api.hsvd_solve_ex(Gh, Jh, opts_e2e, out=(sh, Uh, Vh))
         e2e_t = []
         for _ in range(max(3, args.steps // 2)):
@@ -736,6 +755,7 @@ def main():
             "ms_per_step_median": ms_median,
             "config": {"workload": wdesc + ", blocked, b=%d, %s" % (block, args.form), "m": m, "n": n,
                        "block_w": block, "form": args.form, "tol": tol, "tstop": args.tstop,
+                       "schedule": args.schedule,
                        "sweeps": sweeps, "sweeps_in_flop_count": s_eff,
                        "inner": "block-oriented",
                        "sort": False, "l2": "flushed (256 MB write) between steps",
