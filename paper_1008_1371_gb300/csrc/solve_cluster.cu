@@ -529,53 +529,51 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
             }
         } else {
             const int mt = LA ? tid - 32 : tid;
-            // the column mix on every owned row of A and of W: pair j's columns j and h + (j + s) mod h
+            // The column mix on every owned row of A (and of W): pair j's columns
+            // j and h + (j + s) mod h.  A thread keeps one pair (its rotation in
+            // registers) and walks rows; consecutive threads take consecutive
+            // pairs, so a warp's loads of one row are consecutive words.
             auto col_mix = [&](bool with_w) {
-                constexpr int nA = 2 * P * h, nW = RW * h;
-                const int n_items = nA + (with_w ? nW : 0);
-                for (int e = mt; e < n_items; e += kMixThreads) {
-                    double *row;
-                    int j;
-                    if (e < nA) {
-                        const int r = e / h;
-                        j = e % h;
-                        row = r < P ? fix + r * NN : mov + slot(r - P) * NN;
-                    } else {
-                        const int x = (e - nA) / h;
-                        j = (e - nA) % h;
-                        row = Wl + x * NN;
-                    }
-                    if (!(Fl[b][j] & 1)) continue;
-                    const int p = j, q = h + (j + s) % h;
-                    const double t = T[b][j], c = Cc[b][j], ht = (sg[p] == sg[q]) ? -t : t;
+                static_assert(kMixThreads % h == 0, "whole rows per pass");
+                const int j = mt % h;
+                if (!(Fl[b][j] & 1)) return;
+                const int p = j, q = h + (j + s) % h;
+                const double t = T[b][j], c = Cc[b][j], ht = (sg[p] == sg[q]) ? -t : t;
+                const int nrows = 2 * P + (with_w ? RW : 0);
+                for (int r = mt / h; r < nrows; r += kMixThreads / h) {
+                    double *row = r < P ? fix + r * NN : (r < 2 * P ? mov + slot(r - P) * NN : Wl + (r - 2 * P) * NN);
                     const double a = row[p], bb = row[q];
                     row[p] = fma(ht, bb, a) * c;
                     row[q] = fma(t, a, bb) * c;
                 }
             };
-            // the row mix of every owned pair
+            // The row mix of every owned pair: rows k and its partner, every
+            // column; a thread keeps one pair and walks columns.  With W, also
+            // W's column mix (as in col_mix, on W's rows only).
             auto row_mix = [&](bool with_w) {
-                const int n_items = P * NN + (with_w ? RW * h : 0);
-                for (int e = mt; e < n_items; e += kMixThreads) {
-                    if (e >= P * NN) {
-                        const int x = (e - P * NN) / h, j = (e - P * NN) % h;
-                        if (!(Fl[b][j] & 1)) continue;
-                        double *row = Wl + x * NN;
-                        const int p = j, q = h + (j + s) % h;
-                        const double t = T[b][j], c = Cc[b][j], ht = (sg[p] == sg[q]) ? -t : t;
-                        const double a = row[p], bb = row[q];
-                        row[p] = fma(ht, bb, a) * c;
-                        row[q] = fma(t, a, bb) * c;
-                        continue;
-                    }
-                    const int kl = e / NN, y = e % NN, k = k0 + kl;
-                    if (!(Fl[b][k] & 1)) continue;
+                static_assert(kMixThreads % P == 0, "threads split evenly over the owned pairs");
+                constexpr int TP = kMixThreads / P;  // threads per owned pair
+                const int kl = mt / TP, k = k0 + kl;
+                if (Fl[b][k] & 1) {
                     const int p = k, q = h + (k + s) % h;
                     const double t = T[b][k], c = Cc[b][k], ht = (sg[p] == sg[q]) ? -t : t;
                     double *rp = fix + kl * NN, *rq = mov + slot(kl) * NN;
-                    const double a = rp[y], bb = rq[y];
-                    rp[y] = fma(ht, bb, a) * c;
-                    rq[y] = fma(t, a, bb) * c;
+                    for (int y = mt % TP; y < NN; y += TP) {
+                        const double a = rp[y], bb = rq[y];
+                        rp[y] = fma(ht, bb, a) * c;
+                        rq[y] = fma(t, a, bb) * c;
+                    }
+                }
+                if (!with_w) return;
+                const int j = mt % h;
+                if (!(Fl[b][j] & 1)) return;
+                const int pw = j, qw = h + (j + s) % h;
+                const double t = T[b][j], c = Cc[b][j], ht = (sg[pw] == sg[qw]) ? -t : t;
+                for (int x = mt / h; x < RW; x += kMixThreads / h) {
+                    double *row = Wl + x * NN;
+                    const double a = row[pw], bb = row[qw];
+                    row[pw] = fma(ht, bb, a) * c;
+                    row[qw] = fma(t, a, bb) * c;
                 }
             };
             if ((s & 1) == 0) {
