@@ -204,20 +204,22 @@ k_solve_cluster(const double *__restrict__ part, int nsplit, int full_part, doub
             }
             __syncthreads();
             if (s_flag) { err = 1; break; }
-            // 2. first half on own rows of S, W rows, diagonal (Eq. 2.6), transpose-scatter
-            for (int e = tid; e < R * H; e += kClThreads) {
-                const int x = e / H, k = e % H;
-                if (!Rot[buf][k]) continue;
-                const int p = P[buf][k], q = Q[buf][k];
+            // 2. first half on own rows of S, W rows, diagonal (Eq. 2.6), transpose-scatter;
+            //    a thread keeps one pair (its rotation in registers) and walks rows
+            static_assert(kClThreads % H == 0, "whole rows per pass");
+            if (Rot[buf][tid % H]) {
+                const int k = tid % H, p = P[buf][k], q = Q[buf][k];
                 const double t = T[buf][k], c = Cc[buf][k], ht = Hy[buf][k] < 0 ? -t : t;
-                double *row = S + x * LD;
-                const double a = row[p], b = row[q];
-                row[p] = fma(ht, b, a) * c;
-                row[q] = fma(t, a, b) * c;
-                double *wr = Wl + x * NN;
-                const double wa = wr[p], wb = wr[q];
-                wr[p] = fma(ht, wb, wa) * c;
-                wr[q] = fma(t, wa, wb) * c;
+                for (int x = tid / H; x < R; x += kClThreads / H) {
+                    double *row = S + x * LD;
+                    const double a = row[p], b = row[q];
+                    row[p] = fma(ht, b, a) * c;
+                    row[q] = fma(t, a, b) * c;
+                    double *wr = Wl + x * NN;
+                    const double wa = wr[p], wb = wr[q];
+                    wr[p] = fma(ht, wb, wa) * c;
+                    wr[q] = fma(t, wa, wb) * c;
+                }
             }
             if (tid < H && Rot[buf][tid]) {
                 const int p = P[buf][tid], q = Q[buf][tid];
@@ -236,15 +238,15 @@ k_solve_cluster(const double *__restrict__ part, int nsplit, int full_part, doub
             { double *tmp = S; S = Rv; Rv = tmp; }
             transposed ^= 1;
             // 3. second half on the received rows, then the pair's own entries
-            for (int e = tid; e < R * H; e += kClThreads) {
-                const int x = e / H, k = e % H;
-                if (!Rot[buf][k]) continue;
-                const int p = P[buf][k], q = Q[buf][k];
+            if (Rot[buf][tid % H]) {
+                const int k = tid % H, p = P[buf][k], q = Q[buf][k];
                 const double t = T[buf][k], c = Cc[buf][k], ht = Hy[buf][k] < 0 ? -t : t;
-                double *row = S + x * LD;
-                const double a = row[p], b = row[q];
-                row[p] = fma(ht, b, a) * c;
-                row[q] = fma(t, a, b) * c;
+                for (int x = tid / H; x < R; x += kClThreads / H) {
+                    double *row = S + x * LD;
+                    const double a = row[p], b = row[q];
+                    row[p] = fma(ht, b, a) * c;
+                    row[q] = fma(t, a, b) * c;
+                }
             }
             __syncthreads();
             if (tid < H && Rot[buf][tid]) {
