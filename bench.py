@@ -578,13 +578,16 @@ def main():
     V = torch.empty((n, n), dtype=torch.float64, device=dev).t()
     schedule = {"auto": api.HSVD_SCHEDULE_AUTO, "steps": api.HSVD_SCHEDULE_STEPS,
                 "pairs": api.HSVD_SCHEDULE_PAIRS}[args.schedule]
+    # diagonal sorting: the library's choice (on for split precision, off for
+    # FP64); the learned form follows visits across sweeps and needs it off
+    sort = False if learned else None
     opts = api.make_opts(tol=tol, max_sweeps=MAX_SWEEPS * (2 if learned else 1), method=api.HSVD_METHOD_BLOCKED,
-                         block_w=block, precision=prec, sort=False, skip_model=skip_model,
+                         block_w=block, precision=prec, sort=sort, skip_model=skip_model,
                          skip_tau=args.tau, tstop=args.tstop, schedule=schedule)
     # kernel timing: the same solve with every kernel bracketed by CUDA events,
     # under the step schedule (each kernel alone on the GPU, back to back)
     opts_prof = api.make_opts(tol=tol, max_sweeps=MAX_SWEEPS * (2 if learned else 1), method=api.HSVD_METHOD_BLOCKED,
-                              block_w=block, profile=True, precision=prec, sort=False, skip_model=skip_model,
+                              block_w=block, profile=True, precision=prec, sort=sort, skip_model=skip_model,
                               skip_tau=args.tau, tstop=args.tstop, schedule=api.HSVD_SCHEDULE_STEPS)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
     stream = torch.cuda.current_stream(dev)
@@ -598,7 +601,7 @@ def main():
     plain = None
     if learned or args.tstop != 0.0:
         popts = api.make_opts(tol=tol, max_sweeps=MAX_SWEEPS, method=api.HSVD_METHOD_BLOCKED, block_w=block,
-                              precision=prec, sort=False)
+                              precision=prec, sort=sort)
         api.hsvd_solve_ex(G, J, popts, out=(sigma, U, V), stream=stream)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -729,7 +732,7 @@ def main():
         Uh = torch.empty((n, m), dtype=torch.float64).pin_memory().t()
         Vh = torch.empty((n, n), dtype=torch.float64).pin_memory().t()
         opts_e2e = api.make_opts(tol=tol, max_sweeps=MAX_SWEEPS * (2 if learned else 1),
-                                 method=api.HSVD_METHOD_BLOCKED, block_w=block, precision=prec, sort=False,
+                                 method=api.HSVD_METHOD_BLOCKED, block_w=block, precision=prec, sort=sort,
                                  skip_model=skip_model, skip_tau=args.tau, tstop=args.tstop, schedule=schedule)
         api.hsvd_solve_ex(Gh, Jh, opts_e2e, out=(sh, Uh, Vh))
         e2e_t = []
@@ -758,7 +761,8 @@ def main():
                        "schedule": args.schedule,
                        "sweeps": sweeps, "sweeps_in_flop_count": s_eff,
                        "inner": "block-oriented",
-                       "sort": False, "l2": "flushed (256 MB write) between steps",
+                       "sort": bool(sort is None and prec == api.HSVD_PRECISION_BF16X8),
+                       "l2": "flushed (256 MB write) between steps",
                        "parallelism": "replicas" if world > 1 else "single"},
             "accuracy": accuracy, "learned_vs_plain": vs_plain, "tstop_vs_plain": tstop_vs_plain,
             "gpu_launches": int(sum(i.kernel_launches for i in infos)),

@@ -117,7 +117,8 @@ typedef struct hsvd_opts {
     int sort;             /* 1: diagonal sorting before the first sweep and after each
                              sweep (Sec. 4): J+ part by ||g||^2 decreasing, J- part
                              increasing; 0: no sorting; HSVD_SORT_AUTO: sorting for the
-                             pointwise method only                                     */
+                             pointwise method and the split-precision form (without
+                             skip_model or trace_out), none for FP64 blocked          */
     int profile;          /* nonzero: time every kernel with CUDA events (hsvd_info)   */
     int precision;        /* HSVD_PRECISION_FP64 or HSVD_PRECISION_BF16X8              */
     const float *skip_model; /* learned form (blocked method, sort = 0): HSVD_MLP_PARAMS

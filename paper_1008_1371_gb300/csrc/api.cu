@@ -680,9 +680,15 @@ int hsvd_solve_ex(const double *G, int64_t m, int64_t n, int64_t ldg, const int8
     if (method == HSVD_METHOD_AUTO)
         method = (pointwise_fits(m, n) && o.precision == HSVD_PRECISION_FP64) ? HSVD_METHOD_POINTWISE
                                                                               : HSVD_METHOD_BLOCKED;
-    // diagonal sorting pays for the pointwise method (Sec. 5, Table 5.3) but
-    // costs sweeps in the blocked one (measured on the graded 1024 factor)
-    if (o.sort == HSVD_SORT_AUTO) o.sort = (method == HSVD_METHOD_POINTWISE) ? 1 : 0;
+    // diagonal sorting pays for the pointwise method (Sec. 5, Table 5.3) and for
+    // the split-precision form (measured: Haar 4096, 2269 -> 2085 ms; Haar 1024,
+    // 211 -> 197 ms), but costs sweeps in the FP64 blocked one (graded 1024:
+    // 14 sweeps sorted, 11 unsorted); the learned form needs unsorted sweeps
+    if (o.sort == HSVD_SORT_AUTO)
+        o.sort = (method == HSVD_METHOD_POINTWISE ||
+                  (o.precision == HSVD_PRECISION_BF16X8 && !o.skip_model && !o.trace_out))
+                     ? 1
+                     : 0;
     // the learned form and the trace export follow block-pair visits across
     // sweeps: blocked method without column reordering
     if ((o.skip_model || o.trace_out) && (method != HSVD_METHOD_BLOCKED || o.sort != 0 ||

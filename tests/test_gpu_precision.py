@@ -139,9 +139,14 @@ def test_precision_solve_matches_oracle(api, kind, n):
     assert np.max(np.abs(V.T @ Jd @ V - Jd)) / max(1.0, np.max(np.abs(V)) ** 2) <= 1e-12 * n
     res = np.max(np.linalg.norm(G @ V - U_ * s[None, :], axis=0) / (np.linalg.norm(G) * np.linalg.norm(V, axis=0)))
     assert res <= 1e-12 * n
-    # the FP64 run of the same blocked method converges in about as many sweeps
-    r64 = _run(api, G, J, tol=tol, max_sweeps=40, method=api.HSVD_METHOD_BLOCKED, block_w=64)
+    # the FP64 run of the same blocked method (the same sorting) converges in
+    # about as many sweeps
+    r64 = _run(api, G, J, tol=tol, max_sweeps=40, method=api.HSVD_METHOD_BLOCKED, block_w=64, sort=True)
     assert r64.status == 0 and abs(r64.sweeps - r.sweeps) <= 2
+    # automatic sorting: on for split precision (measured faster), off for FP64
+    r0 = _run(api, G, J, tol=tol, max_sweeps=40, method=api.HSVD_METHOD_BLOCKED,
+              precision=api.HSVD_PRECISION_BF16X8, sort=True)
+    assert torch.equal(r0.sigma, r.sigma) and r0.sweeps == r.sweeps
 
 
 def _invariants_gpu(G, J, sigma, U, V):

@@ -36,7 +36,7 @@ FORMS = {
     "blocked16": lambda api: dict(method=api.HSVD_METHOD_BLOCKED, block_w=16),
     "blocked32": lambda api: dict(method=api.HSVD_METHOD_BLOCKED, block_w=32),
     "blocked64": lambda api: dict(method=api.HSVD_METHOD_BLOCKED, block_w=64),
-    "bf16x8": lambda api: dict(method=api.HSVD_METHOD_BLOCKED, precision=api.HSVD_PRECISION_BF16X8),
+    "bf16x8": lambda api: dict(method=api.HSVD_METHOD_BLOCKED, precision=api.HSVD_PRECISION_BF16X8, sort=False),
 }
 
 
