@@ -233,7 +233,8 @@ def check_against_fp64(api, G, J, sigma, U, V, tol, J_np):
     return {"vs_plain_fp64_max_rel_sigma_diff": worst, "vs_plain_fp64_worst_over_floor_gate": worst_gate,
             "plain_fp64_sweeps": r64.sweeps, "max_abs_UtU_minus_I": e1, "max_VtJV_minus_J_scaled": e2,
             "max_residual_GV_minus_U_sigma": float(res.max()),
-            "gate": "|d sigma|/sigma <= max(1e-12, u kappa_j) per value; invariants <= 1e-12 n"}
+            "gate": "two runs, each within its floor of the exact value: |d sigma|/sigma <= 2 max(1e-12, "
+                    "u kappa_j) per value (worst_over_floor_gate <= 2); invariants <= 1e-12 n"}
 
 
 def cpu_baseline(G, J, tol, sweeps):
