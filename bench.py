@@ -513,7 +513,7 @@ def run_reference(args):
         return run_reference_batched(args, oracle)
     G, J = make_input(args.workload)
     m, n = G.shape
-    tol = n * 2.0 ** -53
+    tol = args.tol if args.tol > 0 else n * 2.0 ** -53
     cores = oracle.set_threads(0)
     times = []
     for i in range(args.warmup + args.steps):
