@@ -200,7 +200,8 @@ int solve_blocked_core(const double *G, int64_t m, int64_t n, int64_t ldg, const
     double *Wp = ws.get<double>((size_t)nslot * nn * nn);
     int *rotated = ws.get<int>(nslot);
     // counters: [0] status (int), [2..3] rotations (u64), [4..5] updated pairs (u64),
-    // [6] a rotation of the sweep had |t| > tstop (the (11)_2 code of Eq. 4.2)
+    // [6] a rotation of the sweep had |t| > tstop (the (11)_2 code of Eq. 4.2),
+    // [7] visits kept by the skip mask of a masked sweep
     int *cnt = ws.get<int>(8);
     int *d_tab_outer = ws.get<int>((size_t)nb * npairs * 2);
     int *d_tab_full = ws.get<int>((size_t)nn * b * 2);
@@ -443,6 +444,11 @@ int solve_blocked_core(const double *G, int64_t m, int64_t n, int64_t ldg, const
         stats.ms_other += evs.between(evr, evr + 1);
     };
 
+    // masked sweeps under the pair schedule (FP64 products) keep the mask on the
+    // device and reuse one graph; otherwise the host compacts the visit table
+    const bool mask_on_device = learned && pair_sched && !prec;
+    GraphGuard gm;
+    long long mask_launches = 0;
     int status = HSVD_NOT_CONVERGED, sweep;
     bool judge_next = false;  // the next sweep must be a full one
     for (sweep = 1; sweep <= o.max_sweeps; ++sweep) {
@@ -453,7 +459,29 @@ int solve_blocked_core(const double *G, int64_t m, int64_t n, int64_t ldg, const
             stats.launches += 1;
         }
         unsigned long long rots, upds;
-        if (masked) {
+        if (masked && mask_on_device) {
+            // the mask stays on the device: one graph over every visit, skipped
+            // visits reduced to empty kernels by the (-1, -1) table entries
+            CKR(launch_mlp_infer(params, X, nvis, nullptr, skip, logit_tau, st));
+            CKR(cudaMemsetAsync(cnt + 7, 0, sizeof(int), st));
+            CKR(launch_mask_table(d_tab_outer, skip, nvis, d_tab_mask, cnt + 7, st));
+            CKR(cudaMemcpyAsync(prev_skip, skip, nvis, cudaMemcpyDeviceToDevice, st));
+            stats.launches += 2;
+            if (!gm.exec) {
+                if (capture_pairs(d_tab_mask, d_visit, full_n, full_off, outer.data(), &gm.graph, &mask_launches) !=
+                    cudaSuccess)
+                    return HSVD_ERR_CUDA;
+                CKR(cudaGraphInstantiate(&gm.exec, gm.graph, 0));
+            }
+            CKR(evs.record_now(evr + 2, st));
+            CKR(cudaGraphLaunch(gm.exec, st));
+            CKR(evs.record_now(evr + 3, st));
+            CKR(cudaStreamSynchronize(st));
+            stats.launches += mask_launches;
+            stats.pair_visits += h_cnt[7];
+            stats.masked_sweeps += 1;
+            add_profile(full_n, false);
+        } else if (masked) {
             CKR(launch_mlp_infer(params, X, nvis, nullptr, skip, logit_tau, st));
             CKR(cudaMemcpyAsync(h_skip, skip, nvis, cudaMemcpyDeviceToHost, st));
             CKR(cudaMemcpyAsync(prev_skip, skip, nvis, cudaMemcpyDeviceToDevice, st));

@@ -35,6 +35,7 @@ k_gram(const double *__restrict__ G, int64_t rows, int64_t ldg, int npairs,
     const int pair = idx / (3 * nsplit);
     const int x0 = col0[2 * pair + (blk == 2 ? 1 : 0)];
     const int y0 = col0[2 * pair + (blk >= 1 ? 1 : 0)];
+    if (x0 < 0) return;  // a visit the skip mask removed
     const int64_t r0 = (int64_t)split * rows_per;
     const int64_t r1 = min(rows, r0 + rows_per);
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;

@@ -177,6 +177,8 @@ cudaError_t launch_features(const float *trace, const int8_t *prev_skip, const i
 cudaError_t launch_mlp_infer(const float *params, const float *X, int n, float *logits, int8_t *skip,
                              float logit_tau, cudaStream_t st);
 cudaError_t launch_export(const float *X, const float *trace, int nvis, float *out, cudaStream_t st);
+// visit table of a masked sweep: skipped visits become (-1, -1)
+cudaError_t launch_mask_table(const int *outer, const int8_t *skip, int nvis, int *tab, int *kept, cudaStream_t st);
 cudaError_t launch_assemble(int b, int npairs, const double *part, int nsplit, double *A, cudaStream_t st);
 cudaError_t launch_update(double *X, int64_t rows, int64_t ldx, double *Y, int64_t rowsY,
                           int64_t ldy, int b, int npairs, const int *col0, const double *Wp,

@@ -230,6 +230,21 @@ __global__ void k_export(const float *__restrict__ X, const float *__restrict__ 
     out[(size_t)v * (kF + 1) + kF] = trace[(size_t)v * HSVD_TRACE_FIELDS + 2] > 0.0f ? 1.0f : 0.0f;
 }
 
+// the visit table of a masked sweep under the pair schedule: a skipped visit's
+// entry becomes (-1, -1), which the Gram and inner-solve kernels treat as "no
+// visit"; *kept counts the visits that stay
+__global__ void k_mask_table(const int *__restrict__ outer, const int8_t *__restrict__ skip, int nvis,
+                             int *__restrict__ tab, int *__restrict__ kept) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool keep = v < nvis && !skip[v];
+    if (v < nvis) {
+        tab[2 * v] = keep ? outer[2 * v] : -1;
+        tab[2 * v + 1] = keep ? outer[2 * v + 1] : -1;
+    }
+    const unsigned n = __popc(__ballot_sync(0xffffffffu, keep));
+    if ((threadIdx.x & 31) == 0 && n) atomicAdd(kept, (int)n);
+}
+
 size_t grad_smem() {
     return sizeof(float) * (kParams + kTrainSamples * kF + 4 * kTrainSamples * kH + 2 * kTrainSamples);
 }
@@ -246,6 +261,11 @@ cudaError_t launch_mlp_infer(const float *params, const float *X, int n, float *
                              float logit_tau, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     k_mlp_infer<<<(n + 127) / 128, 128, 0, st>>>(params, X, n, logits, skip, logit_tau);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mask_table(const int *outer, const int8_t *skip, int nvis, int *tab, int *kept, cudaStream_t st) {
+    k_mask_table<<<(nvis + 127) / 128, 128, 0, st>>>(outer, skip, nvis, tab, kept);
     return cudaGetLastError();
 }
 

@@ -71,6 +71,10 @@ k_solve_cluster(const double *__restrict__ part, int nsplit, int full_part, doub
     const int row0 = rank * R;
     const int tid = threadIdx.x;
 
+    if (col0 && col0[2 * pair] < 0) {  // a visit the skip mask removed: the whole cluster leaves
+        if (rank == 0 && tid == 0) rotated[pair] = 0;
+        return;
+    }
     extern __shared__ __align__(16) double sm[];
     double *Sa = sm;               // [R][LD] stored rows (current or receive)
     double *Sb = Sa + R * LD;      // [R][LD]
@@ -336,6 +340,10 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
     const int tid = threadIdx.x;
     const int k0 = rank * P;        // first pair owned
     const int w0 = rank * RW;       // first row of W owned
+    if (col0 && col0[2 * pair] < 0) {  // a visit the skip mask removed: the whole cluster leaves
+        if (rank == 0 && tid == 0) rotated[pair] = 0;
+        return;
+    }
 
     extern __shared__ __align__(16) double sm[];
     double *fix = sm;                 // [P][NN]    rows k0 .. k0 + P - 1

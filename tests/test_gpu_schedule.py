@@ -66,6 +66,31 @@ def test_schedules_with_learned_form_and_trace(api):
     assert rows[0].shape == rows[1].shape and torch.equal(rows[0], rows[1])
 
 
+def test_schedules_with_a_partial_skip_mask(api):
+    """A network that keeps some visits and skips others: under the pair
+    schedule the mask stays on the device (skipped visits become empty
+    kernels of one fixed graph), under the step schedule the host compacts
+    the visit table.  Same visits kept, same bits, same counts."""
+    G, J = W.graded(384, seed=64)
+    rng = np.random.default_rng(65)
+    p = torch.from_numpy((rng.standard_normal(api.HSVD_MLP_PARAMS) * 0.6).astype(np.float32)).cuda()
+    kw = dict(method=api.HSVD_METHOD_BLOCKED, block_w=16, sort=False, max_sweeps=80, skip_model=p)
+    a = _run(api, G, J, schedule=api.HSVD_SCHEDULE_STEPS, **kw)
+    q = _run(api, G, J, schedule=api.HSVD_SCHEDULE_PAIRS, **kw)
+    plain = _run(api, G, J, method=api.HSVD_METHOD_BLOCKED, block_w=16, sort=False, max_sweeps=80)
+    assert a.status == q.status == api.HSVD_OK
+    assert (a.sweeps, a.masked_sweeps, a.judge_sweeps, a.pair_visits) == \
+        (q.sweeps, q.masked_sweeps, q.judge_sweeps, q.pair_visits)
+    nvis = (384 // 16) * (384 // 32)
+    masked_visits = a.pair_visits - (a.sweeps - a.masked_sweeps) * nvis
+    assert 0 < masked_visits < a.masked_sweeps * nvis  # the mask kept some visits and skipped others
+    assert torch.equal(a.sigma, q.sigma) and torch.equal(a.V, q.V)
+    s, r = q.sigma.cpu().numpy(), plain.sigma.cpu().numpy()
+    for sg in (1, -1):
+        x, y = np.sort(s[J == sg]), np.sort(r[J == sg])
+        assert np.max(np.abs(x - y) / y) <= 1e-12
+
+
 def test_pair_schedule_profile_and_early_stop(api):
     """Profiling under the pair schedule reports the sweeps' total only; the
     early stop behaves as under the step schedule."""
