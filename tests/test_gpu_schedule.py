@@ -71,9 +71,17 @@ def test_schedules_with_a_partial_skip_mask(api):
     schedule the mask stays on the device (skipped visits become empty
     kernels of one fixed graph), under the step schedule the host compacts
     the visit table.  Same visits kept, same bits, same counts."""
+    from oracle import mlp as M
+
     G, J = W.graded(384, seed=64)
-    rng = np.random.default_rng(65)
-    p = torch.from_numpy((rng.standard_normal(api.HSVD_MLP_PARAMS) * 0.6).astype(np.float32)).cuda()
+    # logit = 200 relu(f0) - 1, f0 = log2(max scaled |a_ij| / tol) / 64 from the
+    # visit's last record: keep a visit whose block failed the test last time
+    w = np.zeros(M.PARAMS, dtype=np.float32)
+    w[M.OFF_W1 + 0] = 1.0
+    w[M.OFF_W2 + 0] = 1.0
+    w[M.OFF_W3 + 0] = 200.0
+    w[M.OFF_B3] = -1.0
+    p = torch.from_numpy(w).cuda()
     kw = dict(method=api.HSVD_METHOD_BLOCKED, block_w=16, sort=False, max_sweeps=80, skip_model=p)
     a = _run(api, G, J, schedule=api.HSVD_SCHEDULE_STEPS, **kw)
     q = _run(api, G, J, schedule=api.HSVD_SCHEDULE_PAIRS, **kw)
