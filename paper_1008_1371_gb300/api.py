@@ -38,6 +38,9 @@ HSVD_STOP_TANGENT = 2
 HSVD_SCHEDULE_AUTO = 0
 HSVD_SCHEDULE_STEPS = 1
 HSVD_SCHEDULE_PAIRS = 2
+HSVD_SHORTEN_AUTO = 0
+HSVD_SHORTEN_NEVER = 1
+HSVD_SHORTEN_ALWAYS = 2
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libhsvd.so")
@@ -59,7 +62,7 @@ class HsvdOpts(ctypes.Structure):
     _fields_ = [("tol", _dbl), ("max_sweeps", _int), ("method", _int), ("block_w", _int),
                 ("inner_mode", _int), ("inner_max_passes", _int), ("sort", _int), ("profile", _int),
                 ("precision", _int), ("skip_model", _p), ("skip_tau", _dbl), ("trace_out", _p),
-                ("trace_cap", _i64), ("tstop", _dbl), ("schedule", _int), ("reserved", _int * 3)]
+                ("trace_cap", _i64), ("tstop", _dbl), ("schedule", _int), ("shorten", _int), ("reserved", _int * 2)]
 
 
 class HsvdInfo(ctypes.Structure):
@@ -67,7 +70,7 @@ class HsvdInfo(ctypes.Structure):
                 ("rotations", _i64), ("pair_updates", _i64), ("kernel_launches", _i64),
                 ("ms_gram", _dbl), ("ms_solve", _dbl), ("ms_update", _dbl), ("ms_other", _dbl),
                 ("pair_visits", _i64), ("masked_sweeps", _int), ("judge_sweeps", _int), ("trace_rows", _i64),
-                ("stop_rule", _int)]
+                ("stop_rule", _int), ("shortened", _int)]
 
 
 class HsvdBatchOpts(ctypes.Structure):
@@ -107,6 +110,8 @@ def lib():
             L.hsvd_solve_ex.restype = _int
             L.hsvd_modulus_pairs.argtypes = [_int, _int, _p]
             L.hsvd_modulus_pairs.restype = _int
+            L.hsvd_shorten_qr.argtypes = [_p, _i64, _i64, _i64, _p, _i64, _p, _i64, _p]
+            L.hsvd_shorten_qr.restype = _int
             L.hsvd_pivot_gram.argtypes = [_p, _i64, _i64, _int, _int, _p, _p, _p]
             L.hsvd_pivot_gram.restype = _int
             L.hsvd_pivot_solve.argtypes = [_int, _int, _p, _p, _dbl, _int, _int, _p, _p, _p, _p]
@@ -182,6 +187,7 @@ class HsvdResult:
     judge_sweeps: int = 0
     trace_rows: int = 0
     stop_rule: int = HSVD_STOP_NONE
+    shortened: int = 0
 
 
 HSVD_SORT_AUTO = -1
@@ -189,7 +195,7 @@ HSVD_SORT_AUTO = -1
 
 def make_opts(tol=0.0, max_sweeps=30, method=HSVD_METHOD_AUTO, block_w=0, inner_mode=HSVD_INNER_ORIENTED,
               inner_max_passes=8, sort=None, profile=False, precision=HSVD_PRECISION_FP64, skip_model=None,
-              skip_tau=0.0, trace_out=None, tstop=0.0, schedule=HSVD_SCHEDULE_AUTO):
+              skip_tau=0.0, trace_out=None, tstop=0.0, schedule=HSVD_SCHEDULE_AUTO, shorten=HSVD_SHORTEN_AUTO):
     """Options record; ``sort=None`` lets the library choose (sorting for the
     pointwise method only).  ``tstop``: tangent threshold of the early stop
     (0 = off, negative = HSVD_TSTOP_PAPER).  ``skip_model``: a float32 tensor of
@@ -220,6 +226,7 @@ def make_opts(tol=0.0, max_sweeps=30, method=HSVD_METHOD_AUTO, block_w=0, inner_
         o.trace_cap = trace_out.shape[0]
     o.tstop = float(tstop)
     o.schedule = int(schedule)
+    o.shorten = int(shorten)
     return o
 
 
@@ -256,7 +263,8 @@ def hsvd_solve_ex(G, J, opts=None, compute_u=True, compute_v=True, stream=None, 
         raise HsvdError(st)
     return HsvdResult(sigma, U, V, info.sweeps, st, info.method, info.block_w, info.rotations, info.pair_updates,
                       info.kernel_launches, info.ms_gram, info.ms_solve, info.ms_update, info.ms_other,
-                      info.pair_visits, info.masked_sweeps, info.judge_sweeps, info.trace_rows, info.stop_rule)
+                      info.pair_visits, info.masked_sweeps, info.judge_sweeps, info.trace_rows, info.stop_rule,
+                      info.shortened)
 
 
 def hsvd_solve(G, J, tol=0.0, max_sweeps=30, compute_u=True, compute_v=True, stream=None, check=True):
@@ -274,6 +282,22 @@ def hsvd_modulus_pairs(r, nsteps=None):
     if st != HSVD_OK:
         raise HsvdError(st)
     return out
+
+
+def hsvd_shorten_qr(G, want_q=True, stream=None):
+    """(R, Q) of the shortening QR of a CUDA float64 tensor G (m x n, m >= n);
+    Q is None unless want_q."""
+    L = lib()
+    Gc = _colmajor(G, torch.float64)
+    m, n = Gc.shape
+    R = _empty_colmajor(n, n, Gc)
+    Q = _empty_colmajor(m, n, Gc) if want_q else None
+    st = L.hsvd_shorten_qr(Gc.data_ptr(), m, n, Gc.stride(1) if n > 1 else m, R.data_ptr(), R.stride(1) if n > 1 else n,
+                           Q.data_ptr() if Q is not None else None, (Q.stride(1) if n > 1 else m) if Q is not None else m,
+                           _stream_ptr(stream, Gc.device))
+    if st != HSVD_OK:
+        raise HsvdError(st)
+    return R, Q
 
 
 def hsvd_pivot_gram(G, b, col0, stream=None):

@@ -621,6 +621,39 @@ int solve_pointwise(const double *G, int64_t m, int64_t n, int64_t ldg, const in
     return h_out[0];
 }
 
+// Shortening (Sec. 1): G = Q R, the HSVD of R (n x n) by the chosen method,
+// U = Q [U_R; 0].  V and sigma are R's.
+int solve_shortened(const double *G, int64_t m, int64_t n, int64_t ldg, const int8_t *J, double *sigma, double *U,
+                    int64_t ldu, double *V, int64_t ldv, const hsvd_opts &o, double tol, int method, int b,
+                    hsvd_info *info, cudaStream_t st) {
+    Ws ws(st);
+    double *A = ws.get<double>((size_t)m * n);  // QR in place on a copy: G is read-only
+    double *R = ws.get<double>((size_t)n * n);
+    double *UR = U ? ws.get<double>((size_t)n * n) : nullptr;
+    double *qws = ws.get<double>(qr_workspace_doubles(n));
+    if (!A || !R || (U && !UR) || !qws) return HSVD_ERR_NOMEM;
+    long long nl = 0;
+    CKR(cudaMemcpy2DAsync(A, sizeof(double) * m, G, sizeof(double) * ldg, sizeof(double) * m, n,
+                          cudaMemcpyDeviceToDevice, st));
+    CKR(qr_factor(A, m, m, n, qws, st, &nl));
+    CKR(qr_extract_r(A, m, n, R, n, st));
+    nl += 1;
+    const int rc = method == HSVD_METHOD_POINTWISE
+                       ? solve_pointwise(R, n, n, n, J, sigma, UR, n, V, ldv, o, tol, info, st)
+                       : solve_blocked(R, n, n, n, J, sigma, UR, n, V, ldv, o, tol, b, info, st);
+    if ((rc == HSVD_OK || rc == HSVD_NOT_CONVERGED) && U) {
+        CKR(qr_embed_u(UR, n, m, n, U, ldu, st));
+        CKR(qr_apply_q(A, m, m, n, qws, U, ldu, st, &nl));
+        nl += 1;
+    }
+    CKR(cudaStreamSynchronize(st));
+    if (info) {
+        info->shortened = 1;
+        info->kernel_launches += nl;
+    }
+    return rc;
+}
+
 int validate(const double *G, int64_t m, int64_t n, int64_t ldg, const int8_t *J, const double *sigma, int64_t ldu,
              const double *U, int64_t ldv, const double *V) {
     if (!G || !J || !sigma) return HSVD_ERR_ARG;
@@ -674,9 +707,10 @@ int hsvd_solve_ex(const double *G, int64_t m, int64_t n, int64_t ldg, const int8
     if (info) memset(info, 0, sizeof *info);
     int rc = validate(G, m, n, ldg, J, sigma, ldu, U, ldv, V);
     if (rc == HSVD_OK) {
-        for (int i = 0; i < 3; ++i)
+        for (int i = 0; i < 2; ++i)
             if (o.reserved[i]) rc = HSVD_ERR_ARG;
         if (o.schedule < HSVD_SCHEDULE_AUTO || o.schedule > HSVD_SCHEDULE_PAIRS) rc = HSVD_ERR_ARG;
+        if (o.shorten < HSVD_SHORTEN_AUTO || o.shorten > HSVD_SHORTEN_ALWAYS) rc = HSVD_ERR_ARG;
         if (o.tstop < 0.0) o.tstop = HSVD_TSTOP_PAPER;
         if (!(o.tstop >= 0.0 && o.tstop <= 1.0)) rc = HSVD_ERR_ARG;
         if (o.max_sweeps <= 0) o.max_sweeps = 30;
@@ -707,10 +741,14 @@ int hsvd_solve_ex(const double *G, int64_t m, int64_t n, int64_t ldg, const int8
             if (info) info->status = HSVD_ERR_ARG;
             return HSVD_ERR_ARG;
         }
+    // a tall factor is shortened first; the method is then chosen for the square R
+    const bool shorten =
+        m > n && (o.shorten == HSVD_SHORTEN_ALWAYS || (o.shorten == HSVD_SHORTEN_AUTO && 4 * m >= 5 * n));
+    const int64_t m_eff = shorten ? n : m;
     int method = o.method;
     if (method == HSVD_METHOD_AUTO)
-        method = (pointwise_fits(m, n) && o.precision == HSVD_PRECISION_FP64) ? HSVD_METHOD_POINTWISE
-                                                                              : HSVD_METHOD_BLOCKED;
+        method = (pointwise_fits(m_eff, n) && o.precision == HSVD_PRECISION_FP64) ? HSVD_METHOD_POINTWISE
+                                                                                  : HSVD_METHOD_BLOCKED;
     // diagonal sorting pays for the pointwise method (Sec. 5, Table 5.3) and for
     // the split-precision form (measured: Haar 4096, 2269 -> 2085 ms; Haar 1024,
     // 211 -> 197 ms), but costs sweeps in the FP64 blocked one (graded 1024:
@@ -727,7 +765,7 @@ int hsvd_solve_ex(const double *G, int64_t m, int64_t n, int64_t ldg, const int8
         if (info) info->status = HSVD_ERR_ARG;
         return HSVD_ERR_ARG;
     }
-    if (method == HSVD_METHOD_POINTWISE && !pointwise_fits(m, n)) {
+    if (method == HSVD_METHOD_POINTWISE && !pointwise_fits(m_eff, n)) {
         if (info) info->status = HSVD_ERR_ARG;
         return HSVD_ERR_ARG;
     }
@@ -768,7 +806,9 @@ int hsvd_solve_ex(const double *G, int64_t m, int64_t n, int64_t ldg, const int8
         double *u = dev ? U : dU;
         double *v = dev ? V : dV;
         const int64_t lg = dev ? ldg : m, lu = dev ? ldu : m, lv = dev ? ldv : n;
-        if (method == HSVD_METHOD_POINTWISE)
+        if (shorten)
+            rc = solve_shortened(g, m, n, lg, j, s, u, lu, v, lv, o, tol, method, b, info, st);
+        else if (method == HSVD_METHOD_POINTWISE)
             rc = solve_pointwise(g, m, n, lg, j, s, u, lu, v, lv, o, tol, info, st);
         else
             rc = solve_blocked(g, m, n, lg, j, s, u, lu, v, lv, o, tol, b, info, st);
@@ -803,6 +843,39 @@ int hsvd_solve(const double *G, int64_t m, int64_t n, int64_t ldg, const int8_t 
     hsvd_info info;
     const int rc = hsvd_solve_ex(G, m, n, ldg, J, sigma, U, ldu, V, ldv, &o, &info, stream);
     if (sweeps) *sweeps = info.sweeps;
+    return rc;
+}
+
+int hsvd_shorten_qr(const double *G, int64_t m, int64_t n, int64_t ldg, double *R, int64_t ldr, double *Q,
+                    int64_t ldq, void *stream) {
+    if (!G || !R || n < 1 || m < n || ldg < m || ldr < n || (Q && ldq < m)) return HSVD_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = HSVD_OK;
+    {
+        Ws ws(st);
+        double *A = ws.get<double>((size_t)m * n);
+        double *qws = ws.get<double>(qr_workspace_doubles(n));
+        double *I = Q ? ws.get<double>((size_t)n * n) : nullptr;
+        long long nl = 0;
+        if (!A || !qws || (Q && !I)) {
+            rc = HSVD_ERR_NOMEM;
+        } else if (cudaMemcpy2DAsync(A, sizeof(double) * m, G, sizeof(double) * ldg, sizeof(double) * m, n,
+                                     cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+                   qr_factor(A, m, m, n, qws, st, &nl) != cudaSuccess ||
+                   qr_extract_r(A, m, n, R, ldr, st) != cudaSuccess) {
+            rc = HSVD_ERR_CUDA;
+        } else if (Q) {
+            // Q = Q [I; 0]: the identity embedded, then the reflectors applied
+            std::vector<double> eye((size_t)n * n, 0.0);
+            for (int64_t i = 0; i < n; ++i) eye[(size_t)(i + i * n)] = 1.0;
+            if (cudaMemcpyAsync(I, eye.data(), sizeof(double) * n * n, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+                qr_embed_u(I, n, m, n, Q, ldq, st) != cudaSuccess ||
+                qr_apply_q(A, m, m, n, qws, Q, ldq, st, &nl) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess)
+                rc = HSVD_ERR_CUDA;
+        }
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess && rc == HSVD_OK) rc = HSVD_ERR_CUDA;
     return rc;
 }
 

@@ -171,6 +171,18 @@ cudaError_t launch_solve(int b, int npairs, const double *part, int nsplit, doub
                          int full_part = 0, int *dexp = nullptr, const int *visit = nullptr,
                          float *trace = nullptr, double tstop = 0.0, int *tbig = nullptr);
 
+// qr.cu: the shortening front end (Householder QR of a tall factor)
+size_t qr_workspace_doubles(int64_t n);
+// A <- R (upper triangle) and the reflectors (below); ws: qr_workspace_doubles(n)
+cudaError_t qr_factor(double *A, int64_t lda, int64_t m, int64_t n, double *ws, cudaStream_t st,
+                      long long *launches);
+// U (m x n) <- Q U, Q from the reflectors in A and the T factors in ws
+cudaError_t qr_apply_q(double *A, int64_t lda, int64_t m, int64_t n, double *ws, double *U, int64_t ldu,
+                       cudaStream_t st, long long *launches);
+cudaError_t qr_extract_r(const double *A, int64_t lda, int64_t n, double *R, int64_t ldr, cudaStream_t st);
+cudaError_t qr_embed_u(const double *UR, int64_t ldur, int64_t m, int64_t n, double *U, int64_t ldu,
+                       cudaStream_t st);
+
 // learned form (learned.cu)
 cudaError_t launch_features(const float *trace, const int8_t *prev_skip, const int *tab, int nvis, int b, int nb,
                             int sweep, int max_sweeps, double tol, float *X, cudaStream_t st);

@@ -1,0 +1,371 @@
+// qr.cu -- the shortening front end for tall factors (Sec. 1): G = Q R by
+// Householder reflections, the HSVD of the square R, and U = Q [U_R; 0].
+// R V = U_R Sigma gives G V = Q R V = (Q [U_R; 0]) Sigma with the same J-unitary
+// V, and Householder QR is column-wise backward stable, so relative accuracy
+// for column-scaled factors carries over.  One sweep of the blocked method on
+// the m x n factor costs 2 n^2 (4m + 2n) flops, on R 12 n^3; the QR and the
+// application of Q cost about 4 m n^2 once.
+//
+// Blocked QR with panels of width kQB (compact WY form, H_1 ... H_w =
+// I - V T V^T, T upper triangular):
+//   k_qr_panel   factors one panel column by column (reflector as in LAPACK's
+//                dlarfg: beta = -sign(alpha) ||x||, tau = (beta - alpha) / beta,
+//                v = x / (alpha - beta) below the unit diagonal).  One CTA.
+//   k_qr_vtc     partial products V^T C over row splits (C: the trailing
+//                columns, V itself for T, or U when Q is applied).
+//   k_qr_tbuild  T from tau and V^T V (T_jj = tau_j,
+//                T_{0:j,j} = -tau_j T_{0:j,0:j} V_{:,0:j}^T v_j).  One warp.
+//   k_qr_tz      Z = op(T) (sum of the partials): op = T^T for the
+//                factorisation (Q^T C), T for applying Q.
+//   k_qr_update  C -= V Z.
+// Every product is an FP64 FMA chain (the library is compiled without
+// floating-point contraction).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "hsvd_internal.cuh"
+
+namespace hsvd {
+namespace {
+
+constexpr int kQB = 32;         // panel width
+constexpr int kPanelThreads = 256;
+constexpr int kVtcThreads = 256;
+constexpr int kVtcRows = 32;    // rows per shared-memory slice
+
+// V's entry (i, a) for the panel starting at column j0: zero above the
+// diagonal, one on it, the stored reflector below
+__device__ __forceinline__ double v_entry(const double *__restrict__ A, int64_t lda, int64_t i, int j0, int a) {
+    const int64_t d = (int64_t)j0 + a;
+    if (i < d) return 0.0;
+    if (i == d) return 1.0;
+    return A[i + d * lda];
+}
+
+// One CTA factors columns j0 .. j0 + w - 1 of A over rows j0 .. m - 1.  For
+// column j: one pass forms x^T x and x^T a_c over the rows below j for the
+// later panel columns c, a block reduction gives beta, tau and w_c = v^T a_c,
+// and a second pass stores v and updates the later columns.
+__global__ void __launch_bounds__(kPanelThreads)
+k_qr_panel(double *__restrict__ A, int64_t lda, int64_t m, int j0, int w, double *__restrict__ tau) {
+    __shared__ double red[kPanelThreads / 32][kQB];
+    __shared__ double sw[kQB];   // w_c of the current column
+    __shared__ double s_scale, s_tau;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int jj = 0; jj < w; ++jj) {
+        const int64_t j = (int64_t)j0 + jj;
+        const double *x = A + j * lda;
+        // pass A: acc[0] = sum x_i^2, acc[c] = sum x_i a_{i, j + c} (rows i > j)
+        double acc[kQB];
+#pragma unroll
+        for (int c = 0; c < kQB; ++c) acc[c] = 0.0;
+        for (int64_t i = j + 1 + tid; i < m; i += kPanelThreads) {
+            const double xi = x[i];
+            acc[0] = fma(xi, xi, acc[0]);
+#pragma unroll
+            for (int c = 1; c < kQB; ++c)
+                if (jj + c < w) acc[c] = fma(xi, A[i + (j + c) * lda], acc[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < kQB; ++c) {
+            double v = acc[c];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) red[warp][c] = v;
+        }
+        __syncthreads();
+        if (tid < kQB) {
+            double s = 0.0;
+            for (int q = 0; q < kPanelThreads / 32; ++q) s += red[q][tid];
+            red[0][tid] = s;  // warp 0's row is read only below, after the barrier
+        }
+        __syncthreads();
+        if (tid == 0) {
+            const double alpha = x[j], xnorm2 = red[0][0];
+            double t = 0.0, scale = 0.0, beta = alpha;
+            if (xnorm2 > 0.0) {
+                beta = -copysign(sqrt(fma(alpha, alpha, xnorm2)), alpha);
+                t = (beta - alpha) / beta;
+                scale = 1.0 / (alpha - beta);
+            }
+            s_tau = t;
+            s_scale = scale;
+            tau[j] = t;
+            A[j + j * lda] = beta;
+        }
+        __syncthreads();
+        const double t = s_tau, scale = s_scale;
+        if (tid > 0 && tid < kQB && jj + tid < w) {
+            const int c = tid;  // w_c = a_{j, j+c} + scale * sum_{i>j} x_i a_{i, j+c}
+            sw[c] = fma(scale, red[0][c], A[j + (j + c) * lda]);
+        }
+        __syncthreads();
+        // pass B: v below the diagonal, then a_c -= tau w_c v for the later columns
+        double *xm = A + j * lda;
+        for (int64_t i = j + 1 + tid; i < m; i += kPanelThreads) {
+            const double vi = xm[i] * scale;
+            xm[i] = vi;
+            for (int c = 1; jj + c < w; ++c) {
+                double *ac = A + (j + c) * lda;
+                ac[i] = fma(-t * sw[c], vi, ac[i]);
+            }
+        }
+        if (tid > 0 && jj + tid < w) {  // row j: v_j = 1
+            double *ac = A + (j + tid) * lda;
+            ac[j] = fma(-t, sw[tid], ac[j]);
+        }
+        __syncthreads();
+    }
+}
+
+// part[s][a][c] = sum over the rows of split s (from j0 on) of V(i, a) C(i, c0 + c),
+// a < w, c < ncols; C is V itself (c_is_v) or a plain matrix.
+__global__ void __launch_bounds__(kVtcThreads)
+k_qr_vtc(const double *__restrict__ A, int64_t lda, int64_t m, int j0, int w, const double *__restrict__ C,
+         int64_t ldc, int c0, int ncols, int c_is_v, int nsplit, int64_t rows_per, double *__restrict__ part) {
+    __shared__ double Vs[kVtcRows][kQB + 1];
+    __shared__ double Cs[kVtcRows][kQB + 1];
+    const int tile = blockIdx.x, split = blockIdx.y;
+    const int ct0 = tile * kQB;
+    const int64_t r0 = (int64_t)j0 + (int64_t)split * rows_per;
+    const int64_t r1 = m < r0 + rows_per ? m : r0 + rows_per;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+    for (int64_t rb = r0; rb < r1; rb += kVtcRows) {
+        for (int e = tid; e < kVtcRows * kQB; e += kVtcThreads) {
+            const int rr = e % kVtcRows, k = e / kVtcRows;
+            const int64_t i = rb + rr;
+            const bool in = i < r1;
+            Vs[rr][k] = (in && k < w) ? v_entry(A, lda, i, j0, k) : 0.0;
+            const int c = ct0 + k;
+            double cv = 0.0;
+            if (in && c < ncols) cv = c_is_v ? v_entry(A, lda, i, j0, c) : C[i + (int64_t)(c0 + c) * ldc];
+            Cs[rr][k] = cv;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int rr = 0; rr < kVtcRows; ++rr) {
+            const double v0 = Vs[rr][ty], v1 = Vs[rr][ty + 16];
+            const double x0 = Cs[rr][tx], x1 = Cs[rr][tx + 16];
+            acc[0][0] = fma(v0, x0, acc[0][0]);
+            acc[0][1] = fma(v0, x1, acc[0][1]);
+            acc[1][0] = fma(v1, x0, acc[1][0]);
+            acc[1][1] = fma(v1, x1, acc[1][1]);
+        }
+        __syncthreads();
+    }
+    double *pp = part + (size_t)split * kQB * ncols;
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+            const int a = ty + 16 * u, c = ct0 + tx + 16 * v;
+            if (a < w && c < ncols) pp[(size_t)a * ncols + c] = acc[u][v];
+        }
+}
+
+// T of the panel from tau and Y = V^T V (the sum of the partials), one warp:
+// lane r holds row r of T; column j is formed from column j of Y.
+__global__ void k_qr_tbuild(const double *__restrict__ part, int nsplit, int w, const double *__restrict__ tau_j0,
+                            double *__restrict__ T) {
+    __shared__ double Ts[kQB][kQB + 1];
+    __shared__ double y[kQB];
+    const int r = threadIdx.x;
+    for (int c = 0; c < kQB; ++c) Ts[r][c] = 0.0;
+    __syncwarp();
+    for (int j = 0; j < w; ++j) {
+        // y_r = v_r^T v_j for r < j
+        if (r < j) {
+            double s = 0.0;
+            for (int q = 0; q < nsplit; ++q) s += part[(size_t)q * kQB * w + (size_t)r * w + j];
+            y[r] = s;
+        }
+        __syncwarp();
+        const double tj = tau_j0[j];
+        if (r < j) {  // T_{r,j} = -tau_j sum_{k=r}^{j-1} T_{r,k} y_k
+            double s = 0.0;
+            for (int k = r; k < j; ++k) s = fma(Ts[r][k], y[k], s);
+            Ts[r][j] = -tj * s;
+        }
+        if (r == j) Ts[r][j] = tj;
+        __syncwarp();
+    }
+    for (int c = 0; c < kQB; ++c) T[r * kQB + c] = Ts[r][c];
+}
+
+// Z[a][c] = sum_b op(T)[a][b] X[b][c], X the sum of the partials; op = T^T
+// when trans (the factorisation applies H^T), T otherwise (Q applied).
+__global__ void k_qr_tz(const double *__restrict__ part, int nsplit, int w, int ncols, const double *__restrict__ T,
+                        int trans, double *__restrict__ Z) {
+    __shared__ double Xs[kQB][kQB + 1];
+    __shared__ double Ts[kQB][kQB + 1];
+    const int ct0 = blockIdx.x * kQB, tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+    for (int a = ty; a < kQB; a += 8) {
+        const int c = ct0 + tx;
+        double s = 0.0;
+        if (a < w && c < ncols)
+            for (int q = 0; q < nsplit; ++q) s += part[(size_t)q * kQB * ncols + (size_t)a * ncols + c];
+        Xs[a][tx] = s;
+        Ts[a][tx] = T[a * kQB + tx];
+    }
+    __syncthreads();
+    for (int a = ty; a < w; a += 8) {
+        const int c = ct0 + tx;
+        if (c >= ncols) continue;
+        double s = 0.0;
+        for (int b = 0; b < w; ++b) s = fma(trans ? Ts[b][a] : Ts[a][b], Xs[b][tx], s);
+        Z[(size_t)a * ncols + c] = s;
+    }
+}
+
+// C(i, c0 + c) -= sum_a V(i, a) Z[a][c] for rows i >= j0; one CTA per (row
+// chunk of 64, column tile of 32)
+__global__ void __launch_bounds__(256)
+k_qr_update(double *__restrict__ C, int64_t ldc, int64_t m, int c0, int ncols, const double *__restrict__ A,
+            int64_t lda, int j0, int w, const double *__restrict__ Z) {
+    __shared__ double Vs[kQB][64];
+    __shared__ double Zs[kQB][kQB];
+    const int64_t r0 = (int64_t)j0 + (int64_t)blockIdx.x * 64;
+    const int ct0 = blockIdx.y * kQB;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < kQB * 64; e += 256) {
+        const int a = e / 64, rr = e % 64;
+        const int64_t i = r0 + rr;
+        Vs[a][rr] = (i < m && a < w) ? v_entry(A, lda, i, j0, a) : 0.0;
+    }
+    for (int e = tid; e < kQB * kQB; e += 256) {
+        const int a = e / kQB, c = e % kQB;
+        Zs[a][c] = (a < w && ct0 + c < ncols) ? Z[(size_t)a * ncols + ct0 + c] : 0.0;
+    }
+    __syncthreads();
+    const int rr = tid & 63, cg = tid >> 6;  // 64 rows x 4 column groups of 8
+    const int64_t i = r0 + rr;
+    if (i >= m) return;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int c = cg * 8 + k;
+        if (ct0 + c >= ncols) break;
+        double s = 0.0;
+        for (int a = 0; a < w; ++a) s = fma(Vs[a][rr], Zs[a][c], s);
+        double *p = C + i + (int64_t)(c0 + ct0 + c) * ldc;
+        *p -= s;
+    }
+}
+
+int qr_nsplit(int64_t rows) {
+    const int64_t s = (rows + 255) / 256;  // at least 256 rows per split
+    return (int)std::max<int64_t>(1, std::min<int64_t>(s, 64));
+}
+
+// Applies H_panel^T (trans) or H_panel to columns c0 .. c0 + ncols - 1 of C,
+// in chunks of kMaxCols columns (workspace: part, Z).
+constexpr int kMaxCols = 2048;
+cudaError_t apply_panel(double *A, int64_t lda, int64_t m, int j0, int w, const double *T, int trans, double *C,
+                        int64_t ldc, int c0, int ncols, double *part, double *Z, cudaStream_t st) {
+    const int64_t rows = m - j0;
+    const int nsplit = qr_nsplit(rows);
+    const int64_t rows_per = (rows + nsplit - 1) / nsplit;
+    for (int cb = 0; cb < ncols; cb += kMaxCols) {
+        const int nc = std::min(kMaxCols, ncols - cb);
+        const dim3 g1((nc + kQB - 1) / kQB, nsplit);
+        k_qr_vtc<<<g1, kVtcThreads, 0, st>>>(A, lda, m, j0, w, C, ldc, c0 + cb, nc, 0, nsplit, rows_per, part);
+        k_qr_tz<<<(nc + kQB - 1) / kQB, 256, 0, st>>>(part, nsplit, w, nc, T, trans, Z);
+        const dim3 g2((unsigned)((rows + 63) / 64), (nc + kQB - 1) / kQB);
+        k_qr_update<<<g2, 256, 0, st>>>(C, ldc, m, c0 + cb, nc, A, lda, j0, w, Z);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+size_t qr_workspace_doubles(int64_t n) {
+    const int64_t panels = (n + kQB - 1) / kQB;
+    return (size_t)panels * kQB * kQB            // T of every panel
+           + (size_t)n                            // tau
+           + (size_t)64 * kQB * kMaxCols          // partials
+           + (size_t)kQB * kMaxCols;              // Z
+}
+
+namespace {
+// R (n x n, ldr) <- the upper triangle of A, zeros below; U (m x n, ldu) <-
+// [U_R; 0] from U_R (n x n, ldur)
+__global__ void k_qr_extract_r(const double *__restrict__ A, int64_t lda, int64_t n, double *__restrict__ R,
+                               int64_t ldr) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * n) return;
+    const int64_t i = e % n, j = e / n;
+    R[i + j * ldr] = i <= j ? A[i + j * lda] : 0.0;
+}
+__global__ void k_qr_embed_u(const double *__restrict__ UR, int64_t ldur, int64_t m, int64_t n,
+                             double *__restrict__ U, int64_t ldu) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m * n) return;
+    const int64_t i = e % m, j = e / m;
+    U[i + j * ldu] = i < n ? UR[i + j * ldur] : 0.0;
+}
+}  // namespace
+
+cudaError_t qr_extract_r(const double *A, int64_t lda, int64_t n, double *R, int64_t ldr, cudaStream_t st) {
+    const int64_t total = n * n;
+    k_qr_extract_r<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(A, lda, n, R, ldr);
+    return cudaGetLastError();
+}
+
+cudaError_t qr_embed_u(const double *UR, int64_t ldur, int64_t m, int64_t n, double *U, int64_t ldu,
+                       cudaStream_t st) {
+    const int64_t total = m * n;
+    k_qr_embed_u<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(UR, ldur, m, n, U, ldu);
+    return cudaGetLastError();
+}
+
+// A (m x n, lda) <- R in the upper triangle and the reflectors below it; T of
+// every panel into ws.  m >= n.
+cudaError_t qr_factor(double *A, int64_t lda, int64_t m, int64_t n, double *ws, cudaStream_t st,
+                      long long *launches) {
+    const int64_t panels = (n + kQB - 1) / kQB;
+    double *Tall = ws, *tau = Tall + (size_t)panels * kQB * kQB;
+    double *part = tau + n, *Z = part + (size_t)64 * kQB * kMaxCols;
+    for (int64_t p = 0; p < panels; ++p) {
+        const int j0 = (int)(p * kQB), w = (int)std::min<int64_t>(kQB, n - j0);
+        double *T = Tall + (size_t)p * kQB * kQB;
+        k_qr_panel<<<1, kPanelThreads, 0, st>>>(A, lda, m, j0, w, tau);
+        // T from V^T V
+        const int64_t rows = m - j0;
+        const int nsplit = qr_nsplit(rows);
+        const int64_t rows_per = (rows + nsplit - 1) / nsplit;
+        k_qr_vtc<<<dim3(1, nsplit), kVtcThreads, 0, st>>>(A, lda, m, j0, w, nullptr, 0, 0, w, 1, nsplit, rows_per,
+                                                          part);
+        k_qr_tbuild<<<1, 32, 0, st>>>(part, nsplit, w, tau + j0, T);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        *launches += 3;
+        const int nt = (int)(n - j0 - w);
+        if (nt > 0) {
+            e = apply_panel(A, lda, m, j0, w, T, 1, A, lda, j0 + w, nt, part, Z, st);
+            if (e != cudaSuccess) return e;
+            *launches += 3 * ((nt + kMaxCols - 1) / kMaxCols);
+        }
+    }
+    return cudaSuccess;
+}
+
+// U (m x n, ldu) holds [U_R; 0] on entry; U <- Q U with the reflectors in A and
+// the T factors in ws (as left by qr_factor).
+cudaError_t qr_apply_q(double *A, int64_t lda, int64_t m, int64_t n, double *ws, double *U, int64_t ldu,
+                       cudaStream_t st, long long *launches) {
+    const int64_t panels = (n + kQB - 1) / kQB;
+    double *Tall = ws, *tau = Tall + (size_t)panels * kQB * kQB;
+    double *part = tau + n, *Z = part + (size_t)64 * kQB * kMaxCols;
+    for (int64_t p = panels - 1; p >= 0; --p) {
+        const int j0 = (int)(p * kQB), w = (int)std::min<int64_t>(kQB, n - j0);
+        const cudaError_t e = apply_panel(A, lda, m, j0, w, Tall + (size_t)p * kQB * kQB, 0, U, ldu, 0, (int)n,
+                                          part, Z, st);
+        if (e != cudaSuccess) return e;
+        *launches += 3 * ((n + kMaxCols - 1) / kMaxCols);
+    }
+    return cudaSuccess;
+}
+
+}  // namespace hsvd

@@ -180,3 +180,20 @@ def test_struct_layouts_match_header(api, tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(cls), cname
         for fname, _ in cls._fields_:
             assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
+
+
+def test_shorten_argument_errors_without_gpu(api):
+    L = api.lib()
+    G = np.zeros((6, 4))
+    J = np.ones(4, dtype=np.int8)
+    s = np.zeros(4)
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    info = api.HsvdInfo()
+    o = api.make_opts(shorten=3)
+    assert L.hsvd_solve_ex(p(G), 6, 4, 6, p(J), p(s), None, 6, None, 4, ctypes.byref(o), ctypes.byref(info),
+                           None) == api.HSVD_ERR_ARG
+    R = np.zeros((4, 4))
+    # m < n, ldg < m, ldr < n
+    assert L.hsvd_shorten_qr(p(G), 3, 4, 6, p(R), 4, None, 6, None) == api.HSVD_ERR_ARG
+    assert L.hsvd_shorten_qr(p(G), 6, 4, 5, p(R), 4, None, 6, None) == api.HSVD_ERR_ARG
+    assert L.hsvd_shorten_qr(p(G), 6, 4, 6, p(R), 3, None, 6, None) == api.HSVD_ERR_ARG
