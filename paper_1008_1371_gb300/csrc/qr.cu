@@ -14,7 +14,8 @@
 //   k_qr_vtc     partial products V^T C over row splits (C: the trailing
 //                columns, V itself for T, or U when Q is applied).
 //   k_qr_tbuild  T from tau and V^T V (T_jj = tau_j,
-//                T_{0:j,j} = -tau_j T_{0:j,0:j} V_{:,0:j}^T v_j).  One warp.
+//                T_{0:j,j} = -tau_j T_{0:j,0:j} V_{:,0:j}^T v_j): the partials
+//                summed by one thread per entry, the recurrence by one warp.
 //   k_qr_tz      Z = op(T) (sum of the partials): op = T^T for the
 //                factorisation (Q^T C), T for applying Q.
 //   k_qr_update  C -= V Z.
@@ -62,10 +63,14 @@ k_qr_panel(double *__restrict__ A, int64_t lda, int64_t m, int j0, int w, double
         for (int c = 0; c < kQB; ++c) acc[c] = 0.0;
         for (int64_t i = j + 1 + tid; i < m; i += kPanelThreads) {
             const double xi = x[i];
+            double val[kQB];
+#pragma unroll
+            for (int c = 1; c < kQB; ++c)
+                if (jj + c < w) val[c] = A[i + (j + c) * lda];
             acc[0] = fma(xi, xi, acc[0]);
 #pragma unroll
             for (int c = 1; c < kQB; ++c)
-                if (jj + c < w) acc[c] = fma(xi, A[i + (j + c) * lda], acc[c]);
+                if (jj + c < w) acc[c] = fma(xi, val[c], acc[c]);
         }
 #pragma unroll
         for (int c = 0; c < kQB; ++c) {
@@ -100,17 +105,21 @@ k_qr_panel(double *__restrict__ A, int64_t lda, int64_t m, int j0, int w, double
             sw[c] = fma(scale, red[0][c], A[j + (j + c) * lda]);
         }
         __syncthreads();
-        // pass B: v below the diagonal, then a_c -= tau w_c v for the later columns
+        // pass B: v below the diagonal, then a_c -= tau w_c v for the later
+        // columns; a row's loads are all issued before its stores
         double *xm = A + j * lda;
         for (int64_t i = j + 1 + tid; i < m; i += kPanelThreads) {
             const double vi = xm[i] * scale;
+            double val[kQB];
+#pragma unroll
+            for (int c = 1; c < kQB; ++c)
+                if (jj + c < w) val[c] = A[i + (j + c) * lda];
             xm[i] = vi;
-            for (int c = 1; jj + c < w; ++c) {
-                double *ac = A + (j + c) * lda;
-                ac[i] = fma(-t * sw[c], vi, ac[i]);
-            }
+#pragma unroll
+            for (int c = 1; c < kQB; ++c)
+                if (jj + c < w) A[i + (j + c) * lda] = fma(-t * sw[c], vi, val[c]);
         }
-        if (tid > 0 && jj + tid < w) {  // row j: v_j = 1
+        if (tid > 0 && tid < kQB && jj + tid < w) {  // row j: v_j = 1
             double *ac = A + (j + tid) * lda;
             ac[j] = fma(-t, sw[tid], ac[j]);
         }
@@ -166,25 +175,28 @@ k_qr_vtc(const double *__restrict__ A, int64_t lda, int64_t m, int j0, int w, co
 
 // T of the panel from tau and Y = V^T V (the sum of the partials), one warp:
 // lane r holds row r of T; column j is formed from column j of Y.
-__global__ void k_qr_tbuild(const double *__restrict__ part, int nsplit, int w, const double *__restrict__ tau_j0,
-                            double *__restrict__ T) {
+__global__ void __launch_bounds__(kQB * kQB)
+k_qr_tbuild(const double *__restrict__ part, int nsplit, int w, const double *__restrict__ tau_j0,
+            double *__restrict__ T) {
     __shared__ double Ts[kQB][kQB + 1];
-    __shared__ double y[kQB];
+    __shared__ double Y[kQB][kQB + 1];
+    // every entry of Y = V^T V (the sum of the partials) by its own thread
+    {
+        const int a = threadIdx.x / kQB, c = threadIdx.x % kQB;
+        double s = 0.0;
+        if (a < w && c < w)
+            for (int q = 0; q < nsplit; ++q) s += part[(size_t)q * kQB * w + (size_t)a * w + c];
+        Y[a][c] = s;
+        Ts[a][c] = 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x >= 32) return;
     const int r = threadIdx.x;
-    for (int c = 0; c < kQB; ++c) Ts[r][c] = 0.0;
-    __syncwarp();
     for (int j = 0; j < w; ++j) {
-        // y_r = v_r^T v_j for r < j
-        if (r < j) {
-            double s = 0.0;
-            for (int q = 0; q < nsplit; ++q) s += part[(size_t)q * kQB * w + (size_t)r * w + j];
-            y[r] = s;
-        }
-        __syncwarp();
         const double tj = tau_j0[j];
-        if (r < j) {  // T_{r,j} = -tau_j sum_{k=r}^{j-1} T_{r,k} y_k
+        if (r < j) {  // T_{r,j} = -tau_j sum_{k=r}^{j-1} T_{r,k} y_k, y_k = v_k^T v_j
             double s = 0.0;
-            for (int k = r; k < j; ++k) s = fma(Ts[r][k], y[k], s);
+            for (int k = r; k < j; ++k) s = fma(Ts[r][k], Y[k][j], s);
             Ts[r][j] = -tj * s;
         }
         if (r == j) Ts[r][j] = tj;
@@ -241,14 +253,24 @@ k_qr_update(double *__restrict__ C, int64_t ldc, int64_t m, int c0, int ncols, c
     const int rr = tid & 63, cg = tid >> 6;  // 64 rows x 4 column groups of 8
     const int64_t i = r0 + rr;
     if (i >= m) return;
+    double s[8], old[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s[k] = 0.0;
+    for (int a = 0; a < w; ++a) {
+        const double v = Vs[a][rr];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s[k] = fma(v, Zs[a][cg * 8 + k], s[k]);
+    }
+    // every load before any store (the columns of C are disjoint)
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        const int c = cg * 8 + k;
-        if (ct0 + c >= ncols) break;
-        double s = 0.0;
-        for (int a = 0; a < w; ++a) s = fma(Vs[a][rr], Zs[a][c], s);
-        double *p = C + i + (int64_t)(c0 + ct0 + c) * ldc;
-        *p -= s;
+        const int c = ct0 + cg * 8 + k;
+        old[k] = c < ncols ? C[i + (int64_t)(c0 + c) * ldc] : 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int c = ct0 + cg * 8 + k;
+        if (c < ncols) C[i + (int64_t)(c0 + c) * ldc] = old[k] - s[k];
     }
 }
 
@@ -337,7 +359,7 @@ cudaError_t qr_factor(double *A, int64_t lda, int64_t m, int64_t n, double *ws, 
         const int64_t rows_per = (rows + nsplit - 1) / nsplit;
         k_qr_vtc<<<dim3(1, nsplit), kVtcThreads, 0, st>>>(A, lda, m, j0, w, nullptr, 0, 0, w, 1, nsplit, rows_per,
                                                           part);
-        k_qr_tbuild<<<1, 32, 0, st>>>(part, nsplit, w, tau + j0, T);
+        k_qr_tbuild<<<1, kQB * kQB, 0, st>>>(part, nsplit, w, tau + j0, T);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         *launches += 3;
