@@ -21,11 +21,14 @@
 //   k_qr_update  C -= V Z.
 // Every product is an FP64 FMA chain (the library is compiled without
 // floating-point contraction).
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 
 #include "hsvd_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace hsvd {
 namespace {
@@ -125,6 +128,110 @@ k_qr_panel(double *__restrict__ A, int64_t lda, int64_t m, int j0, int w, double
         }
         __syncthreads();
     }
+}
+
+// The same panel factorisation on a cluster of kPanelCl CTAs that keep the
+// panel in shared memory: CTA r holds rows j0 + r rp .. j0 + (r+1) rp - 1
+// (column-major, stride rp).  Per column, every CTA reduces its rows' part of
+// x^T x and x^T a_c and writes it, with the diagonal row when it owns it, into
+// every CTA (double-buffered by column parity); after one cluster barrier
+// every CTA sums the same partials in the same order, forms beta, tau, w_c
+// itself and updates its own rows.  The panel goes back to A at the end.
+constexpr int kPanelCl = 16;
+constexpr int kPanelClMaxRows = 832;  // rows per CTA: 32 x 832 doubles = 208 KB
+__global__ void __launch_bounds__(kPanelThreads)
+k_qr_panel_cl(double *__restrict__ A, int64_t lda, int64_t m, int j0, int w, int rp, double *__restrict__ tau) {
+    extern __shared__ __align__(16) double P[];  // [kQB][rp]
+    __shared__ double red[2][kPanelCl][kQB];     // partial sums from every CTA
+    __shared__ double drow[2][kQB];              // the diagonal row of the column
+    __shared__ double wred[kPanelThreads / 32][kQB];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t row0 = (int64_t)j0 + (int64_t)rank * rp;
+    const int64_t left = m - row0;
+    const int nrows = left <= 0 ? 0 : (left < rp ? (int)left : rp);
+    for (int e = tid; e < kQB * rp; e += kPanelThreads) {
+        const int c = e / rp, i = e % rp;
+        P[e] = (c < w && i < nrows) ? A[row0 + i + (int64_t)(j0 + c) * lda] : 0.0;
+    }
+    cluster.sync();  // every CTA loaded and running before any remote write
+    for (int jj = 0; jj < w; ++jj) {
+        const int buf = jj & 1;
+        // local rows strictly below the diagonal row j0 + jj
+        const int64_t below = (int64_t)j0 + jj + 1 - row0;
+        const int first = below <= 0 ? 0 : (below < rp ? (int)below : rp);
+        double acc[kQB];
+#pragma unroll
+        for (int c = 0; c < kQB; ++c) acc[c] = 0.0;
+        for (int i = first + tid; i < nrows; i += kPanelThreads) {
+            const double x = P[jj * rp + i];
+#pragma unroll
+            for (int c = 0; c < kQB; ++c)
+                if (c >= jj && c < w) acc[c] = fma(x, P[c * rp + i], acc[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < kQB; ++c) {
+            double v = acc[c];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) wred[warp][c] = v;
+        }
+        __syncthreads();
+        const int64_t dl = (int64_t)j0 + jj - row0;  // the diagonal row, local index
+        const bool own_diag = dl >= 0 && dl < nrows;
+        if (tid < kQB) {
+            double ssum = 0.0;
+            for (int q = 0; q < kPanelThreads / 32; ++q) ssum += wred[q][tid];
+            const double dv = own_diag ? P[tid * rp + dl] : 0.0;
+            for (int r = 0; r < kPanelCl; ++r) {
+                *cluster.map_shared_rank(&red[buf][rank][tid], r) = ssum;
+                if (own_diag) *cluster.map_shared_rank(&drow[buf][tid], r) = dv;
+            }
+        }
+        cluster.sync();
+        // every CTA: the same sums in the same order
+        __shared__ double s_beta, s_tau, s_scale, sw[kQB];
+        if (tid < kQB) {
+            double tot = 0.0;
+            for (int r = 0; r < kPanelCl; ++r) tot += red[buf][r][tid];
+            wred[0][tid] = tot;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            const double alpha = drow[buf][jj], xnorm2 = wred[0][jj];
+            double t = 0.0, scale = 0.0, beta = alpha;
+            if (xnorm2 > 0.0) {
+                beta = -copysign(sqrt(fma(alpha, alpha, xnorm2)), alpha);
+                t = (beta - alpha) / beta;
+                scale = 1.0 / (alpha - beta);
+            }
+            s_beta = beta;
+            s_tau = t;
+            s_scale = scale;
+            if (rank == 0) tau[j0 + jj] = t;
+        }
+        __syncthreads();
+        const double t = s_tau, scale = s_scale;
+        if (tid > jj && tid < w) sw[tid] = fma(scale, wred[0][tid], drow[buf][tid]);
+        __syncthreads();
+        for (int i = first + tid; i < nrows; i += kPanelThreads) {
+            const double v = P[jj * rp + i] * scale;
+            P[jj * rp + i] = v;
+#pragma unroll
+            for (int c = 0; c < kQB; ++c)
+                if (c > jj && c < w) P[c * rp + i] = fma(-t * sw[c], v, P[c * rp + i]);
+        }
+        if (own_diag) {
+            if (tid == 0) P[jj * rp + dl] = s_beta;
+            if (tid > jj && tid < w) P[tid * rp + dl] = fma(-t, sw[tid], P[tid * rp + dl]);
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < kQB * rp; e += kPanelThreads) {
+        const int c = e / rp, i = e % rp;
+        if (c < w && i < nrows) A[row0 + i + (int64_t)(j0 + c) * lda] = P[e];
+    }
+    cluster.sync();  // no CTA leaves while another may still read its partials
 }
 
 // part[s][a][c] = sum over the rows of split s (from j0 on) of V(i, a) C(i, c0 + c),
@@ -274,6 +381,35 @@ k_qr_update(double *__restrict__ C, int64_t ldc, int64_t m, int c0, int ncols, c
     }
 }
 
+// the panel on a 16-CTA cluster when its rows fit the CTAs' shared memory
+cudaError_t panel_cluster(double *A, int64_t lda, int64_t m, int j0, int w, double *tau, cudaStream_t st) {
+    const int64_t L = m - j0;
+    const int rp = (int)((L + kPanelCl - 1) / kPanelCl);
+    if (rp > kPanelClMaxRows || L < 2 * kPanelCl) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)kQB * rp * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(k_qr_panel_cl, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_qr_panel_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kPanelCl);
+    cfg.blockDim = dim3(kPanelThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kPanelCl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;  // launch only what the GPU can hold at once
+    e = cudaOccupancyMaxActiveClusters(&clusters, k_qr_panel_cl, &cfg);
+    if (e != cudaSuccess) return e;
+    if (clusters < 1) return cudaErrorInvalidConfiguration;
+    return cudaLaunchKernelEx(&cfg, k_qr_panel_cl, A, lda, m, j0, w, rp, tau);
+}
+
 int qr_nsplit(int64_t rows) {
     const int64_t s = (rows + 255) / 256;  // at least 256 rows per split
     return (int)std::max<int64_t>(1, std::min<int64_t>(s, 64));
@@ -352,7 +488,10 @@ cudaError_t qr_factor(double *A, int64_t lda, int64_t m, int64_t n, double *ws, 
     for (int64_t p = 0; p < panels; ++p) {
         const int j0 = (int)(p * kQB), w = (int)std::min<int64_t>(kQB, n - j0);
         double *T = Tall + (size_t)p * kQB * kQB;
-        k_qr_panel<<<1, kPanelThreads, 0, st>>>(A, lda, m, j0, w, tau);
+        if (panel_cluster(A, lda, m, j0, w, tau, st) != cudaSuccess) {
+            cudaGetLastError();  // clear a refused cluster launch; the one-CTA kernel does the panel
+            k_qr_panel<<<1, kPanelThreads, 0, st>>>(A, lda, m, j0, w, tau);
+        }
         // T from V^T V
         const int64_t rows = m - j0;
         const int nsplit = qr_nsplit(rows);

@@ -23,8 +23,11 @@ def api():
     return api
 
 
-@pytest.mark.parametrize("m,n", [(700, 200), (257, 33), (64, 1), (96, 96), (1000, 320), (129, 64)])
+@pytest.mark.parametrize("m,n", [(700, 200), (257, 33), (64, 1), (96, 96), (1000, 320), (129, 64), (14000, 64), (40, 40)])
 def test_qr_matches_lapack(api, m, n):
+    """Panels on a 16-CTA cluster where their rows fit its shared memory
+    (14000 rows do not: the one-CTA panel kernel takes them; 40 rows are
+    too few for the cluster)."""
     rng = np.random.default_rng(m + n)
     G = np.asfortranarray(rng.standard_normal((m, n)) * 10.0 ** rng.uniform(-4, 2, n)[None, :])
     R, Q = api.hsvd_shorten_qr(torch.from_numpy(G).cuda())
