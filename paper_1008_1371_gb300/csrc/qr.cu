@@ -138,23 +138,53 @@ k_qr_panel(double *__restrict__ A, int64_t lda, int64_t m, int j0, int w, double
 // every CTA sums the same partials in the same order, forms beta, tau, w_c
 // itself and updates its own rows.  The panel goes back to A at the end.
 constexpr int kPanelCl = 16;
-constexpr int kPanelClMaxRows = 832;  // rows per CTA: 32 x 832 doubles = 208 KB
+constexpr int kPanelClMaxRows = 832;  // rows per CTA kept in shared memory: 32 x 832 doubles = 208 KB
+
+// Sum over the warp of 32 per-lane values v[0..31]; lane l receives the sum of
+// v[l] (a butterfly that halves the values a lane carries at each level: 31
+// shuffles instead of 32 x 5).
+__device__ __forceinline__ double warp_transpose_sum(double (&v)[kQB], int lane) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        const bool hi = lane & o;
+#pragma unroll
+        for (int i = 0; i < o; ++i) {
+            const double send = hi ? v[i] : v[i + o];
+            const double keep = hi ? v[i + o] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    return v[0];
+}
+
+// The same panel factorisation on a cluster of kPanelCl CTAs: CTA r owns rows
+// j0 + r rp .. j0 + (r+1) rp - 1, kept in shared memory (column-major, stride
+// rp) when SMEM, else worked on in place in A.  Per column, every CTA reduces
+// its rows' part of x^T x and x^T a_c and writes it, with the diagonal row
+// when it owns it, into every CTA (double-buffered by column parity); after
+// one cluster barrier every CTA sums the same partials in the same order,
+// forms beta, tau, w_c itself and updates its own rows.
+template <bool SMEM>
 __global__ void __launch_bounds__(kPanelThreads)
 k_qr_panel_cl(double *__restrict__ A, int64_t lda, int64_t m, int j0, int w, int rp, double *__restrict__ tau) {
-    extern __shared__ __align__(16) double P[];  // [kQB][rp]
+    extern __shared__ __align__(16) double P[];  // [kQB][rp] when SMEM
     __shared__ double red[2][kPanelCl][kQB];     // partial sums from every CTA
     __shared__ double drow[2][kQB];              // the diagonal row of the column
     __shared__ double wred[kPanelThreads / 32][kQB];
+    __shared__ double s_beta, s_tau, s_scale, sw[kQB];
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t row0 = (int64_t)j0 + (int64_t)rank * rp;
     const int64_t left = m - row0;
     const int nrows = left <= 0 ? 0 : (left < rp ? (int)left : rp);
-    for (int e = tid; e < kQB * rp; e += kPanelThreads) {
-        const int c = e / rp, i = e % rp;
-        P[e] = (c < w && i < nrows) ? A[row0 + i + (int64_t)(j0 + c) * lda] : 0.0;
-    }
+    double *const Ab = A + row0 + (int64_t)j0 * lda;
+    auto at = [&](int c, int i) -> double & { return SMEM ? P[c * rp + i] : Ab[i + (int64_t)c * lda]; };
+    if (SMEM)
+        for (int e = tid; e < kQB * rp; e += kPanelThreads) {
+            const int c = e / rp, i = e % rp;
+            P[e] = (c < w && i < nrows) ? Ab[i + (int64_t)c * lda] : 0.0;
+        }
     cluster.sync();  // every CTA loaded and running before any remote write
     for (int jj = 0; jj < w; ++jj) {
         const int buf = jj & 1;
@@ -165,24 +195,20 @@ k_qr_panel_cl(double *__restrict__ A, int64_t lda, int64_t m, int j0, int w, int
 #pragma unroll
         for (int c = 0; c < kQB; ++c) acc[c] = 0.0;
         for (int i = first + tid; i < nrows; i += kPanelThreads) {
-            const double x = P[jj * rp + i];
+            const double x = at(jj, i);
 #pragma unroll
             for (int c = 0; c < kQB; ++c)
-                if (c >= jj && c < w) acc[c] = fma(x, P[c * rp + i], acc[c]);
+                if (c >= jj && c < w) acc[c] = fma(x, at(c, i), acc[c]);
         }
-#pragma unroll
-        for (int c = 0; c < kQB; ++c) {
-            double v = acc[c];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) wred[warp][c] = v;
-        }
+        const double mine = warp_transpose_sum(acc, lane);  // this warp's sum for column `lane`
+        wred[warp][lane] = mine;
         __syncthreads();
         const int64_t dl = (int64_t)j0 + jj - row0;  // the diagonal row, local index
         const bool own_diag = dl >= 0 && dl < nrows;
         if (tid < kQB) {
             double ssum = 0.0;
             for (int q = 0; q < kPanelThreads / 32; ++q) ssum += wred[q][tid];
-            const double dv = own_diag ? P[tid * rp + dl] : 0.0;
+            const double dv = own_diag ? at(tid, (int)dl) : 0.0;
             for (int r = 0; r < kPanelCl; ++r) {
                 *cluster.map_shared_rank(&red[buf][rank][tid], r) = ssum;
                 if (own_diag) *cluster.map_shared_rank(&drow[buf][tid], r) = dv;
@@ -190,7 +216,6 @@ k_qr_panel_cl(double *__restrict__ A, int64_t lda, int64_t m, int j0, int w, int
         }
         cluster.sync();
         // every CTA: the same sums in the same order
-        __shared__ double s_beta, s_tau, s_scale, sw[kQB];
         if (tid < kQB) {
             double tot = 0.0;
             for (int r = 0; r < kPanelCl; ++r) tot += red[buf][r][tid];
@@ -210,27 +235,40 @@ k_qr_panel_cl(double *__restrict__ A, int64_t lda, int64_t m, int j0, int w, int
             s_scale = scale;
             if (rank == 0) tau[j0 + jj] = t;
         }
+        if (tid > jj && tid < w) sw[tid] = wred[0][tid];  // the dot; w_c is formed after the barrier
         __syncthreads();
         const double t = s_tau, scale = s_scale;
-        if (tid > jj && tid < w) sw[tid] = fma(scale, wred[0][tid], drow[buf][tid]);
+        if (tid > jj && tid < w) sw[tid] = fma(scale, sw[tid], drow[buf][tid]);
         __syncthreads();
         for (int i = first + tid; i < nrows; i += kPanelThreads) {
-            const double v = P[jj * rp + i] * scale;
-            P[jj * rp + i] = v;
+            const double v = at(jj, i) * scale;
+            if constexpr (SMEM) {
+                at(jj, i) = v;
 #pragma unroll
-            for (int c = 0; c < kQB; ++c)
-                if (c > jj && c < w) P[c * rp + i] = fma(-t * sw[c], v, P[c * rp + i]);
+                for (int c = 0; c < kQB; ++c)
+                    if (c > jj && c < w) at(c, i) = fma(-t * sw[c], v, at(c, i));
+            } else {  // global memory: a row's loads are all issued before its stores
+                double val[kQB];
+#pragma unroll
+                for (int c = 0; c < kQB; ++c)
+                    if (c > jj && c < w) val[c] = at(c, i);
+                at(jj, i) = v;
+#pragma unroll
+                for (int c = 0; c < kQB; ++c)
+                    if (c > jj && c < w) at(c, i) = fma(-t * sw[c], v, val[c]);
+            }
         }
         if (own_diag) {
-            if (tid == 0) P[jj * rp + dl] = s_beta;
-            if (tid > jj && tid < w) P[tid * rp + dl] = fma(-t, sw[tid], P[tid * rp + dl]);
+            if (tid == 0) at(jj, (int)dl) = s_beta;
+            if (tid > jj && tid < w) at(tid, (int)dl) = fma(-t, sw[tid], at(tid, (int)dl));
         }
         __syncthreads();
     }
-    for (int e = tid; e < kQB * rp; e += kPanelThreads) {
-        const int c = e / rp, i = e % rp;
-        if (c < w && i < nrows) A[row0 + i + (int64_t)(j0 + c) * lda] = P[e];
-    }
+    if (SMEM)
+        for (int e = tid; e < kQB * rp; e += kPanelThreads) {
+            const int c = e / rp, i = e % rp;
+            if (c < w && i < nrows) Ab[i + (int64_t)c * lda] = P[e];
+        }
     cluster.sync();  // no CTA leaves while another may still read its partials
 }
 
@@ -381,15 +419,14 @@ k_qr_update(double *__restrict__ C, int64_t ldc, int64_t m, int c0, int ncols, c
     }
 }
 
-// the panel on a 16-CTA cluster when its rows fit the CTAs' shared memory
-cudaError_t panel_cluster(double *A, int64_t lda, int64_t m, int j0, int w, double *tau, cudaStream_t st) {
-    const int64_t L = m - j0;
-    const int rp = (int)((L + kPanelCl - 1) / kPanelCl);
-    if (rp > kPanelClMaxRows || L < 2 * kPanelCl) return cudaErrorInvalidValue;
-    const size_t smem = (size_t)kQB * rp * sizeof(double);
-    cudaError_t e = cudaFuncSetAttribute(k_qr_panel_cl, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+// the panel on a 16-CTA cluster: rows in shared memory when they fit, else in
+// place in A
+template <bool SMEM>
+cudaError_t launch_panel_cl(double *A, int64_t lda, int64_t m, int j0, int w, int rp, double *tau, cudaStream_t st) {
+    const size_t smem = SMEM ? (size_t)kQB * rp * sizeof(double) : 0;
+    cudaError_t e = cudaFuncSetAttribute(k_qr_panel_cl<SMEM>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_qr_panel_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k_qr_panel_cl<SMEM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(kPanelCl);
@@ -404,10 +441,18 @@ cudaError_t panel_cluster(double *A, int64_t lda, int64_t m, int j0, int w, doub
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int clusters = 0;  // launch only what the GPU can hold at once
-    e = cudaOccupancyMaxActiveClusters(&clusters, k_qr_panel_cl, &cfg);
+    e = cudaOccupancyMaxActiveClusters(&clusters, k_qr_panel_cl<SMEM>, &cfg);
     if (e != cudaSuccess) return e;
     if (clusters < 1) return cudaErrorInvalidConfiguration;
-    return cudaLaunchKernelEx(&cfg, k_qr_panel_cl, A, lda, m, j0, w, rp, tau);
+    return cudaLaunchKernelEx(&cfg, k_qr_panel_cl<SMEM>, A, lda, m, j0, w, rp, tau);
+}
+
+cudaError_t panel_cluster(double *A, int64_t lda, int64_t m, int j0, int w, double *tau, cudaStream_t st) {
+    const int64_t L = m - j0;
+    const int rp = (int)((L + kPanelCl - 1) / kPanelCl);
+    if (L < 2 * kPanelCl) return cudaErrorInvalidValue;
+    return rp <= kPanelClMaxRows ? launch_panel_cl<true>(A, lda, m, j0, w, rp, tau, st)
+                                 : launch_panel_cl<false>(A, lda, m, j0, w, rp, tau, st);
 }
 
 int qr_nsplit(int64_t rows) {
