@@ -53,7 +53,8 @@ extern "C" {
 #define HSVD_ERR_NOMEM (-5)    /* workspace allocation failed                           */
 
 /* Methods. */
-#define HSVD_METHOD_AUTO 0      /* pointwise when the factor fits one SM, else blocked */
+#define HSVD_METHOD_AUTO 0      /* pointwise for n < 32 (measured faster only there),
+                                   else blocked                                        */
 #define HSVD_METHOD_POINTWISE 1 /* column-pair rotations (Alg. 4.5), one CTA per factor */
 #define HSVD_METHOD_BLOCKED 2   /* block-column pairs (Sec. 5 block-oriented method)    */
 

@@ -745,10 +745,13 @@ int hsvd_solve_ex(const double *G, int64_t m, int64_t n, int64_t ldg, const int8
     const bool shorten =
         m > n && (o.shorten == HSVD_SHORTEN_ALWAYS || (o.shorten == HSVD_SHORTEN_AUTO && 4 * m >= 5 * n));
     const int64_t m_eff = shorten ? n : m;
+    // the one-CTA pointwise solve is the faster method only for narrow factors
+    // (measured, N(0,1) square factors: n = 16: 1.07 ms against 2.39 ms blocked
+    // with b = 16; n = 32: 3.27 against 2.91 ms; n = 128: 53.8 against 8.5 ms)
     int method = o.method;
     if (method == HSVD_METHOD_AUTO)
-        method = (pointwise_fits(m_eff, n) && o.precision == HSVD_PRECISION_FP64) ? HSVD_METHOD_POINTWISE
-                                                                                  : HSVD_METHOD_BLOCKED;
+        method = (n < 32 && pointwise_fits(m_eff, n) && o.precision == HSVD_PRECISION_FP64) ? HSVD_METHOD_POINTWISE
+                                                                                             : HSVD_METHOD_BLOCKED;
     // diagonal sorting pays for the pointwise method (Sec. 5, Table 5.3) and for
     // the split-precision form (measured: Haar 4096, 2269 -> 2085 ms; Haar 1024,
     // 211 -> 197 ms), but costs sweeps in the FP64 blocked one (graded 1024:
