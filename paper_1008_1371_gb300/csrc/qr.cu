@@ -485,10 +485,11 @@ cudaError_t apply_panel(double *A, int64_t lda, int64_t m, int j0, int w, const 
 
 size_t qr_workspace_doubles(int64_t n) {
     const int64_t panels = (n + kQB - 1) / kQB;
-    return (size_t)panels * kQB * kQB            // T of every panel
+    const int64_t cols = std::min<int64_t>(n, kMaxCols);  // widest column chunk
+    return (size_t)panels * kQB * kQB             // T of every panel
            + (size_t)n                            // tau
-           + (size_t)64 * kQB * kMaxCols          // partials
-           + (size_t)kQB * kMaxCols;              // Z
+           + (size_t)64 * kQB * cols              // partials (at most 64 row splits)
+           + (size_t)kQB * cols;                  // Z
 }
 
 namespace {
@@ -529,7 +530,7 @@ cudaError_t qr_factor(double *A, int64_t lda, int64_t m, int64_t n, double *ws, 
                       long long *launches) {
     const int64_t panels = (n + kQB - 1) / kQB;
     double *Tall = ws, *tau = Tall + (size_t)panels * kQB * kQB;
-    double *part = tau + n, *Z = part + (size_t)64 * kQB * kMaxCols;
+    double *part = tau + n, *Z = part + (size_t)64 * kQB * std::min<int64_t>(n, kMaxCols);
     for (int64_t p = 0; p < panels; ++p) {
         const int j0 = (int)(p * kQB), w = (int)std::min<int64_t>(kQB, n - j0);
         double *T = Tall + (size_t)p * kQB * kQB;
@@ -563,7 +564,7 @@ cudaError_t qr_apply_q(double *A, int64_t lda, int64_t m, int64_t n, double *ws,
                        cudaStream_t st, long long *launches) {
     const int64_t panels = (n + kQB - 1) / kQB;
     double *Tall = ws, *tau = Tall + (size_t)panels * kQB * kQB;
-    double *part = tau + n, *Z = part + (size_t)64 * kQB * kMaxCols;
+    double *part = tau + n, *Z = part + (size_t)64 * kQB * std::min<int64_t>(n, kMaxCols);
     for (int64_t p = panels - 1; p >= 0; --p) {
         const int j0 = (int)(p * kQB), w = (int)std::min<int64_t>(kQB, n - j0);
         const cudaError_t e = apply_panel(A, lda, m, j0, w, Tall + (size_t)p * kQB * kQB, 0, U, ldu, 0, (int)n,
