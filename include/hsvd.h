@@ -295,6 +295,24 @@ int hsvd_shorten_qr(const double *G, int64_t m, int64_t n, int64_t ldg, double *
                     int64_t ldq, void *stream);
 
 /*
+ * hsvd_sym_factor -- the symmetric indefinite factorisation that turns an
+ * eigenproblem into an HSVD (Sec. 1): M (n x n, ldm, device, symmetric; only
+ * read) = G J G^T with G (n x n, ldg, device) and J (n signs, device, int8),
+ * from M = P L D L^T P^T with complete (Bunch-Parlett) pivoting, D of 1 x 1 and
+ * 2 x 2 blocks.  Returns HSVD_ERR_RANK for a zero pivot (M singular) or a
+ * non-finite entry, HSVD_ERR_ARG for bad sizes or host pointers.  Returns after
+ * the results are complete.
+ *
+ * hsvd_sym_eig -- the eigendecomposition M = U diag(lambda) U^T through the
+ * factorisation and the HSVD of G (opts and info as for hsvd_solve_ex; NULL
+ * opts = defaults): lambda[j] = sigma_j^2 J_jj with eigenvector U(:, j) (n x n,
+ * ldu, device; may be NULL).  Device arrays only.
+ */
+int hsvd_sym_factor(const double *M, int64_t n, int64_t ldm, double *G, int64_t ldg, int8_t *J, void *stream);
+int hsvd_sym_eig(const double *M, int64_t n, int64_t ldm, double *lambda, double *U, int64_t ldu,
+                 const hsvd_opts *opts, hsvd_info *info, void *stream);
+
+/*
  * Batched form: many independent factors of mixed sizes in one persistent
  * launch (a captured CUDA graph), each solved by the pointwise method
  * (Sec. 2, Alg. 4.5) with diagonal sorting (Sec. 4).  Factors are dispatched

@@ -110,6 +110,11 @@ def lib():
             L.hsvd_solve_ex.restype = _int
             L.hsvd_modulus_pairs.argtypes = [_int, _int, _p]
             L.hsvd_modulus_pairs.restype = _int
+            L.hsvd_sym_factor.argtypes = [_p, _i64, _i64, _p, _i64, _p, _p]
+            L.hsvd_sym_factor.restype = _int
+            L.hsvd_sym_eig.argtypes = [_p, _i64, _i64, _p, _p, _i64, ctypes.POINTER(HsvdOpts),
+                                       ctypes.POINTER(HsvdInfo), _p]
+            L.hsvd_sym_eig.restype = _int
             L.hsvd_shorten_qr.argtypes = [_p, _i64, _i64, _i64, _p, _i64, _p, _i64, _p]
             L.hsvd_shorten_qr.restype = _int
             L.hsvd_pivot_gram.argtypes = [_p, _i64, _i64, _int, _int, _p, _p, _p]
@@ -282,6 +287,38 @@ def hsvd_modulus_pairs(r, nsteps=None):
     if st != HSVD_OK:
         raise HsvdError(st)
     return out
+
+
+def hsvd_sym_factor(M, stream=None):
+    """(G, J) with M = G J G^T for a symmetric CUDA float64 tensor M (n x n)."""
+    L = lib()
+    Mc = _colmajor(M, torch.float64)
+    n = Mc.shape[0]
+    G = _empty_colmajor(n, n, Mc)
+    J = torch.empty(n, dtype=torch.int8, device=Mc.device)
+    st = L.hsvd_sym_factor(Mc.data_ptr(), n, Mc.stride(1) if n > 1 else n, G.data_ptr(), G.stride(1) if n > 1 else n,
+                           J.data_ptr(), _stream_ptr(stream, Mc.device))
+    if st != HSVD_OK:
+        raise HsvdError(st)
+    return G, J
+
+
+def hsvd_sym_eig(M, opts=None, compute_u=True, stream=None):
+    """(lambda, U, info) of M = U diag(lambda) U^T through M = G J G^T and the
+    HSVD of G; M a symmetric CUDA float64 tensor."""
+    L = lib()
+    Mc = _colmajor(M, torch.float64)
+    n = Mc.shape[0]
+    lam = torch.empty(n, dtype=torch.float64, device=Mc.device)
+    U = _empty_colmajor(n, n, Mc) if compute_u else None
+    info = HsvdInfo()
+    o = opts if opts is not None else make_opts()
+    st = L.hsvd_sym_eig(Mc.data_ptr(), n, Mc.stride(1) if n > 1 else n, lam.data_ptr(),
+                        U.data_ptr() if U is not None else None, (U.stride(1) if n > 1 else n) if U is not None else n,
+                        ctypes.byref(o), ctypes.byref(info), _stream_ptr(stream, Mc.device))
+    if st < 0:
+        raise HsvdError(st)
+    return lam, U, info
 
 
 def hsvd_shorten_qr(G, want_q=True, stream=None):

@@ -849,6 +849,54 @@ int hsvd_solve(const double *G, int64_t m, int64_t n, int64_t ldg, const int8_t 
     return rc;
 }
 
+int hsvd_sym_factor(const double *M, int64_t n, int64_t ldm, double *G, int64_t ldg, int8_t *J, void *stream) {
+    if (!M || !G || !J || n < 1 || n > ((int64_t)1 << 20) || ldm < n || ldg < n) return HSVD_ERR_ARG;
+    if (!is_device_ptr(M) || !is_device_ptr(G) || !is_device_ptr(J)) return HSVD_ERR_ARG;
+    return ldl_factor(M, n, ldm, G, ldg, J, static_cast<cudaStream_t>(stream), nullptr);
+}
+
+namespace {
+__global__ void k_sym_lambda(const double *__restrict__ sigma, const int8_t *__restrict__ J, int64_t n,
+                             double *__restrict__ lambda) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) lambda[j] = sigma[j] * sigma[j] * (double)J[j];
+}
+}  // namespace
+
+int hsvd_sym_eig(const double *M, int64_t n, int64_t ldm, double *lambda, double *U, int64_t ldu,
+                 const hsvd_opts *opts, hsvd_info *info, void *stream) {
+    if (info) memset(info, 0, sizeof *info);
+    if (!M || !lambda || n < 1 || n > ((int64_t)1 << 20) || ldm < n || (U && ldu < n)) return HSVD_ERR_ARG;
+    if (!is_device_ptr(M) || !is_device_ptr(lambda) || (U && !is_device_ptr(U))) return HSVD_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    double *G = nullptr, *sigma = nullptr;
+    int8_t *J = nullptr;
+    int rc = HSVD_OK;
+    if (cudaMallocAsync((void **)&G, sizeof(double) * n * n, st) != cudaSuccess ||
+        cudaMallocAsync((void **)&sigma, sizeof(double) * n, st) != cudaSuccess ||
+        cudaMallocAsync((void **)&J, (size_t)n, st) != cudaSuccess)
+        rc = HSVD_ERR_NOMEM;
+    long long nl = 0;
+    if (rc == HSVD_OK) rc = ldl_factor(M, n, ldm, G, n, J, st, &nl);
+    if (rc == HSVD_OK) {
+        rc = hsvd_solve_ex(G, n, n, n, J, sigma, U, ldu, nullptr, n, opts, info, stream);
+        if (rc == HSVD_OK || rc == HSVD_NOT_CONVERGED) {
+            k_sym_lambda<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(sigma, J, n, lambda);
+            if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) rc = HSVD_ERR_CUDA;
+            nl += 1;
+        }
+    }
+    if (G) cudaFreeAsync(G, st);
+    if (sigma) cudaFreeAsync(sigma, st);
+    if (J) cudaFreeAsync(J, st);
+    cudaStreamSynchronize(st);
+    if (info) {
+        info->kernel_launches += nl;
+        info->status = rc;
+    }
+    return rc;
+}
+
 int hsvd_shorten_qr(const double *G, int64_t m, int64_t n, int64_t ldg, double *R, int64_t ldr, double *Q,
                     int64_t ldq, void *stream) {
     if (!G || !R || n < 1 || m < n || ldg < m || ldr < n || (Q && ldq < m)) return HSVD_ERR_ARG;

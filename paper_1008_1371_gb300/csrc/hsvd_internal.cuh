@@ -183,6 +183,10 @@ cudaError_t qr_extract_r(const double *A, int64_t lda, int64_t n, double *R, int
 cudaError_t qr_embed_u(const double *UR, int64_t ldur, int64_t m, int64_t n, double *U, int64_t ldu,
                        cudaStream_t st);
 
+// ldl.cu: M = G J G^T by Bunch-Parlett pivoting (device arrays)
+int ldl_factor(const double *M, int64_t n, int64_t ldm, double *G, int64_t ldg, int8_t *J, cudaStream_t st,
+               long long *launches);
+
 // learned form (learned.cu)
 cudaError_t launch_features(const float *trace, const int8_t *prev_skip, const int *tab, int nvis, int b, int nb,
                             int sweep, int max_sweeps, double tol, float *X, cudaStream_t st);

@@ -197,3 +197,18 @@ def test_shorten_argument_errors_without_gpu(api):
     assert L.hsvd_shorten_qr(p(G), 3, 4, 6, p(R), 4, None, 6, None) == api.HSVD_ERR_ARG
     assert L.hsvd_shorten_qr(p(G), 6, 4, 5, p(R), 4, None, 6, None) == api.HSVD_ERR_ARG
     assert L.hsvd_shorten_qr(p(G), 6, 4, 6, p(R), 3, None, 6, None) == api.HSVD_ERR_ARG
+
+
+def test_sym_argument_errors_without_gpu(api):
+    """Host pointers and bad sizes are refused before any GPU work."""
+    L = api.lib()
+    M = np.eye(4)
+    G = np.zeros((4, 4))
+    J = np.zeros(4, dtype=np.int8)
+    lam = np.zeros(4)
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    assert L.hsvd_sym_factor(p(M), 4, 4, p(G), 4, p(J), None) == api.HSVD_ERR_ARG  # host arrays
+    assert L.hsvd_sym_factor(p(M), 0, 4, p(G), 4, p(J), None) == api.HSVD_ERR_ARG
+    assert L.hsvd_sym_factor(p(M), 4, 3, p(G), 4, p(J), None) == api.HSVD_ERR_ARG
+    info = api.HsvdInfo()
+    assert L.hsvd_sym_eig(p(M), 4, 4, p(lam), None, 4, None, ctypes.byref(info), None) == api.HSVD_ERR_ARG
