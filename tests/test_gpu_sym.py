@@ -27,7 +27,7 @@ def _sym(kind, n, seed):
     if kind == "random":
         A = rng.standard_normal((n, n))
         return (A + A.T) / 2
-    if kind == "saddle":  # zero diagonal blocks: 2 x 2 pivots are forced
+    if kind == "saddle":  # zero diagonal blocks (n even, so M is nonsingular): 2 x 2 pivots are forced
         h = n // 2
         B = rng.standard_normal((h, n - h))
         M = np.zeros((n, n))
@@ -44,7 +44,7 @@ def _sym(kind, n, seed):
 
 
 @pytest.mark.parametrize("kind,n", [("random", 5), ("random", 33), ("random", 100), ("random", 257),
-                                    ("saddle", 64), ("saddle", 31), ("definite", 80), ("paper", 160), ("random", 1)])
+                                    ("saddle", 64), ("saddle", 30), ("definite", 80), ("paper", 160), ("random", 1)])
 def test_factor_residual_and_inertia(api, kind, n):
     M = _sym(kind, n, 7 + n)
     G, J = api.hsvd_sym_factor(torch.from_numpy(np.asfortranarray(M)).cuda())
@@ -74,8 +74,10 @@ def test_eig_against_lapack(api, kind, n):
         assert np.max(np.abs(np.sort(lam) - ref) / np.abs(ref)) <= 1e-10
 
 
-def test_singular_matrix(api):
-    M = np.zeros((8, 8))
+@pytest.mark.parametrize("n", [8, 31])
+def test_singular_matrix(api, n):
+    """The zero matrix, and a saddle point matrix of odd order (rank n - 1)."""
+    M = np.zeros((n, n)) if n == 8 else _sym("saddle", n, 3)
     with pytest.raises(api.HsvdError) as e:
-        api.hsvd_sym_factor(torch.from_numpy(M).cuda())
+        api.hsvd_sym_factor(torch.from_numpy(np.asfortranarray(M)).cuda())
     assert e.value.status == api.HSVD_ERR_RANK
