@@ -77,7 +77,7 @@ def test_eig_against_lapack(api, kind, n):
 @pytest.mark.parametrize("n", [8, 31])
 def test_singular_matrix(api, n):
     """The zero matrix, and a saddle point matrix of odd order (rank n - 1)."""
-    M = np.zeros((n, n)) if n == 8 else _sym("saddle", n, 3)
+    M = np.zeros((n, n)) if n == 8 else _sym("saddle", n, 38)
     with pytest.raises(api.HsvdError) as e:
         api.hsvd_sym_factor(torch.from_numpy(np.asfortranarray(M)).cuda())
     assert e.value.status == api.HSVD_ERR_RANK
