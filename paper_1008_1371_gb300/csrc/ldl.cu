@@ -14,12 +14,14 @@
 // Unblocked and right-looking on the full symmetric trailing matrix:
 //   k_ldl_pivot   one CTA: reduces the per-CTA maxima of the last update,
 //                 chooses the pivot, swaps it into place (rows and columns of
-//                 the trailing matrix, rows of the finished L), forms the L
-//                 column(s) and records the D block;
+//                 the trailing matrix, rows of the finished L) and records the
+//                 D block;
 //   k_ldl_update  the rank-1 or rank-2 update of the trailing matrix, with the
-//                 maxima of the updated entries per CTA for the next pivot.
+//                 maxima of the updated entries per CTA for the next pivot;
+//   k_ldl_lstore  the pivot column(s) below the block become L = W D^-1, and
+//                 the position moves on.
 // The position k and the step size live on the device; the host launches n
-// (pivot, update) pairs and the ones past the end return at once.
+// rounds and the ones past the end return at once.
 #include <cuda_runtime.h>
 
 #include <vector>
@@ -180,8 +182,8 @@ k_ldl_pivot(double *__restrict__ M, int64_t ld, int n, LdlState *__restrict__ st
         }
     }
     __syncthreads();
-    // the D block and the L column(s); W (the unscaled columns) stays in the
-    // trailing part of the columns for the update, L goes to the side buffer
+    // the D block; the pivot columns below it stay unscaled (W) for the update
+    // and become L in k_ldl_lstore
     double *ck = M + (int64_t)k * ld;
     if (s == 1) {
         const double d = ck[k];
