@@ -213,8 +213,13 @@ def check_against_fp64(api, G, J, sigma, U, V, tol, J_np):
     import torch
 
     n = G.shape[1]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
     r64 = api.hsvd_solve_ex(G, J, api.make_opts(tol=tol, max_sweeps=MAX_SWEEPS, method=api.HSVD_METHOD_BLOCKED,
                                                 block_w=64, sort=False))
+    ev1.record()
+    ev1.synchronize()
+    plain_ms = ev0.elapsed_time(ev1)  # one run, graphs built inside: an upper bound
     kap = (2.0 ** -53 * torch.linalg.vector_norm(G.abs() @ r64.V.abs(), dim=0) / r64.sigma).cpu().numpy()
     sx, s64 = sigma.cpu().numpy(), r64.sigma.cpu().numpy()
     worst, worst_gate = 0.0, 0.0
@@ -231,7 +236,8 @@ def check_against_fp64(api, G, J, sigma, U, V, tol, J_np):
     res = torch.linalg.vector_norm(G @ V - U * sigma[None, :], dim=0) / (
         torch.linalg.matrix_norm(G) * torch.linalg.vector_norm(V, dim=0))
     return {"vs_plain_fp64_max_rel_sigma_diff": worst, "vs_plain_fp64_worst_over_floor_gate": worst_gate,
-            "plain_fp64_sweeps": r64.sweeps, "max_abs_UtU_minus_I": e1, "max_VtJV_minus_J_scaled": e2,
+            "plain_fp64_sweeps": r64.sweeps, "plain_fp64_ms": plain_ms,
+            "max_abs_UtU_minus_I": e1, "max_VtJV_minus_J_scaled": e2,
             "max_residual_GV_minus_U_sigma": float(res.max()),
             "gate": "two runs, each within its floor of the exact value: |d sigma|/sigma <= 2 max(1e-12, "
                     "u kappa_j) per value (worst_over_floor_gate <= 2); invariants <= 1e-12 n"}
