@@ -295,6 +295,15 @@ int hsvd_shorten_qr(const double *G, int64_t m, int64_t n, int64_t ldg, double *
                     int64_t ldq, void *stream);
 
 /*
+ * hsvd_diag_wait_timeout -- a diagnostic of failure detection without a GPU
+ * fault: runs the bounded mbarrier wait of the tensor-core kernels on a
+ * barrier that nothing arrives at, with a short poll limit.  Returns HSVD_OK
+ * when the wait gave up as designed (the kernels then report HSVD_ERR_CUDA
+ * instead of hanging) and the context stays usable, else HSVD_ERR_CUDA.
+ */
+int hsvd_diag_wait_timeout(void *stream);
+
+/*
  * hsvd_sym_factor -- the symmetric indefinite factorisation that turns an
  * eigenproblem into an HSVD (Sec. 1): M (n x n, ldm, device, symmetric; only
  * read) = G J G^T with G (n x n, ldg, device) and J (n signs, device, int8),

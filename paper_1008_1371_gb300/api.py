@@ -110,6 +110,8 @@ def lib():
             L.hsvd_solve_ex.restype = _int
             L.hsvd_modulus_pairs.argtypes = [_int, _int, _p]
             L.hsvd_modulus_pairs.restype = _int
+            L.hsvd_diag_wait_timeout.argtypes = [_p]
+            L.hsvd_diag_wait_timeout.restype = _int
             L.hsvd_sym_factor.argtypes = [_p, _i64, _i64, _p, _i64, _p, _p]
             L.hsvd_sym_factor.restype = _int
             L.hsvd_sym_eig.argtypes = [_p, _i64, _i64, _p, _p, _i64, ctypes.POINTER(HsvdOpts),

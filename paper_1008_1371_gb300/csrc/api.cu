@@ -849,6 +849,21 @@ int hsvd_solve(const double *G, int64_t m, int64_t n, int64_t ldg, const int8_t 
     return rc;
 }
 
+int hsvd_diag_wait_timeout(void *stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int *d = nullptr, h = -1;
+    if (cudaMallocAsync((void **)&d, sizeof(int), st) != cudaSuccess) return HSVD_ERR_NOMEM;
+    int rc = HSVD_OK;
+    if (launch_diag_wait(4096, d, st) != cudaSuccess ||
+        cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        rc = HSVD_ERR_CUDA;
+    cudaFreeAsync(d, st);
+    cudaStreamSynchronize(st);
+    if (rc == HSVD_OK && h != 1) rc = HSVD_ERR_CUDA;  // the wait must have given up
+    return rc;
+}
+
 int hsvd_sym_factor(const double *M, int64_t n, int64_t ldm, double *G, int64_t ldg, int8_t *J, void *stream) {
     if (!M || !G || !J || n < 1 || n > ((int64_t)1 << 20) || ldm < n || ldg < n) return HSVD_ERR_ARG;
     if (!is_device_ptr(M) || !is_device_ptr(G) || !is_device_ptr(J)) return HSVD_ERR_ARG;

@@ -171,6 +171,9 @@ cudaError_t launch_solve(int b, int npairs, const double *part, int nsplit, doub
                          int full_part = 0, int *dexp = nullptr, const int *visit = nullptr,
                          float *trace = nullptr, double tstop = 0.0, int *tbig = nullptr);
 
+// precision.cu: the bounded mbarrier wait run out on purpose (a diagnostic)
+cudaError_t launch_diag_wait(uint32_t iters, int *out, cudaStream_t st);
+
 // qr.cu: the shortening front end (Householder QR of a tall factor)
 size_t qr_workspace_doubles(int64_t n);
 // A <- R (upper triangle) and the reflectors (below); ws: qr_workspace_doubles(n)

@@ -584,4 +584,26 @@ cudaError_t launch_update_x(double *X, int64_t rowsX, int64_t ldx, double *Y, in
     return cudaGetLastError();
 }
 
+namespace {
+// The bounded wait of the tensor-core kernels, run out on purpose: an
+// mbarrier that nothing arrives at, waited on for `iters` polls.  out[0] = 1 if
+// the wait gave up (the path the kernels take to report HSVD_ERR_CUDA instead
+// of hanging), 0 if it completed.
+__global__ void k_diag_wait(uint32_t iters, int *out) {
+    __shared__ __align__(8) uint64_t mb;
+    if (threadIdx.x == 0) mbar_init(&mb, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const bool done = mbar_wait(&mb, 0, iters);
+        out[0] = done ? 0 : 1;
+        if (!done) mbar_arrive(&mb);  // complete the phase before the CTA leaves
+    }
+}
+}  // namespace
+
+cudaError_t launch_diag_wait(uint32_t iters, int *out, cudaStream_t st) {
+    k_diag_wait<<<1, 32, 0, st>>>(iters, out);
+    return cudaGetLastError();
+}
+
 }  // namespace hsvd

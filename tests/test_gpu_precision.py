@@ -195,3 +195,14 @@ def test_full_size_haar4096_split_vs_plain(api):
     lam = np.sort(np.linalg.eigvalsh(M))
     mine = np.sort(sx ** 2 * J)
     assert np.max(np.abs(lam - mine)) <= n * U64 * np.max(np.abs(lam)) * 10
+
+
+def test_bounded_wait_gives_up_and_context_survives(api):
+    """Failure detection without a GPU fault: the tensor-core kernels' bounded
+    mbarrier wait, run on a barrier that nothing arrives at, gives up after its
+    poll limit (the kernels then report HSVD_ERR_CUDA instead of hanging), and
+    the context stays usable for the next solve."""
+    assert api.lib().hsvd_diag_wait_timeout(None) == api.HSVD_OK
+    G, J = W.gaussian(64, seed=5)
+    r = _run(api, G, J, max_sweeps=40, method=api.HSVD_METHOD_BLOCKED, precision=api.HSVD_PRECISION_BF16X8)
+    assert r.status == api.HSVD_OK
