@@ -10,6 +10,8 @@
 #include <math.h>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "hsvd_internal.cuh"
 
 using namespace hsvd;
@@ -161,6 +163,13 @@ struct DagStreams {
     do {                                            \
         if ((expr) != cudaSuccess) return HSVD_ERR_CUDA; \
     } while (0)
+
+// A named range on the timeline of a profiler that reads NVTX (a no-op
+// without one): the solve, each sweep, the front and back ends.
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
 
 // Blocked method on device arrays (Sec. 5; host loop of Alg. 4.1).
 int solve_blocked_core(const double *G, int64_t m, int64_t n, int64_t ldg, const int8_t *J, double *sigma,
@@ -452,6 +461,7 @@ int solve_blocked_core(const double *G, int64_t m, int64_t n, int64_t ldg, const
     int status = HSVD_NOT_CONVERGED, sweep;
     bool judge_next = false;  // the next sweep must be a full one
     for (sweep = 1; sweep <= o.max_sweeps; ++sweep) {
+        Range sweep_range("hsvd sweep");
         const bool masked = learned && sweep >= 2 && !judge_next;
         if ((masked || export_rows) && sweep >= 2) {
             CKR(launch_features(trace, masked ? prev_skip : nullptr, d_tab_outer, nvis, b, nb, sweep, o.max_sweeps,
@@ -626,6 +636,7 @@ int solve_pointwise(const double *G, int64_t m, int64_t n, int64_t ldg, const in
 int solve_shortened(const double *G, int64_t m, int64_t n, int64_t ldg, const int8_t *J, double *sigma, double *U,
                     int64_t ldu, double *V, int64_t ldv, const hsvd_opts &o, double tol, int method, int b,
                     hsvd_info *info, cudaStream_t st) {
+    Range range("hsvd shortened solve");
     Ws ws(st);
     double *A = ws.get<double>((size_t)m * n);  // QR in place on a copy: G is read-only
     double *R = ws.get<double>((size_t)n * n);
@@ -701,6 +712,7 @@ int hsvd_modulus_pairs(int r, int nsteps, int *pairs) {
 
 int hsvd_solve_ex(const double *G, int64_t m, int64_t n, int64_t ldg, const int8_t *J, double *sigma, double *U,
                   int64_t ldu, double *V, int64_t ldv, const hsvd_opts *opts_in, hsvd_info *info, void *stream) {
+    Range range("hsvd_solve_ex");
     hsvd_opts o;
     if (opts_in) o = *opts_in;
     else hsvd_default_opts(&o);
@@ -865,6 +877,7 @@ int hsvd_diag_wait_timeout(void *stream) {
 }
 
 int hsvd_sym_factor(const double *M, int64_t n, int64_t ldm, double *G, int64_t ldg, int8_t *J, void *stream) {
+    Range range("hsvd_sym_factor");
     if (!M || !G || !J || n < 1 || n > ((int64_t)1 << 20) || ldm < n || ldg < n) return HSVD_ERR_ARG;
     if (!is_device_ptr(M) || !is_device_ptr(G) || !is_device_ptr(J)) return HSVD_ERR_ARG;
     return ldl_factor(M, n, ldm, G, ldg, J, static_cast<cudaStream_t>(stream), nullptr);
