@@ -1,0 +1,68 @@
+"""bench.py's host-side helpers on the CPU: the effective flop counts against
+a count taken from the method's structure, the clock-sample parser, and the
+comparison with the stored oracle values."""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+@pytest.mark.parametrize("m,n,b", [(1024, 1024, 32), (4096, 4096, 64), (700, 256, 16), (8192, 512, 32)])
+def test_blocked_flops_from_the_visits(m, n, b):
+    """A quasi-sweep visits (n/b)(n/2b) block pairs.  Each forms a 2b x 2b Gram
+    block (4b^2 dot products of length m, 2m flops each) and updates an m x 2b
+    and an n x 2b panel by a 2b x 2b matrix (2 flops per product term)."""
+    visits = (n // b) * (n // (2 * b))
+    per_visit = 2 * m * (2 * b) ** 2 + 2 * m * (2 * b) ** 2 + 2 * n * (2 * b) ** 2
+    assert bench.flops_per_sweep(m, n) == visits * per_visit
+
+
+@pytest.mark.parametrize("m,n", [(128, 128), (300, 200)])
+def test_pointwise_flops_from_the_pairs(m, n):
+    """n(n-1)/2 distinct pairs per sweep, counted as n^2/2: three dot products of
+    length m (2m flops each), and a rotation of two G columns and two W columns,
+    x <- (x + h t y) c and y <- (t x + y) c: 3 flops per entry of each column."""
+    per_pair = 3 * 2 * m + 3 * 2 * m + 3 * 2 * n
+    assert bench.pointwise_flops_per_sweep(m, n) == 0.5 * n * n * per_pair
+
+
+def test_clock_sampler_summary(tmp_path):
+    """The nvidia-smi CSV parser: the median SM clock, the maximum, and the
+    throttle reasons reported Active."""
+    s = bench.ClockSampler(0)
+    s.path = str(tmp_path / "clocks.csv")
+    s.proc = object()  # as if nvidia-smi had run
+    rows = [
+        "0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, 2055, 2070, 1300.5, 0x4, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1350.0, 0x4, Not Active, Not Active, Not Active, Active",
+        "garbage line",
+    ]
+    with open(s.path, "w") as f:
+        f.write("\n".join(rows) + "\n")
+    out = s.summary()
+    assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0 and out["samples"] == 3
+    assert out["reasons"] == ["sw_power_cap"]
+
+
+def test_accuracy_vs_golden_branches():
+    """The stored oracle values are compared only when G has the same bytes as
+    the factor they were computed for; then their own values have error 0 and
+    a planted relative error of 1e-10 is reported."""
+    G, J = bench.make_input("graded1024")
+    ref = np.loadtxt(bench.GOLDEN)
+    out = bench.accuracy_vs_golden(G, J, ref[:, 0].copy())
+    if "note" in out:  # this host's libm rounds G differently: nothing is compared
+        assert "not compared" in out["note"]
+        return
+    assert out["sigma_max_rel_err"] == 0.0
+    s = ref[:, 0].copy()
+    k = int(np.argmax(ref[:, 1] <= 1e-12))  # a value whose floor is below 1e-12
+    s[k] *= 1.0 + 1e-10
+    out = bench.accuracy_vs_golden(G, J, s)
+    assert abs(out["sigma_max_rel_err_where_floor_below_1e-12"] - 1e-10) < 1e-12
