@@ -67,7 +67,8 @@ extern "C" {
 #define HSVD_SORT_AUTO (-1)
 
 /* Schedule of a sweep of the blocked method.  Either way a sweep is one CUDA
- * graph and the arithmetic is the same, so are the results. */
+ * graph and every visit does the same arithmetic, so the results are the same
+ * bit for bit. */
 #define HSVD_SCHEDULE_AUTO 0  /* pairs for FP64 products, steps for split precision
                                  or with opts.profile                               */
 #define HSVD_SCHEDULE_STEPS 1 /* the steps of the pivot strategy one after the other:
@@ -86,6 +87,7 @@ extern "C" {
  * is the paper's T_eps = sqrt(eps)/2 with eps = 2^-52; a negative tstop
  * selects it. */
 #define HSVD_TSTOP_PAPER 7.450580596923828125e-9 /* 2^-27 */
+
 /* Shortening (Sec. 1) of a tall factor: G = Q R by Householder reflections,
  * the HSVD of the square R, U = Q [U_R; 0]; V and Sigma are R's.  One sweep
  * then costs 12 n^3 flops instead of 2 n^2 (4m + 2n). */
