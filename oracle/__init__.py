@@ -23,4 +23,5 @@ from .oracle import (  # noqa: F401
     modulus_pairs,
     rotation,
     set_threads,
+    sym_factor,
 )

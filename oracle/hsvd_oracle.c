@@ -30,6 +30,9 @@
  *                         two-sided rotations (Sec. 5 block-oriented method,
  *                         Sec. 6 full-block variant), pair order taken from the
  *                         modulus strategy applied inside the block.
+ *   orc_sym_factor     -- symmetric indefinite factorisation M = G J G^T with
+ *                         complete (Bunch-Parlett) pivoting (Sec. 1: M given
+ *                         explicitly is factored first).
  *   orc_block_hsvd     -- blocked one-sided method: modulus strategy over block
  *                         columns, Gram block, inner solve, G/V update
  *                         (Sec. 5 block-oriented description, Eq. 2.1).
@@ -736,5 +739,171 @@ done:
     if (stop_rule && status == ORC_OK) *stop_rule = rule;
     free(Gw); free(W); free(Gt); free(Wt); free(sgn); free(sgt); free(col); free(colt);
     free(pos); free(d); free(A); free(Wp); free(Pan); free(ps); free(pairs);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Symmetric indefinite factorisation (Sec. 1: M given explicitly is first    */
+/* factored as M = G J G^T).  Complete pivoting after Bunch and Parlett: with */
+/* alpha = (1 + sqrt 17) / 8, mu0 = max |a_ij| and mu1 = max |a_ii| over the  */
+/* trailing matrix, a 1 x 1 pivot on the largest diagonal entry when          */
+/* mu1 >= alpha mu0, else a 2 x 2 pivot on the rows and columns of the        */
+/* largest off-diagonal entry (ties: the smallest indices, column first).     */
+/* The pivot is swapped to position k (rows and columns of the trailing       */
+/* matrix, rows of the finished L); with W the pivot column(s) and D the      */
+/* block, L = W D^-1 and the trailing matrix loses L D L^T = W D^-1 W^T.      */
+/* G = P L B: B = sqrt|d| on a 1 x 1 block, Q sqrt|Lambda| on a 2 x 2 block    */
+/* D = Q Lambda Q^T (a Jacobi rotation with the smaller angle), J = the signs. */
+/* The whole symmetric matrix is kept; every product is an explicit fma.      */
+/* Returns ORC_OK, ORC_RANK (a zero pivot) or ORC_ARG.  perm (may be NULL)    */
+/* receives the original index held at each position.                        */
+/* ------------------------------------------------------------------------ */
+static void orc_sym_swap(int n, double *A, int k, int a, int b)
+{
+    if (a == b) return;
+    for (int j = 0; j < n; ++j) { /* rows a, b in every column but a and b */
+        if (j == a || j == b) continue;
+        double t = A[a + (int64_t)j * n];
+        A[a + (int64_t)j * n] = A[b + (int64_t)j * n];
+        A[b + (int64_t)j * n] = t;
+    }
+    for (int i = k; i < n; ++i) { /* columns a, b in the trailing rows but a and b */
+        if (i == a || i == b) continue;
+        double t = A[i + (int64_t)a * n];
+        A[i + (int64_t)a * n] = A[i + (int64_t)b * n];
+        A[i + (int64_t)b * n] = t;
+    }
+    double t = A[a + (int64_t)a * n];
+    A[a + (int64_t)a * n] = A[b + (int64_t)b * n];
+    A[b + (int64_t)b * n] = t;
+}
+
+int orc_sym_factor(int64_t n64, const double *M, int64_t ldm, double *G, int64_t ldg, int8_t *J, int *perm_out)
+{
+    if (n64 < 1 || ldm < n64 || ldg < n64 || n64 > (1 << 20)) return ORC_ARG;
+    const int n = (int)n64;
+    double *A = (double *)malloc(sizeof(double) * (size_t)n * n);
+    double *D = (double *)calloc((size_t)4 * n, sizeof(double));
+    int *perm = (int *)malloc(sizeof(int) * (size_t)n);
+    int8_t *bs = (int8_t *)malloc((size_t)n);
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) A[i + (int64_t)j * n] = M[i + (int64_t)j * ldm];
+    for (int i = 0; i < n; ++i) { perm[i] = i; bs[i] = 1; }
+    const double alpha = (1.0 + sqrt(17.0)) / 8.0;
+    int status = ORC_OK;
+    int k = 0;
+    while (k < n) {
+        /* the largest |diagonal| and |off-diagonal| entries of the trailing matrix */
+        double dmax = -1.0, omax = -1.0;
+        int di = -1, r = -1, q = -1;
+        for (int j = k; j < n; ++j) {
+            const double ad = fabs(A[j + (int64_t)j * n]);
+            if (ad > dmax) { dmax = ad; di = j; }
+            for (int i = j + 1; i < n; ++i) {
+                const double ao = fabs(A[i + (int64_t)j * n]);
+                if (ao > omax) { omax = ao; r = j; q = i; }
+            }
+        }
+        const double mu0 = dmax > omax ? dmax : omax;
+        int s;
+        if (k == n - 1 || omax <= 0.0 || dmax >= alpha * mu0) {
+            s = 1;
+            if (di < 0) { status = ORC_RANK; break; } /* NaN everywhere */
+            orc_sym_swap(n, A, k, k, di);
+            int t = perm[k]; perm[k] = perm[di]; perm[di] = t;
+        } else {
+            s = 2;
+            orc_sym_swap(n, A, k, k, r); /* r < q, so q stays where it is */
+            int t = perm[k]; perm[k] = perm[r]; perm[r] = t;
+            orc_sym_swap(n, A, k, k + 1, q);
+            t = perm[k + 1]; perm[k + 1] = perm[q]; perm[q] = t;
+        }
+        double *wk = A + (int64_t)k * n, *wk1 = A + (int64_t)(k + 1) * n;
+        double i00, i01 = 0.0, i11 = 0.0;
+        if (s == 1) {
+            const double d = wk[k];
+            D[4 * k] = d;
+            bs[k] = 1;
+            if (d == 0.0) { status = ORC_RANK; break; }
+            i00 = 1.0 / d;
+        } else {
+            const double d00 = wk[k], d01 = wk[k + 1], d11 = wk1[k + 1];
+            D[4 * k] = d00; D[4 * k + 1] = d01; D[4 * k + 2] = d01; D[4 * k + 3] = d11;
+            bs[k] = 2;
+            bs[k + 1] = 0;
+            const double det = fma(d00, d11, -d01 * d01);
+            if (det == 0.0) { status = ORC_RANK; break; }
+            i00 = d11 / det;
+            i01 = -d01 / det;
+            i11 = d00 / det;
+        }
+        /* trailing matrix minus W D^-1 W^T, then the pivot columns become L */
+        for (int j = k + s; j < n; ++j)
+            for (int i = k + s; i < n; ++i) {
+                double v;
+                if (s == 1) {
+                    const double li = wk[i] * i00;
+                    v = fma(-li, wk[j], A[i + (int64_t)j * n]);
+                } else {
+                    const double li0 = fma(wk[i], i00, wk1[i] * i01), li1 = fma(wk[i], i01, wk1[i] * i11);
+                    v = fma(-li0, wk[j], fma(-li1, wk1[j], A[i + (int64_t)j * n]));
+                }
+                A[i + (int64_t)j * n] = v;
+            }
+        for (int i = k + s; i < n; ++i) {
+            if (s == 1) {
+                wk[i] = wk[i] * i00;
+            } else {
+                const double w0 = wk[i], w1 = wk1[i];
+                wk[i] = fma(w0, i00, w1 * i01);
+                wk1[i] = fma(w0, i01, w1 * i11);
+            }
+        }
+        k += s;
+    }
+    if (status == ORC_OK) {
+        for (int j = 0; j < n; ++j) {
+            const int b0 = bs[j] == 0 ? j - 1 : j, size = bs[b0];
+            double c0, c1, sgn;
+            if (size == 1) {
+                const double d = D[4 * b0];
+                c0 = sqrt(fabs(d));
+                c1 = 0.0;
+                sgn = d > 0.0 ? 1.0 : -1.0;
+            } else {
+                const double a = D[4 * b0], b = D[4 * b0 + 1], c = D[4 * b0 + 3];
+                double t = 0.0;
+                if (b != 0.0) {
+                    const double zeta = (c - a) / (2.0 * b);
+                    t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+                }
+                const double cs = 1.0 / sqrt(fma(t, t, 1.0)), sn = t * cs;
+                const double l1 = fma(-t, b, a), l2 = fma(t, b, c);
+                if (j == b0) {
+                    c0 = cs * sqrt(fabs(l1));
+                    c1 = -sn * sqrt(fabs(l1));
+                    sgn = l1 > 0.0 ? 1.0 : -1.0;
+                } else {
+                    c0 = sn * sqrt(fabs(l2));
+                    c1 = cs * sqrt(fabs(l2));
+                    sgn = l2 > 0.0 ? 1.0 : -1.0;
+                }
+            }
+            for (int i = 0; i < n; ++i) {
+                double l0 = 0.0, l1v = 0.0;
+                if (i == b0) l0 = 1.0;
+                else if (i > b0 + (size - 1)) l0 = A[i + (int64_t)b0 * n];
+                if (size == 2) {
+                    if (i == b0 + 1) l1v = 1.0;
+                    else if (i > b0 + 1) l1v = A[i + (int64_t)(b0 + 1) * n];
+                }
+                G[perm[i] + (int64_t)j * ldg] = fma(c0, l0, c1 * l1v);
+            }
+            J[j] = sgn > 0.0 ? 1 : -1;
+        }
+        if (perm_out)
+            for (int i = 0; i < n; ++i) perm_out[i] = perm[i];
+    }
+    free(A); free(D); free(perm); free(bs);
     return status;
 }

@@ -76,6 +76,8 @@ def _bind(lib):
     lib.orc_block_hsvd.argtypes = [_i64, _i64, _p, _i64, _p, _int, _dbl, _int, _int, _int,
                                    _int, _p, _p, _i64, _p, _i64, _p, _p, _dbl, _p]
     lib.orc_block_hsvd.restype = _int
+    lib.orc_sym_factor.argtypes = [_i64, _p, _i64, _p, _i64, _p, _p]
+    lib.orc_sym_factor.restype = _int
     return lib
 
 
@@ -184,3 +186,15 @@ def block_hsvd(G, J, b, tol, max_sweeps=30, inner_mode=0, inner_max_passes=8, so
                                 _ptr(sigma), _ptr(U), m, _ptr(V), n, ctypes.byref(sweeps), ctypes.byref(rots),
                                 float(tstop), ctypes.byref(stop))
     return dict(sigma=sigma, U=U, V=V, sweeps=sweeps.value, rotations=rots.value, status=st, stop=stop.value)
+
+
+def sym_factor(M, lib=None):
+    """(G, J, perm, status) with M = G J G^T (Bunch-Parlett pivoting) for a
+    symmetric M; perm[i] is the original index at position i."""
+    M = np.asfortranarray(np.asarray(M, dtype=np.float64))
+    n = M.shape[0]
+    G = np.zeros((n, n), order="F")
+    J = np.zeros(n, dtype=np.int8)
+    perm = np.zeros(n, dtype=np.int32)
+    st = (lib or _load()).orc_sym_factor(n, _ptr(M), n, _ptr(G), n, _ptr(J), _ptr(perm))
+    return G, J, perm, st

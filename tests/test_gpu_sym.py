@@ -57,6 +57,20 @@ def test_factor_residual_and_inertia(api, kind, n):
         assert np.all(J > 0)
 
 
+@pytest.mark.parametrize("kind,n", [("random", 33), ("saddle", 64), ("random", 100), ("definite", 50)])
+def test_factor_matches_oracle(api, kind, n):
+    """The same pivots and the same arithmetic as the CPU oracle's Bunch-Parlett
+    factorisation: J equal, G equal bit for bit."""
+    import oracle
+
+    M = _sym(kind, n, 3 + n)
+    G, J = api.hsvd_sym_factor(torch.from_numpy(np.asfortranarray(M)).cuda())
+    Go, Jo, perm, st = oracle.sym_factor(M)
+    assert st == 0
+    assert np.array_equal(J.cpu().numpy(), Jo)
+    assert np.array_equal(G.cpu().numpy(), Go)
+
+
 @pytest.mark.parametrize("kind,n", [("random", 96), ("saddle", 128), ("paper", 288), ("random", 513)])
 def test_eig_against_lapack(api, kind, n):
     M = _sym(kind, n, 11 + n)
