@@ -243,6 +243,27 @@ def check_against_fp64(api, G, J, sigma, U, V, tol, J_np):
                     "u kappa_j) per value (worst_over_floor_gate <= 2); invariants <= 1e-12 n"}
 
 
+def host_info():
+    """The host the CPU baseline ran on: CPU model, logical cores, and the
+    oracle's compiler flags."""
+    import platform
+
+    import oracle
+
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"cpu": model, "machine": platform.machine(), "nproc": os.cpu_count(),
+            "oracle_cflags": " ".join(oracle.oracle.CFLAGS) + " -fopenmp (if available)"}
+
+
 def cpu_baseline(G, J, tol, sweeps):
     """The oracle as it stands on the host's cores: `sweeps` sweeps of its
     modulus-parallel mode (the disjoint pairs of each step on OpenMP threads)
@@ -257,6 +278,7 @@ def cpu_baseline(G, J, tol, sweeps):
     dt = time.perf_counter() - t0
     per_sweep = dt / max(r["sweeps"], 1)
     return {"value": flops_per_sweep(m, n) / per_sweep / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+            "host": host_info(),
             "sample": "%d sweep(s) of the modulus-parallel FP64 oracle (%d OpenMP threads) on the same %dx%d "
                       "factor, %.2f s per sweep; effective rate per sweep with the blocked flop count 2n^2(4m+2n)"
                       % (r["sweeps"], cores, m, n, per_sweep)}
@@ -536,7 +558,7 @@ def run_reference(args):
         "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOADS[args.workload][1], "m": m, "n": n,
                                         "sample": "one sweep of the CPU oracle per step"},
-        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "host": host_info(),
                          "sample": "one sweep of the modulus-parallel FP64 oracle (%d OpenMP threads) per step on "
                                    "the same factor" % cores},
         "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

@@ -35,6 +35,10 @@ _SO = os.path.join(_OUT_DIR, "liboracle_hsvd.so")
 _lock = threading.Lock()
 _lib = None
 
+# optimisation without floating-point contraction: every fused multiply-add in
+# the oracle is one written as fma(); -fopenmp is added when gcc has it
+CFLAGS = ["-O2", "-ffp-contract=off"]
+
 _p = ctypes.c_void_p
 _i64 = ctypes.c_int64
 _int = ctypes.c_int
@@ -52,7 +56,7 @@ def build(force=False, src=None, out=None):
     if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(src):
         return out
     tmp = out + ".tmp.%d" % os.getpid()
-    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-Wall", "-o", tmp, src, "-lm"]
+    cmd = ["gcc"] + CFLAGS + ["-fPIC", "-shared", "-Wall", "-o", tmp, src, "-lm"]
     # the modulus order runs its steps' pairs on OpenMP threads when the
     # compiler has OpenMP; otherwise the same code is compiled serially
     if subprocess.run(cmd[:1] + ["-fopenmp"] + cmd[1:], capture_output=True).returncode != 0:
