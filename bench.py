@@ -254,14 +254,17 @@ def host_info():
     try:
         with open("/proc/cpuinfo") as f:
             for line in f:
-                key = line.split(":")[0].strip().lower()
-                if key in ("model name", "cpu part", "hardware"):
-                    model = line.split(":", 1)[1].strip()
+                if ":" not in line:
+                    continue
+                key, val = line.split(":", 1)
+                if key.strip().lower() in ("model name", "cpu part", "hardware"):
+                    model = val.strip()
                     break
-    except OSError:
+    except (OSError, UnicodeDecodeError):
         pass
+    flags = " ".join(getattr(getattr(oracle, "oracle", None), "CFLAGS", []))
     return {"cpu": model, "machine": platform.machine(), "nproc": os.cpu_count(),
-            "oracle_cflags": " ".join(oracle.oracle.CFLAGS) + " -fopenmp (if available)"}
+            "oracle_cflags": flags + " -fopenmp (if available)"}
 
 
 def cpu_baseline(G, J, tol, sweeps):
