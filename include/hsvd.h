@@ -24,7 +24,10 @@
  *    the inputs in and the results out on `stream` and returns after the copy
  *    back.  The caller owns every array; the library allocates only its own
  *    workspace (stream-ordered, released before return) and never keeps a
- *    pointer after return.  G is read-only.
+ *    pointer after return.  G is read-only.  A call that mixes the kinds
+ *    returns HSVD_ERR_ARG.  Every other entry point takes device arrays only
+ *    and returns HSVD_ERR_ARG, before any allocation or launch, when one of
+ *    its arrays is host memory.
  *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  With
  *    device arrays the call still synchronises `stream` once per sweep to read
  *    the convergence flag, and before returning.

@@ -14,6 +14,26 @@
 
 #include "hsvd_internal.cuh"
 
+namespace hsvd {
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+bool all_device(std::initializer_list<const void *> ps) {
+    for (const void *p : ps)
+        if (p && !is_device_ptr(p)) return false;
+    return true;
+}
+
+}  // namespace hsvd
+
 using namespace hsvd;
 
 namespace {
@@ -40,16 +60,6 @@ void fill_cross(int h, int *pairs) {
             pairs[2 * (s * h + k)] = k;
             pairs[2 * (s * h + k) + 1] = h + (k + s) % h;
         }
-}
-
-bool is_device_ptr(const void *p) {
-    if (!p) return false;
-    cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
 struct Ws {
@@ -928,6 +938,8 @@ int hsvd_sym_eig(const double *M, int64_t n, int64_t ldm, double *lambda, double
 int hsvd_shorten_qr(const double *G, int64_t m, int64_t n, int64_t ldg, double *R, int64_t ldr, double *Q,
                     int64_t ldq, void *stream) {
     if (!G || !R || n < 1 || m < n || ldg < m || ldr < n || (Q && ldq < m)) return HSVD_ERR_ARG;
+    if (n > (int64_t)1 << 24 || m > (int64_t)1 << 31) return HSVD_ERR_ARG;
+    if (!all_device({G, R, Q})) return HSVD_ERR_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int rc = HSVD_OK;
     {
@@ -962,6 +974,7 @@ int hsvd_pivot_gram(const double *G, int64_t rows, int64_t ldg, int b, int npair
                     void *stream) {
     if (!G || !col0 || !A || npairs < 1 || rows < 1 || (rows % 64) || ldg < rows) return HSVD_ERR_ARG;
     if (b != 16 && b != 32 && b != 64) return HSVD_ERR_ARG;
+    if (!all_device({G, col0, A})) return HSVD_ERR_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int nsplit = gram_nsplit(rows, npairs);
     double *part = nullptr;
@@ -980,6 +993,7 @@ int hsvd_pivot_solve(int b, int npairs, double *A, const int8_t *sgn, double tol
     if (!A || !sgn || !W || !rotated || npairs < 1 || !(tol > 0.0)) return HSVD_ERR_ARG;
     if (b != 16 && b != 32 && b != 64) return HSVD_ERR_ARG;
     if (mode < 0 || mode > 2 || (mode == 0 && max_passes < 1)) return HSVD_ERR_ARG;
+    if (!all_device({A, sgn, W, rotated, status_dev})) return HSVD_ERR_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int nn = 2 * b;
     std::vector<int> full((size_t)nn * b * 2), cross((size_t)b * b * 2);
@@ -1005,6 +1019,7 @@ int hsvd_pivot_update(double *X, int64_t rows, int64_t ldx, int b, int npairs, c
                       const int *rotated, void *stream) {
     if (!X || !col0 || !W || !rotated || npairs < 1 || rows < 1 || (rows % 32) || ldx < rows) return HSVD_ERR_ARG;
     if (b != 16 && b != 32 && b != 64) return HSVD_ERR_ARG;
+    if (!all_device({X, col0, W, rotated})) return HSVD_ERR_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     return launch_update(X, rows, ldx, nullptr, 0, 0, b, npairs, col0, W, rotated, nullptr, st) == cudaSuccess
                ? HSVD_OK
@@ -1014,6 +1029,7 @@ int hsvd_pivot_update(double *X, int64_t rows, int64_t ldx, int b, int npairs, c
 int hsvd_pivot_gram_x(const double *G, int64_t rows, int64_t ldg, int npairs, const int *col0, double *A,
                       void *stream) {
     if (!G || !col0 || !A || npairs < 1 || rows < 1 || ldg < rows) return HSVD_ERR_ARG;
+    if (!all_device({G, col0, A})) return HSVD_ERR_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int ks = precision_gram_ksplit(rows);
     double *part = nullptr;
@@ -1040,6 +1056,7 @@ int hsvd_pivot_gram_x(const double *G, int64_t rows, int64_t ldg, int npairs, co
 int hsvd_pivot_update_x(double *X, int64_t rows, int64_t ldx, int npairs, const int *col0, const double *W,
                         const int *rotated, const int *dexp, void *stream) {
     if (!X || !col0 || !W || !rotated || npairs < 1 || rows < 1 || ldx < rows) return HSVD_ERR_ARG;
+    if (!all_device({X, col0, W, rotated, dexp})) return HSVD_ERR_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     uint16_t *wsl = nullptr;
     int *wexp = nullptr, *dz = nullptr, *status = nullptr;

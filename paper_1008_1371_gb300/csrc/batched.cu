@@ -306,16 +306,6 @@ cudaError_t tune_widths(const std::vector<BTask> &all, int grid, int *res, long 
     return cudaSuccess;
 }
 
-bool is_dev(const void *p) {
-    if (!p) return false;
-    cudaPointerAttributes at;
-    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-}
-
 }  // namespace
 }  // namespace hsvd
 
@@ -352,13 +342,17 @@ int hsvd_solve_batched_ex(int64_t count, const double *const *G, const int64_t *
     if (count == 0) return HSVD_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // host arrays: stage through device copies, one copy per matrix
-    const bool host = !is_dev(G[0]);
+    const bool host = !is_device_ptr(G[0]);
     std::vector<BTask> tasks((size_t)count);
     size_t g_off = 0, j_off = 0, s_off = 0, u_off = 0, v_off = 0;
     for (int64_t k = 0; k < count; ++k) {
         if (n[k] < 1 || m[k] < n[k] || ldg[k] < m[k] || n[k] > 2048 || m[k] > 4096) return HSVD_ERR_ARG;
         if (!G[k] || !J[k] || !sigma[k]) return HSVD_ERR_ARG;
-        if (is_dev(G[k]) == host) return HSVD_ERR_ARG;  // all of one kind
+        // all of one kind: host arrays are staged, device arrays used in place
+        if (is_device_ptr(G[k]) == host || is_device_ptr(J[k]) == host || is_device_ptr(sigma[k]) == host)
+            return HSVD_ERR_ARG;
+        if ((U && U[k] && is_device_ptr(U[k]) == host) || (V && V[k] && is_device_ptr(V[k]) == host))
+            return HSVD_ERR_ARG;
         if (need_bytes(m[k], n[k]) > (size_t)1 << 30) return HSVD_ERR_ARG;
         BTask &t = tasks[(size_t)k];
         t.m = (int)m[k];

@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <initializer_list>
+
 #include "../../include/hsvd.h"
 
 namespace hsvd {
@@ -152,6 +154,14 @@ __device__ __forceinline__ double assemble_entry(const double *__restrict__ part
 
 // pointwise.cu: one CTA solves one factor held in shared memory.
 size_t pointwise_smem_bytes(int64_t m_pad, int64_t n_pad);
+// True for device or managed memory (the kernels may read and write it);
+// false for host memory, pinned or not, for NULL, and when no GPU answers.
+bool is_device_ptr(const void *p);
+// Every non-NULL pointer of the list is device memory.  The device-only entry
+// points refuse host pointers with HSVD_ERR_ARG instead of launching kernels
+// on them.
+bool all_device(std::initializer_list<const void *> ps);
+
 bool pointwise_fits(int64_t m, int64_t n);
 // dev_out: status, sweeps, stop rule (HSVD_STOP_*); tstop = 0: strict stop only
 cudaError_t launch_pointwise(const double *G, int64_t ldg, int m, int n, const int8_t *J,

@@ -303,6 +303,7 @@ extern "C" {
 
 int hsvd_mlp_forward(const float *params, const float *X, int64_t n, float *logits, void *stream) {
     if (!params || !X || !logits || n < 0 || n > (1 << 30)) return HSVD_ERR_ARG;
+    if (!all_device({params, X, logits})) return HSVD_ERR_ARG;
     return launch_mlp_infer(params, X, (int)n, logits, nullptr, 0.0f, static_cast<cudaStream_t>(stream)) ==
                    cudaSuccess
                ? HSVD_OK
@@ -312,6 +313,7 @@ int hsvd_mlp_forward(const float *params, const float *X, int64_t n, float *logi
 int hsvd_mlp_grad(const float *params, const float *X, const float *y, int64_t n, float *grad, float *loss,
                   void *stream) {
     if (!params || !X || !y || !grad || n < 1 || n > (1 << 26)) return HSVD_ERR_ARG;
+    if (!all_device({params, X, y, grad, loss})) return HSVD_ERR_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int nblk = mlp_grad_blocks((int)n);
     float *gpart = nullptr, *lpart = nullptr;
@@ -330,6 +332,7 @@ int hsvd_mlp_grad(const float *params, const float *X, const float *y, int64_t n
 int hsvd_mlp_adam(float *params, float *m, float *v, const float *grad, int t, float lr, float beta1, float beta2,
                   float eps, void *stream) {
     if (!params || !m || !v || !grad || t < 1 || !(lr > 0.0f)) return HSVD_ERR_ARG;
+    if (!all_device({params, m, v, grad})) return HSVD_ERR_ARG;
     return launch_adam(params, m, v, grad, t, lr, beta1, beta2, eps, static_cast<cudaStream_t>(stream)) ==
                    cudaSuccess
                ? HSVD_OK

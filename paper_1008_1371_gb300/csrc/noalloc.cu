@@ -53,6 +53,7 @@ extern "C" int hsvd_solve_pointwise_noalloc(const double *G, int64_t m, int64_t 
     if (!G || !J || !sigma || n < 1 || m < n || ldg < m) return HSVD_ERR_ARG;
     if (n > HSVD_NOALLOC_MAX_N || !pointwise_fits(m, n)) return HSVD_ERR_ARG;
     if ((U && ldu < m) || (V && ldv < n) || max_sweeps < 0 || !(tol == tol)) return HSVD_ERR_ARG;
+    if (!all_device({G, J, sigma, U, V})) return HSVD_ERR_ARG;
     if (max_sweeps == 0) max_sweeps = 30;
     if (!(tol > 0.0)) tol = (double)n * 0x1p-53;
     double *scratch = nullptr;

@@ -212,3 +212,49 @@ def test_sym_argument_errors_without_gpu(api):
     assert L.hsvd_sym_factor(p(M), 4, 3, p(G), 4, p(J), None) == api.HSVD_ERR_ARG
     info = api.HsvdInfo()
     assert L.hsvd_sym_eig(p(M), 4, 4, p(lam), None, 4, None, ctypes.byref(info), None) == api.HSVD_ERR_ARG
+
+
+def test_device_only_entries_refuse_host_pointers(api):
+    """The entry points documented as device-only check every array they get
+    and return HSVD_ERR_ARG for host memory, before any allocation or
+    launch (a kernel handed a host pointer would fault instead).  Sizes are
+    valid, so only the pointer kind trips the check."""
+    L = api.lib()
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+    ERR = api.HSVD_ERR_ARG
+    G = np.zeros((64, 32), order="F")
+    R = np.zeros((32, 32), order="F")
+    Q = np.zeros((64, 32), order="F")
+    assert L.hsvd_shorten_qr(p(G), 64, 32, 64, p(R), 32, None, 64, None) == ERR
+    assert L.hsvd_shorten_qr(p(G), 64, 32, 64, p(R), 32, p(Q), 64, None) == ERR
+    col0 = np.array([0, 16], dtype=np.int32)
+    A = np.zeros((32, 32))
+    W = np.zeros((32, 32))
+    sgn = np.ones(32, dtype=np.int8)
+    rot = np.zeros(1, dtype=np.int32)
+    assert L.hsvd_pivot_gram(p(G), 64, 64, 16, 1, p(col0), p(A), None) == ERR
+    assert L.hsvd_pivot_solve(16, 1, p(A), p(sgn), 1e-14, 1, 1, p(W), p(rot), None, None) == ERR
+    assert L.hsvd_pivot_update(p(G), 64, 64, 16, 1, p(col0), p(W), p(rot), None) == ERR
+    Ax = np.zeros((128, 128))
+    Wx = np.zeros((128, 128))
+    col0x = np.array([0, 64], dtype=np.int32)
+    assert L.hsvd_pivot_gram_x(p(G), 64, 64, 1, p(col0x), p(Ax), None) == ERR
+    assert L.hsvd_pivot_update_x(p(G), 64, 64, 1, p(col0x), p(Wx), p(rot), None, None) == ERR
+    prm = np.zeros(api.HSVD_MLP_PARAMS, dtype=np.float32)
+    X = np.zeros(8, dtype=np.float32)
+    y = np.zeros(1, dtype=np.float32)
+    out = np.zeros(1, dtype=np.float32)
+    grad = np.zeros_like(prm)
+    assert L.hsvd_mlp_forward(p(prm), p(X), 1, p(out), None) == ERR
+    assert L.hsvd_mlp_grad(p(prm), p(X), p(y), 1, p(grad), p(out), None) == ERR
+    assert L.hsvd_mlp_adam(p(prm), p(np.zeros_like(prm)), p(np.zeros_like(prm)), p(grad), 1, 1e-3, 0.9, 0.999,
+                           1e-8, None) == ERR
+    c_p, i64 = ctypes.c_void_p, ctypes.c_int64
+    L.hsvd_solve_pointwise_noalloc.argtypes = [c_p, i64, i64, i64, c_p, ctypes.c_double, ctypes.c_int,
+                                               ctypes.c_int, c_p, c_p, i64, c_p, i64, c_p, c_p]
+    L.hsvd_solve_pointwise_noalloc.restype = ctypes.c_int
+    G4 = np.eye(4, order="F")
+    J4 = np.ones(4, dtype=np.int8)
+    s4 = np.zeros(4)
+    assert L.hsvd_solve_pointwise_noalloc(p(G4), 4, 4, 4, p(J4), 0.0, 30, 1, p(s4), None, 4, None, 4, None,
+                                          None) == ERR
