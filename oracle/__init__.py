@@ -18,10 +18,13 @@ from .oracle import (  # noqa: F401
     block_hsvd,
     build,
     hsvd,
+    hyp_qr,
+    hyp_qr_apply_tt,
     inner_solve,
     load,
     modulus_pairs,
     rotation,
     set_threads,
     sym_factor,
+    wide_hsvd,
 )

@@ -36,6 +36,14 @@
  *   orc_block_hsvd     -- blocked one-sided method: modulus strategy over block
  *                         columns, Gram block, inner solve, G/V update
  *                         (Sec. 5 block-oriented description, Eq. 2.1).
+ *   orc_hyp_qr         -- hyperbolic (J-orthogonal) Householder QR of a tall
+ *                         matrix (Sec. 1: a factor whose transpose is tall is
+ *                         shortened by the hyperbolic QR of its transpose),
+ *                         reading R15 below; orc_hyp_qr_apply_tt applies the
+ *                         transformation's transpose.
+ *   orc_wide_hsvd      -- HSVD of a wide factor through that QR (Sec. 1: the
+ *                         HSVD of the square R^T, then V premultiplied by the
+ *                         transformation).
  *
  * Readings of the paper where it is silent or garbled (also listed in the
  * design notes of the repository):
@@ -79,6 +87,14 @@
  *       (01)_2 also stops, after that sweep, and (11)_2 goes on.  Pairs that
  *       pass Eq. 2.3 compute no tangent and contribute nothing.  The sweep
  *       count includes the sweep that stopped.
+ *   R15 Sec. 1 names the hyperbolic QR factorisation of G^T for a wide G but
+ *       does not define it.  Here: J-orthogonal Householder reflectors
+ *       I - beta v v^T S, the column with the largest |J-norm^2| of its
+ *       trailing part pivoted first, a row interchange when the pivot row's
+ *       sign is not that of the J-norm^2, and 1 x 1 pivots only (a zero
+ *       J-norm^2 in every trailing column is reported as ORC_RANK; Singer's
+ *       2 x 2 pivots are not built).  With J = I this is Householder QR with
+ *       column pivoting on the largest trailing norm.
  */
 #include <math.h>
 #include <stdint.h>
@@ -905,5 +921,200 @@ int orc_sym_factor(int64_t n64, const double *M, int64_t ldm, double *G, int64_t
             for (int i = 0; i < n; ++i) perm_out[i] = perm[i];
     }
     free(A); free(D); free(perm); free(bs);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* orc_hyp_qr -- hyperbolic QR of a tall A (n x m, n >= m) with signature J  */
+/* (Sec. 1: a factor G whose transpose is tall is shortened by the           */
+/* hyperbolic QR of G^T; the HSVD then runs on the square R^T).  Reading    */
+/* R15: J-orthogonal Householder reflectors H = I - beta v v^T S with       */
+/* S the current signature, 1 x 1 pivots only:                              */
+/*   step k: the trailing column with the largest |gamma_j|,               */
+/*     gamma_j = sum_{i >= k} S_i A_ij^2, moves to position k;             */
+/*   if S_k differs from sign(gamma), row k is interchanged with the row   */
+/*     i > k of that sign with the largest |A_ik| (ties: smallest i);      */
+/*   alpha = -sign(x_k) sqrt|gamma| (the J-norm is kept: alpha^2 S_k =     */
+/*     gamma), v = x - alpha e_k, v^T S v = 2 S_k sqrt|gamma| (sqrt|gamma| */
+/*     + |x_k|), beta = 2 / v^T S v, and every later column y becomes     */
+/*     y - beta v (v^T S y).                                                */
+/* With T = H_{m-1} P_{m-1} ... H_0 P_0 (P_k the row interchanges) and C   */
+/* the column permutation:  T A C = [R; 0],  T^T Jh T = J  (Jh = J after   */
+/* the interchanges), so A C = Q [R; 0] with Q = T^-1 and Q^T J Q = Jh,   */
+/* and C^T (A^T J A) C = R^T Jh_1 R with Jh_1 the first m entries of Jh.   */
+/* A zero gamma (a trailing J-Gram with a zero diagonal, where Singer's     */
+/* 2 x 2 pivots would be needed) returns ORC_RANK.                          */
+/* Outputs: R (m x m, ldr; zero below the diagonal), Jh (n signs), cperm    */
+/* (m: the original column at each position), and, each may be NULL, the   */
+/* reflectors V (n x m, ldv; v_k in rows k..n-1 of column k in the row      */
+/* order of step k, zero above), beta (m) and rswap (m: the row             */
+/* interchanged with row k at step k).                                      */
+/* ------------------------------------------------------------------------ */
+int orc_hyp_qr(int64_t n64, int64_t m64, const double *A, int64_t lda, const int8_t *J, double *R, int64_t ldr,
+               int8_t *Jh, int *cperm, double *Vr, int64_t ldv, double *beta_out, int *rswap_out)
+{
+    if (m64 < 1 || n64 < m64 || lda < n64 || ldr < m64 || n64 > (1 << 24)) return ORC_ARG;
+    if (Vr && ldv < n64) return ORC_ARG;
+    const int n = (int)n64, m = (int)m64;
+    for (int i = 0; i < n; ++i)
+        if (J[i] != 1 && J[i] != -1) return ORC_ARG;
+    if (!all_finite(n, m, A, lda)) return ORC_NONFINITE;
+    double *W = (double *)malloc(sizeof(double) * (size_t)n * m);
+    double *v = (double *)malloc(sizeof(double) * (size_t)n);
+    int8_t *s = (int8_t *)malloc((size_t)n);
+    int *cp = (int *)malloc(sizeof(int) * (size_t)m);
+    for (int j = 0; j < m; ++j) {
+        cp[j] = j;
+        for (int i = 0; i < n; ++i) W[i + (int64_t)j * n] = A[i + (int64_t)j * lda];
+    }
+    for (int i = 0; i < n; ++i) s[i] = J[i];
+    if (Vr)
+        for (int j = 0; j < m; ++j)
+            for (int i = 0; i < n; ++i) Vr[i + (int64_t)j * ldv] = 0.0;
+    int status = ORC_OK;
+    for (int k = 0; k < m && status == ORC_OK; ++k) {
+        /* column pivot: the largest |gamma_j| over the trailing columns */
+        int jp = -1;
+        double gbest = -1.0, gamma = 0.0;
+        for (int j = k; j < m; ++j) {
+            double g = 0.0;
+            for (int i = k; i < n; ++i) {
+                const double w = W[i + (int64_t)j * n];
+                g += s[i] > 0 ? w * w : -(w * w);
+            }
+            if (fabs(g) > gbest) { gbest = fabs(g); jp = j; gamma = g; }
+        }
+        if (!(gbest > 0.0)) { status = ORC_RANK; break; }
+        if (jp != k) {
+            for (int i = 0; i < n; ++i) {
+                const double t = W[i + (int64_t)k * n];
+                W[i + (int64_t)k * n] = W[i + (int64_t)jp * n];
+                W[i + (int64_t)jp * n] = t;
+            }
+            const int t = cp[k]; cp[k] = cp[jp]; cp[jp] = t;
+        }
+        double *x = W + (int64_t)k * n;
+        /* row interchange when the sign at row k is not that of gamma */
+        const int8_t sg = gamma > 0.0 ? 1 : -1;
+        int ip = k;
+        if (s[k] != sg) {
+            double xbest = -1.0;
+            for (int i = k + 1; i < n; ++i)
+                if (s[i] == sg && fabs(x[i]) > xbest) { xbest = fabs(x[i]); ip = i; }
+            if (ip == k) { status = ORC_RANK; break; } /* cannot happen for gamma != 0 */
+            for (int j = 0; j < m; ++j) {
+                const double t = W[k + (int64_t)j * n];
+                W[k + (int64_t)j * n] = W[ip + (int64_t)j * n];
+                W[ip + (int64_t)j * n] = t;
+            }
+            const int8_t t = s[k]; s[k] = s[ip]; s[ip] = t;
+        }
+        if (rswap_out) rswap_out[k] = ip;
+        /* the reflector */
+        const double root = sqrt(fabs(gamma));
+        const double alpha = x[k] >= 0.0 ? -root : root;
+        for (int i = 0; i < n; ++i) v[i] = i < k ? 0.0 : x[i];
+        v[k] = x[k] - alpha;
+        const double vsv = 2.0 * (double)s[k] * root * (root + fabs(x[k]));
+        const double beta = 2.0 / vsv;
+        if (beta_out) beta_out[k] = beta;
+        if (Vr)
+            for (int i = k; i < n; ++i) Vr[i + (int64_t)k * ldv] = v[i];
+        for (int j = k + 1; j < m; ++j) {
+            double *y = W + (int64_t)j * n;
+            double vsy = 0.0;
+            for (int i = k; i < n; ++i) vsy += s[i] > 0 ? v[i] * y[i] : -(v[i] * y[i]);
+            const double f = beta * vsy;
+            for (int i = k; i < n; ++i) y[i] -= f * v[i];
+        }
+        x[k] = alpha;
+        for (int i = k + 1; i < n; ++i) x[i] = 0.0;
+    }
+    if (status == ORC_OK) {
+        for (int j = 0; j < m; ++j)
+            for (int i = 0; i < m; ++i) R[i + (int64_t)j * ldr] = i <= j ? W[i + (int64_t)j * n] : 0.0;
+        for (int i = 0; i < n; ++i) Jh[i] = s[i];
+        for (int j = 0; j < m; ++j) cperm[j] = cp[j];
+    }
+    free(W); free(v); free(s); free(cp);
+    return status;
+}
+
+/* X (n x c, ldx) <- T^T X with T = H_{m-1} P_{m-1} ... H_0 P_0 from           */
+/* orc_hyp_qr: T^T = P_0 H_0^T P_1 H_1^T ... P_{m-1} H_{m-1}^T, applied right */
+/* to left.  H_k^T = I - beta_k S_k v_k v_k^T, where S_k, the signature at    */
+/* step k, is recovered from the final Jh by undoing the later interchanges. */
+/* With X = [V_F; 0], V_F the HSVD right factor of the square F = C R^T,     */
+/* the result V satisfies G V = U Sigma and V^T J V = Jh_1 for G = A^T.       */
+int orc_hyp_qr_apply_tt(int64_t n64, int64_t m64, const double *Vr, int64_t ldv, const double *beta,
+                        const int *rswap, const int8_t *Jh, double *X, int64_t ldx, int64_t c64)
+{
+    if (m64 < 1 || n64 < m64 || ldv < n64 || ldx < n64 || c64 < 0) return ORC_ARG;
+    const int n = (int)n64, m = (int)m64, c = (int)c64;
+    int8_t *s = (int8_t *)malloc((size_t)n);
+    for (int i = 0; i < n; ++i) s[i] = Jh[i];
+    for (int k = m - 1; k >= 0; --k) {
+        const double *v = Vr + (int64_t)k * ldv;
+        for (int j = 0; j < c; ++j) {
+            double *y = X + (int64_t)j * ldx;
+            double vy = 0.0;
+            for (int i = k; i < n; ++i) vy += v[i] * y[i];
+            const double f = beta[k] * vy;
+            for (int i = k; i < n; ++i) y[i] -= s[i] > 0 ? f * v[i] : -(f * v[i]);
+        }
+        const int ip = rswap[k];
+        if (ip != k) {
+            for (int j = 0; j < c; ++j) {
+                double *y = X + (int64_t)j * ldx;
+                const double t = y[k]; y[k] = y[ip]; y[ip] = t;
+            }
+            const int8_t t = s[k]; s[k] = s[ip]; s[ip] = t;
+        }
+    }
+    free(s);
+    return ORC_OK;
+}
+
+/* HSVD of a wide factor G (m x n, m < n is the case it is for; m <= n) with   */
+/* signature J (n), through the hyperbolic QR of A = G^T (Sec. 1):           */
+/*   A C = Q [R; 0]  gives  G J G^T = F Jh_1 F^T  with F = C R^T (m x m),    */
+/*   F V_F = U Sigma (orc_hsvd, row-cyclic or modulus order),                 */
+/*   V = T^T [V_F; 0]  (n x m):  G V = U Sigma,  V^T J V = Jh_1.               */
+/* sigma, U (m x m) and Jout (m signs, lambda_j = sigma_j^2 Jout_j) follow    */
+/* F's columns; V may be NULL.                                                 */
+int orc_wide_hsvd(int64_t m64, int64_t n64, const double *G, int64_t ldg, const int8_t *J, double tol,
+                  int max_sweeps, int order, double *sigma, double *U, int64_t ldu, double *V, int64_t ldv,
+                  int8_t *Jout, int *sweeps)
+{
+    if (m64 < 1 || n64 < m64 || ldg < m64 || n64 > (1 << 24)) return ORC_ARG;
+    if ((U && ldu < m64) || (V && ldv < n64)) return ORC_ARG;
+    const int m = (int)m64, n = (int)n64;
+    double *A = (double *)calloc((size_t)n * m, sizeof(double));
+    double *R = (double *)malloc(sizeof(double) * (size_t)m * m);
+    double *F = (double *)malloc(sizeof(double) * (size_t)m * m);
+    double *VF = (double *)malloc(sizeof(double) * (size_t)m * m);
+    double *Vr = (double *)malloc(sizeof(double) * (size_t)n * m);
+    double *beta = (double *)malloc(sizeof(double) * (size_t)m);
+    int *rswap = (int *)malloc(sizeof(int) * (size_t)m);
+    int *cperm = (int *)malloc(sizeof(int) * (size_t)m);
+    int8_t *Jh = (int8_t *)malloc((size_t)n);
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < n; ++j) A[j + (int64_t)i * n] = G[i + (int64_t)j * ldg];
+    int status = orc_hyp_qr(n, m, A, n, J, R, m, Jh, cperm, Vr, n, beta, rswap);
+    if (status == ORC_OK) {
+        for (int j = 0; j < m; ++j)
+            for (int l = 0; l < m; ++l) F[cperm[j] + (int64_t)l * m] = R[l + (int64_t)j * m];
+        int64_t rots = 0;
+        status = orc_hsvd(m, m, F, m, Jh, tol, max_sweeps, order, 0, sigma, U, ldu, VF, m, sweeps, &rots, 0.0, NULL);
+    }
+    if (status == ORC_OK || status == ORC_NOT_CONVERGED) {
+        for (int i = 0; i < m; ++i) Jout[i] = Jh[i];
+        if (V) {
+            for (int j = 0; j < m; ++j)
+                for (int i = 0; i < n; ++i) V[i + (int64_t)j * ldv] = i < m ? VF[i + (int64_t)j * m] : 0.0;
+            orc_hyp_qr_apply_tt(n, m, Vr, n, beta, rswap, Jh, V, ldv, m);
+        }
+    }
+    free(A); free(R); free(F); free(VF); free(Vr); free(beta); free(rswap); free(cperm); free(Jh);
     return status;
 }

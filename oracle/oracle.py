@@ -82,6 +82,12 @@ def _bind(lib):
     lib.orc_block_hsvd.restype = _int
     lib.orc_sym_factor.argtypes = [_i64, _p, _i64, _p, _i64, _p, _p]
     lib.orc_sym_factor.restype = _int
+    lib.orc_hyp_qr.argtypes = [_i64, _i64, _p, _i64, _p, _p, _i64, _p, _p, _p, _i64, _p, _p]
+    lib.orc_hyp_qr.restype = _int
+    lib.orc_hyp_qr_apply_tt.argtypes = [_i64, _i64, _p, _i64, _p, _p, _p, _p, _i64, _i64]
+    lib.orc_hyp_qr_apply_tt.restype = _int
+    lib.orc_wide_hsvd.argtypes = [_i64, _i64, _p, _i64, _p, _dbl, _int, _int, _p, _p, _i64, _p, _i64, _p, _p]
+    lib.orc_wide_hsvd.restype = _int
     return lib
 
 
@@ -202,3 +208,54 @@ def sym_factor(M, lib=None):
     perm = np.zeros(n, dtype=np.int32)
     st = (lib or _load()).orc_sym_factor(n, _ptr(M), n, _ptr(G), n, _ptr(J), _ptr(perm))
     return G, J, perm, st
+
+
+def hyp_qr(A, J, lib=None):
+    """Hyperbolic QR of a tall A (n x m) with signature J (n): a dict with R
+    (m x m), Jh (n signs after the row interchanges), cperm (the original
+    column at each position), the reflectors refl (n x m), beta and rswap,
+    and status.  T A[:, cperm] = [R; 0] with T^T diag(Jh) T = diag(J)."""
+    A = _fcol(A)
+    n, m = A.shape
+    j = _signs(J, n)
+    R = np.zeros((m, m), order="F")
+    Jh = np.zeros(n, dtype=np.int8)
+    cperm = np.zeros(m, dtype=np.int32)
+    refl = np.zeros((n, m), order="F")
+    beta = np.zeros(m)
+    rswap = np.zeros(m, dtype=np.int32)
+    st = (lib or _load()).orc_hyp_qr(n, m, _ptr(A), n, _ptr(j), _ptr(R), m, _ptr(Jh), _ptr(cperm), _ptr(refl), n,
+                                     _ptr(beta), _ptr(rswap))
+    return dict(R=R, Jh=Jh, cperm=cperm, refl=refl, beta=beta, rswap=rswap, status=st)
+
+
+def hyp_qr_apply_tt(qr, X, lib=None):
+    """T^T X for the transformation T of a :func:`hyp_qr` result (X n x c)."""
+    X = np.array(X, dtype=np.float64, order="F", copy=True)
+    if X.ndim == 1:
+        X = X.reshape(-1, 1, order="F")
+    n, c = X.shape
+    m = qr["R"].shape[0]
+    st = (lib or _load()).orc_hyp_qr_apply_tt(n, m, _ptr(qr["refl"]), n, _ptr(qr["beta"]), _ptr(qr["rswap"]),
+                                              _ptr(qr["Jh"]), _ptr(X), n, c)
+    if st != ORC_OK:
+        raise ValueError("orc_hyp_qr_apply_tt: status %d" % st)
+    return X
+
+
+def wide_hsvd(G, J, tol, max_sweeps=30, order="cyclic", want_u=True, want_v=True, lib=None):
+    """HSVD of a wide factor G (m x n, m <= n) through the hyperbolic QR of
+    G^T: a dict with sigma, U (m x m), V (n x m), Jout (the m signs of the
+    result, lambda_j = sigma_j^2 Jout_j), sweeps and status."""
+    G = _fcol(G)
+    m, n = G.shape
+    j = _signs(J, n)
+    sigma = np.zeros(m)
+    U = np.zeros((m, m), order="F") if want_u else None
+    V = np.zeros((n, m), order="F") if want_v else None
+    Jout = np.zeros(m, dtype=np.int8)
+    sweeps = _int()
+    st = (lib or _load()).orc_wide_hsvd(m, n, _ptr(G), m, _ptr(j), float(tol), int(max_sweeps),
+                                        1 if order == "modulus" else 0, _ptr(sigma), _ptr(U), m, _ptr(V), n,
+                                        _ptr(Jout), ctypes.byref(sweeps))
+    return dict(sigma=sigma, U=U, V=V, Jout=Jout, sweeps=sweeps.value, status=st)

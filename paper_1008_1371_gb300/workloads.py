@@ -17,6 +17,9 @@ paper      the spectrum shape of the paper's test matrices (Sec. 5,
            Table 5.2): lambda uniform on [-a,-a 1e-5) U (a 1e-5, a],
            G = Q |Lambda|^(1/2) K with K J-unitary, so sigma = sqrt|lambda|
            is known by construction
+wide       a wide factor (m < n, Sec. 1: its transpose is tall) with the
+           same spectrum shape: G = Q |Lambda|^(1/2) [I 0] K, K J-unitary,
+           so G J G^T = Q Lambda Q^T is known by construction
 =========  ===============================================================
 """
 import numpy as np
@@ -147,3 +150,37 @@ def paper(n, p=None, tanh_max=0.5, mixes=2, seed=6):
     Q = _haar(rng, n)
     G = np.asfortranarray((Q * sigma[None, :]) @ K)
     return G, J, sigma
+
+
+def wide(m, n, p=None, tanh_max=0.5, mixes=2, seed=9):
+    """Known-answer wide factor G (m x n, m <= n): K (n x n) a product of
+    random J-unitary plane rotations (trigonometric inside a sign group,
+    hyperbolic with |tanh| <= tanh_max across groups), so K J K^T = J and
+    G = Q diag(sqrt|lambda|) K[:m, :] gives G J G^T = Q diag(lambda) Q^T with
+    lambda_j = |lambda_j| J_j for the first m positions of J (random signs,
+    p of the n positive).
+
+    Returns (G, J, lambda_true) with lambda_true sorted ascending."""
+    rng = _rng(seed)
+    p = n // 2 if p is None else p
+    J = signs_random(rng, n, p)
+    a = paper_a(m)
+    mag = rng.uniform(a * 1e-5, a, size=m)
+    K = np.eye(n)
+    for _ in range(mixes):
+        perm = rng.permutation(n)
+        for k in range(0, n - 1, 2):
+            i, j = perm[k], perm[k + 1]
+            if J[i] == J[j]:
+                phi = rng.uniform(-np.pi, np.pi)
+                c, s = np.cos(phi), np.sin(phi)
+                R = np.array([[c, s], [-s, c]])
+            else:
+                th = rng.uniform(-tanh_max, tanh_max)
+                ch = 1.0 / np.sqrt(1.0 - th * th)
+                R = np.array([[ch, th * ch], [th * ch, ch]])
+            K[[i, j], :] = R @ K[[i, j], :]
+    Q = _haar(rng, m)
+    G = np.asfortranarray((Q * np.sqrt(mag)[None, :]) @ K[:m, :])
+    lam = np.sort(mag * J[:m].astype(np.float64))
+    return G, J, lam
