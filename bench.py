@@ -10,8 +10,11 @@ the split-precision form on the 4096 Haar factor.  The metric is effective
 TFLOP/s = S * 2 n^2 (4m + 2n) / time, S the sweeps of the run (the same flop
 count for every form), and the time per HSVD.
 
-``--impl reference`` times the CPU oracle (plain row-cyclic FP64 C code) on
-the host cores instead: each step is one sweep of the oracle on the same G.
+``--impl reference`` times the CPU oracle (plain FP64 C code, the disjoint
+pairs of each modulus step on OpenMP threads) on the host cores instead: each
+step is one sweep of the oracle on the same G, with the same workload string
+in ``config``; on the batch workload each step solves a sample of the factors
+completely with the row-cyclic oracle.
 
 Multi-GPU: independent factors per rank (replicas, weak scaling), no
 collective on the data path; a barrier and max-over-ranks timing only.
@@ -447,7 +450,7 @@ def run_batched(args):
             rr = oracle.hsvd(G, J, G.shape[1] * 2.0 ** -53, 30, want_u=False, want_v=False)
             f += rr["sweeps"] * pointwise_flops_per_sweep(*G.shape)
         dt = time.perf_counter() - t0
-        cpu = {"value": f / dt / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+        cpu = {"value": f / dt / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle", "host": host_info(),
                "sample": "%d of %d factors (every %dth), complete row-cyclic FP64 oracle solves, %.1f s"
                          % (len(idx), count, max(1, count // 20), dt)}
 
@@ -525,8 +528,10 @@ def run_reference_batched(args, oracle):
         "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOADS["batch10k"][1].replace("10000", str(count)), "count": count,
+                                        "method": "CPU oracle, pointwise per factor, row-cyclic order",
                                         "sample": sample},
-        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": 1, "kind": "oracle", "host": host_info(),
+                         "sample": sample},
         "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -559,8 +564,9 @@ def run_reference(args):
         "impl": "reference", "metric": metric_name(args.form),
         "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOADS[args.workload][1], "m": m, "n": n,
-                                        "sample": "one sweep of the CPU oracle per step"},
+        "data": "synthetic", "config": {"workload": WORKLOADS[args.workload][1],
+                                        "method": "CPU oracle, pointwise, modulus order on OpenMP threads",
+                                        "m": m, "n": n, "tol": tol, "sample": "one sweep of the CPU oracle per step"},
         "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "host": host_info(),
                          "sample": "one sweep of the modulus-parallel FP64 oracle (%d OpenMP threads) per step on "
                                    "the same factor" % cores},
@@ -788,7 +794,7 @@ def main():
             "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "ms_per_step_median": ms_median,
-            "config": {"workload": wdesc + ", blocked, b=%d, %s" % (block, args.form), "m": m, "n": n,
+            "config": {"workload": wdesc, "method": "blocked, b=%d, %s" % (block, args.form), "m": m, "n": n,
                        "block_w": block, "form": args.form, "tol": tol, "tstop": args.tstop,
                        "schedule": args.schedule,
                        "sweeps": sweeps, "sweeps_in_flop_count": s_eff,

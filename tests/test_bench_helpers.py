@@ -1,6 +1,6 @@
 """bench.py's host-side helpers on the CPU: the effective flop counts against
-a count taken from the method's structure, the clock-sample parser, and the
-comparison with the stored oracle values."""
+a count taken from the method's structure, the clock-sample parser, the
+comparison with the stored oracle values, and the reference arm's line."""
 import os
 import sys
 
@@ -66,3 +66,26 @@ def test_accuracy_vs_golden_branches():
     s[k] *= 1.0 + 1e-10
     out = bench.accuracy_vs_golden(G, J, s)
     assert abs(out["sigma_max_rel_err_where_floor_below_1e-12"] - 1e-10) < 1e-12
+
+
+@pytest.mark.parametrize("extra", [["--workload", "graded1024"], ["--workload", "batch10k", "--count", "60"]])
+def test_reference_arm_line(extra):
+    """The reference arm runs the oracle on the host alone and prints one
+    JSON line with the GPU arm's metric, unit and workload string."""
+    import json
+    import subprocess
+    import sys
+
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "3"] + extra, capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "TFLOP/s" and d["higher_is_better"] is True
+    assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    assert d["steps"] == 1 and d["warmup"] == 3 and d["n_gpus"] == 1
+    if extra[1] == "graded1024":
+        assert d["metric"] == bench.metric_name("fp64")
+        assert d["config"]["workload"] == bench.WORKLOADS["graded1024"][1]
