@@ -1,0 +1,107 @@
+"""The paper's experiments (Sec. 5) re-run on one GPU with the library.
+
+    python -m paper_1008_1371_gb300.experiments table53   # Table 5.3: p-sweep, sorting on/off, n = 4096
+    python -m paper_1008_1371_gb300.experiments tstop     # the T_eps stop against the plain stop
+    python -m paper_1008_1371_gb300.experiments order     # GPU sweeps on the pivot-order sizes
+
+Every point is one ``hsvd_solve_ex`` call on the paper-shaped factor
+(``workloads.paper``: lambda uniform on +-[a 1e-5, a], G = Q |Lambda|^(1/2) K
+with K J-unitary, so sigma is known), U and V computed, timed with CUDA events
+(the minimum over ``--reps`` runs after one warm-up).  Each line printed is one
+JSON record with the time in ms, the sweep count and the largest relative
+sigma error against the known values.
+"""
+import argparse
+import json
+
+import numpy as np
+import torch
+
+from . import api
+from . import workloads as W
+
+EPS = 2.0 ** -52  # the paper's epsilon in Eq. 2.3
+
+
+def _solve(G, J, reps, **kw):
+    dev = torch.device("cuda:0")
+    Gd = torch.from_numpy(np.asfortranarray(G)).to(dev)
+    Jd = torch.from_numpy(J).to(dev)
+    o = api.make_opts(max_sweeps=40, method=api.HSVD_METHOD_BLOCKED, **kw)
+    api.hsvd_solve_ex(Gd, Jd, o, check=False)
+    best, r = None, None
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = api.hsvd_solve_ex(Gd, Jd, o, check=False)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    return best, r
+
+
+def _sigma_err(J, s, sig):
+    e = 0.0
+    for g in (1, -1):
+        if np.any(J == g):
+            x, y = np.sort(s[J == g]), np.sort(sig[J == g])
+            e = max(e, float(np.max(np.abs(x - y) / y)))
+    return e
+
+
+def _record(ms, r, J, sig, **extra):
+    return dict(extra, ms=round(ms, 1), sweeps=r.sweeps, status=r.status, stop=r.stop_rule,
+                err="%.1e" % _sigma_err(J, r.sigma.cpu().numpy(), sig))
+
+
+def table53(reps, n=4096):
+    """Time and sweeps against the number p of positive signs, with and
+    without diagonal sorting (Table 5.3); the split-precision form at every p,
+    plain FP64 at the ends."""
+    bf16 = dict(precision=api.HSVD_PRECISION_BF16X8, block_w=64)
+    for p in (0, 1, 5, 10, 50, 100, 500, 1000, n // 2):
+        G, J, sig = W.paper(n, p=p, seed=6)
+        forms = [("bf16x8", bf16)] + ([("fp64", dict(block_w=32))] if p in (0, n // 2) else [])
+        for form, kw in forms:
+            for sort in (True, False):
+                ms, r = _solve(G, J, reps, sort=sort, **kw)
+                print(json.dumps(_record(ms, r, J, sig, p=p, form=form, sort=sort)), flush=True)
+
+
+def tstop(reps, n=4096):
+    """The tangent-threshold stop (Sec. 2, Eq. 4.2) against the plain stop, at
+    the paper's epsilon and at the library's default n 2^-53."""
+    G, J, sig = W.paper(n, p=n // 2, seed=6)
+    for form, kw in (("bf16x8", dict(precision=api.HSVD_PRECISION_BF16X8, block_w=64)), ("fp64", dict(block_w=32))):
+        for tol_name, tol in (("2^-52", EPS), ("n 2^-53", n * 2.0 ** -53)):
+            for t in (0.0, -1.0):
+                ms, r = _solve(G, J, reps, tol=tol, tstop=t, **kw)
+                print(json.dumps(_record(ms, r, J, sig, form=form, tol=tol_name,
+                                         tstop="T_eps" if t else "off")), flush=True)
+
+
+def order(reps):
+    """Sweeps of the blocked method (modulus strategy over block columns,
+    b = 16, sorted) at the paper's epsilon, on the sizes where the pivot
+    orders are compared."""
+    for n in (160, 288, 416, 544):
+        G, J, sig = W.paper(n, seed=6)
+        ms, r = _solve(G, J, reps, block_w=16, tol=EPS, sort=True)
+        print(json.dumps(_record(ms, r, J, sig, n=n)), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("part", choices=["table53", "tstop", "order"])
+    ap.add_argument("--reps", type=int, default=1)
+    args = ap.parse_args(argv)
+    from . import build_lib
+
+    build_lib.build()
+    {"table53": table53, "tstop": tstop, "order": order}[args.part](args.reps)
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())
