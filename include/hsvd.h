@@ -190,6 +190,9 @@ void hsvd_default_opts(hsvd_opts *opts);
  *   U      m x n, ldu >= m, may be NULL                               (output)
  *   V      n x n, ldv >= n, may be NULL                               (output)
  *   sweeps may be NULL; receives the number of sweeps run
+ * Sizes up to n = 2^24 and m = 2^31 are accepted (device memory permitting).
+ * A wide factor (m < n) returns HSVD_ERR_ARG: the paper shortens it by a
+ * hyperbolic QR of G^T (Sec. 1), which this library does not provide yet.
  */
 int hsvd_solve(const double *G, int64_t m, int64_t n, int64_t ldg, const int8_t *J,
                double tol, int max_sweeps, double *sigma, double *U, int64_t ldu,
