@@ -173,6 +173,44 @@ def _stream_ptr(stream, device):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+def _need(cond, msg):
+    if not cond:
+        raise ValueError(msg)
+
+
+def _check_vec(t, n, dtype, device, name):
+    """A 1-D tensor of n elements, unit stride, on `device`."""
+    _need(isinstance(t, torch.Tensor) and t.dtype == dtype and t.device == device, "%s: %s tensor on %s expected"
+          % (name, dtype, device))
+    _need(t.dim() == 1 and t.numel() == n and (n <= 1 or t.stride(0) == 1),
+          "%s: %d contiguous elements expected, got shape %s" % (name, n, tuple(t.shape)))
+
+
+def _check_colmajor(t, rows, cols, device, name):
+    """A float64 rows x cols tensor on `device` in column-major layout
+    (unit row stride, column stride >= rows)."""
+    _need(isinstance(t, torch.Tensor) and t.dtype == torch.float64 and t.device == device,
+          "%s: float64 tensor on %s expected" % (name, device))
+    _need(t.dim() == 2 and tuple(t.shape) == (rows, cols), "%s: shape (%d, %d) expected, got %s"
+          % (name, rows, cols, tuple(t.shape)))
+    _need((rows <= 1 or t.stride(0) == 1) and (cols <= 1 or t.stride(1) >= rows),
+          "%s: column-major layout expected (strides (1, >= %d)), got %s" % (name, rows, t.stride()))
+
+
+def _ld(t, rows):
+    """Leading dimension of a column-major tensor for the C ABI."""
+    return t.stride(1) if t.shape[1] > 1 else max(rows, 1)
+
+
+def _check_pairs(col0, ncols, b, name="col0"):
+    """Block pairs: an integer (npairs, 2) tensor of first columns, each block
+    of b columns inside the ncols columns of the matrix."""
+    _need(col0.dim() == 2 and col0.shape[0] >= 1 and col0.shape[1] == 2,
+          "%s: integer tensor of shape (npairs >= 1, 2) expected" % name)
+    _need(int(col0.min()) >= 0 and int(col0.max()) + b <= ncols,
+          "%s: blocks of %d columns must lie inside the %d columns" % (name, b, ncols))
+
+
 @dataclass
 class HsvdResult:
     sigma: torch.Tensor
@@ -253,8 +291,14 @@ def hsvd_solve_ex(G, J, opts=None, compute_u=True, compute_v=True, stream=None, 
     Jc = J.to(torch.int8).contiguous()
     if Jc.device != Gc.device:
         raise ValueError("G and J must be on the same device")
+    _need(Jc.dim() == 1 and Jc.numel() == n, "J: one sign per column of G (%d) expected" % n)
     if out is not None:
         sigma, U, V = out
+        _check_vec(sigma, n, torch.float64, Gc.device, "sigma")
+        if U is not None:
+            _check_colmajor(U, m, n, Gc.device, "U")
+        if V is not None:
+            _check_colmajor(V, n, n, Gc.device, "V")
     else:
         sigma = torch.empty(n, dtype=torch.float64, device=Gc.device,
                             pin_memory=(Gc.device.type == "cpu" and Gc.is_pinned()))
@@ -263,8 +307,8 @@ def hsvd_solve_ex(G, J, opts=None, compute_u=True, compute_v=True, stream=None, 
     o = opts if opts is not None else make_opts()
     info = HsvdInfo()
     st = L.hsvd_solve_ex(Gc.data_ptr(), m, n, Gc.stride(1) if n > 1 else m, Jc.data_ptr(), sigma.data_ptr(),
-                         U.data_ptr() if U is not None else None, U.stride(1) if U is not None else m,
-                         V.data_ptr() if V is not None else None, V.stride(1) if V is not None else n,
+                         U.data_ptr() if U is not None else None, _ld(U, m) if U is not None else m,
+                         V.data_ptr() if V is not None else None, _ld(V, n) if V is not None else n,
                          ctypes.byref(o), ctypes.byref(info), _stream_ptr(stream, Gc.device))
     if check and st < 0:
         raise HsvdError(st)
@@ -296,6 +340,7 @@ def hsvd_sym_factor(M, stream=None):
     L = lib()
     Mc = _colmajor(M, torch.float64)
     n = Mc.shape[0]
+    _need(Mc.shape[1] == n, "M must be square")
     G = _empty_colmajor(n, n, Mc)
     J = torch.empty(n, dtype=torch.int8, device=Mc.device)
     st = L.hsvd_sym_factor(Mc.data_ptr(), n, Mc.stride(1) if n > 1 else n, G.data_ptr(), G.stride(1) if n > 1 else n,
@@ -311,6 +356,7 @@ def hsvd_sym_eig(M, opts=None, compute_u=True, stream=None):
     L = lib()
     Mc = _colmajor(M, torch.float64)
     n = Mc.shape[0]
+    _need(Mc.shape[1] == n, "M must be square")
     lam = torch.empty(n, dtype=torch.float64, device=Mc.device)
     U = _empty_colmajor(n, n, Mc) if compute_u else None
     info = HsvdInfo()
@@ -346,6 +392,7 @@ def hsvd_pivot_gram(G, b, col0, stream=None):
     L = lib()
     Gc = _colmajor(G, torch.float64)
     rows = Gc.shape[0]
+    _check_pairs(col0, Gc.shape[1], b)
     npairs = col0.shape[0]
     c0 = col0.to(torch.int32).contiguous()
     A = torch.empty((npairs, 2 * b, 2 * b), dtype=torch.float64, device=Gc.device)
@@ -361,7 +408,10 @@ def hsvd_pivot_solve(A, sgn, tol, mode=1, max_passes=8, stream=None):
     """J-orthogonalise pivot blocks A (npairs, 2b, 2b); returns
     (A_out, W, rotations, status)."""
     L = lib()
+    _need(A.dim() == 3 and A.shape[1] == A.shape[2] and A.shape[1] in (32, 64, 128) and A.shape[0] >= 1,
+          "A: (npairs, 2b, 2b) with b = 16, 32 or 64 expected")
     npairs, nn, _ = A.shape
+    _need(tuple(sgn.shape) == (npairs, nn), "sgn: shape (npairs, 2b) expected")
     Ab = A.transpose(1, 2).contiguous().clone()  # column-major blocks
     W = torch.empty_like(Ab)
     s = sgn.to(torch.int8).contiguous()
@@ -380,6 +430,9 @@ def hsvd_pivot_update(X, b, col0, W, rotated, stream=None):
     if not (X.stride(0) == 1):
         raise ValueError("X must be column-major")
     rows = X.shape[0]
+    _check_pairs(col0, X.shape[1], b)
+    _need(tuple(W.shape) == (col0.shape[0], 2 * b, 2 * b), "W: shape (npairs, 2b, 2b) expected")
+    _need(rotated.numel() == col0.shape[0], "rotated: one flag per pair expected")
     c0 = col0.to(torch.int32).contiguous()
     Wb = W.transpose(1, 2).contiguous()
     r = rotated.to(torch.int32).contiguous()
@@ -395,6 +448,7 @@ def hsvd_pivot_gram_x(G, col0, stream=None):
     L = lib()
     Gc = _colmajor(G, torch.float64)
     rows = Gc.shape[0]
+    _check_pairs(col0, Gc.shape[1], 64)
     c0 = col0.to(torch.int32).contiguous()
     npairs = c0.shape[0]
     A = torch.empty((npairs, 128, 128), dtype=torch.float64, device=Gc.device)
@@ -410,6 +464,11 @@ def hsvd_pivot_update_x(X, col0, W, rotated, dexp=None, stream=None):
     L = lib()
     if not (X.stride(0) == 1):
         raise ValueError("X must be column-major")
+    _check_pairs(col0, X.shape[1], 64)
+    npairs = col0.shape[0]
+    _need(tuple(W.shape) == (npairs, 128, 128), "W: shape (npairs, 128, 128) expected")
+    _need(rotated.numel() == npairs, "rotated: one flag per pair expected")
+    _need(dexp is None or tuple(dexp.shape) == (npairs, 128), "dexp: shape (npairs, 128) expected")
     c0 = col0.to(torch.int32).contiguous()
     Wb = W.transpose(1, 2).contiguous()
     r = rotated.to(torch.int32).contiguous()
@@ -469,8 +528,23 @@ def hsvd_solve_batched(Gs, Js, opts=None, compute_u=True, compute_v=True, stream
     n = (ctypes.c_int64 * max(count, 1))(*[G.shape[1] for G in Gc])
     ld = (ctypes.c_int64 * max(count, 1))(*[(G.stride(1) if G.shape[1] > 1 else G.shape[0]) for G in Gc])
     pin = dev.type == "cpu" and count > 0 and Gc[0].is_pinned()
+    for k, (G, J) in enumerate(zip(Gc, Jc)):
+        _need(G.device == dev and J.device == dev, "factor %d: every G and J on %s expected" % (k, dev))
+        _need(J.dim() == 1 and J.numel() == G.shape[1], "factor %d: one sign per column of G expected" % k)
     if out is not None:
         sig, Us, Vs = out
+        _need(len(sig) == count and (Us is None or len(Us) == count) and (Vs is None or len(Vs) == count),
+              "out: one sigma, U and V per factor expected")
+        for k, G in enumerate(Gc):
+            mk, nk = G.shape
+            _check_vec(sig[k], nk, torch.float64, dev, "sigma[%d]" % k)
+            # the batched ABI takes leading dimensions m_k and n_k
+            if Us is not None:
+                _check_colmajor(Us[k], mk, nk, dev, "U[%d]" % k)
+                _need(nk <= 1 or Us[k].stride(1) == mk, "U[%d]: leading dimension %d expected" % (k, mk))
+            if Vs is not None:
+                _check_colmajor(Vs[k], nk, nk, dev, "V[%d]" % k)
+                _need(nk <= 1 or Vs[k].stride(1) == nk, "V[%d]: leading dimension %d expected" % (k, nk))
     else:
         sig = [torch.empty(G.shape[1], dtype=torch.float64, device=dev, pin_memory=pin) for G in Gc]
         Us = [torch.empty((G.shape[1], G.shape[0]), dtype=torch.float64, device=dev, pin_memory=pin).t()
@@ -503,6 +577,7 @@ def hsvd_mlp_forward(params, X, stream=None):
     """Logits of the learned-form network for the rows of X (n x 8)."""
     _f32_cuda(params, (HSVD_MLP_PARAMS,))
     _f32_cuda(X)
+    _need(X.dim() == 2 and X.shape[1] == HSVD_MLP_FEATURES, "X: shape (n, %d) expected" % HSVD_MLP_FEATURES)
     n = X.shape[0]
     out = torch.empty(n, dtype=torch.float32, device=X.device)
     rc = lib().hsvd_mlp_forward(params.data_ptr(), X.data_ptr(), n, out.data_ptr(), _stream_ptr(stream, X.device))
@@ -515,6 +590,7 @@ def hsvd_mlp_grad(params, X, y, stream=None):
     """(gradient, mean loss) of the mean binary cross-entropy with logits."""
     _f32_cuda(params, (HSVD_MLP_PARAMS,))
     _f32_cuda(X)
+    _need(X.dim() == 2 and X.shape[1] == HSVD_MLP_FEATURES, "X: shape (n, %d) expected" % HSVD_MLP_FEATURES)
     _f32_cuda(y, (X.shape[0],))
     g = torch.empty(HSVD_MLP_PARAMS, dtype=torch.float32, device=X.device)
     loss = torch.empty(1, dtype=torch.float32, device=X.device)
