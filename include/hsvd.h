@@ -219,7 +219,10 @@ int hsvd_modulus_pairs(int r, int nsteps, int *pairs);
 /*
  * Kernel-level entry points of the blocked method, exposed so each kernel can
  * be checked on its own.  All pointers are device pointers; the call is
- * stream-ordered (no synchronisation); the caller owns all memory.
+ * stream-ordered (no synchronisation); the caller owns all memory.  The pair
+ * table col0 lives in device memory and is not read on the host: every block
+ * [col0, col0 + b) must lie inside the columns of G (or X), and the two blocks
+ * of a pair must not overlap; the Python binding checks this before the call.
  *
  * hsvd_pivot_gram: A_P = [G_I G_J]^T [G_I G_J] for npairs block-column pairs
  * (Sec. 2 pivot block A_P, blocked as in Sec. 5).  G has `rows` rows (a
