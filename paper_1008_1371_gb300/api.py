@@ -202,13 +202,20 @@ def _ld(t, rows):
     return t.stride(1) if t.shape[1] > 1 else max(rows, 1)
 
 
-def _check_pairs(col0, ncols, b, name="col0"):
+def _check_pairs(col0, ncols, b, disjoint=False, name="col0"):
     """Block pairs: an integer (npairs, 2) tensor of first columns, each block
-    of b columns inside the ncols columns of the matrix."""
+    of b columns inside the ncols columns of the matrix, the two blocks of a
+    pair apart; with `disjoint` (the in-place updates, where pairs run side
+    by side) no two blocks of the table overlap."""
     _need(col0.dim() == 2 and col0.shape[0] >= 1 and col0.shape[1] == 2,
           "%s: integer tensor of shape (npairs >= 1, 2) expected" % name)
-    _need(int(col0.min()) >= 0 and int(col0.max()) + b <= ncols,
+    c = col0.detach().to("cpu", torch.int64)
+    _need(int(c.min()) >= 0 and int(c.max()) + b <= ncols,
           "%s: blocks of %d columns must lie inside the %d columns" % (name, b, ncols))
+    _need(bool(((c[:, 0] - c[:, 1]).abs() >= b).all()), "%s: the two blocks of a pair overlap" % name)
+    if disjoint:
+        starts = torch.sort(c.reshape(-1)).values
+        _need(bool((starts[1:] - starts[:-1] >= b).all()), "%s: blocks of different pairs overlap" % name)
 
 
 @dataclass
@@ -430,7 +437,7 @@ def hsvd_pivot_update(X, b, col0, W, rotated, stream=None):
     if not (X.stride(0) == 1):
         raise ValueError("X must be column-major")
     rows = X.shape[0]
-    _check_pairs(col0, X.shape[1], b)
+    _check_pairs(col0, X.shape[1], b, disjoint=True)
     _need(tuple(W.shape) == (col0.shape[0], 2 * b, 2 * b), "W: shape (npairs, 2b, 2b) expected")
     _need(rotated.numel() == col0.shape[0], "rotated: one flag per pair expected")
     c0 = col0.to(torch.int32).contiguous()
@@ -464,7 +471,7 @@ def hsvd_pivot_update_x(X, col0, W, rotated, dexp=None, stream=None):
     L = lib()
     if not (X.stride(0) == 1):
         raise ValueError("X must be column-major")
-    _check_pairs(col0, X.shape[1], 64)
+    _check_pairs(col0, X.shape[1], 64, disjoint=True)
     npairs = col0.shape[0]
     _need(tuple(W.shape) == (npairs, 128, 128), "W: shape (npairs, 128, 128) expected")
     _need(rotated.numel() == npairs, "rotated: one flag per pair expected")

@@ -95,6 +95,10 @@ def test_pivot_tables_checked(api):
     W = torch.zeros((2, 2 * b, 2 * b), dtype=torch.float64)
     rot = torch.ones(2, dtype=torch.int32)
     _reaches_library(lambda: api.hsvd_pivot_update(G, b, good, W, rot))
+    with pytest.raises(ValueError):  # two pairs writing the same block
+        api.hsvd_pivot_update(G, b, torch.tensor([[0, 2 * b], [2 * b, 3 * b]], dtype=torch.int32), W, rot)
+    with pytest.raises(ValueError):  # the blocks of one pair overlap
+        api.hsvd_pivot_gram(G, b, torch.tensor([[0, b // 2]], dtype=torch.int32))
     with pytest.raises(ValueError):
         api.hsvd_pivot_update(G, b, good, W[:1], rot)
     with pytest.raises(ValueError):
