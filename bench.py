@@ -83,7 +83,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-sweeps", type=int, default=2, help="oracle sweeps timed for cpu_baseline")
+    ap.add_argument("--cpu-sweeps", type=int, default=0,
+                    help="oracle sweeps timed for cpu_baseline (0: a complete solve within about 10 s)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="graded1024", choices=sorted(WORKLOADS))
@@ -270,24 +271,37 @@ def host_info():
             "oracle_cflags": flags + " -fopenmp (if available)"}
 
 
-def cpu_baseline(G, J, tol, sweeps):
-    """The oracle as it stands on the host's cores: `sweeps` sweeps of its
-    modulus-parallel mode (the disjoint pairs of each step on OpenMP threads)
-    on the same factor."""
+def cpu_baseline(G, J, tol, sweeps, budget_s=10.0):
+    """The oracle as it stands on the host's cores: its modulus-parallel mode
+    (the disjoint pairs of each step on OpenMP threads) on the same factor.
+    `sweeps` > 0 times that many sweeps; 0 times a complete solve when one
+    sweep is cheap enough, else as many sweeps as fit in about `budget_s`
+    seconds (one timed sweep decides)."""
     import oracle
 
     oracle.build()
     cores = oracle.set_threads(0)
     m, n = G.shape
-    t0 = time.perf_counter()
-    r = oracle.hsvd(G, J, tol, sweeps, order="modulus", want_u=False, want_v=False)
-    dt = time.perf_counter() - t0
+
+    def run(k):
+        t0 = time.perf_counter()
+        r = oracle.hsvd(G, J, tol, k, order="modulus", want_u=False, want_v=False)
+        return r, time.perf_counter() - t0
+
+    if sweeps <= 0:
+        r, dt = run(1)
+        k = max(1, min(MAX_SWEEPS, int(budget_s / max(dt, 1e-9))))
+        if k > 1:
+            r, dt = run(k)
+    else:
+        r, dt = run(sweeps)
     per_sweep = dt / max(r["sweeps"], 1)
+    what = "a complete solve (%d sweeps)" % r["sweeps"] if r["status"] == 0 else "%d sweep(s)" % r["sweeps"]
     return {"value": flops_per_sweep(m, n) / per_sweep / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
             "host": host_info(),
-            "sample": "%d sweep(s) of the modulus-parallel FP64 oracle (%d OpenMP threads) on the same %dx%d "
-                      "factor, %.2f s per sweep; effective rate per sweep with the blocked flop count 2n^2(4m+2n)"
-                      % (r["sweeps"], cores, m, n, per_sweep)}
+            "sample": "%s of the modulus-parallel FP64 oracle (%d OpenMP threads) on the same %dx%d factor, %.2f s "
+                      "per sweep; effective rate per sweep with the blocked flop count 2n^2(4m+2n)"
+                      % (what, cores, m, n, per_sweep)}
 
 
 def pointwise_flops_per_sweep(m, n):
