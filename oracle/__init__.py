@@ -3,7 +3,8 @@
 Test infrastructure only: the tests, ``__graft_entry__.smoke()`` and the CPU
 baseline leg of ``bench.py`` import it.  The library path never does; the two
 share no code.  ``hsvd_oracle.c`` holds the arithmetic, ``oracle.py`` the
-ctypes marshalling and its build step.
+ctypes marshalling and its build step; ``mlp.py`` models the learned form's
+network and ``split.py`` the split-precision Gram exactly, both in numpy.
 """
 from .oracle import (  # noqa: F401
     ORC_ARG,
