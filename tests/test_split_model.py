@@ -1,5 +1,5 @@
-"""Pins for the exact CPU model of the split-precision Gram (the BF16x8
-form's A_P, reading R12), against what is fixed outside it: exact rational
+"""Pins for the exact CPU models of the split-precision Gram and update (the
+BF16x8 form, reading R12), against what is fixed outside them: exact rational
 dot products (Python fractions), the digit identity V = sum q_k 128^(8-k),
 inputs whose digits the kept products cover completely (then the model is
 the exact dot product rounded once), the error bound of the dropped products
@@ -98,12 +98,79 @@ def test_symmetric_scaled_and_zero_columns():
     assert np.array_equal(split.gram(P2), A)
 
 
+def _pinned(rng, shape, exps, axis):
+    """Integers n 2^(e - 27), |n| < 2^27 (four base-128 digits), with one
+    entry per row (axis 1) or column (axis 0) at (2^26 + 1) 2^(e - 27), so the
+    split exponent is e there."""
+    N = rng.integers(-(2 ** 27) + 1, 2 ** 27, size=shape)
+    if axis == 1:
+        N[:, 0] = 2 ** 26 + 1
+        return N.astype(np.float64) * np.exp2(np.asarray(exps) - 27)[:, None]
+    N[0, :] = 2 ** 26 + 1
+    return N.astype(np.float64) * np.exp2(np.asarray(exps) - 27)[None, :]
+
+
+def test_update_four_digit_inputs_are_exact():
+    """Update without balancing on four-digit inputs: every kept product
+    covers them, so each output is the exact dot product rounded once."""
+    rng = np.random.default_rng(11)
+    X = _pinned(rng, (20, 128), rng.integers(-10, 10, size=20), axis=1)
+    Wm = _pinned(rng, (128, 128), rng.integers(-10, 10, size=128), axis=0)
+    O = split.update(X, Wm)
+    for i in (0, 7, 19):
+        for j in (0, 1, 64, 127):
+            assert O[i, j] == float(_exact_dot(X[i], Wm[:, j])), (i, j)
+
+
+def test_update_balancing_shift_and_scaling():
+    """A common shift of all dk moves E_i and F_j in opposite directions and
+    changes no digit: the same bits.  A power of two on a row of X or a
+    column of W scales that output row or column exactly."""
+    rng = np.random.default_rng(12)
+    X = rng.standard_normal((30, 128)) * 10.0 ** rng.uniform(-6, 0, 128)[None, :]
+    Wm = np.eye(128) + 0.3 * rng.standard_normal((128, 128))
+    dk = np.floor(np.log2(np.linalg.norm(X, axis=0))).astype(np.int64)
+    O = split.update(X, Wm, dk)
+    assert np.array_equal(split.update(X, Wm, dk + 5), O)
+    X2 = X.copy()
+    X2[3] *= 2.0 ** 30
+    W2 = Wm.copy()
+    W2[:, 9] *= 2.0 ** -20
+    O2 = split.update(X2, W2, dk)
+    ref = O.copy()
+    ref[3] *= 2.0 ** 30
+    ref[:, 9] *= 2.0 ** -20
+    assert np.array_equal(O2, ref)
+
+
+@pytest.mark.parametrize("balanced", [False, True])
+def test_update_error_bound(balanced):
+    """Against exact rational dot products: within 5.6 K 2^-55 of the scale
+    2^(E_i + F_j) <= 4 max_k |x_ik 2^-dk_k| max_k |w_kj 2^dk_k|, plus one
+    rounding.  Balancing a graded panel shrinks that scale for the small
+    columns' outputs."""
+    rng = np.random.default_rng(13 + balanced)
+    X = rng.standard_normal((12, 128)) * 10.0 ** rng.uniform(-6, 0, 128)[None, :]
+    Wm = np.eye(128) + 0.3 * rng.standard_normal((128, 128))
+    Wm[:, 7] *= 1e-9
+    dk = np.floor(np.log2(np.linalg.norm(X, axis=0))).astype(np.int64) if balanced else np.zeros(128, np.int64)
+    O = split.update(X, Wm, dk)
+    sx = np.max(np.abs(X) * np.exp2(-dk)[None, :], axis=1)
+    sw = np.max(np.abs(Wm) * np.exp2(dk)[:, None], axis=0)
+    for i in range(0, 12, 3):
+        for j in (0, 7, 50, 127):
+            exact = _exact_dot(X[i], Wm[:, j])
+            bound = 5.6 * 128 * 2.0 ** -55 * 4 * sx[i] * sw[j] + U * abs(O[i, j])
+            assert abs(Fraction(float(O[i, j])) - exact) <= Fraction(bound), (i, j)
+
+
 @pytest.mark.parametrize("name,attr,value", [("drops_d9", "MAX_D", 8), ("wrong_bias", "BIAS", 63 * sum(
     128 ** j for j in range(7)))])
 def test_pins_catch_planted_mistakes(monkeypatch, name, attr, value):
     monkeypatch.setattr(split, attr, value)
     caught = False
-    for test in (test_digits_reconstruct_the_truncated_integer, lambda: test_error_bound(512, 3.0)):
+    for test in (test_digits_reconstruct_the_truncated_integer, lambda: test_error_bound(512, 3.0),
+                 lambda: test_update_error_bound(True)):
         try:
             test()
         except AssertionError:
