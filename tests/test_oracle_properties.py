@@ -1,7 +1,9 @@
-"""Property-based checks of the oracle on random small factors (hypothesis
+"""Property-based checks of the oracle on random small inputs (hypothesis
 draws shapes, signatures, scalings and seeds): every solver form returns the
 HSVD invariants and LAPACK's eigenvalues of G J G^T, and with J = I LAPACK's
-singular values.  CPU only; skipped where hypothesis is not installed."""
+singular values; the symmetric factorisation reproduces M and its inertia;
+the hyperbolic QR satisfies its defining identities.  CPU only; skipped where
+hypothesis is not installed."""
 import numpy as np
 import pytest
 
@@ -63,3 +65,57 @@ def test_identity_signature_gives_lapack_singular_values(orc, fj):
     # LAPACK's SVD is accurate relative to sigma_max (a graded factor's small
     # values carry its normwise error), so compare on that scale
     assert np.max(np.abs(np.sort(r["sigma"])[::-1] - sv)) <= 64 * G.shape[0] * U * sv[0]
+
+
+@st.composite
+def symmetric(draw):
+    n = draw(st.integers(1, 10))
+    seed = draw(st.integers(0, 2 ** 31 - 1))
+    kind = draw(st.sampled_from(["random", "saddle", "graded"]))
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((n, n))
+    M = (A + A.T) / 2
+    if kind == "saddle" and n % 2 == 0:
+        M[: n // 2, : n // 2] = 0.0
+        M[n // 2:, n // 2:] = 0.0
+    if kind == "graded":
+        d = 10.0 ** (-3 * rng.random(n))
+        M = M * d[:, None] * d[None, :]
+    return np.asfortranarray(M)
+
+
+@settings(max_examples=60, deadline=None)
+@given(symmetric())
+def test_symmetric_factorisation_properties(orc, M):
+    """M = G J G^T to rounding, and the signs of J are the inertia of M."""
+    n = M.shape[0]
+    ev = np.linalg.eigvalsh(M)
+    hypothesis.assume(np.min(np.abs(ev)) > 1e-8 * np.max(np.abs(ev)))  # numerically nonsingular
+    G, J, perm, st_ = orc.sym_factor(M)
+    assert st_ == 0
+    R = (G * J.astype(np.float64)[None, :]) @ G.T - M
+    assert np.max(np.abs(R)) <= 100 * n * U * np.max(np.abs(G)) ** 2
+    assert int((J > 0).sum()) == int((ev > 0).sum())
+    assert sorted(perm.tolist()) == list(range(n))
+
+
+@settings(max_examples=60, deadline=None)
+@given(st.integers(1, 8), st.integers(0, 6), st.integers(0, 2 ** 31 - 1))
+def test_hyperbolic_qr_properties(orc, m, extra, seed):
+    """T A C = [R; 0] and T^T Jh T = J, with T formed explicitly, R upper
+    triangular, Jh a permutation of J, whenever the factorisation exists."""
+    n = m + extra
+    rng = np.random.default_rng(seed)
+    A = np.asfortranarray(rng.standard_normal((n, m)))
+    J = np.where(rng.random(n) < 0.5, 1, -1).astype(np.int8)
+    q = orc.hyp_qr(A, J)
+    assert q["status"] in (0, orc.ORC_RANK)
+    hypothesis.assume(q["status"] == 0)
+    T = orc.hyp_qr_apply_tt(q, np.eye(n)).T
+    R, Jh = q["R"], q["Jh"].astype(np.float64)
+    nt = max(1.0, float(np.max(np.abs(T))))
+    assert np.max(np.abs(T @ A[:, q["cperm"]] - np.vstack([R, np.zeros((n - m, m))]))) <= 64 * n * U * nt * np.max(
+        np.abs(A))
+    assert np.max(np.abs(T.T @ (Jh[:, None] * T) - np.diag(J.astype(np.float64)))) <= 64 * n * U * nt ** 2
+    assert np.array_equal(np.tril(R, -1), np.zeros((m, m)))
+    assert sorted(q["Jh"].tolist()) == sorted(J.tolist())
