@@ -89,11 +89,11 @@
  *       count includes the sweep that stopped.
  *   R15 Sec. 1 names the hyperbolic QR factorisation of G^T for a wide G but
  *       does not define it.  Here: J-orthogonal Householder reflectors
- *       I - beta v v^T S, the column with the largest |J-norm^2| of its
- *       trailing part pivoted first, a row interchange when the pivot row's
- *       sign is not that of the J-norm^2, and 1 x 1 pivots only (a zero
- *       J-norm^2 in every trailing column is reported as ORC_RANK; Singer's
- *       2 x 2 pivots are not built).  With J = I this is Householder QR with
+ *       I - beta v v^T S, pivots chosen on the trailing J-Gram by the
+ *       Bunch-Parlett rule (1 x 1 on the largest |J-norm^2|, else a 2 x 2
+ *       block reduced through z = x +- y and then y), a row interchange when
+ *       the pivot row's sign is not that of the reduced J-norm^2.  A zero
+ *       trailing J-Gram is ORC_RANK.  With J = I this is Householder QR with
  *       column pivoting on the largest trailing norm.
  */
 #include <math.h>
@@ -928,30 +928,95 @@ int orc_sym_factor(int64_t n64, const double *M, int64_t ldm, double *G, int64_t
 /* orc_hyp_qr -- hyperbolic QR of a tall A (n x m, n >= m) with signature J  */
 /* (Sec. 1: a factor G whose transpose is tall is shortened by the           */
 /* hyperbolic QR of G^T; the HSVD then runs on the square R^T).  Reading    */
-/* R15: J-orthogonal Householder reflectors H = I - beta v v^T S with       */
-/* S the current signature, 1 x 1 pivots only:                              */
-/*   step k: the trailing column with the largest |gamma_j|,               */
-/*     gamma_j = sum_{i >= k} S_i A_ij^2, moves to position k;             */
-/*   if S_k differs from sign(gamma), row k is interchanged with the row   */
-/*     i > k of that sign with the largest |A_ik| (ties: smallest i);      */
-/*   alpha = -sign(x_k) sqrt|gamma| (the J-norm is kept: alpha^2 S_k =     */
-/*     gamma), v = x - alpha e_k, v^T S v = 2 S_k sqrt|gamma| (sqrt|gamma| */
-/*     + |x_k|), beta = 2 / v^T S v, and every later column y becomes     */
-/*     y - beta v (v^T S y).                                                */
+/* R15: J-orthogonal Householder reflectors H = I - beta v v^T S with S the */
+/* current signature, pivots chosen on the trailing J-Gram C = X^T S X (X   */
+/* the trailing rows k..n-1 of the remaining columns) by the Bunch-Parlett   */
+/* rule, alpha = (1 + sqrt 17) / 8:                                          */
+/*   1 x 1 (the largest |C_jj| >= alpha times the largest |C_ij|, i != j):  */
+/*     that column moves to position k and is reduced to R_kk e_k;          */
+/*   2 x 2 otherwise: the columns x, y of the largest |C_ij| move to k, k+1; */
+/*     z = x + tau y (tau = +-1 so that |z^T S z| = |C_xx + C_yy| + 2|C_xy|) */
+/*     is reduced at row k, then y's rows k+1.. at row k+1, each reflector  */
+/*     applied to every remaining column, x included; R gets a full 2 x 2   */
+/*     diagonal block.                                                       */
+/* A reduction of a vector z at row k: if S_k is not sign(gamma), gamma =   */
+/* z^T S z over rows k.., row k is interchanged with the row i > k of that   */
+/* sign with the largest |z_i| (ties: smallest i); then alpha = -sign(z_k)  */
+/* sqrt|gamma| (the J-norm is kept: alpha^2 S_k = gamma), v = z - alpha e_k, */
+/* v^T S v = 2 S_k sqrt|gamma| (sqrt|gamma| + |z_k|), beta = 2 / v^T S v.   */
 /* With T = H_{m-1} P_{m-1} ... H_0 P_0 (P_k the row interchanges) and C   */
 /* the column permutation:  T A C = [R; 0],  T^T Jh T = J  (Jh = J after   */
 /* the interchanges), so A C = Q [R; 0] with Q = T^-1 and Q^T J Q = Jh,   */
 /* and C^T (A^T J A) C = R^T Jh_1 R with Jh_1 the first m entries of Jh.   */
-/* A zero gamma (a trailing J-Gram with a zero diagonal, where Singer's     */
-/* 2 x 2 pivots would be needed) returns ORC_RANK.                          */
-/* Outputs: R (m x m, ldr; zero below the diagonal), Jh (n signs), cperm    */
-/* (m: the original column at each position), and, each may be NULL, the   */
+/* A zero trailing J-Gram (A^T J A singular) returns ORC_RANK.  With J = I  */
+/* every pivot is 1 x 1 and this is Householder QR with column pivoting.    */
+/* Outputs: R (m x m, ldr; block upper triangular), Jh (n signs), cperm (m: */
+/* the original column at each position), and, each may be NULL, the       */
 /* reflectors V (n x m, ldv; v_k in rows k..n-1 of column k in the row      */
-/* order of step k, zero above), beta (m) and rswap (m: the row             */
-/* interchanged with row k at step k).                                      */
+/* order of step k, zero above), beta (m), rswap (m: the row interchanged    */
+/* with row k at step k) and bsize (m: 1 for a 1 x 1 pivot, 2 and 0 for the  */
+/* two positions of a 2 x 2 pivot).                                          */
 /* ------------------------------------------------------------------------ */
+static double hq_sdot(int n, int k, const int8_t *s, const double *x, const double *y)
+{
+    double acc = 0.0;
+    for (int i = k; i < n; ++i) acc += s[i] > 0 ? x[i] * y[i] : -(x[i] * y[i]);
+    return acc;
+}
+
+static void hq_swap_cols(int n, double *W, int a, int b)
+{
+    if (a == b) return;
+    for (int i = 0; i < n; ++i) {
+        const double t = W[i + (int64_t)a * n];
+        W[i + (int64_t)a * n] = W[i + (int64_t)b * n];
+        W[i + (int64_t)b * n] = t;
+    }
+}
+
+/* reduce z (rows k..n-1, a work vector) at row k: the row interchange, then */
+/* the reflector applied to the columns c0..m-1 of W                         */
+static int hq_reduce(int n, int m, double *W, int8_t *s, double *z, int k, int c0, double *v,
+                     double *alpha_out, double *beta_out, int *rswap_out)
+{
+    const double gamma = hq_sdot(n, k, s, z, z);
+    if (!(gamma != 0.0)) return ORC_RANK;
+    const int8_t sg = gamma > 0.0 ? 1 : -1;
+    int ip = k;
+    if (s[k] != sg) {
+        double xbest = -1.0;
+        for (int i = k + 1; i < n; ++i)
+            if (s[i] == sg && fabs(z[i]) > xbest) { xbest = fabs(z[i]); ip = i; }
+        if (ip == k) return ORC_RANK; /* cannot happen for gamma != 0 */
+        for (int j = 0; j < m; ++j) {
+            const double t = W[k + (int64_t)j * n];
+            W[k + (int64_t)j * n] = W[ip + (int64_t)j * n];
+            W[ip + (int64_t)j * n] = t;
+        }
+        const double tz = z[k]; z[k] = z[ip]; z[ip] = tz;
+        const int8_t t = s[k]; s[k] = s[ip]; s[ip] = t;
+    }
+    *rswap_out = ip;
+    const double root = sqrt(fabs(gamma));
+    const double alpha = z[k] >= 0.0 ? -root : root;
+    for (int i = 0; i < n; ++i) v[i] = i < k ? 0.0 : z[i];
+    v[k] = z[k] - alpha;
+    const double vsv = 2.0 * (double)s[k] * root * (root + fabs(z[k]));
+    const double beta = 2.0 / vsv;
+    for (int j = c0; j < m; ++j) {
+        double *y = W + (int64_t)j * n;
+        double vsy = 0.0;
+        for (int i = k; i < n; ++i) vsy += s[i] > 0 ? v[i] * y[i] : -(v[i] * y[i]);
+        const double f = beta * vsy;
+        for (int i = k; i < n; ++i) y[i] -= f * v[i];
+    }
+    *alpha_out = alpha;
+    *beta_out = beta;
+    return ORC_OK;
+}
+
 int orc_hyp_qr(int64_t n64, int64_t m64, const double *A, int64_t lda, const int8_t *J, double *R, int64_t ldr,
-               int8_t *Jh, int *cperm, double *Vr, int64_t ldv, double *beta_out, int *rswap_out)
+               int8_t *Jh, int *cperm, double *Vr, int64_t ldv, double *beta_out, int *rswap_out, int *bsize_out)
 {
     if (m64 < 1 || n64 < m64 || lda < n64 || ldr < m64 || n64 > (1 << 24)) return ORC_ARG;
     if (Vr && ldv < n64) return ORC_ARG;
@@ -961,8 +1026,12 @@ int orc_hyp_qr(int64_t n64, int64_t m64, const double *A, int64_t lda, const int
     if (!all_finite(n, m, A, lda)) return ORC_NONFINITE;
     double *W = (double *)malloc(sizeof(double) * (size_t)n * m);
     double *v = (double *)malloc(sizeof(double) * (size_t)n);
+    double *z = (double *)malloc(sizeof(double) * (size_t)n);
+    double *bt = (double *)malloc(sizeof(double) * (size_t)m);
     int8_t *s = (int8_t *)malloc((size_t)n);
     int *cp = (int *)malloc(sizeof(int) * (size_t)m);
+    int *rs = (int *)malloc(sizeof(int) * (size_t)m);
+    int *bs = (int *)malloc(sizeof(int) * (size_t)m);
     for (int j = 0; j < m; ++j) {
         cp[j] = j;
         for (int i = 0; i < n; ++i) W[i + (int64_t)j * n] = A[i + (int64_t)j * lda];
@@ -971,72 +1040,79 @@ int orc_hyp_qr(int64_t n64, int64_t m64, const double *A, int64_t lda, const int
     if (Vr)
         for (int j = 0; j < m; ++j)
             for (int i = 0; i < n; ++i) Vr[i + (int64_t)j * ldv] = 0.0;
+    const double alpha_bp = (1.0 + sqrt(17.0)) / 8.0;
     int status = ORC_OK;
-    for (int k = 0; k < m && status == ORC_OK; ++k) {
-        /* column pivot: the largest |gamma_j| over the trailing columns */
-        int jp = -1;
-        double gbest = -1.0, gamma = 0.0;
+    int k = 0;
+    while (k < m && status == ORC_OK) {
+        /* the trailing J-Gram: largest |diagonal| and |off-diagonal| entries */
+        int jp = -1, pr = -1, pq = -1;
+        double gbest = -1.0, obest = -1.0;
         for (int j = k; j < m; ++j) {
-            double g = 0.0;
-            for (int i = k; i < n; ++i) {
-                const double w = W[i + (int64_t)j * n];
-                g += s[i] > 0 ? w * w : -(w * w);
+            const double *xj = W + (int64_t)j * n;
+            const double g = hq_sdot(n, k, s, xj, xj);
+            if (fabs(g) > gbest) { gbest = fabs(g); jp = j; }
+            for (int i = k; i < j; ++i) {
+                const double o = fabs(hq_sdot(n, k, s, W + (int64_t)i * n, xj));
+                if (o > obest) { obest = o; pr = i; pq = j; }
             }
-            if (fabs(g) > gbest) { gbest = fabs(g); jp = j; gamma = g; }
         }
-        if (!(gbest > 0.0)) { status = ORC_RANK; break; }
-        if (jp != k) {
-            for (int i = 0; i < n; ++i) {
-                const double t = W[i + (int64_t)k * n];
-                W[i + (int64_t)k * n] = W[i + (int64_t)jp * n];
-                W[i + (int64_t)jp * n] = t;
-            }
-            const int t = cp[k]; cp[k] = cp[jp]; cp[jp] = t;
-        }
-        double *x = W + (int64_t)k * n;
-        /* row interchange when the sign at row k is not that of gamma */
-        const int8_t sg = gamma > 0.0 ? 1 : -1;
+        double alpha = 0.0, beta = 0.0;
         int ip = k;
-        if (s[k] != sg) {
-            double xbest = -1.0;
-            for (int i = k + 1; i < n; ++i)
-                if (s[i] == sg && fabs(x[i]) > xbest) { xbest = fabs(x[i]); ip = i; }
-            if (ip == k) { status = ORC_RANK; break; } /* cannot happen for gamma != 0 */
-            for (int j = 0; j < m; ++j) {
-                const double t = W[k + (int64_t)j * n];
-                W[k + (int64_t)j * n] = W[ip + (int64_t)j * n];
-                W[ip + (int64_t)j * n] = t;
-            }
-            const int8_t t = s[k]; s[k] = s[ip]; s[ip] = t;
+        if (k == m - 1 || !(obest > 0.0) || gbest >= alpha_bp * obest) {
+            if (!(gbest > 0.0)) { status = ORC_RANK; break; }
+            hq_swap_cols(n, W, k, jp);
+            { const int t = cp[k]; cp[k] = cp[jp]; cp[jp] = t; }
+            double *x = W + (int64_t)k * n;
+            for (int i = 0; i < n; ++i) z[i] = i < k ? 0.0 : x[i];
+            status = hq_reduce(n, m, W, s, z, k, k, v, &alpha, &beta, &ip);
+            if (status != ORC_OK) break;
+            x[k] = alpha;
+            for (int i = k + 1; i < n; ++i) x[i] = 0.0;
+            bt[k] = beta; rs[k] = ip; bs[k] = 1;
+            if (Vr)
+                for (int i = k; i < n; ++i) Vr[i + (int64_t)k * ldv] = v[i];
+            k += 1;
+        } else {
+            /* columns pr < pq to positions k, k + 1 */
+            hq_swap_cols(n, W, k, pr);
+            { const int t = cp[k]; cp[k] = cp[pr]; cp[pr] = t; }
+            const int q2 = pq == k ? pr : pq;
+            hq_swap_cols(n, W, k + 1, q2);
+            { const int t = cp[k + 1]; cp[k + 1] = cp[q2]; cp[q2] = t; }
+            double *x = W + (int64_t)k * n, *y = W + (int64_t)(k + 1) * n;
+            const double gx = hq_sdot(n, k, s, x, x), gy = hq_sdot(n, k, s, y, y), d = hq_sdot(n, k, s, x, y);
+            const double tau = ((gx + gy >= 0.0) == (d >= 0.0)) ? 1.0 : -1.0;
+            for (int i = 0; i < n; ++i) z[i] = i < k ? 0.0 : x[i] + tau * y[i];
+            status = hq_reduce(n, m, W, s, z, k, k, v, &alpha, &beta, &ip);
+            if (status != ORC_OK) break;
+            bt[k] = beta; rs[k] = ip; bs[k] = 2;
+            if (Vr)
+                for (int i = k; i < n; ++i) Vr[i + (int64_t)k * ldv] = v[i];
+            for (int i = 0; i < n; ++i) z[i] = i <= k ? 0.0 : y[i];
+            double alpha2 = 0.0;
+            status = hq_reduce(n, m, W, s, z, k + 1, k, v, &alpha2, &beta, &ip);
+            if (status != ORC_OK) break;
+            bt[k + 1] = beta; rs[k + 1] = ip; bs[k + 1] = 0;
+            if (Vr)
+                for (int i = k + 1; i < n; ++i) Vr[i + (int64_t)(k + 1) * ldv] = v[i];
+            y[k + 1] = alpha2;
+            for (int i = k + 2; i < n; ++i) { x[i] = 0.0; y[i] = 0.0; }
+            k += 2;
         }
-        if (rswap_out) rswap_out[k] = ip;
-        /* the reflector */
-        const double root = sqrt(fabs(gamma));
-        const double alpha = x[k] >= 0.0 ? -root : root;
-        for (int i = 0; i < n; ++i) v[i] = i < k ? 0.0 : x[i];
-        v[k] = x[k] - alpha;
-        const double vsv = 2.0 * (double)s[k] * root * (root + fabs(x[k]));
-        const double beta = 2.0 / vsv;
-        if (beta_out) beta_out[k] = beta;
-        if (Vr)
-            for (int i = k; i < n; ++i) Vr[i + (int64_t)k * ldv] = v[i];
-        for (int j = k + 1; j < m; ++j) {
-            double *y = W + (int64_t)j * n;
-            double vsy = 0.0;
-            for (int i = k; i < n; ++i) vsy += s[i] > 0 ? v[i] * y[i] : -(v[i] * y[i]);
-            const double f = beta * vsy;
-            for (int i = k; i < n; ++i) y[i] -= f * v[i];
-        }
-        x[k] = alpha;
-        for (int i = k + 1; i < n; ++i) x[i] = 0.0;
     }
     if (status == ORC_OK) {
         for (int j = 0; j < m; ++j)
-            for (int i = 0; i < m; ++i) R[i + (int64_t)j * ldr] = i <= j ? W[i + (int64_t)j * n] : 0.0;
+            for (int i = 0; i < m; ++i)
+                R[i + (int64_t)j * ldr] = (i <= j || (i == j + 1 && bs[j] == 2)) ? W[i + (int64_t)j * n] : 0.0;
         for (int i = 0; i < n; ++i) Jh[i] = s[i];
         for (int j = 0; j < m; ++j) cperm[j] = cp[j];
+        for (int j = 0; j < m; ++j) {
+            if (beta_out) beta_out[j] = bt[j];
+            if (rswap_out) rswap_out[j] = rs[j];
+            if (bsize_out) bsize_out[j] = bs[j];
+        }
     }
-    free(W); free(v); free(s); free(cp);
+    free(W); free(v); free(z); free(bt); free(s); free(cp); free(rs); free(bs);
     return status;
 }
 
@@ -1100,7 +1176,7 @@ int orc_wide_hsvd(int64_t m64, int64_t n64, const double *G, int64_t ldg, const 
     int8_t *Jh = (int8_t *)malloc((size_t)n);
     for (int i = 0; i < m; ++i)
         for (int j = 0; j < n; ++j) A[j + (int64_t)i * n] = G[i + (int64_t)j * ldg];
-    int status = orc_hyp_qr(n, m, A, n, J, R, m, Jh, cperm, Vr, n, beta, rswap);
+    int status = orc_hyp_qr(n, m, A, n, J, R, m, Jh, cperm, Vr, n, beta, rswap, NULL);
     if (status == ORC_OK) {
         for (int j = 0; j < m; ++j)
             for (int l = 0; l < m; ++l) F[cperm[j] + (int64_t)l * m] = R[l + (int64_t)j * m];

@@ -82,7 +82,7 @@ def _bind(lib):
     lib.orc_block_hsvd.restype = _int
     lib.orc_sym_factor.argtypes = [_i64, _p, _i64, _p, _i64, _p, _p]
     lib.orc_sym_factor.restype = _int
-    lib.orc_hyp_qr.argtypes = [_i64, _i64, _p, _i64, _p, _p, _i64, _p, _p, _p, _i64, _p, _p]
+    lib.orc_hyp_qr.argtypes = [_i64, _i64, _p, _i64, _p, _p, _i64, _p, _p, _p, _i64, _p, _p, _p]
     lib.orc_hyp_qr.restype = _int
     lib.orc_hyp_qr_apply_tt.argtypes = [_i64, _i64, _p, _i64, _p, _p, _p, _p, _i64, _i64]
     lib.orc_hyp_qr_apply_tt.restype = _int
@@ -212,9 +212,10 @@ def sym_factor(M, lib=None):
 
 def hyp_qr(A, J, lib=None):
     """Hyperbolic QR of a tall A (n x m) with signature J (n): a dict with R
-    (m x m), Jh (n signs after the row interchanges), cperm (the original
-    column at each position), the reflectors refl (n x m), beta and rswap,
-    and status.  T A[:, cperm] = [R; 0] with T^T diag(Jh) T = diag(J)."""
+    (m x m, block upper triangular), Jh (n signs after the row interchanges),
+    cperm (the original column at each position), the reflectors refl
+    (n x m), beta, rswap, bsize (1, or 2 and 0 for a 2 x 2 pivot) and status.
+    T A[:, cperm] = [R; 0] with T^T diag(Jh) T = diag(J)."""
     A = _fcol(A)
     n, m = A.shape
     j = _signs(J, n)
@@ -224,9 +225,10 @@ def hyp_qr(A, J, lib=None):
     refl = np.zeros((n, m), order="F")
     beta = np.zeros(m)
     rswap = np.zeros(m, dtype=np.int32)
+    bsize = np.zeros(m, dtype=np.int32)
     st = (lib or _load()).orc_hyp_qr(n, m, _ptr(A), n, _ptr(j), _ptr(R), m, _ptr(Jh), _ptr(cperm), _ptr(refl), n,
-                                     _ptr(beta), _ptr(rswap))
-    return dict(R=R, Jh=Jh, cperm=cperm, refl=refl, beta=beta, rswap=rswap, status=st)
+                                     _ptr(beta), _ptr(rswap), _ptr(bsize))
+    return dict(R=R, Jh=Jh, cperm=cperm, refl=refl, beta=beta, rswap=rswap, bsize=bsize, status=st)
 
 
 def hyp_qr_apply_tt(qr, X, lib=None):

@@ -95,9 +95,44 @@ def test_two_by_one_by_hand(orc):
         assert np.max(np.abs(T.T @ np.diag(Jh) @ T - np.diag(Jc))) <= 32 * U * np.max(np.abs(T)) ** 2
 
 
+def test_two_by_two_pivot_by_hand(orc):
+    """A = [[1, 1], [1, -1]], J = diag(1, -1): both columns have J-norm^2 0
+    and A^T J A = [[0, 2], [2, 0]] is nonsingular, so the only pivot is a
+    2 x 2 block: R^T Jh_1 R = [[0, 2], [2, 0]] and Jh_1 has one sign of each
+    kind (the eigenvalues are +-2)."""
+    A = np.array([[1.0, 1.0], [1.0, -1.0]])
+    J = np.array([1, -1], dtype=np.int8)
+    q = orc.hyp_qr(A, J)
+    assert q["status"] == 0 and list(q["bsize"]) == [2, 0]
+    R, Jh = q["R"], _signed(q["Jh"])
+    C = np.eye(2)[:, q["cperm"]]
+    M = A.T @ np.diag(_signed(J)) @ A
+    assert np.max(np.abs(R.T @ np.diag(Jh) @ R - C.T @ M @ C)) <= 16 * U
+    assert sorted(q["Jh"].tolist()) == [-1, 1]
+    r = orc.wide_hsvd(A.T, J, 4 * U, 20)
+    assert r["status"] == 0
+    assert np.allclose(np.sort(r["sigma"] ** 2 * r["Jout"]), [-2.0, 2.0], rtol=1e-15, atol=0)
+
+
+def test_saddle_tall_factors_need_two_by_two_pivots(orc):
+    """A = [B; B'] with J = diag(I, -I) and B' = B + a small perturbation:
+    every column's J-norm^2 is small against the J-inner products, so 2 x 2
+    pivots carry the factorisation, and the identities and the inertia
+    hold."""
+    rng = np.random.default_rng(5)
+    B = rng.standard_normal((10, 6))
+    A = np.asfortranarray(np.vstack([B, B + 0.3 * rng.standard_normal((10, 6))]))
+    J = np.array([1] * 10 + [-1] * 10, dtype=np.int8)
+    q, e1, e2, e3 = _identity_errors(orc, A, J)
+    assert max(e1, e2, e3) <= 64 * U
+    ev = np.linalg.eigvalsh(A.T @ (_signed(J)[:, None] * A))
+    assert int(np.sum(q["Jh"][:6] > 0)) == int(np.sum(ev > 0))
+    assert 2 in q["bsize"].tolist()
+
+
 def test_breakdown_and_argument_errors(orc):
-    """A column with zero J-norm^2 and nothing else to pivot is the 1 x 1
-    pivot's breakdown: ORC_RANK.  NaN, a bad sign, n < m are refused."""
+    """A zero trailing J-Gram (A^T J A singular, here 0) is ORC_RANK.  NaN, a
+    bad sign, n < m are refused."""
     J = np.array([1, -1], dtype=np.int8)
     assert orc.hyp_qr(np.array([[1.0], [1.0]]), J)["status"] == orc.ORC_RANK
     assert orc.hyp_qr(np.array([[1.0], [np.nan]]), J)["status"] == orc.ORC_NONFINITE
@@ -110,12 +145,16 @@ def test_defining_identities_and_inertia(orc, n, m, p):
     A, J = _tall(n, m, p, seed=n * 100 + m + p)
     q, e1, e2, e3 = _identity_errors(orc, A, J)
     assert e1 <= 16 * U and e2 <= 16 * U and e3 <= 16 * U, (e1, e2, e3)
-    R = q["R"]
-    assert np.array_equal(np.tril(R, -1), np.zeros((m, m)))
-    # Jh is J permuted; the first pivot has the largest |J-norm^2| of A's columns
+    R, bs = q["R"], q["bsize"]
+    # block upper triangular: 1 x 1 pivots, and 2 x 2 blocks marked (2, 0)
+    for j in range(m):
+        assert bs[j] in (1, 2, 0) and (bs[j] != 0 or (j > 0 and bs[j - 1] == 2))
+        assert np.all(R[j + (2 if bs[j] == 2 else 1):, j] == 0.0)
+    # Jh is J permuted; a first 1 x 1 pivot has the largest |J-norm^2| of A's columns
     assert sorted(q["Jh"].tolist()) == sorted(J.tolist())
     g = np.einsum("ij,i,ij->j", A, _signed(J), A)
-    assert abs(R[0, 0] ** 2 - np.max(np.abs(g))) <= 8 * n * U * np.max(np.abs(A)) ** 2
+    if bs[0] == 1:
+        assert abs(R[0, 0] ** 2 - np.max(np.abs(g))) <= 8 * n * U * np.max(np.abs(A)) ** 2
     # Sylvester: the signs of R^T Jh_1 R are those of A^T J A's eigenvalues
     ev = np.linalg.eigvalsh(A.T @ (_signed(J)[:, None] * A))
     assert int(np.sum(q["Jh"][:m] > 0)) == int(np.sum(ev > 0))
@@ -171,8 +210,10 @@ def test_square_factor_agrees_with_direct_hsvd(orc):
 MUTANTS = {
     "beta_sign": ("const double beta = 2.0 / vsv;", "const double beta = -2.0 / vsv;"),
     "no_row_interchange": ("if (s[k] != sg) {", "if (0) {"),
-    "alpha_sign": ("const double alpha = x[k] >= 0.0 ? -root : root;",
-                   "const double alpha = x[k] >= 0.0 ? root : -root;"),
+    "alpha_sign": ("const double alpha = z[k] >= 0.0 ? -root : root;",
+                   "const double alpha = z[k] >= 0.0 ? root : -root;"),
+    "two_by_two_second_reflector_skips_x": ("status = hq_reduce(n, m, W, s, z, k + 1, k, v, &alpha2, &beta, &ip);",
+                                            "status = hq_reduce(n, m, W, s, z, k + 1, k + 1, v, &alpha2, &beta, &ip);"),
     "update_plain_inner_product": ("for (int i = k; i < n; ++i) vsy += s[i] > 0 ? v[i] * y[i] : -(v[i] * y[i]);",
                                    "for (int i = k; i < n; ++i) vsy += v[i] * y[i];"),
     "apply_tt_drops_signature": ("for (int i = k; i < n; ++i) y[i] -= s[i] > 0 ? f * v[i] : -(f * v[i]);",
@@ -198,7 +239,7 @@ def _battery(orc, lib):
     q = orc.hyp_qr(np.array([[1.0], [3.0]]), np.array([1, -1], dtype=np.int8), lib=lib)
     if q["status"] != 0 or abs(q["R"][0, 0] + np.sqrt(8.0)) > 1e-15 or list(q["Jh"]) != [-1, 1]:
         failed.append("hand")
-    for n, m, p in ((20, 8, 9), (30, 12, 25)):
+    for n, m, p in ((20, 8, 9), (30, 12, 25), (16, 8, 8)):
         A, J = _tall(n, m, p, seed=n + m)
         try:
             _, e1, e2, e3 = _identity_errors(orc, A, J, lib=lib)

@@ -102,8 +102,9 @@ def test_symmetric_factorisation_properties(orc, M):
 @settings(max_examples=60, deadline=None)
 @given(st.integers(1, 8), st.integers(0, 6), st.integers(0, 2 ** 31 - 1))
 def test_hyperbolic_qr_properties(orc, m, extra, seed):
-    """T A C = [R; 0] and T^T Jh T = J, with T formed explicitly, R upper
-    triangular, Jh a permutation of J, whenever the factorisation exists."""
+    """T A C = [R; 0] and T^T Jh T = J, with T formed explicitly, R block
+    upper triangular, Jh a permutation of J, whenever the factorisation
+    exists."""
     n = m + extra
     rng = np.random.default_rng(seed)
     A = np.asfortranarray(rng.standard_normal((n, m)))
@@ -117,5 +118,7 @@ def test_hyperbolic_qr_properties(orc, m, extra, seed):
     assert np.max(np.abs(T @ A[:, q["cperm"]] - np.vstack([R, np.zeros((n - m, m))]))) <= 64 * n * U * nt * np.max(
         np.abs(A))
     assert np.max(np.abs(T.T @ (Jh[:, None] * T) - np.diag(J.astype(np.float64)))) <= 64 * n * U * nt ** 2
-    assert np.array_equal(np.tril(R, -1), np.zeros((m, m)))
+    bs = q["bsize"]
+    for j in range(m):  # block upper triangular: 1 x 1 pivots and 2 x 2 blocks (2, 0)
+        assert np.all(R[j + (2 if bs[j] == 2 else 1):, j] == 0.0)
     assert sorted(q["Jh"].tolist()) == sorted(J.tolist())
