@@ -2,7 +2,8 @@
 draws shapes, signatures, scalings and seeds): every solver form returns the
 HSVD invariants and LAPACK's eigenvalues of G J G^T, and with J = I LAPACK's
 singular values; the symmetric factorisation reproduces M and its inertia;
-the hyperbolic QR satisfies its defining identities.  CPU only; skipped where
+the hyperbolic QR satisfies its defining identities; the split-precision
+Gram model stays within its error bound.  CPU only; skipped where
 hypothesis is not installed."""
 import numpy as np
 import pytest
@@ -122,3 +123,28 @@ def test_hyperbolic_qr_properties(orc, m, extra, seed):
     for j in range(m):  # block upper triangular: 1 x 1 pivots and 2 x 2 blocks (2, 0)
         assert np.all(R[j + (2 if bs[j] == 2 else 1):, j] == 0.0)
     assert sorted(q["Jh"].tolist()) == sorted(J.tolist())
+
+
+@settings(max_examples=40, deadline=None)
+@given(st.integers(1, 600), st.integers(0, 2 ** 31 - 1), st.sampled_from([0.0, 3.0, 8.0]))
+def test_split_gram_within_its_bound(rows, seed, spread):
+    """The split-precision Gram model on random windows: symmetric, and each
+    entry within 5.6 K 2^-55 2^(E_i + E_j) per window (plus the roundings) of
+    the exact dot product."""
+    from fractions import Fraction
+
+    from oracle import split
+
+    rng = np.random.default_rng(seed)
+    P = rng.standard_normal((rows, 4)) * 10.0 ** rng.uniform(-spread, spread, size=(rows, 4))
+    A = split.gram(P)
+    assert np.array_equal(A, A.T)
+    for i in range(4):
+        for j in range(i, 4):
+            exact = sum(Fraction(float(a)) * Fraction(float(b)) for a, b in zip(P[:, i], P[:, j]))
+            bound = 2 * U * abs(A[i, j])
+            for r0 in range(0, rows, split.WINDOW):
+                w = P[r0:r0 + split.WINDOW]
+                E = split.column_exponents(w)
+                bound += 5.6 * w.shape[0] * 2.0 ** -55 * 2.0 ** int(E[i] + E[j]) + 2 * U * abs(float(w[:, i] @ w[:, j]))
+            assert abs(Fraction(float(A[i, j])) - exact) <= Fraction(bound)
