@@ -45,8 +45,7 @@
  *                         HSVD of the square R^T, then V premultiplied by the
  *                         transformation).
  *
- * Readings of the paper where it is silent or garbled (also listed in the
- * design notes of the repository):
+ * Readings of the paper where it is silent or garbled:
  *   R1  theta as printed in Sec. 2 has the sign of `hyp' flipped against the
  *       update of Alg. 4.5; requiring a'_ij = 0 under that update gives
  *       theta = 2 a_ij / (-a_ii - hyp a_jj).  Eq. 2.6 agrees with this form.

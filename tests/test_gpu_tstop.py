@@ -70,9 +70,10 @@ def _oracle(G, J, tol, form, tstop):
 def test_paper_threshold_matches_oracle(api, form, case):
     """eps = 2^-52 in Eq. 2.3, T = T_eps: the threshold ends the iteration
     before the plain stop, on the GPU as in the oracle, with the same values.
-    The split-precision products carry an error of about K 2^-53 of the
-    column norms (reading R12), so at this eps the plain stop may never come
-    for them; the threshold still does."""
+    The split-precision products carry an error of up to about 1.4 K 2^-53
+    of the column scales (the truncated digits and the dropped slice
+    products), so at this eps the plain stop may never come for them; the
+    threshold still does."""
     n = 128 if form == "pointwise" else 256  # the pointwise factor must fit one SM
     if case == "paper":
         G, J, _ = W.paper(n, p=n // 2, seed=20 + n)

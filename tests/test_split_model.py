@@ -1,5 +1,7 @@
 """Pins for the exact CPU models of the split-precision Gram and update (the
-BF16x8 form, reading R12), against what is fixed outside them: exact rational
+BF16x8 form: 55-bit truncation, balanced base-128 digits, the slice products
+with k + l <= 9 summed exactly, one rounding), against what is fixed outside
+them: exact rational
 dot products (Python fractions), the digit identity V = sum q_k 128^(8-k),
 inputs whose digits the kept products cover completely (then the model is
 the exact dot product rounded once), the error bound of the dropped products
