@@ -4,7 +4,9 @@ Test infrastructure only: the tests, ``__graft_entry__.smoke()`` and the CPU
 baseline leg of ``bench.py`` import it.  The library path never does; the two
 share no code.  ``hsvd_oracle.c`` holds the arithmetic, ``oracle.py`` the
 ctypes marshalling and its build step; ``mlp.py`` models the learned form's
-network and ``split.py`` the split-precision Gram exactly, both in numpy.
+network and ``split.py`` the split-precision Gram exactly, both in numpy;
+``inner_model.c`` / ``inner_model.py`` model the library's inner-solve
+kernels exactly (a model of the kernels, not the oracle).
 """
 from .oracle import (  # noqa: F401
     ORC_ARG,

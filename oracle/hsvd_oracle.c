@@ -27,9 +27,10 @@
  *                         early stop at the tangent threshold T_eps (Sec. 2)
  *                         through the convergence statistic of Eq. 4.2.
  *   orc_inner_solve    -- J-orthogonalisation of one 2b x 2b pivot block A_P by
- *                         two-sided rotations (Sec. 5 block-oriented method,
- *                         Sec. 6 full-block variant), pair order taken from the
- *                         modulus strategy applied inside the block.
+ *                         rotations applied one at a time as R^T A R (Sec. 5
+ *                         block-oriented method, Sec. 6 full-block variant),
+ *                         row-cyclic inner order (Sec. 5) or, on request, the
+ *                         pairs of the parallel strategy (R9).
  *   orc_sym_factor     -- symmetric indefinite factorisation M = G J G^T with
  *                         complete (Bunch-Parlett) pivoting (Sec. 1: M given
  *                         explicitly is factored first).
@@ -69,10 +70,13 @@
  *       pair rotates (Sec. 2 stopping rule).
  *   R7  Inside a pivot block the diagonal is carried by Eq. 2.6 (as Sec. 4
  *       carries d for the pointwise method) rather than recomputed.
- *   R8  The paper leaves the order of the two one-sided halves of R^T A R on
- *       a pivot block open; here they alternate from inner step to inner step
- *       (column half first on even steps, row half first on odd steps), which
- *       lets a distributed implementation transpose once per step.
+ *   R9  Inner pair order.  Sec. 5 gives the block-oriented method a
+ *       row-cyclic inner order, one rotation at a time; that is the default
+ *       (order 0).  Order 1 takes the pairs of the parallel strategy of
+ *       Sec. 2 (modified modulus over the 2b indices of the block; for the
+ *       cross pass k paired with b + ((k + s) mod b) at step s), still one
+ *       rotation at a time, so that a parallel implementation can be
+ *       compared with it pair for pair.
  *   R6  A pair with a_ij == 0 exactly is orthogonal and is never rotated (the
  *       strict test of Eq. 2.3 would otherwise "rotate" a zero column by the
  *       identity for ever).  A zero column (sigma_j = 0) is rank deficiency,
@@ -449,149 +453,121 @@ done:
 /* ------------------------------------------------------------------------ */
 /* Inner solve: J-orthogonalisation of a pivot block A_P (nn x nn, nn even,   */
 /* symmetric on entry, column-major, ld = nn) with signs sgn[nn] (Sec. 5      */
-/* block method, Sec. 6 full-block variant).  One inner step takes the        */
-/* disjoint pairs of one step of a pivot strategy and applies all their       */
-/* rotations R at once, A <- R^T A R (Eq. 2.1 / 2.2 on the pivot block):      */
-/*   - the diagonal of A is kept in d[] (reading R7);                         */
-/*   - pair (p,q), p < q: test Eq. 2.3 on (d_p, d_q, a_pq) with a_pq the      */
-/*     entry in row p, column q; if it fails, (t, c) from orc_rotation,       */
-/*     else the pair is left alone (identity);                                */
-/*   - the two one-sided halves of R^T A R are applied as two passes of the   */
-/*     column update of Alg. 4.5, x_p <- fma(hyp t, x_q, x_p) c,             */
-/*     x_q <- fma(t, x_p, x_q) c, over every row of a stored matrix S, with   */
-/*     S transposed between the passes: S = A at the first step, so the first */
-/*     step computes A R, transposes, then mixes the rows of (A R)^T, giving  */
-/*     S = (R^T A R)^T; the next step therefore starts from S = A^T and ends  */
-/*     with S = A, and so on -- the order of the two halves alternates from   */
-/*     step to step (reading R8);                                             */
-/*   - for a rotated pair, Eq. 2.6: d_p += hyp t a_pq, d_q += t a_pq (one fma */
-/*     each, with the a_pq of the step's start); the entries (p,p), (q,q) of  */
-/*     S take d_p, d_q and (p,q), (q,p) become 0;                             */
+/* block-oriented method, Sec. 6 full-block variant).  Rotations are applied  */
+/* one at a time, each as the symmetric two-sided update A <- R^T A R of the  */
+/* plane rotation R of its pair (p, q), p < q (Eq. 2.1 / 2.2 on the pivot     */
+/* block), see rotate_block:                                                  */
+/*   - the test of Eq. 2.3 on (a_pp, a_qq, a_pq) (R6: a_pq == 0 is never      */
+/*     rotated); if it fails, (t, c) from orc_rotation, hyp from the signs;   */
+/*   - the diagonal is carried by Eq. 2.6 (R7), a_pq becomes 0;               */
 /*   - W <- W R: columns p, q of W as in Alg. 4.5.                           */
+/* Pair order (`order'):                                                      */
+/*   0 row-cyclic: the inner order of the block-oriented method (Sec. 5):     */
+/*     p outer, q inner, over the pairs the mode visits;                      */
+/*   1 the parallel order: the steps of the modified modulus strategy over    */
+/*     the nn indices (Sec. 2, Alg. 4.3/4.4), or for the cross pass the steps */
+/*     s = 0 .. h-1 pairing k with h + ((k + s) mod h), h = nn/2; the         */
+/*     disjoint pairs of a step are applied one after the other in task      */
+/*     order (they touch disjoint rows and columns, so their rotation         */
+/*     parameters do not depend on that order).                              */
 /* Modes:                                                                     */
-/*   0 full-block: passes of the modulus strategy over nn indices (nn steps), */
-/*     until a pass rotates nothing or max_passes passes ran;                 */
-/*   1 cross pass: one pass over the pairs (k, h + ((k + s) mod h)),          */
-/*     s = 0 .. h-1, h = nn/2 -- only the off-diagonal block of A_P (Sec. 5,  */
-/*     block-oriented method, steps after the first);                         */
-/*   2 one pass of the modulus strategy over all nn indices (Sec. 5, first    */
-/*     step of the block-oriented method).                                    */
-/* On return A holds the final R^T A R (A itself, not its transpose) and W    */
-/* (nn x nn) the accumulated transformation, starting from I; *tmax_out (may  */
-/* be NULL) the largest |t| of the rotations applied (0 if none).             */
+/*   0 full-block: passes over all pairs p < q until a pass rotates nothing   */
+/*     or max_passes passes ran (Sec. 6);                                     */
+/*   1 cross pass: one pass over the pairs of the off-diagonal block,         */
+/*     p < h <= q (Sec. 5, every step of a sweep after the first);            */
+/*   2 one pass over all pairs p < q (Sec. 5, the first step of a sweep).     */
+/* On return A holds R^T A R for the product R of the applied rotations, W    */
+/* (nn x nn) that product (starting from I); *tmax_out (may be NULL) the     */
+/* largest |t| applied (0 if none).                                           */
 /* ------------------------------------------------------------------------ */
-static void mix_rows(int nn, double *S, int h, const int *P, const int *Q, const double *T,
-                     const double *C, const int *H, const int *rot)
+
+/* One rotation of the pivot block: for every other index x the entries       */
+/* (x, p), (x, q) take the column update of Alg. 4.5, and (p, x), (q, x) the  */
+/* same values (the row update of R^T on a symmetric matrix); a_pp and a_qq   */
+/* follow Eq. 2.6 with the a_pq before the rotation; a_pq = a_qp = 0.         */
+static void rotate_block(int nn, double *A, double *W, int p, int q, int hyp, double t, double c)
 {
-    /* every row x of the row-major nn x nn matrix S: columns p, q of pair k */
-    for (int x = 0; x < nn; ++x)
-        for (int k = 0; k < h; ++k) {
-            if (!rot[k]) continue;
-            double *row = S + (int64_t)x * nn;
-            double a = row[P[k]], b = row[Q[k]];
-            double ht = H[k] < 0 ? -T[k] : T[k];
-            row[P[k]] = fma(ht, b, a) * C[k];
-            row[Q[k]] = fma(T[k], a, b) * C[k];
-        }
+    const double apq = A[p + (int64_t)q * nn];
+    const double ht = hyp < 0 ? -t : t;
+    for (int x = 0; x < nn; ++x) {
+        if (x == p || x == q) continue;
+        const double axp = A[x + (int64_t)p * nn], axq = A[x + (int64_t)q * nn];
+        const double np_ = fma(ht, axq, axp) * c;
+        const double nq_ = fma(t, axp, axq) * c;
+        A[x + (int64_t)p * nn] = np_;
+        A[p + (int64_t)x * nn] = np_;
+        A[x + (int64_t)q * nn] = nq_;
+        A[q + (int64_t)x * nn] = nq_;
+    }
+    A[p + (int64_t)p * nn] = fma(ht, apq, A[p + (int64_t)p * nn]);
+    A[q + (int64_t)q * nn] = fma(t, apq, A[q + (int64_t)q * nn]);
+    A[p + (int64_t)q * nn] = 0.0;
+    A[q + (int64_t)p * nn] = 0.0;
+    rotate_cols(nn, W + (int64_t)p * nn, W + (int64_t)q * nn, hyp, t, c);
 }
 
-int orc_inner_solve(int nn, double *A, const int8_t *sgn, double tol, int mode,
+/* Test and, if it fails, rotation of one pair; returns ORC_OK or ORC_RANK. */
+static int inner_pair(int nn, double *A, double *W, const int8_t *sgn, double tol, int p, int q,
+                      int64_t *nrot, double *tmax)
+{
+    const double apq = A[p + (int64_t)q * nn];
+    const double app = A[p + (int64_t)p * nn], aqq = A[q + (int64_t)q * nn];
+    if (apq == 0.0 || fabs(apq) < tol * sqrt(app * aqq)) return ORC_OK; /* Eq. 2.3, R6 */
+    const int hyp = (sgn[p] == sgn[q]) ? -1 : 1;
+    double t, c;
+    if (orc_rotation(app, aqq, apq, hyp, &t, &c) != ORC_OK) return ORC_RANK;
+    rotate_block(nn, A, W, p, q, hyp, t, c);
+    ++*nrot;
+    if (fabs(t) > *tmax) *tmax = fabs(t);
+    return ORC_OK;
+}
+
+int orc_inner_solve(int nn, double *A, const int8_t *sgn, double tol, int mode, int order,
                     int max_passes, double *W, int64_t *nrot_out, int *passes_out, double *tmax_out)
 {
-    double tmax = 0.0; /* largest |t| of an applied rotation */
-    if (nn < 2 || (nn % 2) || max_passes < 1) return ORC_ARG;
-    int h = nn / 2;
-    int *pairs = (int *)malloc(sizeof(int) * (size_t)nn * (size_t)h * 2);
-    int *P = (int *)malloc(sizeof(int) * h), *Q = (int *)malloc(sizeof(int) * h);
-    double *T = (double *)malloc(sizeof(double) * h), *C = (double *)malloc(sizeof(double) * h);
-    int *H = (int *)malloc(sizeof(int) * h), *rot = (int *)malloc(sizeof(int) * h);
-    double *S = (double *)malloc(sizeof(double) * (size_t)nn * nn);
-    double *St = (double *)malloc(sizeof(double) * (size_t)nn * nn);
-    double *d = (double *)malloc(sizeof(double) * nn);
-    double *apq = (double *)malloc(sizeof(double) * h);
-    orc_modulus_pairs(nn, nn, pairs);
-    memset(W, 0, sizeof(double) * (size_t)nn * nn);
-    for (int i = 0; i < nn; ++i) W[i + i * nn] = 1.0;
-    /* S row-major: S[x*nn + y] = A(x, y); A column-major A[x + y*nn] */
-    for (int x = 0; x < nn; ++x)
-        for (int y = 0; y < nn; ++y) S[(int64_t)x * nn + y] = A[x + (int64_t)y * nn];
-    for (int x = 0; x < nn; ++x) d[x] = A[x + (int64_t)x * nn];
-    int transposed = 0; /* 0: S = A, 1: S = A^T */
-    int status = ORC_OK, npass = 0;
-    int64_t nrot_total = 0;
-    int npass_max = (mode == 0) ? max_passes : 1;
-    for (int pass = 0; pass < npass_max; ++pass) {
-        ++npass;
-        int64_t nrot_pass = 0;
-        int nsteps = (mode == 1) ? h : nn;
-        for (int s = 0; s < nsteps; ++s) {
-            for (int k = 0; k < h; ++k) {
-                int a, b;
-                if (mode == 1) {
-                    a = k;
-                    b = h + ((k + s) % h);
-                } else {
-                    a = pairs[(s * h + k) * 2];
-                    b = pairs[(s * h + k) * 2 + 1];
-                }
-                P[k] = a < b ? a : b;
-                Q[k] = a < b ? b : a;
-            }
-            for (int k = 0; k < h; ++k) {
-                int p = P[k], q = Q[k];
-                double a_pq = transposed ? S[(int64_t)q * nn + p] : S[(int64_t)p * nn + q];
-                apq[k] = a_pq;
-                H[k] = (sgn[p] == sgn[q]) ? -1 : 1;
-                T[k] = 0.0;
-                C[k] = 1.0;
-                rot[k] = 0;
-                if (a_pq == 0.0 || fabs(a_pq) < tol * sqrt(d[p] * d[q])) continue; /* Eq. 2.3, R6 */
-                if (orc_rotation(d[p], d[q], a_pq, H[k], &T[k], &C[k]) != ORC_OK) {
-                    status = ORC_RANK;
-                    goto out;
-                }
-                rot[k] = 1;
-                ++nrot_pass;
-                if (fabs(T[k]) > tmax) tmax = fabs(T[k]);
-            }
-            /* first half on the rows of S, transpose, second half */
-            mix_rows(nn, S, h, P, Q, T, C, H, rot);
-            for (int x = 0; x < nn; ++x)
-                for (int y = 0; y < nn; ++y) St[(int64_t)y * nn + x] = S[(int64_t)x * nn + y];
-            memcpy(S, St, sizeof(double) * (size_t)nn * nn);
-            transposed ^= 1;
-            mix_rows(nn, S, h, P, Q, T, C, H, rot);
-            /* Eq. 2.6 on the diagonal, zeros at (p,q) and (q,p) */
-            for (int k = 0; k < h; ++k) {
-                if (!rot[k]) continue;
-                int p = P[k], q = Q[k];
-                double ht = H[k] < 0 ? -T[k] : T[k];
-                d[p] = fma(ht, apq[k], d[p]);
-                d[q] = fma(T[k], apq[k], d[q]);
-                S[(int64_t)p * nn + p] = d[p];
-                S[(int64_t)q * nn + q] = d[q];
-                S[(int64_t)p * nn + q] = 0.0;
-                S[(int64_t)q * nn + p] = 0.0;
-            }
-            /* W <- W R */
-            for (int k = 0; k < h; ++k) {
-                if (!rot[k]) continue;
-                rotate_cols(nn, W + (int64_t)P[k] * nn, W + (int64_t)Q[k] * nn, H[k], T[k], C[k]);
-            }
-        }
-        nrot_total += nrot_pass;
-        if (nrot_pass == 0) break;
+    if (nn < 2 || (nn % 2) || max_passes < 1 || mode < 0 || mode > 2 || order < 0 || order > 1) return ORC_ARG;
+    const int h = nn / 2;
+    int *pairs = NULL;
+    if (order == 1 && mode != 1) {
+        pairs = (int *)malloc(sizeof(int) * (size_t)nn * (size_t)h * 2);
+        orc_modulus_pairs(nn, nn, pairs);
     }
-out:
-    /* A <- the current R^T A R (S or its transpose) */
-    for (int x = 0; x < nn; ++x)
-        for (int y = 0; y < nn; ++y)
-            A[x + (int64_t)y * nn] = transposed ? S[(int64_t)y * nn + x] : S[(int64_t)x * nn + y];
+    memset(W, 0, sizeof(double) * (size_t)nn * nn);
+    for (int i = 0; i < nn; ++i) W[i + (int64_t)i * nn] = 1.0;
+    double tmax = 0.0;
+    int64_t nrot_total = 0;
+    int status = ORC_OK, npass = 0;
+    const int npass_max = (mode == 0) ? max_passes : 1;
+    for (int pass = 0; pass < npass_max && status == ORC_OK; ++pass) {
+        ++npass;
+        int64_t nrot = 0;
+        if (order == 0) {
+            /* row-cyclic: p outer, q inner; the cross pass keeps p < h <= q */
+            for (int p = 0; p < (mode == 1 ? h : nn - 1) && status == ORC_OK; ++p)
+                for (int q = (mode == 1 ? h : p + 1); q < nn && status == ORC_OK; ++q)
+                    status = inner_pair(nn, A, W, sgn, tol, p, q, &nrot, &tmax);
+        } else {
+            const int nsteps = (mode == 1) ? h : nn;
+            for (int s = 0; s < nsteps && status == ORC_OK; ++s)
+                for (int k = 0; k < h && status == ORC_OK; ++k) {
+                    int a, b;
+                    if (mode == 1) {
+                        a = k;
+                        b = h + ((k + s) % h);
+                    } else {
+                        a = pairs[(s * h + k) * 2];
+                        b = pairs[(s * h + k) * 2 + 1];
+                    }
+                    status = inner_pair(nn, A, W, sgn, tol, a < b ? a : b, a < b ? b : a, &nrot, &tmax);
+                }
+        }
+        nrot_total += nrot;
+        if (nrot == 0) break;
+    }
     if (nrot_out) *nrot_out = nrot_total;
     if (passes_out) *passes_out = npass;
     if (tmax_out) *tmax_out = tmax;
-    free(pairs); free(P); free(Q); free(T); free(C); free(H); free(rot);
-    free(S); free(St); free(d); free(apq);
+    free(pairs);
     return status;
 }
 
@@ -606,18 +582,21 @@ out:
 /* (I, J) of a step forms A_P = [G_I G_J]^T [G_I G_J] (plain triple loop),    */
 /* calls orc_inner_solve (inner_mode 0: full-block with inner_max_passes;     */
 /* inner_mode 1: block-oriented -- whole block in the first step of a sweep,  */
-/* cross pass afterwards), and, if any inner rotation was applied, updates    */
+/* cross pass afterwards; inner_order 0 row-cyclic, 1 the parallel order),    */
+/* and, if any inner rotation was applied, updates                            */
 /* [G_I G_J] <- [G_I G_J] W_P and [V_I V_J] <- [V_I V_J] W_P (plain triple    */
 /* loops).  Stops after a sweep with no rotation, or (tstop > 0, R14) after a  */
 /* sweep whose inner tangents are all <= tstop.  Outputs in input order.      */
 /* ------------------------------------------------------------------------ */
 int orc_block_hsvd(int64_t m, int64_t n, const double *G, int64_t ldg, const int8_t *J,
                    int b, double tol, int max_sweeps, int inner_mode, int inner_max_passes,
-                   int sort, double *sigma, double *U, int64_t ldu, double *V, int64_t ldv,
+                   int inner_order, int sort, double *sigma, double *U, int64_t ldu, double *V, int64_t ldv,
                    int *sweeps, int64_t *rotations, double tstop, int *stop_rule)
 {
     if (stop_rule) *stop_rule = ORC_STOP_NONE;
-    if (m < n || n < 1 || ldg < m || b < 1 || max_sweeps < 1 || !(tol > 0.0) || !(tstop >= 0.0)) return ORC_ARG;
+    if (m < n || n < 1 || ldg < m || b < 1 || max_sweeps < 1 || !(tol > 0.0) || !(tstop >= 0.0) ||
+        inner_order < 0 || inner_order > 1)
+        return ORC_ARG;
     for (int64_t j = 0; j < n; ++j)
         if (J[j] != 1 && J[j] != -1) return ORC_ARG;
     if (!all_finite(m, n, G, ldg)) return ORC_NONFINITE;
@@ -687,7 +666,7 @@ int orc_block_hsvd(int64_t m, int64_t n, const double *G, int64_t ldg, const int
                 int mode = (inner_mode == 0) ? 0 : (s == 0 ? 2 : 1);
                 int64_t nr = 0;
                 double tmax = 0.0;
-                int st = orc_inner_solve(nn, A, ps, tol, mode, inner_max_passes, Wp, &nr, NULL, &tmax);
+                int st = orc_inner_solve(nn, A, ps, tol, mode, inner_order, inner_max_passes, Wp, &nr, NULL, &tmax);
                 if (st != ORC_OK) { status = st; goto done; }
                 if (nr == 0) continue;
                 nrot += nr;

@@ -1,0 +1,167 @@
+/*
+ * inner_model.c -- exact CPU model of the library's inner-solve kernels
+ * (the J-orthogonalisation of one pivot block, Sec. 5 / Sec. 6).
+ *
+ * TEST INFRASTRUCTURE ONLY, and NOT the oracle.  The oracle's inner solve
+ * (orc_inner_solve in hsvd_oracle.c) applies one rotation at a time, in the
+ * paper's row-cyclic order.  This file instead reproduces, operation for
+ * operation, what the library's cluster kernels compute, so that a test can
+ * compare them bit for bit; a second test bounds this model against the
+ * oracle.  It shares no code with the CUDA library: it is written from the
+ * kernels' documented arithmetic, and the rotation parameters and the pivot
+ * table come from the oracle (orc_rotation, orc_modulus_pairs).
+ *
+ * The model's choices where the paper leaves the implementation open:
+ *   M1  Pair order: the steps of the parallel strategy inside the block --
+ *       the modified modulus strategy over the 2b indices for a full pass,
+ *       (k, b + ((k + s) mod b)) at step s for the cross pass -- with all
+ *       pairs of a step tested on the step's starting values and rotated at
+ *       once (they are disjoint).
+ *   M2  The two one-sided halves of R^T A R alternate their order from step
+ *       to step: the step's rotations mix the rows of a row-major copy S of
+ *       the block, S is transposed, and the rows are mixed again, so S holds
+ *       the transpose of the block after an odd number of steps.  (The
+ *       kernels transpose once per step this way.)
+ *   M3  After the mixing, a rotated pair's diagonal entries take Eq. 2.6
+ *       with the step's starting a_pq, and (p, q), (q, p) become 0.
+ *
+ * Build: compiled into the oracle's shared object by oracle.py (gcc -O2
+ * -ffp-contract=off: every fused multiply-add is an explicit fma()).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define MDL_OK 0
+#define MDL_ARG (-1)
+#define MDL_RANK (-2)
+
+int orc_rotation(double aii, double ajj, double aij, int hyp, double *t, double *c);
+void orc_modulus_pairs(int r, int nsteps, int *pairs);
+
+/* the column update of Alg. 4.5 on two vectors of length m */
+static void mdl_rotate_cols(int m, double *x, double *y, int hyp, double t, double c)
+{
+    const double ht = hyp < 0 ? -t : t;
+    for (int i = 0; i < m; ++i) {
+        const double xi = x[i], yi = y[i];
+        x[i] = fma(ht, yi, xi) * c;
+        y[i] = fma(t, xi, yi) * c;
+    }
+}
+
+/* the step's rotations on every row x of the row-major nn x nn matrix S:
+ * entries p, q of the row as the column update of Alg. 4.5 */
+static void mdl_mix_rows(int nn, double *S, int h, const int *P, const int *Q, const double *T,
+                         const double *C, const int *H, const int *rot)
+{
+    for (int x = 0; x < nn; ++x)
+        for (int k = 0; k < h; ++k) {
+            if (!rot[k]) continue;
+            double *row = S + (int64_t)x * nn;
+            const double a = row[P[k]], b = row[Q[k]];
+            const double ht = H[k] < 0 ? -T[k] : T[k];
+            row[P[k]] = fma(ht, b, a) * C[k];
+            row[Q[k]] = fma(T[k], a, b) * C[k];
+        }
+}
+
+/* Model of the inner solve of one pivot block (nn x nn column-major,
+ * symmetric, signs sgn).  mode 0: full passes until one rotates nothing or
+ * max_passes ran; 1: one cross pass; 2: one full pass.  Outputs as for
+ * orc_inner_solve: A <- the final block (A itself, not its transpose), W the
+ * accumulated transformation, rotation count, passes, largest |t|. */
+int mdl_inner_solve(int nn, double *A, const int8_t *sgn, double tol, int mode,
+                    int max_passes, double *W, int64_t *nrot_out, int *passes_out, double *tmax_out)
+{
+    if (nn < 2 || (nn % 2) || max_passes < 1 || mode < 0 || mode > 2) return MDL_ARG;
+    const int h = nn / 2;
+    int *pairs = (int *)malloc(sizeof(int) * (size_t)nn * (size_t)h * 2);
+    int *P = (int *)malloc(sizeof(int) * h), *Q = (int *)malloc(sizeof(int) * h);
+    double *T = (double *)malloc(sizeof(double) * h), *C = (double *)malloc(sizeof(double) * h);
+    int *H = (int *)malloc(sizeof(int) * h), *rot = (int *)malloc(sizeof(int) * h);
+    double *S = (double *)malloc(sizeof(double) * (size_t)nn * nn);
+    double *St = (double *)malloc(sizeof(double) * (size_t)nn * nn);
+    double *d = (double *)malloc(sizeof(double) * nn);
+    double *apq = (double *)malloc(sizeof(double) * h);
+    double tmax = 0.0;
+    orc_modulus_pairs(nn, nn, pairs);
+    memset(W, 0, sizeof(double) * (size_t)nn * nn);
+    for (int i = 0; i < nn; ++i) W[i + (int64_t)i * nn] = 1.0;
+    for (int x = 0; x < nn; ++x)
+        for (int y = 0; y < nn; ++y) S[(int64_t)x * nn + y] = A[x + (int64_t)y * nn];
+    for (int x = 0; x < nn; ++x) d[x] = A[x + (int64_t)x * nn];
+    int transposed = 0; /* 0: S = A, 1: S = A^T (M2) */
+    int status = MDL_OK, npass = 0;
+    int64_t nrot_total = 0;
+    const int npass_max = (mode == 0) ? max_passes : 1;
+    for (int pass = 0; pass < npass_max; ++pass) {
+        ++npass;
+        int64_t nrot_pass = 0;
+        const int nsteps = (mode == 1) ? h : nn;
+        for (int s = 0; s < nsteps; ++s) {
+            for (int k = 0; k < h; ++k) { /* M1 */
+                int a, b;
+                if (mode == 1) {
+                    a = k;
+                    b = h + ((k + s) % h);
+                } else {
+                    a = pairs[(s * h + k) * 2];
+                    b = pairs[(s * h + k) * 2 + 1];
+                }
+                P[k] = a < b ? a : b;
+                Q[k] = a < b ? b : a;
+            }
+            for (int k = 0; k < h; ++k) {
+                const int p = P[k], q = Q[k];
+                const double a_pq = transposed ? S[(int64_t)q * nn + p] : S[(int64_t)p * nn + q];
+                apq[k] = a_pq;
+                H[k] = (sgn[p] == sgn[q]) ? -1 : 1;
+                T[k] = 0.0;
+                C[k] = 1.0;
+                rot[k] = 0;
+                if (a_pq == 0.0 || fabs(a_pq) < tol * sqrt(d[p] * d[q])) continue; /* Eq. 2.3 */
+                if (orc_rotation(d[p], d[q], a_pq, H[k], &T[k], &C[k]) != 0) {
+                    status = MDL_RANK;
+                    goto out;
+                }
+                rot[k] = 1;
+                ++nrot_pass;
+                if (fabs(T[k]) > tmax) tmax = fabs(T[k]);
+            }
+            /* M2: one half on the rows of S, transpose, the other half */
+            mdl_mix_rows(nn, S, h, P, Q, T, C, H, rot);
+            for (int x = 0; x < nn; ++x)
+                for (int y = 0; y < nn; ++y) St[(int64_t)y * nn + x] = S[(int64_t)x * nn + y];
+            memcpy(S, St, sizeof(double) * (size_t)nn * nn);
+            transposed ^= 1;
+            mdl_mix_rows(nn, S, h, P, Q, T, C, H, rot);
+            for (int k = 0; k < h; ++k) { /* M3 */
+                if (!rot[k]) continue;
+                const int p = P[k], q = Q[k];
+                const double ht = H[k] < 0 ? -T[k] : T[k];
+                d[p] = fma(ht, apq[k], d[p]);
+                d[q] = fma(T[k], apq[k], d[q]);
+                S[(int64_t)p * nn + p] = d[p];
+                S[(int64_t)q * nn + q] = d[q];
+                S[(int64_t)p * nn + q] = 0.0;
+                S[(int64_t)q * nn + p] = 0.0;
+            }
+            for (int k = 0; k < h; ++k) /* W <- W R */
+                if (rot[k]) mdl_rotate_cols(nn, W + (int64_t)P[k] * nn, W + (int64_t)Q[k] * nn, H[k], T[k], C[k]);
+        }
+        nrot_total += nrot_pass;
+        if (nrot_pass == 0) break;
+    }
+out:
+    for (int x = 0; x < nn; ++x)
+        for (int y = 0; y < nn; ++y)
+            A[x + (int64_t)y * nn] = transposed ? S[(int64_t)y * nn + x] : S[(int64_t)x * nn + y];
+    if (nrot_out) *nrot_out = nrot_total;
+    if (passes_out) *passes_out = npass;
+    if (tmax_out) *tmax_out = tmax;
+    free(pairs); free(P); free(Q); free(T); free(C); free(H); free(rot);
+    free(S); free(St); free(d); free(apq);
+    return status;
+}

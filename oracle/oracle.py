@@ -30,6 +30,9 @@ T_EPS = 2.0 ** -27
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "hsvd_oracle.c")
+# the exact model of the library's inner-solve kernels (not the oracle) is
+# compiled into the same shared object; see inner_model.c and inner_model.py
+_MODEL_SRC = os.path.join(_HERE, "inner_model.c")
 _OUT_DIR = os.path.join(_HERE, "_build")
 _SO = os.path.join(_OUT_DIR, "liboracle_hsvd.so")
 _lock = threading.Lock()
@@ -50,13 +53,13 @@ def build(force=False, src=None, out=None):
 
     ``src``/``out`` compile another copy of the source (used by the tests
     that plant mistakes in a copy of the oracle)."""
-    src = _SRC if src is None else src
+    srcs = [_SRC, _MODEL_SRC] if src is None else [src]
     out = _SO if out is None else out
     os.makedirs(os.path.dirname(out), exist_ok=True)
-    if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(src):
+    if not force and os.path.exists(out) and all(os.path.getmtime(out) >= os.path.getmtime(f) for f in srcs):
         return out
     tmp = out + ".tmp.%d" % os.getpid()
-    cmd = ["gcc"] + CFLAGS + ["-fPIC", "-shared", "-Wall", "-o", tmp, src, "-lm"]
+    cmd = ["gcc"] + CFLAGS + ["-fPIC", "-shared", "-Wall", "-o", tmp] + srcs + ["-lm"]
     # the modulus order runs its steps' pairs on OpenMP threads when the
     # compiler has OpenMP; otherwise the same code is compiled serially
     if subprocess.run(cmd[:1] + ["-fopenmp"] + cmd[1:], capture_output=True).returncode != 0:
@@ -73,12 +76,12 @@ def _bind(lib):
     lib.orc_hsvd.argtypes = [_i64, _i64, _p, _i64, _p, _dbl, _int, _int, _int,
                              _p, _p, _i64, _p, _i64, _p, _p, _dbl, _p]
     lib.orc_hsvd.restype = _int
-    lib.orc_inner_solve.argtypes = [_int, _p, _p, _dbl, _int, _int, _p, _p, _p, _p]
+    lib.orc_inner_solve.argtypes = [_int, _p, _p, _dbl, _int, _int, _int, _p, _p, _p, _p]
     lib.orc_set_threads.argtypes = [_int]
     lib.orc_set_threads.restype = _int
     lib.orc_inner_solve.restype = _int
     lib.orc_block_hsvd.argtypes = [_i64, _i64, _p, _i64, _p, _int, _dbl, _int, _int, _int,
-                                   _int, _p, _p, _i64, _p, _i64, _p, _p, _dbl, _p]
+                                   _int, _int, _p, _p, _i64, _p, _i64, _p, _p, _dbl, _p]
     lib.orc_block_hsvd.restype = _int
     lib.orc_sym_factor.argtypes = [_i64, _p, _i64, _p, _i64, _p, _p]
     lib.orc_sym_factor.restype = _int
@@ -165,25 +168,32 @@ def hsvd(G, J, tol, max_sweeps=30, order="cyclic", sort=False, want_u=True, want
     return dict(sigma=sigma, U=U, V=V, sweeps=sweeps.value, rotations=rots.value, status=st, stop=stop.value)
 
 
-def inner_solve(A, sgn, tol, mode=0, max_passes=8, lib=None, want_tmax=False):
-    """J-orthogonalise one pivot block; returns (A_out, W, rotations, passes,
-    status), and the largest applied |t| after them with ``want_tmax``."""
+_ORDERS = {"cyclic": 0, "parallel": 1}
+
+
+def inner_solve(A, sgn, tol, mode=0, max_passes=8, order="cyclic", lib=None, want_tmax=False):
+    """J-orthogonalise one pivot block, one rotation at a time; ``order`` is
+    ``"cyclic"`` (row-cyclic, Sec. 5) or ``"parallel"`` (the pairs of the
+    parallel strategy).  Returns (A_out, W, rotations, passes, status), and
+    the largest applied |t| after them with ``want_tmax``."""
     A = np.array(A, dtype=np.float64, order="F", copy=True)
     nn = A.shape[0]
     s = _signs(sgn, nn)
     W = np.zeros((nn, nn), order="F")
     nrot, passes, tmax = _i64(), _int(), _dbl()
-    st = (lib or _load()).orc_inner_solve(nn, _ptr(A), _ptr(s), float(tol), int(mode), int(max_passes),
-                                 _ptr(W), ctypes.byref(nrot), ctypes.byref(passes), ctypes.byref(tmax))
+    st = (lib or _load()).orc_inner_solve(nn, _ptr(A), _ptr(s), float(tol), int(mode), _ORDERS[order],
+                                          int(max_passes), _ptr(W), ctypes.byref(nrot), ctypes.byref(passes),
+                                          ctypes.byref(tmax))
     if want_tmax:
         return A, W, nrot.value, passes.value, st, tmax.value
     return A, W, nrot.value, passes.value, st
 
 
 def block_hsvd(G, J, b, tol, max_sweeps=30, inner_mode=0, inner_max_passes=8, sort=True,
-               want_u=True, want_v=True, lib=None, tstop=0.0):
+               want_u=True, want_v=True, lib=None, tstop=0.0, inner_order="cyclic"):
     """Blocked one-sided hyperbolic Jacobi SVD on the CPU (block width b);
-    ``tstop`` as for :func:`hsvd`, over the inner rotations' tangents."""
+    ``tstop`` as for :func:`hsvd`, over the inner rotations' tangents;
+    ``inner_order`` as ``order`` of :func:`inner_solve`."""
     G = _fcol(G)
     m, n = G.shape
     j = _signs(J, n)
@@ -192,7 +202,7 @@ def block_hsvd(G, J, b, tol, max_sweeps=30, inner_mode=0, inner_max_passes=8, so
     V = np.zeros((n, n), order="F") if want_v else None
     sweeps, rots, stop = _int(), _i64(), _int()
     st = (lib or _load()).orc_block_hsvd(m, n, _ptr(G), m, _ptr(j), int(b), float(tol), int(max_sweeps),
-                                int(inner_mode), int(inner_max_passes), 1 if sort else 0,
+                                int(inner_mode), int(inner_max_passes), _ORDERS[inner_order], 1 if sort else 0,
                                 _ptr(sigma), _ptr(U), m, _ptr(V), n, ctypes.byref(sweeps), ctypes.byref(rots),
                                 float(tstop), ctypes.byref(stop))
     return dict(sigma=sigma, U=U, V=V, sweeps=sweeps.value, rotations=rots.value, status=st, stop=stop.value)

@@ -172,11 +172,16 @@ def test_blocked_graded_256(api, b, inner, sort):
     assert max(orth, junit, resid) <= 1e-12 * n
     _vectors_match(J, r, ref, 1e-8)
     # the oracle's blocked method with the same block width, inner mode and sorting
-    # (the oracle numbers its inner modes 0 = full-block, 1 = block-oriented)
-    ob = oracle.block_hsvd(G, J, b, tol, 40, inner_mode=1 if inner == api.HSVD_INNER_ORIENTED else 0,
-                           inner_max_passes=8, sort=sort)
-    assert ob["status"] == 0 and abs(ob["sweeps"] - r["sweeps"]) <= 1
+    # (the oracle numbers its inner modes 0 = full-block, 1 = block-oriented):
+    # sigma against its row-cyclic inner order (Sec. 5), the sweep count
+    # against its parallel inner order (the library's pairs)
+    im = 1 if inner == api.HSVD_INNER_ORIENTED else 0
+    ob = oracle.block_hsvd(G, J, b, tol, 40, inner_mode=im, inner_max_passes=8, sort=sort)
+    assert ob["status"] == 0
     assert _sigma_err(J, r["sigma"], ob["sigma"]) <= 1e-12
+    op = oracle.block_hsvd(G, J, b, tol, 40, inner_mode=im, inner_max_passes=8, sort=sort, inner_order="parallel",
+                           want_u=False, want_v=False)
+    assert op["status"] == 0 and abs(op["sweeps"] - r["sweeps"]) <= 1
 
 
 @pytest.mark.parametrize("m,n,p,b", [(200, 100, 30, 16), (129, 97, 97, 16), (500, 130, 0, 32)])
@@ -254,32 +259,80 @@ def test_kernel_gram(api, b):
         assert np.array_equal(A[k], A[k].T)
 
 
-@pytest.mark.parametrize("b,mode", [(16, 0), (16, 1), (16, 2), (32, 0), (32, 1), (64, 1), (64, 2)])
-def test_kernel_inner_solve_matches_oracle(api, b, mode):
-    """Same A_P, same pivot order, same formulas: the kernel reproduces the
-    oracle's inner solve bit for bit (the library is compiled without
-    floating-point contraction; every FMA is explicit on both sides)."""
+def _pivot_blocks(b, seed, npairs=3):
     nn = 2 * b
-    rng = np.random.default_rng(100 + b + mode)
-    npairs = 3
+    rng = np.random.default_rng(seed)
     As, sg = [], []
     for k in range(npairs):
         P = rng.standard_normal((3 * nn, nn)) * 10.0 ** rng.uniform(-3, 0, nn)[None, :]
         As.append(P.T @ P)
-        sg.append(W.signs_block(nn, [nn // 2, 5, nn][k]))
-    As = np.stack(As)
-    sg = np.stack(sg)
+        sg.append(W.signs_block(nn, [nn // 2, 5, nn][k % 3]))
+    return np.stack(As), np.stack(sg)
+
+
+def _gpu_inner(api, As, sg, tol, mode, max_passes=10):
     dev = torch.device("cuda:0")
-    tol = nn * U64
     Ao, Wg, rot, st = api.hsvd_pivot_solve(torch.from_numpy(As).to(dev), torch.from_numpy(sg).to(dev), tol,
-                                           mode=mode, max_passes=10)
-    Ao, Wg, rot = Ao.cpu().numpy(), Wg.cpu().numpy(), rot.cpu().numpy()
+                                           mode=mode, max_passes=max_passes)
     assert int(st.cpu()[0]) == 0
-    for k in range(npairs):
-        Ar, Wr, nrot, passes, s = oracle.inner_solve(As[k], sg[k], tol, mode=mode, max_passes=10)
+    return Ao.cpu().numpy(), Wg.cpu().numpy(), rot.cpu().numpy()
+
+
+@pytest.mark.parametrize("b,mode", [(16, 0), (16, 1), (16, 2), (32, 0), (32, 1), (64, 1), (64, 2)])
+def test_kernel_inner_solve_matches_model(api, b, mode):
+    """Same A_P: the kernel reproduces the exact CPU model of its arithmetic
+    (oracle/inner_model.c: the parallel strategy's pairs, a step's pairs at
+    once, the halves of R^T A R alternating between steps) bit for bit (the
+    library is compiled without floating-point contraction; every FMA is
+    explicit on both sides)."""
+    from oracle import inner_model
+
+    nn = 2 * b
+    As, sg = _pivot_blocks(b, 100 + b + mode)
+    tol = nn * U64
+    Ao, Wg, rot = _gpu_inner(api, As, sg, tol, mode)
+    for k in range(As.shape[0]):
+        Ar, Wr, nrot, passes, s = inner_model.inner_solve(As[k], sg[k], tol, mode=mode, max_passes=10)
         assert s == 0 and nrot == rot[k]
         assert np.array_equal(Wg[k], Wr), np.max(np.abs(Wg[k] - Wr))
         assert np.array_equal(Ao[k], Ar), np.max(np.abs(Ao[k] - Ar))
+
+
+@pytest.mark.parametrize("b,mode", [(16, 0), (16, 1), (16, 2), (32, 0), (32, 1), (32, 2), (64, 0), (64, 1), (64, 2)])
+def test_kernel_inner_solve_against_oracle(api, b, mode):
+    """The kernel against the oracle's plain inner solve (one rotation at a
+    time as R^T A R) on the same A_P.
+    - Same pairs (the oracle's parallel order): the same rotations are
+      applied, only the rounding of entries that two rotations of a step
+      both touch differs (about 3 roundings each, in another order), so per
+      step the results differ by a few u of the entry's |R|^T |A| |R| scale;
+      over a pass of at most 2b steps, carried through the later rotation
+      parameters, the stated bound is |A_gpu - A_orc| <= 8 p (2b) u
+      (|W|^T |A| |W|) and |W_gpu - W_orc| <= 8 p (2b) u max(1, max |W|), p the
+      passes; the rotation counts agree.
+    - The paper's row-cyclic order (Sec. 5) rotates other pairs in another
+      order, so only what is order-free is compared: both are congruences by
+      J-unitary W that keep the eigenvalues of J A, and in full-block mode
+      both diagonals are those eigenvalues (per sign group)."""
+    nn = 2 * b
+    As, sg = _pivot_blocks(b, 200 + b + mode)
+    tol = nn * U64
+    Ao, Wg, rot = _gpu_inner(api, As, sg, tol, mode)
+    for k in range(As.shape[0]):
+        Ar, Wr, nrot, passes, s = oracle.inner_solve(As[k], sg[k], tol, mode=mode, max_passes=10, order="parallel")
+        assert s == 0 and nrot == rot[k]
+        bound = 8 * passes * nn * U64
+        assert np.all(np.abs(Ao[k] - Ar) <= bound * (np.abs(Wr).T @ np.abs(As[k]) @ np.abs(Wr)))
+        assert np.max(np.abs(Wg[k] - Wr)) <= bound * max(1.0, np.max(np.abs(Wr)))
+        Jd = np.diag(sg[k].astype(float))
+        ev = np.sort(np.linalg.eigvals(Jd @ As[k]).real)
+        Ac, Wc, _, pc, s = oracle.inner_solve(As[k], sg[k], tol, mode=mode, max_passes=10, order="cyclic")
+        assert s == 0
+        for A_, W_ in ((Ao[k], Wg[k]), (Ac, Wc)):
+            assert np.max(np.abs(W_.T @ Jd @ W_ - Jd)) <= 8 * max(pc, passes) * nn * U64 * max(1, np.max(np.abs(W_))) ** 2
+            assert np.allclose(np.sort(np.linalg.eigvals(Jd @ A_).real), ev, rtol=1e-10, atol=0)
+            if mode == 0:
+                assert np.allclose(np.sort(sg[k] * np.diag(A_)), ev, rtol=1e-10, atol=0)
 
 
 @pytest.mark.parametrize("b", [16, 32, 64])
@@ -288,7 +341,10 @@ def test_kernel_cross_pass_late_first_rotation(api, b, first):
     """Cross pass (mode 1) on pivot blocks whose off-diagonal block is zero
     except at chosen pairs, so the first rotation comes at a chosen step (or
     never): the steps before it change nothing, and the kernel, which starts
-    the pass at that step, still matches the oracle bit for bit."""
+    the pass at that step, still matches the exact model of its arithmetic bit
+    for bit and rotates the same pairs as the oracle."""
+    from oracle import inner_model
+
     nn, h = 2 * b, b
     rng = np.random.default_rng(500 + b)
     picks = {"none": [], "late": [(5, h // 2 + 1), (h - 2, h // 2 + 3)], "last": [(1, h - 1)]}[first]
@@ -310,9 +366,10 @@ def test_kernel_cross_pass_late_first_rotation(api, b, first):
     Ao, Wg, rot = Ao.cpu().numpy(), Wg.cpu().numpy(), rot.cpu().numpy()
     assert int(st.cpu()[0]) == 0
     for k in range(3):
-        Ar, Wr, nrot, passes, s = oracle.inner_solve(As[k], sg[k], tol, mode=1)
+        Ar, Wr, nrot, passes, s = inner_model.inner_solve(As[k], sg[k], tol, mode=1)
         assert s == 0 and nrot == rot[k]
         assert np.array_equal(Wg[k], Wr) and np.array_equal(Ao[k], Ar)
+        assert oracle.inner_solve(As[k], sg[k], tol, mode=1, order="parallel")[2] == nrot
         if first == "none":
             assert rot[k] == 0 and np.array_equal(Wg[k], np.eye(nn)) and np.array_equal(Ao[k], As[k])
         else:

@@ -27,10 +27,14 @@ MUTANTS = {
     "dot_drops_first_term": ("for (int64_t i = 0; i < m; ++i) s += x[i] * y[i];",
                              "for (int64_t i = 1; i < m; ++i) s += x[i] * y[i];"),
     "stepper_threshold": ("if (ip[k] + jp[k] > r - 2) {", "if (ip[k] + jp[k] > r - 3) {"),
-    "inner_diag_drops_hyp": ("d[p] = fma(ht, apq[k], d[p]);", "d[p] = fma(T[k], apq[k], d[p]);"),
-    "inner_update_transposed": ("row[P[k]] = fma(ht, b, a) * C[k];", "row[P[k]] = fma(ht, a, b) * C[k];"),
-    "inner_second_half_dropped": ("            transposed ^= 1;\n            mix_rows(nn, S, h, P, Q, T, C, H, rot);",
-                                  "            transposed ^= 1;\n"),
+    "inner_diag_drops_hyp": ("A[p + (int64_t)p * nn] = fma(ht, apq, A[p + (int64_t)p * nn]);",
+                             "A[p + (int64_t)p * nn] = fma(t, apq, A[p + (int64_t)p * nn]);"),
+    "inner_update_transposed": ("const double np_ = fma(ht, axq, axp) * c;",
+                                "const double np_ = fma(ht, axp, axq) * c;"),
+    "inner_mirror_dropped": ("        A[p + (int64_t)x * nn] = np_;\n", ""),
+    "inner_cross_pass_whole_triangle": ("for (int q = (mode == 1 ? h : p + 1); q < nn", "for (int q = p + 1; q < nn"),
+    "inner_pass_skips_last_row": ("for (int p = 0; p < (mode == 1 ? h : nn - 1)", "for (int p = 0; p < (mode == 1 ? h : nn - 2)"),
+    "inner_cross_shift_wrong": ("b = h + ((k + s) % h);", "b = h + ((k + 2 * s) % h);"),
     "block_update_transposed_W": ("* Wp[x + y * nn];", "* Wp[y + x * nn];"),
     "test_uses_product_not_sqrt": ("if (aij == 0.0 || fabs(aij) < tol * sqrt(aii * ajj)) return ORC_OK;",
                                    "if (aij == 0.0 || fabs(aij) < tol * (aii * ajj)) return ORC_OK;"),
@@ -40,8 +44,7 @@ MUTANTS = {
     "conv_code_overwritten": ("*cd |= conv_code(t, tstop);", "*cd = conv_code(t, tstop);"),
     "block_code_overwritten": ("cd |= conv_code(tmax, tstop);", "cd = conv_code(tmax, tstop);"),
     "stop_on_large_tangents": ("if (cd == 0 || cd == 1) {", "if (cd == 0 || cd == 3) {"),
-    "inner_tmax_first_rotation": ("if (fabs(T[k]) > tmax) tmax = fabs(T[k]);",
-                                  "if (tmax == 0.0) tmax = fabs(T[k]);"),
+    "inner_tmax_first_rotation": ("if (fabs(t) > *tmax) *tmax = fabs(t);", "if (*tmax == 0.0) *tmax = fabs(t);"),
 }
 
 
@@ -103,17 +106,59 @@ def _battery(orc, lib):
     for r in (r1, r2):
         if r["status"] == 0 and np.max(np.abs(r["U"].T @ r["U"] - np.eye(n))) > 2 * n * U + 8 * n * U:
             failed.append("final-orthogonality")
-    # inner solve: congruence and eigenvalues of J A
+    # inner solve: congruence and eigenvalues of J A, in every mode and order
     nn = 16
     Gp = rng.standard_normal((40, nn))
     A = Gp.T @ Gp
     sg = W.signs_block(nn, 6)
-    Ao, Wp, nrot, passes, st = orc.inner_solve(A, sg, nn * U, mode=0, max_passes=20, lib=lib)
     Jn = np.diag(sg.astype(float))
-    if st != 0 or not np.allclose(Wp.T @ A @ Wp, Ao, rtol=0, atol=1e-11 * np.max(np.abs(A))) \
-            or not np.allclose(np.sort(sg * np.diag(Ao)), np.sort(np.linalg.eigvals(Jn @ A).real), rtol=1e-9) \
-            or np.max(np.abs(Wp.T @ Jn @ Wp - Jn)) > 1e-11 * max(1, np.max(np.abs(Wp)) ** 2):
-        failed.append("inner")
+    ev = np.sort(np.linalg.eigvals(Jn @ A).real)
+    for order in ("cyclic", "parallel"):
+        for mode in (0, 1, 2):
+            Ao, Wp, nrot, passes, st = orc.inner_solve(A, sg, nn * U, mode=mode, max_passes=20, order=order,
+                                                       lib=lib)
+            if st != 0 or not np.allclose(Wp.T @ A @ Wp, Ao, rtol=0, atol=1e-11 * np.max(np.abs(A))) \
+                    or not np.allclose(np.sort(np.linalg.eigvals(Jn @ Ao).real), ev, rtol=1e-9) \
+                    or np.max(np.abs(Wp.T @ Jn @ Wp - Jn)) > 1e-11 * max(1, np.max(np.abs(Wp)) ** 2):
+                failed.append("inner-%s-%d" % (order, mode))
+            elif mode == 0 and not np.allclose(np.sort(sg * np.diag(Ao)), ev, rtol=1e-9):
+                failed.append("inner-diag-%s" % order)
+            elif mode == 1 and nrot > (nn // 2) ** 2:
+                failed.append("inner-cross-count-%s" % order)
+        # a zero off-diagonal block: the cross pass is the identity
+        Z = A.copy()
+        Z[:8, 8:] = 0.0
+        Z[8:, :8] = 0.0
+        if orc.inner_solve(Z, sg, nn * U, mode=1, order=order, lib=lib)[2] != 0:
+            failed.append("inner-cross-zero-%s" % order)
+    # the hand-worked 4 x 4 blocks (two disjoint couplings, closed forms)
+    for hyp, a, b, t, dd in ((-1, 2.0, 1.0, 1.0, (1.0, 3.0)), (1, 5.0, -4.0, 0.5, (3.0, 3.0))):
+        B = np.array([[a, 0, b, 0], [0, a, 0, b], [b, 0, a, 0], [0, b, 0, a]])
+        s4 = np.ones(4, dtype=np.int8) if hyp < 0 else np.array([1, 1, -1, -1], dtype=np.int8)
+        c = 1 / np.sqrt(1 - hyp * t * t)
+        for mode in (1, 2):
+            Bo, Wb, nr, _, st = orc.inner_solve(B, s4, 4 * U, mode=mode, lib=lib)
+            want = np.array([[c, 0, t * c, 0], [0, c, 0, t * c], [hyp * t * c, 0, c, 0], [0, hyp * t * c, 0, c]])
+            if st != 0 or nr != 2 or np.max(np.abs(Wb - want)) > 8 * U or \
+                    np.max(np.abs(Bo - np.diag([dd[0], dd[0], dd[1], dd[1]]))) > 64 * U:
+                failed.append("inner-hand-%d-%d" % (hyp, mode))
+    # every pair of the off-diagonal block is visited once per cross pass:
+    # one coupling at (k, h + j) on a diagonal block is rotated exactly once
+    D = np.diag(np.arange(1.0, nn + 1.0))
+    for order in ("cyclic", "parallel"):
+        for k, j in ((0, 1), (3, 6), (7, 2), (5, 5)):
+            Dc = D.copy()
+            Dc[k, 8 + j] = Dc[8 + j, k] = 0.3
+            for mode in (1, 2):
+                if orc.inner_solve(Dc, sg, nn * U, mode=mode, order=order, lib=lib)[2] != 1:
+                    failed.append("inner-visit-%s-%d" % (order, mode))
+    # one row-cyclic pass (Sec. 5): the pair visited last ends exactly zero
+    # (or passes the test)
+    Ab = Gp.T @ Gp * np.outer(10.0 ** -np.arange(nn) / 8, 10.0 ** -np.arange(nn) / 8)
+    for mode, (p, q) in ((1, (7, 15)), (2, (14, 15))):
+        Ao = orc.inner_solve(Ab, sg, nn * U, mode=mode, lib=lib)[0]
+        if not (Ao[p, q] == 0.0 or abs(Ao[p, q]) < nn * U * np.sqrt(Ao[p, p] * Ao[q, q])):
+            failed.append("inner-last-pair-%d" % mode)
     # blocked method against LAPACK
     r = orc.block_hsvd(G, J, 4, n * U, 30, inner_mode=1, lib=lib)
     lam = np.sort(r["sigma"] ** 2 * J)

@@ -258,52 +258,171 @@ def test_modulus_matches_appendix_tables(orc):
 
 
 # --------------------------------------------------------------------------
-# Pin 8: the inner pivot-block solve (Sec. 5 / Sec. 6)
+# Pin 8: the inner pivot-block solve (Sec. 5 / Sec. 6).  Rotations one at a
+# time as R^T A R, row-cyclic (Sec. 5) or in the parallel strategy's pairs.
 # --------------------------------------------------------------------------
-def test_inner_solve_2x2_is_rotation(orc):
+ORDERS = ("cyclic", "parallel")
+
+
+def _pivot_block(nn, seed, rows=None, lo=-2):
+    rng = np.random.default_rng(seed)
+    Gp = rng.standard_normal((rows or 3 * nn, nn)) * (10.0 ** rng.uniform(lo, 0, nn))[None, :]
+    return Gp.T @ Gp
+
+
+def _congruence_checks(A, sg, Ao, Wp, passes=1):
+    """What every inner solve must give, whatever its pair order: W is
+    J-unitary (W^T J W = J), A_out is the congruence W^T A W, A_out stays
+    symmetric, and the eigenvalues of J A are unchanged (J A_out =
+    W^-1 (J A) W, a similarity), the last against LAPACK."""
+    nn = A.shape[0]
+    Jd = np.diag(sg.astype(float))
+    wmax = max(1.0, np.max(np.abs(Wp)) ** 2)
+    assert np.max(np.abs(Wp.T @ Jd @ Wp - Jd)) <= 8 * passes * nn * U * wmax
+    scale = np.abs(Wp).T @ np.abs(A) @ np.abs(Wp)
+    assert np.all(np.abs(Wp.T @ A @ Wp - Ao) <= 8 * passes * nn * U * scale)
+    assert np.array_equal(Ao, Ao.T)
+    ev_in = np.sort(np.linalg.eigvals(Jd @ A).real)
+    ev_out = np.sort(np.linalg.eigvals(Jd @ Ao).real)
+    assert np.allclose(ev_out, ev_in, rtol=1e-10, atol=0)
+
+
+@pytest.mark.parametrize("order", ORDERS)
+def test_inner_solve_2x2_is_rotation(orc, order):
     rng = np.random.default_rng(81)
     for hyp in (-1, 1):
         sg = np.array([1, 1 if hyp < 0 else -1], dtype=np.int8)
         x, y = rng.standard_normal(4), rng.standard_normal(4)
         A = np.array([[x @ x, x @ y], [x @ y, y @ y]])
-        Ao, Wp, nrot, passes, st = orc.inner_solve(A, sg, 1e-15, mode=0, max_passes=4)
         t, c, _ = orc.rotation(A[0, 0], A[1, 1], A[0, 1], hyp)
-        assert st == 0 and nrot == 1
-        assert np.allclose(Wp, c * np.array([[1.0, t], [hyp * t, 1.0]]), rtol=0, atol=4 * U)
-        assert Ao[0, 1] == 0.0
+        for mode in (0, 1, 2):
+            Ao, Wp, nrot, passes, st = orc.inner_solve(A, sg, 1e-15, mode=mode, max_passes=4, order=order)
+            assert st == 0 and nrot == 1
+            assert np.allclose(Wp, c * np.array([[1.0, t], [hyp * t, 1.0]]), rtol=0, atol=4 * U)
+            assert Ao[0, 1] == 0.0 and Ao[1, 0] == 0.0
 
 
+@pytest.mark.parametrize("order", ORDERS)
 @pytest.mark.parametrize("p", [0, 5, 16, 32])
-def test_inner_solve_full_block_diagonalises(orc, p):
+def test_inner_solve_full_block_diagonalises(orc, p, order):
     """Full-block mode: W^T A W = diag(A_out) with W J-unitary, so the
     eigenvalues of J A are J diag(A_out) (a similarity), checked by LAPACK."""
     nn = 32
-    rng = np.random.default_rng(90 + p)
-    Gp = rng.standard_normal((200, nn)) * (10.0 ** rng.uniform(-2, 0, nn))[None, :]
-    A = Gp.T @ Gp
+    A = _pivot_block(nn, 90 + p, rows=200)
     sg = W.signs_block(nn, p)
-    Ao, Wp, nrot, passes, st = orc.inner_solve(A, sg, _tol(nn), mode=0, max_passes=20)
+    Ao, Wp, nrot, passes, st = orc.inner_solve(A, sg, _tol(nn), mode=0, max_passes=20, order=order)
     assert st == 0 and passes < 20
-    Jd = np.diag(sg.astype(float))
-    assert np.max(np.abs(Wp.T @ Jd @ Wp - Jd)) <= 1e-12 * max(1.0, np.max(np.abs(Wp)) ** 2)
+    _congruence_checks(A, sg, Ao, Wp, passes)
     D = np.sqrt(np.diag(Ao))
     off = Ao - np.diag(np.diag(Ao))
     assert np.max(np.abs(off) / np.outer(D, D)) <= _tol(nn)
-    ev = np.sort(np.linalg.eigvals(Jd @ A).real)
+    ev = np.sort(np.linalg.eigvals(np.diag(sg.astype(float)) @ A).real)
     assert np.allclose(np.sort(sg * np.diag(Ao)), ev, rtol=1e-10, atol=0)
-    # A_out is the congruence W^T A W
-    assert np.max(np.abs(Wp.T @ A @ Wp - Ao)) <= 1e-12 * np.max(np.abs(A))
 
 
-def test_inner_solve_cross_pass_touches_only_cross_pairs(orc):
-    nn = 16
-    rng = np.random.default_rng(95)
-    Gp = rng.standard_normal((50, nn))
-    A = Gp.T @ Gp
-    sg = W.signs_block(nn, 5)
-    Ao, Wp, nrot, passes, st = orc.inner_solve(A, sg, _tol(nn), mode=1)
-    h = nn // 2
+def test_inner_solve_full_block_orders_agree(orc):
+    """Both pair orders diagonalise the same block to the same pencil
+    eigenvalues (each sign group sorted)."""
+    nn = 48
+    A = _pivot_block(nn, 97)
+    sg = W.signs_random(np.random.default_rng(3), nn, 20)
+    d = [orc.inner_solve(A, sg, _tol(nn), mode=0, max_passes=20, order=o)[0] for o in ORDERS]
+    for s in (1, -1):
+        a, b = np.sort(np.diag(d[0])[sg == s]), np.sort(np.diag(d[1])[sg == s])
+        assert np.allclose(a, b, rtol=1e-11, atol=0)
+
+
+def _hand_block(hyp):
+    """4 x 4 pivot block with two disjoint couplings, (0, 2) and (1, 3), and
+    its cross pass worked by hand.  Trigonometric (J = I): a_00 = a_22 = 2,
+    a_02 = 1, so zeta = 0, t = 1, c = 1/sqrt 2, the new diagonal 2 -+ 1 (Eq.
+    2.6).  Hyperbolic (J = diag(1, 1, -1, -1)): a_00 = a_22 = 5, a_02 = -4,
+    so zeta = 10/8, t = 1/(5/4 + 3/4) = 1/2, c = 1/sqrt(3/4), the new
+    diagonal 5 + t a_02 = 3 twice (J A has eigenvalues +-3).  The pair (0, 3)
+    and (1, 2) entries stay exactly zero, so the pass rotates two pairs."""
+    if hyp < 0:
+        a, b, sg, t, c, dp, dq = 2.0, 1.0, np.ones(4, dtype=np.int8), 1.0, 1 / np.sqrt(2.0), 1.0, 3.0
+    else:
+        a, b, sg, t, c, dp, dq = 5.0, -4.0, np.array([1, 1, -1, -1], dtype=np.int8), 0.5, 2 / np.sqrt(3.0), 3.0, 3.0
+    A = np.array([[a, 0, b, 0], [0, a, 0, b], [b, 0, a, 0], [0, b, 0, a]], dtype=float)
+    Wk = np.zeros((4, 4))
+    for p, q in ((0, 2), (1, 3)):
+        Wk[p, p], Wk[q, p] = c, hyp * t * c  # column p: (e_p + hyp t e_q) c
+        Wk[p, q], Wk[q, q] = t * c, c  # column q: (t e_p + e_q) c
+    return A, sg, Wk, np.diag([dp, dp, dq, dq])
+
+
+@pytest.mark.parametrize("order", ORDERS)
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("hyp", [-1, 1])
+def test_inner_solve_hand_worked_block(orc, mode, hyp, order):
+    A, sg, Wk, Dk = _hand_block(hyp)
+    Ao, Wp, nrot, passes, st = orc.inner_solve(A, sg, _tol(4), mode=mode, order=order)
+    assert st == 0 and nrot == 2 and passes == 1
+    assert np.max(np.abs(Wp - Wk)) <= 4 * U * np.max(np.abs(Wk))
+    assert np.max(np.abs(Ao - Dk)) <= 8 * U * np.max(np.abs(A))
+
+
+@pytest.mark.parametrize("order", ORDERS)
+@pytest.mark.parametrize("p", [0, 3, 8, 16])
+def test_inner_solve_cross_pass(orc, order, p):
+    """Cross pass (mode 1): a congruence by a J-unitary W that keeps J A's
+    eigenvalues (LAPACK), rotating only pairs of the off-diagonal block: at
+    most h^2 of them, and none at all when that block is zero, however full
+    the diagonal blocks are."""
+    nn, h = 16, 8
+    A = _pivot_block(nn, 95 + p, rows=50)
+    sg = W.signs_block(nn, p)
+    Ao, Wp, nrot, passes, st = orc.inner_solve(A, sg, _tol(nn), mode=1, order=order)
     assert st == 0 and passes == 1 and 0 < nrot <= h * h
+    _congruence_checks(A, sg, Ao, Wp)
+    Z = A.copy()
+    Z[:h, h:] = 0.0
+    Z[h:, :h] = 0.0
+    Zo, Wz, nz, _, st = orc.inner_solve(Z, sg, _tol(nn), mode=1, order=order)
+    assert st == 0 and nz == 0 and np.array_equal(Wz, np.eye(nn)) and np.array_equal(Zo, Z)
+
+
+@pytest.mark.parametrize("order", ORDERS)
+@pytest.mark.parametrize("mode", [1, 2])
+def test_inner_solve_visits_every_cross_pair_once(orc, order, mode):
+    """A pass visits every pair of the off-diagonal block once (Sec. 5): a
+    diagonal block with one coupling at (k, h + j), anywhere in that block,
+    is rotated exactly once, and the coupling ends exactly zero."""
+    nn, h = 16, 8
+    D = np.diag(np.arange(1.0, nn + 1.0))
+    sg = W.signs_block(nn, 5)
+    for k in range(h):
+        for j in range(h):
+            A = D.copy()
+            A[k, h + j] = A[h + j, k] = 0.25
+            Ao, Wp, nrot, passes, st = orc.inner_solve(A, sg, _tol(nn), mode=mode, order=order)
+            assert st == 0 and nrot == 1 and Ao[k, h + j] == 0.0, (k, j, nrot)
+
+
+@pytest.mark.parametrize("order", ORDERS)
+@pytest.mark.parametrize("mode", [1, 2])
+def test_inner_solve_one_pass_invariants(orc, order, mode):
+    """One pass (the cross pass, or one pass over the whole strict upper
+    triangle, Sec. 5): the congruence checks on graded blocks with mixed
+    signs; with J = I every rotation is orthogonal, so the Frobenius norm of
+    the block is kept and the off-diagonal mass can only fall (each rotation
+    removes 2 a_pq^2 of it); the pair the order visits last is exactly zero."""
+    for nn, seed in ((8, 1), (32, 2), (64, 3)):
+        h = nn // 2
+        A = _pivot_block(nn, 300 + seed, lo=-3)
+        for sg in (W.signs_block(nn, h), W.signs_random(np.random.default_rng(seed), nn, nn // 3),
+                   np.ones(nn, dtype=np.int8)):
+            Ao, Wp, nrot, passes, st = orc.inner_solve(A, sg, _tol(nn), mode=mode, order=order)
+            assert st == 0 and nrot > 0
+            _congruence_checks(A, sg, Ao, Wp)
+            if np.all(sg == 1):
+                assert abs(np.linalg.norm(Ao) - np.linalg.norm(A)) <= 4 * nn * U * np.linalg.norm(A)
+                off = lambda X: np.linalg.norm(X - np.diag(np.diag(X)))  # noqa: E731
+                assert off(Ao) <= off(A)
+            if order == "cyclic":
+                p, q = (h - 1, nn - 1) if mode == 1 else (nn - 2, nn - 1)
+                assert Ao[p, q] == 0.0 or abs(Ao[p, q]) < _tol(nn) * np.sqrt(Ao[p, p] * Ao[q, q])
 
 
 # --------------------------------------------------------------------------
