@@ -55,40 +55,50 @@ def _record(ms, r, J, sig, **extra):
                 err="%.1e" % _sigma_err(J, r.sigma.cpu().numpy(), sig))
 
 
-def table53(reps, n=4096):
+def _emit(out, rec):
+    print(json.dumps(rec), flush=True)
+    out.append(rec)
+
+
+def table53(reps, n=4096, ps=None):
     """Time and sweeps against the number p of positive signs, with and
     without diagonal sorting (Table 5.3); the split-precision form at every p,
-    plain FP64 at the ends."""
+    plain FP64 at the ends.  Returns the records printed."""
     bf16 = dict(precision=api.HSVD_PRECISION_BF16X8, block_w=64)
-    for p in (0, 1, 5, 10, 50, 100, 500, 1000, n // 2):
+    out = []
+    for p in ps or (0, 1, 5, 10, 50, 100, 500, 1000, n // 2):
         G, J, sig = W.paper(n, p=p, seed=6)
         forms = [("bf16x8", bf16)] + ([("fp64", dict(block_w=32))] if p in (0, n // 2) else [])
         for form, kw in forms:
             for sort in (True, False):
                 ms, r = _solve(G, J, reps, sort=sort, **kw)
-                print(json.dumps(_record(ms, r, J, sig, p=p, form=form, sort=sort)), flush=True)
+                _emit(out, _record(ms, r, J, sig, p=p, form=form, sort=sort))
+    return out
 
 
 def tstop(reps, n=4096):
     """The tangent-threshold stop (Sec. 2, Eq. 4.2) against the plain stop, at
     the paper's epsilon and at the library's default n 2^-53."""
     G, J, sig = W.paper(n, p=n // 2, seed=6)
+    out = []
     for form, kw in (("bf16x8", dict(precision=api.HSVD_PRECISION_BF16X8, block_w=64)), ("fp64", dict(block_w=32))):
         for tol_name, tol in (("2^-52", EPS), ("n 2^-53", n * 2.0 ** -53)):
             for t in (0.0, -1.0):
                 ms, r = _solve(G, J, reps, tol=tol, tstop=t, **kw)
-                print(json.dumps(_record(ms, r, J, sig, form=form, tol=tol_name,
-                                         tstop="T_eps" if t else "off")), flush=True)
+                _emit(out, _record(ms, r, J, sig, form=form, tol=tol_name, tstop="T_eps" if t else "off"))
+    return out
 
 
-def order(reps):
+def order(reps, sizes=(160, 288, 416, 544)):
     """Sweeps of the blocked method (modulus strategy over block columns,
     b = 16, sorted) at the paper's epsilon, on the sizes where the pivot
     orders are compared."""
-    for n in (160, 288, 416, 544):
+    out = []
+    for n in sizes:
         G, J, sig = W.paper(n, seed=6)
         ms, r = _solve(G, J, reps, block_w=16, tol=EPS, sort=True)
-        print(json.dumps(_record(ms, r, J, sig, n=n)), flush=True)
+        _emit(out, _record(ms, r, J, sig, n=n))
+    return out
 
 
 def main(argv=None):

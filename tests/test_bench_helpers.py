@@ -60,15 +60,45 @@ def test_accuracy_vs_golden_branches():
     if "note" in out:  # this host's libm rounds G differently: nothing is compared
         assert "not compared" in out["note"]
         return
-    assert out["sigma_max_rel_err"] == 0.0
+    assert out["sigma_max_rel_err"] == 0.0 and out["gate"] == "pass"
     s = ref[:, 0].copy()
-    k = int(np.argmax(ref[:, 1] <= 1e-12))  # a value whose floor is below 1e-12
+    k = int(np.argmax(2 * ref[:, 1] <= 1e-12))  # a value held to 1e-12
     s[k] *= 1.0 + 1e-10
     out = bench.accuracy_vs_golden(G, J, s)
-    assert abs(out["sigma_max_rel_err_where_floor_below_1e-12"] - 1e-10) < 1e-12
+    assert abs(out["sigma_max_rel_err_where_2floor_below_1e-12"] - 1e-10) < 1e-12
+    assert out["gate"] == "fail"
+    s = ref[:, 0].copy()
+    s[k] *= 1.0 + 0.9e-12
+    assert bench.accuracy_vs_golden(G, J, s)["gate"] == "pass"
+    # a value whose doubled floor is above 1e-12 may move by up to twice its floor
+    loose = np.where(2 * ref[:, 1] > 1e-12)[0]
+    if loose.size:
+        j = int(loose[0])
+        s = ref[:, 0].copy()
+        s[j] *= 1.0 + 1.5 * ref[j, 1]
+        assert bench.accuracy_vs_golden(G, J, s)["gate"] == "pass"
+        s[j] = ref[j, 0] * (1.0 + 3.0 * ref[j, 1])
+        assert bench.accuracy_vs_golden(G, J, s)["gate"] == "fail"
 
 
-@pytest.mark.parametrize("extra", [["--workload", "graded1024"], ["--workload", "batch10k", "--count", "16"]])
+def test_stored_oracle_values_are_well_formed():
+    """Every stored file: one row per column (sigma > 0, a floor u kappa_j
+    >= u, since kappa_j >= 1), a sweep count and the SHA-256 of G."""
+    import glob
+
+    files = sorted(glob.glob(os.path.join(bench.GOLDEN_DIR, "*_sigma.txt")))
+    assert files
+    for path in files:
+        name = os.path.basename(path)[:-len("_sigma.txt")]
+        head = [ln for ln in open(path) if ln.startswith("#")]
+        assert "sweeps=" in head[0] and head[1].startswith("# sha256(G)=")
+        ref = np.loadtxt(path)
+        assert ref.shape == (bench.WORKLOADS[name][0], 2)
+        assert np.all(ref[:, 0] > 0) and np.all(ref[:, 1] >= 2.0 ** -53 * (1 - 1e-12))
+
+
+@pytest.mark.parametrize("extra", [["--workload", "graded1024", "--form", "fp64"],
+                                   ["--workload", "batch10k", "--count", "16"], []])
 def test_reference_arm_line(extra):
     """The reference arm runs the oracle on the host alone and prints one
     JSON line with the GPU arm's metric, unit and workload string."""
@@ -76,8 +106,9 @@ def test_reference_arm_line(extra):
     import subprocess
     import sys
 
+    warm = "3" if extra else "0"  # the default workload's oracle sweep takes seconds here
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                          "--warmup", "3"] + extra, capture_output=True, text=True, timeout=600, cwd=ROOT)
+                          "--warmup", warm] + extra, capture_output=True, text=True, timeout=900, cwd=ROOT)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
     assert len(lines) == 1
@@ -85,7 +116,11 @@ def test_reference_arm_line(extra):
     assert d["impl"] == "reference" and d["unit"] == "TFLOP/s" and d["higher_is_better"] is True
     assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
-    assert d["steps"] == 1 and d["warmup"] == 3 and d["n_gpus"] == 1
-    if extra[1] == "graded1024":
+    assert d["steps"] == 1 and d["warmup"] == int(warm) and d["n_gpus"] == 1
+    if extra and extra[1] == "graded1024":
         assert d["metric"] == bench.metric_name("fp64")
         assert d["config"]["workload"] == bench.WORKLOADS["graded1024"][1]
+    if not extra:  # the default line: the metric on the Haar 4096 factor, a bounded sample per step
+        assert d["metric"] == bench.METRIC
+        assert d["config"]["workload"] == bench.WORKLOADS["haar4096"][1]
+        assert "first 2048 columns" in d["config"]["sample"]

@@ -1,0 +1,54 @@
+"""The paper's experiments module (Sec. 5: Table 5.3's p-sweep with sorting
+on and off, the T_eps stop against the plain stop, the sweeps of the pivot
+order) on small paper-shaped factors: every point converges (or, for the
+split-precision form at the paper's epsilon with the plain stop, may run out
+of sweeps, as at full size) and matches the known spectrum to 1e-12."""
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def exp():
+    from paper_1008_1371_gb300 import build_lib, experiments
+
+    build_lib.build()
+    assert torch.cuda.is_available()
+    return experiments
+
+
+def _ok(rec):
+    if rec["status"] != 0:
+        return False
+    return float(rec["err"]) <= 1e-12
+
+
+def test_table53_small(exp):
+    recs = exp.table53(1, n=256, ps=(0, 5, 128))
+    assert len(recs) == 3 * 2 + 2 * 2  # bf16x8 at every p, FP64 at p = 0 and n/2, sorted and unsorted
+    assert all(_ok(r) for r in recs), recs
+    assert {r["p"] for r in recs} == {0, 5, 128}
+
+
+def test_tstop_small(exp):
+    recs = exp.tstop(1, n=256)
+    assert len(recs) == 8
+    for r in recs:
+        if r["tstop"] == "T_eps":
+            assert _ok(r) and r["stop"] == 2, r  # HSVD_STOP_TANGENT
+        elif r["form"] == "bf16x8" and r["tol"] == "2^-52":
+            assert r["status"] in (0, 1), r  # the plain stop may lie below the products' rounding
+        else:
+            assert _ok(r) and r["stop"] == 1, r
+    # the tangent stop never takes more sweeps than the plain stop
+    for form in ("bf16x8", "fp64"):
+        for tol in ("2^-52", "n 2^-53"):
+            a = [r for r in recs if r["form"] == form and r["tol"] == tol]
+            plain, early = (x for x in sorted(a, key=lambda r: r["tstop"] != "off"))
+            assert early["sweeps"] <= plain["sweeps"]
+
+
+def test_order_small(exp):
+    recs = exp.order(1, sizes=(160, 288))
+    assert [r["n"] for r in recs] == [160, 288] and all(_ok(r) for r in recs), recs

@@ -162,13 +162,18 @@ def _invariants_gpu(G, J, sigma, U, V):
 
 
 def test_full_size_haar4096_split_vs_plain(api):
-    """The split-precision configuration at full size (Haar 4096, random J):
-    the oracle cannot finish it, so the checks are what holds at any size --
-    the invariants of Eq. 1.1, the eigenvalues of M = G J G^T from LAPACK
-    against sigma^2 J (absolute tolerance n u ||M||), and agreement with the
-    plain FP64 run within the per-value floor max(1e-12, u kappa_j)."""
+    """The split-precision configuration at full size (Haar 4096, random J),
+    split-precision and plain FP64 products, each gated per value against the
+    stored oracle values (the modulus-parallel CPU oracle on this factor,
+    tests/golden/haar4096_sigma.txt): within 1e-12 where the per-value floor
+    u kappa_j is below 1e-12, within 2 u kappa_j elsewhere.  Also the
+    invariants of Eq. 1.1 and the eigenvalues of M = G J G^T from LAPACK
+    against sigma^2 J (absolute tolerance n u ||M||)."""
+    import golden_ref
+
     n = 4096
     G, J = W.haar(n, seed=3)
+    ref_sigma, ref_floor = golden_ref.load("haar4096", G)
     dev = torch.device("cuda:0")
     Gd = torch.from_numpy(np.asfortranarray(G)).to(dev)
     Jd = torch.from_numpy(J).to(dev)
@@ -181,16 +186,9 @@ def test_full_size_haar4096_split_vs_plain(api):
     for r in (rx, r64):
         e1, e2, e3 = _invariants_gpu(Gd, Jd, r.sigma, r.U, r.V)
         assert e1 <= 1e-12 * n and e2 <= 1e-12 * n and e3 <= 1e-12 * n, (e1, e2, e3)
-    kap = (U64 * torch.linalg.vector_norm(Gd.abs() @ r64.V.abs(), dim=0) / r64.sigma).cpu().numpy()
-    sx, s64 = rx.sigma.cpu().numpy(), r64.sigma.cpu().numpy()
-    # which column ends with which value depends on the rotation sequence:
-    # compare per sign group, sorted
-    for sg in (1, -1):
-        idx = np.where(J == sg)[0]
-        o = np.argsort(s64[idx])
-        err = np.abs(np.sort(sx[idx]) - s64[idx][o]) / s64[idx][o] / np.maximum(1e-12, kap[idx][o])
-        assert np.max(err) <= 2.0, np.max(err)  # two runs, each within its floor
+        golden_ref.assert_gate(J, r.sigma.cpu().numpy(), ref_sigma, ref_floor)
     # eigenvalues of M = G J G^T against sigma^2 J
+    sx = rx.sigma.cpu().numpy()
     M = (G * J[None, :].astype(float)) @ G.T
     lam = np.sort(np.linalg.eigvalsh(M))
     mine = np.sort(sx ** 2 * J)
