@@ -149,6 +149,9 @@ typedef struct hsvd_opts {
     int schedule;         /* HSVD_SCHEDULE_* (blocked method); with the pair schedule
                              opts.profile reports only the sweep total, in ms_other  */
     int shorten;          /* HSVD_SHORTEN_*                                            */
+    int8_t *jout;         /* wide factor (m < n): receives the m signs of the result,
+                             lambda_j = sigma_j^2 jout_j (same kind of memory as G);
+                             may be NULL; unused for m >= n                           */
     int reserved[2];      /* must be zero                                              */
 } hsvd_opts;
 
@@ -170,7 +173,8 @@ typedef struct hsvd_info {
                              rotations                                                  */
     int64_t trace_rows;   /* rows written to trace_out                                 */
     int stop_rule;        /* HSVD_STOP_*: which rule ended the iteration               */
-    int shortened;        /* 1: the factor was shortened by a QR first                 */
+    int shortened;        /* 1: a tall factor was shortened by a QR first, 2: a wide
+                             one by the hyperbolic QR of its transpose              */
 } hsvd_info;
 
 /* Fills *opts with the defaults (tol = n 2^-53 at call time, 30 sweeps, auto
@@ -191,8 +195,16 @@ void hsvd_default_opts(hsvd_opts *opts);
  *   V      n x n, ldv >= n, may be NULL                               (output)
  *   sweeps may be NULL; receives the number of sweeps run
  * Sizes up to n = 2^24 and m = 2^31 are accepted (device memory permitting).
- * A wide factor (m < n) returns HSVD_ERR_ARG: the paper shortens it by a
- * hyperbolic QR of G^T (Sec. 1), which this library does not provide yet.
+ * A wide factor (m < n, m <= 2^24) is shortened first, as Sec. 1 prescribes,
+ * by a hyperbolic QR of G^T: T G^T C = [R; 0] with J-orthogonal Householder
+ * reflectors and row interchanges (T^T Jh T = J) and Bunch-Parlett column
+ * pivoting on the trailing J-Gram; the square F = C R^T (m x m) with the
+ * signature Jh_1 (the first m of Jh) satisfies G J G^T = F Jh_1 F^T, and its
+ * HSVD F V_F = U Sigma gives V = T^T [V_F; 0].  Then sigma has m entries, U is
+ * m x m (ldu >= m), V is n x m (ldv >= n) with G V = U Sigma and
+ * V^T J V = Jh_1; the m signs Jh_1 go to hsvd_opts.jout (hsvd_solve_ex), so
+ * the eigenvalues of M = G J G^T are sigma_j^2 jout_j.  G J G^T singular
+ * returns HSVD_ERR_RANK.
  */
 int hsvd_solve(const double *G, int64_t m, int64_t n, int64_t ldg, const int8_t *J,
                double tol, int max_sweeps, double *sigma, double *U, int64_t ldu,
@@ -275,21 +287,26 @@ int hsvd_pivot_update_x(double *X, int64_t rows, int64_t ldx, int npairs, const 
  * code that forbids allocation after start-up, memory-capped contexts.  The
  * paper has no counterpart; it is an interface choice of this library.
  *
- * Its scratch (the accumulated transformation and two status words) is a fixed
- * device array inside the library, sized for n <= HSVD_NOALLOC_MAX_N, that every
- * GPU which loads the library holds until the process exits (about 200 KB).
+ * Its scratch (the accumulated transformation W, three status ints -- status,
+ * sweeps, stop rule -- and a 64-bit rotation count) is a fixed device array
+ * inside the library, sized for n <= HSVD_NOALLOC_MAX_N, that every GPU which
+ * loads the library holds until the process exits (about 195 KB).  156 is the
+ * largest n whose square factor (m = n) fits one SM's shared memory, which the
+ * pointwise kernel needs anyway.
  * The caller passes inputs and outputs as DEVICE pointers with the meanings of
  * hsvd_solve; sort != 0 selects diagonal sorting (Sec. 4).  The call launches
  * on `stream`, then waits for it to read the status; it calls no cudaMalloc,
- * cudaFree or other allocating routine.  Sizes beyond the limit, or a factor
+ * cudaFree or other allocating routine.  n > HSVD_NOALLOC_MAX_N, or a factor
  * whose G does not fit one SM's shared memory (m x n FP64 up to about 200 KB),
- * return HSVD_ERR_ARG.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current: make that first call
- * before any stream capture.  Every call on a device shares the one array, so
- * calls that overlap on the GPU (other streams, other host threads) race: issue
- * them one after the other.  Nothing has to be cleared between calls.
+ * returns HSVD_ERR_ARG.  The first call on a device (and the first after a
+ * cudaDeviceReset) looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current: make that first call before any stream capture.
+ * Every call on a device shares the one array, so calls that overlap on the GPU
+ * (other streams, other host threads) race: issue them one after the other.
+ * Nothing has to be cleared between calls: the kernel writes every scratch
+ * word before it reads it.
  */
-#define HSVD_NOALLOC_MAX_N 160
+#define HSVD_NOALLOC_MAX_N 156
 int hsvd_solve_pointwise_noalloc(const double *G, int64_t m, int64_t n, int64_t ldg, const int8_t *J,
                                  double tol, int max_sweeps, int sort, double *sigma, double *U,
                                  int64_t ldu, double *V, int64_t ldv, int *sweeps, void *stream);
@@ -319,16 +336,24 @@ int hsvd_diag_wait_timeout(void *stream);
  * eigenproblem into an HSVD (Sec. 1): M (n x n, ldm, device, symmetric; only
  * read) = G J G^T with G (n x n, ldg, device) and J (n signs, device, int8),
  * from M = P L D L^T P^T with complete (Bunch-Parlett) pivoting, D of 1 x 1 and
- * 2 x 2 blocks.  Returns HSVD_ERR_RANK for a zero pivot (M singular) or a
+ * 2 x 2 blocks.  A singular M is postprocessed (Sec. 1): the factorisation
+ * stops once the trailing matrix is zero, and M = G_r J_r G_r^T with the first
+ * r columns of G (full column rank) and r signs; the columns and signs past r
+ * are zero, and *rank (may be NULL) receives r.  Returns HSVD_ERR_RANK for a
  * non-finite entry, HSVD_ERR_ARG for bad sizes or host pointers.  Returns after
  * the results are complete.
  *
  * hsvd_sym_eig -- the eigendecomposition M = U diag(lambda) U^T through the
  * factorisation and the HSVD of G (opts and info as for hsvd_solve_ex; NULL
  * opts = defaults): lambda[j] = sigma_j^2 J_jj with eigenvector U(:, j) (n x n,
- * ldu, device; may be NULL).  Device arrays only.
+ * ldu, device; may be NULL).  For a singular M of rank r the HSVD of the
+ * n x r factor G_r (shortened by QR) gives the first r pairs; lambda[r..n-1]
+ * are zero with eigenvectors spanning the orthogonal complement of range(G_r)
+ * (the last n - r columns of the Q of a QR of U(:, 0..r-1)).  Device arrays
+ * only.
  */
-int hsvd_sym_factor(const double *M, int64_t n, int64_t ldm, double *G, int64_t ldg, int8_t *J, void *stream);
+int hsvd_sym_factor(const double *M, int64_t n, int64_t ldm, double *G, int64_t ldg, int8_t *J, int64_t *rank,
+                    void *stream);
 int hsvd_sym_eig(const double *M, int64_t n, int64_t ldm, double *lambda, double *U, int64_t ldu,
                  const hsvd_opts *opts, hsvd_info *info, void *stream);
 

@@ -467,9 +467,9 @@ done:
 /*   1 the parallel order: the steps of the modified modulus strategy over    */
 /*     the nn indices (Sec. 2, Alg. 4.3/4.4), or for the cross pass the steps */
 /*     s = 0 .. h-1 pairing k with h + ((k + s) mod h), h = nn/2; the         */
-/*     disjoint pairs of a step are applied one after the other in task      */
-/*     order (they touch disjoint rows and columns, so their rotation         */
-/*     parameters do not depend on that order).                              */
+/*     disjoint pairs of a step are applied one after the other in ascending */
+/*     order of their smaller index (they touch disjoint rows and columns,    */
+/*     so their rotation parameters do not depend on that order).            */
 /* Modes:                                                                     */
 /*   0 full-block: passes over all pairs p < q until a pass rotates nothing   */
 /*     or max_passes passes ran (Sec. 6);                                     */
@@ -532,6 +532,7 @@ int orc_inner_solve(int nn, double *A, const int8_t *sgn, double tol, int mode, 
         pairs = (int *)malloc(sizeof(int) * (size_t)nn * (size_t)h * 2);
         orc_modulus_pairs(nn, nn, pairs);
     }
+    int *step_p = (int *)malloc(sizeof(int) * (size_t)h), *step_q = (int *)malloc(sizeof(int) * (size_t)h);
     memset(W, 0, sizeof(double) * (size_t)nn * nn);
     for (int i = 0; i < nn; ++i) W[i + (int64_t)i * nn] = 1.0;
     double tmax = 0.0;
@@ -548,8 +549,9 @@ int orc_inner_solve(int nn, double *A, const int8_t *sgn, double tol, int mode, 
                     status = inner_pair(nn, A, W, sgn, tol, p, q, &nrot, &tmax);
         } else {
             const int nsteps = (mode == 1) ? h : nn;
-            for (int s = 0; s < nsteps && status == ORC_OK; ++s)
-                for (int k = 0; k < h && status == ORC_OK; ++k) {
+            for (int s = 0; s < nsteps && status == ORC_OK; ++s) {
+                /* the step's pairs (p < q), applied in ascending order of p */
+                for (int k = 0; k < h; ++k) {
                     int a, b;
                     if (mode == 1) {
                         a = k;
@@ -558,8 +560,23 @@ int orc_inner_solve(int nn, double *A, const int8_t *sgn, double tol, int mode, 
                         a = pairs[(s * h + k) * 2];
                         b = pairs[(s * h + k) * 2 + 1];
                     }
-                    status = inner_pair(nn, A, W, sgn, tol, a < b ? a : b, a < b ? b : a, &nrot, &tmax);
+                    step_p[k] = a < b ? a : b;
+                    step_q[k] = a < b ? b : a;
                 }
+                for (int k = 1; k < h; ++k) { /* insertion sort by p */
+                    const int pk = step_p[k], qk = step_q[k];
+                    int x = k - 1;
+                    while (x >= 0 && step_p[x] > pk) {
+                        step_p[x + 1] = step_p[x];
+                        step_q[x + 1] = step_q[x];
+                        --x;
+                    }
+                    step_p[x + 1] = pk;
+                    step_q[x + 1] = qk;
+                }
+                for (int k = 0; k < h && status == ORC_OK; ++k)
+                    status = inner_pair(nn, A, W, sgn, tol, step_p[k], step_q[k], &nrot, &tmax);
+            }
         }
         nrot_total += nrot;
         if (nrot == 0) break;
@@ -568,6 +585,8 @@ int orc_inner_solve(int nn, double *A, const int8_t *sgn, double tol, int mode, 
     if (passes_out) *passes_out = npass;
     if (tmax_out) *tmax_out = tmax;
     free(pairs);
+    free(step_p);
+    free(step_q);
     return status;
 }
 
@@ -749,8 +768,12 @@ done:
 /* G = P L B: B = sqrt|d| on a 1 x 1 block, Q sqrt|Lambda| on a 2 x 2 block    */
 /* D = Q Lambda Q^T (a Jacobi rotation with the smaller angle), J = the signs. */
 /* The whole symmetric matrix is kept; every product is an explicit fma.      */
-/* Returns ORC_OK, ORC_RANK (a zero pivot) or ORC_ARG.  perm (may be NULL)    */
-/* receives the original index held at each position.                        */
+/* R16 (postprocessing of a singular M): when the whole trailing matrix is   */
+/* zero after r steps, M = G J G^T holds with the first r columns of G (full */
+/* column rank) and r signs; the columns and signs past r are returned as     */
+/* zeros and *rank_out (may be NULL) = r.  Returns ORC_OK, ORC_RANK (a non-   */
+/* finite entry) or ORC_ARG.  perm (may be NULL) receives the original index */
+/* held at each position.                                                    */
 /* ------------------------------------------------------------------------ */
 static void orc_sym_swap(int n, double *A, int k, int a, int b)
 {
@@ -772,9 +795,11 @@ static void orc_sym_swap(int n, double *A, int k, int a, int b)
     A[b + (int64_t)b * n] = t;
 }
 
-int orc_sym_factor(int64_t n64, const double *M, int64_t ldm, double *G, int64_t ldg, int8_t *J, int *perm_out)
+int orc_sym_factor(int64_t n64, const double *M, int64_t ldm, double *G, int64_t ldg, int8_t *J, int *perm_out,
+                   int *rank_out)
 {
     if (n64 < 1 || ldm < n64 || ldg < n64 || n64 > (1 << 20)) return ORC_ARG;
+    if (!all_finite(n64, n64, M, ldm)) return ORC_RANK;
     const int n = (int)n64;
     double *A = (double *)malloc(sizeof(double) * (size_t)n * n);
     double *D = (double *)calloc((size_t)4 * n, sizeof(double));
@@ -799,6 +824,7 @@ int orc_sym_factor(int64_t n64, const double *M, int64_t ldm, double *G, int64_t
             }
         }
         const double mu0 = dmax > omax ? dmax : omax;
+        if (mu0 == 0.0) break; /* R16: the trailing matrix is zero, M has rank k */
         int s;
         if (k == n - 1 || omax <= 0.0 || dmax >= alpha * mu0) {
             s = 1;
@@ -855,8 +881,14 @@ int orc_sym_factor(int64_t n64, const double *M, int64_t ldm, double *G, int64_t
         }
         k += s;
     }
+    const int rank = k < n ? k : n;
     if (status == ORC_OK) {
         for (int j = 0; j < n; ++j) {
+            if (j >= rank) { /* past the rank: no column, no sign */
+                for (int i = 0; i < n; ++i) G[i + (int64_t)j * ldg] = 0.0;
+                J[j] = 0;
+                continue;
+            }
             const int b0 = bs[j] == 0 ? j - 1 : j, size = bs[b0];
             double c0, c1, sgn;
             if (size == 1) {
@@ -897,6 +929,7 @@ int orc_sym_factor(int64_t n64, const double *M, int64_t ldm, double *G, int64_t
         }
         if (perm_out)
             for (int i = 0; i < n; ++i) perm_out[i] = perm[i];
+        if (rank_out) *rank_out = rank;
     }
     free(A); free(D); free(perm); free(bs);
     return status;

@@ -83,7 +83,7 @@ def _bind(lib):
     lib.orc_block_hsvd.argtypes = [_i64, _i64, _p, _i64, _p, _int, _dbl, _int, _int, _int,
                                    _int, _int, _p, _p, _i64, _p, _i64, _p, _p, _dbl, _p]
     lib.orc_block_hsvd.restype = _int
-    lib.orc_sym_factor.argtypes = [_i64, _p, _i64, _p, _i64, _p, _p]
+    lib.orc_sym_factor.argtypes = [_i64, _p, _i64, _p, _i64, _p, _p, _p]
     lib.orc_sym_factor.restype = _int
     lib.orc_hyp_qr.argtypes = [_i64, _i64, _p, _i64, _p, _p, _i64, _p, _p, _p, _i64, _p, _p, _p]
     lib.orc_hyp_qr.restype = _int
@@ -208,15 +208,20 @@ def block_hsvd(G, J, b, tol, max_sweeps=30, inner_mode=0, inner_max_passes=8, so
     return dict(sigma=sigma, U=U, V=V, sweeps=sweeps.value, rotations=rots.value, status=st, stop=stop.value)
 
 
-def sym_factor(M, lib=None):
+def sym_factor(M, lib=None, want_rank=False):
     """(G, J, perm, status) with M = G J G^T (Bunch-Parlett pivoting) for a
-    symmetric M; perm[i] is the original index at position i."""
+    symmetric M; perm[i] is the original index at position i.  A singular M
+    stops once the trailing matrix is zero: with ``want_rank`` the rank r is
+    returned fifth, and G's columns and J's entries past r are zero."""
     M = np.asfortranarray(np.asarray(M, dtype=np.float64))
     n = M.shape[0]
     G = np.zeros((n, n), order="F")
     J = np.zeros(n, dtype=np.int8)
     perm = np.zeros(n, dtype=np.int32)
-    st = (lib or _load()).orc_sym_factor(n, _ptr(M), n, _ptr(G), n, _ptr(J), _ptr(perm))
+    rank = _int()
+    st = (lib or _load()).orc_sym_factor(n, _ptr(M), n, _ptr(G), n, _ptr(J), _ptr(perm), ctypes.byref(rank))
+    if want_rank:
+        return G, J, perm, st, rank.value
     return G, J, perm, st
 
 

@@ -62,7 +62,8 @@ class HsvdOpts(ctypes.Structure):
     _fields_ = [("tol", _dbl), ("max_sweeps", _int), ("method", _int), ("block_w", _int),
                 ("inner_mode", _int), ("inner_max_passes", _int), ("sort", _int), ("profile", _int),
                 ("precision", _int), ("skip_model", _p), ("skip_tau", _dbl), ("trace_out", _p),
-                ("trace_cap", _i64), ("tstop", _dbl), ("schedule", _int), ("shorten", _int), ("reserved", _int * 2)]
+                ("trace_cap", _i64), ("tstop", _dbl), ("schedule", _int), ("shorten", _int), ("jout", _p),
+                ("reserved", _int * 2)]
 
 
 class HsvdInfo(ctypes.Structure):
@@ -112,7 +113,7 @@ def lib():
             L.hsvd_modulus_pairs.restype = _int
             L.hsvd_diag_wait_timeout.argtypes = [_p]
             L.hsvd_diag_wait_timeout.restype = _int
-            L.hsvd_sym_factor.argtypes = [_p, _i64, _i64, _p, _i64, _p, _p]
+            L.hsvd_sym_factor.argtypes = [_p, _i64, _i64, _p, _i64, _p, _p, _p]
             L.hsvd_sym_factor.restype = _int
             L.hsvd_sym_eig.argtypes = [_p, _i64, _i64, _p, _p, _i64, ctypes.POINTER(HsvdOpts),
                                        ctypes.POINTER(HsvdInfo), _p]
@@ -240,6 +241,7 @@ class HsvdResult:
     trace_rows: int = 0
     stop_rule: int = HSVD_STOP_NONE
     shortened: int = 0
+    jout: Optional[torch.Tensor] = None  # wide factor: the m signs of the result (lambda = sigma^2 jout)
 
 
 HSVD_SORT_AUTO = -1
@@ -288,30 +290,39 @@ def hsvd_solve_ex(G, J, opts=None, compute_u=True, compute_v=True, stream=None, 
     ``G`` (m x n float64) and ``J`` (n signs) are both CUDA tensors or both
     CPU tensors (pinned memory makes the copies asynchronous).  ``opts`` is an
     :class:`HsvdOpts` (see :func:`make_opts`).  ``out`` may hold preallocated
-    (sigma, U, V) tensors in column-major layout.  Returns an
-    :class:`HsvdResult`; raises :class:`HsvdError` on a negative status when
-    ``check``.
+    (sigma, U, V) tensors in column-major layout.  A wide factor (m < n) is
+    shortened by the hyperbolic QR of G^T first: sigma has m entries, U is
+    m x m, V is n x m with V^T J V = diag(jout), and the result's ``jout``
+    holds the m signs (the eigenvalues of G J G^T are sigma^2 jout).  Returns
+    an :class:`HsvdResult`; raises :class:`HsvdError` on a negative status
+    when ``check``.
     """
     L = lib()
     Gc = _colmajor(G, torch.float64)
     m, n = Gc.shape
+    r = min(m, n)  # values and singular vectors
     Jc = J.to(torch.int8).contiguous()
     if Jc.device != Gc.device:
         raise ValueError("G and J must be on the same device")
     _need(Jc.dim() == 1 and Jc.numel() == n, "J: one sign per column of G (%d) expected" % n)
+    pin = Gc.device.type == "cpu" and Gc.is_pinned()
     if out is not None:
         sigma, U, V = out
-        _check_vec(sigma, n, torch.float64, Gc.device, "sigma")
+        _check_vec(sigma, r, torch.float64, Gc.device, "sigma")
         if U is not None:
-            _check_colmajor(U, m, n, Gc.device, "U")
+            _check_colmajor(U, m, r, Gc.device, "U")
         if V is not None:
-            _check_colmajor(V, n, n, Gc.device, "V")
+            _check_colmajor(V, n, r, Gc.device, "V")
     else:
-        sigma = torch.empty(n, dtype=torch.float64, device=Gc.device,
-                            pin_memory=(Gc.device.type == "cpu" and Gc.is_pinned()))
-        U = _empty_colmajor(m, n, Gc) if compute_u else None
-        V = _empty_colmajor(n, n, Gc) if compute_v else None
+        sigma = torch.empty(r, dtype=torch.float64, device=Gc.device, pin_memory=pin)
+        U = _empty_colmajor(m, r, Gc) if compute_u else None
+        V = _empty_colmajor(n, r, Gc) if compute_v else None
     o = opts if opts is not None else make_opts()
+    jout = None
+    if m < n:
+        o = HsvdOpts.from_buffer_copy(o)
+        jout = torch.zeros(m, dtype=torch.int8, device=Gc.device, pin_memory=pin)
+        o.jout = jout.data_ptr()
     info = HsvdInfo()
     st = L.hsvd_solve_ex(Gc.data_ptr(), m, n, Gc.stride(1) if n > 1 else m, Jc.data_ptr(), sigma.data_ptr(),
                          U.data_ptr() if U is not None else None, _ld(U, m) if U is not None else m,
@@ -322,7 +333,7 @@ def hsvd_solve_ex(G, J, opts=None, compute_u=True, compute_v=True, stream=None, 
     return HsvdResult(sigma, U, V, info.sweeps, st, info.method, info.block_w, info.rotations, info.pair_updates,
                       info.kernel_launches, info.ms_gram, info.ms_solve, info.ms_update, info.ms_other,
                       info.pair_visits, info.masked_sweeps, info.judge_sweeps, info.trace_rows, info.stop_rule,
-                      info.shortened)
+                      info.shortened, jout)
 
 
 def hsvd_solve(G, J, tol=0.0, max_sweeps=30, compute_u=True, compute_v=True, stream=None, check=True):
@@ -342,19 +353,22 @@ def hsvd_modulus_pairs(r, nsteps=None):
     return out
 
 
-def hsvd_sym_factor(M, stream=None):
-    """(G, J) with M = G J G^T for a symmetric CUDA float64 tensor M (n x n)."""
+def hsvd_sym_factor(M, stream=None, want_rank=False):
+    """(G, J) with M = G J G^T for a symmetric CUDA float64 tensor M (n x n).
+    A singular M of rank r gives zero columns and signs past r; with
+    ``want_rank`` the rank is returned third."""
     L = lib()
     Mc = _colmajor(M, torch.float64)
     n = Mc.shape[0]
     _need(Mc.shape[1] == n, "M must be square")
     G = _empty_colmajor(n, n, Mc)
     J = torch.empty(n, dtype=torch.int8, device=Mc.device)
+    rank = ctypes.c_int64(0)
     st = L.hsvd_sym_factor(Mc.data_ptr(), n, Mc.stride(1) if n > 1 else n, G.data_ptr(), G.stride(1) if n > 1 else n,
-                           J.data_ptr(), _stream_ptr(stream, Mc.device))
+                           J.data_ptr(), ctypes.byref(rank), _stream_ptr(stream, Mc.device))
     if st != HSVD_OK:
         raise HsvdError(st)
-    return G, J
+    return (G, J, rank.value) if want_rank else (G, J)
 
 
 def hsvd_sym_eig(M, opts=None, compute_u=True, stream=None):

@@ -675,6 +675,115 @@ int solve_shortened(const double *G, int64_t m, int64_t n, int64_t ldg, const in
     return rc;
 }
 
+// A wide factor (m < n, Sec. 1): the hyperbolic QR of G^T (hypqr.cu) gives the
+// square F = C R^T with signature Jh_1, whose HSVD F V_F = U Sigma gives
+// V = T^T [V_F; 0]: G V = U Sigma and V^T J V = Jh_1.
+int solve_wide(const double *G, int64_t m, int64_t n, int64_t ldg, const int8_t *J, double *sigma, double *U,
+               int64_t ldu, double *V, int64_t ldv, const hsvd_opts *opts_in, hsvd_info *info, void *stream) {
+    Range range("hsvd wide solve");
+    hsvd_opts o;
+    if (opts_in) o = *opts_in;
+    else hsvd_default_opts(&o);
+    auto fail = [&](int rc) {
+        if (info) info->status = rc;
+        return rc;
+    };
+    if (!G || !J || !sigma || m < 1 || n <= m || ldg < m || n > ((int64_t)1 << 24)) return fail(HSVD_ERR_ARG);
+    if ((U && ldu < m) || (V && ldv < n)) return fail(HSVD_ERR_ARG);
+    const bool dev = is_device_ptr(G);
+    const void *arrs[5] = {J, sigma, U, V, o.jout};
+    for (int i = 0; i < 5; ++i)
+        if (arrs[i] && is_device_ptr(arrs[i]) != dev) return fail(HSVD_ERR_ARG);
+    cudaStream_t user = static_cast<cudaStream_t>(stream), st = nullptr;
+    cudaEvent_t ev = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return fail(HSVD_ERR_CUDA);
+    int rc = HSVD_OK;
+    long long nl = 0;
+    {
+        Ws ws(st);
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventRecord(ev, user) != cudaSuccess || cudaStreamWaitEvent(st, ev, 0) != cudaSuccess)
+            rc = HSVD_ERR_CUDA;
+        HypQr hq = {};
+        hq.A = ws.get<double>((size_t)n * m);
+        hq.C = ws.get<double>((size_t)m * m);
+        hq.Vr = ws.get<double>((size_t)n * m);
+        hq.z = ws.get<double>((size_t)n);
+        hq.beta = ws.get<double>((size_t)m);
+        hq.cperm = ws.get<int>((size_t)m);
+        hq.rswap = ws.get<int>((size_t)m);
+        hq.drows = ws.get<int>(4);
+        hq.s = ws.get<int8_t>((size_t)n);
+        hq.bsize = ws.get<int8_t>((size_t)m);
+        hq.state = ws.get<unsigned char>(hypqr_state_bytes());
+        hq.mx = ws.get<unsigned char>(hypqr_mx_bytes(m));
+        double *F = ws.get<double>((size_t)m * m);
+        int8_t *Jh1 = ws.get<int8_t>((size_t)m);
+        double *VF = V ? ws.get<double>((size_t)m * m) : nullptr;
+        const double *g = G;
+        const int8_t *j = J;
+        double *s = sigma, *u = U, *v = V;
+        int64_t lg = ldg, lu = ldu, lv = ldv;
+        if (!dev) {  // host arrays: staged through device memory
+            double *dG = ws.get<double>((size_t)m * n);
+            int8_t *dJ = ws.get<int8_t>((size_t)n);
+            s = ws.get<double>((size_t)m);
+            u = U ? ws.get<double>((size_t)m * m) : nullptr;
+            v = V ? ws.get<double>((size_t)n * m) : nullptr;
+            lg = m;
+            lu = m;
+            lv = n;
+            if (!dG || !dJ || !s || (U && !u) || (V && !v)) rc = HSVD_ERR_NOMEM;
+            else if (cudaMemcpy2DAsync(dG, sizeof(double) * m, G, sizeof(double) * ldg, sizeof(double) * m, n,
+                                       cudaMemcpyHostToDevice, st) != cudaSuccess ||
+                     cudaMemcpyAsync(dJ, J, (size_t)n, cudaMemcpyHostToDevice, st) != cudaSuccess)
+                rc = HSVD_ERR_CUDA;
+            g = dG;
+            j = dJ;
+        }
+        if (rc == HSVD_OK && (!hq.A || !hq.C || !hq.Vr || !hq.z || !hq.beta || !hq.cperm || !hq.rswap ||
+                              !hq.drows || !hq.s || !hq.bsize || !hq.state || !hq.mx || !F || !Jh1 || (V && !VF)))
+            rc = HSVD_ERR_NOMEM;
+        if (rc == HSVD_OK) rc = hypqr_factor(g, m, n, lg, j, hq, F, st, &nl);
+        if (rc == HSVD_OK) {
+            if (cudaMemcpyAsync(Jh1, hq.s, (size_t)m, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess)
+                rc = HSVD_ERR_CUDA;
+        }
+        if (rc == HSVD_OK) {
+            // the square F with the signature Jh_1, on the internal stream
+            hsvd_opts o2 = o;
+            o2.jout = nullptr;
+            rc = hsvd_solve_ex(F, m, m, m, Jh1, s, u, lu, VF, m, &o2, info, st);
+        }
+        if ((rc == HSVD_OK || rc == HSVD_NOT_CONVERGED) && V &&
+            hypqr_apply_tt(hq, m, n, VF, v, lv, st, &nl) != HSVD_OK)
+            rc = HSVD_ERR_CUDA;
+        if ((rc == HSVD_OK || rc == HSVD_NOT_CONVERGED) && o.jout &&
+            cudaMemcpyAsync(o.jout, Jh1, (size_t)m, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st) !=
+                cudaSuccess)
+            rc = HSVD_ERR_CUDA;
+        if (!dev && (rc == HSVD_OK || rc == HSVD_NOT_CONVERGED)) {
+            if (cudaMemcpyAsync(sigma, s, sizeof(double) * m, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                (U && cudaMemcpy2DAsync(U, sizeof(double) * ldu, u, sizeof(double) * m, sizeof(double) * m, m,
+                                        cudaMemcpyDeviceToHost, st) != cudaSuccess) ||
+                (V && cudaMemcpy2DAsync(V, sizeof(double) * ldv, v, sizeof(double) * n, sizeof(double) * n, m,
+                                        cudaMemcpyDeviceToHost, st) != cudaSuccess))
+                rc = HSVD_ERR_CUDA;
+        }
+        if (cudaStreamSynchronize(st) != cudaSuccess && rc >= 0) rc = HSVD_ERR_CUDA;
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess && rc >= 0) rc = HSVD_ERR_CUDA;
+    if (ev) cudaEventDestroy(ev);
+    cudaStreamDestroy(st);
+    if (info) {
+        info->kernel_launches += nl;
+        info->shortened = 2;
+        info->status = rc;
+    }
+    return rc;
+}
+
 int validate(const double *G, int64_t m, int64_t n, int64_t ldg, const int8_t *J, const double *sigma, int64_t ldu,
              const double *U, int64_t ldv, const double *V) {
     if (!G || !J || !sigma) return HSVD_ERR_ARG;
@@ -727,6 +836,7 @@ int hsvd_solve_ex(const double *G, int64_t m, int64_t n, int64_t ldg, const int8
     if (opts_in) o = *opts_in;
     else hsvd_default_opts(&o);
     if (info) memset(info, 0, sizeof *info);
+    if (G && m >= 1 && n > m) return solve_wide(G, m, n, ldg, J, sigma, U, ldu, V, ldv, opts_in, info, stream);
     int rc = validate(G, m, n, ldg, J, sigma, ldu, U, ldv, V);
     if (rc == HSVD_OK) {
         for (int i = 0; i < 2; ++i)
@@ -886,11 +996,12 @@ int hsvd_diag_wait_timeout(void *stream) {
     return rc;
 }
 
-int hsvd_sym_factor(const double *M, int64_t n, int64_t ldm, double *G, int64_t ldg, int8_t *J, void *stream) {
+int hsvd_sym_factor(const double *M, int64_t n, int64_t ldm, double *G, int64_t ldg, int8_t *J, int64_t *rank,
+                    void *stream) {
     Range range("hsvd_sym_factor");
     if (!M || !G || !J || n < 1 || n > ((int64_t)1 << 20) || ldm < n || ldg < n) return HSVD_ERR_ARG;
     if (!is_device_ptr(M) || !is_device_ptr(G) || !is_device_ptr(J)) return HSVD_ERR_ARG;
-    return ldl_factor(M, n, ldm, G, ldg, J, static_cast<cudaStream_t>(stream), nullptr);
+    return ldl_factor(M, n, ldm, G, ldg, J, static_cast<cudaStream_t>(stream), nullptr, rank);
 }
 
 namespace {
@@ -898,6 +1009,13 @@ __global__ void k_sym_lambda(const double *__restrict__ sigma, const int8_t *__r
                              double *__restrict__ lambda) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j < n) lambda[j] = sigma[j] * sigma[j] * (double)J[j];
+}
+// X (n x (n - r), ldx) <- [0; I_(n-r)]
+__global__ void k_sym_null_init(double *__restrict__ X, int64_t ldx, int64_t n, int64_t r) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * (n - r)) return;
+    const int64_t i = e % n, c = e / n;
+    X[i + c * ldx] = (i == r + c) ? 1.0 : 0.0;
 }
 }  // namespace
 
@@ -907,26 +1025,52 @@ int hsvd_sym_eig(const double *M, int64_t n, int64_t ldm, double *lambda, double
     if (!M || !lambda || n < 1 || n > ((int64_t)1 << 20) || ldm < n || (U && ldu < n)) return HSVD_ERR_ARG;
     if (!is_device_ptr(M) || !is_device_ptr(lambda) || (U && !is_device_ptr(U))) return HSVD_ERR_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    double *G = nullptr, *sigma = nullptr;
-    int8_t *J = nullptr;
     int rc = HSVD_OK;
-    if (cudaMallocAsync((void **)&G, sizeof(double) * n * n, st) != cudaSuccess ||
-        cudaMallocAsync((void **)&sigma, sizeof(double) * n, st) != cudaSuccess ||
-        cudaMallocAsync((void **)&J, (size_t)n, st) != cudaSuccess)
-        rc = HSVD_ERR_NOMEM;
     long long nl = 0;
-    if (rc == HSVD_OK) rc = ldl_factor(M, n, ldm, G, n, J, st, &nl);
-    if (rc == HSVD_OK) {
-        rc = hsvd_solve_ex(G, n, n, n, J, sigma, U, ldu, nullptr, n, opts, info, stream);
-        if (rc == HSVD_OK || rc == HSVD_NOT_CONVERGED) {
-            k_sym_lambda<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(sigma, J, n, lambda);
-            if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) rc = HSVD_ERR_CUDA;
-            nl += 1;
+    int64_t r = 0;
+    {
+        Ws ws(st);
+        double *G = ws.get<double>((size_t)n * n), *sigma = ws.get<double>((size_t)n);
+        int8_t *J = ws.get<int8_t>((size_t)n);
+        if (!G || !sigma || !J) rc = HSVD_ERR_NOMEM;
+        if (rc == HSVD_OK) rc = ldl_factor(M, n, ldm, G, n, J, st, &nl, &r);
+        // eigenvalues past the rank of a singular M are zero; the HSVD of the
+        // n x r factor gives the others
+        if (rc == HSVD_OK && cudaMemsetAsync(lambda, 0, sizeof(double) * n, st) != cudaSuccess) rc = HSVD_ERR_CUDA;
+        if (rc == HSVD_OK && r > 0) {
+            rc = hsvd_solve_ex(G, n, r, n, J, sigma, U, ldu, nullptr, r, opts, info, stream);
+            if (rc == HSVD_OK || rc == HSVD_NOT_CONVERGED) {
+                k_sym_lambda<<<(unsigned)((r + 255) / 256), 256, 0, st>>>(sigma, J, r, lambda);
+                if (cudaGetLastError() != cudaSuccess) rc = HSVD_ERR_CUDA;
+                nl += 1;
+            }
         }
+        // eigenvectors of the zero eigenvalues: the orthogonal complement of
+        // range(U_r) = range(G_r), the last n - r columns of the full Q of a QR
+        // of U_r
+        if ((rc == HSVD_OK || rc == HSVD_NOT_CONVERGED) && U && r < n) {
+            double *A = ws.get<double>((size_t)n * (r > 0 ? r : 1));
+            double *qws = ws.get<double>(qr_workspace_doubles(r > 0 ? r : 1));
+            if (!A || !qws) {
+                rc = HSVD_ERR_NOMEM;
+            } else {
+                double *Un = U + r * ldu;
+                const int64_t tot = n * (n - r);
+                k_sym_null_init<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(Un, ldu, n, r);  // [0; I_(n-r)]
+                nl += 1;
+                if (cudaGetLastError() != cudaSuccess)
+                    rc = HSVD_ERR_CUDA;
+                else if (r > 0 &&
+                         (cudaMemcpy2DAsync(A, sizeof(double) * n, U, sizeof(double) * ldu, sizeof(double) * n, r,
+                                            cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+                          qr_factor(A, n, n, r, qws, st, &nl) != cudaSuccess ||
+                          qr_apply_q(A, n, n, r, qws, Un, ldu, st, &nl, n - r) != cudaSuccess))
+                    rc = HSVD_ERR_CUDA;
+                if (cudaStreamSynchronize(st) != cudaSuccess && rc >= 0) rc = HSVD_ERR_CUDA;
+            }
+        }
+        if (cudaStreamSynchronize(st) != cudaSuccess && rc >= 0) rc = HSVD_ERR_CUDA;
     }
-    if (G) cudaFreeAsync(G, st);
-    if (sigma) cudaFreeAsync(sigma, st);
-    if (J) cudaFreeAsync(J, st);
     cudaStreamSynchronize(st);
     if (info) {
         info->kernel_launches += nl;

@@ -180,7 +180,6 @@ cudaError_t launch_solve(int b, int npairs, const double *part, int nsplit, doub
                          unsigned long long *rot_count, int *status, cudaStream_t st,
                          int full_part = 0, int *dexp = nullptr, const int *visit = nullptr,
                          float *trace = nullptr, double tstop = 0.0, int *tbig = nullptr);
-
 // precision.cu: the bounded mbarrier wait run out on purpose (a diagnostic)
 cudaError_t launch_diag_wait(uint32_t iters, int *out, cudaStream_t st);
 
@@ -190,15 +189,36 @@ size_t qr_workspace_doubles(int64_t n);
 cudaError_t qr_factor(double *A, int64_t lda, int64_t m, int64_t n, double *ws, cudaStream_t st,
                       long long *launches);
 // U (m x n) <- Q U, Q from the reflectors in A and the T factors in ws
+// U (m x ncols, ldu) <- Q U; ncols = 0 means n
 cudaError_t qr_apply_q(double *A, int64_t lda, int64_t m, int64_t n, double *ws, double *U, int64_t ldu,
-                       cudaStream_t st, long long *launches);
+                       cudaStream_t st, long long *launches, int64_t ncols = 0);
 cudaError_t qr_extract_r(const double *A, int64_t lda, int64_t n, double *R, int64_t ldr, cudaStream_t st);
 cudaError_t qr_embed_u(const double *UR, int64_t ldur, int64_t m, int64_t n, double *U, int64_t ldu,
                        cudaStream_t st);
 
+// hypqr.cu: the hyperbolic QR of G^T for a wide G (m < n).  Device buffers,
+// filled by the caller: A, Vr (n x m), C (m x m), z (n), beta (m), cperm,
+// rswap (m), drows (4), s (n), bsize (m), state and mx (hypqr_state_bytes,
+// hypqr_mx_bytes).
+struct HypQr {
+    double *A, *C, *Vr, *z, *beta;
+    int *cperm, *rswap, *drows;
+    int8_t *s, *bsize;
+    void *state, *mx;
+};
+size_t hypqr_state_bytes();
+size_t hypqr_mx_bytes(int64_t m);
+// F = C R^T (m x m) from T G^T C = [R; 0]; hq.s ends as Jh (the first m: the
+// signature of F).  HSVD_OK, HSVD_ERR_RANK (G J G^T singular) or HSVD_ERR_CUDA.
+int hypqr_factor(const double *G, int64_t m, int64_t n, int64_t ldg, const int8_t *J, HypQr &hq, double *F,
+                 cudaStream_t st, long long *launches);
+// V (n x m, ldv) <- T^T [V_F; 0]; consumes hq.s
+int hypqr_apply_tt(HypQr &hq, int64_t m, int64_t n, const double *VF, double *V, int64_t ldv, cudaStream_t st,
+                   long long *launches);
+
 // ldl.cu: M = G J G^T by Bunch-Parlett pivoting (device arrays)
 int ldl_factor(const double *M, int64_t n, int64_t ldm, double *G, int64_t ldg, int8_t *J, cudaStream_t st,
-               long long *launches);
+               long long *launches, int64_t *rank);
 
 // learned form (learned.cu)
 cudaError_t launch_features(const float *trace, const int8_t *prev_skip, const int *tab, int nvis, int b, int nb,

@@ -37,8 +37,8 @@ constexpr int kUpdThreads = 256;
 struct LdlState {
     int k;       // first column of the current step
     int s;       // its size (1 or 2; 0 once k reaches n)
-    int bad;     // a zero pivot (M singular): HSVD_ERR_RANK
-    int pad;
+    int bad;     // a non-finite entry (or no pivot found): HSVD_ERR_RANK
+    int rank;    // columns factored: n, or the step at which the trailing matrix was zero
     double d[4];  // the step's D block, row-major
 };
 
@@ -132,7 +132,11 @@ k_ldl_pivot(double *__restrict__ M, int64_t ld, int n, LdlState *__restrict__ st
         for (int w = 1; w < kPivThreads / 32; ++w) max_merge(t, red[w]);
         const double alpha = (1.0 + sqrt(17.0)) / 8.0;
         const double mu0 = fmax(t.dmax, t.omax), mu1 = t.dmax;
-        if (k == n - 1 || t.omax <= 0.0 || mu1 >= alpha * mu0) {
+        if (t.di >= k && t.di < n && mu0 == 0.0) {
+            // the trailing matrix is zero: M has rank k (the postprocessing of a
+            // singular M keeps the k columns found so far)
+            s_choice[0] = -1;
+        } else if (k == n - 1 || t.omax <= 0.0 || mu1 >= alpha * mu0) {
             s_choice[0] = 1;
             s_choice[1] = t.di;
         } else {
@@ -141,12 +145,21 @@ k_ldl_pivot(double *__restrict__ M, int64_t ld, int n, LdlState *__restrict__ st
             s_choice[2] = t.r < t.q ? t.q : t.r;
         }
         // no valid pivot (NaN or Inf in the trailing matrix): stop with an error
-        const bool valid = s_choice[0] == 1 ? (s_choice[1] >= k && s_choice[1] < n)
-                                            : (s_choice[1] >= k && s_choice[2] < n && s_choice[1] < s_choice[2]);
+        const bool valid = s_choice[0] == -1 ||
+                           (s_choice[0] == 1 ? (s_choice[1] >= k && s_choice[1] < n)
+                                             : (s_choice[1] >= k && s_choice[2] < n && s_choice[1] < s_choice[2]));
         if (!valid) s_choice[0] = 0;
     }
     __syncthreads();
     const int s = s_choice[0];
+    if (s == -1) {
+        if (tid == 0) {
+            st->rank = k;
+            st->s = 0;
+            st->k = n;
+        }
+        return;
+    }
     if (s == 0) {
         if (tid == 0) {
             st->bad = 1;
@@ -315,7 +328,7 @@ __global__ void k_ldl_lstore(double *__restrict__ M, int64_t ld, int n, LdlState
 
 // maxima of the whole matrix before the first pivot
 __global__ void __launch_bounds__(kUpdThreads)
-k_ldl_max0(const double *__restrict__ M, int64_t ld, int n, LdlMax *__restrict__ mx) {
+k_ldl_max0(const double *__restrict__ M, int64_t ld, int n, LdlMax *__restrict__ mx, LdlState *__restrict__ st) {
     __shared__ LdlMax red[kUpdThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     LdlMax a = max_none();
@@ -323,6 +336,7 @@ k_ldl_max0(const double *__restrict__ M, int64_t ld, int n, LdlMax *__restrict__
     for (int64_t e = (int64_t)blockIdx.x * kUpdThreads + tid; e < total; e += (int64_t)gridDim.x * kUpdThreads) {
         const int i = (int)(e % n), j = (int)(e / n);
         const double av = fabs(M[i + (int64_t)j * ld]);
+        if (!(av <= 1.7976931348623157e308)) atomicExch(&st->bad, 1);  // NaN or Inf in M
         if (i == j) {
             if (av > a.dmax || (av == a.dmax && i < a.di)) {
                 a.dmax = av;
@@ -361,8 +375,14 @@ k_ldl_max0(const double *__restrict__ M, int64_t ld, int n, LdlMax *__restrict__
 // matrix holds original index perm[i]: G(perm[i], j) = (L B)(i, j).
 __global__ void k_ldl_form_g(const double *__restrict__ M, int64_t ld, int n, const int *__restrict__ perm,
                              const double *__restrict__ Dblk, const int8_t *__restrict__ bsize,
-                             double *__restrict__ G, int64_t ldg, int8_t *__restrict__ J) {
+                             double *__restrict__ G, int64_t ldg, int8_t *__restrict__ J,
+                             const LdlState *__restrict__ st) {
     const int j = blockIdx.x;  // one CTA per column of G
+    if (j >= st->rank) {       // past the rank of a singular M: no column, no sign
+        for (int i = threadIdx.x; i < n; i += blockDim.x) G[i + (int64_t)j * ldg] = 0.0;
+        if (threadIdx.x == 0) J[j] = 0;
+        return;
+    }
     const int bs = bsize[j];
     int b0 = j;                  // first column of j's block
     if (bs == 0) b0 = j - 1;
@@ -415,10 +435,12 @@ constexpr int kUpdGrid = 608;
 }  // namespace
 
 // M (n x n, ldm, device, symmetric; read-only) -> G (n x n, ldg, device) and
-// J (n, device) with M = G J G^T.  Returns HSVD_OK or HSVD_ERR_RANK (a zero
-// pivot: M singular).
+// J (n, device) with M = G J G^T.  A singular M stops once the trailing matrix
+// is zero: *rank (may be NULL) receives the columns factored, and G's columns
+// and J's entries past it are zero.  Returns HSVD_OK or HSVD_ERR_RANK (a
+// non-finite entry).
 int ldl_factor(const double *M, int64_t n, int64_t ldm, double *G, int64_t ldg, int8_t *J, cudaStream_t st,
-               long long *launches) {
+               long long *launches, int64_t *rank) {
     double *W = nullptr, *Dblk = nullptr;
     int *perm = nullptr;
     int8_t *bsize = nullptr;
@@ -441,12 +463,13 @@ int ldl_factor(const double *M, int64_t n, int64_t ldm, double *G, int64_t ldg, 
         std::vector<int> p((size_t)n);
         for (int64_t i = 0; i < n; ++i) p[(size_t)i] = (int)i;
         LdlState s0 = {};
+        s0.rank = (int)n;
         ok(cudaMemcpy2DAsync(W, sizeof(double) * n, M, sizeof(double) * ldm, sizeof(double) * n, n,
                              cudaMemcpyDeviceToDevice, st));
         ok(cudaMemcpyAsync(perm, p.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
         ok(cudaMemcpyAsync(state, &s0, sizeof s0, cudaMemcpyHostToDevice, st));
         ok(cudaMemsetAsync(bsize, 1, (size_t)n, st));
-        k_ldl_max0<<<kUpdGrid, kUpdThreads, 0, st>>>(W, n, (int)n, mx);
+        k_ldl_max0<<<kUpdGrid, kUpdThreads, 0, st>>>(W, n, (int)n, mx, state);
         ok(cudaGetLastError());
         // every step takes one or two columns: n (pivot, update, store) rounds
         // cover the worst case, rounds past the end return at once
@@ -456,12 +479,13 @@ int ldl_factor(const double *M, int64_t n, int64_t ldm, double *G, int64_t ldg, 
             k_ldl_lstore<<<1, 256, 0, st>>>(W, n, (int)n, state);
             ok(cudaGetLastError());
         }
-        k_ldl_form_g<<<(unsigned)n, 256, 0, st>>>(W, n, (int)n, perm, Dblk, bsize, G, ldg, J);
+        k_ldl_form_g<<<(unsigned)n, 256, 0, st>>>(W, n, (int)n, perm, Dblk, bsize, G, ldg, J, state);
         ok(cudaGetLastError());
         LdlState fin = {};
         if (ok(cudaMemcpyAsync(&fin, state, sizeof fin, cudaMemcpyDeviceToHost, st)) &&
             ok(cudaStreamSynchronize(st)) && fin.bad)
             rc = HSVD_ERR_RANK;
+        if (rank) *rank = fin.rank;
         if (launches) *launches += 2 + 3 * n;
     }
     if (W) cudaFreeAsync(W, st);

@@ -558,19 +558,26 @@ cudaError_t qr_factor(double *A, int64_t lda, int64_t m, int64_t n, double *ws, 
     return cudaSuccess;
 }
 
-// U (m x n, ldu) holds [U_R; 0] on entry; U <- Q U with the reflectors in A and
-// the T factors in ws (as left by qr_factor).
+// U (m x ncols, ldu; ncols = 0: n) holds [U_R; 0] on entry; U <- Q U with the
+// reflectors in A and the T factors in ws (as left by qr_factor).  The
+// workspace holds partials for min(n, 2048) columns, so U is taken in chunks
+// of that many columns.
 cudaError_t qr_apply_q(double *A, int64_t lda, int64_t m, int64_t n, double *ws, double *U, int64_t ldu,
-                       cudaStream_t st, long long *launches) {
+                       cudaStream_t st, long long *launches, int64_t ncols) {
     const int64_t panels = (n + kQB - 1) / kQB;
     double *Tall = ws, *tau = Tall + (size_t)panels * kQB * kQB;
-    double *part = tau + n, *Z = part + (size_t)64 * kQB * std::min<int64_t>(n, kMaxCols);
-    for (int64_t p = panels - 1; p >= 0; --p) {
-        const int j0 = (int)(p * kQB), w = (int)std::min<int64_t>(kQB, n - j0);
-        const cudaError_t e = apply_panel(A, lda, m, j0, w, Tall + (size_t)p * kQB * kQB, 0, U, ldu, 0, (int)n,
-                                          part, Z, st);
-        if (e != cudaSuccess) return e;
-        *launches += 3 * ((n + kMaxCols - 1) / kMaxCols);
+    const int64_t wcols = std::min<int64_t>(n, kMaxCols);
+    double *part = tau + n, *Z = part + (size_t)64 * kQB * wcols;
+    if (ncols <= 0) ncols = n;
+    for (int64_t c0 = 0; c0 < ncols; c0 += wcols) {
+        const int nc = (int)std::min<int64_t>(wcols, ncols - c0);
+        for (int64_t p = panels - 1; p >= 0; --p) {
+            const int j0 = (int)(p * kQB), w = (int)std::min<int64_t>(kQB, n - j0);
+            const cudaError_t e = apply_panel(A, lda, m, j0, w, Tall + (size_t)p * kQB * kQB, 0, U, ldu, (int)c0,
+                                              nc, part, Z, st);
+            if (e != cudaSuccess) return e;
+            *launches += 3;
+        }
     }
     return cudaSuccess;
 }

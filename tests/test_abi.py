@@ -63,8 +63,11 @@ def test_argument_errors_without_gpu(api):
     J = np.ones(4, dtype=np.int8)
     s = np.zeros(4)
     p = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
-    # m < n, ldg < m, n < 1, bad pair-table argument
-    assert L.hsvd_solve(p(G), 3, 4, 4, p(J), 0.0, 30, p(s), None, 3, None, 4, None, None) == api.HSVD_ERR_ARG
+    # a wide factor (m < n) with ldu < m, with ldv < n, with ldg < m; ldg < m; n < 1; bad pair-table argument
+    U = np.zeros((4, 4))
+    assert L.hsvd_solve(p(G), 3, 4, 4, p(J), 0.0, 30, p(s), p(U), 2, None, 4, None, None) == api.HSVD_ERR_ARG
+    assert L.hsvd_solve(p(G), 3, 4, 4, p(J), 0.0, 30, p(s), None, 3, p(U), 3, None, None) == api.HSVD_ERR_ARG
+    assert L.hsvd_solve(p(G), 3, 4, 2, p(J), 0.0, 30, p(s), None, 3, None, 4, None, None) == api.HSVD_ERR_ARG
     assert L.hsvd_solve(p(G), 4, 4, 3, p(J), 0.0, 30, p(s), None, 4, None, 4, None, None) == api.HSVD_ERR_ARG
     assert L.hsvd_solve(p(G), 4, 0, 4, p(J), 0.0, 30, p(s), None, 4, None, 4, None, None) == api.HSVD_ERR_ARG
     assert L.hsvd_solve(None, 4, 4, 4, p(J), 0.0, 30, p(s), None, 4, None, 4, None, None) == api.HSVD_ERR_ARG
@@ -207,9 +210,9 @@ def test_sym_argument_errors_without_gpu(api):
     J = np.zeros(4, dtype=np.int8)
     lam = np.zeros(4)
     p = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
-    assert L.hsvd_sym_factor(p(M), 4, 4, p(G), 4, p(J), None) == api.HSVD_ERR_ARG  # host arrays
-    assert L.hsvd_sym_factor(p(M), 0, 4, p(G), 4, p(J), None) == api.HSVD_ERR_ARG
-    assert L.hsvd_sym_factor(p(M), 4, 3, p(G), 4, p(J), None) == api.HSVD_ERR_ARG
+    assert L.hsvd_sym_factor(p(M), 4, 4, p(G), 4, p(J), None, None) == api.HSVD_ERR_ARG  # host arrays
+    assert L.hsvd_sym_factor(p(M), 0, 4, p(G), 4, p(J), None, None) == api.HSVD_ERR_ARG
+    assert L.hsvd_sym_factor(p(M), 4, 3, p(G), 4, p(J), None, None) == api.HSVD_ERR_ARG
     info = api.HsvdInfo()
     assert L.hsvd_sym_eig(p(M), 4, 4, p(lam), None, 4, None, ctypes.byref(info), None) == api.HSVD_ERR_ARG
 

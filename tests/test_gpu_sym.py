@@ -88,10 +88,56 @@ def test_eig_against_lapack(api, kind, n):
         assert np.max(np.abs(np.sort(lam) - ref) / np.abs(ref)) <= 1e-10
 
 
-@pytest.mark.parametrize("n", [8, 31])
-def test_singular_matrix(api, n):
-    """The zero matrix, and a saddle point matrix of odd order (rank n - 1)."""
-    M = np.zeros((n, n)) if n == 8 else _sym("saddle", n, 38)
+def _singular(case):
+    rng = np.random.default_rng(91)
+    if case == "zero":
+        return np.zeros((8, 8))
+    if case == "saddle31":  # odd order: rank 30
+        return _sym("saddle", 31, 38)
+    if case == "block":  # [[A, 0], [0, 0]], A random symmetric of order 40, permuted
+        M = np.zeros((64, 64))
+        A = rng.standard_normal((40, 40))
+        M[:40, :40] = A + A.T
+        p = rng.permutation(64)
+        return M[np.ix_(p, p)]
+    v = np.array([1.0, 2.0, 0.0, 4.0, 0.5, 0.0])  # v v^T - w w^T, every step exact
+    w = np.array([0.0, 1.0, 8.0, 0.0, 2.0, 0.25])
+    return np.outer(v, v) - np.outer(w, w)
+
+
+@pytest.mark.parametrize("case", ["zero", "saddle31", "block", "pow2"])
+def test_singular_matrix_factor(api, case):
+    """A singular M (the factorisation with postprocessing, Sec. 1): the GPU
+    stops where the oracle stops, with the same rank, G and J bit for bit."""
+    import oracle
+
+    M = _singular(case)
+    G, J, r = api.hsvd_sym_factor(torch.from_numpy(np.asfortranarray(M)).cuda(), want_rank=True)
+    Go, Jo, perm, st, ro = oracle.sym_factor(M, want_rank=True)
+    assert st == 0 and r == ro < M.shape[0]
+    assert np.array_equal(J.cpu().numpy(), Jo) and np.array_equal(G.cpu().numpy(), Go)
+
+
+@pytest.mark.parametrize("case", ["zero", "saddle31", "block", "pow2"])
+def test_singular_matrix_eig(api, case):
+    """The eigendecomposition of a singular M: r eigenvalues from the HSVD of
+    the n x r factor, the others zero, with an orthonormal basis of the null
+    space: against LAPACK, U^T U = I and M U = U diag(lambda)."""
+    M = _singular(case)
+    n = M.shape[0]
+    lam, U, info = api.hsvd_sym_eig(torch.from_numpy(np.asfortranarray(M)).cuda())
+    assert info.status == api.HSVD_OK
+    lam, U = lam.cpu().numpy(), U.cpu().numpy()
+    ev = np.linalg.eigvalsh(M)
+    nrm = max(np.max(np.abs(ev)), 1.0)
+    assert np.max(np.abs(np.sort(lam) - ev)) <= 10 * n * U64 * nrm
+    assert np.max(np.abs(U.T @ U - np.eye(n))) <= 1e-12 * n
+    assert np.max(np.linalg.norm(M @ U - U * lam[None, :], axis=0)) <= 10 * n * U64 * nrm
+
+
+def test_non_finite_matrix(api):
+    M = np.eye(6)
+    M[2, 4] = M[4, 2] = np.inf
     with pytest.raises(api.HsvdError) as e:
         api.hsvd_sym_factor(torch.from_numpy(np.asfortranarray(M)).cuda())
     assert e.value.status == api.HSVD_ERR_RANK

@@ -61,9 +61,50 @@ def test_pivot_rule_by_hand(orc):
     assert st == 0 and perm.tolist() == [1, 0]
 
 
-def test_singular(orc):
-    assert orc.sym_factor(np.zeros((5, 5)))[3] == orc.ORC_RANK
-    M = np.diag([1.0, -1.0, 0.0])
+def _numerical_rank(M):
+    ev = np.linalg.eigvalsh(M)
+    return int(np.sum(np.abs(ev) > M.shape[0] * U * max(np.max(np.abs(ev)), 1e-300))), ev
+
+
+@pytest.mark.parametrize("case", ["zero", "diag", "saddle9", "saddle31", "block", "pow2"])
+def test_singular_postprocessing(orc, case):
+    """A singular M (Sec. 1, the factorisation with postprocessing; reading
+    R16): the factorisation stops once the trailing matrix is zero, with rank
+    r = the number of nonzero eigenvalues (LAPACK), M = G_r J_r G_r^T for the
+    first r columns, G_r of full column rank, J_r's inertia that of M, and
+    zeros past r."""
+    rng = np.random.default_rng(77)
+    if case == "zero":
+        M = np.zeros((5, 5))
+    elif case == "diag":
+        M = np.diag([1.0, -1.0, 0.0])
+    elif case.startswith("saddle"):  # odd order: rank n - 1
+        M = _sym("saddle", int(case[6:]), 38)
+    elif case == "block":  # [[A, 0], [0, 0]] with A random symmetric of order 7
+        M = np.zeros((12, 12))
+        A = rng.standard_normal((7, 7))
+        M[:7, :7] = A + A.T
+        p = rng.permutation(12)
+        M = M[np.ix_(p, p)]
+    else:  # v v^T - w w^T with power-of-two entries: every step exact
+        v = np.array([1.0, 2.0, 0.0, 4.0, 0.5, 0.0])
+        w = np.array([0.0, 1.0, 8.0, 0.0, 2.0, 0.25])
+        M = np.outer(v, v) - np.outer(w, w)
+    n = M.shape[0]
+    G, J, perm, st, r = orc.sym_factor(M, want_rank=True)
+    want, ev = _numerical_rank(M)
+    assert st == 0 and r == want, (r, want)
+    assert np.all(G[:, r:] == 0.0) and np.all(J[r:] == 0) and set(J[:r].tolist()) <= {-1, 1}
+    Gr, Jr = G[:, :r], J[:r].astype(float)
+    assert np.max(np.abs((Gr * Jr[None, :]) @ Gr.T - M)) <= 50 * n * U * max(np.max(np.abs(M)), 1.0)
+    assert int((Jr > 0).sum()) == int((ev > n * U * np.max(np.abs(ev) + 1e-300)).sum())
+    if r:
+        assert np.linalg.svd(Gr, compute_uv=False)[-1] > 1e-8 * np.linalg.norm(Gr)
+
+
+def test_non_finite_is_rank_error(orc):
+    M = np.eye(4)
+    M[2, 1] = M[1, 2] = np.nan
     assert orc.sym_factor(M)[3] == orc.ORC_RANK
 
 
@@ -75,7 +116,24 @@ MUTANTS = {
     "column_swap_dropped": ("    for (int i = k; i < n; ++i) { /* columns a, b in the trailing rows but a and b */",
                             "    for (int i = n; i < n; ++i) { /* columns a, b in the trailing rows but a and b */"),
     "schur_angle_sign": ("                    c1 = -sn * sqrt(fabs(l1));", "                    c1 = sn * sqrt(fabs(l1));"),
+    "rank_stop_dropped": ("        if (mu0 == 0.0) break; /* R16: the trailing matrix is zero, M has rank k */\n", ""),
 }
+
+
+def _battery_fails(orc, lib):
+    for kind, n in (("random", 30), ("saddle", 20), ("random", 9), ("saddle", 9)):
+        M = _sym(kind, n, 5 + n)
+        G, J, perm, st = orc.sym_factor(M, lib=lib)
+        ev = np.linalg.eigvalsh(M)
+        pos = int((ev > n * U * np.max(np.abs(ev))).sum())
+        if st != 0 or not np.all(np.isfinite(G)) or _residual(G, J, M) > 50 * n * U \
+                or int((J > 0).sum()) != pos:
+            return True
+    return False
+
+
+def test_battery_passes_on_oracle(orc):
+    assert not _battery_fails(orc, orc.load())
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
@@ -86,12 +144,4 @@ def test_residual_catches_planted_mistake(orc, tmp_path, name):
     path = tmp_path / ("orc_%s.c" % name)
     path.write_text(src.replace(old, new))
     lib = orc.load(orc.build(force=True, src=str(path), out=str(tmp_path / ("liborc_%s.so" % name))))
-    bad = False
-    for kind, n in (("random", 30), ("saddle", 20), ("random", 9)):
-        M = _sym(kind, n, 5 + n)
-        G, J, perm, st = orc.sym_factor(M, lib=lib)
-        ev = np.linalg.eigvalsh(M)
-        if st != 0 or not np.all(np.isfinite(G)) or _residual(G, J, M) > 50 * n * U \
-                or int((J > 0).sum()) != int((ev > 0).sum()):
-            bad = True
-    assert bad, "planted mistake %s went unnoticed" % name
+    assert _battery_fails(orc, lib), "planted mistake %s went unnoticed" % name
