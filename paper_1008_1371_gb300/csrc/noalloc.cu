@@ -5,9 +5,14 @@
 // caching allocator of a host framework owns the device, real-time or
 // safety-critical callers that forbid allocation after start-up, and callers
 // on memory-capped contexts.  For them this entry point allocates nothing:
-// its scratch (the accumulated transformation W and two status words) lives
-// in `g_noalloc_scratch`, a file-scope device array of a fixed, modest size
-// that every GPU which loads the library keeps until the process exits.
+// its scratch lives in `g_noalloc_scratch`, a file-scope device array of a
+// fixed, modest size that every GPU which loads the library keeps until the
+// process exits.  The array holds, for n_pad = n rounded up to even:
+//   [0, n_pad^2)            doubles: the accumulated transformation W
+//   kStatusOff (n_pad^2)    three ints: status, sweeps, stop rule
+//   kRotOff (n_pad^2 + 2)   one 64-bit integer: the rotation count
+#include <cuda.h>
+
 #include <mutex>
 
 #include "hsvd_internal.cuh"
@@ -15,30 +20,73 @@
 namespace hsvd {
 namespace {
 
-// W of up to HSVD_NOALLOC_MAX_N + 1 bordered columns, then the status words
 constexpr int64_t kNoallocMaxPad = HSVD_NOALLOC_MAX_N + (HSVD_NOALLOC_MAX_N & 1);
-constexpr int64_t kScratchDoubles = kNoallocMaxPad * kNoallocMaxPad + 8;
+constexpr int64_t status_off(int64_t n_pad) { return n_pad * n_pad; }  // in doubles
+constexpr int64_t rot_off(int64_t n_pad) { return n_pad * n_pad + 2; }  // in doubles
+constexpr int64_t kScratchDoubles = kNoallocMaxPad * kNoallocMaxPad + 4;
+// three ints fit the two doubles before the rotation count, and the count
+// fits the array at the largest n
+static_assert(3 * sizeof(int) <= 2 * sizeof(double), "status words overrun the rotation count");
+static_assert(rot_off(kNoallocMaxPad) + 1 <= kScratchDoubles, "scratch array too small");
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
-double *g_scratch_ptr[kMaxDevices] = {nullptr};
+struct ScratchAddr {
+    unsigned long long ctx_id;  // the context the address belongs to (0: unknown)
+    double *ptr;
+};
+ScratchAddr g_scratch[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device (set up once per
-// device; the host-side name of the array is not a device address).
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
+// Identity of the current context, 0 if it cannot be read.  A device reset
+// (cudaDeviceReset) ends the context and reloads the module with the array
+// at a possibly different address; the new context has a new identity.
+unsigned long long current_context_id() {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        looked_up = true;
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
+    }
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
+// Device address of the scratch array in the current device's context.  The
+// host-side name of the array is not a device address; the address is looked
+// up (cudaGetSymbolAddress, which allocates nothing) with the device current,
+// once per device and context, and again after a device reset.
 cudaError_t scratch_for_current_device(double **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
+    const unsigned long long ctx = current_context_id();
+    ScratchAddr &s = g_scratch[dev];
+    if (!s.ptr || ctx == 0 || s.ctx_id != ctx) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = static_cast<double *>(p);
+        s.ptr = static_cast<double *>(p);
+        s.ctx_id = ctx;
     }
-    *out = g_scratch_ptr[dev];
+    *out = s.ptr;
     return cudaSuccess;
 }
 
@@ -60,8 +108,8 @@ extern "C" int hsvd_solve_pointwise_noalloc(const double *G, int64_t m, int64_t 
     if (scratch_for_current_device(&scratch) != cudaSuccess) return HSVD_ERR_CUDA;
     const int64_t n_pad = n + (n & 1);
     double *W = scratch;
-    int *out = reinterpret_cast<int *>(scratch + n_pad * n_pad);
-    long long *rot = reinterpret_cast<long long *>(scratch + n_pad * n_pad + 2);
+    int *out = reinterpret_cast<int *>(scratch + status_off(n_pad));
+    long long *rot = reinterpret_cast<long long *>(scratch + rot_off(n_pad));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // the kernel writes every scratch word it later reads (W = I first, the
     // status words last), so nothing has to be cleared between calls

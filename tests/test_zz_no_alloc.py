@@ -61,7 +61,10 @@ def _alloc(api, G, J, tol, sort):
 def test_noalloc_matches_allocating_entry_point_twice(api):
     from paper_1008_1371_gb300 import workloads
 
-    cases = [(workloads.gaussian(128, seed=1), True), (workloads.gaussian(37, m=50, p=11, seed=3), False)]
+    # n = 156 is the largest square factor the limit allows: the scratch array
+    # is then nearly full
+    cases = [(workloads.gaussian(128, seed=1), True), (workloads.gaussian(37, m=50, p=11, seed=3), False),
+             (workloads.gaussian(156, p=70, seed=4), True)]
     for (G, J), sort in cases:
         n = G.shape[1]
         tol = n * U64
@@ -75,12 +78,14 @@ def test_noalloc_matches_allocating_entry_point_twice(api):
             assert np.max(np.abs(V - V_a)) <= 1e-12 * n * max(1.0, np.max(np.abs(V_a)))
 
 
-def test_noalloc_rejects_sizes_beyond_its_limit(api):
+@pytest.mark.parametrize("m,n", [(157, 157), (200, 200), (300, 150)])
+def test_noalloc_rejects_sizes_beyond_its_limit(api, m, n):
+    """n above HSVD_NOALLOC_MAX_N = 156, or a G too tall for one SM's shared
+    memory: HSVD_ERR_ARG before anything is launched."""
     dev = torch.device("cuda:0")
-    n = 200  # above HSVD_NOALLOC_MAX_N
-    G = torch.zeros((n, n), dtype=torch.float64, device=dev)
+    G = torch.zeros((n, m), dtype=torch.float64, device=dev).t()
     J = torch.ones(n, dtype=torch.int8, device=dev)
     s = torch.empty(n, dtype=torch.float64, device=dev)
-    st = api.lib().hsvd_solve_pointwise_noalloc(G.data_ptr(), n, n, n, J.data_ptr(), 0.0, 30, 1, s.data_ptr(),
-                                                None, n, None, n, None, None)
+    st = api.lib().hsvd_solve_pointwise_noalloc(G.data_ptr(), m, n, m, J.data_ptr(), 0.0, 30, 1, s.data_ptr(),
+                                                None, m, None, n, None, None)
     assert st == api.HSVD_ERR_ARG
