@@ -195,8 +195,9 @@ cudaError_t update_impl(double *X, int64_t rowsX, int64_t ldx, double *Y, int64_
 int gram_nsplit(int64_t rows, int npairs) {
     // The kernel is bound by the FP64 pipe of each SM, so what matters is an
     // even number of work items per SM: at most one resident wave (4 CTAs per
-    // SM on 152 SMs), at least 32 rows per item.
-    const int64_t slots = 4 * 152;
+    // SM), at least 32 rows per item.  The row split fixes the order of the
+    // partial sums, so results are reproducible on one GPU model.
+    const int64_t slots = 4 * (int64_t)num_sms();
     int64_t s = slots / (3 * (int64_t)npairs);
     const int64_t maxs = (rows + 31) / 32;
     if (s > maxs) s = maxs;

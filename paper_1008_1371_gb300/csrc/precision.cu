@@ -387,7 +387,7 @@ k_update_x(double *__restrict__ X, int64_t rowsX, int64_t ldx, double *__restric
                     float dd[8];
 #pragma unroll
                     for (int a = 0; a < 8; ++a) dd[a] = v[a][t];
-                    d.M[row + (int64_t)jj * d.ld] = combine8(dd, Erow[slot][i] + Fcol[slot][j]);
+                    d.M[row + (int64_t)jj * d.ld] = combine8_small(dd, Erow[slot][i] + Fcol[slot][j]);
                 }
             }
         }

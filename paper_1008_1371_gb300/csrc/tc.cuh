@@ -231,10 +231,32 @@ __device__ __forceinline__ uint32_t slice_pair(long long Wlo, long long Whi, int
 // 2^(7(5-d)) (units 2^-33), L = sum_{d>=6} I_d 2^(7(9-d)) (units 2^-61),
 // T = H 2^28 + L exactly (128 bits), value = T 2^(escale-61) rounded once to
 // nearest even.  No FP64 instruction on the normal-range path.
+__device__ __forceinline__ double combine_ints(const long long (&I)[8], int escale);
+
 __device__ __forceinline__ double combine8(const float (&d)[8], int escale) {
     long long I[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) I[k] = (long long)__float2int_rn(d[k] * __int_as_float((127 + 12 + 7 * k) << 23));
+    return combine_ints(I, escale);
+}
+
+// The same rounding for accumulators whose integers are at most 2^22 in
+// magnitude (at most 128 terms per accumulation: |I_d| <= (d - 1) 128 64^2 <=
+// 2^22, the update's case).  The integer is read from the bits of an exact
+// FP32 add: with M = 1.5 2^23 in the accumulator's unit, d + M lies in
+// [2^23, 2^24] units, where consecutive integers are consecutive bit patterns,
+// so bits(d + M) - bits(M) = I with no conversion instruction.
+__device__ __forceinline__ double combine8_small(const float (&d)[8], int escale) {
+    long long I[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int mb = ((127 + 11 - 7 * k) << 23) | 0x400000;  // 1.5 2^(11 - 7k) = 1.5 2^23 units of 2^-(12+7k)
+        I[k] = (long long)(__float_as_int(d[k] + __int_as_float(mb)) - mb);
+    }
+    return combine_ints(I, escale);
+}
+
+__device__ __forceinline__ double combine_ints(const long long (&I)[8], int escale) {
     const long long H = (I[0] << 21) + (I[1] << 14) + (I[2] << 7) + I[3];
     const long long L = (I[4] << 21) + (I[5] << 14) + (I[6] << 7) + I[7];
     // T = H 2^28 + L as hi:lo (two's complement, 128 bits)
