@@ -36,7 +36,11 @@ def test_tstop_small(exp):
     assert len(recs) == 8
     for r in recs:
         if r["tstop"] == "T_eps":
-            assert _ok(r) and r["stop"] == 2, r  # HSVD_STOP_TANGENT
+            # either rule may end it (HSVD_STOP_TANGENT 2, HSVD_STOP_ORTHO 1); at the
+            # paper's eps the tangent rule comes first
+            assert _ok(r) and r["stop"] in (1, 2), r
+            if r["tol"] == "2^-52":
+                assert r["stop"] == 2, r
         elif r["form"] == "bf16x8" and r["tol"] == "2^-52":
             assert r["status"] in (0, 1), r  # the plain stop may lie below the products' rounding
         else:
