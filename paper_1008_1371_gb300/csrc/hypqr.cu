@@ -96,14 +96,16 @@ __device__ __forceinline__ HqMax hq_shfl(const HqMax &a, int o) {
     return b;
 }
 
-// the maximum entries (i, j >= k) seen by this thread into the CTA's slot
+// the maximum entries (i, j >= k) seen by the CTA's threads into its slot
+// (NT threads in a 1-D or 2-D block, whole warps)
 template <int NT>
 __device__ void hq_block_max(HqMax a, HqMax *out) {
     __shared__ HqMax red[NT / 32];
+    const int lt = (int)(threadIdx.x + threadIdx.y * blockDim.x);
     for (int o = 16; o > 0; o >>= 1) hq_merge(a, hq_shfl(a, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+    if ((lt & 31) == 0) red[lt >> 5] = a;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (lt == 0) {
         HqMax t = red[0];
         for (int w = 1; w < NT / 32; ++w) hq_merge(t, red[w]);
         *out = t;
