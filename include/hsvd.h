@@ -229,6 +229,22 @@ const char *hsvd_status_string(int status);
 int hsvd_modulus_pairs(int r, int nsteps, int *pairs);
 
 /*
+ * The ring that the full pass of the inner solve follows (Sec. 2 modulus
+ * order on the 2b columns of a pivot block, Sec. 5 first visit): from one
+ * step to the next each pair keeps one row and takes the row leaving the
+ * previous pair, so the b pairs form a ring of slots.  Writes 2b steps x b
+ * slots x 4 ints (8 b^2 ints), entry [s][k] =
+ * {lo, hi, buf_lo | buf_hi << 8, lo_arrived}: the pair (lo < hi) of slot k at
+ * step s (as a set, step s's pairs are those of hsvd_modulus_pairs(2b, ...)
+ * step s), the row buffers of lo and hi in the pool of the slot's owning CTA
+ * (slots split evenly over 4 CTAs at b = 16, 8 otherwise; 2P + 1 buffers for
+ * P slots), and 1 if row lo (else row hi) came from slot k - 1 (always 0 at
+ * step 0).  Host memory, host computation, no GPU needed.  b in {16, 32, 64};
+ * HSVD_ERR_ARG otherwise or for a NULL tab.
+ */
+int hsvd_ring_table(int b, int *tab);
+
+/*
  * Kernel-level entry points of the blocked method, exposed so each kernel can
  * be checked on its own.  All pointers are device pointers; the call is
  * stream-ordered (no synchronisation); the caller owns all memory.  The pair

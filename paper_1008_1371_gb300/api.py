@@ -111,6 +111,8 @@ def lib():
             L.hsvd_solve_ex.restype = _int
             L.hsvd_modulus_pairs.argtypes = [_int, _int, _p]
             L.hsvd_modulus_pairs.restype = _int
+            L.hsvd_ring_table.argtypes = [_int, _p]
+            L.hsvd_ring_table.restype = _int
             L.hsvd_diag_wait_timeout.argtypes = [_p]
             L.hsvd_diag_wait_timeout.restype = _int
             L.hsvd_sym_factor.argtypes = [_p, _i64, _i64, _p, _i64, _p, _p, _p]
@@ -348,6 +350,18 @@ def hsvd_modulus_pairs(r, nsteps=None):
     nsteps = r if nsteps is None else nsteps
     out = np.zeros((nsteps, r // 2, 2), dtype=np.int32)
     st = lib().hsvd_modulus_pairs(int(r), int(nsteps), out.ctypes.data_as(ctypes.c_void_p))
+    if st != HSVD_OK:
+        raise HsvdError(st)
+    return out
+
+
+def hsvd_ring_table(b):
+    """The full pass's ring of slots: int32 array (2b, b, 4) of
+    (lo, hi, buf_lo | buf_hi << 8, lo_arrived) per step and slot."""
+    import numpy as np
+
+    out = np.zeros((2 * b, b, 4), dtype=np.int32)
+    st = lib().hsvd_ring_table(int(b), out.ctypes.data_as(ctypes.c_void_p))
     if st != HSVD_OK:
         raise HsvdError(st)
     return out

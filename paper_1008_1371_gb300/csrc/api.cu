@@ -223,7 +223,7 @@ int solve_blocked_core(const double *G, int64_t m, int64_t n, int64_t ldg, const
     // [7] visits kept by the skip mask of a masked sweep
     int *cnt = ws.get<int>(8);
     int *d_tab_outer = ws.get<int>((size_t)nb * npairs * 2);
-    int *d_tab_full = ws.get<int>((size_t)nn * b * 2);
+    int *d_tab_full = ws.get<int>((size_t)nn * b * 2 + ring_table_ints(b));
     int *d_tab_cross = ws.get<int>((size_t)b * b * 2);
     if (!Gw || !Gt || !Ww || !Wt || !perm || !perm_t || !newpos || !sgn || !sgn_t || !d || !part || !Wp ||
         !rotated || !cnt || !d_tab_outer || !d_tab_full || !d_tab_cross)
@@ -245,8 +245,9 @@ int solve_blocked_core(const double *G, int64_t m, int64_t n, int64_t ldg, const
     fill_modulus(nb, nb, outer.data());
     for (auto &v : outer) v *= b;
     {
-        std::vector<int> full((size_t)nn * b * 2), cross((size_t)b * b * 2);
+        std::vector<int> full((size_t)nn * b * 2 + ring_table_ints(b)), cross((size_t)b * b * 2);
         fill_modulus(nn, nn, full.data());
+        if (!fill_ring(b, full.data() + (size_t)nn * b * 2)) return HSVD_ERR_ARG;
         fill_cross(b, cross.data());
         CKR(cudaMemcpyAsync(d_tab_outer, outer.data(), outer.size() * sizeof(int), cudaMemcpyHostToDevice, st));
         CKR(cudaMemcpyAsync(d_tab_full, full.data(), full.size() * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -829,6 +830,11 @@ int hsvd_modulus_pairs(int r, int nsteps, int *pairs) {
     return HSVD_OK;
 }
 
+int hsvd_ring_table(int b, int *tab) {
+    if ((b != 16 && b != 32 && b != 64) || !tab) return HSVD_ERR_ARG;
+    return fill_ring(b, tab) ? HSVD_OK : HSVD_ERR_ARG;
+}
+
 int hsvd_solve_ex(const double *G, int64_t m, int64_t n, int64_t ldg, const int8_t *J, double *sigma, double *U,
                   int64_t ldu, double *V, int64_t ldv, const hsvd_opts *opts_in, hsvd_info *info, void *stream) {
     Range range("hsvd_solve_ex");
@@ -1140,8 +1146,9 @@ int hsvd_pivot_solve(int b, int npairs, double *A, const int8_t *sgn, double tol
     if (!all_device({A, sgn, W, rotated, status_dev})) return HSVD_ERR_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int nn = 2 * b;
-    std::vector<int> full((size_t)nn * b * 2), cross((size_t)b * b * 2);
+    std::vector<int> full((size_t)nn * b * 2 + ring_table_ints(b)), cross((size_t)b * b * 2);
     fill_modulus(nn, nn, full.data());
+    if (!fill_ring(b, full.data() + (size_t)nn * b * 2)) return HSVD_ERR_ARG;
     fill_cross(b, cross.data());
     int *dt = nullptr;
     if (cudaMallocAsync((void **)&dt, sizeof(int) * (full.size() + cross.size()), st) != cudaSuccess)

@@ -173,6 +173,12 @@ cudaError_t launch_pointwise(const double *G, int64_t ldg, int m, int n, const i
 int gram_nsplit(int64_t rows, int npairs);
 cudaError_t launch_gram(const double *G, int64_t rows, int64_t ldg, int b, int npairs,
                         const int *col0, int nsplit, double *part, cudaStream_t st);
+// solve_cluster.cu: the inner pivot-block solve.  tab_full holds the modulus
+// pairs of the 2b columns (2b steps of b pairs, 2 ints each) followed by the
+// ring table of the full pass (ring_table_ints(b) ints, fill_ring).
+size_t ring_table_ints(int b);
+// false if the ring of the full pass cannot be formed (not for b = 16, 32, 64)
+bool fill_ring(int b, int *tab);
 cudaError_t launch_solve(int b, int npairs, const double *part, int nsplit, double *A,
                          const int8_t *sgn_cols, const int *col0, const int8_t *sgn_direct,
                          double tol, int mode, int max_passes, const int *tab_full,

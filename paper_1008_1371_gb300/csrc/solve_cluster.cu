@@ -26,6 +26,8 @@
 // element, so the result is bit-identical to it.
 #include <cooperative_groups.h>
 
+#include <vector>
+
 #include "hsvd_internal.cuh"
 
 namespace cg = cooperative_groups;
@@ -673,6 +675,404 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
     }
 }
 
+// One ring table entry of the full pass: the pair (lo, hi) of a slot at a
+// step, the row buffers holding rows lo and hi in the owning CTA's pool, and
+// whether row lo (else row hi) arrived from the previous slot.
+__device__ __forceinline__ int ring_buf_lo(int4 e) { return e.z & 0xff; }
+__device__ __forceinline__ int ring_buf_hi(int4 e) { return (e.z >> 8) & 0xff; }
+
+// The full pass (every pair of the 2b columns once, in the modulus order of
+// Sec. 2: the first visit of a block pair in a sweep of the block-oriented
+// method, Sec. 5) without transposes.  Step s pairs a with c - a (mod 2b);
+// from one step to the next every pair keeps one of its two rows and takes
+// the row that leaves the previous pair, so the b pairs form a ring of slots
+// in which one row per slot moves on by one slot per step.  The host table
+// (fill_ring) gives, per step and slot, the pair, which of its rows arrived
+// and the pool buffers of both.  CTA r of the cluster owns slots
+// [r P, r P + P) and holds both rows of each, in a pool of 2P + 1 row buffers
+// (one free to receive); per step the row leaving its last slot is written
+// into the next CTA's free buffer, the only exchange of rows.  Both halves of
+// R^T A R are then local, as in the cross pass.  The entry a_lo,hi of a pair
+// is read from row lo (as the transposing kernel reads it), so the (t, c) of
+// a pair is formed by the CTA holding row lo at the end of the previous step:
+// the slot's own CTA, or the previous one when row lo is the row crossing
+// over.  The element operations and their order (column mix first on even
+// steps, row mix first on odd steps, Eq. 2.6 on the diagonal, zeros at the
+// pair) are those of k_solve_cluster in one-pass mode: the same bits.
+template <int NN, int C, bool LA>
+__global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(LA ? kCrossThreads : kClThreads, 3)
+k_solve_ring(const double *__restrict__ part, int nsplit, int full_part, double *__restrict__ A_io,
+             const int8_t *__restrict__ sgn_cols, const int *__restrict__ col0,
+             const int8_t *__restrict__ sgn_direct, double tol, const int4 *__restrict__ ring,
+             double *__restrict__ Wout, int *__restrict__ rotated, unsigned long long *__restrict__ rot_count,
+             int *__restrict__ status, int *__restrict__ dexp, const int *__restrict__ visit,
+             float *__restrict__ trace, double tstop, int *__restrict__ tbig) {
+    constexpr int h = NN / 2, P = h / C, RW = NN / C, B = NN / 2, NBUF = 2 * P + 1;
+    constexpr int kT = LA ? kCrossThreads : kClThreads;
+    static_assert(P * C == h && RW * C == NN, "the slots and rows split evenly over the cluster");
+    static_assert(!LA || P + 1 <= 32, "the look-ahead warp has one lane per pair it forms");
+    static_assert(NBUF <= 255, "buffer indices fit the table's byte fields");
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int pair = blockIdx.x / C;
+    const int tid = threadIdx.x;
+    const int k0 = rank * P;   // first slot owned
+    const int w0 = rank * RW;  // first row of W owned
+    if (col0 && col0[2 * pair] < 0) {  // a visit the skip mask removed: the whole cluster leaves
+        if (rank == 0 && tid == 0) rotated[pair] = 0;
+        return;
+    }
+
+    extern __shared__ __align__(16) double sm[];
+    double *pool = sm;               // [NBUF][NN] rows of A: both rows of every owned slot, one free
+    double *Wl = pool + NBUF * NN;   // [RW][NN] rows w0 .. w0 + RW - 1 of W_P
+    __shared__ double D[NN];
+    __shared__ int sg[NN];
+    __shared__ double T[2][h], Cc[2][h], Apq[2][h];
+    __shared__ int Fl[2][h];         // bit 0: rotate, bit 1: rank deficient
+    __shared__ int4 tb[3][h];        // ring table rows of steps s, s + 1, s + 2 (at step % 3)
+    __shared__ double tr_max[C], tr_sum[C], tr_red[2][kT / 32];
+
+    auto entry = [&](int x, int y) -> double {
+        if (!part) return A_io[(size_t)pair * NN * NN + x + y * NN];
+        if (!full_part) return assemble_entry<NN>(part, nsplit, pair, x + y * NN);
+        const int lo = x < y ? x : y, hi = x < y ? y : x;
+        const double *pp = part + (size_t)pair * nsplit * NN * NN + lo + (size_t)hi * NN;
+        double v = 0.0;
+        for (int s = 0; s < nsplit; ++s) v += pp[(size_t)s * NN * NN];
+        return v;
+    };
+    for (int x = tid; x < NN; x += kT) {
+        if (sgn_direct) sg[x] = sgn_direct[(size_t)pair * NN + x];
+        else sg[x] = sgn_cols[col0[2 * pair + (x >= B)] + (x % B)];
+        D[x] = entry(x, x);
+        if (dexp && rank == 0) dexp[(size_t)pair * NN + x] = D[x] > 0.0 ? (ilogb(D[x]) >> 1) : 0;
+    }
+    for (int e = tid; e < 2 * h; e += kT) tb[e / h][e % h] = ring[e];
+    __syncthreads();
+    // rows of the owned slots at step 0, W = I
+    for (int e = tid; e < 2 * P * NN; e += kT) {
+        const int r = e / NN, y = e % NN;
+        const int4 t = tb[0][k0 + (r >> 1)];
+        const int x = (r & 1) ? t.y : t.x, bf = (r & 1) ? ring_buf_hi(t) : ring_buf_lo(t);
+        pool[bf * NN + y] = entry(x, y);
+    }
+    for (int e = tid; e < RW * NN; e += kT) {
+        const int x = e / NN, y = e % NN;
+        Wl[x * NN + y] = (w0 + x == y) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    // visit record for the learned form: the I x J block of A_P scaled by the
+    // diagonal over the rows this CTA holds, reduced into rank 0
+    float rec_meanI = 0.f, rec_meanJ = 0.f, rec_hyp = 0.f;
+    double rec_max = 0.0, rec_sum = 0.0;
+    if (trace) {
+        double lmax = 0.0, lsum = 0.0;
+        for (int e = tid; e < 2 * P * B; e += kT) {
+            const int r = e / B, y = B + e % B;
+            const int4 t = tb[0][k0 + (r >> 1)];
+            const int x = (r & 1) ? t.y : t.x, bf = (r & 1) ? ring_buf_hi(t) : ring_buf_lo(t);
+            if (x >= B) continue;
+            const double dd = D[x] * D[y];
+            const double sc = dd > 0.0 ? fabs(pool[bf * NN + y]) / sqrt(dd) : 0.0;
+            lmax = fmax(lmax, sc);
+            lsum = fma(sc, sc, lsum);
+        }
+        lmax = warp_max(lmax);
+        lsum = warp_sum(lsum);
+        if ((tid & 31) == 0) {
+            tr_red[0][tid >> 5] = lmax;
+            tr_red[1][tid >> 5] = lsum;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            for (int w = 0; w < kT / 32; ++w) {
+                rec_max = fmax(rec_max, tr_red[0][w]);
+                rec_sum += tr_red[1][w];
+            }
+            if (rank == 0) {
+                double mi = 0.0, mj = 0.0;
+                int pi = 0, pj = 0;
+                for (int x = 0; x < B; ++x) {
+                    mi += D[x];
+                    mj += D[B + x];
+                    pi += sg[x] > 0;
+                    pj += sg[B + x] > 0;
+                }
+                rec_meanI = (float)(mi / B);
+                rec_meanJ = (float)(mj / B);
+                rec_hyp = (float)(pi * (B - pj) + (B - pi) * pj) / (float)(B * B);
+            }
+        }
+    }
+    cluster.sync();  // every CTA initialised before any remote write
+    if (trace && tid == 0) {
+        *cluster.map_shared_rank(&tr_max[rank], 0) = rec_max;
+        *cluster.map_shared_rank(&tr_sum[rank], 0) = rec_sum;
+    }
+    // (t, c) of a pair into every CTA (buffer s & 1)
+    auto put_params = [&](int s, int k, double t, double c, double apq, int fl) {
+        const int b = s & 1;
+        for (int r = 0; r < C; ++r) {
+            *cluster.map_shared_rank(&T[b][k], r) = t;
+            *cluster.map_shared_rank(&Cc[b][k], r) = c;
+            *cluster.map_shared_rank(&Apq[b][k], r) = apq;
+            *cluster.map_shared_rank(&Fl[b][k], r) = fl;
+        }
+    };
+    // Lane l <= P forms the step-s pair of slot k0 + l (l = P: the next CTA's
+    // first slot) when this CTA holds its row lo at the end of step s - 1:
+    // row lo stays in slot k0 + l, or arrives from slot k0 + l - 1 (local for
+    // l >= 1; for l = P, this CTA's last slot).
+    auto forms = [&](int s, int l) -> bool {
+        const int4 e = tb[s % 3][(k0 + l) % h];
+        const bool lo_arr = e.w & 1;
+        return l < P ? !(lo_arr && l == 0) : lo_arr;
+    };
+    // step 0: every CTA forms the pairs of its own slots
+    if (tid < P) {
+        const int k = k0 + tid;
+        const int4 e = tb[0][k];
+        const double apq = pool[ring_buf_lo(e) * NN + e.y];
+        const int hyp = (sg[e.x] == sg[e.y]) ? -1 : 1;
+        double t, c;
+        const int fl = pair_decision(D[e.x], D[e.y], apq, hyp, tol, t, c);
+        put_params(0, k, t, c, apq, fl);
+    }
+    cluster.sync();
+
+    // Warp 0 works one step ahead (LA): lane l reads, at the top of step s,
+    // the four entries of the rows of pair i (the slot holding row lo of the
+    // step-(s+1) pair) in the columns of pair j (the slot holding its row hi)
+    // and the two diagonal values, forms their step-s values with the
+    // operations of the bulk update and the (t, c) of the step-(s+1) pair,
+    // while warps 1.. update the rows (named barrier 1).
+    constexpr int kMixThreads = LA ? kT - 32 : kT;
+    const int warp = tid >> 5, lane = tid & 31;
+    int total = 0, bad = 0, s_end = NN - 1;
+    int big = 0;  // a rotation of pair tid had |t| > tstop (Eq. 4.2 code (11)_2)
+    for (int s = 0; s < NN; ++s) {
+        const int b = s & 1;
+        const int4 *cur = tb[s % 3];
+        double nx_t = 0.0, nx_c = 1.0, nx_apq = 0.0;
+        int nx_fl = 0;
+        double e_pp = 0.0, e_pq = 0.0, e_qp = 0.0, e_qq = 0.0, d_lo = 0.0, d_hi = 0.0;
+        int si = 0, sj = 0;
+        bool lo_p = false, hi_p = false, trig_i = false, trig_j = false, trig_n = false;
+        const bool ahead = LA && warp == 0 && lane <= P && s + 1 < NN && forms(s + 1, lane);
+        if (ahead) {
+            const int k = (k0 + lane) % h;
+            const int4 ne = tb[(s + 1) % 3][k];
+            const bool lo_arr = ne.w & 1;
+            si = lo_arr ? (k + h - 1) % h : k;
+            sj = lo_arr ? k : (k + h - 1) % h;
+            const int4 fi = cur[si], fj = cur[sj];
+            const double *rp = pool + ring_buf_lo(fi) * NN, *rq = pool + ring_buf_hi(fi) * NN;
+            e_pp = rp[fj.x];
+            e_pq = rp[fj.y];
+            e_qp = rq[fj.x];
+            e_qq = rq[fj.y];
+            d_lo = D[ne.x];
+            d_hi = D[ne.y];
+            lo_p = ne.x == fi.x;  // row lo is pair i's first row
+            hi_p = ne.y == fj.x;  // column hi is pair j's first column
+            trig_i = sg[fi.x] == sg[fi.y];
+            trig_j = sg[fj.x] == sg[fj.y];
+            trig_n = sg[ne.x] == sg[ne.y];
+        }
+        // every CTA sees every pair's flags: the same decision everywhere
+        const int f = tid < h ? Fl[b][tid] : 0;
+        if ((f & 1) && fabs(T[b][tid]) > tstop) big = 1;
+        const int nrot = __syncthreads_count(f & 1);
+        bad = __syncthreads_or(f & 2);
+        if (bad) {
+            s_end = s;
+            break;
+        }
+        total += nrot;
+        if (LA && warp == 0) {
+            if (ahead) {
+                const int ri = Fl[b][si] & 1, rj = Fl[b][sj] & 1;
+                const double ti = T[b][si], ci = Cc[b][si], hti = trig_i ? -ti : ti;
+                const double tj = T[b][sj], cj = Cc[b][sj], htj = trig_j ? -tj : tj;
+                double v;
+                if ((s & 1) == 0) {  // column mix (pair j) of rows p_i, q_i, then row mix (pair i)
+                    double up = hi_p ? e_pp : e_pq, uq = hi_p ? e_qp : e_qq;
+                    if (rj) {
+                        up = hi_p ? fma(htj, e_pq, e_pp) * cj : fma(tj, e_pp, e_pq) * cj;
+                        uq = hi_p ? fma(htj, e_qq, e_qp) * cj : fma(tj, e_qp, e_qq) * cj;
+                    }
+                    v = lo_p ? up : uq;
+                    if (ri) v = lo_p ? fma(hti, uq, up) * ci : fma(ti, up, uq) * ci;
+                } else {  // row mix (pair i) in columns p_j, q_j, then column mix (pair j)
+                    double wp = lo_p ? e_pp : e_qp, wq = lo_p ? e_pq : e_qq;
+                    if (ri) {
+                        wp = lo_p ? fma(hti, e_qp, e_pp) * ci : fma(ti, e_pp, e_qp) * ci;
+                        wq = lo_p ? fma(hti, e_qq, e_pq) * ci : fma(ti, e_pq, e_qq) * ci;
+                    }
+                    v = hi_p ? wp : wq;
+                    if (rj) v = hi_p ? fma(htj, wq, wp) * cj : fma(tj, wp, wq) * cj;
+                }
+                // Eq. 2.6 on the two diagonal entries
+                const double app = ri ? fma(lo_p ? hti : ti, Apq[b][si], d_lo) : d_lo;
+                const double aqq = rj ? fma(hi_p ? htj : tj, Apq[b][sj], d_hi) : d_hi;
+                nx_fl = pair_decision_eager(app, aqq, v, trig_n ? -1 : 1, tol, nx_t, nx_c);
+                nx_apq = v;
+            }
+        } else {
+            const int mt = LA ? tid - 32 : tid;
+            // the column mix on every held row of A (and of W): a thread keeps
+            // one pair (its rotation in registers) and walks rows
+            auto col_mix = [&](bool with_w) {
+                static_assert(kMixThreads % h == 0, "whole rows per pass");
+                const int j = mt % h;
+                if (!(Fl[b][j] & 1)) return;
+                const int p = cur[j].x, q = cur[j].y;
+                const double t = T[b][j], c = Cc[b][j], ht = (sg[p] == sg[q]) ? -t : t;
+                const int nrows = 2 * P + (with_w ? RW : 0);
+                for (int r = mt / h; r < nrows; r += kMixThreads / h) {
+                    double *row;
+                    if (r < 2 * P) {
+                        const int4 e = cur[k0 + (r >> 1)];
+                        row = pool + ((r & 1) ? ring_buf_hi(e) : ring_buf_lo(e)) * NN;
+                    } else {
+                        row = Wl + (r - 2 * P) * NN;
+                    }
+                    const double a = row[p], bb = row[q];
+                    row[p] = fma(ht, bb, a) * c;
+                    row[q] = fma(t, a, bb) * c;
+                }
+            };
+            // the row mix of every owned slot's pair, every column; with W,
+            // also W's column mix
+            auto row_mix = [&](bool with_w) {
+                static_assert(kMixThreads % P == 0, "threads split evenly over the owned slots");
+                constexpr int TP = kMixThreads / P;  // threads per owned slot
+                const int kl = mt / TP, k = k0 + kl;
+                if (Fl[b][k] & 1) {
+                    const int4 e = cur[k];
+                    const double t = T[b][k], c = Cc[b][k], ht = (sg[e.x] == sg[e.y]) ? -t : t;
+                    double *rp = pool + ring_buf_lo(e) * NN, *rq = pool + ring_buf_hi(e) * NN;
+                    for (int y = mt % TP; y < NN; y += TP) {
+                        const double a = rp[y], bb = rq[y];
+                        rp[y] = fma(ht, bb, a) * c;
+                        rq[y] = fma(t, a, bb) * c;
+                    }
+                }
+                if (!with_w) return;
+                const int j = mt % h;
+                if (!(Fl[b][j] & 1)) return;
+                const int pw = cur[j].x, qw = cur[j].y;
+                const double t = T[b][j], c = Cc[b][j], ht = (sg[pw] == sg[qw]) ? -t : t;
+                for (int x = mt / h; x < RW; x += kMixThreads / h) {
+                    double *row = Wl + x * NN;
+                    const double a = row[pw], bb = row[qw];
+                    row[pw] = fma(ht, bb, a) * c;
+                    row[qw] = fma(t, a, bb) * c;
+                }
+            };
+            if ((s & 1) == 0) {
+                col_mix(true);
+                mix_sync<LA>(kMixThreads);
+                row_mix(false);
+            } else {
+                row_mix(true);
+                mix_sync<LA>(kMixThreads);
+                col_mix(false);
+            }
+            mix_sync<LA>(kMixThreads);
+            // Eq. 2.6 on the replicated diagonal, and the owned pairs' own entries
+            if (mt < h && (Fl[b][mt] & 1)) {
+                const int4 e = cur[mt];
+                const int p = e.x, q = e.y;
+                const double t = T[b][mt], ht = (sg[p] == sg[q]) ? -t : t, apq = Apq[b][mt];
+                const double dp = fma(ht, apq, D[p]), dq = fma(t, apq, D[q]);
+                D[p] = dp;
+                D[q] = dq;
+                if (mt >= k0 && mt < k0 + P) {
+                    double *rp = pool + ring_buf_lo(e) * NN, *rq = pool + ring_buf_hi(e) * NN;
+                    rp[p] = dp;
+                    rp[q] = 0.0;
+                    rq[q] = dq;
+                    rq[p] = 0.0;
+                }
+            }
+        }
+        __syncthreads();
+        if (s + 1 < NN) {
+            const int4 *nxt = tb[(s + 1) % 3];
+            // the row leaving the last owned slot: the row arriving in slot
+            // k0 + P at step s + 1, into its buffer in the next CTA
+            {
+                const int4 en = nxt[(k0 + P) % h];
+                const bool lo_arr = en.w & 1;
+                const int mv = lo_arr ? en.x : en.y, dbf = lo_arr ? ring_buf_lo(en) : ring_buf_hi(en);
+                const int4 el = cur[k0 + P - 1];
+                const int sbf = el.x == mv ? ring_buf_lo(el) : ring_buf_hi(el);
+                double *rdst = cluster.map_shared_rank(pool, (rank + 1) % C) + dbf * NN;
+                const double *src = pool + sbf * NN;
+                for (int y = tid; y < NN; y += kT) rdst[y] = src[y];
+            }
+            if (!LA && tid <= P && forms(s + 1, tid)) {
+                // row lo of the step-(s+1) pair, where it is at step s
+                const int k = (k0 + tid) % h;
+                const int4 e = nxt[k];
+                const int4 fl = cur[(e.w & 1) ? (k + h - 1) % h : k];
+                const int bf = fl.x == e.x ? ring_buf_lo(fl) : ring_buf_hi(fl);
+                const double apq = pool[bf * NN + e.y];
+                const int hyp = (sg[e.x] == sg[e.y]) ? -1 : 1;
+                double t, c;
+                const int fd = pair_decision(D[e.x], D[e.y], apq, hyp, tol, t, c);
+                put_params(s + 1, k, t, c, apq, fd);
+            }
+            if (ahead) put_params(s + 1, (k0 + lane) % h, nx_t, nx_c, nx_apq, nx_fl);
+            // the table row of step s + 2 into the slot of step s - 1
+            if (s + 2 < NN)
+                for (int e = tid; e < h; e += kT) tb[(s + 2) % 3][e] = ring[(size_t)(s + 2) * h + e];
+        }
+        cluster.sync();
+    }
+    // outputs: own rows of W (column-major W_P), and A_P when asked for
+    double *wo = Wout + (size_t)pair * NN * NN;
+    for (int e = tid; e < RW * NN; e += kT) {
+        const int x = e / NN, y = e % NN;
+        wo[(w0 + x) + (size_t)y * NN] = Wl[x * NN + y];
+    }
+    if (!part) {
+        // the rows of the owned slots where the pass ended
+        double *ao = A_io + (size_t)pair * NN * NN;
+        const int4 *at = tb[s_end % 3];
+        for (int e = tid; e < 2 * P * NN; e += kT) {
+            const int r = e / NN, y = e % NN;
+            const int4 t = at[k0 + (r >> 1)];
+            const int x = (r & 1) ? t.y : t.x, bf = (r & 1) ? ring_buf_hi(t) : ring_buf_lo(t);
+            ao[x + (size_t)y * NN] = pool[bf * NN + y];
+        }
+    }
+    cluster.sync();
+    const int any_big = tbig ? __syncthreads_or(big) : 0;
+    if (rank == 0 && tid == 0) {
+        rotated[pair] = total;
+        if (rot_count && total) atomicAdd(rot_count, (unsigned long long)total);
+        if (bad && status) atomicExch(status, HSVD_ERR_RANK);
+        if (any_big) atomicOr(tbig, 1);
+        if (trace) {
+            double mx = 0.0, sm2 = 0.0;
+            for (int r = 0; r < C; ++r) {
+                mx = fmax(mx, tr_max[r]);
+                sm2 += tr_sum[r];
+            }
+            float *rec = trace + (size_t)visit[pair] * HSVD_TRACE_FIELDS;
+            rec[0] = (float)mx;
+            rec[1] = (float)sqrt(sm2);
+            rec[2] = (float)total;
+            rec[3] = rec_meanI;
+            rec[4] = rec_meanJ;
+            rec[5] = rec_hyp;
+        }
+    }
+}
+
 template <int NN>
 cudaError_t solve_cluster_impl(int npairs, const double *part, int nsplit, int full_part, double *A,
                                const int8_t *sgn_cols, const int *col0, const int8_t *sgn_direct, double tol,
@@ -694,6 +1094,20 @@ cudaError_t solve_cluster_impl(int npairs, const double *part, int nsplit, int f
                                                                      status, dexp, visit, trace, tstop, tbig);
         return cudaGetLastError();
     }
+    if (mode == 2) {
+        constexpr int CX = CrossClusterOf<NN>::C, P = NN / 2 / CX, RX = NN / CX;
+        const size_t smem_r = (size_t)((2 * P + 1) * NN + RX * NN) * sizeof(double);
+        constexpr bool LA = NN >= 128;
+        constexpr int threads = LA ? kCrossThreads : kClThreads;
+        const int4 *ring = reinterpret_cast<const int4 *>(tab_full + (size_t)NN * (NN / 2) * 2);
+        cudaError_t e = cudaFuncSetAttribute(k_solve_ring<NN, CX, LA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem_r);
+        if (e != cudaSuccess) return e;
+        k_solve_ring<NN, CX, LA><<<npairs * CX, threads, smem_r, st>>>(part, nsplit, full_part, A, sgn_cols, col0,
+                                                                    sgn_direct, tol, ring, Wp, rotated, rot_count,
+                                                                    status, dexp, visit, trace, tstop, tbig);
+        return cudaGetLastError();
+    }
     const size_t smem = (size_t)(2 * R * (NN + 1) + R * NN) * sizeof(double);
     cudaError_t e = cudaFuncSetAttribute(k_solve_cluster<NN, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
@@ -706,6 +1120,77 @@ cudaError_t solve_cluster_impl(int npairs, const double *part, int nsplit, int f
 }
 
 }  // namespace
+
+// Cluster size of the ring kernel for block width b (CrossClusterOf).
+static int ring_cluster(int b) { return b == 16 ? 4 : 8; }
+
+size_t ring_table_ints(int b) { return (size_t)(2 * b) * b * 4; }
+
+// The ring of the full pass (k_solve_ring): step 0's slots are the modulus
+// pairs of step 0 in their order; at every later step the pair holding one
+// row of slot k and one row of slot k - 1 (cyclically) takes slot k, the row
+// from slot k - 1 being the one that moved.  Rows keep their pool buffer
+// while they move inside a CTA; a row crossing into the next CTA takes that
+// CTA's free buffer, and the buffer it leaves becomes the sender's free one.
+// Entry [s][k] = {lo, hi, buf_lo | buf_hi << 8, lo arrived}.
+bool fill_ring(int b, int *tab) {
+    if (b != 16 && b != 32 && b != 64) return false;
+    const int nn = 2 * b, h = b, C = ring_cluster(b), P = h / C;
+    std::vector<int> slot_lo(h), slot_hi(h), where(nn), buf(nn), freeb(C, 2 * P);
+    std::vector<int> nlo(h, -1), nhi(h), narr(h);
+    for (int k = 0; k < h; ++k) {
+        int lo, hi;
+        modulus_pair(nn, 0, k, lo, hi);
+        slot_lo[k] = lo;
+        slot_hi[k] = hi;
+        buf[lo] = 2 * (k % P);
+        buf[hi] = 2 * (k % P) + 1;
+        int *e = tab + 4 * k;
+        e[0] = lo;
+        e[1] = hi;
+        e[2] = buf[lo] | (buf[hi] << 8);
+        e[3] = 0;
+    }
+    for (int s = 1; s < nn; ++s) {
+        for (int k = 0; k < h; ++k) {
+            where[slot_lo[k]] = k;
+            where[slot_hi[k]] = k;
+            nlo[k] = -1;
+        }
+        for (int j = 0; j < h; ++j) {
+            int lo, hi;
+            modulus_pair(nn, s, j, lo, hi);
+            const int kl = where[lo], kh = where[hi];
+            int k, arr;
+            if ((kl + h - 1) % h == kh) { k = kl; arr = 0; }       // row hi came from slot k - 1
+            else if ((kh + h - 1) % h == kl) { k = kh; arr = 1; }  // row lo came from slot k - 1
+            else return false;
+            if (nlo[k] >= 0) return false;
+            nlo[k] = lo;
+            nhi[k] = hi;
+            narr[k] = arr;
+        }
+        // rows crossing into CTA r's first slot take its free buffer; the
+        // buffer the crossing row leaves in CTA r - 1 becomes that CTA's free one
+        std::vector<int> nfree(C);
+        for (int r = 0; r < C; ++r) {
+            const int k = r * P, mv = narr[k] ? nlo[k] : nhi[k];
+            nfree[(r + C - 1) % C] = buf[mv];
+            buf[mv] = freeb[r];
+        }
+        freeb = nfree;
+        for (int k = 0; k < h; ++k) {
+            slot_lo[k] = nlo[k];
+            slot_hi[k] = nhi[k];
+            int *e = tab + 4 * ((size_t)s * h + k);
+            e[0] = nlo[k];
+            e[1] = nhi[k];
+            e[2] = buf[nlo[k]] | (buf[nhi[k]] << 8);
+            e[3] = narr[k];
+        }
+    }
+    return true;
+}
 
 cudaError_t launch_solve(int b, int npairs, const double *part, int nsplit, double *A, const int8_t *sgn_cols,
                          const int *col0, const int8_t *sgn_direct, double tol, int mode, int max_passes,

@@ -278,7 +278,7 @@ def _gpu_inner(api, As, sg, tol, mode, max_passes=10):
     return Ao.cpu().numpy(), Wg.cpu().numpy(), rot.cpu().numpy()
 
 
-@pytest.mark.parametrize("b,mode", [(16, 0), (16, 1), (16, 2), (32, 0), (32, 1), (64, 1), (64, 2)])
+@pytest.mark.parametrize("b,mode", [(16, 0), (16, 1), (16, 2), (32, 0), (32, 1), (32, 2), (64, 1), (64, 2)])
 def test_kernel_inner_solve_matches_model(api, b, mode):
     """Same A_P: the kernel reproduces the exact CPU model of its arithmetic
     (oracle/inner_model.c: the parallel strategy's pairs, a step's pairs at
@@ -296,6 +296,49 @@ def test_kernel_inner_solve_matches_model(api, b, mode):
         assert s == 0 and nrot == rot[k]
         assert np.array_equal(Wg[k], Wr), np.max(np.abs(Wg[k] - Wr))
         assert np.array_equal(Ao[k], Ar), np.max(np.abs(Ao[k] - Ar))
+
+
+@pytest.mark.parametrize("b", [16, 32, 64])
+def test_ring_full_pass_equals_transposing_pass(api, b):
+    """The full pass on the ring of slots (mode 2, rows moving one slot per
+    step between the CTAs of the cluster) and the transposing full pass
+    (mode 0 stopped after one pass) apply the same rotations with the same
+    element operations: A, W and the rotation counts agree bit for bit."""
+    nn = 2 * b
+    As, sg = _pivot_blocks(b, 300 + b, npairs=5)
+    tol = nn * U64
+    Ar, Wr, rr = _gpu_inner(api, As, sg, tol, 2)
+    At, Wt, rt = _gpu_inner(api, As, sg, tol, 0, max_passes=1)
+    assert np.array_equal(rr, rt)
+    assert np.array_equal(Wr, Wt) and np.array_equal(Ar, At)
+
+
+@pytest.mark.parametrize("b", [16, 64])
+def test_ring_full_pass_rank_deficient_pair(api, b):
+    """A hyperbolic pair with |zeta| <= 1 (two equal columns of opposite sign,
+    every other pair already orthogonal) stops the pass at the first step that
+    holds it with HSVD_ERR_RANK; A_P comes back as it stood (nothing rotated),
+    from wherever the ring had moved its rows, as in the transposing pass."""
+    nn = 2 * b
+    dev = torch.device("cuda:0")
+    rng = np.random.default_rng(b)
+    A = np.diag(rng.uniform(1.0, 2.0, nn))
+    p, q = 3, nn - 7  # a pair of a late step of the modulus order
+    A[q, q] = A[p, p]
+    A[p, q] = A[q, p] = A[p, p]
+    sg = np.ones(nn, dtype=np.int8)
+    sg[q] = -1
+    out = []
+    for mode, mp in ((2, 1), (0, 1)):
+        Ao, Wg, rot, st = api.hsvd_pivot_solve(torch.from_numpy(A[None].copy()).to(dev),
+                                               torch.from_numpy(sg[None].copy()).to(dev), nn * U64, mode=mode,
+                                               max_passes=mp)
+        assert int(st.cpu()[0]) == api.HSVD_ERR_RANK
+        out.append((Ao.cpu().numpy()[0], Wg.cpu().numpy()[0], int(rot.cpu()[0])))
+    (Ar, Wr, rr), (At, Wt, rt) = out
+    assert rr == rt == 0
+    assert np.array_equal(Ar, A) and np.array_equal(At, A)
+    assert np.array_equal(Wr, np.eye(nn)) and np.array_equal(Wt, np.eye(nn))
 
 
 @pytest.mark.parametrize("b,mode", [(16, 0), (16, 1), (16, 2), (32, 0), (32, 1), (32, 2), (64, 0), (64, 1), (64, 2)])
