@@ -32,7 +32,7 @@ using namespace tc;
 constexpr int NNX = 128;             // pivot block order 2b
 constexpr int kThrX = 256;           // eight warps: two per TMEM lane quarter
 constexpr int kThrU = 512;           // update: sixteen warps, four per TMEM lane quarter
-constexpr int kThrG = 512;           // Gram: sixteen warps
+constexpr int kThrG = 544;           // Gram: the products warp and sixteen splitting warps
 constexpr int kGramK = 512;          // rows of G per Gram CTA pair (exactness window)
 constexpr int kGramKT = 32;          // rows per shared-memory tile of the Gram
 constexpr int kUpdKT = 32;           // k per shared-memory tile of the update
@@ -69,6 +69,8 @@ __device__ __forceinline__ void issue_products(uint32_t tmem, uint32_t a_base, u
     }
 }
 
+__device__ __forceinline__ void bar_named(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+
 // this thread's lane and 8 columns [c0, c0+8) of all eight accumulators: the
 // eight loads are issued back to back and waited for once
 __device__ __forceinline__ void read_accs(uint32_t tmem, int lane_base, int c0, float (&v)[8][8]) {
@@ -85,38 +87,44 @@ __device__ __forceinline__ void read_accs(uint32_t tmem, int lane_base, int c0, 
 }
 
 // ---------------------------------------------------------------- Gram
-// A cluster of two CTAs per (pair, split): CTA h forms columns [64 h, 64 h + 64)
-// of the partial A_P over rows [512 split, 512 split + 512) of the panel
-// P = [G_I G_J] (m x 128): A = P^T (128 x K, K-major), B = rows [64 h, 64 h + 64)
-// of the same tile.  Each CTA splits its own 64 columns of every 32-row tile
-// and writes the slices to both CTAs' shared memory, so the tile is split once;
-// tiles are double-buffered, the split of tile t overlapping the products of
-// tile t - 1.  One cluster barrier per tile.
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThrG, 1)
+// Two CTAs per (pair, split): CTA h forms columns [64 h, 64 h + 64) of the
+// partial A_P over rows [512 split, 512 split + 512) of the panel
+// P = [G_I G_J] (m x 128): A = P^T (128 x K, K-major), B = columns
+// [64 h, 64 h + 64) of the same tile.  Each CTA splits the whole 128-column
+// tile itself (the split is cheap next to the products; no shared memory is
+// written across CTAs and no cluster barrier is needed).  Warp-specialised
+// pipeline over 32-row tiles, double-buffered:
+//   - warps 1..16 wait until the products that last read a buffer are done
+//     (mbarrier `empty`), split the tile into it (its values loaded one tile
+//     ahead) and arrive on `full`;
+//   - warp 0, lane 0 waits on `full`, issues the tile's 72 products and
+//     commits them to `empty`.
+// Every wait is bounded; after a failure each role still passes the same
+// barriers and the kernel reports HSVD_ERR_CUDA.
+__global__ void __launch_bounds__(kThrG, 1)
 k_gram_x(const double *__restrict__ G, int64_t rows, int64_t ldg, const int *__restrict__ col0, int ksplit,
          double *__restrict__ part, int *__restrict__ status) {
     extern __shared__ __align__(1024) unsigned char smem[];
     constexpr uint32_t kSliceBytes = NNX * kGramKT * 2;     // one slice of a tile (8 KB)
     constexpr uint32_t kBufBytes = kSlices * kSliceBytes;   // one tile (64 KB)
+    constexpr int kProd = kThrG - 32;                       // splitting threads (warps 1..16)
+    constexpr int kProdWarps = kProd / 32;
     __shared__ int Ecol[NNX];
-    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ __align__(8) uint64_t full[2], empty[2];
     __shared__ uint32_t tbase;
     __shared__ int s_fail;
-    const uint32_t half = cluster_rank(), peer = half ^ 1u;
+    const uint32_t half = blockIdx.x & 1u;
     const int pair = (blockIdx.x >> 1) / ksplit, split = (blockIdx.x >> 1) % ksplit;
     const int64_t r0 = (int64_t)split * kGramK, r1 = min(rows, r0 + kGramK);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int cI = col0[2 * pair], cJ = col0[2 * pair + 1];
-    const uint32_t sbase = smem_addr(smem), sbase_peer = map_peer(sbase, peer);
-    cluster_sync();  // both CTAs are running before either touches the other's shared memory
-    // column exponents of this CTA's 64 columns over the CTA pair's rows, to both CTAs
-    for (int cc = warp; cc < NNX / 2; cc += kThrG / 32) {
-        const int c = NNX / 2 * (int)half + cc;
-        const double *g = G + (int64_t)(c < NNX / 2 ? cI + c : cJ + c - NNX / 2) * ldg;
+    auto colptr = [&](int c) { return G + (int64_t)(c < NNX / 2 ? cI + c : cJ + c - NNX / 2) * ldg; };
+    // column exponents over the split's rows (both CTAs of the pair: the same values)
+    for (int c = warp; c < NNX; c += kThrG / 32) {
+        const double *g = colptr(c);
         int e = -2000;
-        // eight loads in flight per lane
         int64_t r = r0 + lane;
-        for (; r + 7 * 32 < r1; r += 8 * 32) {
+        for (; r + 7 * 32 < r1; r += 8 * 32) {  // eight loads in flight per lane
             double x[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) x[u] = g[r + u * 32];
@@ -125,111 +133,116 @@ k_gram_x(const double *__restrict__ G, int64_t rows, int64_t ldg, const int *__r
         }
         for (; r < r1; r += 32) e = max(e, exp_bound(g[r]));
         e = warp_max_i(e);
-        if (lane == 0) {
-            e = e < -1000 ? 0 : e;
-            Ecol[c] = e;
-            st_cluster_s32(map_peer(smem_addr(&Ecol[c]), peer), e);
-        }
+        if (lane == 0) Ecol[c] = e < -1000 ? 0 : e;
     }
     if (tid == 0) {
         s_fail = 0;
-        mbar_init(&mbar[0], 1);
-        mbar_init(&mbar[1], 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&full[b], 1);   // the splitters' arrival
+            mbar_init(&empty[b], 1);  // the products' commit
+        }
     }
     if (warp == 0) tmem_alloc(&tbase, kTmemCols);
     fence_before();
-    cluster_sync();
+    __syncthreads();
     fence_after();
     const uint32_t tmem = tbase;
-    const uint32_t idesc = idesc_bf16(NNX, kN);
-    const uint32_t sbo = (kGramKT / 8) * 128;
-    const uint32_t b_off = core_offset(kN * (int)half, 0, kGramKT);
-    int inited[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const int ntiles = (int)((r1 - r0 + kGramKT - 1) / kGramKT);
-    // split mapping: a warp writes one 8 x 8 core matrix per step; lane -> column
-    // (lane >> 2) of the group, rows 2 (lane & 3) and 2 (lane & 3) + 1
-    const int cc = lane >> 2, kp = 2 * (lane & 3);
-    constexpr int kCoresPerWarp = (NNX / 2 / 8) * (kGramKT / 8) / (kThrG / 32);
-    static_assert(kCoresPerWarp * (kThrG / 32) == (NNX / 2 / 8) * (kGramKT / 8), "Gram split mapping");
-    // the values of tile t this thread splits; the next tile's are loaded while
-    // the barrier and the products of the current one run
-    auto load_tile = [&](int t, double (&x)[kCoresPerWarp][2]) {
-        const int64_t t0 = r0 + (int64_t)t * kGramKT;
-#pragma unroll
-        for (int ci = 0; ci < kCoresPerWarp; ++ci) {
-            const int core = warp + ci * (kThrG / 32);
-            const int cg = core / (kGramKT / 8), kg = core % (kGramKT / 8);
-            const int c = NNX / 2 * (int)half + cg * 8 + cc, k = kg * 8 + kp;
-            const double *g = G + (int64_t)(c < NNX / 2 ? cI + c : cJ + c - NNX / 2) * ldg;
-            const int64_t row = t0 + k;
-            x[ci][0] = row < r1 ? g[row] : 0.0;
-            x[ci][1] = row + 1 < r1 ? g[row + 1] : 0.0;
-        }
+    auto wait1 = [&](uint64_t *mb, int use) {
+        if (!s_fail && !mbar_wait(mb, (uint32_t)((use >> 1) & 1), kWaitIter)) s_fail = 1;
     };
-    double cur[kCoresPerWarp][2];
-    if (ntiles > 0) load_tile(0, cur);
-    for (int t = 0; t < ntiles; ++t) {
-        const uint32_t buf = (uint32_t)(t & 1) * kBufBytes;
+    if (warp > 0) {
+        // ------------------------------------------------ splitters
+        // a warp writes one 8 x 8 core matrix per step: lane -> column
+        // (lane >> 2) of the group, rows 2 (lane & 3) and 2 (lane & 3) + 1
+        const int pw = warp - 1, ptid = tid - 32;
+        const int cc = lane >> 2, kp = 2 * (lane & 3);
+        constexpr int kCoresPerWarp = (NNX / 8) * (kGramKT / 8) / kProdWarps;
+        static_assert(kCoresPerWarp * kProdWarps == (NNX / 8) * (kGramKT / 8), "Gram split mapping");
+        auto load_tile = [&](int t, double (&x)[kCoresPerWarp][2]) {
+            const int64_t t0 = r0 + (int64_t)t * kGramKT;
 #pragma unroll
-        for (int ci = 0; ci < kCoresPerWarp; ++ci) {
-            const int core = warp + ci * (kThrG / 32);
-            const int cg = core / (kGramKT / 8), kg = core % (kGramKT / 8);
-            const int c = NNX / 2 * (int)half + cg * 8 + cc, k = kg * 8 + kp;
-            const long long w0 = digit_word(cur[ci][0], Ecol[c]), w1 = digit_word(cur[ci][1], Ecol[c]);
-            const uint32_t off = buf + core_offset(c, k, kGramKT);
-#pragma unroll
-            for (int s = 0; s < kSlices; ++s) {
-                const uint32_t v = slice_pair(w0, w1, s + 1);
-                const uint32_t o = off + (uint32_t)s * kSliceBytes;
-                *reinterpret_cast<uint32_t *>(smem + o) = v;
-                st_cluster_u32(sbase_peer + o, v);
+            for (int ci = 0; ci < kCoresPerWarp; ++ci) {
+                const int core = pw + ci * kProdWarps;
+                const int c = (core / (kGramKT / 8)) * 8 + cc, k = (core % (kGramKT / 8)) * 8 + kp;
+                const double *g = colptr(c);
+                const int64_t row = t0 + k;
+                x[ci][0] = row < r1 ? g[row] : 0.0;
+                x[ci][1] = row + 1 < r1 ? g[row + 1] : 0.0;
             }
-        }
-        if (t + 1 < ntiles) load_tile(t + 1, cur);
-        fence_proxy_async_cluster();
-        fence_proxy_async();
-        // the products of tile t - 1 are done in this CTA: its buffer is free
-        // for tile t + 1 in both CTAs once both have passed the barrier below
-        // one thread waits; the others block in the cluster barrier (no polling)
-        if (tid == 0 && t >= 1 && !s_fail && !mbar_wait(&mbar[(t - 1) & 1], ((t - 1) >> 1) & 1, kWaitIter))
-            s_fail = 1;
-        fence_before();
-        cluster_sync();
-        fence_after();
-        if (tid == 0 && !s_fail) {
+        };
+        double cur[kCoresPerWarp][2];
+        if (ntiles > 0) load_tile(0, cur);
+        for (int t = 0; t < ntiles; ++t) {
+            const int b = t & 1;
+            if (ptid == 0 && t >= 2) wait1(&empty[b], t - 2);  // the products of tile t - 2 read buffer b
+            bar_named(1, kProd);
+            if (!s_fail) {
+                unsigned char *buf = smem + (uint32_t)b * kBufBytes;
+#pragma unroll
+                for (int ci = 0; ci < kCoresPerWarp; ++ci) {
+                    const int core = pw + ci * kProdWarps;
+                    const int c = (core / (kGramKT / 8)) * 8 + cc, k = (core % (kGramKT / 8)) * 8 + kp;
+                    const long long w0 = digit_word(cur[ci][0], Ecol[c]), w1 = digit_word(cur[ci][1], Ecol[c]);
+                    const uint32_t off = core_offset(c, k, kGramKT);
+#pragma unroll
+                    for (int sl = 0; sl < kSlices; ++sl)
+                        *reinterpret_cast<uint32_t *>(buf + off + (uint32_t)sl * kSliceBytes) = slice_pair(w0, w1, sl + 1);
+                }
+            }
             fence_proxy_async();
-            const uint32_t base = sbase + buf;
-            for (int ks = 0; ks < kGramKT / 16; ++ks)
-                issue_products(tmem, base, kSliceBytes, base + b_off, kSliceBytes, ks * 256, sbo, idesc, inited);
-            commit(&mbar[t & 1]);
+            bar_named(1, kProd);
+            if (ptid == 0 && !s_fail) mbar_arrive(&full[b]);
+            if (t + 1 < ntiles) load_tile(t + 1, cur);
         }
+    } else {
+        // ------------------------------------------------ products (warp 0, lane 0)
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(NNX, kN);
+            const uint32_t sbo = (kGramKT / 8) * 128;
+            const uint32_t b_off = core_offset(kN * (int)half, 0, kGramKT);
+            int inited[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            for (int t = 0; t < ntiles; ++t) {
+                const int b = t & 1;
+                wait1(&full[b], t);
+                if (s_fail) continue;
+                fence_after();
+                const uint32_t base = smem_addr(smem) + (uint32_t)b * kBufBytes;
+                for (int ks = 0; ks < kGramKT / 16; ++ks)
+                    issue_products(tmem, base, kSliceBytes, base + b_off, kSliceBytes, ks * 256, sbo, idesc, inited);
+                commit(&empty[b]);
+            }
+            if (ntiles > 0) wait1(&empty[(ntiles - 1) & 1], ntiles - 1);
+        }
+        __syncwarp();
     }
-    if (tid == 0 && ntiles > 0 && !s_fail && !mbar_wait(&mbar[(ntiles - 1) & 1], ((ntiles - 1) >> 1) & 1, kWaitIter))
-        s_fail = 1;
     __syncthreads();
     fence_after();
     if (!s_fail) {
-        // lane c = row of A_P; warp group h2 takes TMEM columns [16 h2, 16 h2 + 16)
-        const int q = warp & 3, c = 32 * q + lane, h2 = warp >> 2;
-        constexpr int kCols = kN / (kThrG / 128);
-        double *out = part + ((size_t)pair * ksplit + split) * NNX * NNX;
-        for (int c0 = kCols * h2; c0 < kCols * h2 + kCols; c0 += 8) {
-            float v[8][8];
-            read_accs(tmem, 32 * q, c0, v);
+        // warps 1..16: lane c = row of A_P (TMEM lane quarter warp % 4), the
+        // four warps of a quarter take 16 TMEM columns each
+        if (warp > 0) {
+            const int q = warp & 3, c = 32 * q + lane, h2 = (warp - 1) >> 2;
+            constexpr int kCols = kN / 4;
+            double *out = part + ((size_t)pair * ksplit + split) * NNX * NNX;
+            for (int c0 = kCols * h2; c0 < kCols * h2 + kCols; c0 += 8) {
+                float v[8][8];
+                read_accs(tmem, 32 * q, c0, v);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                float d[8];
+                for (int j = 0; j < 8; ++j) {
+                    float d[8];
 #pragma unroll
-                for (int a = 0; a < 8; ++a) d[a] = v[a][j];
-                const int col = kN * (int)half + c0 + j;
-                out[c + (size_t)col * NNX] = combine8(d, Ecol[c] + Ecol[col]);
+                    for (int a = 0; a < 8; ++a) d[a] = v[a][j];
+                    const int col = kN * (int)half + c0 + j;
+                    out[c + (size_t)col * NNX] = combine8(d, Ecol[c] + Ecol[col]);
+                }
             }
         }
     } else if (tid == 0 && status) {
         atomicExch(status, HSVD_ERR_CUDA);
     }
     fence_before();
-    cluster_sync();  // no CTA leaves while its peer may still touch its shared memory
+    __syncthreads();
     fence_after();
     if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
@@ -304,7 +317,6 @@ struct UpdItem {
     int pair, which, cI, cJ;
 };
 
-__device__ __forceinline__ void bar_named(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 
 __global__ void __launch_bounds__(kThrU, 1)
 k_update_x(double *__restrict__ X, int64_t rowsX, int64_t ldx, double *__restrict__ Y, int64_t rowsY, int64_t ldy,
@@ -376,18 +388,31 @@ k_update_x(double *__restrict__ X, int64_t rowsX, int64_t ldx, double *__restric
             const int qd = warp & 3, j = 32 * qd + lane, h2 = warp >> 2;
             const int jj = j < NNX / 2 ? d.cI + j : d.cJ + j - NNX / 2;
             constexpr int kCols = kN / (kThrU / 128);
+            // a thread's values are consecutive rows of one column: stored two
+            // at a time (16 B) where the column start allows it
+            double *col = d.M + (int64_t)jj * d.ld;
+            const bool vec = ((reinterpret_cast<uintptr_t>(col) & 15u) == 0);
             for (int c0 = kCols * h2; c0 < kCols * h2 + kCols; c0 += 8) {
                 float v[8][8];
                 read_accs(tmem, 32 * qd, c0, v);
 #pragma unroll
-                for (int t = 0; t < 8; ++t) {
+                for (int t = 0; t < 8; t += 2) {
                     const int i = c0 + t;
                     const int64_t row = d.r0 + i;
-                    if (row >= d.rows) continue;
-                    float dd[8];
+                    float d0[8], d1[8];
 #pragma unroll
-                    for (int a = 0; a < 8; ++a) dd[a] = v[a][t];
-                    d.M[row + (int64_t)jj * d.ld] = combine8_small(dd, Erow[slot][i] + Fcol[slot][j]);
+                    for (int a = 0; a < 8; ++a) {
+                        d0[a] = v[a][t];
+                        d1[a] = v[a][t + 1];
+                    }
+                    const double x0 = combine8_small(d0, Erow[slot][i] + Fcol[slot][j]);
+                    const double x1 = combine8_small(d1, Erow[slot][i + 1] + Fcol[slot][j]);
+                    if (vec && row + 1 < d.rows) {
+                        *reinterpret_cast<double2 *>(col + row) = make_double2(x0, x1);
+                    } else {
+                        if (row < d.rows) col[row] = x0;
+                        if (row + 1 < d.rows) col[row + 1] = x1;
+                    }
                 }
             }
         }
