@@ -35,6 +35,7 @@ constexpr int kThrU = 512;           // update: sixteen warps, four per TMEM lan
 constexpr int kThrG = 544;           // Gram: the products warp and sixteen splitting warps
 constexpr int kGramK = 512;          // rows of G per Gram CTA pair (exactness window)
 constexpr int kGramKT = 32;          // rows per shared-memory tile of the Gram
+constexpr int kGramBufs = 2;         // Gram tiles in flight (64 KB each)
 constexpr int kUpdKT = 32;           // k per shared-memory tile of the update
 constexpr int kUpdRows = 64;         // rows of G or V per update item (N)
 constexpr int kN = 64;               // MMA N
@@ -60,10 +61,16 @@ __device__ __forceinline__ void issue_products(uint32_t tmem, uint32_t a_base, u
 #pragma unroll
     for (int a = 1; a <= kSlices; ++a) {
         const uint64_t da = da0 + (uint64_t)(a - 1) * as;
+        // the products of slice a of A, which is read once (collector buffer)
 #pragma unroll
         for (int b = 1; a + b <= kSlices + 1; ++b) {
-            const int acc = a + b - 2;
-            mma(tmem + (uint32_t)acc * kN, da, db0 + (uint64_t)(b - 1) * bs, idesc, (uint32_t)inited[acc]);
+            const int acc = a + b - 2, last = kSlices + 1 - a;
+            const uint32_t d = tmem + (uint32_t)acc * kN, en = (uint32_t)inited[acc];
+            const uint64_t db = db0 + (uint64_t)(b - 1) * bs;
+            if (last == 1) mma(d, da, db, idesc, en);
+            else if (b == 1) mma_keep_a<CollectorA::Fill>(d, da, db, idesc, en);
+            else if (b < last) mma_keep_a<CollectorA::Use>(d, da, db, idesc, en);
+            else mma_keep_a<CollectorA::LastUse>(d, da, db, idesc, en);
             inited[acc] = 1;
         }
     }
@@ -93,7 +100,7 @@ __device__ __forceinline__ void read_accs(uint32_t tmem, int lane_base, int c0, 
 // [64 h, 64 h + 64) of the same tile.  Each CTA splits the whole 128-column
 // tile itself (the split is cheap next to the products; no shared memory is
 // written across CTAs and no cluster barrier is needed).  Warp-specialised
-// pipeline over 32-row tiles, double-buffered:
+// pipeline over 32-row tiles, kGramBufs in flight:
 //   - warps 1..16 wait until the products that last read a buffer are done
 //     (mbarrier `empty`), split the tile into it (its values loaded one tile
 //     ahead) and arrive on `full`;
@@ -110,7 +117,7 @@ k_gram_x(const double *__restrict__ G, int64_t rows, int64_t ldg, const int *__r
     constexpr int kProd = kThrG - 32;                       // splitting threads (warps 1..16)
     constexpr int kProdWarps = kProd / 32;
     __shared__ int Ecol[NNX];
-    __shared__ __align__(8) uint64_t full[2], empty[2];
+    __shared__ __align__(8) uint64_t full[kGramBufs], empty[kGramBufs];
     __shared__ uint32_t tbase;
     __shared__ int s_fail;
     const uint32_t half = blockIdx.x & 1u;
@@ -124,12 +131,12 @@ k_gram_x(const double *__restrict__ G, int64_t rows, int64_t ldg, const int *__r
         const double *g = colptr(c);
         int e = -2000;
         int64_t r = r0 + lane;
-        for (; r + 7 * 32 < r1; r += 8 * 32) {  // eight loads in flight per lane
-            double x[8];
+        for (; r + 15 * 32 < r1; r += 16 * 32) {  // sixteen loads in flight per lane
+            double x[16];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) x[u] = g[r + u * 32];
+            for (int u = 0; u < 16; ++u) x[u] = g[r + u * 32];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) e = max(e, exp_bound(x[u]));
+            for (int u = 0; u < 16; ++u) e = max(e, exp_bound(x[u]));
         }
         for (; r < r1; r += 32) e = max(e, exp_bound(g[r]));
         e = warp_max_i(e);
@@ -137,7 +144,7 @@ k_gram_x(const double *__restrict__ G, int64_t rows, int64_t ldg, const int *__r
     }
     if (tid == 0) {
         s_fail = 0;
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < kGramBufs; ++b) {
             mbar_init(&full[b], 1);   // the splitters' arrival
             mbar_init(&empty[b], 1);  // the products' commit
         }
@@ -148,8 +155,9 @@ k_gram_x(const double *__restrict__ G, int64_t rows, int64_t ldg, const int *__r
     fence_after();
     const uint32_t tmem = tbase;
     const int ntiles = (int)((r1 - r0 + kGramKT - 1) / kGramKT);
-    auto wait1 = [&](uint64_t *mb, int use) {
-        if (!s_fail && !mbar_wait(mb, (uint32_t)((use >> 1) & 1), kWaitIter)) s_fail = 1;
+    // the use-th fill of a buffer (tile t is fill t / kGramBufs of buffer t % kGramBufs)
+    auto wait1 = [&](uint64_t *mb, int tile) {
+        if (!s_fail && !mbar_wait(mb, (uint32_t)((tile / kGramBufs) & 1), kWaitIter)) s_fail = 1;
     };
     if (warp > 0) {
         // ------------------------------------------------ splitters
@@ -174,8 +182,9 @@ k_gram_x(const double *__restrict__ G, int64_t rows, int64_t ldg, const int *__r
         double cur[kCoresPerWarp][2];
         if (ntiles > 0) load_tile(0, cur);
         for (int t = 0; t < ntiles; ++t) {
-            const int b = t & 1;
-            if (ptid == 0 && t >= 2) wait1(&empty[b], t - 2);  // the products of tile t - 2 read buffer b
+            const int b = t % kGramBufs;
+            // the products of tile t - kGramBufs read buffer b
+            if (ptid == 0 && t >= kGramBufs) wait1(&empty[b], t - kGramBufs);
             bar_named(1, kProd);
             if (!s_fail) {
                 unsigned char *buf = smem + (uint32_t)b * kBufBytes;
@@ -185,9 +194,11 @@ k_gram_x(const double *__restrict__ G, int64_t rows, int64_t ldg, const int *__r
                     const int c = (core / (kGramKT / 8)) * 8 + cc, k = (core % (kGramKT / 8)) * 8 + kp;
                     const long long w0 = digit_word(cur[ci][0], Ecol[c]), w1 = digit_word(cur[ci][1], Ecol[c]);
                     const uint32_t off = core_offset(c, k, kGramKT);
+                    uint32_t sw[kSlices];
+                    slice_pairs8(w0, w1, sw);
 #pragma unroll
                     for (int sl = 0; sl < kSlices; ++sl)
-                        *reinterpret_cast<uint32_t *>(buf + off + (uint32_t)sl * kSliceBytes) = slice_pair(w0, w1, sl + 1);
+                        *reinterpret_cast<uint32_t *>(buf + off + (uint32_t)sl * kSliceBytes) = sw[sl];
                 }
             }
             fence_proxy_async();
@@ -203,7 +214,7 @@ k_gram_x(const double *__restrict__ G, int64_t rows, int64_t ldg, const int *__r
             const uint32_t b_off = core_offset(kN * (int)half, 0, kGramKT);
             int inited[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             for (int t = 0; t < ntiles; ++t) {
-                const int b = t & 1;
+                const int b = t % kGramBufs;
                 wait1(&full[b], t);
                 if (s_fail) continue;
                 fence_after();
@@ -212,7 +223,7 @@ k_gram_x(const double *__restrict__ G, int64_t rows, int64_t ldg, const int *__r
                     issue_products(tmem, base, kSliceBytes, base + b_off, kSliceBytes, ks * 256, sbo, idesc, inited);
                 commit(&empty[b]);
             }
-            if (ntiles > 0) wait1(&empty[(ntiles - 1) & 1], ntiles - 1);
+            if (ntiles > 0) wait1(&empty[(ntiles - 1) % kGramBufs], ntiles - 1);
         }
         __syncwarp();
     }
@@ -286,9 +297,10 @@ k_wprep_x(const double *__restrict__ Wp, const int *__restrict__ dexp, const int
         const long long d0 = digit_word(w0, F[j] - dk[k]);
         const long long d1 = digit_word(w1, F[j] - dk[k + 1]);
         const uint32_t off = core_offset(j, kk, kUpdKT) >> 1;
+        uint32_t sw[kSlices];
+        slice_pairs8(d0, d1, sw);
 #pragma unroll
-        for (int s = 0; s < kSlices; ++s)
-            *reinterpret_cast<uint32_t *>(dst + s * kTile + off) = slice_pair(d0, d1, s + 1);
+        for (int s = 0; s < kSlices; ++s) *reinterpret_cast<uint32_t *>(dst + s * kTile + off) = sw[s];
     }
 }
 
@@ -488,9 +500,10 @@ k_update_x(double *__restrict__ X, int64_t rowsX, int64_t ldx, double *__restric
                     const long long w0 = digit_word(x0, Erow[slot][i] + dk[slot][k]);
                     const long long w1 = digit_word(x1, Erow[slot][i] + dk[slot][k + 1]);
                     const uint32_t off = core_offset(i, kk, kUpdKT);
+                    uint32_t sw[kSlices];
+                    slice_pairs8(w0, w1, sw);
 #pragma unroll
-                    for (int sl = 0; sl < kSlices; ++sl)
-                        *reinterpret_cast<uint32_t *>(Bb + sl * kBTile + off) = slice_pair(w0, w1, sl + 1);
+                    for (int sl = 0; sl < kSlices; ++sl) *reinterpret_cast<uint32_t *>(Bb + sl * kBTile + off) = sw[sl];
                 }
                 fence_proxy_async();
                 bar_named(1, kProd);
@@ -571,7 +584,7 @@ int precision_gram_ksplit(int64_t rows) { return (int)((rows + kGramK - 1) / kGr
 cudaError_t launch_gram_x(const double *G, int64_t rows, int64_t ldg, int npairs, const int *col0, double *part,
                           int *status, cudaStream_t st) {
     const int ksplit = precision_gram_ksplit(rows);
-    const size_t smem = (size_t)2 * kSlices * NNX * kGramKT * 2;  // two tiles
+    const size_t smem = (size_t)kGramBufs * kSlices * NNX * kGramKT * 2;
     cudaError_t e = cudaFuncSetAttribute(k_gram_x, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_gram_x<<<npairs * ksplit * 2, kThrG, smem, st>>>(G, rows, ldg, col0, ksplit, part, status);

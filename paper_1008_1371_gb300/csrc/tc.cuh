@@ -64,6 +64,30 @@ __device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a_desc, uint64_t b
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
         "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate));
 }
+// The same product with the A operand kept in the tensor core's collector
+// buffer: FILL reads A from shared memory and keeps it, USE takes the kept A
+// (no shared-memory read), LASTUSE takes it and releases the buffer.  A run
+// of products sharing one A descriptor reads A once.
+enum class CollectorA { Fill, Use, LastUse };
+template <CollectorA C>
+__device__ __forceinline__ void mma_keep_a(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                           uint32_t accumulate) {
+    if constexpr (C == CollectorA::Fill)
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+            "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate));
+    else if constexpr (C == CollectorA::Use)
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::f16.collector::a::use [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+            "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate));
+    else
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+            "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate));
+}
 __device__ __forceinline__ void commit(uint64_t *mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
         smem_addr(mbar)));
@@ -225,6 +249,44 @@ __device__ __forceinline__ uint32_t slice_pair(long long Wlo, long long Whi, int
     return *reinterpret_cast<const uint32_t *>(&r);
 }
 
+// All eight slices of two elements (as slice_pair for k = 1..8) from 32-bit
+// halves of W: h = W >> 28 (|W| < 2^56, so h fits 32 bits) holds digits 1..4
+// (q_1 = h >> 21 arithmetically, the others 7-bit fields), the low 28 bits of
+// W hold digits 5..8.  The two elements' digits are paired by a byte permute.
+__device__ __forceinline__ void slice_pairs8(long long W0, long long W1, uint32_t (&out)[kSlices]) {
+    const int h0 = (int)(W0 >> 28), h1 = (int)(W1 >> 28);
+    const uint32_t l0 = (uint32_t)W0 & 0x0FFFFFFFu, l1 = (uint32_t)W1 & 0x0FFFFFFFu;
+    uint32_t u0[kSlices], u1[kSlices];
+    u0[0] = (uint32_t)((h0 >> 21) + 64);
+    u1[0] = (uint32_t)((h1 >> 21) + 64);
+    u0[1] = ((uint32_t)h0 >> 14) & 127u;
+    u1[1] = ((uint32_t)h1 >> 14) & 127u;
+    u0[2] = ((uint32_t)h0 >> 7) & 127u;
+    u1[2] = ((uint32_t)h1 >> 7) & 127u;
+    u0[3] = (uint32_t)h0 & 127u;
+    u1[3] = (uint32_t)h1 & 127u;
+    u0[4] = l0 >> 21;
+    u1[4] = l1 >> 21;
+    u0[5] = (l0 >> 14) & 127u;
+    u1[5] = (l1 >> 14) & 127u;
+    u0[6] = (l0 >> 7) & 127u;
+    u1[6] = (l1 >> 7) & 127u;
+    u0[7] = l0 & 127u;
+    u1[7] = l1 & 127u;
+#pragma unroll
+    for (int k = 1; k <= kSlices; ++k) {
+        const uint32_t packed = __byte_perm(u0[k - 1], u1[k - 1], 0x5410) + 0x43004300u;
+        const uint32_t sc = (uint32_t)(128 - 7 * k) << 7;
+        const uint32_t off = 0x8000u | ((uint32_t)(135 - 7 * k) << 7) | 0x40u;
+        const __nv_bfloat162 r = __hfma2(*reinterpret_cast<const __nv_bfloat162 *>(&packed),
+                                         __halves2bfloat162(__ushort_as_bfloat16((unsigned short)sc),
+                                                            __ushort_as_bfloat16((unsigned short)sc)),
+                                         __halves2bfloat162(__ushort_as_bfloat16((unsigned short)off),
+                                                            __ushort_as_bfloat16((unsigned short)off)));
+        out[k - 1] = *reinterpret_cast<const uint32_t *>(&r);
+    }
+}
+
 // Products S_a S_b with a + b = d (d = 2..9) accumulate in accumulator d - 2:
 // integers in units 2^(2-7d) of magnitude at most K (d-1) 2^12 <= 2^24 for
 // K <= 512, exact in FP32.  Recombination in integers: H = sum_{d<=5} I_d
@@ -233,11 +295,36 @@ __device__ __forceinline__ uint32_t slice_pair(long long Wlo, long long Whi, int
 // nearest even.  No FP64 instruction on the normal-range path.
 __device__ __forceinline__ double combine_ints(const long long (&I)[8], int escale);
 
+// v 2^e as a double, exactly, for an integer |v| < 2^53 whose scaled value is
+// a normal number (the caller checks the range): the bits are assembled.
+__device__ __forceinline__ double exact_scaled(long long v, int e) {
+    if (v == 0) return 0.0;
+    const unsigned long long sgn = v < 0 ? (1ull << 63) : 0ull;
+    const unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+    const int lz = __clzll((long long)a);               // >= 11
+    const unsigned long long mant = a << (lz - 11);     // leading one at bit 52
+    const unsigned long long ex = (unsigned long long)(63 - lz + e + 1022);
+    return __longlong_as_double((long long)(sgn | (mant + (ex << 52))));  // the leading one adds 1
+}
+
+// T 2^(escale - 61), T = sum_k I_k 2^(7 (7 - k)), rounded once.  With
+// H = sum_{k<4} I_k 2^(7 (3 - k)) and L = sum_{k>=4} I_k 2^(7 (7 - k)) (both
+// below 2^53 in magnitude), T = H 2^28 + L: the two scaled halves are exact
+// doubles and one FP64 addition rounds their sum correctly.  Scales where a
+// half could leave the normal range take the 128-bit integer path.
+__device__ __forceinline__ double combine_halves(const long long (&I)[8], int escale) {
+    const int sc = escale - 61;
+    if (sc < -1000 || sc > 900) return combine_ints(I, escale);
+    const long long H = (I[0] << 21) + (I[1] << 14) + (I[2] << 7) + I[3];
+    const long long L = (I[4] << 21) + (I[5] << 14) + (I[6] << 7) + I[7];
+    return exact_scaled(H, sc + 28) + exact_scaled(L, sc);
+}
+
 __device__ __forceinline__ double combine8(const float (&d)[8], int escale) {
     long long I[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) I[k] = (long long)__float2int_rn(d[k] * __int_as_float((127 + 12 + 7 * k) << 23));
-    return combine_ints(I, escale);
+    return combine_halves(I, escale);
 }
 
 // The same rounding for accumulators whose integers are at most 2^22 in
@@ -253,7 +340,7 @@ __device__ __forceinline__ double combine8_small(const float (&d)[8], int escale
         const int mb = ((127 + 11 - 7 * k) << 23) | 0x400000;  // 1.5 2^(11 - 7k) = 1.5 2^23 units of 2^-(12+7k)
         I[k] = (long long)(__float_as_int(d[k] + __int_as_float(mb)) - mb);
     }
-    return combine_ints(I, escale);
+    return combine_halves(I, escale);
 }
 
 __device__ __forceinline__ double combine_ints(const long long (&I)[8], int escale) {
