@@ -35,7 +35,7 @@ constexpr int kThrU = 512;           // update: sixteen warps, four per TMEM lan
 constexpr int kThrG = 544;           // Gram: the products warp and sixteen splitting warps
 constexpr int kGramK = 512;          // rows of G per Gram CTA pair (exactness window)
 constexpr int kGramKT = 32;          // rows per shared-memory tile of the Gram
-constexpr int kGramBufs = 2;         // Gram tiles in flight (64 KB each)
+constexpr int kGramBufs = 2;         // Gram tiles in flight (96 KB each)
 constexpr int kUpdKT = 32;           // k per shared-memory tile of the update
 constexpr int kUpdRows = 64;         // rows of G or V per update item (N)
 constexpr int kN = 64;               // MMA N
@@ -48,30 +48,26 @@ __device__ __forceinline__ int warp_max_i(int v) {
     return v;
 }
 
-// The 36 slice products of one K step (16 k): slice s of A at a_base + s *
-// a_stride bytes, of B at b_base + s * b_stride; koff selects the K step.  The
-// descriptors of one K step differ only in the start-address field (address
-// >> 4 in the low 14 bits; every address here is below 2^18), so they are
-// formed once and advanced by one add per slice.
+// The 36 slice products of one K step (16 k) as 12 instructions.  Slice a of
+// A (at a_base + (a - 1) a_stride) meets B slices 1 .. 9 - a, which lie side
+// by side along N (slice b at b_base + (b - 1) b_stride, b_stride = 8 core
+// groups of sbo bytes, so one descriptor with a uniform group stride covers
+// several): one product with N = 64 nb covers b = b1 .. b1 + nb - 1 and writes
+// accumulators a + b1 - 2 .. a + b1 + nb - 3, adjacent in TMEM.  Large N keeps
+// the tensor core near its peak; 36 products with N = 64 ran at 0.42 of it.
+// `first`: the first K step of an accumulation (slice 1 initialises all eight
+// accumulators; the later products add to them).
 __device__ __forceinline__ void issue_products(uint32_t tmem, uint32_t a_base, uint32_t a_stride, uint32_t b_base,
-                                               uint32_t b_stride, uint32_t koff, uint32_t sbo, uint32_t idesc,
-                                               int (&inited)[8]) {
-    const uint64_t da0 = smem_desc(a_base + koff, 128, sbo), db0 = smem_desc(b_base + koff, 128, sbo);
-    const uint64_t as = a_stride >> 4, bs = b_stride >> 4;
+                                               uint32_t b_stride, uint32_t koff, uint32_t sbo, bool first) {
+    const uint64_t da0 = smem_desc(a_base + koff, 128, sbo);
 #pragma unroll
     for (int a = 1; a <= kSlices; ++a) {
-        const uint64_t da = da0 + (uint64_t)(a - 1) * as;
-        // the products of slice a of A, which is read once (collector buffer)
+        const uint64_t da = da0 + (uint64_t)(a - 1) * (a_stride >> 4);
 #pragma unroll
-        for (int b = 1; a + b <= kSlices + 1; ++b) {
-            const int acc = a + b - 2, last = kSlices + 1 - a;
-            const uint32_t d = tmem + (uint32_t)acc * kN, en = (uint32_t)inited[acc];
-            const uint64_t db = db0 + (uint64_t)(b - 1) * bs;
-            if (last == 1) mma(d, da, db, idesc, en);
-            else if (b == 1) mma_keep_a<CollectorA::Fill>(d, da, db, idesc, en);
-            else if (b < last) mma_keep_a<CollectorA::Use>(d, da, db, idesc, en);
-            else mma_keep_a<CollectorA::LastUse>(d, da, db, idesc, en);
-            inited[acc] = 1;
+        for (int b1 = 1; a + b1 <= kSlices + 1; b1 += 4) {
+            const int nb = (kSlices + 2 - a - b1) < 4 ? (kSlices + 2 - a - b1) : 4;
+            const uint64_t db = smem_desc(b_base + (uint32_t)(b1 - 1) * b_stride + koff, 128, sbo);
+            mma(tmem + (uint32_t)(a + b1 - 2) * kN, da, db, idesc_bf16(NNX, kN * nb), (first && a == 1) ? 0u : 1u);
         }
     }
 }
@@ -97,14 +93,15 @@ __device__ __forceinline__ void read_accs(uint32_t tmem, int lane_base, int c0, 
 // Two CTAs per (pair, split): CTA h forms columns [64 h, 64 h + 64) of the
 // partial A_P over rows [512 split, 512 split + 512) of the panel
 // P = [G_I G_J] (m x 128): A = P^T (128 x K, K-major), B = columns
-// [64 h, 64 h + 64) of the same tile.  Each CTA splits the whole 128-column
-// tile itself (the split is cheap next to the products; no shared memory is
-// written across CTAs and no cluster barrier is needed).  Warp-specialised
+// [64 h, 64 h + 64) of the same tile, written a second time with the eight
+// slices side by side (the wide products of issue_products).  Each CTA splits
+// the whole 128-column tile itself (no shared memory is written across CTAs
+// and no cluster barrier is needed).  Warp-specialised
 // pipeline over 32-row tiles, kGramBufs in flight:
 //   - warps 1..16 wait until the products that last read a buffer are done
 //     (mbarrier `empty`), split the tile into it (its values loaded one tile
 //     ahead) and arrive on `full`;
-//   - warp 0, lane 0 waits on `full`, issues the tile's 72 products and
+//   - warp 0, lane 0 waits on `full`, issues the tile's 24 products and
 //     commits them to `empty`.
 // Every wait is bounded; after a failure each role still passes the same
 // barriers and the kernel reports HSVD_ERR_CUDA.
@@ -112,8 +109,10 @@ __global__ void __launch_bounds__(kThrG, 1)
 k_gram_x(const double *__restrict__ G, int64_t rows, int64_t ldg, const int *__restrict__ col0, int ksplit,
          double *__restrict__ part, int *__restrict__ status) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    constexpr uint32_t kSliceBytes = NNX * kGramKT * 2;     // one slice of a tile (8 KB)
-    constexpr uint32_t kBufBytes = kSlices * kSliceBytes;   // one tile (64 KB)
+    constexpr uint32_t kSliceBytes = NNX * kGramKT * 2;     // one slice of a tile, all columns (8 KB)
+    constexpr uint32_t kHalfBytes = kN * kGramKT * 2;       // one slice, this CTA's columns (4 KB)
+    constexpr uint32_t kBOff = kSlices * kSliceBytes;       // the B copy after the A slices
+    constexpr uint32_t kBufBytes = kBOff + kSlices * kHalfBytes;  // one tile (96 KB)
     constexpr int kProd = kThrG - 32;                       // splitting threads (warps 1..16)
     constexpr int kProdWarps = kProd / 32;
     __shared__ int Ecol[NNX];
@@ -199,6 +198,12 @@ k_gram_x(const double *__restrict__ G, int64_t rows, int64_t ldg, const int *__r
 #pragma unroll
                     for (int sl = 0; sl < kSlices; ++sl)
                         *reinterpret_cast<uint32_t *>(buf + off + (uint32_t)sl * kSliceBytes) = sw[sl];
+                    if ((c >> 6) == (int)half) {  // this CTA's columns again, for B (warp-uniform)
+                        const uint32_t offb = kBOff + core_offset(c - kN * (int)half, k, kGramKT);
+#pragma unroll
+                        for (int sl = 0; sl < kSlices; ++sl)
+                            *reinterpret_cast<uint32_t *>(buf + offb + (uint32_t)sl * kHalfBytes) = sw[sl];
+                    }
                 }
             }
             fence_proxy_async();
@@ -209,10 +214,8 @@ k_gram_x(const double *__restrict__ G, int64_t rows, int64_t ldg, const int *__r
     } else {
         // ------------------------------------------------ products (warp 0, lane 0)
         if (lane == 0) {
-            const uint32_t idesc = idesc_bf16(NNX, kN);
             const uint32_t sbo = (kGramKT / 8) * 128;
-            const uint32_t b_off = core_offset(kN * (int)half, 0, kGramKT);
-            int inited[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            static_assert(kHalfBytes == (kN / 8) * (kGramKT / 8) * 128, "B slices side by side along N");
             for (int t = 0; t < ntiles; ++t) {
                 const int b = t % kGramBufs;
                 wait1(&full[b], t);
@@ -220,7 +223,7 @@ k_gram_x(const double *__restrict__ G, int64_t rows, int64_t ldg, const int *__r
                 fence_after();
                 const uint32_t base = smem_addr(smem) + (uint32_t)b * kBufBytes;
                 for (int ks = 0; ks < kGramKT / 16; ++ks)
-                    issue_products(tmem, base, kSliceBytes, base + b_off, kSliceBytes, ks * 256, sbo, idesc, inited);
+                    issue_products(tmem, base, kSliceBytes, base + kBOff, kHalfBytes, ks * 256, sbo, t == 0 && ks == 0);
                 commit(&empty[b]);
             }
             if (ntiles > 0) wait1(&empty[(ntiles - 1) % kGramBufs], ntiles - 1);
@@ -363,8 +366,8 @@ k_update_x(double *__restrict__ X, int64_t rowsX, int64_t ldx, double *__restric
     __syncthreads();
     fence_after();
     const uint32_t tmem = tbase;
-    const uint32_t idesc = idesc_bf16(NNX, kN);
     const uint32_t sbo = (kUpdKT / 8) * 128;
+    static_assert(kBTile == (kUpdRows / 8) * (kUpdKT / 8) * 128, "B slices side by side along N");
 
     auto next_item = [&](int64_t from) -> int64_t {
         for (int64_t it = from; it < items; it += gridDim.x)
@@ -525,7 +528,7 @@ k_update_x(double *__restrict__ X, int64_t rowsX, int64_t ldx, double *__restric
         int64_t g = 0;
         while (it >= 0) {
             const UpdItem cur = describe(it);
-            int inited[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            (void)cur;
             for (int q = 0; q < kTiles; ++q, ++g) {
                 if (q == 0 && ii > 0) epilogue(prev, (ii - 1) & 1, g - 1);
                 const int b = (int)(g & 1);
@@ -535,7 +538,7 @@ k_update_x(double *__restrict__ X, int64_t rowsX, int64_t ldx, double *__restric
                         fence_after();
                         const uint32_t ab = smem_addr(As + b * kABuf), bb = smem_addr(Bs + b * kBBuf);
                         for (int ks = 0; ks < kUpdKT / 16; ++ks)
-                            issue_products(tmem, ab, kATile, bb, kBTile, ks * 256, sbo, idesc, inited);
+                            issue_products(tmem, ab, kATile, bb, kBTile, ks * 256, sbo, q == 0 && ks == 0);
                         commit(&empty[b]);
                     }
                 }
@@ -584,7 +587,7 @@ int precision_gram_ksplit(int64_t rows) { return (int)((rows + kGramK - 1) / kGr
 cudaError_t launch_gram_x(const double *G, int64_t rows, int64_t ldg, int npairs, const int *col0, double *part,
                           int *status, cudaStream_t st) {
     const int ksplit = precision_gram_ksplit(rows);
-    const size_t smem = (size_t)kGramBufs * kSlices * NNX * kGramKT * 2;
+    const size_t smem = (size_t)kGramBufs * kSlices * (NNX + kN) * kGramKT * 2;
     cudaError_t e = cudaFuncSetAttribute(k_gram_x, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_gram_x<<<npairs * ksplit * 2, kThrG, smem, st>>>(G, rows, ldg, col0, ksplit, part, status);
