@@ -94,18 +94,20 @@ __device__ __forceinline__ void read_accs(uint32_t tmem, int lane_base, int c0, 
 // partial A_P over rows [512 split, 512 split + 512) of the panel
 // P = [G_I G_J] (m x 128): A = P^T (128 x K, K-major), B = columns
 // [64 h, 64 h + 64) of the same tile, written a second time with the eight
-// slices side by side (the wide products of issue_products).  Each CTA splits
-// the whole 128-column tile itself (no shared memory is written across CTAs
-// and no cluster barrier is needed).  Warp-specialised
-// pipeline over 32-row tiles, kGramBufs in flight:
+// slices side by side (the wide products of issue_products).  The two CTAs
+// form a cluster: each splits only its own 64 columns (into its A and B
+// regions) and bulk-copies its A part into the peer's A region, so every
+// column is split once.  Warp-specialised pipeline over 32-row tiles,
+// kGramBufs in flight:
 //   - warps 1..16 wait until the products that last read a buffer are done
-//     (mbarrier `empty`), split the tile into it (its values loaded one tile
-//     ahead) and arrive on `full`;
+//     in both CTAs (mbarrier `empty`, one commit from each), split the own
+//     columns of the tile into it (values loaded one tile ahead), send the A
+//     part to the peer and arrive on `full` expecting the peer's A part;
 //   - warp 0, lane 0 waits on `full`, issues the tile's 24 products and
-//     commits them to `empty`.
+//     commits them to `empty` in both CTAs.
 // Every wait is bounded; after a failure each role still passes the same
 // barriers and the kernel reports HSVD_ERR_CUDA.
-__global__ void __launch_bounds__(kThrG, 1)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThrG, 1)
 k_gram_x(const double *__restrict__ G, int64_t rows, int64_t ldg, const int *__restrict__ col0, int ksplit,
          double *__restrict__ part, int *__restrict__ status) {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -119,14 +121,15 @@ k_gram_x(const double *__restrict__ G, int64_t rows, int64_t ldg, const int *__r
     __shared__ __align__(8) uint64_t full[kGramBufs], empty[kGramBufs];
     __shared__ uint32_t tbase;
     __shared__ int s_fail;
-    const uint32_t half = blockIdx.x & 1u;
+    const uint32_t half = cluster_rank(), peer = half ^ 1u;
     const int pair = (blockIdx.x >> 1) / ksplit, split = (blockIdx.x >> 1) % ksplit;
     const int64_t r0 = (int64_t)split * kGramK, r1 = min(rows, r0 + kGramK);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int cI = col0[2 * pair], cJ = col0[2 * pair + 1];
     auto colptr = [&](int c) { return G + (int64_t)(c < NNX / 2 ? cI + c : cJ + c - NNX / 2) * ldg; };
-    // column exponents over the split's rows (both CTAs of the pair: the same values)
-    for (int c = warp; c < NNX; c += kThrG / 32) {
+    cluster_sync();  // both CTAs run before either writes into the other
+    // exponents of the own columns over the split's rows, into both CTAs
+    for (int c = kN * (int)half + warp; c < kN * (int)half + kN; c += kThrG / 32) {
         const double *g = colptr(c);
         int e = -2000;
         int64_t r = r0 + lane;
@@ -139,18 +142,22 @@ k_gram_x(const double *__restrict__ G, int64_t rows, int64_t ldg, const int *__r
         }
         for (; r < r1; r += 32) e = max(e, exp_bound(g[r]));
         e = warp_max_i(e);
-        if (lane == 0) Ecol[c] = e < -1000 ? 0 : e;
+        if (lane == 0) {
+            e = e < -1000 ? 0 : e;
+            Ecol[c] = e;
+            st_cluster_s32(map_peer(smem_addr(&Ecol[c]), peer), e);
+        }
     }
     if (tid == 0) {
         s_fail = 0;
         for (int b = 0; b < kGramBufs; ++b) {
-            mbar_init(&full[b], 1);   // the splitters' arrival
-            mbar_init(&empty[b], 1);  // the products' commit
+            mbar_init(&full[b], 1);   // the splitters' arrival (expecting the peer's A part)
+            mbar_init(&empty[b], 2);  // the products' commits of both CTAs
         }
     }
     if (warp == 0) tmem_alloc(&tbase, kTmemCols);
     fence_before();
-    __syncthreads();
+    cluster_sync();  // exponents exchanged, barriers of both CTAs initialised
     fence_after();
     const uint32_t tmem = tbase;
     const int ntiles = (int)((r1 - r0 + kGramKT - 1) / kGramKT);
@@ -163,15 +170,15 @@ k_gram_x(const double *__restrict__ G, int64_t rows, int64_t ldg, const int *__r
         // a warp writes one 8 x 8 core matrix per step: lane -> column
         // (lane >> 2) of the group, rows 2 (lane & 3) and 2 (lane & 3) + 1
         const int pw = warp - 1, ptid = tid - 32;
-        const int cc = lane >> 2, kp = 2 * (lane & 3);
-        constexpr int kCoresPerWarp = (NNX / 8) * (kGramKT / 8) / kProdWarps;
-        static_assert(kCoresPerWarp * kProdWarps == (NNX / 8) * (kGramKT / 8), "Gram split mapping");
+        const int cc = lane >> 2, kp = 2 * (lane & 3), cbase = kN * (int)half;
+        constexpr int kCoresPerWarp = (kN / 8) * (kGramKT / 8) / kProdWarps;
+        static_assert(kCoresPerWarp * kProdWarps == (kN / 8) * (kGramKT / 8), "Gram split mapping");
         auto load_tile = [&](int t, double (&x)[kCoresPerWarp][2]) {
             const int64_t t0 = r0 + (int64_t)t * kGramKT;
 #pragma unroll
             for (int ci = 0; ci < kCoresPerWarp; ++ci) {
                 const int core = pw + ci * kProdWarps;
-                const int c = (core / (kGramKT / 8)) * 8 + cc, k = (core % (kGramKT / 8)) * 8 + kp;
+                const int c = cbase + (core / (kGramKT / 8)) * 8 + cc, k = (core % (kGramKT / 8)) * 8 + kp;
                 const double *g = colptr(c);
                 const int64_t row = t0 + k;
                 x[ci][0] = row < r1 ? g[row] : 0.0;
@@ -190,25 +197,28 @@ k_gram_x(const double *__restrict__ G, int64_t rows, int64_t ldg, const int *__r
 #pragma unroll
                 for (int ci = 0; ci < kCoresPerWarp; ++ci) {
                     const int core = pw + ci * kProdWarps;
-                    const int c = (core / (kGramKT / 8)) * 8 + cc, k = (core % (kGramKT / 8)) * 8 + kp;
+                    const int c = cbase + (core / (kGramKT / 8)) * 8 + cc, k = (core % (kGramKT / 8)) * 8 + kp;
                     const long long w0 = digit_word(cur[ci][0], Ecol[c]), w1 = digit_word(cur[ci][1], Ecol[c]);
-                    const uint32_t off = core_offset(c, k, kGramKT);
+                    const uint32_t off = core_offset(c, k, kGramKT), offb = kBOff + core_offset(c - cbase, k, kGramKT);
                     uint32_t sw[kSlices];
                     slice_pairs8(w0, w1, sw);
 #pragma unroll
-                    for (int sl = 0; sl < kSlices; ++sl)
+                    for (int sl = 0; sl < kSlices; ++sl) {
                         *reinterpret_cast<uint32_t *>(buf + off + (uint32_t)sl * kSliceBytes) = sw[sl];
-                    if ((c >> 6) == (int)half) {  // this CTA's columns again, for B (warp-uniform)
-                        const uint32_t offb = kBOff + core_offset(c - kN * (int)half, k, kGramKT);
-#pragma unroll
-                        for (int sl = 0; sl < kSlices; ++sl)
-                            *reinterpret_cast<uint32_t *>(buf + offb + (uint32_t)sl * kHalfBytes) = sw[sl];
+                        *reinterpret_cast<uint32_t *>(buf + offb + (uint32_t)sl * kHalfBytes) = sw[sl];
                     }
                 }
             }
             fence_proxy_async();
             bar_named(1, kProd);
-            if (ptid == 0 && !s_fail) mbar_arrive(&full[b]);
+            if (ptid == 0 && !s_fail) {
+                // the own columns of every A slice (4 KB each) into the peer's buffer
+                const uint32_t lbuf = smem_addr(smem) + (uint32_t)b * kBufBytes + (uint32_t)half * kHalfBytes;
+                const uint32_t pbuf = map_peer(lbuf, peer), pfull = map_peer(smem_addr(&full[b]), peer);
+                for (int sl = 0; sl < kSlices; ++sl)
+                    bulk_s2peer(pbuf + (uint32_t)sl * kSliceBytes, lbuf + (uint32_t)sl * kSliceBytes, kHalfBytes, pfull);
+                mbar_expect_tx(&full[b], kSlices * kHalfBytes);  // own arrival; the peer's part is due
+            }
             if (t + 1 < ntiles) load_tile(t + 1, cur);
         }
     } else {
@@ -224,7 +234,7 @@ k_gram_x(const double *__restrict__ G, int64_t rows, int64_t ldg, const int *__r
                 const uint32_t base = smem_addr(smem) + (uint32_t)b * kBufBytes;
                 for (int ks = 0; ks < kGramKT / 16; ++ks)
                     issue_products(tmem, base, kSliceBytes, base + kBOff, kHalfBytes, ks * 256, sbo, t == 0 && ks == 0);
-                commit(&empty[b]);
+                commit_multicast(&empty[b], 0x3);
             }
             if (ntiles > 0) wait1(&empty[(ntiles - 1) % kGramBufs], ntiles - 1);
         }
@@ -256,7 +266,7 @@ k_gram_x(const double *__restrict__ G, int64_t rows, int64_t ldg, const int *__r
         atomicExch(status, HSVD_ERR_CUDA);
     }
     fence_before();
-    __syncthreads();
+    cluster_sync();  // no CTA leaves while its peer may still write into it
     fence_after();
     if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }

@@ -184,6 +184,25 @@ __device__ __forceinline__ void st_cluster_s32(uint32_t caddr, int v) {
 __device__ __forceinline__ void cluster_sync() {
     asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
+// Bulk copy from this CTA's shared memory into another CTA of the cluster
+// (dst and mbar are shared::cluster addresses from map_peer); the bytes are
+// counted on the destination's mbarrier.  16-byte aligned, size a multiple of 16.
+__device__ __forceinline__ void bulk_s2peer(uint32_t dst_cluster, uint32_t src_cta, uint32_t bytes,
+                                            uint32_t mbar_cluster) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            dst_cluster),
+        "r"(src_cta), "r"(bytes), "r"(mbar_cluster)
+        : "memory");
+}
+// Commit of this thread's earlier products to the mbarrier at the same offset
+// in every CTA of cta_mask (one arrival each).
+__device__ __forceinline__ void commit_multicast(uint64_t *mbar, uint16_t cta_mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_addr(mbar)),
+        "h"(cta_mask));
+}
 __device__ __forceinline__ void fence_proxy_async_cluster() {
     asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
 }
