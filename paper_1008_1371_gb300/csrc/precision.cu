@@ -31,7 +31,7 @@ using namespace tc;
 
 constexpr int NNX = 128;             // pivot block order 2b
 constexpr int kThrX = 256;           // eight warps: two per TMEM lane quarter
-constexpr int kThrU = 512;           // update: sixteen warps, four per TMEM lane quarter
+constexpr int kThrU = 544;           // update: the products warp and sixteen producer warps
 constexpr int kThrG = 544;           // Gram: the products warp and sixteen splitting warps
 constexpr int kGramK = 512;          // rows of G per Gram CTA pair (exactness window)
 constexpr int kGramKT = 32;          // rows per shared-memory tile of the Gram
@@ -73,6 +73,20 @@ __device__ __forceinline__ void issue_products(uint32_t tmem, uint32_t a_base, u
 }
 
 __device__ __forceinline__ void bar_named(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+
+// this thread's lane and 4 columns [c0, c0+4) of all eight accumulators
+__device__ __forceinline__ void read_accs4(uint32_t tmem, int lane_base, int c0, float (&v)[8][4]) {
+    uint32_t r[8][4];
+#pragma unroll
+    for (int acc = 0; acc < 8; ++acc) tmem_ld4_raw(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(acc * kN + c0), r[acc]);
+    tmem_wait_ld();
+#pragma unroll
+    for (int acc = 0; acc < 8; ++acc) {
+        reg_dep4(r[acc]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[acc][j] = __uint_as_float(r[acc][j]);
+    }
+}
 
 // this thread's lane and 8 columns [c0, c0+8) of all eight accumulators: the
 // eight loads are issued back to back and waited for once
@@ -324,16 +338,17 @@ k_wprep_x(const double *__restrict__ Wp, const int *__restrict__ dexp, const int
 // 128 columns), split per row after balancing.  D is 128 (columns j) x 64 (rows).
 // Warp-specialised pipeline over the flat sequence of k-quarter tiles of the
 // CTA's items, A and B tiles double-buffered:
-//   - warps 1..15 (producers) wait until the products that last read a
+//   - warps 1..16 (producers) wait until the products that last read a
 //     buffer are done (mbarrier `empty`), start the bulk copy of the A tile
-//     and split the B tile, then arrive on `full` (two arrivals: the copy's
-//     expect-tx and the split);
-//   - warp 0, lane 0 waits on `full`, issues the 72 products of the tile and
+//     and split the B tile (its values loaded while the previous tile was
+//     split), then arrive on `full` (two arrivals: the copy's expect-tx and
+//     the split); the next item's block is prefetched into L2 one item ahead;
+//   - warp 0, lane 0 waits on `full`, issues the 24 products of the tile and
 //     commits them to `empty`;
-//   - after the producers have filled the first tile of item i + 1, all 16
-//     warps form item i's epilogue (TMEM -> FP64), then warp 0 issues item
-//     i + 1's products: the eight accumulators take all of TMEM, so only the
-//     epilogue waits for the tensor cores.
+//   - after the producers have filled the first tile of item i + 1, warps
+//     1..16 form item i's epilogue (TMEM -> FP64) while warp 0 waits, then
+//     warp 0 issues item i + 1's products: the eight accumulators take all of
+//     TMEM, so only the epilogue waits for the tensor cores.
 // Every wait is bounded; after a failure each role still passes the same
 // barriers (no deadlock) and the kernel reports HSVD_ERR_CUDA.
 struct UpdItem {
@@ -402,26 +417,26 @@ k_update_x(double *__restrict__ X, int64_t rowsX, int64_t ldx, double *__restric
         if (!s_fail && !mbar_wait(mb, (uint32_t)((use >> 1) & 1), kWaitIter)) s_fail = 1;
     };
 
-    // item i's epilogue, all 512 threads: lane j = output column, warp group
-    // h2 = rows [16 h2, 16 h2 + 16); glast = the item's last tile.  (Staging
-    // the tile through shared memory for coalesced stores measured slower.)
+    // item i's epilogue, warps 1..16: lane j = output column, the four warps
+    // of a TMEM lane quarter take rows [16 h2, 16 h2 + 16); glast = the item's
+    // last tile.  Warp 0 passes the barriers only.
     auto epilogue = [&](const UpdItem &d, int slot, int64_t glast) {
         if (tid == 0) wait1(&empty[glast & 1], glast);
         bar_named(2, kThrU);
         fence_after();
-        if (!s_fail) {
-            const int qd = warp & 3, j = 32 * qd + lane, h2 = warp >> 2;
+        if (!s_fail && warp > 0) {
+            const int qd = warp & 3, j = 32 * qd + lane, h2 = (warp - 1) >> 2;
             const int jj = j < NNX / 2 ? d.cI + j : d.cJ + j - NNX / 2;
-            constexpr int kCols = kN / (kThrU / 128);
+            constexpr int kCols = kN / 4;
             // a thread's values are consecutive rows of one column: stored two
             // at a time (16 B) where the column start allows it
             double *col = d.M + (int64_t)jj * d.ld;
             const bool vec = ((reinterpret_cast<uintptr_t>(col) & 15u) == 0);
-            for (int c0 = kCols * h2; c0 < kCols * h2 + kCols; c0 += 8) {
-                float v[8][8];
-                read_accs(tmem, 32 * qd, c0, v);
+            for (int c0 = kCols * h2; c0 < kCols * h2 + kCols; c0 += 4) {
+                float v[8][4];
+                read_accs4(tmem, 32 * qd, c0, v);
 #pragma unroll
-                for (int t = 0; t < 8; t += 2) {
+                for (int t = 0; t < 4; t += 2) {
                     const int i = c0 + t;
                     const int64_t row = d.r0 + i;
                     float d0[8], d1[8];
@@ -445,20 +460,53 @@ k_update_x(double *__restrict__ X, int64_t rowsX, int64_t ldx, double *__restric
         bar_named(2, kThrU);
         fence_after();
     };
+    auto epilogue_barriers = [&](int64_t glast) {
+        if (tid == 0) wait1(&empty[glast & 1], glast);
+        bar_named(2, kThrU);
+        fence_after();
+        fence_before();
+        bar_named(2, kThrU);
+        fence_after();
+    };
 
     int64_t g_end = -1;  // last tile of the last item
     if (warp > 0) {
         // ------------------------------------------------ producers
-        const int ptid = tid - 32, pwarp = warp - 1;
+        const int ptid = tid - 32, pw = warp - 1;
         const int rr = lane >> 2, kp = 2 * (lane & 3);
-        int64_t it = next_item(blockIdx.x);
+        // a warp splits two 8 x 8 core matrices of a tile: lane -> row rr of
+        // the core, k pair kp
+        constexpr int kCoresPerWarp = (kUpdRows / 8) * (kUpdKT / 8) / (kProd / 32);
+        static_assert(kCoresPerWarp * (kProd / 32) == (kUpdRows / 8) * (kUpdKT / 8), "update split mapping");
+        auto colof = [](const UpdItem &d, int k) { return k < NNX / 2 ? d.cI + k : d.cJ + k - NNX / 2; };
+        auto load_tile = [&](const UpdItem &d, int q, double (&x)[kCoresPerWarp][2]) {
+#pragma unroll
+            for (int ci = 0; ci < kCoresPerWarp; ++ci) {
+                const int core = pw + ci * (kProd / 32);
+                const int i = (core / (kUpdKT / 8)) * 8 + rr, k = q * kUpdKT + (core % (kUpdKT / 8)) * 8 + kp;
+                const int64_t row = d.r0 + i;
+                x[ci][0] = row < d.rows ? d.M[row + (int64_t)colof(d, k) * d.ld] : 0.0;
+                x[ci][1] = row < d.rows ? d.M[row + (int64_t)colof(d, k + 1) * d.ld] : 0.0;
+            }
+        };
+        // the item's 64 x 128 block into L2: 128 columns x four 128-byte lines
+        auto prefetch_item = [&](const UpdItem &d) {
+            const int k = ptid >> 2;
+            const int64_t row = d.r0 + (ptid & 3) * 16;
+            if (row < d.rows) prefetch_l2(d.M + row + (int64_t)colof(d, k) * d.ld);
+        };
+        int64_t it = next_item(blockIdx.x), itp = -1;
         int ii = 0;
-        UpdItem cur{}, prev{};
         int64_t g = 0;
+        double xv[kCoresPerWarp][2], xn[kCoresPerWarp][2];
+        if (it >= 0) load_tile(describe(it), 0, xv);
         while (it >= 0) {
-            cur = describe(it);
             const int slot = ii & 1;
-            // exponents of the item (producers only, barrier 1)
+            const int64_t itn = next_item(it + gridDim.x);
+            if (itn >= 0) prefetch_item(describe(itn));
+            const UpdItem cur = describe(it);
+            // exponents of the item (producers only, barrier 1): one row
+            // segment of 16 columns per thread
             for (int k = ptid; k < NNX; k += kProd) {
                 dk[slot][k] = cur.which == 0 ? dexp[(size_t)cur.pair * NNX + k] : 0;
                 Fcol[slot][k] = wexp[((size_t)cur.pair * 2 + cur.which) * NNX + k];
@@ -466,30 +514,28 @@ k_update_x(double *__restrict__ X, int64_t rowsX, int64_t ldx, double *__restric
             if (ptid < kUpdRows) Erow[slot][ptid] = -2000;
             bar_named(1, kProd);
             {
-                constexpr int kParts = 8, kPer = NNX / kParts;
-                for (int e = ptid; e < kUpdRows * kParts; e += kProd) {
-                    const int i = e % kUpdRows, part = e / kUpdRows;
-                    const int64_t row = cur.r0 + i;
-                    int ex = -2000;
-                    if (row < cur.rows) {
-                        double x[kPer];
+                constexpr int kParts = kProd / kUpdRows, kPer = NNX / kParts;
+                static_assert(kParts * kUpdRows == kProd && kPer * kParts == NNX, "one segment per thread");
+                const int i = ptid % kUpdRows, part = ptid / kUpdRows;
+                const int64_t row = cur.r0 + i;
+                int ex = -2000;
+                if (row < cur.rows) {
+                    double x[kPer];
 #pragma unroll
-                        for (int u = 0; u < kPer; ++u) {
-                            const int k = part * kPer + u;
-                            const int col = k < NNX / 2 ? cur.cI + k : cur.cJ + k - NNX / 2;
-                            x[u] = cur.M[row + (int64_t)col * cur.ld];
-                        }
+                    for (int u = 0; u < kPer; ++u) x[u] = cur.M[row + (int64_t)colof(cur, part * kPer + u) * cur.ld];
 #pragma unroll
-                        for (int u = 0; u < kPer; ++u) ex = max(ex, exp_bound(x[u]) - dk[slot][part * kPer + u]);
-                    }
-                    atomicMax(&Erow[slot][i], ex);
+                    for (int u = 0; u < kPer; ++u) ex = max(ex, exp_bound(x[u]) - dk[slot][part * kPer + u]);
                 }
+                atomicMax(&Erow[slot][i], ex);
             }
             bar_named(1, kProd);
             if (ptid < kUpdRows && Erow[slot][ptid] < -1000) Erow[slot][ptid] = 0;
             bar_named(1, kProd);
             for (int q = 0; q < kTiles; ++q, ++g) {
                 const int b = (int)(g & 1);
+                // the values of the next tile (this item's, or the next item's first)
+                if (q + 1 < kTiles) load_tile(cur, q + 1, xn);
+                else if (itn >= 0) load_tile(describe(itn), 0, xn);
                 // the products that last read buffer b (tile g - 2) are done
                 if (ptid == 0) {
                     if (g >= 2) wait1(&empty[b], g - 2);
@@ -502,45 +548,45 @@ k_update_x(double *__restrict__ X, int64_t rowsX, int64_t ldx, double *__restric
                 }
                 bar_named(1, kProd);
                 unsigned char *Bb = Bs + b * kBBuf;
-                for (int core = pwarp; core < (kUpdRows / 8) * (kUpdKT / 8); core += kProd / 32) {
+#pragma unroll
+                for (int ci = 0; ci < kCoresPerWarp; ++ci) {
+                    const int core = pw + ci * (kProd / 32);
                     const int i = (core / (kUpdKT / 8)) * 8 + rr, kk = (core % (kUpdKT / 8)) * 8 + kp;
                     const int k = q * kUpdKT + kk;
-                    const int64_t row = cur.r0 + i;
-                    const int c0 = k < NNX / 2 ? cur.cI + k : cur.cJ + k - NNX / 2;
-                    const int c1 = k + 1 < NNX / 2 ? cur.cI + k + 1 : cur.cJ + k + 1 - NNX / 2;
-                    const double x0 = row < cur.rows ? cur.M[row + (int64_t)c0 * cur.ld] : 0.0;
-                    const double x1 = row < cur.rows ? cur.M[row + (int64_t)c1 * cur.ld] : 0.0;
-                    const long long w0 = digit_word(x0, Erow[slot][i] + dk[slot][k]);
-                    const long long w1 = digit_word(x1, Erow[slot][i] + dk[slot][k + 1]);
+                    const long long w0 = digit_word(xv[ci][0], Erow[slot][i] + dk[slot][k]);
+                    const long long w1 = digit_word(xv[ci][1], Erow[slot][i] + dk[slot][k + 1]);
                     const uint32_t off = core_offset(i, kk, kUpdKT);
                     uint32_t sw[kSlices];
                     slice_pairs8(w0, w1, sw);
 #pragma unroll
                     for (int sl = 0; sl < kSlices; ++sl) *reinterpret_cast<uint32_t *>(Bb + sl * kBTile + off) = sw[sl];
                 }
+#pragma unroll
+                for (int ci = 0; ci < kCoresPerWarp; ++ci) {
+                    xv[ci][0] = xn[ci][0];
+                    xv[ci][1] = xn[ci][1];
+                }
                 fence_proxy_async();
                 bar_named(1, kProd);
                 if (ptid == 0 && !s_fail) mbar_arrive(&full[b]);
                 // item ii - 1's epilogue once item ii's first tile is on its way
-                if (q == 0 && ii > 0) epilogue(prev, (ii - 1) & 1, g - 1);
+                if (q == 0 && ii > 0) epilogue(describe(itp), (ii - 1) & 1, g - 1);
             }
-            prev = cur;
+            itp = it;
             ++ii;
-            it = next_item(it + gridDim.x);
+            it = itn;
         }
-        if (ii > 0) epilogue(prev, (ii - 1) & 1, g - 1);
+        if (ii > 0) epilogue(describe(itp), (ii - 1) & 1, g - 1);
         g_end = g - 1;
     } else {
         // ------------------------------------------------ warp 0: products
+        // (warp 0 passes the epilogue's barriers: TMEM is reused after it)
         int64_t it = next_item(blockIdx.x);
         int ii = 0;
-        UpdItem prev{};
         int64_t g = 0;
         while (it >= 0) {
-            const UpdItem cur = describe(it);
-            (void)cur;
             for (int q = 0; q < kTiles; ++q, ++g) {
-                if (q == 0 && ii > 0) epilogue(prev, (ii - 1) & 1, g - 1);
+                if (q == 0 && ii > 0) epilogue_barriers(g - 1);
                 const int b = (int)(g & 1);
                 if (lane == 0) {
                     wait1(&full[b], g);
@@ -554,11 +600,10 @@ k_update_x(double *__restrict__ X, int64_t rowsX, int64_t ldx, double *__restric
                 }
                 __syncwarp();
             }
-            prev = cur;
             ++ii;
             it = next_item(it + gridDim.x);
         }
-        if (ii > 0) epilogue(prev, (ii - 1) & 1, g - 1);
+        if (ii > 0) epilogue_barriers(g - 1);
         g_end = g - 1;
     }
     __syncthreads();
