@@ -479,15 +479,18 @@ k_update_x(double *__restrict__ X, int64_t rowsX, int64_t ldx, double *__restric
         constexpr int kCoresPerWarp = (kUpdRows / 8) * (kUpdKT / 8) / (kProd / 32);
         static_assert(kCoresPerWarp * (kProd / 32) == (kUpdRows / 8) * (kUpdKT / 8), "update split mapping");
         auto colof = [](const UpdItem &d, int k) { return k < NNX / 2 ? d.cI + k : d.cJ + k - NNX / 2; };
-        auto load_tile = [&](const UpdItem &d, int q, double (&x)[kCoresPerWarp][2]) {
+        // this lane's 16 values of an item: tile q, core ci, elements k, k + 1
+        auto load_item = [&](const UpdItem &d, double (&x)[kTiles][kCoresPerWarp][2]) {
 #pragma unroll
-            for (int ci = 0; ci < kCoresPerWarp; ++ci) {
-                const int core = pw + ci * (kProd / 32);
-                const int i = (core / (kUpdKT / 8)) * 8 + rr, k = q * kUpdKT + (core % (kUpdKT / 8)) * 8 + kp;
-                const int64_t row = d.r0 + i;
-                x[ci][0] = row < d.rows ? d.M[row + (int64_t)colof(d, k) * d.ld] : 0.0;
-                x[ci][1] = row < d.rows ? d.M[row + (int64_t)colof(d, k + 1) * d.ld] : 0.0;
-            }
+            for (int q = 0; q < kTiles; ++q)
+#pragma unroll
+                for (int ci = 0; ci < kCoresPerWarp; ++ci) {
+                    const int core = pw + ci * (kProd / 32);
+                    const int i = (core / (kUpdKT / 8)) * 8 + rr, k = q * kUpdKT + (core % (kUpdKT / 8)) * 8 + kp;
+                    const int64_t row = d.r0 + i;
+                    x[q][ci][0] = row < d.rows ? d.M[row + (int64_t)colof(d, k) * d.ld] : 0.0;
+                    x[q][ci][1] = row < d.rows ? d.M[row + (int64_t)colof(d, k + 1) * d.ld] : 0.0;
+                }
         };
         // the item's 64 x 128 block into L2: 128 columns x four 128-byte lines
         auto prefetch_item = [&](const UpdItem &d) {
@@ -498,44 +501,43 @@ k_update_x(double *__restrict__ X, int64_t rowsX, int64_t ldx, double *__restric
         int64_t it = next_item(blockIdx.x), itp = -1;
         int ii = 0;
         int64_t g = 0;
-        double xv[kCoresPerWarp][2], xn[kCoresPerWarp][2];
-        if (it >= 0) load_tile(describe(it), 0, xv);
         while (it >= 0) {
             const int slot = ii & 1;
             const int64_t itn = next_item(it + gridDim.x);
-            if (itn >= 0) prefetch_item(describe(itn));
             const UpdItem cur = describe(it);
-            // exponents of the item (producers only, barrier 1): one row
-            // segment of 16 columns per thread
+            double xv[kTiles][kCoresPerWarp][2];
+            load_item(cur, xv);
+            if (itn >= 0) prefetch_item(describe(itn));
             for (int k = ptid; k < NNX; k += kProd) {
                 dk[slot][k] = cur.which == 0 ? dexp[(size_t)cur.pair * NNX + k] : 0;
                 Fcol[slot][k] = wexp[((size_t)cur.pair * 2 + cur.which) * NNX + k];
             }
             if (ptid < kUpdRows) Erow[slot][ptid] = -2000;
             bar_named(1, kProd);
-            {
-                constexpr int kParts = kProd / kUpdRows, kPer = NNX / kParts;
-                static_assert(kParts * kUpdRows == kProd && kPer * kParts == NNX, "one segment per thread");
-                const int i = ptid % kUpdRows, part = ptid / kUpdRows;
-                const int64_t row = cur.r0 + i;
+            // row exponents from the loaded values: a lane holds 8 columns of
+            // each of its two rows; the four lanes of a row group (same rr)
+            // combine by shuffles, and four warps per row by shared atomics
+#pragma unroll
+            for (int ci = 0; ci < kCoresPerWarp; ++ci) {
+                const int core = pw + ci * (kProd / 32);
+                const int i = (core / (kUpdKT / 8)) * 8 + rr;
                 int ex = -2000;
-                if (row < cur.rows) {
-                    double x[kPer];
 #pragma unroll
-                    for (int u = 0; u < kPer; ++u) x[u] = cur.M[row + (int64_t)colof(cur, part * kPer + u) * cur.ld];
-#pragma unroll
-                    for (int u = 0; u < kPer; ++u) ex = max(ex, exp_bound(x[u]) - dk[slot][part * kPer + u]);
+                for (int q = 0; q < kTiles; ++q) {
+                    const int k = q * kUpdKT + (core % (kUpdKT / 8)) * 8 + kp;
+                    ex = max(ex, exp_bound(xv[q][ci][0]) - dk[slot][k]);
+                    ex = max(ex, exp_bound(xv[q][ci][1]) - dk[slot][k + 1]);
                 }
-                atomicMax(&Erow[slot][i], ex);
+                ex = max(ex, __shfl_xor_sync(0xffffffffu, ex, 1));
+                ex = max(ex, __shfl_xor_sync(0xffffffffu, ex, 2));
+                if ((lane & 3) == 0 && cur.r0 + i < cur.rows) atomicMax(&Erow[slot][i], ex);
             }
             bar_named(1, kProd);
             if (ptid < kUpdRows && Erow[slot][ptid] < -1000) Erow[slot][ptid] = 0;
             bar_named(1, kProd);
+#pragma unroll
             for (int q = 0; q < kTiles; ++q, ++g) {
                 const int b = (int)(g & 1);
-                // the values of the next tile (this item's, or the next item's first)
-                if (q + 1 < kTiles) load_tile(cur, q + 1, xn);
-                else if (itn >= 0) load_tile(describe(itn), 0, xn);
                 // the products that last read buffer b (tile g - 2) are done
                 if (ptid == 0) {
                     if (g >= 2) wait1(&empty[b], g - 2);
@@ -553,18 +555,13 @@ k_update_x(double *__restrict__ X, int64_t rowsX, int64_t ldx, double *__restric
                     const int core = pw + ci * (kProd / 32);
                     const int i = (core / (kUpdKT / 8)) * 8 + rr, kk = (core % (kUpdKT / 8)) * 8 + kp;
                     const int k = q * kUpdKT + kk;
-                    const long long w0 = digit_word(xv[ci][0], Erow[slot][i] + dk[slot][k]);
-                    const long long w1 = digit_word(xv[ci][1], Erow[slot][i] + dk[slot][k + 1]);
+                    const long long w0 = digit_word(xv[q][ci][0], Erow[slot][i] + dk[slot][k]);
+                    const long long w1 = digit_word(xv[q][ci][1], Erow[slot][i] + dk[slot][k + 1]);
                     const uint32_t off = core_offset(i, kk, kUpdKT);
                     uint32_t sw[kSlices];
                     slice_pairs8(w0, w1, sw);
 #pragma unroll
                     for (int sl = 0; sl < kSlices; ++sl) *reinterpret_cast<uint32_t *>(Bb + sl * kBTile + off) = sw[sl];
-                }
-#pragma unroll
-                for (int ci = 0; ci < kCoresPerWarp; ++ci) {
-                    xv[ci][0] = xn[ci][0];
-                    xv[ci][1] = xn[ci][1];
                 }
                 fence_proxy_async();
                 bar_named(1, kProd);
