@@ -47,8 +47,9 @@ METRIC = "HSVD time & eff. TFLOP/s at sigma rel-err <= 1e-12: new forms vs plain
 PROFILED_TRAFFIC = {
     ("graded1024", "fp64", "k_update<64>"): (17.317e6, "profiles/kernels_graded1024_fp64.md"),
     ("graded1024", "fp64", "k_gram<32>"): (8.396e6, "profiles/kernels_graded1024_fp64.md"),
-    ("haar4096", "bf16x8", "k_update_x"): (499.55e6, "profiles/kernels_haar4096_bf16x8.md"),
-    ("haar4096", "bf16x8", "k_gram_x"): (149.18e6, "profiles/kernels_haar4096_bf16x8.md"),
+    ("haar4096", "bf16x8", "k_update_x"): (498.72e6, "profiles/kernels_haar4096_bf16x8.md"),
+    ("haar4096", "bf16x8", "k_gram_x"): (148.40e6, "profiles/kernels_haar4096_bf16x8.md"),
+    ("haar4096", "bf16x8", "k_solve_cross<128,8>"): (18.96e6, "profiles/kernels_haar4096_bf16x8.md"),
 }
 # FP64 DFMA peak derived from the unit counts and the maximum clock (no FP64
 # figure in the measured peaks): 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz
@@ -115,6 +116,8 @@ def parse():
                          "agreement and the invariants of Eq. 1.1")
     ap.add_argument("--count", type=int, default=BATCH_COUNT, help="batch10k: number of factors")
     ap.add_argument("--group-width", type=int, default=0, help="batch10k: 0 autotunes, else 256/512/1024")
+    ap.add_argument("--cta-threads", type=int, default=0, choices=[0, 512, 1024],
+                    help="batch10k: threads a CTA of the persistent kernel (0: 1024)")
     ap.add_argument("--block", type=int, default=0, help="block width (0: the workload's)")
     ap.add_argument("--tstop", type=float, default=0.0,
                     help="tangent-threshold early stop (Sec. 2): 0 off, negative = the paper's T_eps = 2^-27; "
@@ -453,7 +456,7 @@ def batched_setup(api, dev, count, seed):
 
 
 def measure_batched(api, dev, count, steps, warmup, group_width, loop_count, rank=0, world=1, with_e2e=True,
-                    with_cpu=True, clocks=False):
+                    with_cpu=True, clocks=False, cta_threads=0):
     """The batched form on `count` factors: `warmup` + `steps` timed
     persistent launches (CUDA events, L2 flushed between steps), a measured
     loop of single hsvd_solve calls on an evenly spread sample of
@@ -464,7 +467,7 @@ def measure_batched(api, dev, count, steps, warmup, group_width, loop_count, ran
 
     B = batched_setup(api, dev, count, 4 + rank)
     facs, ms_, ns_ = B["facs"], B["ms"], B["ns"]
-    opts = api.make_batch_opts(max_sweeps=30, group_width=group_width)
+    opts = api.make_batch_opts(max_sweeps=30, group_width=group_width, cta_threads=cta_threads)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -606,7 +609,8 @@ def run_batched(args):
         dist.barrier()
     count = args.count
     res = measure_batched(api, dev, count, args.steps, args.warmup, args.group_width, args.loop_count, rank, world,
-                          with_e2e=not args.no_e2e, with_cpu=not args.no_cpu_baseline, clocks=True)
+                          with_e2e=not args.no_e2e, with_cpu=not args.no_cpu_baseline, clocks=True,
+                          cta_threads=args.cta_threads)
     value = world * res["eff_flops"] / (res["ms"] * 1e-3) / 1e12
     if rank == 0:
         line = {
@@ -615,6 +619,7 @@ def run_batched(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOADS["batch10k"][1].replace("10000", str(count)), "count": count,
                        "form": "batched", "group_width": args.group_width or "autotuned",
+                       "cta_threads": args.cta_threads or 1024,
                        "method": "pointwise per factor, diagonal sorting", "tol": "n 2^-53 per factor",
                        "max_sweeps_run": res["max_sweeps_run"],
                        "l2": "flushed (256 MB write) between steps; inputs 2.6 GB > L2",
@@ -1054,6 +1059,9 @@ def run_blocked(args):
             "accuracy": accuracy, "forms_vs_plain": forms_vs_plain,
             "learned_vs_plain": vs_plain, "tstop_vs_plain": tstop_vs_plain,
             "gpu_launches": int(sum(i.kernel_launches for i in infos)),
+            # host wall time inside each timed solve spent capturing and
+            # instantiating its sweep graph (part of ms_per_step)
+            "host_graph_ms_per_step": sum(getattr(i, "ms_host_graph", 0.0) for i in infos) / len(infos),
             "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk.summary(),
         }
         # the timed form's own sigma decides the exit status; the comparison

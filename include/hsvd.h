@@ -175,6 +175,9 @@ typedef struct hsvd_info {
     int stop_rule;        /* HSVD_STOP_*: which rule ended the iteration               */
     int shortened;        /* 1: a tall factor was shortened by a QR first, 2: a wide
                              one by the hyperbolic QR of its transpose              */
+    double ms_host_graph; /* blocked method: host wall time spent capturing and
+                             instantiating sweep graphs (one per call, plus one per
+                             masked sweep of the learned form)                      */
 } hsvd_info;
 
 /* Fills *opts with the defaults (tol = n 2^-53 at call time, 30 sweeps, auto
@@ -392,7 +395,11 @@ typedef struct hsvd_batch_opts {
                         that width for every factor                                 */
     int use_graph;   /* nonzero (default): the launch is captured as a CUDA graph  */
     double tstop;    /* tangent threshold of the early stop, as hsvd_opts.tstop    */
-    int reserved[2]; /* must be zero                                                */
+    int cta_threads; /* 0 or 1024 (default): CTAs of 1024 threads (groups of 1024,
+                        512, 256); 512: CTAs of 512 threads with twice the
+                        registers a thread (groups of 512, 256; group_width must
+                        not exceed it)                                              */
+    int reserved;    /* must be zero                                                */
 } hsvd_batch_opts;
 
 typedef struct hsvd_batch_info {
@@ -408,6 +415,7 @@ typedef struct hsvd_batch_info {
     double ms_kernel;     /* CUDA-event time of the batched launch                 */
     double ms_tune;       /* CUDA-event time of the autotuner's sample runs        */
     int64_t tangent_stops; /* factors whose iteration ended at the tangent threshold */
+    int cta_threads;      /* threads of the launch's CTAs                           */
 } hsvd_batch_info;
 
 /* Fills *opts with the defaults above. */

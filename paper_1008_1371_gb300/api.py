@@ -71,18 +71,18 @@ class HsvdInfo(ctypes.Structure):
                 ("rotations", _i64), ("pair_updates", _i64), ("kernel_launches", _i64),
                 ("ms_gram", _dbl), ("ms_solve", _dbl), ("ms_update", _dbl), ("ms_other", _dbl),
                 ("pair_visits", _i64), ("masked_sweeps", _int), ("judge_sweeps", _int), ("trace_rows", _i64),
-                ("stop_rule", _int), ("shortened", _int)]
+                ("stop_rule", _int), ("shortened", _int), ("ms_host_graph", _dbl)]
 
 
 class HsvdBatchOpts(ctypes.Structure):
     _fields_ = [("tol", _dbl), ("max_sweeps", _int), ("sort", _int), ("group_width", _int), ("use_graph", _int),
-                ("tstop", _dbl), ("reserved", _int * 2)]
+                ("tstop", _dbl), ("cta_threads", _int), ("reserved", _int)]
 
 
 class HsvdBatchInfo(ctypes.Structure):
     _fields_ = [("grid", _int), ("tuned", _int), ("bucket_width", _int * 5), ("max_sweeps_run", _int),
                 ("rotations", _i64), ("kernel_launches", _i64), ("resident", _i64 * 3), ("ms_kernel", _dbl),
-                ("ms_tune", _dbl), ("tangent_stops", _i64)]
+                ("ms_tune", _dbl), ("tangent_stops", _i64), ("cta_threads", _int)]
 
 
 class HsvdError(RuntimeError):
@@ -244,6 +244,7 @@ class HsvdResult:
     stop_rule: int = HSVD_STOP_NONE
     shortened: int = 0
     jout: Optional[torch.Tensor] = None  # wide factor: the m signs of the result (lambda = sigma^2 jout)
+    ms_host_graph: float = 0.0  # host time capturing and instantiating sweep graphs
 
 
 HSVD_SORT_AUTO = -1
@@ -335,7 +336,7 @@ def hsvd_solve_ex(G, J, opts=None, compute_u=True, compute_v=True, stream=None, 
     return HsvdResult(sigma, U, V, info.sweeps, st, info.method, info.block_w, info.rotations, info.pair_updates,
                       info.kernel_launches, info.ms_gram, info.ms_solve, info.ms_update, info.ms_other,
                       info.pair_visits, info.masked_sweeps, info.judge_sweeps, info.trace_rows, info.stop_rule,
-                      info.shortened, jout)
+                      info.shortened, jout, info.ms_host_graph)
 
 
 def hsvd_solve(G, J, tol=0.0, max_sweeps=30, compute_u=True, compute_v=True, stream=None, check=True):
@@ -526,9 +527,12 @@ class HsvdBatchResult:
     info: HsvdBatchInfo
 
 
-def make_batch_opts(tol=0.0, max_sweeps=30, sort=True, group_width=0, use_graph=True, tstop=0.0):
+def make_batch_opts(tol=0.0, max_sweeps=30, sort=True, group_width=0, use_graph=True, tstop=0.0, cta_threads=0):
+    """Batched-form options; ``cta_threads`` 512 selects the kernel with 512
+    threads a CTA (twice the registers a thread), 0 the default 1024."""
     o = HsvdBatchOpts()
     lib().hsvd_default_batch_opts(ctypes.byref(o))
+    o.cta_threads = int(cta_threads)
     o.tol = float(tol)
     o.max_sweeps = int(max_sweeps)
     o.sort = 1 if sort else 0

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <math.h>
 #include <vector>
 
@@ -93,6 +94,7 @@ struct SweepStats {
     int sweeps = 0;
     long long rotations = 0, pair_updates = 0, launches = 0;
     double ms_gram = 0, ms_solve = 0, ms_update = 0, ms_other = 0;
+    double ms_host_graph = 0;  // host wall time capturing and instantiating sweep graphs
     long long pair_visits = 0, trace_rows = 0;
     int masked_sweeps = 0, judge_sweeps = 0;
     int stop_rule = HSVD_STOP_NONE;
@@ -439,6 +441,12 @@ int solve_blocked_core(const double *G, int64_t m, int64_t n, int64_t ldg, const
     std::vector<int> full_n((size_t)nb, npairs), full_off((size_t)nb);
     for (int s = 0; s < nb; ++s) full_off[(size_t)s] = s * npairs;
     long long full_launches = 0;
+    // host time of graph capture and instantiation (reported in the info record)
+    using Clock = std::chrono::steady_clock;
+    auto ms_since = [](Clock::time_point t0) {
+        return std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+    };
+    const Clock::time_point tg0 = Clock::now();
     if (pair_sched) {
         if (!dag.create(nslot, nb)) return HSVD_ERR_CUDA;
         if (capture_pairs(d_tab_outer, d_visit, full_n, full_off, outer.data(), &gg.graph, &full_launches) !=
@@ -448,6 +456,7 @@ int solve_blocked_core(const double *G, int64_t m, int64_t n, int64_t ldg, const
         return HSVD_ERR_CUDA;
     }
     CKR(cudaGraphInstantiate(&gg.exec, gg.graph, 0));
+    stats.ms_host_graph += ms_since(tg0);
     // profiling spans every step, skipped ones included (they record nothing)
     auto add_profile = [&](const std::vector<int> &nact, bool steps) {
         if (!o.profile) return;
@@ -489,10 +498,12 @@ int solve_blocked_core(const double *G, int64_t m, int64_t n, int64_t ldg, const
             CKR(cudaMemcpyAsync(prev_skip, skip, nvis, cudaMemcpyDeviceToDevice, st));
             stats.launches += 2;
             if (!gm.exec) {
+                const Clock::time_point t0 = Clock::now();
                 if (capture_pairs(d_tab_mask, d_visit, full_n, full_off, outer.data(), &gm.graph, &mask_launches) !=
                     cudaSuccess)
                     return HSVD_ERR_CUDA;
                 CKR(cudaGraphInstantiate(&gm.exec, gm.graph, 0));
+                stats.ms_host_graph += ms_since(t0);
             }
             CKR(evs.record_now(evr + 2, st));
             CKR(cudaGraphLaunch(gm.exec, st));
@@ -530,8 +541,10 @@ int solve_blocked_core(const double *G, int64_t m, int64_t n, int64_t ldg, const
                                 st));
             GraphGuard mg;
             long long ml = 0;
+            const Clock::time_point t0 = Clock::now();
             if (capture(d_tab_mask, d_visit_mask, nact, off, &mg.graph, &ml) != cudaSuccess) return HSVD_ERR_CUDA;
             CKR(cudaGraphInstantiate(&mg.exec, mg.graph, 0));
+            stats.ms_host_graph += ms_since(t0);
             CKR(cudaGraphLaunch(mg.exec, st));
             CKR(cudaStreamSynchronize(st));
             stats.launches += ml;
@@ -600,6 +613,7 @@ int solve_blocked(const double *G, int64_t m, int64_t n, int64_t ldg, const int8
         info->ms_solve = stats.ms_solve;
         info->ms_update = stats.ms_update;
         info->ms_other = stats.ms_other;
+        info->ms_host_graph = stats.ms_host_graph;
         info->pair_visits = stats.pair_visits;
         info->masked_sweeps = stats.masked_sweeps;
         info->judge_sweeps = stats.judge_sweeps;

@@ -3,8 +3,9 @@
 // Jacobi method (Sec. 2, Alg. 4.5; the per-factor body is pw_solve).
 //
 // Work distribution.  The host sorts the factors by (group width, n), both
-// decreasing, and the kernel's CTAs (1024 threads, one per SM, launched once
-// and captured in a CUDA graph) take them from one atomic counter: the largest
+// decreasing, and the kernel's CTAs (1024 threads, or 512 with twice the
+// registers a thread, one per SM, launched once and captured in a CUDA graph)
+// take them from one atomic counter: the largest
 // first, so the long factors start early and the short ones fill the tail.
 // A CTA starts as one group of 1024 threads.  When the next factor in the
 // queue asks for a narrower group, the CTA splits into two groups of 512
@@ -33,7 +34,6 @@
 namespace hsvd {
 namespace {
 
-constexpr int kCta = 1024;
 constexpr int kBarriers = 7;  // 1 (1024) + 2 (512) + 4 (256)
 
 struct BTask {
@@ -125,12 +125,15 @@ __device__ void group_loop(const BArgs &A, int k, int g, unsigned char *sm, size
     }
 }
 
-__global__ void __launch_bounds__(kCta, 1) k_batched(BArgs A, int smem_budget) {
+// CTA threads: 1024 (64 registers a thread) or 512 (128: the per-thread
+// state of pw_solve without spills)
+template <int CTA>
+__global__ void __launch_bounds__(CTA, 1) k_batched(BArgs A, int smem_budget) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ PwScalars sc[kBarriers];
     __shared__ int fetch[kBarriers];
-    group_loop<kCta>(A, -1, 0, smem, (size_t)smem_budget, A.ws + (size_t)blockIdx.x * A.ws_stride, A.ws_stride, sc,
-                     fetch);
+    group_loop<CTA>(A, -1, 0, smem, (size_t)smem_budget, A.ws + (size_t)blockIdx.x * A.ws_stride, A.ws_stride, sc,
+                    fetch);
 }
 
 // ------------------------------------------------------------------ host side
@@ -150,11 +153,11 @@ size_t need_bytes(int64_t m, int64_t n) {
     return (size_t)(m_pad * n_pad + n_pad * n_pad) * sizeof(double);
 }
 
-// workspace doubles per CTA: a group of width w owns w/1024 of the slot, and
+// workspace doubles per CTA: a group of width w owns w/cta of the slot, and
 // must hold G and W of any factor it may take
-int64_t ws_stride_for(const std::vector<BTask> &tasks) {
+int64_t ws_stride_for(const std::vector<BTask> &tasks, int cta) {
     size_t s = 0;
-    for (const BTask &t : tasks) s = std::max(s, need_bytes(t.m, t.n) * (size_t)(kCta / t.width));
+    for (const BTask &t : tasks) s = std::max(s, need_bytes(t.m, t.n) * (size_t)(cta / t.width));
     return (int64_t)((s / sizeof(double) + 31) / 32 * 32);
 }
 
@@ -166,9 +169,10 @@ struct Launch {
 // Runs the persistent kernel over `tasks` (already in queue order) as one
 // captured graph: counter reset + the launch.
 cudaError_t run_batch(const std::vector<BTask> &tasks, int max_sweeps, int sort, double tstop, bool use_graph,
-                      int grid, int *res, long long *rot, int *where, cudaStream_t st, float *ms) {
+                      int grid, int cta, int *res, long long *rot, int *where, cudaStream_t st, float *ms) {
     const int count = (int)tasks.size();
-    const int64_t stride = ws_stride_for(tasks);
+    const int64_t stride = ws_stride_for(tasks, cta);
+    void (*kern)(BArgs, int) = cta == 512 ? k_batched<512> : k_batched<1024>;
     BTask *d_tasks = nullptr;
     int *d_counter = nullptr;
     double *d_ws = nullptr;
@@ -177,7 +181,7 @@ cudaError_t run_batch(const std::vector<BTask> &tasks, int max_sweeps, int sort,
     if (e == cudaSuccess) e = cudaMallocAsync((void **)&d_ws, sizeof(double) * (size_t)grid * stride + 64, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_tasks, tasks.data(), sizeof(BTask) * (size_t)count, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget);
     BArgs A;
     A.tasks = d_tasks;
     A.count = count;
@@ -210,7 +214,7 @@ cudaError_t run_batch(const std::vector<BTask> &tasks, int max_sweeps, int sort,
         if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             cudaMemsetAsync(d_counter, 0, sizeof(int), cap);
-            k_batched<<<grid, kCta, kSmemBudget, cap>>>(A, kSmemBudget);
+            kern<<<grid, cta, kSmemBudget, cap>>>(A, kSmemBudget);
             const cudaError_t le = cudaGetLastError();
             e = cudaStreamEndCapture(cap, &graph);
             if (e == cudaSuccess) e = le;
@@ -224,7 +228,7 @@ cudaError_t run_batch(const std::vector<BTask> &tasks, int max_sweeps, int sort,
         e = cudaMemsetAsync(d_counter, 0, sizeof(int), st);
         if (e == cudaSuccess && ms) e = cudaEventRecord(e0, st);
         if (e == cudaSuccess) {
-            k_batched<<<grid, kCta, kSmemBudget, st>>>(A, kSmemBudget);
+            kern<<<grid, cta, kSmemBudget, st>>>(A, kSmemBudget);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess && ms) e = cudaEventRecord(e1, st);
@@ -252,19 +256,21 @@ void order_tasks(std::vector<BTask> &tasks) {
 }
 
 std::mutex g_tune_mu;
-std::map<long long, std::vector<int>> g_tune_cache;  // (device, bucket mask) -> width per bucket
+std::map<long long, std::vector<int>> g_tune_cache;  // (device, CTA, bucket mask) -> width per bucket
 
 // Picks the group width of every size bucket present: each candidate width is
 // timed on up to (SMs x 1024 / width) factors of the bucket, two sweeps each,
 // and scored by sum(m n^2) / time.
-cudaError_t tune_widths(const std::vector<BTask> &all, int grid, int *res, long long *rot, int *where,
+long long tune_key(int dev, int cta, long long mask) { return ((long long)dev << 32) | ((long long)cta << 16) | mask; }
+
+cudaError_t tune_widths(const std::vector<BTask> &all, int grid, int cta, int *res, long long *rot, int *where,
                         cudaStream_t st, std::vector<int> &width, float *ms_total) {
-    width.assign(kBuckets, kCta);
+    width.assign(kBuckets, cta);
     int dev = 0;
     cudaGetDevice(&dev);
     long long mask = 0;
     for (const BTask &t : all) mask |= 1LL << bucket_of(t.n);
-    const long long key = ((long long)dev << 32) | mask;
+    const long long key = tune_key(dev, cta, mask);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
@@ -280,7 +286,8 @@ cudaError_t tune_widths(const std::vector<BTask> &all, int grid, int *res, long 
             if (bucket_of(t.n) == b) members.push_back(t);
         double best = -1.0;
         for (int w : {1024, 512, 256}) {
-            const size_t want = (size_t)grid * (kCta / w);
+            if (w > cta) continue;
+            const size_t want = (size_t)grid * (cta / w);
             std::vector<BTask> sample;
             const size_t stepk = std::max<size_t>(1, members.size() / want);
             for (size_t i = 0; i < members.size() && sample.size() < want; i += stepk) sample.push_back(members[i]);
@@ -291,7 +298,7 @@ cudaError_t tune_widths(const std::vector<BTask> &all, int grid, int *res, long 
             }
             order_tasks(sample);
             float ms = 0.f;
-            const cudaError_t e = run_batch(sample, 2, 1, 0.0, false, grid, res, rot, where, st, &ms);
+            const cudaError_t e = run_batch(sample, 2, 1, 0.0, false, grid, cta, res, rot, where, st, &ms);
             if (e != cudaSuccess) return e;
             if (ms_total) *ms_total += ms;
             const double score = work / std::max(ms, 1e-3f);
@@ -334,8 +341,10 @@ int hsvd_solve_batched_ex(int64_t count, const double *const *G, const int64_t *
     if (o.max_sweeps <= 0) o.max_sweeps = 30;
     if (o.group_width != 0 && o.group_width != 256 && o.group_width != 512 && o.group_width != 1024)
         return HSVD_ERR_ARG;
-    for (int r : o.reserved)
-        if (r) return HSVD_ERR_ARG;
+    if (o.cta_threads != 0 && o.cta_threads != 512 && o.cta_threads != 1024) return HSVD_ERR_ARG;
+    const int cta = o.cta_threads ? o.cta_threads : 1024;
+    if (o.group_width > cta) return HSVD_ERR_ARG;
+    if (o.reserved) return HSVD_ERR_ARG;
     if (o.tstop < 0.0) o.tstop = HSVD_TSTOP_PAPER;
     if (!(o.tstop >= 0.0 && o.tstop <= 1.0)) return HSVD_ERR_ARG;
     if (info) memset(info, 0, sizeof *info);
@@ -418,7 +427,7 @@ int hsvd_solve_batched_ex(int64_t count, const double *const *G, const int64_t *
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = (int)std::min<int64_t>(sms, count);
-    std::vector<int> width(kBuckets, o.group_width ? o.group_width : kCta);
+    std::vector<int> width(kBuckets, o.group_width ? o.group_width : cta);
     float ms_tune = 0.f;
     int tuned = 0;
     if (rc == HSVD_OK && o.group_width == 0) {
@@ -427,9 +436,9 @@ int hsvd_solve_batched_ex(int64_t count, const double *const *G, const int64_t *
             std::lock_guard<std::mutex> lk(g_tune_mu);
             long long mask = 0;
             for (const BTask &t : tasks) mask |= 1LL << bucket_of(t.n);
-            return g_tune_cache.count(((long long)dev << 32) | mask) > 0;
+            return g_tune_cache.count(tune_key(dev, cta, mask)) > 0;
         }();
-        if (tune_widths(tasks, sms, d_res, d_rot, d_where, st, w, &ms_tune) != cudaSuccess) fail(HSVD_ERR_CUDA);
+        if (tune_widths(tasks, sms, cta, d_res, d_rot, d_where, st, w, &ms_tune) != cudaSuccess) fail(HSVD_ERR_CUDA);
         else width = w;
         tuned = cached ? 2 : 1;
     }
@@ -437,8 +446,8 @@ int hsvd_solve_batched_ex(int64_t count, const double *const *G, const int64_t *
     order_tasks(tasks);
     float ms = 0.f;
     if (rc == HSVD_OK &&
-        run_batch(tasks, o.max_sweeps, o.sort ? 1 : 0, o.tstop, o.use_graph != 0, grid, d_res, d_rot, d_where, st,
-                  &ms) != cudaSuccess)
+        run_batch(tasks, o.max_sweeps, o.sort ? 1 : 0, o.tstop, o.use_graph != 0, grid, cta, d_res, d_rot, d_where,
+                  st, &ms) != cudaSuccess)
         fail(HSVD_ERR_CUDA);
     std::vector<int> h_res(3 * (size_t)count, 0), h_where((size_t)count, 0);
     std::vector<long long> h_rot((size_t)count, 0);
@@ -483,6 +492,7 @@ int hsvd_solve_batched_ex(int64_t count, const double *const *G, const int64_t *
         }
         if (info) {
             info->grid = grid;
+            info->cta_threads = cta;
             info->tuned = tuned;
             for (int b = 0; b < 5; ++b) info->bucket_width[b] = width[(size_t)b];
             info->ms_kernel = ms;

@@ -101,9 +101,13 @@ def test_batched_argument_errors_without_gpu(api):
     assert L.hsvd_solve_batched_ex(1, arr(G), i64(4), i64(4), i64(4), arr(J), arr(s), None, None, None, None,
                                    ctypes.byref(o2), None, None) == api.HSVD_ERR_ARG
     o3 = api.make_batch_opts()
-    o3.reserved[1] = 7
+    o3.reserved = 7
     assert L.hsvd_solve_batched_ex(1, arr(G), i64(4), i64(4), i64(4), arr(J), arr(s), None, None, None, None,
                                    ctypes.byref(o3), None, None) == api.HSVD_ERR_ARG
+    # CTA size other than 512 / 1024, and a group wider than the 512-thread CTA
+    for bad in (api.make_batch_opts(cta_threads=256), api.make_batch_opts(cta_threads=512, group_width=1024)):
+        assert L.hsvd_solve_batched_ex(1, arr(G), i64(4), i64(4), i64(4), arr(J), arr(s), None, None, None, None,
+                                       ctypes.byref(bad), None, None) == api.HSVD_ERR_ARG
 
 
 def test_learned_option_errors_without_gpu(api):

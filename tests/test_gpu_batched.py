@@ -113,6 +113,23 @@ def test_group_widths_and_graph_are_bitwise_identical(api):
             assert r.sweeps[k] == runs[0].sweeps[k]
 
 
+def test_cta_of_512_threads_is_bitwise_identical(api):
+    """The 512-thread CTA (twice the registers a thread, no spills) runs the
+    same per-factor code for groups of 512 and 256: the same bits as the
+    1024-thread CTA at those widths; autotuned under it, widths stay <= 512."""
+    facs = _mixed(14)
+    for w in (512, 256):
+        a = _run(api, facs, group_width=w)
+        b = _run(api, facs, group_width=w, cta_threads=512)
+        assert a.rc == b.rc == api.HSVD_OK
+        assert a.info.cta_threads == 1024 and b.info.cta_threads == 512
+        for k in range(len(facs)):
+            assert torch.equal(a.sigma[k], b.sigma[k]) and torch.equal(a.V[k], b.V[k])
+            assert a.sweeps[k] == b.sweeps[k]
+    t = _run(api, facs, cta_threads=512)
+    assert t.rc == api.HSVD_OK and all(w in (256, 512) for w in t.info.bucket_width)
+
+
 def test_autotuner_runs_once_then_caches(api):
     facs = W.batch(300, nmin=16, nmax=120, seed=21)
     r1 = _run(api, facs)
