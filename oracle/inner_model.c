@@ -22,8 +22,21 @@
  *       the block, S is transposed, and the rows are mixed again, so S holds
  *       the transpose of the block after an odd number of steps.  (The
  *       kernels transpose once per step this way.)
- *   M3  After the mixing, a rotated pair's diagonal entries take Eq. 2.6
- *       with the step's starting a_pq, and (p, q), (q, p) become 0.
+ *   M3  After the mixing, a rotated pair's diagonal values take Eq. 2.6
+ *       with the step's starting a_pq (a replicated vector d), and the
+ *       stored (p, q), (q, p), (p, p), (q, q) become 0.
+ *   M4  Scaled rotations: the kernels store S = diag(s)^-1 A diag(s)^-1 and
+ *       W = Wh diag(s), with column scales s (and their reciprocals r) that
+ *       start at 1.  A rotation (t, c) of pair (p, q), with q = 1/c computed
+ *       as in the rotation, becomes x_p' = x_p + alpha x_q,
+ *       x_q' = beta x_p + x_q on the stored values, alpha = ht (s_q r_p),
+ *       beta = t (s_p r_q) (two FMAs per element pair instead of two FMAs
+ *       and two multiplies), and s_p, s_q <- s c, r_p, r_q <- r q.  The
+ *       test of Eq. 2.3 reads a_pq = (s_p s_q) S_pq.  When an updated scale
+ *       has a binary exponent beyond +-8 the whole block is brought back to s = r = 1
+ *       (S_xy <- (s_x s_y) S_xy, Wh_xy <- Wh_xy s_y) before the next step.
+ *       At the end, W = Wh diag(s) and A_xy = (s_x s_y) S_xy off the
+ *       diagonal, d on it.
  *
  * Build: compiled into the oracle's shared object by oracle.py (gcc -O2
  * -ffp-contract=off: every fused multiply-add is an explicit fma()).
@@ -40,31 +53,35 @@
 int orc_rotation(double aii, double ajj, double aij, int hyp, double *t, double *c);
 void orc_modulus_pairs(int r, int nsteps, int *pairs);
 
-/* the column update of Alg. 4.5 on two vectors of length m */
-static void mdl_rotate_cols(int m, double *x, double *y, int hyp, double t, double c)
+/* the scaled column update (M4) on two vectors of length m */
+static void mdl_rotate_cols(int m, double *x, double *y, double alpha, double beta)
 {
-    const double ht = hyp < 0 ? -t : t;
     for (int i = 0; i < m; ++i) {
         const double xi = x[i], yi = y[i];
-        x[i] = fma(ht, yi, xi) * c;
-        y[i] = fma(t, xi, yi) * c;
+        x[i] = fma(alpha, yi, xi);
+        y[i] = fma(beta, xi, yi);
     }
 }
 
-/* the step's rotations on every row x of the row-major nn x nn matrix S:
- * entries p, q of the row as the column update of Alg. 4.5 */
-static void mdl_mix_rows(int nn, double *S, int h, const int *P, const int *Q, const double *T,
-                         const double *C, const int *H, const int *rot)
+/* the step's scaled rotations (M4) on every row x of the row-major nn x nn
+ * matrix S: entries p, q of the row */
+static void mdl_mix_rows(int nn, double *S, int h, const int *P, const int *Q, const double *AL,
+                         const double *BE, const int *rot)
 {
     for (int x = 0; x < nn; ++x)
         for (int k = 0; k < h; ++k) {
             if (!rot[k]) continue;
             double *row = S + (int64_t)x * nn;
             const double a = row[P[k]], b = row[Q[k]];
-            const double ht = H[k] < 0 ? -T[k] : T[k];
-            row[P[k]] = fma(ht, b, a) * C[k];
-            row[Q[k]] = fma(T[k], a, b) * C[k];
+            row[P[k]] = fma(AL[k], b, a);
+            row[Q[k]] = fma(BE[k], a, b);
         }
+}
+
+/* q = 1/c as the rotation computes it before dividing */
+static double mdl_inv_c(double t, int hyp)
+{
+    return hyp < 0 ? sqrt(1.0 + t * t) : sqrt((1.0 - t) * (1.0 + t));
 }
 
 /* Model of the inner solve of one pivot block (nn x nn column-major,
@@ -85,13 +102,19 @@ int mdl_inner_solve(int nn, double *A, const int8_t *sgn, double tol, int mode,
     double *St = (double *)malloc(sizeof(double) * (size_t)nn * nn);
     double *d = (double *)malloc(sizeof(double) * nn);
     double *apq = (double *)malloc(sizeof(double) * h);
+    double *sc = (double *)malloc(sizeof(double) * nn), *rc = (double *)malloc(sizeof(double) * nn);
+    double *AL = (double *)malloc(sizeof(double) * h), *BE = (double *)malloc(sizeof(double) * h);
     double tmax = 0.0;
     orc_modulus_pairs(nn, nn, pairs);
     memset(W, 0, sizeof(double) * (size_t)nn * nn);
     for (int i = 0; i < nn; ++i) W[i + (int64_t)i * nn] = 1.0;
     for (int x = 0; x < nn; ++x)
         for (int y = 0; y < nn; ++y) S[(int64_t)x * nn + y] = A[x + (int64_t)y * nn];
-    for (int x = 0; x < nn; ++x) d[x] = A[x + (int64_t)x * nn];
+    for (int x = 0; x < nn; ++x) {
+        d[x] = A[x + (int64_t)x * nn];
+        sc[x] = 1.0;
+        rc[x] = 1.0;
+    }
     int transposed = 0; /* 0: S = A, 1: S = A^T (M2) */
     int status = MDL_OK, npass = 0;
     int64_t nrot_total = 0;
@@ -115,7 +138,7 @@ int mdl_inner_solve(int nn, double *A, const int8_t *sgn, double tol, int mode,
             }
             for (int k = 0; k < h; ++k) {
                 const int p = P[k], q = Q[k];
-                const double a_pq = transposed ? S[(int64_t)q * nn + p] : S[(int64_t)p * nn + q];
+                const double a_pq = (sc[p] * sc[q]) * (transposed ? S[(int64_t)q * nn + p] : S[(int64_t)p * nn + q]);
                 apq[k] = a_pq;
                 H[k] = (sgn[p] == sgn[q]) ? -1 : 1;
                 T[k] = 0.0;
@@ -130,26 +153,47 @@ int mdl_inner_solve(int nn, double *A, const int8_t *sgn, double tol, int mode,
                 ++nrot_pass;
                 if (fabs(T[k]) > tmax) tmax = fabs(T[k]);
             }
+            for (int k = 0; k < h; ++k) { /* M4: coefficients from the step's starting scales */
+                if (!rot[k]) continue;
+                const int p = P[k], q = Q[k];
+                const double ht = H[k] < 0 ? -T[k] : T[k];
+                AL[k] = ht * (sc[q] * rc[p]);
+                BE[k] = T[k] * (sc[p] * rc[q]);
+            }
             /* M2: one half on the rows of S, transpose, the other half */
-            mdl_mix_rows(nn, S, h, P, Q, T, C, H, rot);
+            mdl_mix_rows(nn, S, h, P, Q, AL, BE, rot);
             for (int x = 0; x < nn; ++x)
                 for (int y = 0; y < nn; ++y) St[(int64_t)y * nn + x] = S[(int64_t)x * nn + y];
             memcpy(S, St, sizeof(double) * (size_t)nn * nn);
             transposed ^= 1;
-            mdl_mix_rows(nn, S, h, P, Q, T, C, H, rot);
-            for (int k = 0; k < h; ++k) { /* M3 */
+            mdl_mix_rows(nn, S, h, P, Q, AL, BE, rot);
+            int renorm = 0;
+            for (int k = 0; k < h; ++k) { /* M3, M4 */
                 if (!rot[k]) continue;
                 const int p = P[k], q = Q[k];
                 const double ht = H[k] < 0 ? -T[k] : T[k];
                 d[p] = fma(ht, apq[k], d[p]);
                 d[q] = fma(T[k], apq[k], d[q]);
-                S[(int64_t)p * nn + p] = d[p];
-                S[(int64_t)q * nn + q] = d[q];
+                S[(int64_t)p * nn + p] = 0.0;
+                S[(int64_t)q * nn + q] = 0.0;
                 S[(int64_t)p * nn + q] = 0.0;
                 S[(int64_t)q * nn + p] = 0.0;
+                const double qv = mdl_inv_c(T[k], H[k]);
+                sc[p] = sc[p] * C[k];
+                sc[q] = sc[q] * C[k];
+                rc[p] = rc[p] * qv;
+                rc[q] = rc[q] * qv;
+                if (abs(ilogb(sc[p])) > 8 || abs(ilogb(sc[q])) > 8) renorm = 1;
             }
             for (int k = 0; k < h; ++k) /* W <- W R */
-                if (rot[k]) mdl_rotate_cols(nn, W + (int64_t)P[k] * nn, W + (int64_t)Q[k] * nn, H[k], T[k], C[k]);
+                if (rot[k]) mdl_rotate_cols(nn, W + (int64_t)P[k] * nn, W + (int64_t)Q[k] * nn, AL[k], BE[k]);
+            if (renorm) {
+                for (int x = 0; x < nn; ++x)
+                    for (int y = 0; y < nn; ++y) S[(int64_t)x * nn + y] = (sc[x] * sc[y]) * S[(int64_t)x * nn + y];
+                for (int y = 0; y < nn; ++y)
+                    for (int x = 0; x < nn; ++x) W[x + (int64_t)y * nn] = W[x + (int64_t)y * nn] * sc[y];
+                for (int x = 0; x < nn; ++x) sc[x] = rc[x] = 1.0;
+            }
         }
         nrot_total += nrot_pass;
         if (nrot_pass == 0) break;
@@ -157,11 +201,14 @@ int mdl_inner_solve(int nn, double *A, const int8_t *sgn, double tol, int mode,
 out:
     for (int x = 0; x < nn; ++x)
         for (int y = 0; y < nn; ++y)
-            A[x + (int64_t)y * nn] = transposed ? S[(int64_t)y * nn + x] : S[(int64_t)x * nn + y];
+            A[x + (int64_t)y * nn] =
+                x == y ? d[x] : (sc[x] * sc[y]) * (transposed ? S[(int64_t)y * nn + x] : S[(int64_t)x * nn + y]);
+    for (int y = 0; y < nn; ++y)
+        for (int x = 0; x < nn; ++x) W[x + (int64_t)y * nn] = W[x + (int64_t)y * nn] * sc[y];
     if (nrot_out) *nrot_out = nrot_total;
     if (passes_out) *passes_out = npass;
     if (tmax_out) *tmax_out = tmax;
     free(pairs); free(P); free(Q); free(T); free(C); free(H); free(rot);
-    free(S); free(St); free(d); free(apq);
+    free(S); free(St); free(d); free(apq); free(sc); free(rc); free(AL); free(BE);
     return status;
 }

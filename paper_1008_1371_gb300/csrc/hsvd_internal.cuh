@@ -36,43 +36,54 @@ __device__ __forceinline__ bool pair_passes(double aii, double ajj, double aij, 
 //         c = 1/sqrt((1 - t)(1 + t))
 // sign(0) = +1.  Returns false (t = 0, c = 1) when a hyperbolic pair has
 // |zeta| <= 1: no J-unitary rotation exists, the pair is rank deficient.
+// qv = 1/c as computed before the division (the scaled inner solve keeps it).
 __device__ __forceinline__ bool rotation_params(double aii, double ajj, double aij, int hyp,
-                                                double &t, double &c) {
+                                                double &t, double &c, double &qv) {
     if (hyp < 0) {
         const double zeta = (ajj - aii) / (2.0 * aij);
         double tt = 1.0 / (fabs(zeta) + sqrt(zeta * zeta + 1.0));
         if (zeta < 0.0) tt = -tt;
         t = tt;
-        c = 1.0 / sqrt(1.0 + tt * tt);
+        qv = sqrt(1.0 + tt * tt);
+        c = 1.0 / qv;
         return true;
     }
     const double zeta = -(aii + ajj) / (2.0 * aij);
     if (!(fabs(zeta) > 1.0)) {
         t = 0.0;
         c = 1.0;
+        qv = 1.0;
         return false;
     }
     double tt = 1.0 / (fabs(zeta) + sqrt(zeta * zeta - 1.0));
     if (zeta < 0.0) tt = -tt;
     t = tt;
-    c = 1.0 / sqrt((1.0 - tt) * (1.0 + tt));
+    qv = sqrt((1.0 - tt) * (1.0 + tt));
+    c = 1.0 / qv;
     return true;
 }
 
 // The test of Eq. 2.3, then the rotation of Sec. 2 for a pair that fails it.
-// Returns 0 (the pair passes), 1 (rotate with t, c) or 2 (rank deficient);
-// t = 0, c = 1 unless it returns 1.  Late in the iteration most pairs pass, so
-// the rotation's divides and square roots are skipped for them.
+// Returns 0 (the pair passes), 1 (rotate with t, c; qv = 1/c) or 2 (rank
+// deficient); t = 0, c = qv = 1 unless it returns 1.  Late in the iteration
+// most pairs pass, so the rotation's divides and square roots are skipped.
 __device__ __forceinline__ int pair_decision(double aii, double ajj, double aij, int hyp, double tol,
-                                             double &t, double &c) {
+                                             double &t, double &c, double &qv) {
     t = 0.0;
     c = 1.0;
+    qv = 1.0;
     if (pair_passes(aii, ajj, aij, tol)) return 0;
-    double tt, cc;
-    if (!rotation_params(aii, ajj, aij, hyp, tt, cc)) return 2;
+    double tt, cc, qq;
+    if (!rotation_params(aii, ajj, aij, hyp, tt, cc, qq)) return 2;
     t = tt;
     c = cc;
+    qv = qq;
     return 1;
+}
+__device__ __forceinline__ int pair_decision(double aii, double ajj, double aij, int hyp, double tol,
+                                             double &t, double &c) {
+    double qv;
+    return pair_decision(aii, ajj, aij, hyp, tol, t, c, qv);
 }
 
 // The same decision with the test and the rotation evaluated side by side
@@ -80,18 +91,29 @@ __device__ __forceinline__ int pair_decision(double aii, double ajj, double aij,
 // pair passes): for a thread whose chain is the critical path whatever the
 // outcome (the look-ahead warp of the cross pass).  Same results.
 __device__ __forceinline__ int pair_decision_eager(double aii, double ajj, double aij, int hyp, double tol,
-                                                   double &t, double &c) {
+                                                   double &t, double &c, double &qv) {
     const bool passes = pair_passes(aii, ajj, aij, tol);
-    double tt, cc;
-    const bool ok = rotation_params(aii, ajj, aij, hyp, tt, cc);
+    double tt, cc, qq;
+    const bool ok = rotation_params(aii, ajj, aij, hyp, tt, cc, qq);
     t = 0.0;
     c = 1.0;
+    qv = 1.0;
     if (passes) return 0;
     if (!ok) return 2;
     t = tt;
     c = cc;
+    qv = qq;
     return 1;
 }
+
+// Scaled rotations of the inner solve: the kernels keep S = diag(s)^-1 A
+// diag(s)^-1 and W = Wh diag(s) with column scales s (reciprocals r), so a
+// rotation costs two FMAs per element pair, x_p' = x_p + alpha x_q,
+// x_q' = beta x_p + x_q, with alpha = ht (s_q r_p), beta = t (s_p r_q); then
+// s <- s c and r <- r qv for p and q.  A scale whose binary exponent leaves
+// [-kScaleExp, kScaleExp] sends the block back to s = r = 1 before the next step.
+constexpr int kScaleExp = 8;
+__device__ __forceinline__ bool scale_out_of_range(double s) { return abs(ilogb(s)) > kScaleExp; }
 
 // k-th pivot pair (a < b) of step `s` of the modified modulus strategy on r
 // indices (Sec. 2): the pairs with a + b = c (mod r), c = (r - 1 + s) mod r,

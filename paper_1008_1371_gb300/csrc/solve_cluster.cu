@@ -22,8 +22,15 @@
 //   3. every CTA mixes columns p, q of its received rows (the other half of
 //      R^T A R) and writes Eq. 2.6's diagonal and the zeros of the pair.
 // Parameters and pair lists are double-buffered by step parity, so two
-// barriers per step suffice.  The arithmetic is the oracle's, element for
-// element, so the result is bit-identical to it.
+// barriers per step suffice.
+//
+// All three kernels here apply scaled rotations (hsvd_internal.cuh): they
+// keep S = diag(s)^-1 A diag(s)^-1 and W = Wh diag(s), so a rotation costs two
+// FMAs per element pair instead of two FMAs and two multiplies, which halves
+// the FP64 work of the inner solve; the true a_pq of a test is (s_p s_q) S_pq,
+// and the outputs are the true A_P (diagonal from Eq. 2.6) and W_P.  The
+// element operations and their order are those of the exact CPU model of the
+// kernels (oracle/inner_model.c), so the results are bit-identical to it.
 #include <cooperative_groups.h>
 
 #include <vector>
@@ -84,7 +91,10 @@ k_solve_cluster(const double *__restrict__ part, int nsplit, int full_part, doub
     __shared__ double D[NN];
     __shared__ int sg[NN];
     __shared__ int P[2][H], Q[2][H], Hy[2][H], Rot[2][H];
-    __shared__ double T[2][H], Cc[2][H], Apq[2][H];
+    __shared__ double T[2][H], Cc[2][H], Qv[2][H], Apq[2][H];  // Apq: the true a_pq
+    __shared__ double Sc[NN], Rc[NN];  // column scales of the stored block and their reciprocals
+    __shared__ double Al[H], Be[H];    // the step's scaled-rotation coefficients
+    __shared__ int s_renorm;
     __shared__ int s_flag;
     __shared__ int s_big;  // a rotation had |t| > tstop (Eq. 4.2 code (11)_2)
     __shared__ double tr_max[C], tr_sum[C], tr_red[2][kClThreads / 32];
@@ -105,11 +115,14 @@ k_solve_cluster(const double *__restrict__ part, int nsplit, int full_part, doub
     if (tid == 0) {
         s_flag = 0;
         s_big = 0;
+        s_renorm = 0;
     }
     for (int x = tid; x < NN; x += kClThreads) {
         if (sgn_direct) sg[x] = sgn_direct[(size_t)pair * NN + x];
         else sg[x] = sgn_cols[col0[2 * pair + (x >= B)] + (x % B)];
         D[x] = entry(x, x);
+        Sc[x] = 1.0;
+        Rc[x] = 1.0;
         // column-norm exponents for the balancing of the split-precision update
         if (dexp && rank == 0) dexp[(size_t)pair * NN + x] = D[x] > 0.0 ? (ilogb(D[x]) >> 1) : 0;
     }
@@ -196,17 +209,24 @@ k_solve_cluster(const double *__restrict__ part, int nsplit, int full_part, doub
             cluster.sync();
             if (tid < H) {
                 const int k = tid, p = P[buf][k], q = Q[buf][k];
-                const double apq = Apq[buf][k], app = D[p], aqq = D[q];
+                const double apq = (Sc[p] * Sc[q]) * Apq[buf][k], app = D[p], aqq = D[q];  // true a_pq
                 const int hyp = (sg[p] == sg[q]) ? -1 : 1;
-                double t, c;
-                const int d = pair_decision(app, aqq, apq, hyp, tol, t, c);
+                double t, c, qv;
+                const int d = pair_decision(app, aqq, apq, hyp, tol, t, c, qv);
                 const int rot = d == 1;
                 if (d == 2) s_flag = HSVD_ERR_RANK;
                 if (rot && fabs(t) > tstop) s_big = 1;
                 T[buf][k] = t;
                 Cc[buf][k] = c;
+                Qv[buf][k] = qv;
+                Apq[buf][k] = apq;
                 Hy[buf][k] = hyp;
                 Rot[buf][k] = rot;
+                if (rot) {  // the step's coefficients from its starting scales
+                    const double ht = hyp < 0 ? -t : t;
+                    Al[k] = ht * (Sc[q] * Rc[p]);
+                    Be[k] = t * (Sc[p] * Rc[q]);
+                }
             }
             __syncthreads();
             if (s_flag) { err = 1; break; }
@@ -215,16 +235,16 @@ k_solve_cluster(const double *__restrict__ part, int nsplit, int full_part, doub
             static_assert(kClThreads % H == 0, "whole rows per pass");
             if (Rot[buf][tid % H]) {
                 const int k = tid % H, p = P[buf][k], q = Q[buf][k];
-                const double t = T[buf][k], c = Cc[buf][k], ht = Hy[buf][k] < 0 ? -t : t;
+                const double al = Al[k], be = Be[k];
                 for (int x = tid / H; x < R; x += kClThreads / H) {
                     double *row = S + x * LD;
                     const double a = row[p], b = row[q];
-                    row[p] = fma(ht, b, a) * c;
-                    row[q] = fma(t, a, b) * c;
+                    row[p] = fma(al, b, a);
+                    row[q] = fma(be, a, b);
                     double *wr = Wl + x * NN;
                     const double wa = wr[p], wb = wr[q];
-                    wr[p] = fma(ht, wb, wa) * c;
-                    wr[q] = fma(t, wa, wb) * c;
+                    wr[p] = fma(al, wb, wa);
+                    wr[q] = fma(be, wa, wb);
                 }
             }
             if (tid < H && Rot[buf][tid]) {
@@ -246,27 +266,44 @@ k_solve_cluster(const double *__restrict__ part, int nsplit, int full_part, doub
             // 3. second half on the received rows, then the pair's own entries
             if (Rot[buf][tid % H]) {
                 const int k = tid % H, p = P[buf][k], q = Q[buf][k];
-                const double t = T[buf][k], c = Cc[buf][k], ht = Hy[buf][k] < 0 ? -t : t;
+                const double al = Al[k], be = Be[k];
                 for (int x = tid / H; x < R; x += kClThreads / H) {
                     double *row = S + x * LD;
                     const double a = row[p], b = row[q];
-                    row[p] = fma(ht, b, a) * c;
-                    row[q] = fma(t, a, b) * c;
+                    row[p] = fma(al, b, a);
+                    row[q] = fma(be, a, b);
                 }
             }
             __syncthreads();
             if (tid < H && Rot[buf][tid]) {
                 const int p = P[buf][tid], q = Q[buf][tid];
                 if (p / R == rank) {
-                    S[(p - row0) * LD + p] = D[p];
+                    S[(p - row0) * LD + p] = 0.0;
                     S[(p - row0) * LD + q] = 0.0;
                 }
                 if (q / R == rank) {
-                    S[(q - row0) * LD + q] = D[q];
+                    S[(q - row0) * LD + q] = 0.0;
                     S[(q - row0) * LD + p] = 0.0;
                 }
+                const double c = Cc[buf][tid], qv = Qv[buf][tid];
+                Sc[p] = Sc[p] * c;
+                Sc[q] = Sc[q] * c;
+                Rc[p] = Rc[p] * qv;
+                Rc[q] = Rc[q] * qv;
+                if (scale_out_of_range(Sc[p]) || scale_out_of_range(Sc[q])) s_renorm = 1;
             }
             pass_rot += __syncthreads_count(tid < H && Rot[buf][tid]);
+            if (s_renorm) {  // scales out of range: the block back to s = r = 1
+                for (int e = tid; e < R * NN; e += kClThreads) {
+                    const int x = e / NN, y = e % NN;
+                    S[x * LD + y] = (Sc[row0 + x] * Sc[y]) * S[x * LD + y];
+                    Wl[x * NN + y] = Wl[x * NN + y] * Sc[y];
+                }
+                __syncthreads();
+                for (int x = tid; x < NN; x += kClThreads) Sc[x] = Rc[x] = 1.0;
+                if (tid == 0) s_renorm = 0;
+                __syncthreads();
+            }
         }
         total += pass_rot;
         if (pass_rot == 0) break;
@@ -275,15 +312,17 @@ k_solve_cluster(const double *__restrict__ part, int nsplit, int full_part, doub
     double *wo = Wout + (size_t)pair * NN * NN;
     for (int e = tid; e < R * NN; e += kClThreads) {
         const int x = e / NN, y = e % NN;
-        wo[(row0 + x) + (size_t)y * NN] = Wl[x * NN + y];
+        wo[(row0 + x) + (size_t)y * NN] = Wl[x * NN + y] * Sc[y];
     }
     if (!part) {
+        // true values (s_x s_y) S_xy, the diagonal from D
         double *ao = A_io + (size_t)pair * NN * NN;
         for (int e = tid; e < R * NN; e += kClThreads) {
             const int x = e / NN, y = e % NN;
             const int gx = row0 + x;
-            if (transposed) ao[y + (size_t)gx * NN] = S[x * LD + y];  // stored row gx is column gx of A
-            else ao[gx + (size_t)y * NN] = S[x * LD + y];
+            const double v = gx == y ? D[gx] : (Sc[gx] * Sc[y]) * S[x * LD + y];
+            if (transposed) ao[y + (size_t)gx * NN] = v;  // stored row gx is column gx of A
+            else ao[gx + (size_t)y * NN] = v;
         }
     }
     if (rank == 0 && tid == 0) {
@@ -353,8 +392,11 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
     double *Wl = mov + (P + 1) * NN;  // [RW][NN]   rows w0 .. w0 + RW - 1 of W_P
     __shared__ double D[NN];
     __shared__ int sg[NN];
-    __shared__ double T[2][h], Cc[2][h], Apq[2][h];
+    __shared__ double T[2][h], Cc[2][h], Qv[2][h], Apq[2][h];  // Apq: the true a_pq
     __shared__ int Fl[2][h];          // bit 0: rotate, bit 1: rank deficient
+    __shared__ double Sc[NN], Rc[NN];  // column scales of the stored block and their reciprocals
+    __shared__ double Al[h], Be[h];    // the step's scaled-rotation coefficients
+    __shared__ int s_renorm;
     __shared__ double tr_max[C], tr_sum[C], tr_red[2][kT / 32];
     __shared__ int s_first[C];        // per CTA: first step with a pair failing Eq. 2.3 on A_P
     __shared__ int s_own;
@@ -372,9 +414,14 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
         if (sgn_direct) sg[x] = sgn_direct[(size_t)pair * NN + x];
         else sg[x] = sgn_cols[col0[2 * pair + (x >= B)] + (x % B)];
         D[x] = entry(x, x);
+        Sc[x] = 1.0;
+        Rc[x] = 1.0;
         if (dexp && rank == 0) dexp[(size_t)pair * NN + x] = D[x] > 0.0 ? (ilogb(D[x]) >> 1) : 0;
     }
-    if (tid == 0) s_own = h;
+    if (tid == 0) {
+        s_own = h;
+        s_renorm = 0;
+    }
     for (int e = tid; e < P * NN; e += kT) {
         const int kl = e / NN, y = e % NN;
         fix[kl * NN + y] = entry(k0 + kl, y);
@@ -452,21 +499,25 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
     }
     __syncthreads();
     // (t, c) of the owned pairs for step s into every CTA (buffer s & 1)
+    auto put_params = [&](int s, int k, double t, double c, double qv, double apq, int fl) {
+        const int b = s & 1;
+        for (int r = 0; r < C; ++r) {
+            *cluster.map_shared_rank(&T[b][k], r) = t;
+            *cluster.map_shared_rank(&Cc[b][k], r) = c;
+            *cluster.map_shared_rank(&Qv[b][k], r) = qv;
+            *cluster.map_shared_rank(&Apq[b][k], r) = apq;
+            *cluster.map_shared_rank(&Fl[b][k], r) = fl;
+        }
+    };
     auto params_out = [&](int s) {
         if (tid < P) {
             const int kl = tid, k = k0 + kl, p = k, q = h + (k + s) % h;
-            const double apq = fix[kl * NN + q];
+            const double apq = (Sc[p] * Sc[q]) * fix[kl * NN + q];  // true a_pq
             const double app = D[p], aqq = D[q];
             const int hyp = (sg[p] == sg[q]) ? -1 : 1;
-            double t, c;
-            const int fl = pair_decision(app, aqq, apq, hyp, tol, t, c);
-            const int b = s & 1;
-            for (int r = 0; r < C; ++r) {
-                *cluster.map_shared_rank(&T[b][k], r) = t;
-                *cluster.map_shared_rank(&Cc[b][k], r) = c;
-                *cluster.map_shared_rank(&Apq[b][k], r) = apq;
-                *cluster.map_shared_rank(&Fl[b][k], r) = fl;
-            }
+            double t, c, qv;
+            const int fl = pair_decision(app, aqq, apq, hyp, tol, t, c, qv);
+            put_params(s, k, t, c, qv, apq, fl);
         }
     };
     if (s0 < h) params_out(s0);
@@ -484,11 +535,30 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
     const int warp = tid >> 5, lane = tid & 31;
     int total = 0, bad = 0, s_end = h - 1;
     int big = 0;  // a rotation of pair tid had |t| > tstop (Eq. 4.2 code (11)_2)
+    const int mt = LA ? tid - 32 : tid;  // mixing thread index (warps 1.. with the look-ahead)
     for (int s = s0; s < h; ++s) {
         const int b = s & 1;
-        double nx_t = 0.0, nx_c = 1.0, nx_apq = 0.0;
+        auto slot = [&](int kl) { return (kl + s) % (P + 1); };
+        // scales out of range after the last step: the block back to s = r = 1
+        if (s_renorm) {
+            for (int e = tid; e < (2 * P + RW) * NN; e += kT) {
+                const int r = e / NN, y = e % NN;
+                if (r < 2 * P) {
+                    const int kl = r < P ? r : r - P, x = r < P ? k0 + kl : h + (k0 + kl + s) % h;
+                    double *row = r < P ? fix + kl * NN : mov + slot(kl) * NN;
+                    row[y] = (Sc[x] * Sc[y]) * row[y];
+                } else {
+                    Wl[(r - 2 * P) * NN + y] = Wl[(r - 2 * P) * NN + y] * Sc[y];
+                }
+            }
+            __syncthreads();
+            for (int x = tid; x < NN; x += kT) Sc[x] = Rc[x] = 1.0;
+            if (tid == 0) s_renorm = 0;
+            __syncthreads();
+        }
+        double nx_t = 0.0, nx_c = 1.0, nx_qv = 1.0, nx_apq = 0.0;
         int nx_fl = 0;
-        double e_kj = 0.0, e_kq = 0.0, e_qj = 0.0, e_qq = 0.0, d_k = 0.0, d_q = 0.0;
+        double e_kj = 0.0, e_kq = 0.0, e_qj = 0.0, e_qq = 0.0, d_k = 0.0, d_q = 0.0, s_k = 1.0, s_q = 1.0;
         const bool ahead = LA && warp == 0 && lane < P && s + 1 < h;
         if (ahead) {
             const int kl = lane, k = k0 + kl, j = (k + 1) % h, q2 = h + (j + s) % h;
@@ -499,6 +569,15 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
             e_qq = rq[q2];
             d_k = D[k];
             d_q = D[q2];
+            s_k = Sc[k];
+            s_q = Sc[q2];
+        }
+        // the step's coefficients from its starting scales
+        if (mt >= 0 && mt < h && (Fl[b][mt] & 1)) {
+            const int p = mt, q = h + (mt + s) % h;
+            const double t = T[b][mt], ht = (sg[p] == sg[q]) ? -t : t;
+            Al[mt] = ht * (Sc[q] * Rc[p]);
+            Be[mt] = t * (Sc[p] * Rc[q]);
         }
         // every CTA sees every pair's flags: the same decision everywhere
         const int f = tid < h ? Fl[b][tid] : 0;
@@ -510,37 +589,39 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
             break;
         }
         total += nrot;
-        auto slot = [&](int kl) { return (kl + s) % (P + 1); };
         if (LA && warp == 0) {
             if (ahead) {
                 const int kl = lane, k = k0 + kl, j = (k + 1) % h, q2 = h + (j + s) % h, qk = h + (k + s) % h;
                 const int fk = Fl[b][k] & 1, fj = Fl[b][j] & 1;
-                const double tk = T[b][k], ck = Cc[b][k], htk = (sg[k] == sg[qk]) ? -tk : tk;
-                const double tj = T[b][j], cj = Cc[b][j], htj = (sg[j] == sg[q2]) ? -tj : tj;
+                const double tk = T[b][k], htk = (sg[k] == sg[qk]) ? -tk : tk;
+                const double tj = T[b][j];
+                const double alk = fk ? Al[k] : 0.0, bej = fj ? Be[j] : 0.0;
                 double v;
                 if ((s & 1) == 0) {  // column mix (pair j), then row mix (pair k)
                     double r1 = e_kq, r2 = e_qq;
                     if (fj) {
-                        r1 = fma(tj, e_kj, e_kq) * cj;
-                        r2 = fma(tj, e_qj, e_qq) * cj;
+                        r1 = fma(bej, e_kj, e_kq);
+                        r2 = fma(bej, e_qj, e_qq);
                     }
-                    v = fk ? fma(htk, r2, r1) * ck : r1;
+                    v = fk ? fma(alk, r2, r1) : r1;
                 } else {  // row mix (pair k), then column mix (pair j)
                     double u1 = e_kj, u2 = e_kq;
                     if (fk) {
-                        u1 = fma(htk, e_qj, e_kj) * ck;
-                        u2 = fma(htk, e_qq, e_kq) * ck;
+                        u1 = fma(alk, e_qj, e_kj);
+                        u2 = fma(alk, e_qq, e_kq);
                     }
-                    v = fj ? fma(tj, u1, u2) * cj : u2;
+                    v = fj ? fma(bej, u1, u2) : u2;
                 }
                 const double app = fk ? fma(htk, Apq[b][k], d_k) : d_k;
                 const double aqq = fj ? fma(tj, Apq[b][j], d_q) : d_q;
+                // the step's new scales of rows k and q2 (as the update phase forms them)
+                const double sk = fk ? s_k * Cc[b][k] : s_k, sq = fj ? s_q * Cc[b][j] : s_q;
+                const double apq = (sk * sq) * v;
                 const int hyp = (sg[k] == sg[q2]) ? -1 : 1;
-                nx_fl = pair_decision_eager(app, aqq, v, hyp, tol, nx_t, nx_c);
-                nx_apq = v;
+                nx_fl = pair_decision_eager(app, aqq, apq, hyp, tol, nx_t, nx_c, nx_qv);
+                nx_apq = apq;
             }
         } else {
-            const int mt = LA ? tid - 32 : tid;
             // The column mix on every owned row of A (and of W): pair j's columns
             // j and h + (j + s) mod h.  A thread keeps one pair (its rotation in
             // registers) and walks rows; consecutive threads take consecutive
@@ -550,13 +631,13 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
                 const int j = mt % h;
                 if (!(Fl[b][j] & 1)) return;
                 const int p = j, q = h + (j + s) % h;
-                const double t = T[b][j], c = Cc[b][j], ht = (sg[p] == sg[q]) ? -t : t;
+                const double al = Al[j], be = Be[j];
                 const int nrows = 2 * P + (with_w ? RW : 0);
                 for (int r = mt / h; r < nrows; r += kMixThreads / h) {
                     double *row = r < P ? fix + r * NN : (r < 2 * P ? mov + slot(r - P) * NN : Wl + (r - 2 * P) * NN);
                     const double a = row[p], bb = row[q];
-                    row[p] = fma(ht, bb, a) * c;
-                    row[q] = fma(t, a, bb) * c;
+                    row[p] = fma(al, bb, a);
+                    row[q] = fma(be, a, bb);
                 }
             };
             // The row mix of every owned pair: rows k and its partner, every
@@ -567,25 +648,24 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
                 constexpr int TP = kMixThreads / P;  // threads per owned pair
                 const int kl = mt / TP, k = k0 + kl;
                 if (Fl[b][k] & 1) {
-                    const int p = k, q = h + (k + s) % h;
-                    const double t = T[b][k], c = Cc[b][k], ht = (sg[p] == sg[q]) ? -t : t;
+                    const double al = Al[k], be = Be[k];
                     double *rp = fix + kl * NN, *rq = mov + slot(kl) * NN;
                     for (int y = mt % TP; y < NN; y += TP) {
                         const double a = rp[y], bb = rq[y];
-                        rp[y] = fma(ht, bb, a) * c;
-                        rq[y] = fma(t, a, bb) * c;
+                        rp[y] = fma(al, bb, a);
+                        rq[y] = fma(be, a, bb);
                     }
                 }
                 if (!with_w) return;
                 const int j = mt % h;
                 if (!(Fl[b][j] & 1)) return;
                 const int pw = j, qw = h + (j + s) % h;
-                const double t = T[b][j], c = Cc[b][j], ht = (sg[pw] == sg[qw]) ? -t : t;
+                const double al = Al[j], be = Be[j];
                 for (int x = mt / h; x < RW; x += kMixThreads / h) {
                     double *row = Wl + x * NN;
                     const double a = row[pw], bb = row[qw];
-                    row[pw] = fma(ht, bb, a) * c;
-                    row[qw] = fma(t, a, bb) * c;
+                    row[pw] = fma(al, bb, a);
+                    row[qw] = fma(be, a, bb);
                 }
             };
             if ((s & 1) == 0) {
@@ -598,21 +678,27 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
                 col_mix(false);
             }
             mix_sync<LA>(kMixThreads);
-            // Eq. 2.6 on the replicated diagonal, and the owned pairs' own entries
+            // Eq. 2.6 on the replicated diagonal, the owned pairs' own stored
+            // entries to 0, and the new scales of the rotated rows
             if (mt < h && (Fl[b][mt] & 1)) {
                 const int p = mt, q = h + (mt + s) % h;
                 const double t = T[b][mt], ht = (sg[p] == sg[q]) ? -t : t, apq = Apq[b][mt];
-                const double dp = fma(ht, apq, D[p]), dq = fma(t, apq, D[q]);
-                D[p] = dp;
-                D[q] = dq;
+                D[p] = fma(ht, apq, D[p]);
+                D[q] = fma(t, apq, D[q]);
                 if (p >= k0 && p < k0 + P) {
                     const int kl = p - k0;
                     double *rp = fix + kl * NN, *rq = mov + slot(kl) * NN;
-                    rp[p] = dp;
+                    rp[p] = 0.0;
                     rp[q] = 0.0;
-                    rq[q] = dq;
+                    rq[q] = 0.0;
                     rq[p] = 0.0;
                 }
+                const double c = Cc[b][mt], qv = Qv[b][mt];
+                Sc[p] = Sc[p] * c;
+                Sc[q] = Sc[q] * c;
+                Rc[p] = Rc[p] * qv;
+                Rc[q] = Rc[q] * qv;
+                if (scale_out_of_range(Sc[p]) || scale_out_of_range(Sc[q])) s_renorm = 1;
             }
         }
         __syncthreads();
@@ -624,15 +710,7 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
             double *rdst = cluster.map_shared_rank(mov, dst) + ((P + s) % (P + 1)) * NN;
             for (int y = tid; y < NN; y += kT) rdst[y] = src[y];
             if (!LA) params_out(s + 1);
-            if (ahead) {
-                const int k = k0 + lane, nb = (s + 1) & 1;
-                for (int r = 0; r < C; ++r) {
-                    *cluster.map_shared_rank(&T[nb][k], r) = nx_t;
-                    *cluster.map_shared_rank(&Cc[nb][k], r) = nx_c;
-                    *cluster.map_shared_rank(&Apq[nb][k], r) = nx_apq;
-                    *cluster.map_shared_rank(&Fl[nb][k], r) = nx_fl;
-                }
-            }
+            if (ahead) put_params(s + 1, k0 + lane, nx_t, nx_c, nx_qv, nx_apq, nx_fl);
         }
         cluster.sync();
     }
@@ -640,15 +718,16 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
     double *wo = Wout + (size_t)pair * NN * NN;
     for (int e = tid; e < RW * NN; e += kT) {
         const int x = e / NN, y = e % NN;
-        wo[(w0 + x) + (size_t)y * NN] = Wl[x * NN + y];
+        wo[(w0 + x) + (size_t)y * NN] = Wl[x * NN + y] * Sc[y];
     }
     if (!part) {
-        // rows where the pass ended: fixed rows k, partner rows h + (k + s_end) mod h
+        // rows where the pass ended: fixed rows k, partner rows h + (k + s_end) mod h;
+        // true values (s_x s_y) S_xy, the diagonal from D
         double *ao = A_io + (size_t)pair * NN * NN;
         for (int e = tid; e < P * NN; e += kT) {
-            const int kl = e / NN, y = e % NN, k = k0 + kl;
-            ao[k + (size_t)y * NN] = fix[kl * NN + y];
-            ao[(h + (k + s_end) % h) + (size_t)y * NN] = mov[((kl + s_end) % (P + 1)) * NN + y];
+            const int kl = e / NN, y = e % NN, k = k0 + kl, x = h + (k + s_end) % h;
+            ao[k + (size_t)y * NN] = k == y ? D[k] : (Sc[k] * Sc[y]) * fix[kl * NN + y];
+            ao[x + (size_t)y * NN] = x == y ? D[x] : (Sc[x] * Sc[y]) * mov[((kl + s_end) % (P + 1)) * NN + y];
         }
     }
     cluster.sync();
@@ -728,8 +807,11 @@ k_solve_ring(const double *__restrict__ part, int nsplit, int full_part, double 
     double *Wl = pool + NBUF * NN;   // [RW][NN] rows w0 .. w0 + RW - 1 of W_P
     __shared__ double D[NN];
     __shared__ int sg[NN];
-    __shared__ double T[2][h], Cc[2][h], Apq[2][h];
+    __shared__ double T[2][h], Cc[2][h], Qv[2][h], Apq[2][h];  // Apq: the true a_pq
     __shared__ int Fl[2][h];         // bit 0: rotate, bit 1: rank deficient
+    __shared__ double Sc[NN], Rc[NN];  // column scales of the stored block and their reciprocals
+    __shared__ double Al[h], Be[h];    // the step's scaled-rotation coefficients
+    __shared__ int s_renorm;
     __shared__ int4 tb[3][h];        // ring table rows of steps s, s + 1, s + 2 (at step % 3)
     __shared__ double tr_max[C], tr_sum[C], tr_red[2][kT / 32];
 
@@ -746,8 +828,11 @@ k_solve_ring(const double *__restrict__ part, int nsplit, int full_part, double 
         if (sgn_direct) sg[x] = sgn_direct[(size_t)pair * NN + x];
         else sg[x] = sgn_cols[col0[2 * pair + (x >= B)] + (x % B)];
         D[x] = entry(x, x);
+        Sc[x] = 1.0;
+        Rc[x] = 1.0;
         if (dexp && rank == 0) dexp[(size_t)pair * NN + x] = D[x] > 0.0 ? (ilogb(D[x]) >> 1) : 0;
     }
+    if (tid == 0) s_renorm = 0;
     for (int e = tid; e < 2 * h; e += kT) tb[e / h][e % h] = ring[e];
     __syncthreads();
     // rows of the owned slots at step 0, W = I
@@ -811,11 +896,12 @@ k_solve_ring(const double *__restrict__ part, int nsplit, int full_part, double 
         *cluster.map_shared_rank(&tr_sum[rank], 0) = rec_sum;
     }
     // (t, c) of a pair into every CTA (buffer s & 1)
-    auto put_params = [&](int s, int k, double t, double c, double apq, int fl) {
+    auto put_params = [&](int s, int k, double t, double c, double qv, double apq, int fl) {
         const int b = s & 1;
         for (int r = 0; r < C; ++r) {
             *cluster.map_shared_rank(&T[b][k], r) = t;
             *cluster.map_shared_rank(&Cc[b][k], r) = c;
+            *cluster.map_shared_rank(&Qv[b][k], r) = qv;
             *cluster.map_shared_rank(&Apq[b][k], r) = apq;
             *cluster.map_shared_rank(&Fl[b][k], r) = fl;
         }
@@ -833,11 +919,11 @@ k_solve_ring(const double *__restrict__ part, int nsplit, int full_part, double 
     if (tid < P) {
         const int k = k0 + tid;
         const int4 e = tb[0][k];
-        const double apq = pool[ring_buf_lo(e) * NN + e.y];
+        const double apq = (Sc[e.x] * Sc[e.y]) * pool[ring_buf_lo(e) * NN + e.y];
         const int hyp = (sg[e.x] == sg[e.y]) ? -1 : 1;
-        double t, c;
-        const int fl = pair_decision(D[e.x], D[e.y], apq, hyp, tol, t, c);
-        put_params(0, k, t, c, apq, fl);
+        double t, c, qv;
+        const int fl = pair_decision(D[e.x], D[e.y], apq, hyp, tol, t, c, qv);
+        put_params(0, k, t, c, qv, apq, fl);
     }
     cluster.sync();
 
@@ -851,12 +937,30 @@ k_solve_ring(const double *__restrict__ part, int nsplit, int full_part, double 
     const int warp = tid >> 5, lane = tid & 31;
     int total = 0, bad = 0, s_end = NN - 1;
     int big = 0;  // a rotation of pair tid had |t| > tstop (Eq. 4.2 code (11)_2)
+    const int mt = LA ? tid - 32 : tid;  // mixing thread index (warps 1.. with the look-ahead)
     for (int s = 0; s < NN; ++s) {
         const int b = s & 1;
         const int4 *cur = tb[s % 3];
-        double nx_t = 0.0, nx_c = 1.0, nx_apq = 0.0;
+        // scales out of range after the last step: the block back to s = r = 1
+        if (s_renorm) {
+            for (int e = tid; e < (2 * P + RW) * NN; e += kT) {
+                const int r = e / NN, y = e % NN;
+                if (r < 2 * P) {
+                    const int4 t = cur[k0 + (r >> 1)];
+                    const int x = (r & 1) ? t.y : t.x, bf = (r & 1) ? ring_buf_hi(t) : ring_buf_lo(t);
+                    pool[bf * NN + y] = (Sc[x] * Sc[y]) * pool[bf * NN + y];
+                } else {
+                    Wl[(r - 2 * P) * NN + y] = Wl[(r - 2 * P) * NN + y] * Sc[y];
+                }
+            }
+            __syncthreads();
+            for (int x = tid; x < NN; x += kT) Sc[x] = Rc[x] = 1.0;
+            if (tid == 0) s_renorm = 0;
+            __syncthreads();
+        }
+        double nx_t = 0.0, nx_c = 1.0, nx_qv = 1.0, nx_apq = 0.0;
         int nx_fl = 0;
-        double e_pp = 0.0, e_pq = 0.0, e_qp = 0.0, e_qq = 0.0, d_lo = 0.0, d_hi = 0.0;
+        double e_pp = 0.0, e_pq = 0.0, e_qp = 0.0, e_qq = 0.0, d_lo = 0.0, d_hi = 0.0, s_lo = 1.0, s_hi = 1.0;
         int si = 0, sj = 0;
         bool lo_p = false, hi_p = false, trig_i = false, trig_j = false, trig_n = false;
         const bool ahead = LA && warp == 0 && lane <= P && s + 1 < NN && forms(s + 1, lane);
@@ -874,11 +978,20 @@ k_solve_ring(const double *__restrict__ part, int nsplit, int full_part, double 
             e_qq = rq[fj.y];
             d_lo = D[ne.x];
             d_hi = D[ne.y];
+            s_lo = Sc[ne.x];
+            s_hi = Sc[ne.y];
             lo_p = ne.x == fi.x;  // row lo is pair i's first row
             hi_p = ne.y == fj.x;  // column hi is pair j's first column
             trig_i = sg[fi.x] == sg[fi.y];
             trig_j = sg[fj.x] == sg[fj.y];
             trig_n = sg[ne.x] == sg[ne.y];
+        }
+        // the step's coefficients from its starting scales
+        if (mt >= 0 && mt < h && (Fl[b][mt] & 1)) {
+            const int p = cur[mt].x, q = cur[mt].y;
+            const double t = T[b][mt], ht = (sg[p] == sg[q]) ? -t : t;
+            Al[mt] = ht * (Sc[q] * Rc[p]);
+            Be[mt] = t * (Sc[p] * Rc[q]);
         }
         // every CTA sees every pair's flags: the same decision everywhere
         const int f = tid < h ? Fl[b][tid] : 0;
@@ -893,34 +1006,37 @@ k_solve_ring(const double *__restrict__ part, int nsplit, int full_part, double 
         if (LA && warp == 0) {
             if (ahead) {
                 const int ri = Fl[b][si] & 1, rj = Fl[b][sj] & 1;
-                const double ti = T[b][si], ci = Cc[b][si], hti = trig_i ? -ti : ti;
-                const double tj = T[b][sj], cj = Cc[b][sj], htj = trig_j ? -tj : tj;
+                const double ti = T[b][si], hti = trig_i ? -ti : ti;
+                const double tj = T[b][sj], htj = trig_j ? -tj : tj;
+                const double ali = ri ? Al[si] : 0.0, bei = ri ? Be[si] : 0.0;
+                const double alj = rj ? Al[sj] : 0.0, bej = rj ? Be[sj] : 0.0;
                 double v;
                 if ((s & 1) == 0) {  // column mix (pair j) of rows p_i, q_i, then row mix (pair i)
                     double up = hi_p ? e_pp : e_pq, uq = hi_p ? e_qp : e_qq;
                     if (rj) {
-                        up = hi_p ? fma(htj, e_pq, e_pp) * cj : fma(tj, e_pp, e_pq) * cj;
-                        uq = hi_p ? fma(htj, e_qq, e_qp) * cj : fma(tj, e_qp, e_qq) * cj;
+                        up = hi_p ? fma(alj, e_pq, e_pp) : fma(bej, e_pp, e_pq);
+                        uq = hi_p ? fma(alj, e_qq, e_qp) : fma(bej, e_qp, e_qq);
                     }
                     v = lo_p ? up : uq;
-                    if (ri) v = lo_p ? fma(hti, uq, up) * ci : fma(ti, up, uq) * ci;
+                    if (ri) v = lo_p ? fma(ali, uq, up) : fma(bei, up, uq);
                 } else {  // row mix (pair i) in columns p_j, q_j, then column mix (pair j)
                     double wp = lo_p ? e_pp : e_qp, wq = lo_p ? e_pq : e_qq;
                     if (ri) {
-                        wp = lo_p ? fma(hti, e_qp, e_pp) * ci : fma(ti, e_pp, e_qp) * ci;
-                        wq = lo_p ? fma(hti, e_qq, e_pq) * ci : fma(ti, e_pq, e_qq) * ci;
+                        wp = lo_p ? fma(ali, e_qp, e_pp) : fma(bei, e_pp, e_qp);
+                        wq = lo_p ? fma(ali, e_qq, e_pq) : fma(bei, e_pq, e_qq);
                     }
                     v = hi_p ? wp : wq;
-                    if (rj) v = hi_p ? fma(htj, wq, wp) * cj : fma(tj, wp, wq) * cj;
+                    if (rj) v = hi_p ? fma(alj, wq, wp) : fma(bej, wp, wq);
                 }
-                // Eq. 2.6 on the two diagonal entries
+                // Eq. 2.6 on the two diagonal entries, the step's new scales of the two rows
                 const double app = ri ? fma(lo_p ? hti : ti, Apq[b][si], d_lo) : d_lo;
                 const double aqq = rj ? fma(hi_p ? htj : tj, Apq[b][sj], d_hi) : d_hi;
-                nx_fl = pair_decision_eager(app, aqq, v, trig_n ? -1 : 1, tol, nx_t, nx_c);
-                nx_apq = v;
+                const double sl = ri ? s_lo * Cc[b][si] : s_lo, sh = rj ? s_hi * Cc[b][sj] : s_hi;
+                const double apq = (sl * sh) * v;
+                nx_fl = pair_decision_eager(app, aqq, apq, trig_n ? -1 : 1, tol, nx_t, nx_c, nx_qv);
+                nx_apq = apq;
             }
         } else {
-            const int mt = LA ? tid - 32 : tid;
             // the column mix on every held row of A (and of W): a thread keeps
             // one pair (its rotation in registers) and walks rows
             auto col_mix = [&](bool with_w) {
@@ -928,7 +1044,7 @@ k_solve_ring(const double *__restrict__ part, int nsplit, int full_part, double 
                 const int j = mt % h;
                 if (!(Fl[b][j] & 1)) return;
                 const int p = cur[j].x, q = cur[j].y;
-                const double t = T[b][j], c = Cc[b][j], ht = (sg[p] == sg[q]) ? -t : t;
+                const double al = Al[j], be = Be[j];
                 const int nrows = 2 * P + (with_w ? RW : 0);
                 for (int r = mt / h; r < nrows; r += kMixThreads / h) {
                     double *row;
@@ -939,8 +1055,8 @@ k_solve_ring(const double *__restrict__ part, int nsplit, int full_part, double 
                         row = Wl + (r - 2 * P) * NN;
                     }
                     const double a = row[p], bb = row[q];
-                    row[p] = fma(ht, bb, a) * c;
-                    row[q] = fma(t, a, bb) * c;
+                    row[p] = fma(al, bb, a);
+                    row[q] = fma(be, a, bb);
                 }
             };
             // the row mix of every owned slot's pair, every column; with W,
@@ -951,24 +1067,24 @@ k_solve_ring(const double *__restrict__ part, int nsplit, int full_part, double 
                 const int kl = mt / TP, k = k0 + kl;
                 if (Fl[b][k] & 1) {
                     const int4 e = cur[k];
-                    const double t = T[b][k], c = Cc[b][k], ht = (sg[e.x] == sg[e.y]) ? -t : t;
+                    const double al = Al[k], be = Be[k];
                     double *rp = pool + ring_buf_lo(e) * NN, *rq = pool + ring_buf_hi(e) * NN;
                     for (int y = mt % TP; y < NN; y += TP) {
                         const double a = rp[y], bb = rq[y];
-                        rp[y] = fma(ht, bb, a) * c;
-                        rq[y] = fma(t, a, bb) * c;
+                        rp[y] = fma(al, bb, a);
+                        rq[y] = fma(be, a, bb);
                     }
                 }
                 if (!with_w) return;
                 const int j = mt % h;
                 if (!(Fl[b][j] & 1)) return;
                 const int pw = cur[j].x, qw = cur[j].y;
-                const double t = T[b][j], c = Cc[b][j], ht = (sg[pw] == sg[qw]) ? -t : t;
+                const double al = Al[j], be = Be[j];
                 for (int x = mt / h; x < RW; x += kMixThreads / h) {
                     double *row = Wl + x * NN;
                     const double a = row[pw], bb = row[qw];
-                    row[pw] = fma(ht, bb, a) * c;
-                    row[qw] = fma(t, a, bb) * c;
+                    row[pw] = fma(al, bb, a);
+                    row[qw] = fma(be, a, bb);
                 }
             };
             if ((s & 1) == 0) {
@@ -981,21 +1097,27 @@ k_solve_ring(const double *__restrict__ part, int nsplit, int full_part, double 
                 col_mix(false);
             }
             mix_sync<LA>(kMixThreads);
-            // Eq. 2.6 on the replicated diagonal, and the owned pairs' own entries
+            // Eq. 2.6 on the replicated diagonal, the owned pairs' own stored
+            // entries to 0, and the new scales of the rotated rows
             if (mt < h && (Fl[b][mt] & 1)) {
                 const int4 e = cur[mt];
                 const int p = e.x, q = e.y;
                 const double t = T[b][mt], ht = (sg[p] == sg[q]) ? -t : t, apq = Apq[b][mt];
-                const double dp = fma(ht, apq, D[p]), dq = fma(t, apq, D[q]);
-                D[p] = dp;
-                D[q] = dq;
+                D[p] = fma(ht, apq, D[p]);
+                D[q] = fma(t, apq, D[q]);
                 if (mt >= k0 && mt < k0 + P) {
                     double *rp = pool + ring_buf_lo(e) * NN, *rq = pool + ring_buf_hi(e) * NN;
-                    rp[p] = dp;
+                    rp[p] = 0.0;
                     rp[q] = 0.0;
-                    rq[q] = dq;
+                    rq[q] = 0.0;
                     rq[p] = 0.0;
                 }
+                const double c = Cc[b][mt], qv = Qv[b][mt];
+                Sc[p] = Sc[p] * c;
+                Sc[q] = Sc[q] * c;
+                Rc[p] = Rc[p] * qv;
+                Rc[q] = Rc[q] * qv;
+                if (scale_out_of_range(Sc[p]) || scale_out_of_range(Sc[q])) s_renorm = 1;
             }
         }
         __syncthreads();
@@ -1019,13 +1141,13 @@ k_solve_ring(const double *__restrict__ part, int nsplit, int full_part, double 
                 const int4 e = nxt[k];
                 const int4 fl = cur[(e.w & 1) ? (k + h - 1) % h : k];
                 const int bf = fl.x == e.x ? ring_buf_lo(fl) : ring_buf_hi(fl);
-                const double apq = pool[bf * NN + e.y];
+                const double apq = (Sc[e.x] * Sc[e.y]) * pool[bf * NN + e.y];
                 const int hyp = (sg[e.x] == sg[e.y]) ? -1 : 1;
-                double t, c;
-                const int fd = pair_decision(D[e.x], D[e.y], apq, hyp, tol, t, c);
-                put_params(s + 1, k, t, c, apq, fd);
+                double t, c, qv;
+                const int fd = pair_decision(D[e.x], D[e.y], apq, hyp, tol, t, c, qv);
+                put_params(s + 1, k, t, c, qv, apq, fd);
             }
-            if (ahead) put_params(s + 1, (k0 + lane) % h, nx_t, nx_c, nx_apq, nx_fl);
+            if (ahead) put_params(s + 1, (k0 + lane) % h, nx_t, nx_c, nx_qv, nx_apq, nx_fl);
             // the table row of step s + 2 into the slot of step s - 1
             if (s + 2 < NN)
                 for (int e = tid; e < h; e += kT) tb[(s + 2) % 3][e] = ring[(size_t)(s + 2) * h + e];
@@ -1036,17 +1158,18 @@ k_solve_ring(const double *__restrict__ part, int nsplit, int full_part, double 
     double *wo = Wout + (size_t)pair * NN * NN;
     for (int e = tid; e < RW * NN; e += kT) {
         const int x = e / NN, y = e % NN;
-        wo[(w0 + x) + (size_t)y * NN] = Wl[x * NN + y];
+        wo[(w0 + x) + (size_t)y * NN] = Wl[x * NN + y] * Sc[y];
     }
     if (!part) {
-        // the rows of the owned slots where the pass ended
+        // the rows of the owned slots where the pass ended: true values
+        // (s_x s_y) S_xy, the diagonal from D
         double *ao = A_io + (size_t)pair * NN * NN;
         const int4 *at = tb[s_end % 3];
         for (int e = tid; e < 2 * P * NN; e += kT) {
             const int r = e / NN, y = e % NN;
             const int4 t = at[k0 + (r >> 1)];
             const int x = (r & 1) ? t.y : t.x, bf = (r & 1) ? ring_buf_hi(t) : ring_buf_lo(t);
-            ao[x + (size_t)y * NN] = pool[bf * NN + y];
+            ao[x + (size_t)y * NN] = x == y ? D[x] : (Sc[x] * Sc[y]) * pool[bf * NN + y];
         }
     }
     cluster.sync();

@@ -298,6 +298,32 @@ def test_kernel_inner_solve_matches_model(api, b, mode):
         assert np.array_equal(Ao[k], Ar), np.max(np.abs(Ao[k] - Ar))
 
 
+@pytest.mark.parametrize("b,mode", [(64, 0), (64, 1), (64, 2), (32, 0)])
+def test_kernel_inner_solve_renormalising_blocks_match_model(api, b, mode):
+    """Ungraded pivot blocks (P^T P, P standard normal): the large early
+    rotations move the column scales of the scaled rotations out of
+    [2^-8, 2^8] (at b = 64 the model renormalises five times in full-block mode
+    and once in one full pass on these seeds), so the kernels' renormalisation
+    is exercised; kernel and model agree bit for bit."""
+    from oracle import inner_model
+
+    nn = 2 * b
+    rng = np.random.default_rng(7 + b)
+    As, sg = [], []
+    for trial in range(3):
+        P = rng.standard_normal((nn, nn))
+        As.append(P.T @ P)
+        sg.append(W.signs_block(nn, [nn, nn // 2, 3][trial]))
+    As, sg = np.stack(As), np.stack(sg)
+    tol = nn * U64
+    Ao, Wg, rot = _gpu_inner(api, As, sg, tol, mode)
+    for k in range(As.shape[0]):
+        Ar, Wr, nrot, passes, s = inner_model.inner_solve(As[k], sg[k], tol, mode=mode, max_passes=10)
+        assert s == 0 and nrot == rot[k]
+        assert np.array_equal(Wg[k], Wr), np.max(np.abs(Wg[k] - Wr))
+        assert np.array_equal(Ao[k], Ar), np.max(np.abs(Ao[k] - Ar))
+
+
 @pytest.mark.parametrize("b", [16, 32, 64])
 def test_ring_full_pass_equals_transposing_pass(api, b):
     """The full pass on the ring of slots (mode 2, rows moving one slot per
