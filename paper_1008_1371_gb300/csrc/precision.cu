@@ -288,28 +288,41 @@ k_gram_x(const double *__restrict__ G, int64_t rows, int64_t ldg, const int *__r
 // ---------------------------------------------------------------- W' slices
 // The A operand of the transposed update, W'^T (128 x 128, K-major), for G rows
 // (W' = D W_P) and for V rows (W' = W_P), in four k quarters of 32, with
-// per-column exponents F_j.  Eight CTAs per rotated pair: CTA (which, quarter)
-// forms one 128 x 32 tile of slices; every CTA derives the exponents F_j of its
-// `which` itself (the same operations, the same values).
+// per-column exponents F_j.  A cluster of eight CTAs per rotated pair: CTA
+// (which, quarter) forms one 128 x 32 tile of slices.  The column exponents of
+// both kinds are formed once per pair, each CTA taking 16 columns and writing
+// them into every CTA of the cluster.
 // wsl layout: [pair][which][quarter][slice][128 x 32 core-matrix tile]
-__global__ void __launch_bounds__(kThrX)
+__global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(kThrX)
 k_wprep_x(const double *__restrict__ Wp, const int *__restrict__ dexp, const int *__restrict__ rotated,
           uint16_t *__restrict__ wsl, int *__restrict__ wexp, unsigned long long *__restrict__ upd_count) {
-    const int pair = blockIdx.x >> 3, which = (blockIdx.x >> 2) & 1, q = blockIdx.x & 3;
+    const int pair = blockIdx.x >> 3;
+    const int rank = (int)cluster_rank(), which = (rank >> 2) & 1, q = rank & 3;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (!rotated[pair]) return;
-    if (tid == 0 && upd_count && blockIdx.x % 8 == 0) atomicAdd(upd_count, 1ull);
-    __shared__ int dk[NNX], F[NNX];
+    if (!rotated[pair]) return;  // the whole cluster leaves together
+    if (tid == 0 && upd_count && rank == 0) atomicAdd(upd_count, 1ull);
+    __shared__ int dg[NNX], Fk[2][NNX];
     const double *W = Wp + (size_t)pair * NNX * NNX;  // W(k, j) at k + j * 128
-    for (int k = tid; k < NNX; k += kThrX) dk[k] = which == 0 ? dexp[(size_t)pair * NNX + k] : 0;
-    __syncthreads();
-    for (int j = warp; j < NNX; j += kThrX / 32) {
-        int e0 = -2000;
-        for (int k = lane; k < NNX; k += 32) e0 = max(e0, exp_bound(W[k + (size_t)j * NNX]) + dk[k]);
-        e0 = warp_max_i(e0);
-        if (lane == 0) F[j] = e0 < -1000 ? 0 : e0;
+    for (int k = tid; k < NNX; k += kThrX) dg[k] = dexp[(size_t)pair * NNX + k];
+    cluster_sync();  // every CTA running before any remote write
+    // columns [16 rank, 16 rank + 16): F_j for G rows (with d_k) and for V rows
+    for (int j = NNX / 8 * rank + warp; j < NNX / 8 * (rank + 1); j += kThrX / 32) {
+        int eg = -2000, ev = -2000;
+        for (int k = lane; k < NNX; k += 32) {
+            const int e = exp_bound(W[k + (size_t)j * NNX]);
+            eg = max(eg, e + dg[k]);
+            ev = max(ev, e);
+        }
+        eg = warp_max_i(eg);
+        ev = warp_max_i(ev);
+        if (lane < 8) {
+            const int fg = eg < -1000 ? 0 : eg, fv = ev < -1000 ? 0 : ev;
+            st_cluster_s32(map_peer(smem_addr(&Fk[0][j]), (uint32_t)lane), fg);
+            st_cluster_s32(map_peer(smem_addr(&Fk[1][j]), (uint32_t)lane), fv);
+        }
     }
-    __syncthreads();
+    cluster_sync();
+    const int *F = Fk[which];
     if (q == 0)
         for (int j = tid; j < NNX; j += kThrX) wexp[((size_t)pair * 2 + which) * NNX + j] = F[j];
     constexpr size_t kTile = (size_t)NNX * kUpdKT;  // elements per slice tile
@@ -320,9 +333,10 @@ k_wprep_x(const double *__restrict__ Wp, const int *__restrict__ dexp, const int
     for (int core = warp; core < (NNX / 8) * (kUpdKT / 8); core += kThrX / 32) {
         const int j = (core / (kUpdKT / 8)) * 8 + jj, kk = (core % (kUpdKT / 8)) * 8 + kp;
         const int k = q * kUpdKT + kk;
+        const int dk0 = which == 0 ? dg[k] : 0, dk1 = which == 0 ? dg[k + 1] : 0;
         const double w0 = W[k + (size_t)j * NNX], w1 = W[k + 1 + (size_t)j * NNX];
-        const long long d0 = digit_word(w0, F[j] - dk[k]);
-        const long long d1 = digit_word(w1, F[j] - dk[k + 1]);
+        const long long d0 = digit_word(w0, F[j] - dk0);
+        const long long d1 = digit_word(w1, F[j] - dk1);
         const uint32_t off = core_offset(j, kk, kUpdKT) >> 1;
         uint32_t sw[kSlices];
         slice_pairs8(d0, d1, sw);
