@@ -123,14 +123,13 @@ __device__ __forceinline__ void read_accs(uint32_t tmem, int lane_base, int c0, 
 // barriers and the kernel reports HSVD_ERR_CUDA.
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThrG, 1)
 k_gram_x(const double *__restrict__ G, int64_t rows, int64_t ldg, const int *__restrict__ col0, int ksplit,
-         double *__restrict__ part, int *__restrict__ status) {
+         double *__restrict__ part, int *__restrict__ status, int ahead) {
     extern __shared__ __align__(1024) unsigned char smem[];
     constexpr uint32_t kSliceBytes = NNX * kGramKT * 2;     // one slice of a tile, all columns (8 KB)
     constexpr uint32_t kHalfBytes = kN * kGramKT * 2;       // one slice, this CTA's columns (4 KB)
     constexpr uint32_t kBOff = kSlices * kSliceBytes;       // the B copy after the A slices
     constexpr uint32_t kBufBytes = kBOff + kSlices * kHalfBytes;  // one tile (96 KB)
     constexpr int kProd = kThrG - 32;                       // splitting threads (warps 1..16)
-    constexpr int kProdWarps = kProd / 32;
     __shared__ int Ecol[NNX];
     __shared__ __align__(8) uint64_t full[kGramBufs], empty[kGramBufs];
     __shared__ uint32_t tbase;
@@ -181,57 +180,67 @@ k_gram_x(const double *__restrict__ G, int64_t rows, int64_t ldg, const int *__r
     };
     if (warp > 0) {
         // ------------------------------------------------ splitters
-        // a warp writes one 8 x 8 core matrix per step: lane -> column
-        // (lane >> 2) of the group, rows 2 (lane & 3) and 2 (lane & 3) + 1
-        const int pw = warp - 1, ptid = tid - 32;
-        const int cc = lane >> 2, kp = 2 * (lane & 3), cbase = kN * (int)half;
-        constexpr int kCoresPerWarp = (kN / 8) * (kGramKT / 8) / kProdWarps;
-        static_assert(kCoresPerWarp * kProdWarps == (kN / 8) * (kGramKT / 8), "Gram split mapping");
-        auto load_tile = [&](int t, double (&x)[kCoresPerWarp][2]) {
-            const int64_t t0 = r0 + (int64_t)t * kGramKT;
+        // a thread splits four consecutive rows of one column per tile: warp
+        // (8 column groups x 2 halves of the tile's 32 rows), lane -> column
+        // (lane >> 2) of the group and rows 4 (lane & 3) .. + 3 of the half;
+        // each slice is one 8-byte store (two adjacent words of a core row)
+        const int pw = warp - 1, ptid = tid - 32, cbase = kN * (int)half;
+        static_assert(kProd == kN * (kGramKT / 4), "one row quad of one column per thread");
+        const int c = cbase + (pw >> 1) * 8 + (lane >> 2), k = (pw & 1) * 16 + 4 * (lane & 3);
+        const double *gcol = colptr(c);
+        const uint32_t off = core_offset(c, k, kGramKT), offb = kBOff + core_offset(c - cbase, k, kGramKT);
+        auto load_tile = [&](int t, double (&x)[4]) {
+            const int64_t row = r0 + (int64_t)t * kGramKT + k;
 #pragma unroll
-            for (int ci = 0; ci < kCoresPerWarp; ++ci) {
-                const int core = pw + ci * kProdWarps;
-                const int c = cbase + (core / (kGramKT / 8)) * 8 + cc, k = (core % (kGramKT / 8)) * 8 + kp;
-                const double *g = colptr(c);
-                const int64_t row = t0 + k;
-                x[ci][0] = row < r1 ? g[row] : 0.0;
-                x[ci][1] = row + 1 < r1 ? g[row + 1] : 0.0;
-            }
+            for (int u = 0; u < 4; ++u) x[u] = row + u < r1 ? gcol[row + u] : 0.0;
         };
-        double cur[kCoresPerWarp][2];
+        double cur[4];
         if (ntiles > 0) load_tile(0, cur);
+        // the panel of the CTA `ahead` blocks later (the next wave's CTA in the
+        // same place) into L2, a few lines per tile, so that its column
+        // exponents and tiles read L2 rather than DRAM
+        const int nblk = (int)blockIdx.x + ahead;
+        const double *pf_col = nullptr;
+        int64_t pf_r0 = 0, pf_r1 = 0;
+        if (ahead > 0 && nblk < (int)gridDim.x) {
+            const int npair = (nblk >> 1) / ksplit, nsplit_i = (nblk >> 1) % ksplit, nh = nblk & 1;
+            const int cc2 = kN * nh + ptid % kN;
+            const int ci2 = col0[2 * npair], cj2 = col0[2 * npair + 1];
+            pf_col = G + (int64_t)(cc2 < NNX / 2 ? ci2 + cc2 : cj2 + cc2 - NNX / 2) * ldg;
+            pf_r0 = (int64_t)nsplit_i * kGramK;
+            pf_r1 = min(rows, pf_r0 + kGramK);
+        }
         for (int t = 0; t < ntiles; ++t) {
             const int b = t % kGramBufs;
+            if (pf_col) {  // 512 threads x one 128-byte line per tile: 64 columns x 8 lines per tile
+                const int64_t row = pf_r0 + ((int64_t)t * (kProd / kN) + ptid / kN) * 16;
+                if (row < pf_r1) prefetch_l2(pf_col + row);
+            }
             // the products of tile t - kGramBufs read buffer b
             if (ptid == 0 && t >= kGramBufs) wait1(&empty[b], t - kGramBufs);
             bar_named(1, kProd);
             if (!s_fail) {
                 unsigned char *buf = smem + (uint32_t)b * kBufBytes;
+                const int e = Ecol[c];
+                uint32_t s01[kSlices], s23[kSlices];
+                slice_pairs8(digit_word(cur[0], e), digit_word(cur[1], e), s01);
+                slice_pairs8(digit_word(cur[2], e), digit_word(cur[3], e), s23);
 #pragma unroll
-                for (int ci = 0; ci < kCoresPerWarp; ++ci) {
-                    const int core = pw + ci * kProdWarps;
-                    const int c = cbase + (core / (kGramKT / 8)) * 8 + cc, k = (core % (kGramKT / 8)) * 8 + kp;
-                    const long long w0 = digit_word(cur[ci][0], Ecol[c]), w1 = digit_word(cur[ci][1], Ecol[c]);
-                    const uint32_t off = core_offset(c, k, kGramKT), offb = kBOff + core_offset(c - cbase, k, kGramKT);
-                    uint32_t sw[kSlices];
-                    slice_pairs8(w0, w1, sw);
-#pragma unroll
-                    for (int sl = 0; sl < kSlices; ++sl) {
-                        *reinterpret_cast<uint32_t *>(buf + off + (uint32_t)sl * kSliceBytes) = sw[sl];
-                        *reinterpret_cast<uint32_t *>(buf + offb + (uint32_t)sl * kHalfBytes) = sw[sl];
-                    }
+                for (int sl = 0; sl < kSlices; ++sl) {
+                    const uint2 v = make_uint2(s01[sl], s23[sl]);
+                    *reinterpret_cast<uint2 *>(buf + off + (uint32_t)sl * kSliceBytes) = v;
+                    *reinterpret_cast<uint2 *>(buf + offb + (uint32_t)sl * kHalfBytes) = v;
                 }
             }
             fence_proxy_async();
             bar_named(1, kProd);
-            if (ptid == 0 && !s_fail) {
-                // the own columns of every A slice (4 KB each) into the peer's buffer
-                const uint32_t lbuf = smem_addr(smem) + (uint32_t)b * kBufBytes + (uint32_t)half * kHalfBytes;
-                const uint32_t pbuf = map_peer(lbuf, peer), pfull = map_peer(smem_addr(&full[b]), peer);
-                for (int sl = 0; sl < kSlices; ++sl)
-                    bulk_s2peer(pbuf + (uint32_t)sl * kSliceBytes, lbuf + (uint32_t)sl * kSliceBytes, kHalfBytes, pfull);
-                mbar_expect_tx(&full[b], kSlices * kHalfBytes);  // own arrival; the peer's part is due
+            if (ptid < kSlices && !s_fail) {
+                // the own columns of every A slice (4 KB each) into the peer's
+                // buffer, one copy per lane; lane 0 arrives expecting the peer's part
+                const uint32_t lsrc = smem_addr(smem) + (uint32_t)b * kBufBytes + (uint32_t)half * kHalfBytes +
+                                      (uint32_t)ptid * kSliceBytes;
+                bulk_s2peer(map_peer(lsrc, peer), lsrc, kHalfBytes, map_peer(smem_addr(&full[b]), peer));
+                if (ptid == 0) mbar_expect_tx(&full[b], kSlices * kHalfBytes);
             }
             if (t + 1 < ntiles) load_tile(t + 1, cur);
         }
@@ -656,7 +665,12 @@ cudaError_t launch_gram_x(const double *G, int64_t rows, int64_t ldg, int npairs
     const size_t smem = (size_t)kGramBufs * kSlices * (NNX + kN) * kGramKT * 2;
     cudaError_t e = cudaFuncSetAttribute(k_gram_x, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_gram_x<<<npairs * ksplit * 2, kThrG, smem, st>>>(G, rows, ldg, col0, ksplit, part, status);
+    // one CTA per SM: the CTA an SM count later runs in the next wave
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int ahead = sms & ~1;
+    k_gram_x<<<npairs * ksplit * 2, kThrG, smem, st>>>(G, rows, ldg, col0, ksplit, part, status, ahead);
     return cudaGetLastError();
 }
 
