@@ -123,7 +123,7 @@ def parse():
                     help="tangent-threshold early stop (Sec. 2): 0 off, negative = the paper's T_eps = 2^-27; "
                          "the effective flop count then uses the plain run's sweeps")
     ap.add_argument("--schedule", default="auto", choices=["auto", "steps", "pairs"],
-                    help="sweep schedule of the blocked method (auto: the library's choice, pairs for FP64 products, steps for split precision)")
+                    help="sweep schedule of the blocked method (auto: the library's choice, the pair schedule)")
     ap.add_argument("--tol", type=float, default=0.0,
                     help="eps of Eq. 2.3 (0: n 2^-53; the paper's own is 2^-52)")
     ap.add_argument("--probe-rates", action="store_true",

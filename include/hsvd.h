@@ -72,8 +72,7 @@ extern "C" {
 /* Schedule of a sweep of the blocked method.  Either way a sweep is one CUDA
  * graph and every visit does the same arithmetic, so the results are the same
  * bit for bit. */
-#define HSVD_SCHEDULE_AUTO 0  /* pairs for FP64 products, steps for split precision
-                                 or with opts.profile                               */
+#define HSVD_SCHEDULE_AUTO 0  /* pairs, or steps with opts.profile                 */
 #define HSVD_SCHEDULE_STEPS 1 /* the steps of the pivot strategy one after the other:
                                  Gram of all pairs, inner solves, updates            */
 #define HSVD_SCHEDULE_PAIRS 2 /* every block-pair visit on its own: its Gram waits

@@ -197,12 +197,11 @@ int solve_blocked_core(const double *G, int64_t m, int64_t n, int64_t ldg, const
     // The pair schedule runs visits of up to kRing consecutive steps at once:
     // every visit slot (Gram partials, W_P, flags) exists once per step of the
     // ring.  The step schedule needs one per pair.  Measured (graded factors,
-    // FP64): 9.5% faster at n = 1024, b = 32, 2.4% at n = 2048; the split-
-    // precision kernels are throughput-bound and lose 3-6% to the overlap at
-    // n = 4096, so automatic choice takes the pair schedule for FP64 only.
+    // FP64): 9.5% faster at n = 1024, b = 32, 2.4% at n = 2048; split precision
+    // at Haar 4096: 1.1% faster (1426 against 1442 ms per HSVD).  Automatic
+    // choice takes it unless the call profiles its kernels one by one.
     const bool pair_sched =
-        o.schedule == HSVD_SCHEDULE_PAIRS ||
-        (o.schedule == HSVD_SCHEDULE_AUTO && !o.profile && o.precision == HSVD_PRECISION_FP64);
+        o.schedule == HSVD_SCHEDULE_PAIRS || (o.schedule == HSVD_SCHEDULE_AUTO && !o.profile);
     const int nslot = pair_sched ? kRing * npairs : npairs;
     GraphGuard gg;
     DagStreams dag;
