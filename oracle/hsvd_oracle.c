@@ -127,6 +127,22 @@ static int conv_code(double t, double tstop)
 /* The rotation applied to a column pair is                                   */
 /*   g_i' = (g_i + hyp*t*g_j) * c,   g_j' = (t*g_i + g_j) * c   (Alg. 4.5).   */
 /* ------------------------------------------------------------------------ */
+/* c = 1/sqrt(1 - hyp t^2) to about half a unit in the last place, from an
+ * estimate c0: one Newton step on c^2 (1 - hyp t^2) = 1 whose residual is
+ * formed from t itself, (1 - c0^2) + hyp (c0 t)^2, by fused multiply-adds.
+ * 1/sqrt(x) with x = 1 - hyp t^2 rounded first, as two correctly rounded
+ * operations, leans upward for small t: c^2 (1 - hyp t^2) - 1 averages about
+ * +u over the rotations with t^2 between u and 2^-30 (the rounding of x
+ * before the square root, and the square root's before the division).  A
+ * column takes about 10^5 rotations at n = 4096, and that bias became a
+ * relative +1.2e-12 on every large sigma, measured against LAPACK's
+ * eigenvalues of the pencil (G^T G, J). */
+static double orc_cosine(double t, int hyp, double c0)
+{
+    const double s = c0 * t;
+    return fma(0.5 * c0, fma(hyp < 0 ? -s : s, s, fma(-c0, c0, 1.0)), c0);
+}
+
 int orc_rotation(double aii, double ajj, double aij, int hyp, double *t, double *c)
 {
     double zeta, tt;
@@ -135,7 +151,7 @@ int orc_rotation(double aii, double ajj, double aij, int hyp, double *t, double 
         tt = 1.0 / (fabs(zeta) + sqrt(zeta * zeta + 1.0));
         if (zeta < 0.0) tt = -tt;
         *t = tt;
-        *c = 1.0 / sqrt(1.0 + tt * tt);
+        *c = orc_cosine(tt, -1, 1.0 / sqrt(1.0 + tt * tt));
         return ORC_OK;
     }
     zeta = -(aii + ajj) / (2.0 * aij);
@@ -147,7 +163,7 @@ int orc_rotation(double aii, double ajj, double aij, int hyp, double *t, double 
     tt = 1.0 / (fabs(zeta) + sqrt(zeta * zeta - 1.0));
     if (zeta < 0.0) tt = -tt;
     *t = tt;
-    *c = 1.0 / sqrt((1.0 - tt) * (1.0 + tt));
+    *c = orc_cosine(tt, 1, 1.0 / sqrt((1.0 - tt) * (1.0 + tt)));
     return ORC_OK;
 }
 

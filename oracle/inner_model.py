@@ -39,3 +39,18 @@ def inner_solve(A, sgn, tol, mode=0, max_passes=8, lib=None, want_tmax=False):
     if want_tmax:
         return A, W, nrot.value, passes.value, st, tmax.value
     return A, W, nrot.value, passes.value, st
+
+
+def rotation(aii, ajj, aij, hyp, lib=None):
+    """The model's rotation of one pair that fails Eq. 2.3 (reading M5 of
+    inner_model.c): (t, c, q = 1/c, status), status nonzero for a
+    rank-deficient hyperbolic pair."""
+    lib = lib or _load()
+    f = lib.mdl_rotation
+    if not getattr(f, "_bound", False):
+        f.argtypes = [_dbl, _dbl, _dbl, _int, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl), ctypes.POINTER(_dbl)]
+        f.restype = _int
+        f._bound = True
+    t, c, q = _dbl(), _dbl(), _dbl()
+    st = f(float(aii), float(ajj), float(aij), int(hyp), ctypes.byref(t), ctypes.byref(c), ctypes.byref(q))
+    return t.value, c.value, q.value, st

@@ -18,11 +18,74 @@ namespace hsvd {
 
 constexpr int kWarp = 32;
 
+
+// Bit-level conversions (integer operations only, no floating-point
+// instruction) for the rotation parameters below.
+// Unbiased binary exponent field of x (-1023 for 0 and subnormals, 1024 for
+// infinities and NaN).
+__device__ __forceinline__ int exp_field(double x) { return ((__double2hiint(x) >> 20) & 0x7ff) - 1023; }
+// x 2^-e rounded toward zero to single precision; x normal and x 2^-e in the
+// normal single range (the caller checks both).
+__device__ __forceinline__ float f32_scaled(double x, int e) {
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned ex = (unsigned)((int)((hi >> 20) & 0x7ff) - 1023 - e + 127);
+    return __uint_as_float((hi & 0x80000000u) | (ex << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+}
+// f 2^e exactly in double precision; f a normal single, the result normal.
+__device__ __forceinline__ double f64_scaled(float f, int e) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned ex = (unsigned)((int)((b >> 23) & 0xff) - 127 + e + 1023);
+    return __hiloint2double((int)((b & 0x80000000u) | (ex << 20) | ((b & 0x7fffffu) >> 3)), (int)(b << 29));
+}
+__device__ __forceinline__ double neg_bits(double x) {
+    return __hiloint2double(__double2hiint(x) ^ (int)0x80000000u, __double2loint(x));
+}
+
 // Relative orthogonality test (Eq. 2.3): a pair is left alone when
 // |a_ij| < tol sqrt(a_ii a_jj), and also when a_ij == 0 exactly (exactly
 // orthogonal columns, e.g. a zero or bordering column, are never rotated).
+// The same decision as that expression, with few double-precision
+// instructions: where all four operands are normal with binary exponents in
+// +-500 (+-200 for tol) and a_ii, a_jj > 0, the ratio r = a_ij^2 /
+// (tol^2 a_ii a_jj) is estimated from the exponents and the 23-bit truncated
+// mantissas (relative error below 2^-20) and decides whenever it is outside
+// 1 +- 2^-16; the expression's three roundings move its threshold by less
+// than 2^-51, so both agree there.  Every other case evaluates the
+// expression.
 __device__ __forceinline__ bool pair_passes(double aii, double ajj, double aij, double tol) {
+    const unsigned ha = (unsigned)__double2hiint(aij) & 0x7fffffffu, h1 = (unsigned)__double2hiint(aii),
+                   h2 = (unsigned)__double2hiint(ajj), ht = (unsigned)__double2hiint(tol);
+    const int ea = (int)(ha >> 20) - 1023, e1 = (int)(h1 >> 20) - 1023, e2 = (int)(h2 >> 20) - 1023,
+              et = (int)(ht >> 20) - 1023;  // a_ii, a_jj, tol: the sign bit makes these out of range
+    if (ea >= -500 && ea <= 500 && e1 >= -500 && e1 <= 500 && e2 >= -500 && e2 <= 500 && et >= -200 && et <= 200) {
+        const int k = 2 * ea - 2 * et - e1 - e2;
+        if (k >= 5) return false;
+        if (k <= -3) return true;
+        const float ma = f32_scaled(aij, ea), m1 = f32_scaled(aii, e1), m2 = f32_scaled(ajj, e2),
+                    mt = f32_scaled(tol, et);
+        const float lm = __fmul_rn(__fmul_rn(ma, ma), __int_as_float((127 + k) << 23));
+        const float rm = __fmul_rn(__fmul_rn(mt, mt), __fmul_rn(m1, m2));
+        if (lm < __fmul_rn(rm, 1.0f - 1.52587890625e-05f)) return true;
+        if (lm > __fmul_rn(rm, 1.0f + 1.52587890625e-05f)) return false;
+    }
     return aij == 0.0 || fabs(aij) < tol * sqrt(aii * ajj);
+}
+
+// c = 1/sqrt(1 - hyp t^2) to about half an ulp from an estimate c0: one
+// Newton step on c^2 (1 - hyp t^2) = 1 whose residual (1 - c0^2) + hyp (c0 t)^2
+// is formed from t itself by FMAs.  1/sqrt(x) with x = 1 - hyp t^2 rounded
+// first, as two correctly rounded operations, leans upward for small t
+// (c^2 (1 - hyp t^2) - 1 averages about +u for t^2 between u and 2^-30), a
+// bias that about 10^5 rotations per column at n = 4096 turned into a
+// relative +1.2e-12 on the large sigma.
+__device__ __forceinline__ double cosine_step(double t, int hyp, double c0) {
+    const double s = c0 * t;
+    return fma(0.5 * c0, fma(hyp < 0 ? neg_bits(s) : s, s, fma(neg_bits(c0), c0, 1.0)), c0);
+}
+// qv = 1/c from an estimate q0 by one Newton step, so that c qv - 1 is an
+// unbiased rounding error (the scaled inner solve multiplies by c and by qv)
+__device__ __forceinline__ double reciprocal_step(double c, double q0) {
+    return fma(q0, fma(neg_bits(c), q0, 1.0), q0);
 }
 
 // Rotation annihilating a_ij (Sec. 2, Eq. 2.2).  hyp = -1 trigonometric
@@ -36,7 +99,8 @@ __device__ __forceinline__ bool pair_passes(double aii, double ajj, double aij, 
 //         c = 1/sqrt((1 - t)(1 + t))
 // sign(0) = +1.  Returns false (t = 0, c = 1) when a hyperbolic pair has
 // |zeta| <= 1: no J-unitary rotation exists, the pair is rank deficient.
-// qv = 1/c as computed before the division (the scaled inner solve keeps it).
+// c by cosine_step, qv = 1/c by reciprocal_step (the scaled inner solve keeps
+// qv).
 __device__ __forceinline__ bool rotation_params(double aii, double ajj, double aij, int hyp,
                                                 double &t, double &c, double &qv) {
     if (hyp < 0) {
@@ -44,8 +108,9 @@ __device__ __forceinline__ bool rotation_params(double aii, double ajj, double a
         double tt = 1.0 / (fabs(zeta) + sqrt(zeta * zeta + 1.0));
         if (zeta < 0.0) tt = -tt;
         t = tt;
-        qv = sqrt(1.0 + tt * tt);
-        c = 1.0 / qv;
+        const double q0 = sqrt(1.0 + tt * tt);
+        c = cosine_step(tt, hyp, 1.0 / q0);
+        qv = reciprocal_step(c, q0);
         return true;
     }
     const double zeta = -(aii + ajj) / (2.0 * aij);
@@ -58,8 +123,9 @@ __device__ __forceinline__ bool rotation_params(double aii, double ajj, double a
     double tt = 1.0 / (fabs(zeta) + sqrt(zeta * zeta - 1.0));
     if (zeta < 0.0) tt = -tt;
     t = tt;
-    qv = sqrt((1.0 - tt) * (1.0 + tt));
-    c = 1.0 / qv;
+    const double q0 = sqrt((1.0 - tt) * (1.0 + tt));
+    c = cosine_step(tt, hyp, 1.0 / q0);
+    qv = reciprocal_step(c, q0);
     return true;
 }
 
@@ -86,20 +152,77 @@ __device__ __forceinline__ int pair_decision(double aii, double ajj, double aij,
     return pair_decision(aii, ajj, aij, hyp, tol, t, c, qv);
 }
 
-// The same decision with the test and the rotation evaluated side by side
-// (their square roots and divides overlap, the rotation is discarded when the
-// pair passes): for a thread whose chain is the critical path whatever the
-// outcome (the look-ahead warp of the cross pass).  Same results.
-__device__ __forceinline__ int pair_decision_eager(double aii, double ajj, double aij, int hyp, double tol,
-                                                   double &t, double &c, double &qv) {
-    const bool passes = pair_passes(aii, ajj, aij, tol);
-    double tt, cc, qq;
-    const bool ok = rotation_params(aii, ajj, aij, hyp, tt, cc, qq);
+// The rotation of rotation_params with few double-precision instructions.
+// On this part one warp issues a double-precision instruction every 64
+// cycles (a single-precision or integer one every few), and the rotation of
+// the next step is the critical path of the inner solve's steps, so:
+//   - zeta and a first t in single precision, from a_ij and b scaled by
+//     2^-e(a_ij) (b = a_jj - a_ii trigonometric, a_ii + a_jj hyperbolic);
+//   - two Newton steps in double precision on f(t) = a_ij (t^2 + sg) + b t
+//     (sg = -1 trigonometric, +1 hyperbolic: the equation of rotation_params,
+//     whose smaller root is t), with 1/f' from single precision;
+//   - x = 1 - hyp t^2, y = 1/sqrt(x) by one Newton step
+//     y <- y + (y/2)(1 - x y^2) from the single-precision 1/sqrt(x), then c
+//     from y by cosine_step (the residual from t itself) and qv from x c by
+//     reciprocal_step.
+// t and c agree with rotation_params' to a few units in the last place (other
+// bits).  The single-precision start needs a_ij normal with |e(a_ij)| < 800,
+// b = 0 (trigonometric only) or normal with 2^-100 <= |b / a_ij| < 2^101, and
+// a hyperbolic pair with |zeta| >= 2 (|b| >= 4 |a_ij|, which also settles the
+// rank test); every other pair takes rotation_params.
+__device__ __forceinline__ bool rotation_params_fast(double aii, double ajj, double aij, int hyp, double &t,
+                                                     double &c, double &qv) {
+    const bool trig = hyp < 0;
+    const double b = trig ? ajj - aii : aii + ajj;
+    const int E = exp_field(aij), eb = exp_field(b);
+    const unsigned long long abits = (unsigned long long)__double_as_longlong(aij) & 0x7fffffffffffffffull;
+    const unsigned long long bbits = (unsigned long long)__double_as_longlong(b) & 0x7fffffffffffffffull;
+    bool fast = E > -800 && E < 800;
+    if (bbits == 0) fast = fast && trig;
+    else fast = fast && eb > -1023 && eb < 1024 && eb - E >= -100 && eb - E <= 100;
+    if (fast && !trig) fast = bbits >= abits + (2ull << 52);  // |b| >= 4 |a_ij|
+    if (!fast) return rotation_params(aii, ajj, aij, hyp, t, c, qv);
+    const float af = f32_scaled(aij, E);
+    const float bf = bbits == 0 ? 0.0f : f32_scaled(b, E);
+    const float z = __fdiv_rn(trig ? bf : -bf, __fmul_rn(2.0f, af));  // zeta
+    const float az = fabsf(z);
+    float tf;
+    if (az <= 1048576.0f) {
+        const float r = trig ? __fadd_rn(__fmul_rn(az, az), 1.0f) : __fsub_rn(__fmul_rn(az, az), 1.0f);
+        tf = __fdiv_rn(1.0f, __fadd_rn(az, __fsqrt_rn(r)));
+    } else {
+        tf = __fdiv_rn(0.5f, az);
+    }
+    if (z < 0.0f) tf = -tf;
+    // 1/f'(t) 2^E in single precision, f'(t) = 2 a_ij t + b: |f'| >= 2 |a_ij| at the root
+    const float gf = __fdiv_rn(1.0f, __fadd_rn(__fmul_rn(__fmul_rn(2.0f, af), tf), bf));
+    const double ngd = neg_bits(f64_scaled(gf, -E));
+    const double sa = trig ? neg_bits(aij) : aij;
+    double tt = f64_scaled(tf, 0);
+#pragma unroll
+    for (int it = 0; it < 2; ++it) tt = fma(fma(fma(aij, tt, b), tt, sa), ngd, tt);
+    const double x = fma(tt, trig ? tt : neg_bits(tt), 1.0);
+    const float r0 = __fdiv_rn(1.0f, __fsqrt_rn(f32_scaled(x, 0)));
+    double y = f64_scaled(r0, 0);
+    y = fma(f64_scaled(r0, -1), fma(neg_bits(x * y), y, 1.0), y);
+    t = tt;
+    c = cosine_step(tt, hyp, y);
+    qv = reciprocal_step(c, x * c);
+    return true;
+}
+
+// pair_decision with rotation_params_fast: the rotation of the inner-solve
+// kernels of the block method.  Late in the iteration most pairs pass and
+// the rotation is skipped; evaluating it eagerly gains nothing on a warp
+// whose double-precision instructions issue one at a time.
+__device__ __forceinline__ int pair_decision_fast(double aii, double ajj, double aij, int hyp, double tol,
+                                                  double &t, double &c, double &qv) {
     t = 0.0;
     c = 1.0;
     qv = 1.0;
-    if (passes) return 0;
-    if (!ok) return 2;
+    if (pair_passes(aii, ajj, aij, tol)) return 0;
+    double tt, cc, qq;
+    if (!rotation_params_fast(aii, ajj, aij, hyp, tt, cc, qq)) return 2;
     t = tt;
     c = cc;
     qv = qq;
@@ -113,7 +236,9 @@ __device__ __forceinline__ int pair_decision_eager(double aii, double ajj, doubl
 // s <- s c and r <- r qv for p and q.  A scale whose binary exponent leaves
 // [-kScaleExp, kScaleExp] sends the block back to s = r = 1 before the next step.
 constexpr int kScaleExp = 8;
-__device__ __forceinline__ bool scale_out_of_range(double s) { return abs(ilogb(s)) > kScaleExp; }
+// (a scale is a product of cosines and their reciprocals, always normal:
+// its exponent field is ilogb, read with integer operations)
+__device__ __forceinline__ bool scale_out_of_range(double s) { return abs(exp_field(s)) > kScaleExp; }
 
 // k-th pivot pair (a < b) of step `s` of the modified modulus strategy on r
 // indices (Sec. 2): the pairs with a + b = c (mod r), c = (r - 1 + s) mod r,

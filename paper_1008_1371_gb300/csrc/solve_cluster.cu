@@ -212,7 +212,7 @@ k_solve_cluster(const double *__restrict__ part, int nsplit, int full_part, doub
                 const double apq = (Sc[p] * Sc[q]) * Apq[buf][k], app = D[p], aqq = D[q];  // true a_pq
                 const int hyp = (sg[p] == sg[q]) ? -1 : 1;
                 double t, c, qv;
-                const int d = pair_decision(app, aqq, apq, hyp, tol, t, c, qv);
+                const int d = pair_decision_fast(app, aqq, apq, hyp, tol, t, c, qv);
                 const int rot = d == 1;
                 if (d == 2) s_flag = HSVD_ERR_RANK;
                 if (rot && fabs(t) > tstop) s_big = 1;
@@ -516,7 +516,7 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
             const double app = D[p], aqq = D[q];
             const int hyp = (sg[p] == sg[q]) ? -1 : 1;
             double t, c, qv;
-            const int fl = pair_decision(app, aqq, apq, hyp, tol, t, c, qv);
+            const int fl = pair_decision_fast(app, aqq, apq, hyp, tol, t, c, qv);
             put_params(s, k, t, c, qv, apq, fl);
         }
     };
@@ -618,7 +618,7 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
                 const double sk = fk ? s_k * Cc[b][k] : s_k, sq = fj ? s_q * Cc[b][j] : s_q;
                 const double apq = (sk * sq) * v;
                 const int hyp = (sg[k] == sg[q2]) ? -1 : 1;
-                nx_fl = pair_decision_eager(app, aqq, apq, hyp, tol, nx_t, nx_c, nx_qv);
+                nx_fl = pair_decision_fast(app, aqq, apq, hyp, tol, nx_t, nx_c, nx_qv);
                 nx_apq = apq;
             }
         } else {
@@ -922,7 +922,7 @@ k_solve_ring(const double *__restrict__ part, int nsplit, int full_part, double 
         const double apq = (Sc[e.x] * Sc[e.y]) * pool[ring_buf_lo(e) * NN + e.y];
         const int hyp = (sg[e.x] == sg[e.y]) ? -1 : 1;
         double t, c, qv;
-        const int fl = pair_decision(D[e.x], D[e.y], apq, hyp, tol, t, c, qv);
+        const int fl = pair_decision_fast(D[e.x], D[e.y], apq, hyp, tol, t, c, qv);
         put_params(0, k, t, c, qv, apq, fl);
     }
     cluster.sync();
@@ -1033,7 +1033,7 @@ k_solve_ring(const double *__restrict__ part, int nsplit, int full_part, double 
                 const double aqq = rj ? fma(hi_p ? htj : tj, Apq[b][sj], d_hi) : d_hi;
                 const double sl = ri ? s_lo * Cc[b][si] : s_lo, sh = rj ? s_hi * Cc[b][sj] : s_hi;
                 const double apq = (sl * sh) * v;
-                nx_fl = pair_decision_eager(app, aqq, apq, trig_n ? -1 : 1, tol, nx_t, nx_c, nx_qv);
+                nx_fl = pair_decision_fast(app, aqq, apq, trig_n ? -1 : 1, tol, nx_t, nx_c, nx_qv);
                 nx_apq = apq;
             }
         } else {
@@ -1144,7 +1144,7 @@ k_solve_ring(const double *__restrict__ part, int nsplit, int full_part, double 
                 const double apq = (Sc[e.x] * Sc[e.y]) * pool[bf * NN + e.y];
                 const int hyp = (sg[e.x] == sg[e.y]) ? -1 : 1;
                 double t, c, qv;
-                const int fd = pair_decision(D[e.x], D[e.y], apq, hyp, tol, t, c, qv);
+                const int fd = pair_decision_fast(D[e.x], D[e.y], apq, hyp, tol, t, c, qv);
                 put_params(s + 1, k, t, c, qv, apq, fd);
             }
             if (ahead) put_params(s + 1, (k0 + lane) % h, nx_t, nx_c, nx_qv, nx_apq, nx_fl);

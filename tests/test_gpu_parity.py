@@ -298,6 +298,50 @@ def test_kernel_inner_solve_matches_model(api, b, mode):
         assert np.array_equal(Ao[k], Ar), np.max(np.abs(Ao[k] - Ar))
 
 
+def _threshold_blocks(b, seed, npairs=3):
+    """Pivot blocks whose off-diagonal entries sit on the threshold of Eq. 2.3,
+    tol sqrt(a_ii a_jj) rounded as the test rounds it: exactly on it (the pair
+    rotates), one ulp below (it passes), and 2^-14 .. 2^-20 to either side --
+    inside and outside the margin within which the kernels' test falls back to
+    the plain expression."""
+    nn = 2 * b
+    tol = nn * U64
+    rng = np.random.default_rng(seed)
+    As, sg = [], []
+    rel = [0.0, -1.0, 2.0 ** -14, -(2.0 ** -14), 2.0 ** -17, -(2.0 ** -17), 2.0 ** -20, -(2.0 ** -20), 0.5, -0.5]
+    for k in range(npairs):
+        d = 10.0 ** rng.uniform(-4, 2, nn)
+        A = np.diag(d)
+        for x in range(nn):
+            for y in range(x + 1, nn):
+                T = tol * np.sqrt(d[x] * d[y])
+                r = rel[rng.integers(len(rel))]
+                v = np.nextafter(T, 0.0) if r == -1.0 else T * (1.0 + r)
+                A[x, y] = A[y, x] = v * rng.choice([-1.0, 1.0])
+        As.append(A)
+        sg.append(W.signs_block(nn, [nn // 2, 5, nn][k % 3]))
+    return np.stack(As), np.stack(sg)
+
+
+@pytest.mark.parametrize("b,mode", [(16, 1), (16, 2), (64, 1), (64, 2), (32, 0)])
+def test_kernel_threshold_pairs_match_model(api, b, mode):
+    """Entries on the threshold of Eq. 2.3 (the kernels decide clear cases
+    from exponents and single-precision mantissas and the rest with the plain
+    expression; the model always uses the plain expression): kernel and
+    model agree bit for bit, rotation counts included."""
+    from oracle import inner_model
+
+    nn = 2 * b
+    As, sg = _threshold_blocks(b, 900 + b + mode)
+    tol = nn * U64
+    Ao, Wg, rot = _gpu_inner(api, As, sg, tol, mode)
+    for k in range(As.shape[0]):
+        Ar, Wr, nrot, passes, s = inner_model.inner_solve(As[k], sg[k], tol, mode=mode, max_passes=10)
+        assert s == 0 and nrot == rot[k] and 0 < nrot
+        assert np.array_equal(Wg[k], Wr), np.max(np.abs(Wg[k] - Wr))
+        assert np.array_equal(Ao[k], Ar), np.max(np.abs(Ao[k] - Ar))
+
+
 @pytest.mark.parametrize("b,mode", [(64, 0), (64, 1), (64, 2), (32, 0)])
 def test_kernel_inner_solve_renormalising_blocks_match_model(api, b, mode):
     """Ungraded pivot blocks (P^T P, P standard normal): the large early

@@ -20,7 +20,8 @@ SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), 
 MUTANTS = {
     "hyperbolic_theta_sign": ("zeta = -(aii + ajj) / (2.0 * aij);", "zeta = (aii + ajj) / (2.0 * aij);"),
     "trig_zeta_swapped": ("zeta = (ajj - aii) / (2.0 * aij);", "zeta = (aii - ajj) / (2.0 * aij);"),
-    "hyperbolic_cosh_as_cos": ("*c = 1.0 / sqrt((1.0 - tt) * (1.0 + tt));", "*c = 1.0 / sqrt(1.0 + tt * tt);"),
+    "hyperbolic_cosh_as_cos": ("*c = orc_cosine(tt, 1, 1.0 / sqrt((1.0 - tt) * (1.0 + tt)));",
+                               "*c = orc_cosine(tt, -1, 1.0 / sqrt(1.0 + tt * tt));"),
     "update_drops_hyp": ("    double ht = hyp < 0 ? -t : t;\n    for (int64_t i = 0; i < m; ++i) {",
                          "    double ht = t;\n    for (int64_t i = 0; i < m; ++i) {"),
     "update_operands_transposed": ("x[i] = fma(ht, yi, xi) * c;", "x[i] = fma(ht, xi, yi) * c;"),

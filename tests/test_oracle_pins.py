@@ -81,6 +81,39 @@ def test_rotation_eq26_and_junitary(orc, hyp):
         assert np.max(np.abs(R.T @ J2 @ R - J2)) <= 8 * U * max(1.0, c * c)
 
 
+def test_rotation_cosine_unbiased(orc):
+    """c = 1/sqrt(1 - hyp t^2) to rounding and without bias: over rotations
+    with t^2 between u and 2^-30 the mean of c^2 (1 - hyp t^2) - 1 (exact
+    rational arithmetic on the returned doubles) is within 0.1 u of 0, each
+    within 2 u.  Evaluated as two rounded operations, 1/sqrt(1 + t^2) leans
+    up by about u on average here (checked below as well): over the ~10^5
+    rotations a column takes at n = 4096 that bias scales every sigma up by
+    about 1e-12."""
+    rng = np.random.default_rng(21)
+    F = Fraction
+    ours, naive = [], []
+    for k in range(3000):
+        hyp = -1 if k % 2 == 0 else 1
+        aii = 1.0 + rng.random()
+        ajj = aii * (1.0 + 0.5 * rng.random()) if hyp < 0 else aii * rng.random()
+        b = (ajj - aii) if hyp < 0 else -(aii + ajj)
+        tau = 10.0 ** rng.uniform(-7.8, -4.5)
+        aij = rng.choice([-1.0, 1.0]) * abs(b) * tau
+        t, c, st = orc.rotation(aii, ajj, aij, hyp)
+        assert st == 0
+        if not U <= t * t <= 2.0 ** -30:
+            continue
+        x = 1 - hyp * F(t) ** 2
+        ours.append(float(F(c) ** 2 * x - 1) / U)
+        xn = 1.0 - hyp * t * t if hyp < 0 else (1.0 - t) * (1.0 + t)
+        naive.append(float(F(1.0 / np.sqrt(xn)) ** 2 * x - 1) / U)
+    ours, naive = np.array(ours), np.array(naive)
+    assert len(ours) >= 2000
+    assert np.max(np.abs(ours)) <= 2.0
+    assert abs(ours.mean()) <= 0.1
+    assert naive.mean() >= 0.5
+
+
 def test_rotation_closed_form_values(orc):
     # a_ii = a_jj: trigonometric rotation by pi/4 exactly
     t, c, st = orc.rotation(1.0, 1.0, 0.5, -1)
