@@ -129,27 +129,21 @@ __device__ __forceinline__ bool rotation_params(double aii, double ajj, double a
     return true;
 }
 
-// The test of Eq. 2.3, then the rotation of Sec. 2 for a pair that fails it.
-// Returns 0 (the pair passes), 1 (rotate with t, c; qv = 1/c) or 2 (rank
-// deficient); t = 0, c = qv = 1 unless it returns 1.  Late in the iteration
-// most pairs pass, so the rotation's divides and square roots are skipped.
+// The test of Eq. 2.3, then the rotation of Sec. 2 (rotation_params) for a
+// pair that fails it: the one-sided pointwise kernels, whose rotations are
+// the oracle's bit for bit (a tangent threshold of Eq. 4.2 then stops them
+// at the oracle's sweep).  Returns 0 (the pair passes), 1 (rotate with t, c)
+// or 2 (rank deficient); t = 0, c = 1 unless it returns 1.
 __device__ __forceinline__ int pair_decision(double aii, double ajj, double aij, int hyp, double tol,
-                                             double &t, double &c, double &qv) {
+                                             double &t, double &c) {
     t = 0.0;
     c = 1.0;
-    qv = 1.0;
     if (pair_passes(aii, ajj, aij, tol)) return 0;
     double tt, cc, qq;
     if (!rotation_params(aii, ajj, aij, hyp, tt, cc, qq)) return 2;
     t = tt;
     c = cc;
-    qv = qq;
     return 1;
-}
-__device__ __forceinline__ int pair_decision(double aii, double ajj, double aij, int hyp, double tol,
-                                             double &t, double &c) {
-    double qv;
-    return pair_decision(aii, ajj, aij, hyp, tol, t, c, qv);
 }
 
 // The rotation of rotation_params with few double-precision instructions.
@@ -211,10 +205,12 @@ __device__ __forceinline__ bool rotation_params_fast(double aii, double ajj, dou
     return true;
 }
 
-// pair_decision with rotation_params_fast: the rotation of the inner-solve
-// kernels of the block method.  Late in the iteration most pairs pass and
-// the rotation is skipped; evaluating it eagerly gains nothing on a warp
-// whose double-precision instructions issue one at a time.
+// The test of Eq. 2.3, then the rotation of Sec. 2 (rotation_params_fast) for
+// a pair that fails it.  Returns 0 (the pair passes), 1 (rotate with t, c;
+// qv = 1/c) or 2 (rank deficient); t = 0, c = qv = 1 unless it returns 1.
+// Late in the iteration most pairs pass and the rotation is skipped;
+// evaluating it eagerly gains nothing on a warp whose double-precision
+// instructions issue one at a time.
 __device__ __forceinline__ int pair_decision_fast(double aii, double ajj, double aij, int hyp, double tol,
                                                   double &t, double &c, double &qv) {
     t = 0.0;

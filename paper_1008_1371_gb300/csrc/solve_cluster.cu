@@ -572,12 +572,13 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
             s_k = Sc[k];
             s_q = Sc[q2];
         }
-        // the step's coefficients from its starting scales
-        if (mt >= 0 && mt < h && (Fl[b][mt] & 1)) {
-            const int p = mt, q = h + (mt + s) % h;
-            const double t = T[b][mt], ht = (sg[p] == sg[q]) ? -t : t;
-            Al[mt] = ht * (Sc[q] * Rc[p]);
-            Be[mt] = t * (Sc[p] * Rc[q]);
+        // the step's coefficients from its starting scales (alpha by threads
+        // [0, h), beta by [h, 2h): two FP64 instructions per warp)
+        if (mt >= 0 && mt < 2 * h && (Fl[b][mt % h] & 1)) {
+            const int j = mt % h, p = j, q = h + (j + s) % h;
+            const double t = T[b][j];
+            if (mt < h) Al[j] = ((sg[p] == sg[q]) ? -t : t) * (Sc[q] * Rc[p]);
+            else Be[j] = t * (Sc[p] * Rc[q]);
         }
         // every CTA sees every pair's flags: the same decision everywhere
         const int f = tid < h ? Fl[b][tid] : 0;
@@ -678,27 +679,36 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
                 col_mix(false);
             }
             mix_sync<LA>(kMixThreads);
-            // Eq. 2.6 on the replicated diagonal, the owned pairs' own stored
-            // entries to 0, and the new scales of the rotated rows
-            if (mt < h && (Fl[b][mt] & 1)) {
-                const int p = mt, q = h + (mt + s) % h;
-                const double t = T[b][mt], ht = (sg[p] == sg[q]) ? -t : t, apq = Apq[b][mt];
-                D[p] = fma(ht, apq, D[p]);
-                D[q] = fma(t, apq, D[q]);
-                if (p >= k0 && p < k0 + P) {
-                    const int kl = p - k0;
-                    double *rp = fix + kl * NN, *rq = mov + slot(kl) * NN;
-                    rp[p] = 0.0;
-                    rp[q] = 0.0;
-                    rq[q] = 0.0;
-                    rq[p] = 0.0;
+            // Eq. 2.6 on the replicated diagonal and the owned pairs' own
+            // stored entries to 0 (threads [0, h)), the new scales (threads
+            // [h, 2h)) and their reciprocals (threads [2h, 3h)) of the rotated
+            // rows: three warp groups, so that no warp's chain of FP64
+            // instructions (one issues every 64 cycles) holds up the step
+            static_assert(kMixThreads >= 3 * h, "three groups of h mixing threads");
+            if (mt < 3 * h && (Fl[b][mt % h] & 1)) {
+                const int j = mt % h, p = j, q = h + (j + s) % h;
+                if (mt < h) {
+                    const double t = T[b][j], ht = (sg[p] == sg[q]) ? -t : t, apq = Apq[b][j];
+                    D[p] = fma(ht, apq, D[p]);
+                    D[q] = fma(t, apq, D[q]);
+                    if (p >= k0 && p < k0 + P) {
+                        const int kl = p - k0;
+                        double *rp = fix + kl * NN, *rq = mov + slot(kl) * NN;
+                        rp[p] = 0.0;
+                        rp[q] = 0.0;
+                        rq[q] = 0.0;
+                        rq[p] = 0.0;
+                    }
+                } else if (mt < 2 * h) {
+                    const double c = Cc[b][j];
+                    Sc[p] = Sc[p] * c;
+                    Sc[q] = Sc[q] * c;
+                    if (scale_out_of_range(Sc[p]) || scale_out_of_range(Sc[q])) s_renorm = 1;
+                } else {
+                    const double qv = Qv[b][j];
+                    Rc[p] = Rc[p] * qv;
+                    Rc[q] = Rc[q] * qv;
                 }
-                const double c = Cc[b][mt], qv = Qv[b][mt];
-                Sc[p] = Sc[p] * c;
-                Sc[q] = Sc[q] * c;
-                Rc[p] = Rc[p] * qv;
-                Rc[q] = Rc[q] * qv;
-                if (scale_out_of_range(Sc[p]) || scale_out_of_range(Sc[q])) s_renorm = 1;
             }
         }
         __syncthreads();
@@ -986,12 +996,13 @@ k_solve_ring(const double *__restrict__ part, int nsplit, int full_part, double 
             trig_j = sg[fj.x] == sg[fj.y];
             trig_n = sg[ne.x] == sg[ne.y];
         }
-        // the step's coefficients from its starting scales
-        if (mt >= 0 && mt < h && (Fl[b][mt] & 1)) {
-            const int p = cur[mt].x, q = cur[mt].y;
-            const double t = T[b][mt], ht = (sg[p] == sg[q]) ? -t : t;
-            Al[mt] = ht * (Sc[q] * Rc[p]);
-            Be[mt] = t * (Sc[p] * Rc[q]);
+        // the step's coefficients from its starting scales (alpha by threads
+        // [0, h), beta by [h, 2h))
+        if (mt >= 0 && mt < 2 * h && (Fl[b][mt % h] & 1)) {
+            const int j = mt % h, p = cur[j].x, q = cur[j].y;
+            const double t = T[b][j];
+            if (mt < h) Al[j] = ((sg[p] == sg[q]) ? -t : t) * (Sc[q] * Rc[p]);
+            else Be[j] = t * (Sc[p] * Rc[q]);
         }
         // every CTA sees every pair's flags: the same decision everywhere
         const int f = tid < h ? Fl[b][tid] : 0;
@@ -1097,27 +1108,35 @@ k_solve_ring(const double *__restrict__ part, int nsplit, int full_part, double 
                 col_mix(false);
             }
             mix_sync<LA>(kMixThreads);
-            // Eq. 2.6 on the replicated diagonal, the owned pairs' own stored
-            // entries to 0, and the new scales of the rotated rows
-            if (mt < h && (Fl[b][mt] & 1)) {
-                const int4 e = cur[mt];
+            // Eq. 2.6 on the replicated diagonal and the owned pairs' own
+            // stored entries to 0, the new scales and their reciprocals of
+            // the rotated rows, in three warp groups (as in the cross pass)
+            static_assert(kMixThreads >= 3 * h, "three groups of h mixing threads");
+            if (mt < 3 * h && (Fl[b][mt % h] & 1)) {
+                const int j = mt % h;
+                const int4 e = cur[j];
                 const int p = e.x, q = e.y;
-                const double t = T[b][mt], ht = (sg[p] == sg[q]) ? -t : t, apq = Apq[b][mt];
-                D[p] = fma(ht, apq, D[p]);
-                D[q] = fma(t, apq, D[q]);
-                if (mt >= k0 && mt < k0 + P) {
-                    double *rp = pool + ring_buf_lo(e) * NN, *rq = pool + ring_buf_hi(e) * NN;
-                    rp[p] = 0.0;
-                    rp[q] = 0.0;
-                    rq[q] = 0.0;
-                    rq[p] = 0.0;
+                if (mt < h) {
+                    const double t = T[b][j], ht = (sg[p] == sg[q]) ? -t : t, apq = Apq[b][j];
+                    D[p] = fma(ht, apq, D[p]);
+                    D[q] = fma(t, apq, D[q]);
+                    if (j >= k0 && j < k0 + P) {
+                        double *rp = pool + ring_buf_lo(e) * NN, *rq = pool + ring_buf_hi(e) * NN;
+                        rp[p] = 0.0;
+                        rp[q] = 0.0;
+                        rq[q] = 0.0;
+                        rq[p] = 0.0;
+                    }
+                } else if (mt < 2 * h) {
+                    const double c = Cc[b][j];
+                    Sc[p] = Sc[p] * c;
+                    Sc[q] = Sc[q] * c;
+                    if (scale_out_of_range(Sc[p]) || scale_out_of_range(Sc[q])) s_renorm = 1;
+                } else {
+                    const double qv = Qv[b][j];
+                    Rc[p] = Rc[p] * qv;
+                    Rc[q] = Rc[q] * qv;
                 }
-                const double c = Cc[b][mt], qv = Qv[b][mt];
-                Sc[p] = Sc[p] * c;
-                Sc[q] = Sc[q] * c;
-                Rc[p] = Rc[p] * qv;
-                Rc[q] = Rc[q] * qv;
-                if (scale_out_of_range(Sc[p]) || scale_out_of_range(Sc[q])) s_renorm = 1;
             }
         }
         __syncthreads();
