@@ -400,6 +400,8 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
     __shared__ double tr_max[C], tr_sum[C], tr_red[2][kT / 32];
     __shared__ int s_first[C];        // per CTA: first step with a pair failing Eq. 2.3 on A_P
     __shared__ int s_own;
+    __shared__ int s_tot[2];          // rotations counted by warps 0 and 1
+    static_assert(h <= 64, "the rotation count lives in warps 0 and 1");
 
     auto entry = [&](int x, int y) -> double {
         if (!part) return A_io[(size_t)pair * NN * NN + x + y * NN];
@@ -582,14 +584,16 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
         }
         // every CTA sees every pair's flags: the same decision everywhere
         const int f = tid < h ? Fl[b][tid] : 0;
-        if ((f & 1) && fabs(T[b][tid]) > tstop) big = 1;
-        const int nrot = __syncthreads_count(f & 1);
+        if (tbig && (f & 1) && fabs(T[b][tid]) > tstop) big = 1;
         bad = __syncthreads_or(f & 2);
         if (bad) {
             s_end = s;
             break;
         }
-        total += nrot;
+        // the step's rotations, counted by the warps holding the flags (one
+        // CTA barrier per step instead of two); lane 0 of warp w keeps warp
+        // w's count
+        if (warp * 32 < h) total += __popc(__ballot_sync(0xffffffffu, f & 1));
         if (LA && warp == 0) {
             if (ahead) {
                 const int kl = lane, k = k0 + kl, j = (k + 1) % h, q2 = h + (j + s) % h, qk = h + (k + s) % h;
@@ -740,9 +744,12 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
             ao[x + (size_t)y * NN] = x == y ? D[x] : (Sc[x] * Sc[y]) * mov[((kl + s_end) % (P + 1)) * NN + y];
         }
     }
+    if (lane == 0 && warp * 32 < h) s_tot[warp] = total;
     cluster.sync();
     const int any_big = tbig ? __syncthreads_or(big) : 0;
     if (rank == 0 && tid == 0) {
+        total = 0;
+        for (int w = 0; w * 32 < h; ++w) total += s_tot[w];
         rotated[pair] = total;
         if (rot_count && total) atomicAdd(rot_count, (unsigned long long)total);
         if (bad && status) atomicExch(status, HSVD_ERR_RANK);
@@ -821,6 +828,8 @@ k_solve_ring(const double *__restrict__ part, int nsplit, int full_part, double 
     __shared__ int Fl[2][h];         // bit 0: rotate, bit 1: rank deficient
     __shared__ double Sc[NN], Rc[NN];  // column scales of the stored block and their reciprocals
     __shared__ double Al[h], Be[h];    // the step's scaled-rotation coefficients
+    __shared__ int s_tot[2];           // rotations counted by warps 0 and 1
+    static_assert(h <= 64, "the rotation count lives in warps 0 and 1");
     __shared__ int s_renorm;
     __shared__ int4 tb[3][h];        // ring table rows of steps s, s + 1, s + 2 (at step % 3)
     __shared__ double tr_max[C], tr_sum[C], tr_red[2][kT / 32];
@@ -1006,14 +1015,16 @@ k_solve_ring(const double *__restrict__ part, int nsplit, int full_part, double 
         }
         // every CTA sees every pair's flags: the same decision everywhere
         const int f = tid < h ? Fl[b][tid] : 0;
-        if ((f & 1) && fabs(T[b][tid]) > tstop) big = 1;
-        const int nrot = __syncthreads_count(f & 1);
+        if (tbig && (f & 1) && fabs(T[b][tid]) > tstop) big = 1;
         bad = __syncthreads_or(f & 2);
         if (bad) {
             s_end = s;
             break;
         }
-        total += nrot;
+        // the step's rotations, counted by the warps holding the flags (one
+        // CTA barrier per step instead of two); lane 0 of warp w keeps warp
+        // w's count
+        if (warp * 32 < h) total += __popc(__ballot_sync(0xffffffffu, f & 1));
         if (LA && warp == 0) {
             if (ahead) {
                 const int ri = Fl[b][si] & 1, rj = Fl[b][sj] & 1;
@@ -1191,9 +1202,12 @@ k_solve_ring(const double *__restrict__ part, int nsplit, int full_part, double 
             ao[x + (size_t)y * NN] = x == y ? D[x] : (Sc[x] * Sc[y]) * pool[bf * NN + y];
         }
     }
+    if (lane == 0 && warp * 32 < h) s_tot[warp] = total;
     cluster.sync();
     const int any_big = tbig ? __syncthreads_or(big) : 0;
     if (rank == 0 && tid == 0) {
+        total = 0;
+        for (int w = 0; w * 32 < h; ++w) total += s_tot[w];
         rotated[pair] = total;
         if (rot_count && total) atomicAdd(rot_count, (unsigned long long)total);
         if (bad && status) atomicExch(status, HSVD_ERR_RANK);
