@@ -361,10 +361,14 @@ int solve_blocked_core(const double *G, int64_t m, int64_t n, int64_t ldg, const
     // stream orders the reuse of the slot's buffers kRing steps later.  The
     // group size keeps the graph near kMaxNodes kernel nodes per sweep: the
     // GPU dispatches graph nodes at a bounded rate (about 2 us per node
-    // measured), which would otherwise bound the sweep.
+    // measured), which would otherwise bound the sweep.  From n = 4096 a
+    // visit's kernels take hundreds of microseconds and twice the nodes
+    // (smaller groups, more overlap) measured faster (Haar 4096, split
+    // precision: 1263 against 1275 ms; 11 visits per group: 1344 ms).
     const int kpv = prec ? 4 : 3;  // kernels per visit
-    const int grp = (int)std::min<int64_t>(npairs, std::max<int64_t>(1, ((int64_t)nb * npairs * kpv + kMaxNodes - 1) /
-                                                                          kMaxNodes));
+    const int64_t max_nodes = n_pad >= 4096 ? 2 * kMaxNodes : kMaxNodes;
+    const int grp = (int)std::min<int64_t>(npairs, std::max<int64_t>(1, ((int64_t)nb * npairs * kpv + max_nodes - 1) /
+                                                                          max_nodes));
     auto capture_pairs = [&](const int *tab, const int *vis, const std::vector<int> &nact,
                              const std::vector<int> &off, const int *tab_host, cudaGraph_t *graph,
                              long long *launches) -> cudaError_t {
