@@ -530,7 +530,7 @@ k_solve_cross(const double *__restrict__ part, int nsplit, int full_part, double
     // j = k + 1 and the diagonal values a_kk, a_q'q', forms the step-s values
     // of a_kq' and of the two diagonal entries with the same operations as the
     // bulk update below, and computes the (t, c) of pair (k, q') for step
-    // s + 1 while warps 1..7 update the rows (named barrier 1).
+    // s + 1 while warps 1..8 update the rows (named barrier 1).
     // Without the look-ahead (LA = false) every warp mixes and the owners
     // compute the next parameters after the update.
     constexpr int kMixThreads = LA ? kT - 32 : kT;
