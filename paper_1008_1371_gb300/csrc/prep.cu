@@ -64,6 +64,11 @@ __global__ void k_sort_positions(const double *__restrict__ d, const int8_t *__r
     const bool act = a < n_pad;
     const int grp = act ? sgn[a] : 0;
     const double key = (act && sort) ? d[a] : 0.0;
+    // keys between +0 and +inf compare as their bit patterns (integer
+    // instructions; an FP64 comparison issues at the FP64 rate): the same
+    // order and the same ties as the floating-point comparison
+    constexpr unsigned long long kInf = 0x7FF0000000000000ull;
+    const unsigned long long kbits = (unsigned long long)__double_as_longlong(key);
     int64_t rank = 0, nplus = 0;
     for (int64_t t0 = 0; t0 < n_pad; t0 += kTile) {
         const int len = (int)min((int64_t)kTile, n_pad - t0);
@@ -80,8 +85,16 @@ __global__ void k_sort_positions(const double *__restrict__ d, const int8_t *__r
             const int64_t b = t0 + i;
             if (gb != grp || b == a) continue;
             const double kb = sd[i];
-            const bool before = (grp > 0) ? (kb > key) : (kb < key);
-            if (before || (kb == key && b < a)) ++rank;
+            const unsigned long long bbits = (unsigned long long)__double_as_longlong(kb);
+            bool before, tie;
+            if (kbits <= kInf && bbits <= kInf) {
+                before = (grp > 0) ? (bbits > kbits) : (bbits < kbits);
+                tie = bbits == kbits;
+            } else {
+                before = (grp > 0) ? (kb > key) : (kb < key);
+                tie = kb == key;
+            }
+            if (before || (tie && b < a)) ++rank;
         }
     }
     if (act) newpos[(grp > 0 ? 0 : nplus) + rank] = (int)a;
